@@ -1,0 +1,190 @@
+"""Pins of the oracle's Schwarz and multilevel steps (paper Sec. 3-4)."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import inpaint_ref as ref
+from oracle import oras_ref as oras
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _case(rng, H, W, d=0.08):
+    f = rng.uniform(0, 255, size=(H, W))
+    m = (rng.uniform(size=(H, W)) < d).astype(np.uint8)
+    m[rng.integers(H), rng.integers(W)] = 1
+    return f, m
+
+
+def test_paper_local_problem_count():
+    """Sec. 4: block 32, overlap 6 -> 36852 local problems for 4K RGB."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "paper_layout_counts.txt"))
+            if l.strip() and not l.startswith("#")]
+    for W, H, C, b, o, n in (map(int, r) for r in rows):
+        assert oras.block_count(W, b, o) * oras.block_count(H, b, o) * C == n
+        assert len(oras.subdomains(H, W, b, o)) * C == n
+
+
+@pytest.mark.parametrize("n,b,o", [(3840, 32, 6), (2160, 32, 6), (256, 32, 4), (1920, 64, 4),
+                                   (100, 32, 5), (31, 32, 6), (5, 32, 6), (33, 16, 1), (97, 96, 8)])
+def test_axis_partition_of_unity(n, b, o):
+    """sum_i R_i^T D_i R_i = I on one axis: cores are disjoint, cover every
+    pixel once, and lie inside their block; blocks cover the axis."""
+    blocks = oras.axis_blocks(n, b, o)
+    own = np.zeros(n, dtype=int)
+    cov = np.zeros(n, dtype=int)
+    for j, (lo, hi, olo, ohi) in enumerate(blocks):
+        assert 0 <= lo < hi <= n and hi - lo <= b
+        assert lo <= olo < ohi <= hi
+        own[olo:ohi] += 1
+        cov[lo:hi] += 1
+        for x in range(olo, ohi):
+            assert oras.owner_of(x, n, b, o) == j
+    assert np.all(own == 1) and np.all(cov >= 1)
+    assert blocks[-1][1] == n
+
+
+def test_partition_of_unity_2d():
+    H, W, b, o = 45, 70, 16, 3
+    acc = np.zeros((H, W), dtype=int)
+    for (y0, y1, x0, x1, oy0, oy1, ox0, ox1) in oras.subdomains(H, W, b, o):
+        acc[oy0:oy1, ox0:ox1] += 1
+    assert np.all(acc == 1)
+
+
+def test_ras_local_matrix_is_RART(rng):
+    """With p_R = 1 the local matrix is literally R_i A R_i^T (Eq.
+    eq:ras-local-problem), R_i built as a 0/1 selection matrix."""
+    f, m = _case(rng, 20, 23)
+    A = ref.assemble_A(m)
+    for blk in oras.subdomains(20, 23, 8, 2)[::5]:
+        idx, M = oras.local_matrix(A, m, blk, 1.0)
+        R = sp.csr_matrix((np.ones(idx.size), (np.arange(idx.size), idx)), shape=(idx.size, 20 * 23))
+        assert abs(M - R @ A @ R.T).max() == 0.0
+
+
+def test_oras_interface_diagonal(rng):
+    """ORAS changes only interface diagonals of unknown pixels, by (p_R - 1)
+    per in-image neighbour outside the block."""
+    H, W = 12, 12
+    m = np.zeros((H, W), dtype=np.uint8); m[0, 0] = 1
+    A = ref.assemble_A(m)
+    blk = (4, 8, 4, 8, 0, 0, 0, 0)
+    idx, M1 = oras.local_matrix(A, m, blk, 1.0)
+    _, Mp = oras.local_matrix(A, m, blk, 0.25)
+    d = (Mp - M1).diagonal().reshape(4, 4)
+    exp = np.zeros((4, 4))
+    exp[0, :] += 1; exp[-1, :] += 1; exp[:, 0] += 1; exp[:, -1] += 1
+    assert np.allclose(d, -0.75 * exp)
+    assert abs((Mp - M1) - sp.diags((Mp - M1).diagonal())).max() == 0.0
+
+
+def test_local_cg_exact_after_n_steps(rng):
+    """CG terminates in at most n steps in exact arithmetic: with k = n it
+    matches a dense solve of the local SPD system."""
+    f, m = _case(rng, 10, 10, 0.3)
+    A = ref.assemble_A(m)
+    blk = oras.subdomains(10, 10, 5, 1)[4]
+    idx, M = oras.local_matrix(A, m, blk, 0.4)
+    unk = m.ravel()[idx] == 0
+    Muu = M[unk][:, unk]
+    rhs = rng.normal(size=unk.sum())
+    x = oras.cg_fixed(Muu, rhs, int(unk.sum()))
+    assert np.max(np.abs(x - np.linalg.solve(Muu.toarray(), rhs))) <= 1e-8
+    # symmetric positive definite
+    D = Muu.toarray()
+    assert np.allclose(D, D.T) and np.linalg.eigvalsh(D).min() > 0
+
+
+def test_single_block_one_sweep_is_exact(rng):
+    """One block covering the image: R = I, no interface, so one sweep with
+    an exact local solve gives the solution of A u = b."""
+    f, m = _case(rng, 13, 17)
+    u1, rn = oras.oras_sweep(ref.initial_guess(f, m), f, m, 32, 6, 0.3, None)
+    assert np.max(np.abs(u1 - ref.solve_direct(f, m))) <= 1e-9
+    assert rn[0] == pytest.approx(ref.residual_norms(ref.initial_guess(f, m), f, m)[0])
+
+
+@pytest.mark.parametrize("p,k", [(1.0, None), (0.3, None), (0.3, 8), (0.1, 4)])
+def test_fixed_point_is_exact_solution(rng, p, k):
+    f, m = _case(rng, 40, 36, 0.06)
+    u, n = oras.oras_solve(f, m, 12, 3, p, k, 1e-10, 400)
+    assert ref.rel_residual(u, f, m)[0] <= 1e-10
+    assert np.max(np.abs(u - ref.solve_direct(f, m))) <= 1e-6
+
+
+def test_sweep_keeps_known_pixels(rng):
+    f, m = _case(rng, 30, 30)
+    u, _ = oras.oras_sweep(ref.initial_guess(f, m), f, m, 10, 2, 0.3, 5)
+    assert np.array_equal(u[m != 0], f[m != 0])
+
+
+def test_oras_beats_ras():
+    """Sec. 3: ORAS converges faster than RAS (soft check, exact local solves)."""
+    import synth
+    f, m = synth.make_frame(96, 96, 1, 0.05, "uniform", 11)
+    _, n_ras = oras.oras_solve(f, m, 32, 4, 1.0, None, 1e-6, 100)
+    _, n_oras = oras.oras_solve(f, m, 32, 4, 0.3, None, 1e-6, 100)
+    assert n_oras < n_ras
+
+
+def test_restrict_hand_example():
+    """Worked 3x4 -> 2x2 example: a coarse pixel is known iff one of its
+    (up to) four fine pixels is known; its value is the mean of the known
+    fine values (Sec. 4)."""
+    f = np.array([[10., 20., 30., 40.],
+                  [50., 60., 70., 80.],
+                  [90., 11., 12., 13.]])
+    m = np.array([[1, 0, 0, 0],
+                  [0, 1, 0, 0],
+                  [1, 1, 0, 1]], dtype=np.uint8)
+    fc, mc = oras.restrict_level(f, m)
+    assert mc.tolist() == [[1, 0], [1, 1]]
+    assert fc[0, 0] == pytest.approx((10 + 60) / 2)
+    assert fc[1, 0] == pytest.approx((90 + 11) / 2)
+    assert fc[1, 1] == pytest.approx(13.0)
+    assert fc[0, 1] == 0.0
+
+
+def test_restrict_invariants(rng):
+    f, m = _case(rng, 37, 52, 0.05)
+    fc, mc = oras.restrict_level(f, m)
+    assert mc.shape == (19, 26)
+    assert mc.mean() >= m.mean()                       # density grows (Sec. 4)
+    fcc, _ = oras.restrict_level(np.full_like(f, 9.5), m)
+    assert np.all(fcc[mc != 0] == 9.5)
+    for Y in range(19):
+        for X in range(26):
+            blk_m = m[2 * Y:2 * Y + 2, 2 * X:2 * X + 2] != 0
+            blk_f = f[2 * Y:2 * Y + 2, 2 * X:2 * X + 2]
+            assert bool(mc[Y, X]) == bool(blk_m.any())
+            if blk_m.any():
+                assert blk_f[blk_m].min() - 1e-12 <= fc[Y, X] <= blk_f[blk_m].max() + 1e-12
+
+
+def test_prolong_reproduces_affine():
+    Hc, Wc = 9, 12
+    Y, X = np.mgrid[0:Hc, 0:Wc].astype(float)
+    uc = 2.0 * X - 3.0 * Y + 1.0
+    u = oras.prolong_bilinear(uc, 18, 24)
+    y, x = np.mgrid[0:18, 0:24].astype(float)
+    exp = 2.0 * (x - 0.5) / 2 - 3.0 * (y - 0.5) / 2 + 1.0
+    inner = (slice(1, 17), slice(1, 23))                # away from the clamp
+    assert np.max(np.abs(u[inner] - exp[inner])) <= 1e-12
+    assert np.allclose(oras.prolong_bilinear(np.full((4, 5), 3.0), 7, 9), 3.0)
+
+
+def test_prolong_convex(rng):
+    uc = rng.uniform(-5, 5, size=(6, 7))
+    u = oras.prolong_bilinear(uc, 11, 14)
+    assert u.min() >= uc.min() - 1e-12 and u.max() <= uc.max() + 1e-12
+
+
+def test_cascade_converges_to_solution():
+    import synth
+    f, m = synth.make_frame(64, 80, 1, 0.05, "edge", 5)
+    u, counts = oras.cascade_solve(f, m, 3, 16, 4, 0.3, 8, 1e-8, 200, 1e-2)
+    assert len(counts) == 3
+    assert np.max(np.abs(u - ref.solve_direct(f, m))) <= 1e-4
