@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Throughput of 4K RGB homogeneous diffusion inpainting to relative residual 1e-6.
+
+One step = one frame through the whole solver path: load mask and known values
+(encode, dyadic hierarchy, block masks), coarse-to-fine ORAS initialisation,
+fine-level ORAS sweeps with the FP64 outer residual correction, and the output
+write.  Frames: 3840x2160 RGB, 3 % edge-clustered masks, seeded synthetic
+fields (the paper's test photograph is not available); several distinct frames
+stay resident in HBM and are cycled, and each frame's working set (~0.5 GB) is
+larger than L2.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With N > 1 (torchrun) every rank solves its own frames (replicas; no
+collective on the data path); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "4K RGB frames/s at rel-res 1e-6, batched vs plain ORAS; p99 latency; HBM %roofline"
+UNIT = "frames/s"
+WORKLOAD = "rgb4k_edge3"
+TOL = 1e-6
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=3, help="distinct frames resident in HBM")
+    ap.add_argument("--precision", default="fp32_ref")
+    ap.add_argument("--levels", type=int, default=3)
+    ap.add_argument("--block", type=int, default=32)
+    ap.add_argument("--overlap", type=int, default=6)
+    ap.add_argument("--k", type=int, default=16, help="local CG steps per sweep")
+    ap.add_argument("--robin", type=float, default=0.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------- helpers
+def make_frames(n: int, seed_offset: int):
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    return [synth.make_frame(w.H, w.W, w.C, w.density, w.pattern, w.seed_base + seed_offset + j) for j in range(n)]
+
+
+def sweep_flops(local_unknowns: int, C: int, k: int) -> float:
+    """Algorithmic FP32 flops of one fine-level sweep launch: per unknown pixel
+    of every local problem, the residual (4 differences, 3 sums: 8 flops incl.
+    the source term), k CG steps of 15 flops (5-point operator 5, two dot
+    products 4, three vector updates 6) and the add-back (1)."""
+    return float(local_unknowns) * C * (15.0 * k + 9.0)
+
+
+def sweep_hbm_bytes(H: int, W: int, C: int, store_bytes: int, with_source: bool) -> float:
+    """Algorithmic DRAM bytes of one sweep: read u and write u once per pixel
+    (plus the correction source g), and the 1-byte mask per pixel shared by
+    all channels (counted once)."""
+    per_px = 2 * store_bytes + (store_bytes if with_source else 0)
+    return float(H) * W * (C * per_px) + float(H) * W
+
+
+def traffic_record():
+    """DRAM bytes per sweep launch from the committed ncu summary, valid only
+    while the sweep kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    src = os.path.join(ROOT, "paper_2110_03946_gb300", "csrc", "sweep.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("sweep_cu_sha256") == sha:
+            return rec
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(f, mask):
+    """The FP64 oracle CG on channel 0 of one frame to rel-res 1e-6, all host
+    cores; returns (frames/s, cores, seconds)."""
+    from oracle import cg as ocg
+    t0 = time.perf_counter()
+    _, it, rel = ocg.solve_cg(f[0], mask, tol=TOL)
+    dt = time.perf_counter() - t0
+    C = f.shape[0]
+    return 1.0 / (C * dt), ocg.threads(), dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    from oracle import cg as ocg
+    w = synth.WORKLOADS[WORKLOAD]
+    f, mask = make_frames(1, 0)[0]
+    times = []
+    for i in range(args.warmup + args.steps):
+        c = i % w.C
+        t0 = time.perf_counter()
+        ocg.solve_cg(f[c], mask, tol=TOL)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    per_channel = statistics.mean(times)
+    fps = 1.0 / (w.C * per_channel)
+    cores = ocg.threads()
+    sample = (f"one colour channel of a 3840x2160 frame per step (3 steps = one frame), FP64 oracle CG "
+              f"(C, OpenMP) to rel-res {TOL:g}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_channel * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded smooth RGB fields, 3% edge-clustered masks)",
+        "config": {"workload": "rgb4k_edge3: 3840x2160x3, 3% edge-clustered mask, rel-res 1e-6",
+                   "solver": "CPU FP64 conjugate gradients on the unknown pixels"},
+        "cpu_baseline": {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2110_03946_gb300 import binding as B
+    from paper_2110_03946_gb300.inpaint import Inpainter
+
+    frames = make_frames(args.frames, 100 * rank)
+    C, H, W = frames[0][0].shape
+    dmask = [torch.as_tensor(m).to(dev) for _, m in frames]
+    dvals = [torch.as_tensor(f).to(dev) for f, _ in frames]
+    prm = dict(block=args.block, overlap=args.overlap, local_cg_iters=args.k, levels=args.levels,
+               precision=args.precision, timing=1)
+    if args.robin > 0:
+        prm["robin_p"] = args.robin
+    ip = Inpainter(dmask[0], dvals[0], device=dev, **prm)
+    out = torch.empty((C, H, W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        j = i % args.frames
+        B.check(B.dd_inpaint_set_data(ip._h, dmask[j].data_ptr(), dvals[j].data_ptr(), 0), "set_data")
+        B.check(B.dd_inpaint_solve(ip._h, out.data_ptr(), TOL, stream), "solve")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for i in range(args.warmup):
+        step(i)
+    launches0 = ip.stats()["kernel_launches"]
+    sweep_ms, sweep_n = 0.0, 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    stats = []
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step(args.warmup + i)
+        ev[i][1].record(stream)
+        st = ip.stats()
+        stats.append(st)
+        sweep_ms += st["fine_sweep_ms"]
+        sweep_n += st["fine_sweep_launches"]
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    lat = sorted(e0.elapsed_time(e1) for e0, e1 in ev)
+    launches = stats[-1]["kernel_launches"] - launches0
+    if world > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps / elapsed
+    if not all(s["converged"] for s in stats):
+        raise RuntimeError("a timed solve did not converge")
+    max_rel = max(max(s["rel_residual"][:C]) for s in stats)
+
+    # ---- end to end through the public API with host buffers -------------------
+    pm = [torch.as_tensor(m).pin_memory() for _, m in frames]
+    pv = [torch.as_tensor(f).pin_memory() for f, _ in frames]
+    hout = torch.empty((C, H, W), dtype=torch.float32).pin_memory()
+    p = B.dd_params_default()
+    for key, val in [("block", args.block), ("overlap", args.overlap), ("local_cg_iters", args.k),
+                     ("levels", args.levels)]:
+        setattr(p, key, val)
+    from paper_2110_03946_gb300.inpaint import PRECISIONS
+    p.precision = PRECISIONS[args.precision]
+    if args.robin > 0:
+        p.robin_p = args.robin
+    p.inputs_on_device = 0
+    rc, h2 = B.dd_inpaint_create(H, W, C, pm[0].data_ptr(), pv[0].data_ptr(), p)
+    B.check(rc, "create(host)")
+    dout = torch.empty((C, H, W), dtype=torch.float32, device=dev)
+
+    def e2e_step(i):
+        j = i % args.frames
+        B.check(B.dd_inpaint_set_data(h2, pm[j].data_ptr(), pv[j].data_ptr(), 0), "set_data(host)")
+        B.check(B.dd_inpaint_solve(h2, dout.data_ptr(), TOL, stream), "solve(host)")
+        hout.copy_(dout, non_blocking=True)
+        torch.cuda.synchronize(dev)
+
+    for i in range(args.warmup):
+        e2e_step(i)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        e2e_step(args.warmup + i)
+    barrier()
+    e2e_elapsed = time.perf_counter() - t0
+    B.dd_inpaint_destroy(h2)
+    if world > 1:
+        t = torch.tensor([e2e_elapsed], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_elapsed = float(t.item())
+    e2e_value = world * args.steps / e2e_elapsed
+    h2d = H * W + C * H * W * 4
+    d2h = C * H * W * 4
+
+    # ---- plain FP32 single-level single-frame ORAS on the same frames ----------
+    plain = None
+    if not args.no_plain:
+        pp = dict(block=args.block, overlap=args.overlap, local_cg_iters=args.k, levels=1, precision="fp32")
+        with Inpainter(dmask[0], dvals[0], device=dev, **pp) as ipp:
+            def pstep(i):
+                j = i % args.frames
+                B.check(B.dd_inpaint_set_data(ipp._h, dmask[j].data_ptr(), dvals[j].data_ptr(), 0), "set_data")
+                B.check(B.dd_inpaint_solve(ipp._h, out.data_ptr(), TOL, stream), "solve", (B.DD_OK, B.DD_ENOTCONVERGED))
+            for i in range(args.warmup):
+                pstep(i)
+            torch.cuda.synchronize(dev)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for i in range(args.steps):
+                pstep(args.warmup + i)
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            pst = ipp.stats()
+            plain = {"value": args.steps / (a0.elapsed_time(a1) / 1e3), "unit": UNIT,
+                     "config": "one level, FP32 iterate, no outer correction, one frame per solve",
+                     "fine_sweeps_last": pst["sweeps_per_level"][0],
+                     "rel_residual_last": max(pst["rel_residual"][:C]), "converged_last": pst["converged"]}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (fine-level ORAS sweep) ---------------
+    st = stats[-1]
+    avg_sweep_s = (sweep_ms / sweep_n) / 1e3 if sweep_n else None
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FP32 FMA at max clock
+    flops = sweep_flops(st["local_unknowns"], C, args.k)
+    achieved = flops / avg_sweep_s / 1e12 if avg_sweep_s else None
+    sbytes = 4 if args.precision in ("fp32", "fp32_ref") else 2
+    hbm_alg = sweep_hbm_bytes(H, W, C, sbytes, args.precision != "fp32")
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    tr = traffic_record()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": (achieved / alu_peak) if achieved else None,
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "kernel": "oras_sweep_kernel (fine level)", "launches_timed": sweep_n,
+                "avg_launch_ms": avg_sweep_s * 1e3 if avg_sweep_s else None,
+                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                               f"{sm_max:.0f} MHz (sm_max_mhz of measured peaks)",
+                "hbm": {"achieved_gbs": hbm_alg / avg_sweep_s / 1e9 if avg_sweep_s else None,
+                        "peak_gbs": hbm_peak, "frac": (hbm_alg / avg_sweep_s / 1e9 / hbm_peak) if avg_sweep_s else None,
+                        "algorithmic_bytes_per_launch": hbm_alg, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        f0, m0 = frames[0]
+        fps, cores, secs = cpu_oracle_sample(f0, m0)
+        cpu = {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"channel 0 of one 3840x2160 frame, FP64 oracle CG to rel-res {TOL:g} "
+                         f"({secs:.1f} s), scaled to 3 channels per frame"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded smooth RGB fields, 3% edge-clustered masks; the paper's photo is unavailable)",
+        "config": {"workload": "rgb4k_edge3: 3840x2160x3, 3% edge-clustered mask, rel-res 1e-6",
+                   "block": args.block, "overlap": args.overlap, "local_cg_iters": args.k,
+                   "levels": args.levels, "precision": args.precision, "frames_resident": args.frames,
+                   "l2": "inputs larger than L2 (each frame's working set ~0.5 GB, frames cycled)",
+                   "parallelism": f"replicas x{world}"},
+        "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))],
+        "max_rel_residual": max_rel,
+        "fine_sweeps": st["sweeps_per_level"][0], "corrections": st["corrections"],
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "plain_fp32_oras": plain,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,211 @@
+/*
+ * dd_inpaint -- homogeneous diffusion inpainting by multilevel optimised
+ * restricted additive Schwarz (ORAS) on one GB300 GPU (sm_103a).
+ *
+ * Problem (Kaemper & Weickert, "Domain decomposition algorithms for
+ * real-time homogeneous diffusion inpainting in 4K", Sec. 2, Eq. eq:inp,
+ * eq:homdiff, eq:ls): per colour channel solve A u = b with
+ * A = C - (I - C) L, b = C f, where C is the 0/1 diagonal mask of known
+ * pixels and L the 5-point Laplacian with reflecting image boundaries
+ * (grid size 1).  Known pixels keep u = f; the others satisfy the discrete
+ * Laplace equation.  All channels share one mask (Sec. 2, last paragraph).
+ *
+ * Method (Sec. 3-4): overlapping square blocks of side `block` at stride
+ * block - overlap; each sweep solves every block's local problem
+ * R_i A R_i^T v_i = R_i r^n (Eq. eq:ras-local-problem) by `local_cg_iters`
+ * conjugate-gradient steps with a Robin interface condition (ORAS), and adds
+ * the corrections back on disjoint owned cores (restricted add-back with a
+ * 0/1 partition of unity).  The multilevel variant solves dyadically
+ * subsampled problems coarse to fine (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *  - images are channel-planar, row-major float32 arrays C x H x W with no
+ *    padding (element (c, y, x) at index (c*H + y)*W + x);
+ *  - masks are H x W bytes, nonzero = known pixel;
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream); work is enqueued on it.  Calls that must read a convergence
+ *    test back to the host synchronise that stream before returning; this
+ *    is stated per function;
+ *  - device pointers must be device-accessible memory of the current device
+ *    (e.g. torch CUDA tensors); host pointers ordinary host memory;
+ *  - the library never takes ownership of caller buffers;
+ *  - return codes are DD_* below; no entry point aborts the process.
+ *  - handles are not thread-safe; distinct handles are independent.
+ */
+#ifndef DD_INPAINT_H
+#define DD_INPAINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status codes */
+#define DD_OK             0
+#define DD_EINVAL         1  /* bad size, NULL pointer, block <= overlap, bad enum */
+#define DD_EEMPTYMASK     2  /* no known pixel: A is singular under reflecting boundaries */
+#define DD_ENOMEM         3  /* device or host allocation failed */
+#define DD_ENOTCONVERGED  4  /* sweep limit reached; the best iterate is still written */
+#define DD_ENUMERIC       5  /* NaN or Inf met in a residual norm */
+#define DD_ECUDA          6  /* a CUDA runtime call failed (message: dd_last_error) */
+#define DD_ETIMEOUT       7  /* a bounded device-side wait gave up */
+
+/* multilevel modes */
+#define DD_ML_CASCADE     0  /* coarse-to-fine initialisation (Sec. 4) */
+#define DD_ML_CORRECTION  1  /* two-level: coarse residual correction after each fine sweep */
+
+/* precision modes (storage of the Schwarz iterate; arithmetic is FP32) */
+#define DD_PREC_FP32      0  /* plain FP32 ORAS on u, FP64-verified stop test */
+#define DD_PREC_FP32_REF  1  /* FP32 inner solves + FP64 outer residual correction */
+#define DD_PREC_FP16_REF  2  /* FP16 storage inner solves + FP64 outer residual correction */
+#define DD_PREC_BF16_REF  3  /* BF16 storage inner solves + FP64 outer residual correction */
+
+typedef struct dd_inpaint *dd_handle;
+
+typedef struct dd_params {
+    int    block;            /* block side in pixels: 16, 32 or 64 (default 32, Sec. 4) */
+    int    overlap;          /* overlap in pixels, 0 <= overlap < block (default 6, Sec. 4) */
+    int    local_cg_iters;   /* CG steps per local problem and sweep, >= 1 (default 16) */
+    int    levels;           /* resolution levels, 1..8 (default 3, Sec. 4) */
+    int    ml_mode;          /* DD_ML_CASCADE (default) or DD_ML_CORRECTION */
+    int    coarse_factor;    /* DD_ML_CORRECTION only: 2^(levels-1) is used; kept for ABI */
+    float  robin_p;          /* Robin interface weight p > 0 (1 = RAS); <= 0 selects the default */
+    int    precision;        /* DD_PREC_* (default DD_PREC_FP32_REF) */
+    int    max_sweeps;       /* fine-level sweep limit per solve (default 400) */
+    int    inputs_on_device; /* 1: mask/values pointers are device memory; 0: host */
+    double coarse_tol;       /* relative residual that ends a coarse level (default 1e-2) */
+    double inner_tol;        /* relative residual decrease per outer correction (default 3e-3) */
+    int    max_corrections;  /* outer FP64 corrections limit (default 30) */
+    int    coarse_sweeps;    /* sweep limit per coarse level (default 40) */
+    int    timing;           /* 1: time every fine-level sweep launch with CUDA events (dd_stats) */
+} dd_params;
+
+#define DD_MAX_STAT_CHANNELS 16
+#define DD_MAX_LEVELS 8
+
+typedef struct dd_stats {
+    int    sweeps_total;                       /* ORAS sweeps of the last solve, all levels */
+    int    sweeps_per_level[DD_MAX_LEVELS];    /* level 0 = finest */
+    int    corrections;                        /* FP64 outer corrections applied */
+    int    converged;                          /* 1 if the stop test held */
+    int    channels;
+    double rel_residual[DD_MAX_STAT_CHANNELS]; /* FP64 ||b-Au||/||b-Au0|| of the output, u0 = Cf */
+    double ms_total;                           /* device time of the last solve (CUDA events) */
+    size_t device_bytes;                       /* device memory owned by the handle */
+    long long kernel_launches;                 /* CUDA kernels launched through the handle since create */
+    long long local_unknowns;                  /* unknown pixels summed over the fine level's blocks,
+                                                  one channel (work of one local problem set) */
+    int    fine_sweep_launches;                /* timed fine-level sweep launches (params.timing) */
+    double fine_sweep_ms;                      /* their summed device time */
+} dd_stats;
+
+/* Fill *p with the defaults listed above. */
+void dd_params_default(dd_params *p);
+
+/* Human-readable text for a DD_* code (static storage). */
+const char *dd_strerror(int code);
+
+/* Text of the last DD_ECUDA / DD_EINVAL cause on this thread (static per thread). */
+const char *dd_last_error(void);
+
+/*
+ * Create a solver for one frame (H x W, C channels) and copy its data.
+ *   mask:   H*W bytes, nonzero = known (host or device per inputs_on_device);
+ *   values: C*H*W floats, read only where mask != 0;
+ *   params: NULL = defaults;  out: receives the handle.
+ * The caller's buffers may be freed when the call returns.  Allocates all
+ * device memory the solves need (dd_stats.device_bytes).  Synchronous.
+ * Errors: DD_EINVAL, DD_EEMPTYMASK, DD_ENOMEM, DD_ECUDA (no handle is made).
+ */
+int dd_inpaint_create(int H, int W, int C, const uint8_t *mask, const float *values,
+                      const dd_params *params, dd_handle *out);
+
+/*
+ * Solve to relative residual `tol` (per channel ||b - A u|| / ||b - A u0||,
+ * u0 = C f; stop when the maximum over channels is <= tol) and write the
+ * solution to u_out (DEVICE, C*H*W floats, caller-owned).  The stop test is
+ * read back each sweep chunk, so the call synchronises `stream`.  Starts from
+ * the handle's iterate if dd_inpaint_set_data(..., keep_iterate=1) asked for a
+ * warm start, else from the multilevel initialisation.
+ * Errors: DD_EINVAL, DD_ENOTCONVERGED (u_out still holds the best iterate),
+ * DD_ENUMERIC, DD_ETIMEOUT, DD_ECUDA.
+ */
+int dd_inpaint_solve(dd_handle h, float *u_out, double tol, void *stream);
+
+/* Release the handle and its device memory.  NULL-safe; returns DD_OK. */
+int dd_inpaint_destroy(dd_handle h);
+
+/*
+ * Replace mask and values (same H, W, C; pointers as in create).  With
+ * keep_iterate = 1 the current fine iterate is kept as the next solve's
+ * starting point (known pixels reset to the new values): warm start for
+ * video.  Synchronous.  Errors: DD_EINVAL, DD_EEMPTYMASK, DD_ECUDA.
+ */
+int dd_inpaint_set_data(dd_handle h, const uint8_t *mask, const float *values, int keep_iterate);
+
+/* Copy the statistics of the last solve.  Errors: DD_EINVAL. */
+int dd_inpaint_stats(dd_handle h, dd_stats *out);
+
+/* ---------------------------------------------------------------------------
+ * Step-level entry points (one step of the method on caller device buffers;
+ * used to check each step against an independent implementation).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Set the finest-level iterate from u (DEVICE, C*H*W floats) exactly as
+ * given (no reset of known pixels).  Subsequent dd_inpaint_sweep calls start
+ * from it.  Enqueued on stream.  Errors: DD_EINVAL, DD_ECUDA.
+ */
+int dd_inpaint_set_iterate(dd_handle h, const float *u, void *stream);
+
+/* Copy the finest-level iterate to u_out (DEVICE, C*H*W floats). */
+int dd_inpaint_get_iterate(dd_handle h, float *u_out, void *stream);
+
+/*
+ * Apply n ORAS sweeps (Sec. 3, u^{n+1} = u^n + sum_i R_i^T D_i v_i^n) to the
+ * finest-level iterate, in FP32 storage, with the handle's block, overlap,
+ * Robin weight and CG step count.  If rnorm_out is not NULL it receives C
+ * values: ||b - A u^n||_2 of the INPUT iterate of the last sweep (FP32 terms,
+ * FP64 accumulation); the call then synchronises stream.
+ * Errors: DD_EINVAL, DD_ECUDA.
+ */
+int dd_inpaint_sweep(dd_handle h, int n, double *rnorm_out, void *stream);
+
+/*
+ * Dyadic subsampling of mask and known values (Sec. 4): coarse pixel
+ * (Y, X) covers fine pixels {2Y, 2Y+1} x {2X, 2X+1} inside the image; it is
+ * known iff one of them is known, and its value is the mean of the known fine
+ * values (0 where unknown).  Sizes Hc = ceil(H/2), Wc = ceil(W/2).
+ *   mask (H*W bytes), f (C*H*W floats): DEVICE inputs;
+ *   mask_c (Hc*Wc bytes), f_c (C*Hc*Wc floats): DEVICE outputs.
+ * Enqueued on stream.  Errors: DD_EINVAL, DD_ECUDA.
+ */
+int dd_restrict(int H, int W, int C, const uint8_t *mask, const float *f,
+                uint8_t *mask_c, float *f_c, void *stream);
+
+/*
+ * Coarse-to-fine prolongation: cell-centred bilinear interpolation of
+ * u_c (C x Hc x Wc) onto C x H x W (fine pixel i sits at coarse coordinate
+ * (i - 0.5)/2, clamped to the coarse grid).  If mask/f are not NULL, pixels
+ * with mask != 0 are then set to f (the initialisation of Sec. 4).
+ * All pointers DEVICE.  Enqueued on stream.  Errors: DD_EINVAL, DD_ECUDA.
+ */
+int dd_prolong(int Hc, int Wc, int H, int W, int C, const float *u_c, const uint8_t *mask,
+               const float *f, float *u, void *stream);
+
+/*
+ * FP64 residual norms ||b - A u||_2 per channel of a float32 iterate u, and
+ * the reference norms ||b - A u0||_2, u0 = C f (Sec. 2, Eq. eq:ls).  mask, f, u
+ * are DEVICE; norms and ref_norms HOST arrays of C doubles (either may be
+ * NULL).  Synchronises stream.  Errors: DD_EINVAL, DD_ECUDA.
+ */
+int dd_residual_norms(int H, int W, int C, const uint8_t *mask, const float *f,
+                      const float *u, double *norms, double *ref_norms, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_INPAINT_H */

@@ -1,0 +1,119 @@
+// Internal interfaces between the translation units of the dd_inpaint library.
+// Not part of the public C ABI (that is include/dd_inpaint.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace dd {
+
+// Storage type of a Schwarz iterate (arithmetic is always FP32).
+enum class Store : int { F32 = 0, F16 = 1, BF16 = 2 };
+
+inline size_t store_bytes(Store s) { return s == Store::F32 ? 4 : 2; }
+
+// Block layout of one resolution level (Sec. 4 of the paper): blocks of side b
+// at stride s = b - o, count max(1, ceil((n - o)/s)) per axis, the last block
+// clipped to the image; pixel x of an axis is owned by block
+// clamp(floor((x - floor(o/2))/s), 0, n - 1).
+struct TileGeom {
+    int H = 0, W = 0, pitch = 0;  // image size; row pitch of the level's buffers (elements)
+    int b = 32, o = 6, s = 26, half_o = 3;
+    int ntx = 0, nty = 0, ntiles = 0;
+};
+
+int axis_blocks(int n, int b, int o);
+TileGeom make_geom(int H, int W, int pitch, int b, int o);
+
+// Kernel shape chosen for a block side: threads per block-tile and the number
+// of 32-bit mask words per tile (known bits + owned bits per thread).
+bool block_supported(int b);
+int tile_threads(int b);
+size_t tmask_words(const TileGeom& g);
+
+// Per-tile, per-thread bit masks: bit set in word 0 = pixel known or outside
+// the tile, bit set in word 1 = pixel owned by the tile (restricted add-back).
+cudaError_t launch_build_tmask(const TileGeom& g, const uint8_t* mask, int mask_pitch,
+                               uint32_t* tmask, cudaStream_t st);
+
+// *out += number of unknown in-tile pixels over all tiles (one channel).
+cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsigned long long* out,
+                                 cudaStream_t st);
+
+// TMA descriptor of a C x H x W iterate (row pitch `pitch` elements) whose box
+// is the block tile plus halo of block side b: built once per buffer.
+cudaError_t make_tile_map(CUtensorMap* out, Store st, const void* base, int H, int W, int pitch, int C, int b);
+
+// One ORAS sweep over all tiles of all C channels (planes `plane` elements apart).
+//   map_in: TMA descriptor of the input iterate u_in; u_out receives the owned
+//   cores; map_g: optional source g on unknown pixels (solves
+//   A u = C f + (I - C) g with u = f held on known pixels);
+//   partial[c * ntiles + t] = sum over owned pixels of the squared residual of u_in;
+//   skip: optional device flag, nonzero makes the launch a no-op;
+//   err: set to 1 if a bounded wait for a staged tile gave up.
+cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, const CUtensorMap& map_in,
+                         const CUtensorMap* map_g, void* u_out, const uint32_t* tmask, float* partial,
+                         const int* skip, int* err, float p_robin, int k, cudaStream_t stream);
+
+// ---- auxiliary passes (aux.cu) ----------------------------------------------------
+// dst[c][y][x] (pitch dp) = mask ? src[c][y][x] : 0  (src pitch sp)
+cudaError_t launch_masked_copy(int H, int W, int C, const float* src, int sp, long long splane,
+                               const uint8_t* mask, int mp, float* dst, int dp, long long dplane,
+                               cudaStream_t st);
+// plain strided copy (float)
+cudaError_t launch_copy2d(int H, int W, int C, const float* src, int sp, long long splane,
+                          float* dst, int dp, long long dplane, cudaStream_t st);
+// convert between storage types / set: dst (Store) = (float)src, or zero
+cudaError_t launch_fill_zero(Store s, void* dst, size_t n, cudaStream_t st);
+// dst = keep known: u[c][y][x] = mask ? f : u   (float, pitched)
+cudaError_t launch_reset_known(int H, int W, int C, float* u, int up, long long uplane,
+                               const uint8_t* mask, int mp, const float* f, int fp, long long fplane,
+                               cudaStream_t st);
+
+// FP64 residual r = b - A u on unknown pixels (0 on known), per channel
+// sum r^2 and max |r| per block into part[c*nblk + blk] (double2 {sum, max}).
+// If g_out != nullptr, also writes g_out = r * scale_inv[c] in storage `gst`.
+struct Res64Args {
+    int H, W, C;
+    const float* u; int up; long long uplane;
+    const uint8_t* mask; int mp;
+    void* g_out; Store gst; int gp; long long gplane;
+    const double* scale_inv;   // device, per channel (only with g_out)
+    double2* part; int nblk;
+};
+int res64_blocks(int H, int W);
+cudaError_t launch_res64(const Res64Args& a, cudaStream_t st);
+
+// Reduce per-block partials: out[c] = {sum over blocks, max over blocks}.
+cudaError_t launch_reduce_part(const double2* part, int nblk, int C, double2* out, cudaStream_t st);
+
+// Reduce sweep partials (float, C x ntiles) to norms2[c] (double, 2C entries:
+// current and previous sweep) and test convergence: if max_c sqrt(norms2[c]) /
+// ref[c] <= tol and *flag == 0, set *flag = 1 and *conv_at = sweep_index.
+// *flag = 2 on NaN/Inf; *flag = 3 when stall > 0 and the residual of every
+// channel fell by less than the factor 1/stall in the last sweep (the iterate's
+// storage precision has been reached).  A set flag makes later launches no-ops.
+cudaError_t launch_reduce_sweep(const float* partial, int ntiles, int C, double* norms2,
+                                const double* ref, double tol, double stall, int* flag, int* conv_at,
+                                int sweep_index, cudaStream_t st);
+
+// Dyadic restriction (Sec. 4): mask OR over 2x2, mean of known values.
+cudaError_t launch_restrict(int H, int W, int C, const uint8_t* mask, int mp, const float* f, int fp,
+                            long long fplane, uint8_t* mask_c, int mcp, float* f_c, int fcp,
+                            long long fcplane, cudaStream_t st);
+// Cell-centred bilinear prolongation, optional reset of known pixels to f.
+cudaError_t launch_prolong(int Hc, int Wc, int H, int W, int C, const float* uc, int ucp,
+                           long long ucplane, const uint8_t* mask, int mp, const float* f, int fp,
+                           long long fplane, float* u, int up, long long uplane, cudaStream_t st);
+// u = fl32(u + s_c * e) on unknown pixels (FP64 arithmetic), e in storage `est`.
+cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long uplane, const void* e,
+                           Store est, int ep, long long eplane, const uint8_t* mask, int mp,
+                           const double* scale, cudaStream_t st);
+// Store-typed copy from float with conversion (used to seed low-precision iterates).
+cudaError_t launch_convert(int H, int W, int C, const float* src, int sp, long long splane,
+                           void* dst, Store dst_t, int dp, long long dplane, cudaStream_t st);
+
+}  // namespace dd

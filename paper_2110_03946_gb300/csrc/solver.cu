@@ -1,0 +1,767 @@
+// Host driver and C ABI of the ORAS inpainting solver (include/dd_inpaint.h).
+//
+// Paper mapping (Kaemper & Weickert, arXiv 2110.03946):
+//   Sec. 2      problem A u = b, A = C - (I - C) L, b = C f, per channel;
+//   Sec. 3      ORAS sweeps (sweep.cu);
+//   Sec. 4      32-px blocks with 6-px overlap, local CG, iterate until the
+//               relative residual has decayed to tol, and the coarse-to-fine
+//               multilevel initialisation over dyadic levels (aux.cu).
+// Beyond the paper: an outer residual correction whose residual is formed in
+// FP64 (DD_PREC_*_REF) around inner ORAS solves whose iterate is stored in
+// FP32, FP16 or BF16.
+//
+// All iteration state stays on the device.  The stop test is evaluated on the
+// device after every sweep (reduce kernel + flag); later sweeps of a chunk see
+// the flag and return at once, and the host reads the flag once per chunk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dd_inpaint.h"
+#include "dd_internal.h"
+
+using dd::Store;
+using dd::TileGeom;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void set_error(const std::string& s) { g_last_error = s; }
+
+#define DD_CK(call)                                                                      \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));               \
+            return e_ == cudaErrorMemoryAllocation ? DD_ENOMEM : DD_ECUDA;               \
+        }                                                                                \
+    } while (0)
+
+// A kernel launch through the handle: checked and counted.
+#define DD_LAUNCH(h, call)   \
+    do {                     \
+        DD_CK(call);         \
+        ++(h)->launches;     \
+    } while (0)
+
+#define DD_TRY(expr)                \
+    do {                            \
+        int rc_ = (expr);           \
+        if (rc_ != DD_OK) return rc_; \
+    } while (0)
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+struct Level {
+    int H = 0, W = 0, P = 0;
+    TileGeom geom;
+    uint8_t* mask = nullptr;   // H x W dense
+    float* f = nullptr;        // C x H x P, known values, 0 elsewhere
+    uint32_t* tmask = nullptr;
+    float* u[2] = {nullptr, nullptr};
+    CUtensorMap map_u[2];      // TMA descriptors of u[0], u[1]
+    float* partial = nullptr;  // C x ntiles
+    double* ref_d = nullptr;   // C
+    std::vector<double> ref;   // C
+    long long plane() const { return (long long)H * P; }
+};
+
+}  // namespace
+
+struct dd_inpaint {
+    int H = 0, W = 0, C = 0;
+    dd_params prm{};
+    Store lowst = Store::F32;
+    std::vector<Level> lv;
+    int cur = 0;              // buffer of lv[0] holding the fine iterate
+    bool warm = false;        // next solve starts from the kept iterate
+    // correction equation buffers (fine level): e ping-pong and source g
+    void* e[2] = {nullptr, nullptr};
+    void* g = nullptr;
+    CUtensorMap map_e[2], map_g;
+    double* inner_ref_d = nullptr;  // C
+    double* scale_d = nullptr;      // C
+    double* scale_inv_d = nullptr;  // C
+    // residual / stop-test scratch
+    double2* res_part = nullptr;
+    int res_nblk = 0;
+    double2* res_out = nullptr;     // C
+    double* norms2_d = nullptr;     // C
+    int* flag_d = nullptr;          // [0] flag, [1] conv_at, [2] device wait timed out
+    // pinned host mirrors
+    double2* h_res = nullptr;
+    double* h_small = nullptr;      // 3*C doubles scratch
+    int* h_flag = nullptr;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    static constexpr int kChunk = 8;                 // sweeps per stop-test read-back
+    cudaEvent_t sw_ev[2 * kChunk] = {};              // per-sweep timing events (params.timing)
+    unsigned long long* count_d = nullptr;           // unknown-pixel counter
+    long long launches = 0;                          // kernels launched through this handle
+    long long local_unknowns = 0;
+    dd_stats stats{};
+};
+
+namespace {
+
+int dalloc(dd_inpaint* h, void** p, size_t n) {
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(p, n);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return DD_ENOMEM;
+    }
+    h->allocs.push_back(*p);
+    h->bytes += n;
+    return DD_OK;
+}
+
+template <typename T>
+int dalloc_t(dd_inpaint* h, T** p, size_t count) {
+    void* v = nullptr;
+    int rc = dalloc(h, &v, count * sizeof(T));
+    *p = static_cast<T*>(v);
+    return rc;
+}
+
+Store low_store(int precision) {
+    switch (precision) {
+        case DD_PREC_FP16_REF: return Store::F16;
+        case DD_PREC_BF16_REF: return Store::BF16;
+        default: return Store::F32;
+    }
+}
+
+int validate(int H, int W, int C, const dd_params& p) {
+    if (H <= 0 || W <= 0 || C <= 0) { set_error("H, W and C must be positive"); return DD_EINVAL; }
+    if ((long long)H * W > (1LL << 31) / 4) { set_error("image too large"); return DD_EINVAL; }
+    if (!dd::block_supported(p.block)) { set_error("block must be 16, 32 or 64"); return DD_EINVAL; }
+    if (p.overlap < 0 || p.overlap >= p.block) { set_error("need 0 <= overlap < block"); return DD_EINVAL; }
+    if (p.local_cg_iters < 1 || p.local_cg_iters > 4096) { set_error("local_cg_iters out of range"); return DD_EINVAL; }
+    if (p.levels < 1 || p.levels > DD_MAX_LEVELS) { set_error("levels must be 1..8"); return DD_EINVAL; }
+    if (p.ml_mode != DD_ML_CASCADE && p.ml_mode != DD_ML_CORRECTION) { set_error("bad ml_mode"); return DD_EINVAL; }
+    if (p.precision < DD_PREC_FP32 || p.precision > DD_PREC_BF16_REF) { set_error("bad precision"); return DD_EINVAL; }
+    if (p.max_sweeps < 0 || p.coarse_sweeps < 0 || p.max_corrections < 0) { set_error("negative limit"); return DD_EINVAL; }
+    if (!(p.coarse_tol > 0.0) || !(p.inner_tol > 0.0) || !(p.inner_tol < 1.0)) { set_error("bad tolerance"); return DD_EINVAL; }
+    return DD_OK;
+}
+
+float robin_default(int b, int o) {
+    // Optimised Robin parameter of overlapping Schwarz (Gander, SIAM J. Numer.
+    // Anal. 44 (2006)): p = 2^(-1/3) k_min^(2/3) L^(-1/3), k_min = pi/b, L = o,
+    // scaled by 3 for the inpainting operator, whose many interior Dirichlet
+    // pixels damp the low frequencies the estimate is made for.
+    const double kmin = 3.14159265358979323846 / b;
+    const double L = std::max(o, 1);
+    return (float)(3.0 * std::pow(2.0, -1.0 / 3.0) * std::pow(kmin, 2.0 / 3.0) * std::pow(L, -1.0 / 3.0));
+}
+
+// Copy caller data (mask, values) into level 0 and rebuild all levels.
+int load_data(dd_inpaint* h, const uint8_t* mask, const float* values, cudaStream_t st) {
+    Level& L0 = h->lv[0];
+    const size_t npx = (size_t)h->H * h->W;
+    const uint8_t* dmask = mask;
+    const float* dvals = values;
+    float* tmp_vals = nullptr;
+    if (!h->prm.inputs_on_device) {
+        DD_CK(cudaMemcpyAsync(L0.mask, mask, npx, cudaMemcpyHostToDevice, st));
+        dmask = L0.mask;
+        // values staged through u[1] as a dense C x H x W array (it has room: P >= W)
+        tmp_vals = L0.u[1];
+        DD_CK(cudaMemcpyAsync(tmp_vals, values, npx * h->C * sizeof(float), cudaMemcpyHostToDevice, st));
+        dvals = tmp_vals;
+    } else {
+        DD_CK(cudaMemcpyAsync(L0.mask, mask, npx, cudaMemcpyDeviceToDevice, st));
+        dmask = L0.mask;
+    }
+    DD_LAUNCH(h, dd::launch_masked_copy(h->H, h->W, h->C, dvals, h->W, (long long)npx, dmask, h->W, L0.f, L0.P,
+                                 L0.plane(), st));
+    for (size_t l = 1; l < h->lv.size(); ++l) {
+        Level& F = h->lv[l - 1];
+        Level& Cc = h->lv[l];
+        DD_LAUNCH(h, dd::launch_restrict(F.H, F.W, h->C, F.mask, F.W, F.f, F.P, F.plane(), Cc.mask, Cc.W, Cc.f, Cc.P,
+                                  Cc.plane(), st));
+    }
+    for (auto& L : h->lv) DD_LAUNCH(h, dd::launch_build_tmask(L.geom, L.mask, L.W, L.tmask, st));
+    DD_CK(cudaMemsetAsync(h->count_d, 0, sizeof(unsigned long long), st));
+    DD_LAUNCH(h, dd::launch_count_unknown(L0.geom, L0.tmask, h->count_d, st));
+    {
+        unsigned long long cnt = 0;
+        DD_CK(cudaMemcpyAsync(&cnt, h->count_d, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaStreamSynchronize(st));
+        h->local_unknowns = (long long)cnt;
+    }
+    // reference norms ||b - A u0||, u0 = C f, per level and channel
+    for (auto& L : h->lv) {
+        const int nblk = dd::res64_blocks(L.H, L.W);
+        dd::Res64Args a{};
+        a.H = L.H; a.W = L.W; a.C = h->C;
+        a.u = L.f; a.up = L.P; a.uplane = L.plane();
+        a.mask = L.mask; a.mp = L.W;
+        a.g_out = nullptr; a.gst = Store::F32;
+        a.part = h->res_part; a.nblk = nblk;
+        DD_LAUNCH(h, dd::launch_res64(a, st));
+        DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, nblk, h->C, h->res_out, st));
+        DD_CK(cudaMemcpyAsync(h->h_res, h->res_out, sizeof(double2) * h->C, cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaStreamSynchronize(st));
+        L.ref.resize(h->C);
+        for (int c = 0; c < h->C; ++c) L.ref[c] = std::sqrt(h->h_res[c].x);
+        for (int c = 0; c < h->C; ++c) h->h_small[c] = L.ref[c];
+        DD_CK(cudaMemcpyAsync(L.ref_d, h->h_small, sizeof(double) * h->C, cudaMemcpyHostToDevice, st));
+        DD_CK(cudaStreamSynchronize(st));
+    }
+    return DD_OK;
+}
+
+int count_known(const uint8_t* mask, size_t n, bool on_device, long long* out) {
+    std::vector<uint8_t> tmp;
+    const uint8_t* m = mask;
+    if (on_device) {
+        tmp.resize(n);
+        DD_CK(cudaMemcpy(tmp.data(), mask, n, cudaMemcpyDeviceToHost));
+        m = tmp.data();
+    }
+    long long k = 0;
+    for (size_t i = 0; i < n; ++i) k += m[i] != 0;
+    *out = k;
+    return DD_OK;
+}
+
+// ORAS sweeps on one level until the (lagged) relative residual of the
+// current iterate, measured against ref_d, is <= tol, or max_sweeps sweeps.
+// bufs[cur] holds the input; on return cur indexes the result.
+int run_sweeps(dd_inpaint* h, const TileGeom& g, Store st_t, void* const bufs[2], const CUtensorMap* maps,
+               int& cur, const CUtensorMap* map_g, const uint32_t* tmask, float* partial, const double* ref_d,
+               double tol, double stall, int max_sweeps, cudaStream_t st, int* applied, bool* converged,
+               bool fine = false) {
+    const long long plane = (long long)g.H * g.pitch;
+    DD_CK(cudaMemsetAsync(h->flag_d, 0, 3 * sizeof(int), st));
+    int done = 0;
+    *converged = false;
+    const int chunk = dd_inpaint::kChunk;
+    const bool timed = fine && h->prm.timing != 0;
+    while (true) {
+        // the chunk evaluates the stop test of iterates done .. done+n-1 and
+        // sweeps them; an iterate past max_sweeps is tested but not swept
+        const int n = std::min(chunk, max_sweeps - done + 1);
+        for (int i = 0; i < n; ++i) {
+            const int idx = done + i;
+            const CUtensorMap& in = maps[(cur + idx) & 1];
+            void* out = bufs[(cur + idx + 1) & 1];
+            if (idx < max_sweeps) {
+                if (timed) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
+                DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, in, map_g, out, tmask, partial, h->flag_d,
+                                              h->flag_d + 2, h->prm.robin_p, h->prm.local_cg_iters, st));
+                if (timed) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
+            } else {
+                // evaluation only: a sweep whose output goes to the other buffer is
+                // still needed for the fused residual; run it, it is not counted
+                DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, in, map_g, out, tmask, partial, h->flag_d,
+                                              h->flag_d + 2, h->prm.robin_p, 1, st));
+            }
+            DD_LAUNCH(h, dd::launch_reduce_sweep(partial, g.ntiles, h->C, h->norms2_d, ref_d, tol, stall, h->flag_d,
+                                          h->flag_d + 1, idx, st));
+        }
+        DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaStreamSynchronize(st));
+        if (h->h_flag[2] != 0) {
+            set_error("a bounded device wait for a staged tile gave up");
+            return DD_ETIMEOUT;
+        }
+        if (timed) {
+            // launches that ran in full: up to and including the one that set the flag
+            const int last = h->h_flag[0] != 0 ? h->h_flag[1] : done + n - 1;
+            for (int i = 0; i < n; ++i) {
+                const int idx = done + i;
+                if (idx >= max_sweeps || idx > last) break;
+                float ms = 0.f;
+                DD_CK(cudaEventElapsedTime(&ms, h->sw_ev[2 * i], h->sw_ev[2 * i + 1]));
+                h->stats.fine_sweep_ms += ms;
+                h->stats.fine_sweep_launches += 1;
+            }
+        }
+        if (h->h_flag[0] == 2) {
+            set_error("non-finite residual norm");
+            return DD_ENUMERIC;
+        }
+        if (h->h_flag[0] == 1 || h->h_flag[0] == 3) {
+            const int at = h->h_flag[1];
+            *applied = at;
+            cur = (cur + at) & 1;
+            *converged = h->h_flag[0] == 1;
+            return DD_OK;
+        }
+        done += n;
+        if (done > max_sweeps) {
+            *applied = max_sweeps;
+            cur = (cur + max_sweeps) & 1;
+            return DD_OK;
+        }
+    }
+}
+
+// FP64 residual of the fine FP32 iterate: per-channel relative residuals;
+// optionally writes the scaled residual into h->g (storage lowst).
+int fine_residual64(dd_inpaint* h, cudaStream_t st, std::vector<double>& rel, std::vector<double>& rmax,
+                    std::vector<double>& rnorm) {
+    Level& L = h->lv[0];
+    dd::Res64Args a{};
+    a.H = L.H; a.W = L.W; a.C = h->C;
+    a.u = L.u[h->cur]; a.up = L.P; a.uplane = L.plane();
+    a.mask = L.mask; a.mp = L.W;
+    a.g_out = nullptr; a.gst = h->lowst;
+    a.part = h->res_part; a.nblk = h->res_nblk;
+    DD_LAUNCH(h, dd::launch_res64(a, st));
+    DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, h->res_nblk, h->C, h->res_out, st));
+    DD_CK(cudaMemcpyAsync(h->h_res, h->res_out, sizeof(double2) * h->C, cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaStreamSynchronize(st));
+    rel.assign(h->C, 0.0);
+    rmax.assign(h->C, 0.0);
+    rnorm.assign(h->C, 0.0);
+    for (int c = 0; c < h->C; ++c) {
+        rnorm[c] = std::sqrt(h->h_res[c].x);
+        rmax[c] = h->h_res[c].y;
+        const double den = L.ref[c] > 0.0 ? L.ref[c] : 1.0;
+        rel[c] = rnorm[c] / den;
+        if (!std::isfinite(rel[c])) { set_error("non-finite residual"); return DD_ENUMERIC; }
+    }
+    return DD_OK;
+}
+
+int write_scaled_residual(dd_inpaint* h, cudaStream_t st) {
+    Level& L = h->lv[0];
+    dd::Res64Args a{};
+    a.H = L.H; a.W = L.W; a.C = h->C;
+    a.u = L.u[h->cur]; a.up = L.P; a.uplane = L.plane();
+    a.mask = L.mask; a.mp = L.W;
+    a.g_out = h->g; a.gst = h->lowst; a.gp = L.P; a.gplane = L.plane();
+    a.scale_inv = h->scale_inv_d;
+    a.part = h->res_part; a.nblk = h->res_nblk;
+    DD_LAUNCH(h, dd::launch_res64(a, st));
+    return DD_OK;
+}
+
+// Coarse-to-fine initialisation (Sec. 4): coarsest level from u0 = C f,
+// each level solved to coarse_tol, prolonged as the next level's start.
+int cascade(dd_inpaint* h, cudaStream_t st) {
+    const int nl = (int)h->lv.size();
+    for (int l = nl - 1; l >= 1; --l) {
+        Level& L = h->lv[l];
+        if (l == nl - 1) {
+            DD_LAUNCH(h, dd::launch_copy2d(L.H, L.W, h->C, L.f, L.P, L.plane(), L.u[0], L.P, L.plane(), st));
+        } else {
+            Level& Cc = h->lv[l + 1];
+            DD_LAUNCH(h, dd::launch_prolong(Cc.H, Cc.W, L.H, L.W, h->C, Cc.u[0], Cc.P, Cc.plane(), L.mask, L.W, L.f, L.P,
+                                     L.plane(), L.u[0], L.P, L.plane(), st));
+        }
+        int c = 0, applied = 0;
+        bool conv = false;
+        void* bufs[2] = {L.u[0], L.u[1]};
+        DD_TRY(run_sweeps(h, L.geom, Store::F32, bufs, L.map_u, c, nullptr, L.tmask, L.partial, L.ref_d,
+                          h->prm.coarse_tol, 0.0, h->prm.coarse_sweeps, st, &applied, &conv));
+        if (c != 0) DD_LAUNCH(h, dd::launch_copy2d(L.H, L.W, h->C, L.u[1], L.P, L.plane(), L.u[0], L.P, L.plane(), st));
+        if (l < DD_MAX_LEVELS) h->stats.sweeps_per_level[l] = applied;
+        h->stats.sweeps_total += applied;
+    }
+    Level& F = h->lv[0];
+    if (nl > 1) {
+        Level& Cc = h->lv[1];
+        DD_LAUNCH(h, dd::launch_prolong(Cc.H, Cc.W, F.H, F.W, h->C, Cc.u[0], Cc.P, Cc.plane(), F.mask, F.W, F.f, F.P,
+                                 F.plane(), F.u[0], F.P, F.plane(), st));
+    } else {
+        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.f, F.P, F.plane(), F.u[0], F.P, F.plane(), st));
+    }
+    h->cur = 0;
+    return DD_OK;
+}
+
+int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    h->stats.channels = h->C;
+    h->stats.device_bytes = h->bytes;
+    h->stats.local_unknowns = h->local_unknowns;
+    DD_CK(cudaEventRecord(h->ev0, st));
+    if (!h->warm) DD_TRY(cascade(h, st));
+    h->warm = false;
+    Level& F = h->lv[0];
+    std::vector<double> rel, rmax, rnorm;
+    int fine_sweeps = 0;
+    bool converged = false;
+    int rc = DD_OK;
+    if (h->prm.precision == DD_PREC_FP32) {
+        double target = tol;
+        for (int attempt = 0; attempt < 4 && fine_sweeps < h->prm.max_sweeps; ++attempt) {
+            int applied = 0;
+            bool conv = false;
+            void* bufs[2] = {F.u[0], F.u[1]};
+            DD_TRY(run_sweeps(h, F.geom, Store::F32, bufs, F.map_u, h->cur, nullptr, F.tmask, F.partial, F.ref_d,
+                              target, 0.0, h->prm.max_sweeps - fine_sweeps, st, &applied, &conv, true));
+            fine_sweeps += applied;
+            DD_TRY(fine_residual64(h, st, rel, rmax, rnorm));
+            const double worst = *std::max_element(rel.begin(), rel.end());
+            if (worst <= tol) { converged = true; break; }
+            if (!conv) break;
+            target = target * 0.5;   // the FP32 fused estimate was optimistic: tighten and go on
+        }
+    } else {
+        const Store lt = h->lowst;
+        for (int corr = 0;; ++corr) {
+            DD_TRY(fine_residual64(h, st, rel, rmax, rnorm));
+            const double worst = *std::max_element(rel.begin(), rel.end());
+            if (worst <= tol) { converged = true; break; }
+            if (corr >= h->prm.max_corrections || fine_sweeps >= h->prm.max_sweeps) break;
+            for (int c = 0; c < h->C; ++c) {
+                const double s = rmax[c] > 0.0 ? rmax[c] : 1.0;
+                h->h_small[c] = s;
+                h->h_small[h->C + c] = 1.0 / s;
+                h->h_small[2 * h->C + c] = rnorm[c] / s;
+            }
+            DD_CK(cudaMemcpyAsync(h->scale_d, h->h_small, sizeof(double) * h->C, cudaMemcpyHostToDevice, st));
+            DD_CK(cudaMemcpyAsync(h->scale_inv_d, h->h_small + h->C, sizeof(double) * h->C, cudaMemcpyHostToDevice, st));
+            DD_CK(cudaMemcpyAsync(h->inner_ref_d, h->h_small + 2 * h->C, sizeof(double) * h->C,
+                                  cudaMemcpyHostToDevice, st));
+            DD_TRY(write_scaled_residual(h, st));
+            DD_CK(dd::launch_fill_zero(lt, h->e[0], (size_t)h->C * F.plane(), st));
+            int ecur = 0, applied = 0;
+            bool conv = false;
+            void* bufs[2] = {h->e[0], h->e[1]};
+            const double stall = lt == Store::F32 ? 0.0 : 0.7;
+            DD_TRY(run_sweeps(h, F.geom, lt, bufs, h->map_e, ecur, &h->map_g, F.tmask, F.partial, h->inner_ref_d,
+                              h->prm.inner_tol, stall, h->prm.max_sweeps - fine_sweeps, st, &applied, &conv, true));
+            fine_sweeps += applied;
+            DD_LAUNCH(h, dd::launch_correct(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), bufs[ecur], lt, F.P, F.plane(),
+                                     F.mask, F.W, h->scale_d, st));
+            h->stats.corrections = corr + 1;
+            DD_CK(cudaStreamSynchronize(st));   // h_small is reused by the next correction
+        }
+    }
+    h->stats.sweeps_per_level[0] = fine_sweeps;
+    h->stats.sweeps_total += fine_sweeps;
+    h->stats.converged = converged ? 1 : 0;
+    for (int c = 0; c < h->C && c < DD_MAX_STAT_CHANNELS; ++c) h->stats.rel_residual[c] = rel.empty() ? 0 : rel[c];
+    if (u_out != nullptr)
+        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), u_out, F.W, (long long)F.H * F.W, st));
+    DD_CK(cudaEventRecord(h->ev1, st));
+    DD_CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    DD_CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    h->stats.ms_total = ms;
+    h->stats.kernel_launches = h->launches;
+    if (!converged) rc = DD_ENOTCONVERGED;
+    return rc;
+}
+
+void free_all(dd_inpaint* h) {
+    for (void* p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->h_res) cudaFreeHost(h->h_res);
+    if (h->h_small) cudaFreeHost(h->h_small);
+    if (h->h_flag) cudaFreeHost(h->h_flag);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    for (auto& e : h->sw_ev)
+        if (e) cudaEventDestroy(e);
+}
+
+int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, const dd_params* params,
+                dd_handle* out) {
+    if (out == nullptr || mask == nullptr || values == nullptr) { set_error("NULL argument"); return DD_EINVAL; }
+    *out = nullptr;
+    dd_params p;
+    if (params) p = *params; else dd_params_default(&p);
+    DD_TRY(validate(H, W, C, p));
+    if (!(p.robin_p > 0.f)) p.robin_p = robin_default(p.block, p.overlap);
+    long long nknown = 0;
+    DD_TRY(count_known(mask, (size_t)H * W, p.inputs_on_device != 0, &nknown));
+    if (nknown == 0) { set_error("empty mask"); return DD_EEMPTYMASK; }
+
+    dd_inpaint* h = new (std::nothrow) dd_inpaint();
+    if (!h) { set_error("host allocation"); return DD_ENOMEM; }
+    h->H = H; h->W = W; h->C = C; h->prm = p;
+    h->lowst = low_store(p.precision);
+    auto fail = [&](int rc) { free_all(h); delete h; return rc; };
+    int rc = DD_OK;
+    // levels: stop halving once a dimension would fall below 2 pixels
+    int nl = p.levels;
+    {
+        int hh = H, ww = W, l = 1;
+        while (l < nl && hh > 2 && ww > 2) { hh = (hh + 1) / 2; ww = (ww + 1) / 2; ++l; }
+        nl = l;
+    }
+    h->lv.resize(nl);
+    int hh = H, ww = W;
+    for (int l = 0; l < nl; ++l) {
+        Level& L = h->lv[l];
+        L.H = hh; L.W = ww; L.P = round_up(ww, 32);
+        L.geom = dd::make_geom(hh, ww, L.P, p.block, p.overlap);
+        const size_t plane_bytes = (size_t)C * L.plane() * sizeof(float);
+        if ((rc = dalloc_t(h, &L.mask, (size_t)hh * ww)) != DD_OK) return fail(rc);
+        if ((rc = dalloc(h, (void**)&L.f, plane_bytes)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &L.tmask, dd::tmask_words(L.geom))) != DD_OK) return fail(rc);
+        for (int b = 0; b < 2; ++b)
+            if ((rc = dalloc(h, (void**)&L.u[b], plane_bytes)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &L.partial, (size_t)C * L.geom.ntiles)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &L.ref_d, (size_t)C)) != DD_OK) return fail(rc);
+        hh = (hh + 1) / 2; ww = (ww + 1) / 2;
+    }
+    Level& F = h->lv[0];
+    if (p.precision != DD_PREC_FP32) {
+        const size_t n = (size_t)C * F.plane() * dd::store_bytes(h->lowst);
+        for (int b = 0; b < 2; ++b)
+            if ((rc = dalloc(h, &h->e[b], n)) != DD_OK) return fail(rc);
+        if ((rc = dalloc(h, &h->g, n)) != DD_OK) return fail(rc);
+    }
+    for (auto& L : h->lv)
+        for (int b = 0; b < 2; ++b)
+            if (dd::make_tile_map(&L.map_u[b], Store::F32, L.u[b], L.H, L.W, L.P, C, p.block) != cudaSuccess) {
+                set_error("cuTensorMapEncodeTiled failed");
+                return fail(DD_ECUDA);
+            }
+    if (p.precision != DD_PREC_FP32) {
+        for (int b = 0; b < 2; ++b)
+            if (dd::make_tile_map(&h->map_e[b], h->lowst, h->e[b], F.H, F.W, F.P, C, p.block) != cudaSuccess) {
+                set_error("cuTensorMapEncodeTiled failed");
+                return fail(DD_ECUDA);
+            }
+        if (dd::make_tile_map(&h->map_g, h->lowst, h->g, F.H, F.W, F.P, C, p.block) != cudaSuccess) {
+            set_error("cuTensorMapEncodeTiled failed");
+            return fail(DD_ECUDA);
+        }
+    }
+    h->res_nblk = dd::res64_blocks(H, W);
+    if ((rc = dalloc_t(h, &h->res_part, (size_t)C * h->res_nblk)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->res_out, (size_t)C)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->norms2_d, (size_t)2 * C)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->inner_ref_d, (size_t)C)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->scale_d, (size_t)C)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->scale_inv_d, (size_t)C)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->flag_d, 3)) != DD_OK) return fail(rc);
+    if (cudaMallocHost(&h->h_res, sizeof(double2) * C) != cudaSuccess ||
+        cudaMallocHost(&h->h_small, sizeof(double) * 3 * C) != cudaSuccess ||
+        cudaMallocHost(&h->h_flag, sizeof(int) * 4) != cudaSuccess) {
+        set_error("cudaMallocHost failed");
+        return fail(DD_ENOMEM);
+    }
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+        set_error("cudaEventCreate failed");
+        return fail(DD_ECUDA);
+    }
+    for (auto& e : h->sw_ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { set_error("cudaEventCreate failed"); return fail(DD_ECUDA); }
+    if ((rc = dalloc_t(h, &h->count_d, 1)) != DD_OK) return fail(rc);
+    cudaStream_t st = nullptr;
+    if ((rc = load_data(h, mask, values, st)) != DD_OK) return fail(rc);
+    if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("sync"); return fail(DD_ECUDA); }
+    *out = h;
+    return DD_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+void dd_params_default(dd_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->block = 32;
+    p->overlap = 6;
+    p->local_cg_iters = 16;
+    p->levels = 3;
+    p->ml_mode = DD_ML_CASCADE;
+    p->coarse_factor = 2;
+    p->robin_p = 0.f;
+    p->precision = DD_PREC_FP32_REF;
+    p->max_sweeps = 400;
+    p->inputs_on_device = 0;
+    p->coarse_tol = 1e-2;
+    p->inner_tol = 3e-3;
+    p->max_corrections = 30;
+    p->coarse_sweeps = 40;
+    p->timing = 0;
+}
+
+const char* dd_strerror(int code) {
+    switch (code) {
+        case DD_OK: return "ok";
+        case DD_EINVAL: return "invalid argument";
+        case DD_EEMPTYMASK: return "empty mask (A is singular)";
+        case DD_ENOMEM: return "out of memory";
+        case DD_ENOTCONVERGED: return "not converged within the sweep limit";
+        case DD_ENUMERIC: return "non-finite residual";
+        case DD_ECUDA: return "CUDA error";
+        case DD_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown error";
+}
+
+const char* dd_last_error(void) { return g_last_error.c_str(); }
+
+int dd_inpaint_create(int H, int W, int C, const uint8_t* mask, const float* values, const dd_params* params,
+                      dd_handle* out) {
+    return create_impl(H, W, C, mask, values, params, out);
+}
+
+int dd_inpaint_solve(dd_handle h, float* u_out, double tol, void* stream) {
+    if (!h || !u_out || !(tol > 0.0)) { set_error("bad solve arguments"); return DD_EINVAL; }
+    return solve_impl(h, u_out, tol, static_cast<cudaStream_t>(stream));
+}
+
+int dd_inpaint_destroy(dd_handle h) {
+    if (!h) return DD_OK;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+    return DD_OK;
+}
+
+int dd_inpaint_set_data(dd_handle h, const uint8_t* mask, const float* values, int keep_iterate) {
+    if (!h || !mask || !values) { set_error("NULL argument"); return DD_EINVAL; }
+    long long nknown = 0;
+    DD_TRY(count_known(mask, (size_t)h->H * h->W, h->prm.inputs_on_device != 0, &nknown));
+    if (nknown == 0) { set_error("empty mask"); return DD_EEMPTYMASK; }
+    cudaStream_t st = nullptr;
+    Level& F = h->lv[0];
+    // keep the fine iterate in buffer 0 (load_data stages values through u[1])
+    if (keep_iterate && h->cur != 0)
+        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[1], F.P, F.plane(), F.u[0], F.P, F.plane(), st));
+    h->cur = 0;
+    DD_TRY(load_data(h, mask, values, st));
+    if (keep_iterate) {
+        DD_LAUNCH(h, dd::launch_reset_known(F.H, F.W, h->C, F.u[0], F.P, F.plane(), F.mask, F.W, F.f, F.P, F.plane(), st));
+        h->warm = true;
+    } else {
+        h->warm = false;
+    }
+    DD_CK(cudaStreamSynchronize(st));
+    return DD_OK;
+}
+
+int dd_inpaint_stats(dd_handle h, dd_stats* out) {
+    if (!h || !out) { set_error("NULL argument"); return DD_EINVAL; }
+    *out = h->stats;
+    return DD_OK;
+}
+
+int dd_inpaint_set_iterate(dd_handle h, const float* u, void* stream) {
+    if (!h || !u) { set_error("NULL argument"); return DD_EINVAL; }
+    Level& F = h->lv[0];
+    h->cur = 0;
+    DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, u, F.W, (long long)F.H * F.W, F.u[0], F.P, F.plane(),
+                            static_cast<cudaStream_t>(stream)));
+    h->warm = true;
+    return DD_OK;
+}
+
+int dd_inpaint_get_iterate(dd_handle h, float* u_out, void* stream) {
+    if (!h || !u_out) { set_error("NULL argument"); return DD_EINVAL; }
+    Level& F = h->lv[0];
+    DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), u_out, F.W, (long long)F.H * F.W,
+                            static_cast<cudaStream_t>(stream)));
+    return DD_OK;
+}
+
+int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
+    if (!h || n < 0) { set_error("bad sweep arguments"); return DD_EINVAL; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Level& F = h->lv[0];
+    DD_CK(cudaMemsetAsync(h->flag_d, 0, 3 * sizeof(int), st));
+    for (int i = 0; i < n; ++i) {
+        DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), F.map_u[h->cur], nullptr, F.u[1 - h->cur],
+                                      F.tmask, F.partial, nullptr, h->flag_d + 2, h->prm.robin_p,
+                                      h->prm.local_cg_iters, st));
+        h->cur = 1 - h->cur;
+    }
+    if (n > 0) {
+        int err = 0;
+        DD_CK(cudaMemcpyAsync(&err, h->flag_d + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaStreamSynchronize(st));
+        if (err != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
+    }
+    if (rnorm_out != nullptr && n > 0) {
+        DD_LAUNCH(h, dd::launch_reduce_sweep(F.partial, F.geom.ntiles, h->C, h->norms2_d, F.ref_d, -1.0, 0.0,
+                                      h->flag_d, h->flag_d + 1, 0, st));
+        std::vector<double> tmp(h->C);
+        DD_CK(cudaMemcpyAsync(tmp.data(), h->norms2_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaStreamSynchronize(st));
+        for (int c = 0; c < h->C; ++c) rnorm_out[c] = std::sqrt(tmp[c]);
+    }
+    return DD_OK;
+}
+
+int dd_restrict(int H, int W, int C, const uint8_t* mask, const float* f, uint8_t* mask_c, float* f_c,
+                void* stream) {
+    if (H <= 0 || W <= 0 || C <= 0 || !mask || !f || !mask_c || !f_c) { set_error("bad arguments"); return DD_EINVAL; }
+    const int Hc = (H + 1) / 2, Wc = (W + 1) / 2;
+    DD_CK(dd::launch_restrict(H, W, C, mask, W, f, W, (long long)H * W, mask_c, Wc, f_c, Wc, (long long)Hc * Wc,
+                              static_cast<cudaStream_t>(stream)));
+    return DD_OK;
+}
+
+int dd_prolong(int Hc, int Wc, int H, int W, int C, const float* u_c, const uint8_t* mask, const float* f,
+               float* u, void* stream) {
+    if (Hc <= 0 || Wc <= 0 || H <= 0 || W <= 0 || C <= 0 || !u_c || !u || ((mask == nullptr) != (f == nullptr))) {
+        set_error("bad arguments");
+        return DD_EINVAL;
+    }
+    DD_CK(dd::launch_prolong(Hc, Wc, H, W, C, u_c, Wc, (long long)Hc * Wc, mask, W, f, W, (long long)H * W, u, W,
+                             (long long)H * W, static_cast<cudaStream_t>(stream)));
+    return DD_OK;
+}
+
+int dd_residual_norms(int H, int W, int C, const uint8_t* mask, const float* f, const float* u, double* norms,
+                      double* ref_norms, void* stream) {
+    if (H <= 0 || W <= 0 || C <= 0 || !mask || !f || !u) { set_error("bad arguments"); return DD_EINVAL; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nblk = dd::res64_blocks(H, W);
+    double2* part = nullptr;
+    double2* outd = nullptr;
+    float* u0 = nullptr;
+    std::vector<double2> hout(C);
+    auto cleanup = [&]() {
+        if (part) cudaFree(part);
+        if (outd) cudaFree(outd);
+        if (u0) cudaFree(u0);
+    };
+    if (cudaMalloc(&part, sizeof(double2) * nblk * C) != cudaSuccess ||
+        cudaMalloc(&outd, sizeof(double2) * C) != cudaSuccess ||
+        cudaMalloc(&u0, sizeof(float) * (size_t)C * H * W) != cudaSuccess) {
+        cleanup();
+        set_error("cudaMalloc failed");
+        return DD_ENOMEM;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        double* dst = pass == 0 ? norms : ref_norms;
+        if (!dst) continue;
+        const float* src = u;
+        if (pass == 1) {
+            if (dd::launch_masked_copy(H, W, C, f, W, (long long)H * W, mask, W, u0, W, (long long)H * W, st) !=
+                cudaSuccess) { cleanup(); set_error("launch"); return DD_ECUDA; }
+            src = u0;
+        }
+        dd::Res64Args a{};
+        a.H = H; a.W = W; a.C = C; a.u = src; a.up = W; a.uplane = (long long)H * W;
+        a.mask = mask; a.mp = W; a.g_out = nullptr; a.gst = Store::F32; a.part = part; a.nblk = nblk;
+        if (dd::launch_res64(a, st) != cudaSuccess || dd::launch_reduce_part(part, nblk, C, outd, st) != cudaSuccess ||
+            cudaMemcpyAsync(hout.data(), outd, sizeof(double2) * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cleanup();
+            set_error("residual pass failed");
+            return DD_ECUDA;
+        }
+        for (int c = 0; c < C; ++c) dst[c] = std::sqrt(hout[c].x);
+    }
+    cleanup();
+    return DD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,675 @@
+// ORAS sweep kernels (Sec. 3-4 of Kaemper & Weickert, arXiv 2110.03946).
+//
+// One sweep computes, for every block Omega_i of every channel, the local
+// residual R_i r^n with r^n = b - A u^n, runs k conjugate-gradient steps on the
+// local problem R_i A R_i^T v_i = R_i r^n (Eq. eq:ras-local-problem) with the
+// optimised Robin interface condition, and adds v_i back on the block's owned
+// core only (u^{n+1} = u^n + sum_i R_i^T D_i v_i, D_i 0/1).  All blocks read
+// u^n and write u^{n+1} into a second buffer (additive Schwarz).
+//
+// GPU mapping.  Persistent CTAs walk the (channel, block) list.  Thread 0
+// stages the next block's tile plus a one-pixel halo (and the correction
+// source, if any) into shared memory with a TMA tensor copy while the CTA
+// works on the current block (two buffers, one mbarrier each; every wait is
+// bounded and a timeout sets an error word).  The block is then held in
+// registers by NW warps: lane (lx, ly) of warp wt owns a PX x PY patch (PX
+// columns as PX/2 packed FP32 pairs).  Values across patch borders move by
+// warp shuffles and, between the NW warps, through shared memory.  CG dot
+// products are xor-butterfly warp sums (bitwise identical on every lane, so all
+// break decisions are uniform) plus a fixed-order sum over warps.  Packed pair
+// arithmetic (__ffma2_rn and friends, sm_100+) halves the issue slots.
+//
+// Local operator (unknown pixel p of the block):
+//   (A_i v)_p = dd_p v_p - sum_{q in N(p), q in block} v_q,
+//   dd_p = #{in-block neighbours} + p_R * #{in-image neighbours outside the block},
+// known pixels have identity rows of A and, because u = f is held there, zero
+// right-hand side, so v = 0 on them; the kernel keeps r = p = q = 0 there.
+// The kernel computes q' = -(A_i p) = w (sum + nd p), nd = -dd, w = 1 - known.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "dd_internal.h"
+
+namespace dd {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls (a TMA copy takes ~1 us)
+
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(FULL, v, m);
+    return v;
+}
+
+// ---- TMA / mbarrier primitives (PTX ISA: mbarrier, cp.async.bulk.tensor) ----------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (int n = 0; n < kWaitLimit; ++n)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Tile shape: LX x LY lanes per warp, PX x PY pixels per lane, NW warps stacked
+// vertically; one block tile per CTA at a time.
+template <int PX_, int PY_, int LX_, int NW_>
+struct Cfg {
+    static constexpr int PX = PX_, PY = PY_, LX = LX_, NW = NW_;
+    static constexpr int LY = 32 / LX;
+    static constexpr int BW = LX * PX;
+    static constexpr int BH = NW * LY * PY;
+    static constexpr int NP = PX / 2;
+    static constexpr int NT = NW * 32;
+    static_assert(PX % 2 == 0 && PX * PY <= 32 && BW == BH && 32 % LX == 0, "bad tile shape");
+};
+
+using Cfg16 = Cfg<2, 4, 8, 1>;   // 16 x 16 block, one warp, 8 px per lane
+using Cfg32 = Cfg<4, 8, 8, 1>;   // 32 x 32 block, one warp, 32 px per lane
+using Cfg64 = Cfg<4, 8, 16, 4>;  // 64 x 64 block, four warps of 64 x 16, 32 px per lane
+
+// Shared-memory tile: block plus one-pixel halo; the TMA box starts at a
+// 16-byte aligned column at or left of x0 - 1, so it is BX >= BW + 2 + (align - 1) wide.
+template <class CF, typename T>
+struct Box {
+    static constexpr int ALIGN = 16 / (int)sizeof(T);
+    static constexpr int BX = (CF::BW + 2 + ALIGN - 1 + ALIGN - 1) / ALIGN * ALIGN;
+    static constexpr int BY = CF::BH + 2;
+    static constexpr int BYTES = BX * BY * (int)sizeof(T);
+    static constexpr int STRIDE = (BYTES + 127) / 128 * 128;   // per staged array
+    static_assert(BX <= 256 && BY <= 256, "TMA box too large");
+};
+
+template <typename T>
+struct SweepArgs {
+    T* u_out;
+    const uint32_t* tmask;
+    float* partial;
+    const int* skip;
+    int* err;
+    int H, W, pitch, C;
+    int s, ntx, ntiles;
+    int has_g;
+    long long plane;
+    float p_robin;
+    int k;
+};
+
+// Sum over the threads of one tile; identical result in every thread.
+template <class CF>
+__device__ __forceinline__ float tile_sum(float v, float* red, int wt, int lane) {
+    v = warp_sum(v);
+    if constexpr (CF::NW == 1) {
+        return v;
+    } else {
+        if (lane == 0) red[wt] = v;
+        __syncthreads();
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < CF::NW; ++w) t += red[w];
+        return t;
+    }
+}
+
+template <class CF, typename T>
+__global__ void __launch_bounds__(CF::NT)
+oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_g,
+                  const SweepArgs<T> a) {
+    constexpr int PX = CF::PX, PY = CF::PY, LX = CF::LX, LY = CF::LY, NW = CF::NW;
+    constexpr int BW = CF::BW, BH = CF::BH, NP = CF::NP, NT = CF::NT;
+    using BOX = Box<CF, T>;
+    constexpr int BX = BOX::BX;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ int s_ok;
+    __shared__ float red[3][NW];
+    __shared__ float red3[2][2][NW];   // CG reductions (p,Ap) and (r,r), alternating by step parity
+    __shared__ float xch[2][NW][BW];
+
+    if (a.skip != nullptr && *a.skip != 0) return;   // uniform over the grid
+    const long long total = (long long)a.ntiles * a.C;
+    long long t = blockIdx.x;
+    if (t >= total) return;
+
+    const int tt = threadIdx.x;
+    const int wt = tt >> 5, lane = tt & 31;
+    const int lx = lane % LX, ly = lane / LX;
+    const int ry0 = (wt * LY + ly) * PY, rx0 = lx * PX;
+    const int H = a.H, W = a.W, P = a.pitch;
+    const int narr = a.has_g ? 2 : 1;
+    const uint32_t tx_bytes = (uint32_t)(BOX::BYTES * narr);
+    // TMA destinations must be 128-byte aligned: round the dynamic base up
+    // (the launch reserves 128 bytes of slack for this).
+    unsigned char* const smem =
+        smem_raw + (((smem_addr(smem_raw) + 127u) & ~127u) - smem_addr(smem_raw));
+    auto stage = [&](int buf, int which) {
+        return reinterpret_cast<T*>(smem + (size_t)(buf * narr + which) * BOX::STRIDE);
+    };
+    auto issue = [&](long long tn, int buf) {   // thread 0 only
+        const int c = (int)(tn / a.ntiles);
+        const int tile = (int)(tn - (long long)c * a.ntiles);
+        const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+        const int x0 = tx * a.s, y0 = ty * a.s;
+        const int xs = ((x0 - 1) >= 0 ? (x0 - 1) / BOX::ALIGN : -1) * BOX::ALIGN;
+        fence_proxy_async();
+        mbar_expect_tx(&mbar[buf], tx_bytes);
+        tma_load_3d(stage(buf, 0), &map_u, xs, y0 - 1, c, &mbar[buf]);
+        if (a.has_g) tma_load_3d(stage(buf, 1), &map_g, xs, y0 - 1, c, &mbar[buf]);
+    };
+
+    if (tt == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tt == 0) issue(t, 0);
+
+    const float pr = a.p_robin;
+    const float fW = lx > 0 ? 1.f : 0.f, fE = lx < LX - 1 ? 1.f : 0.f;
+    int it = 0;
+    for (; t < total; t += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const uint32_t parity = (uint32_t)((it >> 1) & 1);
+        if (tt == 0 && t + gridDim.x < total) issue(t + gridDim.x, buf ^ 1);
+
+        const int c = (int)(t / a.ntiles);
+        const int tile = (int)(t - (long long)c * a.ntiles);
+        const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+        const int y0 = ty * a.s, x0 = tx * a.s;
+        const int th = min(BH, H - y0), tw = min(BW, W - x0);
+        const int cx = x0 - ((x0 - 1) >= 0 ? (x0 - 1) / BOX::ALIGN : -1) * BOX::ALIGN;   // smem column of x0
+        const uint32_t kb = a.tmask[(size_t)tile * 2 * NT + tt];
+        const uint32_t ob = a.tmask[(size_t)tile * 2 * NT + NT + tt];
+
+        if (tt == 0) {
+            const bool ok = mbar_wait_bounded(&mbar[buf], parity);
+            s_ok = ok ? 1 : 0;
+            if (!ok) atomicExch(a.err, 1);
+        }
+        __syncthreads();
+        if (!s_ok) break;                               // uniform
+        if (tt != 0) mbar_wait_bounded(&mbar[buf], parity);   // phase already complete: returns at once
+        const T* __restrict__ U = stage(buf, 0);
+        const T* __restrict__ G = stage(buf, 1);
+
+        // ---- local residual R_i (b - A u^n) and the owned residual norm ----------
+        // The patch and its one-pixel ring are read from the staged tile once;
+        // neighbours outside the image are never used (reflecting boundary).
+        float2 r2[PY][NP];
+        float s2 = 0.f;
+        {
+            const int o0 = (1 + ry0) * BX + cx + rx0;
+            float uu[PY + 2][PX + 2];
+#pragma unroll
+            for (int i = 0; i < PY + 2; ++i)
+#pragma unroll
+                for (int j = 0; j < PX + 2; ++j) {
+                    const bool corner = (i == 0 || i == PY + 1) && (j == 0 || j == PX + 1);
+                    uu[i][j] = corner ? 0.f : to_f(U[o0 + (i - 1) * BX + (j - 1)]);
+                }
+#pragma unroll
+            for (int i = 0; i < PY; ++i)
+#pragma unroll
+                for (int j = 0; j < PX; ++j) {
+                    float res = 0.f;
+                    if (!((kb >> (i * PX + j)) & 1u)) {            // unknown and inside the block
+                        const int y = y0 + ry0 + i, x = x0 + rx0 + j;
+                        const float uc = uu[i + 1][j + 1];
+                        float acc = a.has_g ? to_f(G[o0 + i * BX + j]) : 0.f;
+                        if (y > 0) acc += uu[i][j + 1] - uc;
+                        if (y < H - 1) acc += uu[i + 2][j + 1] - uc;
+                        if (x > 0) acc += uu[i + 1][j] - uc;
+                        if (x < W - 1) acc += uu[i + 1][j + 2] - uc;
+                        res = acc;
+                        if ((ob >> (i * PX + j)) & 1u) s2 = fmaf(res, res, s2);
+                    }
+                    if (j & 1) r2[i][j >> 1].y = res; else r2[i][j >> 1].x = res;
+                }
+        }
+        s2 = tile_sum<CF>(s2, red[0], wt, lane);
+        if (a.partial != nullptr && tt == 0) a.partial[t] = s2;
+
+        // ---- local operator coefficients -----------------------------------------
+        float2 rpn[PY];     // -(vertical part of dd), both halves equal
+        float2 cpn[NP];     // -(horizontal part of dd)
+        float2 w2[PY][NP];  // 1 on unknown in-block pixels, else 0
+#pragma unroll
+        for (int i = 0; i < PY; ++i) {
+            const int ry = ry0 + i, y = y0 + ry;
+            const float up = ry > 0 ? 1.f : (y > 0 ? pr : 0.f);
+            const float dn = ry < th - 1 ? 1.f : (y < H - 1 ? pr : 0.f);
+            rpn[i] = make_float2(-(up + dn), -(up + dn));
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            float v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int rx = rx0 + 2 * j + e, x = x0 + rx;
+                const float lf = rx > 0 ? 1.f : (x > 0 ? pr : 0.f);
+                const float rt = rx < tw - 1 ? 1.f : (x < W - 1 ? pr : 0.f);
+                v[e] = -(lf + rt);
+            }
+            cpn[j] = make_float2(v[0], v[1]);
+        }
+#pragma unroll
+        for (int i = 0; i < PY; ++i)
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+                w2[i][j] = make_float2(((kb >> (i * PX + 2 * j)) & 1u) ? 0.f : 1.f,
+                                       ((kb >> (i * PX + 2 * j + 1)) & 1u) ? 0.f : 1.f);
+
+        // ---- k CG steps from v = 0 (Saad, the CG algorithm of Ch. 6) --------------
+        float2 v2[PY][NP], p2[PY][NP], q2[PY][NP];
+        float rr;
+        {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < PY; ++i)
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    v2[i][j] = make_float2(0.f, 0.f);
+                    p2[i][j] = r2[i][j];
+                    acc = fma2(r2[i][j], r2[i][j], acc);
+                }
+            rr = tile_sum<CF>(acc.x + acc.y, red[1], wt, lane);
+        }
+        for (int kk = 0; kk < a.k; ++kk) {
+            if (!(rr > 0.f)) break;
+            float pW[PY], pE[PY];
+#pragma unroll
+            for (int i = 0; i < PY; ++i) {
+                pW[i] = fW * __shfl_up_sync(FULL, p2[i][NP - 1].y, 1, LX);
+                pE[i] = fE * __shfl_down_sync(FULL, p2[i][0].x, 1, LX);
+            }
+            float2 pN[NP], pS[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                pN[j].x = __shfl_up_sync(FULL, p2[PY - 1][j].x, LX);
+                pN[j].y = __shfl_up_sync(FULL, p2[PY - 1][j].y, LX);
+                pS[j].x = __shfl_down_sync(FULL, p2[0][j].x, LX);
+                pS[j].y = __shfl_down_sync(FULL, p2[0][j].y, LX);
+            }
+            if constexpr (NW > 1) {
+                if (ly == 0) {
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        xch[0][wt][rx0 + 2 * j] = p2[0][j].x;
+                        xch[0][wt][rx0 + 2 * j + 1] = p2[0][j].y;
+                    }
+                }
+                if (ly == LY - 1) {
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        xch[1][wt][rx0 + 2 * j] = p2[PY - 1][j].x;
+                        xch[1][wt][rx0 + 2 * j + 1] = p2[PY - 1][j].y;
+                    }
+                }
+                __syncthreads();
+                if (ly == 0) {
+#pragma unroll
+                    for (int j = 0; j < NP; ++j)
+                        pN[j] = wt > 0 ? make_float2(xch[1][wt - 1][rx0 + 2 * j], xch[1][wt - 1][rx0 + 2 * j + 1])
+                                       : make_float2(0.f, 0.f);
+                }
+                if (ly == LY - 1) {
+#pragma unroll
+                    for (int j = 0; j < NP; ++j)
+                        pS[j] = wt < NW - 1 ? make_float2(xch[0][wt + 1][rx0 + 2 * j], xch[0][wt + 1][rx0 + 2 * j + 1])
+                                            : make_float2(0.f, 0.f);
+                }
+            } else {
+                if (ly == 0) {
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) pN[j] = make_float2(0.f, 0.f);
+                }
+                if (ly == LY - 1) {
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) pS[j] = make_float2(0.f, 0.f);
+                }
+            }
+            // q' = -(A_i p), and (p, q'); two independent accumulator chains
+            float2 pqa = make_float2(0.f, 0.f), pqb = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < PY; ++i)
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    const float2 n = i > 0 ? p2[i - 1][j] : pN[j];
+                    const float2 s = i < PY - 1 ? p2[i + 1][j] : pS[j];
+                    const float left = j > 0 ? p2[i][j - 1].y : pW[i];
+                    const float right = j < NP - 1 ? p2[i][j + 1].x : pE[i];
+                    const float2 h = make_float2(left + p2[i][j].y, p2[i][j].x + right);
+                    const float2 sum = add2(add2(n, s), h);
+                    const float2 nd = add2(rpn[i], cpn[j]);
+                    const float2 q = mul2(w2[i][j], fma2(nd, p2[i][j], sum));
+                    q2[i][j] = q;
+                    if (i & 1) pqb = fma2(p2[i][j], q, pqb); else pqa = fma2(p2[i][j], q, pqa);
+                }
+            const float pq = -tile_sum<CF>((pqa.x + pqa.y) + (pqb.x + pqb.y), red3[kk & 1][0], wt, lane);
+            if (!(pq > 0.f)) break;
+            const float alpha = rr / pq;
+            const float2 a2 = make_float2(alpha, alpha);
+            float2 rra = make_float2(0.f, 0.f), rrb = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < PY; ++i)
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    v2[i][j] = fma2(a2, p2[i][j], v2[i][j]);
+                    r2[i][j] = fma2(a2, q2[i][j], r2[i][j]);     // r - alpha A p
+                    if (i & 1) rrb = fma2(r2[i][j], r2[i][j], rrb); else rra = fma2(r2[i][j], r2[i][j], rra);
+                }
+            const float rr_new = tile_sum<CF>((rra.x + rra.y) + (rrb.x + rrb.y), red3[kk & 1][1], wt, lane);
+            const float beta = rr_new / rr;
+            const float2 b2 = make_float2(beta, beta);
+#pragma unroll
+            for (int i = 0; i < PY; ++i)
+#pragma unroll
+                for (int j = 0; j < NP; ++j) p2[i][j] = fma2(b2, p2[i][j], r2[i][j]);
+            rr = rr_new;
+        }
+
+        // ---- restricted add-back on the owned core -------------------------------
+        T* __restrict__ uout = a.u_out + (size_t)c * a.plane;
+#pragma unroll
+        for (int i = 0; i < PY; ++i)
+#pragma unroll
+            for (int j = 0; j < PX; ++j) {
+                if ((ob >> (i * PX + j)) & 1u) {
+                    const int o = (1 + ry0 + i) * BX + cx + rx0 + j;
+                    const float v = (j & 1) ? v2[i][j >> 1].y : v2[i][j >> 1].x;
+                    uout[(size_t)(y0 + ry0 + i) * P + (x0 + rx0 + j)] = from_f<T>(to_f(U[o]) + v);
+                }
+            }
+        __syncthreads();   // the staged tile may now be refilled
+    }
+    if (tt == 0 && !s_ok) {
+        // a copy timed out: wait (bounded) for the other buffer's copy before leaving
+        mbar_wait_bounded(&mbar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+    }
+}
+
+template <class CF>
+__global__ void build_tmask_kernel(const uint8_t* __restrict__ mask, int mp, uint32_t* __restrict__ tmask,
+                                   int H, int W, int s, int half_o, int ntx, int nty, int ntiles) {
+    constexpr int PX = CF::PX, PY = CF::PY, LX = CF::LX, LY = CF::LY, NT = CF::NT;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)ntiles * NT) return;
+    const int tile = (int)(gid / NT), tt = (int)(gid - (long long)tile * NT);
+    const int wt = tt >> 5, lane = tt & 31, lx = lane % LX, ly = lane / LX;
+    const int ty = tile / ntx, tx = tile - ty * ntx;
+    const int y0 = ty * s, x0 = tx * s;
+    const int th = min(CF::BH, H - y0), tw = min(CF::BW, W - x0);
+    const int oy0 = ty == 0 ? 0 : y0 + half_o, oy1 = ty == nty - 1 ? H : y0 + s + half_o;
+    const int ox0 = tx == 0 ? 0 : x0 + half_o, ox1 = tx == ntx - 1 ? W : x0 + s + half_o;
+    const int ry0 = (wt * LY + ly) * PY, rx0 = lx * PX;
+    uint32_t kb = 0, ob = 0;
+    for (int i = 0; i < PY; ++i)
+        for (int j = 0; j < PX; ++j) {
+            const int bit = i * PX + j;
+            const int y = y0 + ry0 + i, x = x0 + rx0 + j;
+            const bool in = (ry0 + i < th) && (rx0 + j < tw);
+            if (!in || mask[(size_t)y * mp + x] != 0) kb |= 1u << bit;
+            if (in && y >= oy0 && y < oy1 && x >= ox0 && x < ox1) ob |= 1u << bit;
+        }
+    tmask[(size_t)tile * 2 * NT + tt] = kb;
+    tmask[(size_t)tile * 2 * NT + NT + tt] = ob;
+}
+
+// Unknown in-block pixels summed over all blocks: each thread word has PX*PY
+// pixels, known-or-outside ones have their bit set.
+template <class CF>
+__global__ void count_unknown_kernel(const uint32_t* __restrict__ tmask, int ntiles,
+                                     unsigned long long* __restrict__ out) {
+    constexpr int NT = CF::NT, NPX = CF::PX * CF::PY;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned v = 0;
+    if (gid < (long long)ntiles * NT) {
+        const int tile = (int)(gid / NT), tt = (int)(gid - (long long)tile * NT);
+        v = NPX - __popc(tmask[(size_t)tile * 2 * NT + tt]);
+    }
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(FULL, v, m);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, (unsigned long long)v);
+}
+
+template <class CF, typename T>
+size_t sweep_smem_bytes(bool has_g) {
+    return (size_t)Box<CF, T>::STRIDE * 2 * (has_g ? 2 : 1) + 128;
+}
+
+template <class CF, typename T>
+int persistent_grid(bool has_g) {
+    // CTAs per SM from the occupancy calculator, cached per instantiation and shape
+    static int cached[2] = {0, 0};
+    int& slot = cached[has_g ? 1 : 0];
+    if (slot == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t smem = sweep_smem_bytes<CF, T>(has_g);
+        cudaFuncSetAttribute(oras_sweep_kernel<CF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oras_sweep_kernel<CF, T>, CF::NT, smem);
+        slot = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+    }
+    return slot;
+}
+
+template <class CF, typename T>
+cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const CUtensorMap& mu, const CUtensorMap* mg,
+                      void* u_out, const uint32_t* tmask, float* partial, const int* skip, int* err,
+                      float p_robin, int k, cudaStream_t st) {
+    SweepArgs<T> a;
+    a.u_out = static_cast<T*>(u_out);
+    a.tmask = tmask;
+    a.partial = partial;
+    a.skip = skip;
+    a.err = err;
+    a.H = g.H; a.W = g.W; a.pitch = g.pitch; a.C = C;
+    a.s = g.s; a.ntx = g.ntx; a.ntiles = g.ntiles;
+    a.has_g = mg != nullptr;
+    a.plane = plane;
+    a.p_robin = p_robin;
+    a.k = k;
+    const long long work = (long long)g.ntiles * C;
+    const long long grid = std::min<long long>(work, persistent_grid<CF, T>(a.has_g));
+    const size_t smem = sweep_smem_bytes<CF, T>(a.has_g);
+    oras_sweep_kernel<CF, T><<<(unsigned)grid, CF::NT, smem, st>>>(mu, mg ? *mg : mu, a);
+    return cudaGetLastError();
+}
+
+template <class CF>
+cudaError_t sweep_store(Store s, const TileGeom& g, int C, long long plane, const CUtensorMap& mu,
+                        const CUtensorMap* mg, void* u_out, const uint32_t* tmask, float* partial, const int* skip,
+                        int* err, float p_robin, int k, cudaStream_t st) {
+    switch (s) {
+        case Store::F32:
+            return sweep_cfg<CF, float>(g, C, plane, mu, mg, u_out, tmask, partial, skip, err, p_robin, k, st);
+        case Store::F16:
+            return sweep_cfg<CF, __half>(g, C, plane, mu, mg, u_out, tmask, partial, skip, err, p_robin, k, st);
+        case Store::BF16:
+            return sweep_cfg<CF, __nv_bfloat16>(g, C, plane, mu, mg, u_out, tmask, partial, skip, err, p_robin, k, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class CF>
+cudaError_t tmask_cfg(const TileGeom& g, const uint8_t* mask, int mp, uint32_t* tmask, cudaStream_t st) {
+    const long long n = (long long)g.ntiles * CF::NT;
+    const int tpb = 256;
+    build_tmask_kernel<CF><<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
+        mask, mp, tmask, g.H, g.W, g.s, g.half_o, g.ntx, g.nty, g.ntiles);
+    return cudaGetLastError();
+}
+
+template <class CF>
+cudaError_t count_cfg(const TileGeom& g, const uint32_t* tmask, unsigned long long* out, cudaStream_t st) {
+    const long long n = (long long)g.ntiles * CF::NT;
+    const int tpb = 256;
+    count_unknown_kernel<CF><<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(tmask, g.ntiles, out);
+    return cudaGetLastError();
+}
+
+template <class CF, typename T>
+void box_dims(int* bx, int* by) {
+    *bx = Box<CF, T>::BX;
+    *by = Box<CF, T>::BY;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (fn == nullptr) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+int axis_blocks(int n, int b, int o) {
+    const int s = b - o;
+    const int m = n - o;
+    const int cnt = m <= 0 ? 1 : (m + s - 1) / s;
+    return cnt < 1 ? 1 : cnt;
+}
+
+TileGeom make_geom(int H, int W, int pitch, int b, int o) {
+    TileGeom g;
+    g.H = H; g.W = W; g.pitch = pitch;
+    g.b = b; g.o = o; g.s = b - o; g.half_o = o / 2;
+    g.ntx = axis_blocks(W, b, o);
+    g.nty = axis_blocks(H, b, o);
+    g.ntiles = g.ntx * g.nty;
+    return g;
+}
+
+bool block_supported(int b) { return b == 16 || b == 32 || b == 64; }
+
+int tile_threads(int b) {
+    switch (b) {
+        case 16: return Cfg16::NT;
+        case 32: return Cfg32::NT;
+        case 64: return Cfg64::NT;
+    }
+    return 0;
+}
+
+size_t tmask_words(const TileGeom& g) { return (size_t)g.ntiles * 2 * tile_threads(g.b); }
+
+cudaError_t make_tile_map(CUtensorMap* out, Store s, const void* base, int H, int W, int pitch, int C, int b) {
+    int bx = 0, by = 0;
+    auto pick = [&](auto cfg) {
+        using CF = decltype(cfg);
+        switch (s) {
+            case Store::F32: box_dims<CF, float>(&bx, &by); break;
+            case Store::F16: box_dims<CF, __half>(&bx, &by); break;
+            case Store::BF16: box_dims<CF, __nv_bfloat16>(&bx, &by); break;
+        }
+    };
+    switch (b) {
+        case 16: pick(Cfg16{}); break;
+        case 32: pick(Cfg32{}); break;
+        case 64: pick(Cfg64{}); break;
+        default: return cudaErrorInvalidValue;
+    }
+    auto fn = encode_fn();
+    if (fn == nullptr) return cudaErrorNotSupported;
+    const size_t es = store_bytes(s);
+    const CUtensorMapDataType dt = s == Store::F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : s == Store::F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)C};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)pitch * H * es};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(out, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_build_tmask(const TileGeom& g, const uint8_t* mask, int mp, uint32_t* tmask,
+                               cudaStream_t st) {
+    switch (g.b) {
+        case 16: return tmask_cfg<Cfg16>(g, mask, mp, tmask, st);
+        case 32: return tmask_cfg<Cfg32>(g, mask, mp, tmask, st);
+        case 64: return tmask_cfg<Cfg64>(g, mask, mp, tmask, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsigned long long* out,
+                                 cudaStream_t st) {
+    switch (g.b) {
+        case 16: return count_cfg<Cfg16>(g, tmask, out, st);
+        case 32: return count_cfg<Cfg32>(g, tmask, out, st);
+        case 64: return count_cfg<Cfg64>(g, tmask, out, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sweep(Store s, const TileGeom& g, int C, long long plane, const CUtensorMap& map_in,
+                         const CUtensorMap* map_g, void* u_out, const uint32_t* tmask, float* partial,
+                         const int* skip, int* err, float p_robin, int k, cudaStream_t st) {
+    switch (g.b) {
+        case 16: return sweep_store<Cfg16>(s, g, C, plane, map_in, map_g, u_out, tmask, partial, skip, err, p_robin, k, st);
+        case 32: return sweep_store<Cfg32>(s, g, C, plane, map_in, map_g, u_out, tmask, partial, skip, err, p_robin, k, st);
+        case 64: return sweep_store<Cfg64>(s, g, C, plane, map_in, map_g, u_out, tmask, partial, skip, err, p_robin, k, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dd
