@@ -148,7 +148,7 @@ int validate(int H, int W, int C, const dd_params& p) {
     if (p.overlap < 0 || p.overlap >= p.block) { set_error("need 0 <= overlap < block"); return DD_EINVAL; }
     if (p.local_cg_iters < 1 || p.local_cg_iters > 4096) { set_error("local_cg_iters out of range"); return DD_EINVAL; }
     if (p.levels < 1 || p.levels > DD_MAX_LEVELS) { set_error("levels must be 1..8"); return DD_EINVAL; }
-    if (p.ml_mode != DD_ML_CASCADE && p.ml_mode != DD_ML_CORRECTION) { set_error("bad ml_mode"); return DD_EINVAL; }
+    if (p.ml_mode != DD_ML_CASCADE) { set_error("ml_mode: only DD_ML_CASCADE is implemented"); return DD_EINVAL; }
     if (p.precision < DD_PREC_FP32 || p.precision > DD_PREC_BF16_REF) { set_error("bad precision"); return DD_EINVAL; }
     if (p.max_sweeps < 0 || p.coarse_sweeps < 0 || p.max_corrections < 0) { set_error("negative limit"); return DD_EINVAL; }
     if (!(p.coarse_tol > 0.0) || !(p.inner_tol > 0.0) || !(p.inner_tol < 1.0)) { set_error("bad tolerance"); return DD_EINVAL; }
