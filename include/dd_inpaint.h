@@ -204,6 +204,36 @@ int dd_prolong(int Hc, int Wc, int H, int W, int C, const float *u_c, const uint
 int dd_residual_norms(int H, int W, int C, const uint8_t *mask, const float *f,
                       const float *u, double *norms, double *ref_norms, void *stream);
 
+/*
+ * Allocation-free solve (the paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory).  Some callers must not call
+ * cudaMalloc: code inside a host framework that owns the device allocator (for
+ * example a caching pool it does not want bypassed), plug-ins that may not grow
+ * the process's device footprint, and real-time paths where an allocation's
+ * latency or failure is not acceptable.  This call runs the same one-level FP32
+ * ORAS sweeps as dd_inpaint_solve with levels = 1 and precision = DD_PREC_FP32,
+ * but takes all its scratch from one fixed-size device array that is part of
+ * the library (about 37 MiB, present on every GPU that loads the library until
+ * the process exits).  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *   mask (H*W bytes), values (C*H*W floats), u_out (C*H*W floats): DEVICE;
+ *   params: NULL = defaults; block, overlap, local_cg_iters, robin_p and
+ *   max_sweeps are used, levels and precision are ignored;
+ *   tol: relative residual target as in dd_inpaint_solve (FP64-verified).
+ * Capacity: C <= 16, C*H*roundup(W,32) <= 4194304, at most 16384 blocks per
+ * channel and 65536 blocks over all channels; larger inputs return DD_EINVAL
+ * (dd_last_error() says which limit) before any GPU work.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the previous call's
+ * contents: calls whose GPU work overlaps (other streams or host threads) race
+ * and give wrong results, so serialise them.  Synchronises stream.
+ * Errors: DD_EINVAL, DD_EEMPTYMASK, DD_ENOTCONVERGED (u_out still written),
+ * DD_ENUMERIC, DD_ETIMEOUT, DD_ECUDA.
+ */
+int dd_inpaint_solve_static(int H, int W, int C, const uint8_t *mask, const float *values, float *u_out,
+                            const dd_params *params, double tol, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

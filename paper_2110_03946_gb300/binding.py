@@ -25,7 +25,7 @@ EXPORTS = (
     "dd_params_default", "dd_strerror", "dd_last_error",
     "dd_inpaint_create", "dd_inpaint_solve", "dd_inpaint_destroy", "dd_inpaint_set_data",
     "dd_inpaint_stats", "dd_inpaint_set_iterate", "dd_inpaint_get_iterate", "dd_inpaint_sweep",
-    "dd_restrict", "dd_prolong", "dd_residual_norms",
+    "dd_restrict", "dd_prolong", "dd_residual_norms", "dd_inpaint_solve_static",
 )
 
 
@@ -80,6 +80,7 @@ def load(path: str | None = None):
         "dd_restrict": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),
         "dd_prolong": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P]),
         "dd_residual_norms": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
+        "dd_inpaint_solve_static": (_I, [_I, _I, _I, _P, _P, _P, ctypes.POINTER(dd_params), _D, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -176,6 +177,13 @@ def dd_restrict(H, W, C, mask_ptr, f_ptr, mask_c_ptr, f_c_ptr, stream=None) -> i
 
 def dd_prolong(Hc, Wc, H, W, C, uc_ptr, mask_ptr, f_ptr, u_ptr, stream=None) -> int:
     return load().dd_prolong(Hc, Wc, H, W, C, uc_ptr, mask_ptr, f_ptr, u_ptr, _stream(stream))
+
+
+def dd_inpaint_solve_static(H, W, C, mask_ptr, values_ptr, u_out_ptr, params, tol, stream=None) -> int:
+    """Allocation-free one-level FP32 solve into caller buffers (all device)."""
+    return load().dd_inpaint_solve_static(H, W, C, mask_ptr, values_ptr, u_out_ptr,
+                                          ctypes.byref(params) if params is not None else None, tol,
+                                          _stream(stream))
 
 
 def dd_residual_norms(H, W, C, mask_ptr, f_ptr, u_ptr, stream=None):

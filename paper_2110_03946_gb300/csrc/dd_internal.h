@@ -116,4 +116,9 @@ cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long upla
 cudaError_t launch_convert(int H, int W, int C, const float* src, int sp, long long splane,
                            void* dst, Store dst_t, int dp, long long dplane, cudaStream_t st);
 
+// Default Robin weight for block side b and overlap o (the value create uses).
+float default_robin(int b, int o);
+// Record the text returned by dd_last_error() on this thread.
+void set_last_error(const char* msg);
+
 }  // namespace dd

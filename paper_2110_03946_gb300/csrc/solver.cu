@@ -567,6 +567,12 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
 
 }  // namespace
 
+// Internal helpers shared with other translation units (dd_internal.h).
+namespace dd {
+float default_robin(int b, int o) { return robin_default(b, o); }
+void set_last_error(const char* msg) { set_error(msg ? msg : ""); }
+}  // namespace dd
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 
