@@ -1,5 +1,5 @@
-// Auxiliary passes of the ORAS solver: data packing, the FP64 residual of the
-// outer correction, norm reductions with the device-side stop test, the
+// Auxiliary passes of the ORAS solver: data packing, the residual of the
+// outer correction and its norm reductions, the
 // dyadic mask/value subsampling and the coarse-to-fine prolongation of the
 // multilevel method (Sec. 4 of Kaemper & Weickert, arXiv 2110.03946).
 // All are HBM-bound streaming passes: one thread per pixel (or per output
@@ -60,9 +60,32 @@ __global__ void convert_kernel(int H, int W, const float* __restrict__ src, int 
     dst[c * dplane + (size_t)y * dp + x] = from_f<T>(src[c * splane + (size_t)y * sp + x]);
 }
 
-// ---- FP64 residual ------------------------------------------------------------------
+// ---- residual of the outer correction -----------------------------------------------
+// r = b - A u on unknown pixels, i.e. r_p = sum over in-image neighbours q of
+// (u_q - u_p) for an FP32 iterate u.  GB300 executes FP64 at a small fraction
+// of its FP32 rate (one FP64 operation per pixel costs as much as an HBM pass
+// over the frame), so the residual is formed with error-free FP32
+// transformations instead: each difference u_q - u_p is split exactly into
+// s + e by TwoSum (Knuth), and the four pairs are accumulated as a
+// double-single number (hi, lo) with a ~48-bit significand, the accuracy FP64
+// gives here.  Per-block sums of r^2 are written as doubles.
 constexpr int RES_TPB = 256;
 constexpr int RES_ROWS = 4;   // rows per block
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += (s, e), renormalised
+__device__ __forceinline__ void ds_add(float& hi, float& lo, float s, float e) {
+    float t, err;
+    two_sum(hi, s, t, err);
+    const float l = __fadd_rn(lo, __fadd_rn(err, e));
+    hi = __fadd_rn(t, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, t));
+}
 
 template <typename T>
 __global__ void __launch_bounds__(RES_TPB) res64_kernel(Res64Args a) {
@@ -70,44 +93,52 @@ __global__ void __launch_bounds__(RES_TPB) res64_kernel(Res64Args a) {
     const int x = blockIdx.x * RES_TPB + threadIdx.x;
     const int c = blockIdx.z;
     const float* __restrict__ u = a.u + c * a.uplane;
-    double s = 0.0, m = 0.0;
-    const double sinv = a.g_out ? a.scale_inv[c] : 0.0;
+    float s = 0.f, m = 0.f;
+    const float sinv = a.g_out ? (float)a.scale_inv[c] : 0.f;
     if (x < a.W) {
         for (int rr = 0; rr < RES_ROWS; ++rr) {
             const int y = blockIdx.y * RES_ROWS + rr;
             if (y >= a.H) break;
-            double r = 0.0;
+            float r = 0.f;
             if (!a.mask[(size_t)y * a.mp + x]) {
                 const size_t o = (size_t)y * a.up + x;
-                const double uc = u[o];
-                if (y > 0) r += (double)u[o - a.up] - uc;
-                if (y < a.H - 1) r += (double)u[o + a.up] - uc;
-                if (x > 0) r += (double)u[o - 1] - uc;
-                if (x < a.W - 1) r += (double)u[o + 1] - uc;
+                const float uc = u[o];
+                float hi = 0.f, lo = 0.f, d, e;
+                if (y > 0) { two_sum(u[o - a.up], -uc, d, e); ds_add(hi, lo, d, e); }
+                if (y < a.H - 1) { two_sum(u[o + a.up], -uc, d, e); ds_add(hi, lo, d, e); }
+                if (x > 0) { two_sum(u[o - 1], -uc, d, e); ds_add(hi, lo, d, e); }
+                if (x < a.W - 1) { two_sum(u[o + 1], -uc, d, e); ds_add(hi, lo, d, e); }
+                r = __fadd_rn(hi, lo);
             }
-            s = fma(r, r, s);
-            m = fmax(m, fabs(r));
+            s = fmaf(r, r, s);
+            m = fmaxf(m, fabsf(r));
             if (a.g_out) {
                 T* g = static_cast<T*>(a.g_out) + c * a.gplane;
-                g[(size_t)y * a.gp + x] = from_f<T>((float)(r * sinv));
+                g[(size_t)y * a.gp + x] = from_f<T>(r * sinv);
             }
         }
     }
-    // fixed-order block reduction
-    __shared__ double ss[RES_TPB], sm[RES_TPB];
-    ss[threadIdx.x] = s;
-    sm[threadIdx.x] = m;
-    __syncthreads();
-    for (int h = RES_TPB / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            ss[threadIdx.x] += ss[threadIdx.x + h];
-            sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + h]);
-        }
-        __syncthreads();
+    // fixed-order block reduction: warp butterflies, then the 8 warp results
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, k);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, k));
     }
+    __shared__ float ss[RES_TPB / 32], sm[RES_TPB / 32];
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = s;
+        sm[threadIdx.x >> 5] = m;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double ts = 0.0;
+        float tm = 0.f;
+        for (int w = 0; w < RES_TPB / 32; ++w) {
+            ts += (double)ss[w];
+            tm = fmaxf(tm, sm[w]);
+        }
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-        a.part[(size_t)c * a.nblk + blk] = make_double2(ss[0], sm[0]);
+        a.part[(size_t)c * a.nblk + blk] = make_double2(ts, (double)tm);
     }
 }
 
@@ -134,50 +165,6 @@ __global__ void __launch_bounds__(RED_TPB) reduce_part_kernel(const double2* __r
         __syncthreads();
     }
     if (threadIdx.x == 0) out[c] = make_double2(ss[0], sm[0]);
-}
-
-// One block: all channels' sweep partials -> norms2[c], then the stop test.
-// norms2[C + c] keeps the previous sweep's value for the stagnation test.
-__global__ void __launch_bounds__(RED_TPB) reduce_sweep_kernel(const float* __restrict__ partial, int ntiles,
-                                                               int C, double* __restrict__ norms2,
-                                                               const double* __restrict__ ref, double tol,
-                                                               double stall, int* flag, int* conv_at,
-                                                               int sweep_index) {
-    __shared__ double ss[RED_TPB];
-    __shared__ int bad;
-    __shared__ double worst, best_ratio;
-    if (threadIdx.x == 0) { bad = 0; worst = 0.0; best_ratio = 1e300; }
-    if (*flag != 0) return;   // already converged or failed: nothing to do (uniform)
-    for (int c = 0; c < C; ++c) {
-        double s = 0.0;
-        for (int i = threadIdx.x; i < ntiles; i += RED_TPB) s += (double)partial[(size_t)c * ntiles + i];
-        __syncthreads();
-        ss[threadIdx.x] = s;
-        __syncthreads();
-        for (int h = RED_TPB / 2; h > 0; h >>= 1) {
-            if (threadIdx.x < h) ss[threadIdx.x] += ss[threadIdx.x + h];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            const double n2 = ss[0];
-            norms2[c] = n2;
-            if (!isfinite(n2)) bad = 1;
-            const double den = ref[c] > 0.0 ? ref[c] : 1.0;
-            const double rel = sqrt(n2) / den;
-            worst = fmax(worst, rel);
-            if (sweep_index > 0) {
-                const double prev = norms2[C + c];
-                best_ratio = fmin(best_ratio, prev > 0.0 ? sqrt(n2 / prev) : 0.0);
-            }
-            norms2[C + c] = n2;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (bad) { *flag = 2; *conv_at = sweep_index; }
-        else if (worst <= tol) { *flag = 1; *conv_at = sweep_index; }
-        else if (stall > 0.0 && sweep_index > 0 && best_ratio > stall) { *flag = 3; *conv_at = sweep_index; }
-    }
 }
 
 // ---- multilevel ----------------------------------------------------------------------
@@ -299,14 +286,6 @@ cudaError_t launch_res64(const Res64Args& a, cudaStream_t st) {
 
 cudaError_t launch_reduce_part(const double2* part, int nblk, int C, double2* out, cudaStream_t st) {
     reduce_part_kernel<<<C, RED_TPB, 0, st>>>(part, nblk, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reduce_sweep(const float* partial, int ntiles, int C, double* norms2, const double* ref,
-                                double tol, double stall, int* flag, int* conv_at, int sweep_index,
-                                cudaStream_t st) {
-    reduce_sweep_kernel<<<1, RED_TPB, 0, st>>>(partial, ntiles, C, norms2, ref, tol, stall, flag, conv_at,
-                                               sweep_index);
     return cudaGetLastError();
 }
 

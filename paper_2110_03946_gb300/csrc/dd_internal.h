@@ -47,16 +47,35 @@ cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsig
 // is the block tile plus halo of block side b: built once per buffer.
 cudaError_t make_tile_map(CUtensorMap* out, Store st, const void* base, int H, int W, int pitch, int C, int b);
 
+// Residual norms and stop test fused into the sweep.  Each CTA writes its
+// per-channel sum of squared owned residuals of u_in to partial[c * slots + cta];
+// the last CTA to finish sums them in a fixed order into norms2[c] (norms2[C + c]
+// keeps the value for the stagnation test) and sets flag[0]:
+//   1 when max_c sqrt(norms2[c]) / ref[c] <= tol (tol < 0: never),
+//   2 on NaN/Inf, 3 when stall > 0 and every channel's residual fell by less
+//   than the factor 1/stall since the previous launch of the run;
+// flag[1] = sweep_index then.  flag[0] != 0 makes later launches no-ops.
+// flag[2] is set if a bounded wait for a staged tile gave up; flag[3] is the
+// completion ticket (0 between launches).  slots >= the launch grid.
+struct SweepStop {
+    float* partial;
+    int slots;
+    double* norms2;
+    const double* ref;
+    double tol;
+    double stall;
+    int* flag;
+    int sweep_index;
+};
+constexpr int kSweepSlots = 4096;   // per-channel partial slots that cover any persistent grid
+
 // One ORAS sweep over all tiles of all C channels (planes `plane` elements apart).
 //   map_in: TMA descriptor of the input iterate u_in; u_out receives the owned
 //   cores; map_g: optional source g on unknown pixels (solves
-//   A u = C f + (I - C) g with u = f held on known pixels);
-//   partial[c * ntiles + t] = sum over owned pixels of the squared residual of u_in;
-//   skip: optional device flag, nonzero makes the launch a no-op;
-//   err: set to 1 if a bounded wait for a staged tile gave up.
+//   A u = C f + (I - C) g with u = f held on known pixels).
 cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, const CUtensorMap& map_in,
-                         const CUtensorMap* map_g, void* u_out, const uint32_t* tmask, float* partial,
-                         const int* skip, int* err, float p_robin, int k, cudaStream_t stream);
+                         const CUtensorMap* map_g, void* u_out, const uint32_t* tmask, const SweepStop& stop,
+                         float p_robin, int k, cudaStream_t stream);
 
 // ---- auxiliary passes (aux.cu) ----------------------------------------------------
 // dst[c][y][x] (pitch dp) = mask ? src[c][y][x] : 0  (src pitch sp)
@@ -73,8 +92,9 @@ cudaError_t launch_reset_known(int H, int W, int C, float* u, int up, long long 
                                const uint8_t* mask, int mp, const float* f, int fp, long long fplane,
                                cudaStream_t st);
 
-// FP64 residual r = b - A u on unknown pixels (0 on known), per channel
-// sum r^2 and max |r| per block into part[c*nblk + blk] (double2 {sum, max}).
+// Residual r = b - A u of an FP32 iterate on unknown pixels (0 on known),
+// formed with error-free FP32 transformations (~48-bit significand); per
+// channel sum r^2 and max |r| per block into part[c*nblk + blk] (double2).
 // If g_out != nullptr, also writes g_out = r * scale_inv[c] in storage `gst`.
 struct Res64Args {
     int H, W, C;
@@ -89,16 +109,6 @@ cudaError_t launch_res64(const Res64Args& a, cudaStream_t st);
 
 // Reduce per-block partials: out[c] = {sum over blocks, max over blocks}.
 cudaError_t launch_reduce_part(const double2* part, int nblk, int C, double2* out, cudaStream_t st);
-
-// Reduce sweep partials (float, C x ntiles) to norms2[c] (double, 2C entries:
-// current and previous sweep) and test convergence: if max_c sqrt(norms2[c]) /
-// ref[c] <= tol and *flag == 0, set *flag = 1 and *conv_at = sweep_index.
-// *flag = 2 on NaN/Inf; *flag = 3 when stall > 0 and the residual of every
-// channel fell by less than the factor 1/stall in the last sweep (the iterate's
-// storage precision has been reached).  A set flag makes later launches no-ops.
-cudaError_t launch_reduce_sweep(const float* partial, int ntiles, int C, double* norms2,
-                                const double* ref, double tol, double stall, int* flag, int* conv_at,
-                                int sweep_index, cudaStream_t st);
 
 // Dyadic restriction (Sec. 4): mask OR over 2x2, mean of known values.
 cudaError_t launch_restrict(int H, int W, int C, const uint8_t* mask, int mp, const float* f, int fp,

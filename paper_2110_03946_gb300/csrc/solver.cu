@@ -68,7 +68,7 @@ struct Level {
     uint32_t* tmask = nullptr;
     float* u[2] = {nullptr, nullptr};
     CUtensorMap map_u[2];      // TMA descriptors of u[0], u[1]
-    float* partial = nullptr;  // C x ntiles
+    float* partial = nullptr;  // C x kSweepSlots per-CTA residual sums
     double* ref_d = nullptr;   // C
     std::vector<double> ref;   // C
     long long plane() const { return (long long)H * P; }
@@ -95,7 +95,7 @@ struct dd_inpaint {
     int res_nblk = 0;
     double2* res_out = nullptr;     // C
     double* norms2_d = nullptr;     // C
-    int* flag_d = nullptr;          // [0] flag, [1] conv_at, [2] device wait timed out
+    int* flag_d = nullptr;          // [0] stop flag, [1] conv_at, [2] device wait timed out, [3] ticket
     // pinned host mirrors
     double2* h_res = nullptr;
     double* h_small = nullptr;      // 3*C doubles scratch
@@ -244,11 +244,12 @@ int run_sweeps(dd_inpaint* h, const TileGeom& g, Store st_t, void* const bufs[2]
                double tol, double stall, int max_sweeps, cudaStream_t st, int* applied, bool* converged,
                bool fine = false) {
     const long long plane = (long long)g.H * g.pitch;
-    DD_CK(cudaMemsetAsync(h->flag_d, 0, 3 * sizeof(int), st));
+    DD_CK(cudaMemsetAsync(h->flag_d, 0, 4 * sizeof(int), st));
     int done = 0;
     *converged = false;
     const int chunk = dd_inpaint::kChunk;
     const bool timed = fine && h->prm.timing != 0;
+    dd::SweepStop stop{partial, dd::kSweepSlots, h->norms2_d, ref_d, tol, stall, h->flag_d, 0};
     while (true) {
         // the chunk evaluates the stop test of iterates done .. done+n-1 and
         // sweeps them; an iterate past max_sweeps is tested but not swept
@@ -257,19 +258,18 @@ int run_sweeps(dd_inpaint* h, const TileGeom& g, Store st_t, void* const bufs[2]
             const int idx = done + i;
             const CUtensorMap& in = maps[(cur + idx) & 1];
             void* out = bufs[(cur + idx + 1) & 1];
+            stop.sweep_index = idx;
             if (idx < max_sweeps) {
                 if (timed) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
-                DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, in, map_g, out, tmask, partial, h->flag_d,
-                                              h->flag_d + 2, h->prm.robin_p, h->prm.local_cg_iters, st));
+                DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, in, map_g, out, tmask, stop, h->prm.robin_p,
+                                              h->prm.local_cg_iters, st));
                 if (timed) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
             } else {
-                // evaluation only: a sweep whose output goes to the other buffer is
-                // still needed for the fused residual; run it, it is not counted
-                DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, in, map_g, out, tmask, partial, h->flag_d,
-                                              h->flag_d + 2, h->prm.robin_p, 1, st));
+                // evaluation only: the fused residual of this iterate needs a sweep;
+                // its output goes to the other buffer and is not used
+                DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, in, map_g, out, tmask, stop, h->prm.robin_p,
+                                              1, st));
             }
-            DD_LAUNCH(h, dd::launch_reduce_sweep(partial, g.ntiles, h->C, h->norms2_d, ref_d, tol, stall, h->flag_d,
-                                          h->flag_d + 1, idx, st));
         }
         DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DD_CK(cudaStreamSynchronize(st));
@@ -509,7 +509,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         if ((rc = dalloc_t(h, &L.tmask, dd::tmask_words(L.geom))) != DD_OK) return fail(rc);
         for (int b = 0; b < 2; ++b)
             if ((rc = dalloc(h, (void**)&L.u[b], plane_bytes)) != DD_OK) return fail(rc);
-        if ((rc = dalloc_t(h, &L.partial, (size_t)C * L.geom.ntiles)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &L.partial, (size_t)C * dd::kSweepSlots)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &L.ref_d, (size_t)C)) != DD_OK) return fail(rc);
         hh = (hh + 1) / 2; ww = (ww + 1) / 2;
     }
@@ -544,7 +544,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if ((rc = dalloc_t(h, &h->inner_ref_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->scale_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->scale_inv_d, (size_t)C)) != DD_OK) return fail(rc);
-    if ((rc = dalloc_t(h, &h->flag_d, 3)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->flag_d, 4)) != DD_OK) return fail(rc);
     if (cudaMallocHost(&h->h_res, sizeof(double2) * C) != cudaSuccess ||
         cudaMallocHost(&h->h_small, sizeof(double) * 3 * C) != cudaSuccess ||
         cudaMallocHost(&h->h_flag, sizeof(int) * 4) != cudaSuccess) {
@@ -680,11 +680,12 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     if (!h || n < 0) { set_error("bad sweep arguments"); return DD_EINVAL; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Level& F = h->lv[0];
-    DD_CK(cudaMemsetAsync(h->flag_d, 0, 3 * sizeof(int), st));
+    DD_CK(cudaMemsetAsync(h->flag_d, 0, 4 * sizeof(int), st));
+    dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, -1.0, 0.0, h->flag_d, 0};
     for (int i = 0; i < n; ++i) {
+        stop.sweep_index = i;
         DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), F.map_u[h->cur], nullptr, F.u[1 - h->cur],
-                                      F.tmask, F.partial, nullptr, h->flag_d + 2, h->prm.robin_p,
-                                      h->prm.local_cg_iters, st));
+                                      F.tmask, stop, h->prm.robin_p, h->prm.local_cg_iters, st));
         h->cur = 1 - h->cur;
     }
     if (n > 0) {
@@ -694,8 +695,6 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
         if (err != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
     }
     if (rnorm_out != nullptr && n > 0) {
-        DD_LAUNCH(h, dd::launch_reduce_sweep(F.partial, F.geom.ntiles, h->C, h->norms2_d, F.ref_d, -1.0, 0.0,
-                                      h->flag_d, h->flag_d + 1, 0, st));
         std::vector<double> tmp(h->C);
         DD_CK(cudaMemcpyAsync(tmp.data(), h->norms2_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
         DD_CK(cudaStreamSynchronize(st));

@@ -36,7 +36,7 @@ namespace {
 constexpr long long kMaxIterElems = 1LL << 22;   // C * H * pitch of one iterate buffer
 constexpr long long kMaxTiles = 16384;           // blocks per channel
 constexpr long long kMaxTileWords = kMaxTiles * 2 * 128;   // block masks (up to 128 threads per block)
-constexpr long long kMaxTileWork = 65536;        // C * blocks (residual partials)
+constexpr long long kMaxPartials = (long long)DD_MAX_STAT_CHANNELS * dd::kSweepSlots;   // per-CTA residual sums
 constexpr long long kMaxResBlocks = 65536;       // C * blocks of the FP64 residual pass
 constexpr int kMaxChannels = DD_MAX_STAT_CHANNELS;
 
@@ -45,7 +45,7 @@ constexpr size_t kOffU0 = 0;
 constexpr size_t kOffU1 = kOffU0 + align256(kMaxIterElems * 4);
 constexpr size_t kOffTmask = kOffU1 + align256(kMaxIterElems * 4);
 constexpr size_t kOffPartial = kOffTmask + align256(kMaxTileWords * 4);
-constexpr size_t kOffResPart = kOffPartial + align256(kMaxTileWork * 4);
+constexpr size_t kOffResPart = kOffPartial + align256(kMaxPartials * 4);
 constexpr size_t kOffResOut = kOffResPart + align256(kMaxResBlocks * 16);
 constexpr size_t kOffNorms = kOffResOut + align256(kMaxChannels * 16);
 constexpr size_t kOffRef = kOffNorms + align256(2 * kMaxChannels * 8);
@@ -125,10 +125,10 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     const long long elems = (long long)C * H * P;
     const dd::TileGeom g = dd::make_geom(H, W, P, p.block, p.overlap);
     const int nblk = dd::res64_blocks(H, W);
-    if (elems > kMaxIterElems || g.ntiles > kMaxTiles || (long long)g.ntiles * C > kMaxTileWork ||
-        (long long)nblk * C > kMaxResBlocks || (long long)dd::tmask_words(g) > kMaxTileWords)
-        return fail(DD_EINVAL, "image exceeds the static scratch capacity: C*H*roundup(W,32) <= 4194304, "
-                               "at most 16384 blocks per channel and 65536 blocks over all channels");
+    if (elems > kMaxIterElems || g.ntiles > kMaxTiles || (long long)nblk * C > kMaxResBlocks ||
+        (long long)dd::tmask_words(g) > kMaxTileWords)
+        return fail(DD_EINVAL, "image exceeds the static scratch capacity: C*H*roundup(W,32) <= 4194304 and "
+                               "at most 16384 blocks per channel");
     const float pr = p.robin_p > 0.f ? p.robin_p : dd::default_robin(p.block, p.overlap);
 
     unsigned char* base = nullptr;
@@ -177,6 +177,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     bool converged = false;
     for (int attempt = 0; attempt < 4 && !converged; ++attempt) {
         SS_CK(cudaMemsetAsync(flag, 0, 4 * sizeof(int), st));
+        dd::SweepStop stop{partial, dd::kSweepSlots, norms2, ref_d, target, 0.0, flag, 0};
         const int start = done;
         int hflag[3] = {0, 0, 0};
         while (true) {
@@ -184,10 +185,9 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
             for (int i = 0; i < n; ++i) {
                 const int idx = done + i;
                 const int k = idx < p.max_sweeps ? p.local_cg_iters : 1;
+                stop.sweep_index = idx - start;
                 SS_CK(dd::launch_sweep(dd::Store::F32, g, C, plane, maps[(cur + idx - start) & 1], nullptr,
-                                       u[(cur + idx - start + 1) & 1], tmask, partial, flag, flag + 2, pr, k, st));
-                SS_CK(dd::launch_reduce_sweep(partial, g.ntiles, C, norms2, ref_d, target, 0.0, flag, flag + 1,
-                                              idx - start, st));
+                                       u[(cur + idx - start + 1) & 1], tmask, stop, pr, k, st));
             }
             SS_CK(cudaMemcpyAsync(hflag, flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
             SS_CK(cudaStreamSynchronize(st));

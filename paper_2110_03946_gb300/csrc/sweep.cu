@@ -133,9 +133,7 @@ template <typename T>
 struct SweepArgs {
     T* u_out;
     const uint32_t* tmask;
-    float* partial;
-    const int* skip;
-    int* err;
+    SweepStop stop;
     int H, W, pitch, C;
     int s, ntx, ntiles;
     int has_g;
@@ -175,7 +173,8 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
     __shared__ float red3[2][2][NW];   // CG reductions (p,Ap) and (r,r), alternating by step parity
     __shared__ float xch[2][NW][BW];
 
-    if (a.skip != nullptr && *a.skip != 0) return;   // uniform over the grid
+    int* const flag = a.stop.flag;                  // [0] stop/skip, [1] conv_at, [2] err, [3] ticket
+    if (flag[0] != 0) return;                        // converged or failed earlier: uniform no-op
     const long long total = (long long)a.ntiles * a.C;
     long long t = blockIdx.x;
     if (t >= total) return;
@@ -216,6 +215,10 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
 
     const float pr = a.p_robin;
     const float fW = lx > 0 ? 1.f : 0.f, fE = lx < LX - 1 ? 1.f : 0.f;
+    float* const part = a.stop.partial;
+    const int slots = a.stop.slots;
+    int cur_c = -1;        // channel whose owned residual sum is being accumulated
+    float acc_c = 0.f;
     int it = 0;
     for (; t < total; t += gridDim.x, ++it) {
         const int buf = it & 1;
@@ -234,7 +237,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
         if (tt == 0) {
             const bool ok = mbar_wait_bounded(&mbar[buf], parity);
             s_ok = ok ? 1 : 0;
-            if (!ok) atomicExch(a.err, 1);
+            if (!ok) atomicExch(flag + 2, 1);
         }
         __syncthreads();
         if (!s_ok) break;                               // uniform
@@ -277,7 +280,15 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
                 }
         }
         s2 = tile_sum<CF>(s2, red[0], wt, lane);
-        if (a.partial != nullptr && tt == 0) a.partial[t] = s2;
+        if (c != cur_c) {   // tiles of one CTA visit channels in increasing order
+            if (tt == 0) {
+                if (cur_c >= 0) part[(size_t)cur_c * slots + blockIdx.x] = acc_c;
+                for (int cc = cur_c + 1; cc < c; ++cc) part[(size_t)cc * slots + blockIdx.x] = 0.f;
+            }
+            cur_c = c;
+            acc_c = 0.f;
+        }
+        acc_c += s2;
 
         // ---- local operator coefficients -----------------------------------------
         float2 rpn[PY];     // -(vertical part of dd), both halves equal
@@ -436,6 +447,49 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
         // a copy timed out: wait (bounded) for the other buffer's copy before leaving
         mbar_wait_bounded(&mbar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
     }
+
+    // ---- per-channel residual norms of u^n and the stop test (last CTA) -----------
+    if (tt == 0) {
+        if (cur_c >= 0) part[(size_t)cur_c * slots + blockIdx.x] = acc_c;
+        for (int cc = cur_c + 1; cc < a.C; ++cc) part[(size_t)cc * slots + blockIdx.x] = 0.f;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int s_last;
+    if (tt == 0) s_last = atomicAdd(flag + 3, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (s_last && wt == 0) {
+        __threadfence();
+        const SweepStop& sp = a.stop;
+        double worst = 0.0, best_ratio = 1e300;
+        int bad = 0;
+        for (int c = 0; c < a.C; ++c) {
+            double v = 0.0;
+            for (int i = lane; i < (int)gridDim.x; i += 32) v += (double)__ldcg(part + (size_t)c * slots + i);
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(FULL, v, m);
+            if (lane == 0) {
+                if (!isfinite(v)) bad = 1;
+                const double den = sp.ref[c] > 0.0 ? sp.ref[c] : 1.0;
+                worst = fmax(worst, sqrt(v) / den);
+                if (sp.sweep_index > 0) {
+                    const double prev = sp.norms2[a.C + c];
+                    best_ratio = fmin(best_ratio, prev > 0.0 ? sqrt(v / prev) : 0.0);
+                }
+                sp.norms2[c] = v;
+                sp.norms2[a.C + c] = v;
+            }
+        }
+        if (lane == 0) {
+            if (bad) { flag[0] = 2; flag[1] = sp.sweep_index; }
+            else if (worst <= sp.tol) { flag[0] = 1; flag[1] = sp.sweep_index; }
+            else if (sp.stall > 0.0 && sp.sweep_index > 0 && best_ratio > sp.stall) {
+                flag[0] = 3;
+                flag[1] = sp.sweep_index;
+            }
+            flag[3] = 0;   // ticket ready for the next launch
+        }
+    }
 }
 
 template <class CF>
@@ -505,14 +559,12 @@ int persistent_grid(bool has_g) {
 
 template <class CF, typename T>
 cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const CUtensorMap& mu, const CUtensorMap* mg,
-                      void* u_out, const uint32_t* tmask, float* partial, const int* skip, int* err,
-                      float p_robin, int k, cudaStream_t st) {
+                      void* u_out, const uint32_t* tmask, const SweepStop& stop, float p_robin, int k,
+                      cudaStream_t st) {
     SweepArgs<T> a;
     a.u_out = static_cast<T*>(u_out);
     a.tmask = tmask;
-    a.partial = partial;
-    a.skip = skip;
-    a.err = err;
+    a.stop = stop;
     a.H = g.H; a.W = g.W; a.pitch = g.pitch; a.C = C;
     a.s = g.s; a.ntx = g.ntx; a.ntiles = g.ntiles;
     a.has_g = mg != nullptr;
@@ -520,7 +572,8 @@ cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const CUtensorM
     a.p_robin = p_robin;
     a.k = k;
     const long long work = (long long)g.ntiles * C;
-    const long long grid = std::min<long long>(work, persistent_grid<CF, T>(a.has_g));
+    const long long grid = std::min<long long>(std::min<long long>(work, persistent_grid<CF, T>(a.has_g)),
+                                               (long long)stop.slots);
     const size_t smem = sweep_smem_bytes<CF, T>(a.has_g);
     oras_sweep_kernel<CF, T><<<(unsigned)grid, CF::NT, smem, st>>>(mu, mg ? *mg : mu, a);
     return cudaGetLastError();
@@ -528,15 +581,15 @@ cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const CUtensorM
 
 template <class CF>
 cudaError_t sweep_store(Store s, const TileGeom& g, int C, long long plane, const CUtensorMap& mu,
-                        const CUtensorMap* mg, void* u_out, const uint32_t* tmask, float* partial, const int* skip,
-                        int* err, float p_robin, int k, cudaStream_t st) {
+                        const CUtensorMap* mg, void* u_out, const uint32_t* tmask, const SweepStop& stop,
+                        float p_robin, int k, cudaStream_t st) {
     switch (s) {
         case Store::F32:
-            return sweep_cfg<CF, float>(g, C, plane, mu, mg, u_out, tmask, partial, skip, err, p_robin, k, st);
+            return sweep_cfg<CF, float>(g, C, plane, mu, mg, u_out, tmask, stop, p_robin, k, st);
         case Store::F16:
-            return sweep_cfg<CF, __half>(g, C, plane, mu, mg, u_out, tmask, partial, skip, err, p_robin, k, st);
+            return sweep_cfg<CF, __half>(g, C, plane, mu, mg, u_out, tmask, stop, p_robin, k, st);
         case Store::BF16:
-            return sweep_cfg<CF, __nv_bfloat16>(g, C, plane, mu, mg, u_out, tmask, partial, skip, err, p_robin, k, st);
+            return sweep_cfg<CF, __nv_bfloat16>(g, C, plane, mu, mg, u_out, tmask, stop, p_robin, k, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -662,12 +715,15 @@ cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsig
 }
 
 cudaError_t launch_sweep(Store s, const TileGeom& g, int C, long long plane, const CUtensorMap& map_in,
-                         const CUtensorMap* map_g, void* u_out, const uint32_t* tmask, float* partial,
-                         const int* skip, int* err, float p_robin, int k, cudaStream_t st) {
+                         const CUtensorMap* map_g, void* u_out, const uint32_t* tmask, const SweepStop& stop,
+                         float p_robin, int k, cudaStream_t st) {
+    if (stop.slots < 1 || stop.partial == nullptr || stop.flag == nullptr || stop.norms2 == nullptr ||
+        stop.ref == nullptr)
+        return cudaErrorInvalidValue;
     switch (g.b) {
-        case 16: return sweep_store<Cfg16>(s, g, C, plane, map_in, map_g, u_out, tmask, partial, skip, err, p_robin, k, st);
-        case 32: return sweep_store<Cfg32>(s, g, C, plane, map_in, map_g, u_out, tmask, partial, skip, err, p_robin, k, st);
-        case 64: return sweep_store<Cfg64>(s, g, C, plane, map_in, map_g, u_out, tmask, partial, skip, err, p_robin, k, st);
+        case 16: return sweep_store<Cfg16>(s, g, C, plane, map_in, map_g, u_out, tmask, stop, p_robin, k, st);
+        case 32: return sweep_store<Cfg32>(s, g, C, plane, map_in, map_g, u_out, tmask, stop, p_robin, k, st);
+        case 64: return sweep_store<Cfg64>(s, g, C, plane, map_in, map_g, u_out, tmask, stop, p_robin, k, st);
     }
     return cudaErrorInvalidValue;
 }

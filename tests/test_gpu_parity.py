@@ -78,8 +78,8 @@ def test_residual_norms_match_oracle():
     B.check(rc, "residual")
     exp = ref.residual_norms(u.astype(np.float64), f, m)
     exp0 = ref.residual_norms(ref.initial_guess(f, m), f, m)
-    assert np.allclose(norms, exp, rtol=1e-12)
-    assert np.allclose(refs, exp0, rtol=1e-12)
+    assert np.allclose(norms, exp, rtol=1e-5)          # FP32 sums of r^2 per block
+    assert np.allclose(refs, exp0, rtol=1e-5)
 
 
 SWEEP_CASES = [
@@ -143,7 +143,7 @@ def test_solve_matches_oracle(name, H, W, C, params):
     assert st["converged"]
     assert err <= TOL_U
     assert np.all(rel <= tol)
-    assert np.allclose(st["rel_residual"][:C], rel, rtol=1e-6, atol=1e-12)
+    assert np.allclose(st["rel_residual"][:C], rel, rtol=1e-5, atol=1e-12)
     assert np.array_equal(u[:, m != 0], f[:, m != 0].astype(np.float32))
 
 
