@@ -45,15 +45,41 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=3, help="distinct frames resident in HBM")
-    ap.add_argument("--precision", default="fp32_ref")
-    ap.add_argument("--levels", type=int, default=3)
-    ap.add_argument("--block", type=int, default=32)
-    ap.add_argument("--overlap", type=int, default=6)
-    ap.add_argument("--k", type=int, default=16, help="local CG steps per sweep")
-    ap.add_argument("--robin", type=float, default=0.0)
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--levels", type=int, default=None)
+    ap.add_argument("--block", type=int, default=None)
+    ap.add_argument("--overlap", type=int, default=None)
+    ap.add_argument("--k", type=int, default=None, help="local CG steps per sweep")
+    ap.add_argument("--robin", type=float, default=None)
+    ap.add_argument("--coarse-tol", type=float, default=None)
+    ap.add_argument("--no-tuned", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP16-storage measurement")
     return ap.parse_args()
+
+
+PAPER_DEFAULTS = {"block": 32, "overlap": 6, "local_cg_iters": 16, "robin_p": 0.0, "levels": 3, "coarse_tol": 1e-2}
+
+
+def solver_params(args, precision):
+    """Autotuned parameters for the workload (if cached), then command-line overrides."""
+    import synth
+    from paper_2110_03946_gb300 import autotune
+    w = synth.WORKLOADS[WORKLOAD]
+    prm = dict(PAPER_DEFAULTS)
+    src = "defaults (block 32, overlap 6 as in the paper)"
+    if not args.no_tuned:
+        t = autotune.lookup(w.H, w.W, w.C, w.density, precision, TOL)
+        if t:
+            prm.update(t)
+            src = "autotuned (paper_2110_03946_gb300/tuned.json)"
+    for key, val in [("block", args.block), ("overlap", args.overlap), ("local_cg_iters", args.k),
+                     ("robin_p", args.robin), ("levels", args.levels), ("coarse_tol", args.coarse_tol)]:
+        if val is not None:
+            prm[key] = val
+            src += f"; {key} overridden"
+    return prm, src
 
 
 def dist_env():
@@ -227,10 +253,8 @@ def run_ours(args):
     C, H, W = frames[0][0].shape
     dmask = [torch.as_tensor(m).to(dev) for _, m in frames]
     dvals = [torch.as_tensor(f).to(dev) for f, _ in frames]
-    prm = dict(block=args.block, overlap=args.overlap, local_cg_iters=args.k, levels=args.levels,
-               precision=args.precision, timing=1)
-    if args.robin > 0:
-        prm["robin_p"] = args.robin
+    tuned, tuned_src = solver_params(args, args.precision)
+    prm = dict(tuned, precision=args.precision, timing=1)
     ip = Inpainter(dmask[0], dvals[0], device=dev, **prm)
     out = torch.empty((C, H, W), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -286,15 +310,8 @@ def run_ours(args):
     pm = [torch.as_tensor(m).pin_memory() for _, m in frames]
     pv = [torch.as_tensor(f).pin_memory() for f, _ in frames]
     hout = torch.empty((C, H, W), dtype=torch.float32).pin_memory()
-    p = B.dd_params_default()
-    for key, val in [("block", args.block), ("overlap", args.overlap), ("local_cg_iters", args.k),
-                     ("levels", args.levels)]:
-        setattr(p, key, val)
-    from paper_2110_03946_gb300.inpaint import PRECISIONS
-    p.precision = PRECISIONS[args.precision]
-    if args.robin > 0:
-        p.robin_p = args.robin
-    p.inputs_on_device = 0
+    from paper_2110_03946_gb300.inpaint import make_params
+    p = make_params(precision=args.precision, inputs_on_device=0, **tuned)
     rc, h2 = B.dd_inpaint_create(H, W, C, pm[0].data_ptr(), pv[0].data_ptr(), p)
     B.check(rc, "create(host)")
     dout = torch.empty((C, H, W), dtype=torch.float32, device=dev)
@@ -326,7 +343,8 @@ def run_ours(args):
     # ---- plain FP32 single-level single-frame ORAS on the same frames ----------
     plain = None
     if not args.no_plain:
-        pp = dict(block=args.block, overlap=args.overlap, local_cg_iters=args.k, levels=1, precision="fp32")
+        pp = dict(PAPER_DEFAULTS, levels=1)
+        pp["precision"] = "fp32"
         with Inpainter(dmask[0], dvals[0], device=dev, **pp) as ipp:
             def pstep(i):
                 j = i % args.frames
@@ -348,6 +366,31 @@ def run_ours(args):
                      "fine_sweeps_last": pst["sweeps_per_level"][0],
                      "rel_residual_last": max(pst["rel_residual"][:C]), "converged_last": pst["converged"]}
 
+    # ---- FP16-storage inner solves with the outer residual correction ----------
+    mixed = None
+    if not args.no_mixed and args.precision == "fp32":
+        mp_, msrc = solver_params(args, "fp16_ref")
+        with Inpainter(dmask[0], dvals[0], device=dev, precision="fp16_ref", **mp_) as ipm:
+            def mstep(i):
+                j = i % args.frames
+                B.check(B.dd_inpaint_set_data(ipm._h, dmask[j].data_ptr(), dvals[j].data_ptr(), 0), "set_data")
+                B.check(B.dd_inpaint_solve(ipm._h, out.data_ptr(), TOL, stream), "solve")
+            for i in range(args.warmup):
+                mstep(i)
+            torch.cuda.synchronize(dev)
+            m0e = torch.cuda.Event(enable_timing=True)
+            m1e = torch.cuda.Event(enable_timing=True)
+            m0e.record(stream)
+            for i in range(args.steps):
+                mstep(args.warmup + i)
+            m1e.record(stream)
+            torch.cuda.synchronize(dev)
+            mst = ipm.stats()
+            mixed = {"value": args.steps / (m0e.elapsed_time(m1e) / 1e3), "unit": UNIT,
+                     "config": "FP16 inner iterate + outer residual correction, " + msrc,
+                     "corrections_last": mst["corrections"], "fine_sweeps_last": mst["sweeps_per_level"][0],
+                     "rel_residual_last": max(mst["rel_residual"][:C])}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -359,7 +402,8 @@ def run_ours(args):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FP32 FMA at max clock
-    flops = sweep_flops(st["local_unknowns"], C, args.k)
+    k_used = prm["local_cg_iters"]
+    flops = sweep_flops(st["local_unknowns"], C, k_used)
     achieved = flops / avg_sweep_s / 1e12 if avg_sweep_s else None
     sbytes = 4 if args.precision in ("fp32", "fp32_ref") else 2
     hbm_alg = sweep_hbm_bytes(H, W, C, sbytes, args.precision != "fp32")
@@ -390,8 +434,9 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded smooth RGB fields, 3% edge-clustered masks; the paper's photo is unavailable)",
         "config": {"workload": "rgb4k_edge3: 3840x2160x3, 3% edge-clustered mask, rel-res 1e-6",
-                   "block": args.block, "overlap": args.overlap, "local_cg_iters": args.k,
-                   "levels": args.levels, "precision": args.precision, "frames_resident": args.frames,
+                   "block": prm["block"], "overlap": prm["overlap"], "local_cg_iters": prm["local_cg_iters"],
+                   "levels": prm["levels"], "robin_p": prm["robin_p"], "coarse_tol": prm["coarse_tol"],
+                   "params_source": tuned_src, "precision": args.precision, "frames_resident": args.frames,
                    "l2": "inputs larger than L2 (each frame's working set ~0.5 GB, frames cycled)",
                    "parallelism": f"replicas x{world}"},
         "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))],
@@ -403,6 +448,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "plain_fp32_oras": plain,
+        "mixed_fp16_oras": mixed,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -1,0 +1,169 @@
+"""Autotuner for the ORAS solver parameters.
+
+Searches block side, overlap, local CG steps, Robin weight, number of levels
+and coarse tolerance for the smallest device time to a relative residual
+``tol`` on sample frames: for every block side a coordinate descent (one
+parameter at a time over its candidates, repeated while something improves and
+time is left), keeping the best result over block sides.  Every trial
+runs through the C ABI; a trial counts only if its solve converged.  Results
+are cached in a JSON file keyed by frame shape, mask density (1 % buckets),
+precision and tolerance.
+
+python -m paper_2110_03946_gb300.autotune --workload rgb4k_edge3 --out tuned.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .inpaint import PRECISIONS, make_params
+
+SPACE = {
+    "block": [16, 32, 64],
+    "overlap": [1, 2, 3, 4, 5, 6, 8],
+    "local_cg_iters": [8, 10, 12, 14, 16, 18, 20, 24],
+    "robin_p": [0.0, 0.1, 0.15, 0.2, 0.3, 0.5, 1.0],   # 0.0 = library default
+    "levels": [1, 2, 3, 4, 5, 6],
+    "coarse_tol": [1e-1, 1e-2, 3e-3, 1e-3, 3e-4],
+}
+START = {"block": 32, "overlap": 6, "local_cg_iters": 16, "robin_p": 0.0, "levels": 3, "coarse_tol": 1e-2}
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
+def cache_key(H: int, W: int, C: int, density: float, precision: str, tol: float) -> str:
+    return f"{H}x{W}x{C}|d{int(round(density * 100))}|{precision}|tol{tol:g}"
+
+
+def load_cache(path: str = DEFAULT_CACHE) -> dict:
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def lookup(H, W, C, density, precision, tol, path: str = DEFAULT_CACHE):
+    """Tuned parameters for this shape/density/precision, or None."""
+    ent = load_cache(path).get(cache_key(H, W, C, density, precision, tol))
+    return dict(ent["params"]) if ent else None
+
+
+class _Trial:
+    """Solves the sample frames with one parameter set; device ms per frame."""
+
+    def __init__(self, frames, precision, tol, reps=1):
+        self.frames = frames
+        self.precision = precision
+        self.tol = tol
+        self.reps = reps
+        C, H, W = frames[0][1].shape
+        self.out = torch.empty((C, H, W), dtype=torch.float32, device=frames[0][1].device)
+
+    def __call__(self, prm: dict) -> float:
+        m0, v0 = self.frames[0]
+        C, H, W = v0.shape
+        p = make_params(precision=self.precision, **prm)
+        rc, h = B.dd_inpaint_create(H, W, C, m0.data_ptr(), v0.data_ptr(), p)
+        if rc != B.DD_OK:
+            return float("inf")
+        try:
+            stream = torch.cuda.current_stream(v0.device)
+            total, n = 0.0, 0
+            for rep in range(self.reps + 1):           # the first pass warms up
+                for m, v in self.frames:
+                    if B.dd_inpaint_set_data(h, m.data_ptr(), v.data_ptr(), 0) != B.DD_OK:
+                        return float("inf")
+                    if B.dd_inpaint_solve(h, self.out.data_ptr(), self.tol, stream) != B.DD_OK:
+                        return float("inf")
+                    rc, st = B.dd_inpaint_stats(h)
+                    if rep > 0:
+                        total += st.ms_total
+                        n += 1
+            return total / max(n, 1)
+        finally:
+            B.dd_inpaint_destroy(h)
+
+
+def autotune(frames, precision: str = "fp32", tol: float = 1e-6, budget_s: float = 60.0,
+             space: dict | None = None, start: dict | None = None, log=None):
+    """Block-major coordinate descent: for every block side, descend over the
+    other parameters from the start point; keep the best overall.
+    frames: list of (mask uint8 (H,W), values f32 (C,H,W)) CUDA tensors.
+    Returns (best_params, best_ms, trials)."""
+    space = dict(space or SPACE)
+    blocks = space.pop("block", [32])
+    trial = _Trial(frames, precision, tol)
+    seen = {}
+    t0 = time.time()
+    best, best_ms = None, float("inf")
+    for b in blocks:
+        per = max(1.0, (budget_s - (time.time() - t0)) / max(1, len(blocks) - blocks.index(b)))
+        cand, ms = _descend(trial, seen, dict(start or START, block=b), space, per, log)
+        if ms < best_ms:
+            best, best_ms = cand, ms
+    return best, best_ms, seen
+
+
+def _descend(trial, seen, best, space, budget_s, log):
+
+    def score(prm):
+        key = json.dumps(prm, sort_keys=True)
+        if key not in seen:
+            if prm["overlap"] >= prm["block"]:
+                seen[key] = float("inf")
+            else:
+                seen[key] = trial(prm)
+                if log:
+                    log(f"{seen[key]:9.3f} ms  {prm}")
+        return seen[key]
+
+    best_ms = score(best)
+    t0 = time.time()
+    improved = True
+    while improved and time.time() - t0 < budget_s:
+        improved = False
+        for name, values in space.items():
+            for v in values:
+                if time.time() - t0 >= budget_s:
+                    break
+                cand = dict(best, **{name: v})
+                ms = score(cand)
+                if ms < best_ms * 0.99:
+                    best, best_ms, improved = cand, ms, True
+    return best, best_ms
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="rgb4k_edge3")
+    ap.add_argument("--frames", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--budget", type=float, default=120.0, help="seconds")
+    ap.add_argument("--out", default=DEFAULT_CACHE)
+    a = ap.parse_args()
+    import synth
+    w = synth.WORKLOADS[a.workload]
+    dev = torch.device("cuda", 0)
+    frames = []
+    for j in range(a.frames):
+        f, m = synth.make_frame(w.H, w.W, w.C, w.density, w.pattern, w.seed_base + 50 + j)
+        frames.append((torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev)))
+    best, ms, seen = autotune(frames, a.precision, a.tol, a.budget, log=lambda s: print(s, flush=True))
+    cache = load_cache(a.out)
+    cache[cache_key(w.H, w.W, w.C, w.density, a.precision, a.tol)] = {
+        "params": best, "ms_per_frame": ms, "trials": len(seen), "workload": a.workload,
+        "sample_seeds": [w.seed_base + 50 + j for j in range(a.frames)]}
+    with open(a.out, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    print(json.dumps({"best": best, "ms_per_frame": ms, "trials": len(seen)}))
+
+
+if __name__ == "__main__":
+    main()
