@@ -78,7 +78,8 @@ typedef struct dd_params {
     double coarse_tol;       /* relative residual that ends a coarse level (default 1e-2) */
     double inner_tol;        /* relative residual decrease per outer correction (default 3e-3) */
     int    max_corrections;  /* outer FP64 corrections limit (default 30) */
-    int    coarse_sweeps;    /* sweep limit per coarse level (default 40) */
+    int    coarse_sweeps;    /* sweeps launched per coarse level (default 12); launches after the
+                                coarse tolerance is met do no work */
     int    timing;           /* 1: time every fine-level sweep launch with CUDA events (dd_stats) */
 } dd_params;
 
@@ -141,7 +142,8 @@ int dd_inpaint_destroy(dd_handle h);
  * Replace mask and values (same H, W, C; pointers as in create).  With
  * keep_iterate = 1 the current fine iterate is kept as the next solve's
  * starting point (known pixels reset to the new values): warm start for
- * video.  Synchronous.  Errors: DD_EINVAL, DD_EEMPTYMASK, DD_ECUDA.
+ * video.  Synchronous.  Errors: DD_EINVAL, DD_EEMPTYMASK, DD_ECUDA; after an
+ * error the handle needs a successful set_data before the next solve.
  */
 int dd_inpaint_set_data(dd_handle h, const uint8_t *mask, const float *values, int keep_iterate);
 

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cfloat>
 
 #include "dd_internal.h"
@@ -225,6 +226,66 @@ __global__ void correct_kernel(int H, int W, float* __restrict__ u, int up, long
     *pu = (float)v;
 }
 
+__global__ void count_nonzero_kernel(const uint8_t* __restrict__ m, long long n,
+                                     unsigned long long* __restrict__ out) {
+    unsigned v = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v += m[i] != 0;
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) v += __shfl_xor_sync(0xffffffffu, v, k);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, (unsigned long long)v);
+}
+
+// ---- device-side control of a sweep sequence ------------------------------------------
+// After n sweep launches that started from buffer 0 under the stop flag:
+// state = {buffer holding the result, sweeps applied, flag value}.
+__global__ void resolve_kernel(const int* __restrict__ flag, int n, int* __restrict__ state) {
+    const int f = flag[0];
+    const int applied = (f == 1 || f == 3) ? flag[1] : n;
+    state[0] = applied & 1;
+    state[1] = applied;
+    state[2] = f;
+}
+
+__global__ void prolong_sel_kernel(int Hc, int Wc, int H, int W, const float* __restrict__ uc0,
+                                   const float* __restrict__ uc1, const int* __restrict__ sel, int ucp,
+                                   long long ucplane, const uint8_t* __restrict__ mask, int mp,
+                                   const float* __restrict__ f, int fp, long long fplane, float* __restrict__ u,
+                                   int up, long long uplane) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
+    if (x >= W || y >= H) return;
+    const float* __restrict__ uc = sel[0] ? uc1 : uc0;
+    float out;
+    if (mask[(size_t)y * mp + x]) {
+        out = f[c * fplane + (size_t)y * fp + x];
+    } else {
+        const float ty = fminf(fmaxf((y - 0.5f) * 0.5f, 0.f), (float)(Hc - 1));
+        const float tx = fminf(fmaxf((x - 0.5f) * 0.5f, 0.f), (float)(Wc - 1));
+        const int y0 = (int)floorf(ty), x0 = (int)floorf(tx);
+        const int y1 = min(y0 + 1, Hc - 1), x1 = min(x0 + 1, Wc - 1);
+        const float wy = ty - (float)y0, wx = tx - (float)x0;
+        const float* p = uc + c * ucplane;
+        const float top = p[(size_t)y0 * ucp + x0] * (1.f - wx) + p[(size_t)y0 * ucp + x1] * wx;
+        const float bot = p[(size_t)y1 * ucp + x0] * (1.f - wx) + p[(size_t)y1 * ucp + x1] * wx;
+        out = top * (1.f - wy) + bot * wy;
+    }
+    u[c * uplane + (size_t)y * up + x] = out;
+}
+
+__global__ void copy2d_sel_kernel(int H, int W, const float* __restrict__ s0, const float* __restrict__ s1,
+                                  const int* __restrict__ sel, int sp, long long splane, float* __restrict__ dst,
+                                  int dp, long long dplane) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
+    if (x >= W || y >= H) return;
+    const float* __restrict__ src = sel[0] ? s1 : s0;
+    dst[c * dplane + (size_t)y * dp + x] = src[c * splane + (size_t)y * sp + x];
+}
+
+__global__ void sqrt_sums_kernel(const double2* __restrict__ in, double* __restrict__ out, int C) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < C) out[c] = sqrt(in[c].x);
+}
+
 }  // namespace
 
 cudaError_t launch_masked_copy(int H, int W, int C, const float* src, int sp, long long splane,
@@ -323,6 +384,45 @@ cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long upla
                 H, W, u, up, uplane, static_cast<const __nv_bfloat16*>(e), ep, eplane, mask, mp, scale);
             break;
     }
+    return cudaGetLastError();
+}
+
+}  // namespace dd
+
+namespace dd {
+
+cudaError_t launch_resolve(const int* flag, int n, int* state, cudaStream_t st) {
+    resolve_kernel<<<1, 1, 0, st>>>(flag, n, state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_sel(int Hc, int Wc, int H, int W, int C, const float* uc0, const float* uc1,
+                               const int* sel, int ucp, long long ucplane, const uint8_t* mask, int mp,
+                               const float* f, int fp, long long fplane, float* u, int up, long long uplane,
+                               cudaStream_t st) {
+    prolong_sel_kernel<<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(Hc, Wc, H, W, uc0, uc1, sel, ucp, ucplane, mask,
+                                                                 mp, f, fp, fplane, u, up, uplane);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy2d_sel(int H, int W, int C, const float* s0, const float* s1, const int* sel, int sp,
+                              long long splane, float* dst, int dp, long long dplane, cudaStream_t st) {
+    copy2d_sel_kernel<<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(H, W, s0, s1, sel, sp, splane, dst, dp, dplane);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sqrt_sums(const double2* in, double* out, int C, cudaStream_t st) {
+    sqrt_sums_kernel<<<(C + 127) / 128, 128, 0, st>>>(in, out, C);
+    return cudaGetLastError();
+}
+
+}  // namespace dd
+
+namespace dd {
+
+cudaError_t launch_count_nonzero(const uint8_t* m, long long n, unsigned long long* out, cudaStream_t st) {
+    const long long blocks = std::min<long long>((n + 255) / 256, 1216);
+    count_nonzero_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, st>>>(m, n, out);
     return cudaGetLastError();
 }
 

@@ -126,6 +126,22 @@ cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long upla
 cudaError_t launch_convert(int H, int W, int C, const float* src, int sp, long long splane,
                            void* dst, Store dst_t, int dp, long long dplane, cudaStream_t st);
 
+// Device-side control of a sweep sequence of n launches started from buffer 0:
+// state[0] = buffer holding the result, state[1] = sweeps applied,
+// state[2] = the stop flag (0: not stopped, 1: converged, 2: NaN/Inf, 3: stalled).
+cudaError_t launch_resolve(const int* flag, int n, int* state, cudaStream_t st);
+// Prolongation / copy reading the source buffer uc0 or uc1 chosen by *sel on the device.
+cudaError_t launch_prolong_sel(int Hc, int Wc, int H, int W, int C, const float* uc0, const float* uc1,
+                               const int* sel, int ucp, long long ucplane, const uint8_t* mask, int mp,
+                               const float* f, int fp, long long fplane, float* u, int up, long long uplane,
+                               cudaStream_t st);
+cudaError_t launch_copy2d_sel(int H, int W, int C, const float* s0, const float* s1, const int* sel, int sp,
+                              long long splane, float* dst, int dp, long long dplane, cudaStream_t st);
+// *out += number of nonzero bytes of m[0..n)
+cudaError_t launch_count_nonzero(const uint8_t* m, long long n, unsigned long long* out, cudaStream_t st);
+// out[c] = sqrt(in[c].x)
+cudaError_t launch_sqrt_sums(const double2* in, double* out, int C, cudaStream_t st);
+
 // Default Robin weight for block side b and overlap o (the value create uses).
 float default_robin(int b, int o);
 // Record the text returned by dd_last_error() on this thread.

@@ -70,7 +70,8 @@ struct Level {
     CUtensorMap map_u[2];      // TMA descriptors of u[0], u[1]
     float* partial = nullptr;  // C x kSweepSlots per-CTA residual sums
     double* ref_d = nullptr;   // C
-    std::vector<double> ref;   // C
+    std::vector<double> ref;   // C (host copy, read after load_data's single sync)
+    int* state_d = nullptr;    // resolve() output of this level's last sweep sequence
     long long plane() const { return (long long)H * P; }
 };
 
@@ -83,6 +84,7 @@ struct dd_inpaint {
     std::vector<Level> lv;
     int cur = 0;              // buffer of lv[0] holding the fine iterate
     bool warm = false;        // next solve starts from the kept iterate
+    bool valid = false;       // mask/values loaded and not empty
     // correction equation buffers (fine level): e ping-pong and source g
     void* e[2] = {nullptr, nullptr};
     void* g = nullptr;
@@ -100,12 +102,14 @@ struct dd_inpaint {
     double2* h_res = nullptr;
     double* h_small = nullptr;      // 3*C doubles scratch
     int* h_flag = nullptr;
+    int* h_state = nullptr;         // 4 ints per level
     std::vector<void*> allocs;
     size_t bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     static constexpr int kChunk = 8;                 // sweeps per stop-test read-back
-    cudaEvent_t sw_ev[2 * kChunk] = {};              // per-sweep timing events (params.timing)
-    unsigned long long* count_d = nullptr;           // unknown-pixel counter
+    static constexpr int kFirst = 16;                // fine sweeps enqueued before the first read-back
+    cudaEvent_t sw_ev[2 * kFirst] = {};              // per-sweep timing events (params.timing)
+    unsigned long long* count_d = nullptr;           // [0] unknown block pixels, [1] known pixels
     long long launches = 0;                          // kernels launched through this handle
     long long local_unknowns = 0;
     dd_stats stats{};
@@ -165,43 +169,38 @@ float robin_default(int b, int o) {
     return (float)(3.0 * std::pow(2.0, -1.0 / 3.0) * std::pow(kmin, 2.0 / 3.0) * std::pow(L, -1.0 / 3.0));
 }
 
-// Copy caller data (mask, values) into level 0 and rebuild all levels.
+// Copy caller data (mask, values) into level 0 and rebuild all levels.  All
+// work is enqueued on st; the only host synchronisation reads back the pixel
+// counts and reference norms once at the end.  Returns DD_EEMPTYMASK if no
+// pixel is known.
 int load_data(dd_inpaint* h, const uint8_t* mask, const float* values, cudaStream_t st) {
     Level& L0 = h->lv[0];
     const size_t npx = (size_t)h->H * h->W;
-    const uint8_t* dmask = mask;
     const float* dvals = values;
-    float* tmp_vals = nullptr;
     if (!h->prm.inputs_on_device) {
         DD_CK(cudaMemcpyAsync(L0.mask, mask, npx, cudaMemcpyHostToDevice, st));
-        dmask = L0.mask;
         // values staged through u[1] as a dense C x H x W array (it has room: P >= W)
-        tmp_vals = L0.u[1];
-        DD_CK(cudaMemcpyAsync(tmp_vals, values, npx * h->C * sizeof(float), cudaMemcpyHostToDevice, st));
-        dvals = tmp_vals;
+        DD_CK(cudaMemcpyAsync(L0.u[1], values, npx * h->C * sizeof(float), cudaMemcpyHostToDevice, st));
+        dvals = L0.u[1];
     } else {
         DD_CK(cudaMemcpyAsync(L0.mask, mask, npx, cudaMemcpyDeviceToDevice, st));
-        dmask = L0.mask;
     }
-    DD_LAUNCH(h, dd::launch_masked_copy(h->H, h->W, h->C, dvals, h->W, (long long)npx, dmask, h->W, L0.f, L0.P,
-                                 L0.plane(), st));
+    DD_LAUNCH(h, dd::launch_masked_copy(h->H, h->W, h->C, dvals, h->W, (long long)npx, L0.mask, h->W, L0.f, L0.P,
+                                        L0.plane(), st));
     for (size_t l = 1; l < h->lv.size(); ++l) {
         Level& F = h->lv[l - 1];
         Level& Cc = h->lv[l];
-        DD_LAUNCH(h, dd::launch_restrict(F.H, F.W, h->C, F.mask, F.W, F.f, F.P, F.plane(), Cc.mask, Cc.W, Cc.f, Cc.P,
-                                  Cc.plane(), st));
+        DD_LAUNCH(h, dd::launch_restrict(F.H, F.W, h->C, F.mask, F.W, F.f, F.P, F.plane(), Cc.mask, Cc.W, Cc.f,
+                                         Cc.P, Cc.plane(), st));
     }
     for (auto& L : h->lv) DD_LAUNCH(h, dd::launch_build_tmask(L.geom, L.mask, L.W, L.tmask, st));
-    DD_CK(cudaMemsetAsync(h->count_d, 0, sizeof(unsigned long long), st));
+    DD_CK(cudaMemsetAsync(h->count_d, 0, 2 * sizeof(unsigned long long), st));
     DD_LAUNCH(h, dd::launch_count_unknown(L0.geom, L0.tmask, h->count_d, st));
-    {
-        unsigned long long cnt = 0;
-        DD_CK(cudaMemcpyAsync(&cnt, h->count_d, sizeof(cnt), cudaMemcpyDeviceToHost, st));
-        DD_CK(cudaStreamSynchronize(st));
-        h->local_unknowns = (long long)cnt;
-    }
-    // reference norms ||b - A u0||, u0 = C f, per level and channel
-    for (auto& L : h->lv) {
+    DD_LAUNCH(h, dd::launch_count_nonzero(L0.mask, (long long)npx, h->count_d + 1, st));
+    // reference norms ||b - A u0||, u0 = C f, per level and channel, kept on the device
+    const int nl = (int)h->lv.size();
+    for (int l = 0; l < nl; ++l) {
+        Level& L = h->lv[l];
         const int nblk = dd::res64_blocks(L.H, L.W);
         dd::Res64Args a{};
         a.H = L.H; a.W = L.W; a.C = h->C;
@@ -210,15 +209,20 @@ int load_data(dd_inpaint* h, const uint8_t* mask, const float* values, cudaStrea
         a.g_out = nullptr; a.gst = Store::F32;
         a.part = h->res_part; a.nblk = nblk;
         DD_LAUNCH(h, dd::launch_res64(a, st));
-        DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, nblk, h->C, h->res_out, st));
-        DD_CK(cudaMemcpyAsync(h->h_res, h->res_out, sizeof(double2) * h->C, cudaMemcpyDeviceToHost, st));
-        DD_CK(cudaStreamSynchronize(st));
-        L.ref.resize(h->C);
-        for (int c = 0; c < h->C; ++c) L.ref[c] = std::sqrt(h->h_res[c].x);
-        for (int c = 0; c < h->C; ++c) h->h_small[c] = L.ref[c];
-        DD_CK(cudaMemcpyAsync(L.ref_d, h->h_small, sizeof(double) * h->C, cudaMemcpyHostToDevice, st));
-        DD_CK(cudaStreamSynchronize(st));
+        DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, nblk, h->C, h->res_out + (size_t)l * h->C, st));
+        DD_LAUNCH(h, dd::launch_sqrt_sums(h->res_out + (size_t)l * h->C, L.ref_d, h->C, st));
     }
+    unsigned long long cnt[2] = {0, 0};
+    DD_CK(cudaMemcpyAsync(cnt, h->count_d, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_res, h->res_out, sizeof(double2) * h->C * nl, cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaStreamSynchronize(st));
+    h->local_unknowns = (long long)cnt[0];
+    for (int l = 0; l < nl; ++l) {
+        Level& L = h->lv[l];
+        L.ref.resize(h->C);
+        for (int c = 0; c < h->C; ++c) L.ref[c] = std::sqrt(h->h_res[(size_t)l * h->C + c].x);
+    }
+    if (cnt[1] == 0) { set_error("empty mask"); return DD_EEMPTYMASK; }
     return DD_OK;
 }
 
@@ -350,8 +354,29 @@ int write_scaled_residual(dd_inpaint* h, cudaStream_t st) {
     return DD_OK;
 }
 
-// Coarse-to-fine initialisation (Sec. 4): coarsest level from u0 = C f,
-// each level solved to coarse_tol, prolonged as the next level's start.
+// Enqueue n sweeps on level L starting from u[0] under the device stop test
+// (tol, stall), then resolve which buffer holds the result into L.state_d.
+// No host synchronisation: launches after the stop are no-ops.  With timing,
+// fine-level launches are bracketed by events (read after the next sync).
+int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed) {
+    DD_CK(cudaMemsetAsync(h->flag_d, 0, 4 * sizeof(int), st));
+    dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, tol, 0.0, h->flag_d, 0};
+    for (int i = 0; i < n; ++i) {
+        stop.sweep_index = i;
+        if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
+        DD_LAUNCH(h, dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), L.map_u[i & 1], nullptr, L.u[(i + 1) & 1],
+                                      L.tmask, stop, h->prm.robin_p, h->prm.local_cg_iters, st));
+        if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
+    }
+    DD_LAUNCH(h, dd::launch_resolve(h->flag_d, n, L.state_d, st));
+    return DD_OK;
+}
+
+// Coarse-to-fine initialisation (Sec. 4): coarsest level from u0 = C f, each
+// level swept to coarse_tol (at most coarse_sweeps sweeps) and prolonged as the
+// next level's start; the fine level's start is left in u[0].  Everything is
+// enqueued without host synchronisation: each level's result buffer is chosen
+// on the device.
 int cascade(dd_inpaint* h, cudaStream_t st) {
     const int nl = (int)h->lv.size();
     for (int l = nl - 1; l >= 1; --l) {
@@ -360,23 +385,18 @@ int cascade(dd_inpaint* h, cudaStream_t st) {
             DD_LAUNCH(h, dd::launch_copy2d(L.H, L.W, h->C, L.f, L.P, L.plane(), L.u[0], L.P, L.plane(), st));
         } else {
             Level& Cc = h->lv[l + 1];
-            DD_LAUNCH(h, dd::launch_prolong(Cc.H, Cc.W, L.H, L.W, h->C, Cc.u[0], Cc.P, Cc.plane(), L.mask, L.W, L.f, L.P,
-                                     L.plane(), L.u[0], L.P, L.plane(), st));
+            DD_LAUNCH(h, dd::launch_prolong_sel(Cc.H, Cc.W, L.H, L.W, h->C, Cc.u[0], Cc.u[1], Cc.state_d, Cc.P,
+                                                Cc.plane(), L.mask, L.W, L.f, L.P, L.plane(), L.u[0], L.P,
+                                                L.plane(), st));
         }
-        int c = 0, applied = 0;
-        bool conv = false;
-        void* bufs[2] = {L.u[0], L.u[1]};
-        DD_TRY(run_sweeps(h, L.geom, Store::F32, bufs, L.map_u, c, nullptr, L.tmask, L.partial, L.ref_d,
-                          h->prm.coarse_tol, 0.0, h->prm.coarse_sweeps, st, &applied, &conv));
-        if (c != 0) DD_LAUNCH(h, dd::launch_copy2d(L.H, L.W, h->C, L.u[1], L.P, L.plane(), L.u[0], L.P, L.plane(), st));
-        if (l < DD_MAX_LEVELS) h->stats.sweeps_per_level[l] = applied;
-        h->stats.sweeps_total += applied;
+        DD_TRY(enqueue_sweeps(h, L, h->prm.coarse_sweeps, h->prm.coarse_tol, st, false));
     }
     Level& F = h->lv[0];
     if (nl > 1) {
         Level& Cc = h->lv[1];
-        DD_LAUNCH(h, dd::launch_prolong(Cc.H, Cc.W, F.H, F.W, h->C, Cc.u[0], Cc.P, Cc.plane(), F.mask, F.W, F.f, F.P,
-                                 F.plane(), F.u[0], F.P, F.plane(), st));
+        DD_LAUNCH(h, dd::launch_prolong_sel(Cc.H, Cc.W, F.H, F.W, h->C, Cc.u[0], Cc.u[1], Cc.state_d, Cc.P,
+                                            Cc.plane(), F.mask, F.W, F.f, F.P, F.plane(), F.u[0], F.P, F.plane(),
+                                            st));
     } else {
         DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.f, F.P, F.plane(), F.u[0], F.P, F.plane(), st));
     }
@@ -384,46 +404,133 @@ int cascade(dd_inpaint* h, cudaStream_t st) {
     return DD_OK;
 }
 
+// Residual norms of a dense FP32 image u (pitch W) at level 0 into h_res[0..C).
+int residual_of(dd_inpaint* h, const float* u, int up, long long uplane, cudaStream_t st) {
+    Level& L = h->lv[0];
+    dd::Res64Args a{};
+    a.H = L.H; a.W = L.W; a.C = h->C;
+    a.u = u; a.up = up; a.uplane = uplane;
+    a.mask = L.mask; a.mp = L.W;
+    a.g_out = nullptr; a.gst = Store::F32;
+    a.part = h->res_part; a.nblk = h->res_nblk;
+    DD_LAUNCH(h, dd::launch_res64(a, st));
+    DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, h->res_nblk, h->C, h->res_out, st));
+    DD_CK(cudaMemcpyAsync(h->h_res, h->res_out, sizeof(double2) * h->C, cudaMemcpyDeviceToHost, st));
+    return DD_OK;
+}
+
+int rel_from_h_res(dd_inpaint* h, std::vector<double>& rel, std::vector<double>& rmax, std::vector<double>& rnorm) {
+    const Level& L = h->lv[0];
+    rel.assign(h->C, 0.0);
+    rmax.assign(h->C, 0.0);
+    rnorm.assign(h->C, 0.0);
+    for (int c = 0; c < h->C; ++c) {
+        rnorm[c] = std::sqrt(h->h_res[c].x);
+        rmax[c] = h->h_res[c].y;
+        rel[c] = rnorm[c] / (L.ref[c] > 0.0 ? L.ref[c] : 1.0);
+        if (!std::isfinite(rel[c])) { set_error("non-finite residual"); return DD_ENUMERIC; }
+    }
+    return DD_OK;
+}
+
+// Read the per-level sweep counts resolved on the device (after a sync).
+void take_level_stats(dd_inpaint* h) {
+    for (size_t l = 1; l < h->lv.size() && l < DD_MAX_LEVELS; ++l) h->stats.sweeps_per_level[l] = h->h_state[4 * l + 1];
+    for (size_t l = 1; l < h->lv.size(); ++l) h->stats.sweeps_total += h->h_state[4 * l + 1];
+}
+
 int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
     std::memset(&h->stats, 0, sizeof(h->stats));
     h->stats.channels = h->C;
     h->stats.device_bytes = h->bytes;
     h->stats.local_unknowns = h->local_unknowns;
+    const int nl = (int)h->lv.size();
     DD_CK(cudaEventRecord(h->ev0, st));
-    if (!h->warm) DD_TRY(cascade(h, st));
-    h->warm = false;
     Level& F = h->lv[0];
+    if (!h->warm) {
+        DD_TRY(cascade(h, st));
+    } else if (h->cur != 0) {
+        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[1], F.P, F.plane(), F.u[0], F.P, F.plane(), st));
+        h->cur = 0;
+    }
+    const bool cascaded = !h->warm;
+    h->warm = false;
     std::vector<double> rel, rmax, rnorm;
     int fine_sweeps = 0;
     bool converged = false;
-    int rc = DD_OK;
+    bool output_written = false;
+    const long long dense_plane = (long long)F.H * F.W;
     if (h->prm.precision == DD_PREC_FP32) {
-        double target = tol;
-        for (int attempt = 0; attempt < 4 && fine_sweeps < h->prm.max_sweeps; ++attempt) {
-            int applied = 0;
-            bool conv = false;
-            void* bufs[2] = {F.u[0], F.u[1]};
-            DD_TRY(run_sweeps(h, F.geom, Store::F32, bufs, F.map_u, h->cur, nullptr, F.tmask, F.partial, F.ref_d,
-                              target, 0.0, h->prm.max_sweeps - fine_sweeps, st, &applied, &conv, true));
-            fine_sweeps += applied;
-            DD_TRY(fine_residual64(h, st, rel, rmax, rnorm));
-            const double worst = *std::max_element(rel.begin(), rel.end());
-            if (worst <= tol) { converged = true; break; }
-            if (!conv) break;
-            target = target * 0.5;   // the FP32 fused estimate was optimistic: tighten and go on
+        // device-controlled first chunk: sweeps, output of the resolved buffer,
+        // its residual, and one read-back
+        const int n1 = std::min(dd_inpaint::kFirst, h->prm.max_sweeps);
+        const bool timed = h->prm.timing != 0;
+        DD_TRY(enqueue_sweeps(h, F, n1, tol, st, timed));
+        DD_LAUNCH(h, dd::launch_copy2d_sel(F.H, F.W, h->C, F.u[0], F.u[1], F.state_d, F.P, F.plane(), u_out, F.W,
+                                           dense_plane, st));
+        DD_TRY(residual_of(h, u_out, F.W, dense_plane, st));
+        DD_CK(cudaMemcpyAsync(h->h_state, F.state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        for (int l = 1; l < nl; ++l)
+            DD_CK(cudaMemcpyAsync(h->h_state + 4 * l, h->lv[l].state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaStreamSynchronize(st));
+        if (h->h_flag[2] != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
+        if (cascaded) take_level_stats(h);
+        const int status = h->h_state[2], applied = h->h_state[1];
+        if (status == 2) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
+        if (timed) {
+            for (int i = 0; i <= applied && i < n1; ++i) {
+                float ms = 0.f;
+                DD_CK(cudaEventElapsedTime(&ms, h->sw_ev[2 * i], h->sw_ev[2 * i + 1]));
+                h->stats.fine_sweep_ms += ms;
+                h->stats.fine_sweep_launches += 1;
+            }
+        }
+        fine_sweeps = applied;
+        h->cur = h->h_state[0];
+        DD_TRY(rel_from_h_res(h, rel, rmax, rnorm));
+        double worst = *std::max_element(rel.begin(), rel.end());
+        output_written = true;
+        if (status == 1 && worst <= tol) {
+            converged = true;
+        } else {
+            // not converged in the first chunk (or the FP32 fused estimate was
+            // optimistic): continue under host control
+            double target = status == 1 ? tol * 0.5 : tol;
+            for (int attempt = 0; attempt < 4 && fine_sweeps < h->prm.max_sweeps; ++attempt) {
+                int app = 0;
+                bool conv = false;
+                void* bufs[2] = {F.u[0], F.u[1]};
+                DD_TRY(run_sweeps(h, F.geom, Store::F32, bufs, F.map_u, h->cur, nullptr, F.tmask, F.partial, F.ref_d,
+                                  target, 0.0, h->prm.max_sweeps - fine_sweeps, st, &app, &conv, true));
+                fine_sweeps += app;
+                DD_TRY(fine_residual64(h, st, rel, rmax, rnorm));
+                worst = *std::max_element(rel.begin(), rel.end());
+                if (worst <= tol) { converged = true; break; }
+                if (!conv) break;
+                target *= 0.5;
+            }
+            output_written = false;
         }
     } else {
         const Store lt = h->lowst;
         for (int corr = 0;; ++corr) {
             DD_TRY(fine_residual64(h, st, rel, rmax, rnorm));
+            if (corr == 0 && cascaded) {
+                for (int l = 1; l < nl; ++l)
+                    DD_CK(cudaMemcpyAsync(h->h_state + 4 * l, h->lv[l].state_d, 4 * sizeof(int),
+                                          cudaMemcpyDeviceToHost, st));
+                DD_CK(cudaStreamSynchronize(st));
+                take_level_stats(h);
+            }
             const double worst = *std::max_element(rel.begin(), rel.end());
             if (worst <= tol) { converged = true; break; }
             if (corr >= h->prm.max_corrections || fine_sweeps >= h->prm.max_sweeps) break;
             for (int c = 0; c < h->C; ++c) {
-                const double s = rmax[c] > 0.0 ? rmax[c] : 1.0;
-                h->h_small[c] = s;
-                h->h_small[h->C + c] = 1.0 / s;
-                h->h_small[2 * h->C + c] = rnorm[c] / s;
+                const double sc = rmax[c] > 0.0 ? rmax[c] : 1.0;
+                h->h_small[c] = sc;
+                h->h_small[h->C + c] = 1.0 / sc;
+                h->h_small[2 * h->C + c] = rnorm[c] / sc;
             }
             DD_CK(cudaMemcpyAsync(h->scale_d, h->h_small, sizeof(double) * h->C, cudaMemcpyHostToDevice, st));
             DD_CK(cudaMemcpyAsync(h->scale_inv_d, h->h_small + h->C, sizeof(double) * h->C, cudaMemcpyHostToDevice, st));
@@ -431,15 +538,15 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
                                   cudaMemcpyHostToDevice, st));
             DD_TRY(write_scaled_residual(h, st));
             DD_CK(dd::launch_fill_zero(lt, h->e[0], (size_t)h->C * F.plane(), st));
-            int ecur = 0, applied = 0;
+            int ecur = 0, app = 0;
             bool conv = false;
             void* bufs[2] = {h->e[0], h->e[1]};
             const double stall = lt == Store::F32 ? 0.0 : 0.7;
             DD_TRY(run_sweeps(h, F.geom, lt, bufs, h->map_e, ecur, &h->map_g, F.tmask, F.partial, h->inner_ref_d,
-                              h->prm.inner_tol, stall, h->prm.max_sweeps - fine_sweeps, st, &applied, &conv, true));
-            fine_sweeps += applied;
-            DD_LAUNCH(h, dd::launch_correct(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), bufs[ecur], lt, F.P, F.plane(),
-                                     F.mask, F.W, h->scale_d, st));
+                              h->prm.inner_tol, stall, h->prm.max_sweeps - fine_sweeps, st, &app, &conv, true));
+            fine_sweeps += app;
+            DD_LAUNCH(h, dd::launch_correct(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), bufs[ecur], lt, F.P,
+                                            F.plane(), F.mask, F.W, h->scale_d, st));
             h->stats.corrections = corr + 1;
             DD_CK(cudaStreamSynchronize(st));   // h_small is reused by the next correction
         }
@@ -448,16 +555,15 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
     h->stats.sweeps_total += fine_sweeps;
     h->stats.converged = converged ? 1 : 0;
     for (int c = 0; c < h->C && c < DD_MAX_STAT_CHANNELS; ++c) h->stats.rel_residual[c] = rel.empty() ? 0 : rel[c];
-    if (u_out != nullptr)
-        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), u_out, F.W, (long long)F.H * F.W, st));
+    if (!output_written)
+        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), u_out, F.W, dense_plane, st));
     DD_CK(cudaEventRecord(h->ev1, st));
     DD_CK(cudaEventSynchronize(h->ev1));
     float ms = 0.f;
     DD_CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     h->stats.ms_total = ms;
     h->stats.kernel_launches = h->launches;
-    if (!converged) rc = DD_ENOTCONVERGED;
-    return rc;
+    return converged ? DD_OK : DD_ENOTCONVERGED;
 }
 
 void free_all(dd_inpaint* h) {
@@ -466,6 +572,7 @@ void free_all(dd_inpaint* h) {
     if (h->h_res) cudaFreeHost(h->h_res);
     if (h->h_small) cudaFreeHost(h->h_small);
     if (h->h_flag) cudaFreeHost(h->h_flag);
+    if (h->h_state) cudaFreeHost(h->h_state);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     for (auto& e : h->sw_ev)
@@ -480,9 +587,11 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if (params) p = *params; else dd_params_default(&p);
     DD_TRY(validate(H, W, C, p));
     if (!(p.robin_p > 0.f)) p.robin_p = robin_default(p.block, p.overlap);
-    long long nknown = 0;
-    DD_TRY(count_known(mask, (size_t)H * W, p.inputs_on_device != 0, &nknown));
-    if (nknown == 0) { set_error("empty mask"); return DD_EEMPTYMASK; }
+    if (!p.inputs_on_device) {   // device masks are counted on the device by load_data
+        long long nknown = 0;
+        DD_TRY(count_known(mask, (size_t)H * W, false, &nknown));
+        if (nknown == 0) { set_error("empty mask"); return DD_EEMPTYMASK; }
+    }
 
     dd_inpaint* h = new (std::nothrow) dd_inpaint();
     if (!h) { set_error("host allocation"); return DD_ENOMEM; }
@@ -511,6 +620,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
             if ((rc = dalloc(h, (void**)&L.u[b], plane_bytes)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &L.partial, (size_t)C * dd::kSweepSlots)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &L.ref_d, (size_t)C)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &L.state_d, 4)) != DD_OK) return fail(rc);
         hh = (hh + 1) / 2; ww = (ww + 1) / 2;
     }
     Level& F = h->lv[0];
@@ -539,13 +649,14 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     }
     h->res_nblk = dd::res64_blocks(H, W);
     if ((rc = dalloc_t(h, &h->res_part, (size_t)C * h->res_nblk)) != DD_OK) return fail(rc);
-    if ((rc = dalloc_t(h, &h->res_out, (size_t)C)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->res_out, (size_t)C * DD_MAX_LEVELS)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->norms2_d, (size_t)2 * C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->inner_ref_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->scale_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->scale_inv_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->flag_d, 4)) != DD_OK) return fail(rc);
-    if (cudaMallocHost(&h->h_res, sizeof(double2) * C) != cudaSuccess ||
+    if (cudaMallocHost(&h->h_res, sizeof(double2) * C * DD_MAX_LEVELS) != cudaSuccess ||
+        cudaMallocHost(&h->h_state, sizeof(int) * 4 * DD_MAX_LEVELS) != cudaSuccess ||
         cudaMallocHost(&h->h_small, sizeof(double) * 3 * C) != cudaSuccess ||
         cudaMallocHost(&h->h_flag, sizeof(int) * 4) != cudaSuccess) {
         set_error("cudaMallocHost failed");
@@ -557,9 +668,10 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     }
     for (auto& e : h->sw_ev)
         if (cudaEventCreate(&e) != cudaSuccess) { set_error("cudaEventCreate failed"); return fail(DD_ECUDA); }
-    if ((rc = dalloc_t(h, &h->count_d, 1)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->count_d, 2)) != DD_OK) return fail(rc);
     cudaStream_t st = nullptr;
     if ((rc = load_data(h, mask, values, st)) != DD_OK) return fail(rc);
+    h->valid = true;
     if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("sync"); return fail(DD_ECUDA); }
     *out = h;
     return DD_OK;
@@ -592,7 +704,7 @@ void dd_params_default(dd_params* p) {
     p->coarse_tol = 1e-2;
     p->inner_tol = 3e-3;
     p->max_corrections = 30;
-    p->coarse_sweeps = 40;
+    p->coarse_sweeps = 12;
     p->timing = 0;
 }
 
@@ -619,6 +731,7 @@ int dd_inpaint_create(int H, int W, int C, const uint8_t* mask, const float* val
 
 int dd_inpaint_solve(dd_handle h, float* u_out, double tol, void* stream) {
     if (!h || !u_out || !(tol > 0.0)) { set_error("bad solve arguments"); return DD_EINVAL; }
+    if (!h->valid) { set_error("no valid data (the last set_data failed)"); return DD_EEMPTYMASK; }
     return solve_impl(h, u_out, tol, static_cast<cudaStream_t>(stream));
 }
 
@@ -632,16 +745,20 @@ int dd_inpaint_destroy(dd_handle h) {
 
 int dd_inpaint_set_data(dd_handle h, const uint8_t* mask, const float* values, int keep_iterate) {
     if (!h || !mask || !values) { set_error("NULL argument"); return DD_EINVAL; }
-    long long nknown = 0;
-    DD_TRY(count_known(mask, (size_t)h->H * h->W, h->prm.inputs_on_device != 0, &nknown));
-    if (nknown == 0) { set_error("empty mask"); return DD_EEMPTYMASK; }
+    if (!h->prm.inputs_on_device) {
+        long long nknown = 0;
+        DD_TRY(count_known(mask, (size_t)h->H * h->W, false, &nknown));
+        if (nknown == 0) { set_error("empty mask"); return DD_EEMPTYMASK; }
+    }
     cudaStream_t st = nullptr;
     Level& F = h->lv[0];
     // keep the fine iterate in buffer 0 (load_data stages values through u[1])
     if (keep_iterate && h->cur != 0)
         DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[1], F.P, F.plane(), F.u[0], F.P, F.plane(), st));
     h->cur = 0;
+    h->valid = false;
     DD_TRY(load_data(h, mask, values, st));
+    h->valid = true;
     if (keep_iterate) {
         DD_LAUNCH(h, dd::launch_reset_known(F.H, F.W, h->C, F.u[0], F.P, F.plane(), F.mask, F.W, F.f, F.P, F.plane(), st));
         h->warm = true;
