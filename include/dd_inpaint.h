@@ -81,6 +81,8 @@ typedef struct dd_params {
     int    coarse_sweeps;    /* sweeps launched per coarse level (default 12); launches after the
                                 coarse tolerance is met do no work */
     int    timing;           /* 1: time every fine-level sweep launch with CUDA events (dd_stats) */
+    int    tile_warps;       /* warps holding one block tile: 0 = default; block 16: 1;
+                                block 32: 1, 2 or 4; block 64: 4 or 8 */
 } dd_params;
 
 #define DD_MAX_STAT_CHANNELS 16

@@ -237,14 +237,18 @@ __global__ void count_nonzero_kernel(const uint8_t* __restrict__ m, long long n,
 }
 
 // ---- device-side control of a sweep sequence ------------------------------------------
-// After n sweep launches that started from buffer 0 under the stop flag:
-// state = {buffer holding the result, sweeps applied, flag value}.
-__global__ void resolve_kernel(const int* __restrict__ flag, int n, int* __restrict__ state) {
-    const int f = flag[0];
-    const int applied = (f == 1 || f == 3) ? flag[1] : n;
-    state[0] = applied & 1;
-    state[1] = applied;
-    state[2] = f;
+// After a sweep sequence: out = {buffer holding the result, full sweeps applied, flag value}.
+__global__ void resolve_kernel(const int* __restrict__ flag, const int* __restrict__ ss, int* __restrict__ out) {
+    out[0] = ss[0];
+    out[1] = ss[1];
+    out[2] = flag[0];
+}
+
+__global__ void reset_sweep_state_kernel(int* __restrict__ state, int* __restrict__ flag, int cur) {
+    if (threadIdx.x < 4) {
+        state[threadIdx.x] = threadIdx.x == 0 ? cur : 0;
+        flag[threadIdx.x] = 0;
+    }
 }
 
 __global__ void prolong_sel_kernel(int Hc, int Wc, int H, int W, const float* __restrict__ uc0,
@@ -391,8 +395,13 @@ cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long upla
 
 namespace dd {
 
-cudaError_t launch_resolve(const int* flag, int n, int* state, cudaStream_t st) {
-    resolve_kernel<<<1, 1, 0, st>>>(flag, n, state);
+cudaError_t launch_resolve(const int* flag, const int* sweep_state, int* out, cudaStream_t st) {
+    resolve_kernel<<<1, 1, 0, st>>>(flag, sweep_state, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, cudaStream_t st) {
+    reset_sweep_state_kernel<<<1, 32, 0, st>>>(state, flag, cur);
     return cudaGetLastError();
 }
 

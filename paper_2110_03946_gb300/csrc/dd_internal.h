@@ -22,16 +22,22 @@ inline size_t store_bytes(Store s) { return s == Store::F32 ? 4 : 2; }
 struct TileGeom {
     int H = 0, W = 0, pitch = 0;  // image size; row pitch of the level's buffers (elements)
     int b = 32, o = 6, s = 26, half_o = 3;
+    int nw = 1;                   // warps that hold one block tile
     int ntx = 0, nty = 0, ntiles = 0;
 };
 
 int axis_blocks(int n, int b, int o);
-TileGeom make_geom(int H, int W, int pitch, int b, int o);
+// nw <= 0 selects default_tile_warps(b)
+TileGeom make_geom(int H, int W, int pitch, int b, int o, int nw = 0);
 
-// Kernel shape chosen for a block side: threads per block-tile and the number
-// of 32-bit mask words per tile (known bits + owned bits per thread).
+// Kernel shape chosen for a block side and warps per tile: threads per
+// block-tile and the number of 32-bit mask words per tile (known bits +
+// owned bits per thread).  Supported: b = 16 (1 warp), 32 (1, 2 or 4 warps),
+// 64 (4 or 8 warps).
 bool block_supported(int b);
-int tile_threads(int b);
+int default_tile_warps(int b);
+bool tile_warps_supported(int b, int nw);
+int tile_threads(int b, int nw);
 size_t tmask_words(const TileGeom& g);
 
 // Per-tile, per-thread bit masks: bit set in word 0 = pixel known or outside
@@ -48,15 +54,23 @@ cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsig
 cudaError_t make_tile_map(CUtensorMap* out, Store st, const void* base, int H, int W, int pitch, int C, int b);
 
 // Residual norms and stop test fused into the sweep.  Each CTA writes its
-// per-channel sum of squared owned residuals of u_in to partial[c * slots + cta];
-// the last CTA to finish sums them in a fixed order into norms2[c] (norms2[C + c]
-// keeps the value for the stagnation test) and sets flag[0]:
+// per-channel sum of squared owned residuals of the input iterate to
+// partial[c * slots + cta]; the last CTA to finish sums them in a fixed order
+// into norms2[c] and sets flag[0]:
 //   1 when max_c sqrt(norms2[c]) / ref[c] <= tol (tol < 0: never),
 //   2 on NaN/Inf, 3 when stall > 0 and every channel's residual fell by less
-//   than the factor 1/stall since the previous launch of the run;
+//   than the factor 1/stall since the previous full sweep;
 // flag[1] = sweep_index then.  flag[0] != 0 makes later launches no-ops.
 // flag[2] is set if a bounded wait for a staged tile gave up; flag[3] is the
 // completion ticket (0 between launches).  slots >= the launch grid.
+// The iterate pair is chosen on the device: state[0] is the buffer holding the
+// current iterate (the launch reads it and writes the other one), state[1]
+// counts full sweeps, state[2] = 1 makes the next launch a probe that only
+// evaluates the residual of the current iterate (no CG, no write-back).  After
+// a full sweep the last CTA requests a probe when the residual ratio of the
+// last two sweeps predicts that the new iterate meets tol.  norms2 holds
+// 2C + 2 doubles: current norms, norms of the previous full sweep, and the
+// previous full sweep's worst relative residual.
 struct SweepStop {
     float* partial;
     int slots;
@@ -65,17 +79,28 @@ struct SweepStop {
     double tol;
     double stall;
     int* flag;
+    int* state;
     int sweep_index;
+    int force_probe;   // 1: this launch is a probe whatever state[2] says
 };
 constexpr int kSweepSlots = 4096;   // per-channel partial slots that cover any persistent grid
 
-// One ORAS sweep over all tiles of all C channels (planes `plane` elements apart).
-//   map_in: TMA descriptor of the input iterate u_in; u_out receives the owned
-//   cores; map_g: optional source g on unknown pixels (solves
-//   A u = C f + (I - C) g with u = f held on known pixels).
-cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, const CUtensorMap& map_in,
-                         const CUtensorMap* map_g, void* u_out, const uint32_t* tmask, const SweepStop& stop,
-                         float p_robin, int k, cudaStream_t stream);
+// The two iterate buffers of a level and their TMA descriptors.
+struct SweepPair {
+    const CUtensorMap* map[2];
+    void* u[2];
+};
+
+// One ORAS sweep (or probe) over all tiles of all C channels (planes `plane`
+// elements apart), from buffer state[0] of `pair` into the other buffer.
+//   map_g: optional source g on unknown pixels (solves A u = C f + (I - C) g
+//   with u = f held on known pixels).
+cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, const SweepPair& pair,
+                         const CUtensorMap* map_g, const uint32_t* tmask, const SweepStop& stop, float p_robin,
+                         int k, cudaStream_t stream);
+
+// state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..3] = 0.
+cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, cudaStream_t st);
 
 // ---- auxiliary passes (aux.cu) ----------------------------------------------------
 // dst[c][y][x] (pitch dp) = mask ? src[c][y][x] : 0  (src pitch sp)
@@ -126,10 +151,10 @@ cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long upla
 cudaError_t launch_convert(int H, int W, int C, const float* src, int sp, long long splane,
                            void* dst, Store dst_t, int dp, long long dplane, cudaStream_t st);
 
-// Device-side control of a sweep sequence of n launches started from buffer 0:
-// state[0] = buffer holding the result, state[1] = sweeps applied,
-// state[2] = the stop flag (0: not stopped, 1: converged, 2: NaN/Inf, 3: stalled).
-cudaError_t launch_resolve(const int* flag, int n, int* state, cudaStream_t st);
+// Summary of a sweep sequence for later steps: out[0] = buffer holding the
+// result, out[1] = full sweeps applied, out[2] = the stop flag (0: not
+// stopped, 1: converged, 2: NaN/Inf, 3: stalled).
+cudaError_t launch_resolve(const int* flag, const int* sweep_state, int* out, cudaStream_t st);
 // Prolongation / copy reading the source buffer uc0 or uc1 chosen by *sel on the device.
 cudaError_t launch_prolong_sel(int Hc, int Wc, int H, int W, int C, const float* uc0, const float* uc1,
                                const int* sel, int ucp, long long ucplane, const uint8_t* mask, int mp,

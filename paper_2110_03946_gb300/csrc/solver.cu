@@ -98,6 +98,7 @@ struct dd_inpaint {
     double2* res_out = nullptr;     // C
     double* norms2_d = nullptr;     // C
     int* flag_d = nullptr;          // [0] stop flag, [1] conv_at, [2] device wait timed out, [3] ticket
+    int* sstate_d = nullptr;        // sweep state: current buffer, full sweeps, probe request
     // pinned host mirrors
     double2* h_res = nullptr;
     double* h_small = nullptr;      // 3*C doubles scratch
@@ -149,6 +150,10 @@ int validate(int H, int W, int C, const dd_params& p) {
     if (H <= 0 || W <= 0 || C <= 0) { set_error("H, W and C must be positive"); return DD_EINVAL; }
     if ((long long)H * W > (1LL << 31) / 4) { set_error("image too large"); return DD_EINVAL; }
     if (!dd::block_supported(p.block)) { set_error("block must be 16, 32 or 64"); return DD_EINVAL; }
+    if (p.tile_warps != 0 && !dd::tile_warps_supported(p.block, p.tile_warps)) {
+        set_error("tile_warps: 16 -> 1; 32 -> 1, 2 or 4; 64 -> 4 or 8");
+        return DD_EINVAL;
+    }
     if (p.overlap < 0 || p.overlap >= p.block) { set_error("need 0 <= overlap < block"); return DD_EINVAL; }
     if (p.local_cg_iters < 1 || p.local_cg_iters > 4096) { set_error("local_cg_iters out of range"); return DD_EINVAL; }
     if (p.levels < 1 || p.levels > DD_MAX_LEVELS) { set_error("levels must be 1..8"); return DD_EINVAL; }
@@ -248,68 +253,55 @@ int run_sweeps(dd_inpaint* h, const TileGeom& g, Store st_t, void* const bufs[2]
                double tol, double stall, int max_sweeps, cudaStream_t st, int* applied, bool* converged,
                bool fine = false) {
     const long long plane = (long long)g.H * g.pitch;
-    DD_CK(cudaMemsetAsync(h->flag_d, 0, 4 * sizeof(int), st));
-    int done = 0;
+    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, cur, st));
     *converged = false;
-    const int chunk = dd_inpaint::kChunk;
+    *applied = 0;
     const bool timed = fine && h->prm.timing != 0;
-    dd::SweepStop stop{partial, dd::kSweepSlots, h->norms2_d, ref_d, tol, stall, h->flag_d, 0};
+    const dd::SweepPair pair{{&maps[0], &maps[1]}, {bufs[0], bufs[1]}};
+    dd::SweepStop stop{partial, dd::kSweepSlots, h->norms2_d, ref_d, tol, stall, h->flag_d, h->sstate_d, 0, 0};
+    int full_done = 0, launched = 0;
     while (true) {
-        // the chunk evaluates the stop test of iterates done .. done+n-1 and
-        // sweeps them; an iterate past max_sweeps is tested but not swept
-        const int n = std::min(chunk, max_sweeps - done + 1);
+        // full sweeps until max_sweeps; then one probe evaluates the last iterate
+        const bool last_probe = full_done >= max_sweeps;
+        const int n = last_probe ? 1 : std::min(dd_inpaint::kChunk, max_sweeps - full_done);
         for (int i = 0; i < n; ++i) {
-            const int idx = done + i;
-            const CUtensorMap& in = maps[(cur + idx) & 1];
-            void* out = bufs[(cur + idx + 1) & 1];
-            stop.sweep_index = idx;
-            if (idx < max_sweeps) {
-                if (timed) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
-                DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, in, map_g, out, tmask, stop, h->prm.robin_p,
-                                              h->prm.local_cg_iters, st));
-                if (timed) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
-            } else {
-                // evaluation only: the fused residual of this iterate needs a sweep;
-                // its output goes to the other buffer and is not used
-                DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, in, map_g, out, tmask, stop, h->prm.robin_p,
-                                              1, st));
-            }
+            stop.sweep_index = launched + i;
+            stop.force_probe = last_probe ? 1 : 0;
+            if (timed && !last_probe) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
+            DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, pair, map_g, tmask, stop, h->prm.robin_p,
+                                          h->prm.local_cg_iters, st));
+            if (timed && !last_probe) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
         }
+        launched += n;
         DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaMemcpyAsync(h->h_flag + 4, h->sstate_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DD_CK(cudaStreamSynchronize(st));
         if (h->h_flag[2] != 0) {
             set_error("a bounded device wait for a staged tile gave up");
             return DD_ETIMEOUT;
         }
-        if (timed) {
-            // launches that ran in full: up to and including the one that set the flag
-            const int last = h->h_flag[0] != 0 ? h->h_flag[1] : done + n - 1;
-            for (int i = 0; i < n; ++i) {
-                const int idx = done + i;
-                if (idx >= max_sweeps || idx > last) break;
+        const int new_full = h->h_flag[5];
+        if (timed && !last_probe) {
+            // launches of this chunk that were full sweeps
+            for (int i = 0; i < n && i < new_full - full_done; ++i) {
                 float ms = 0.f;
                 DD_CK(cudaEventElapsedTime(&ms, h->sw_ev[2 * i], h->sw_ev[2 * i + 1]));
                 h->stats.fine_sweep_ms += ms;
                 h->stats.fine_sweep_launches += 1;
             }
         }
+        full_done = new_full;
+        cur = h->h_flag[4];
+        *applied = full_done;
         if (h->h_flag[0] == 2) {
             set_error("non-finite residual norm");
             return DD_ENUMERIC;
         }
         if (h->h_flag[0] == 1 || h->h_flag[0] == 3) {
-            const int at = h->h_flag[1];
-            *applied = at;
-            cur = (cur + at) & 1;
             *converged = h->h_flag[0] == 1;
             return DD_OK;
         }
-        done += n;
-        if (done > max_sweeps) {
-            *applied = max_sweeps;
-            cur = (cur + max_sweeps) & 1;
-            return DD_OK;
-        }
+        if (last_probe) return DD_OK;
     }
 }
 
@@ -354,21 +346,23 @@ int write_scaled_residual(dd_inpaint* h, cudaStream_t st) {
     return DD_OK;
 }
 
-// Enqueue n sweeps on level L starting from u[0] under the device stop test
-// (tol, stall), then resolve which buffer holds the result into L.state_d.
-// No host synchronisation: launches after the stop are no-ops.  With timing,
+// Enqueue n launches on level L starting from u[0] under the device stop test
+// (tol), then record which buffer holds the result into L.state_d.  No host
+// synchronisation: launches after the stop are no-ops, and a launch that the
+// previous one predicts to be the last only probes the residual.  With timing,
 // fine-level launches are bracketed by events (read after the next sync).
 int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed) {
-    DD_CK(cudaMemsetAsync(h->flag_d, 0, 4 * sizeof(int), st));
-    dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, tol, 0.0, h->flag_d, 0};
+    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, st));
+    const dd::SweepPair pair{{&L.map_u[0], &L.map_u[1]}, {L.u[0], L.u[1]}};
+    dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, tol, 0.0, h->flag_d, h->sstate_d, 0, 0};
     for (int i = 0; i < n; ++i) {
         stop.sweep_index = i;
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
-        DD_LAUNCH(h, dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), L.map_u[i & 1], nullptr, L.u[(i + 1) & 1],
-                                      L.tmask, stop, h->prm.robin_p, h->prm.local_cg_iters, st));
+        DD_LAUNCH(h, dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), pair, nullptr, L.tmask, stop,
+                                      h->prm.robin_p, h->prm.local_cg_iters, st));
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
     }
-    DD_LAUNCH(h, dd::launch_resolve(h->flag_d, n, L.state_d, st));
+    DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, L.state_d, st));
     return DD_OK;
 }
 
@@ -479,7 +473,7 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
         const int status = h->h_state[2], applied = h->h_state[1];
         if (status == 2) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
         if (timed) {
-            for (int i = 0; i <= applied && i < n1; ++i) {
+            for (int i = 0; i < applied && i < n1; ++i) {
                 float ms = 0.f;
                 DD_CK(cudaEventElapsedTime(&ms, h->sw_ev[2 * i], h->sw_ev[2 * i + 1]));
                 h->stats.fine_sweep_ms += ms;
@@ -611,7 +605,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     for (int l = 0; l < nl; ++l) {
         Level& L = h->lv[l];
         L.H = hh; L.W = ww; L.P = round_up(ww, 32);
-        L.geom = dd::make_geom(hh, ww, L.P, p.block, p.overlap);
+        L.geom = dd::make_geom(hh, ww, L.P, p.block, p.overlap, p.tile_warps);
         const size_t plane_bytes = (size_t)C * L.plane() * sizeof(float);
         if ((rc = dalloc_t(h, &L.mask, (size_t)hh * ww)) != DD_OK) return fail(rc);
         if ((rc = dalloc(h, (void**)&L.f, plane_bytes)) != DD_OK) return fail(rc);
@@ -650,7 +644,8 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     h->res_nblk = dd::res64_blocks(H, W);
     if ((rc = dalloc_t(h, &h->res_part, (size_t)C * h->res_nblk)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->res_out, (size_t)C * DD_MAX_LEVELS)) != DD_OK) return fail(rc);
-    if ((rc = dalloc_t(h, &h->norms2_d, (size_t)2 * C)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->norms2_d, (size_t)2 * C + 2)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->sstate_d, 4)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->inner_ref_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->scale_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->scale_inv_d, (size_t)C)) != DD_OK) return fail(rc);
@@ -658,7 +653,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if (cudaMallocHost(&h->h_res, sizeof(double2) * C * DD_MAX_LEVELS) != cudaSuccess ||
         cudaMallocHost(&h->h_state, sizeof(int) * 4 * DD_MAX_LEVELS) != cudaSuccess ||
         cudaMallocHost(&h->h_small, sizeof(double) * 3 * C) != cudaSuccess ||
-        cudaMallocHost(&h->h_flag, sizeof(int) * 4) != cudaSuccess) {
+        cudaMallocHost(&h->h_flag, sizeof(int) * 8) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         return fail(DD_ENOMEM);
     }
@@ -706,6 +701,7 @@ void dd_params_default(dd_params* p) {
     p->max_corrections = 30;
     p->coarse_sweeps = 12;
     p->timing = 0;
+    p->tile_warps = 0;
 }
 
 const char* dd_strerror(int code) {
@@ -797,12 +793,13 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     if (!h || n < 0) { set_error("bad sweep arguments"); return DD_EINVAL; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Level& F = h->lv[0];
-    DD_CK(cudaMemsetAsync(h->flag_d, 0, 4 * sizeof(int), st));
-    dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, -1.0, 0.0, h->flag_d, 0};
-    for (int i = 0; i < n; ++i) {
+    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, h->cur, st));
+    const dd::SweepPair pair{{&F.map_u[0], &F.map_u[1]}, {F.u[0], F.u[1]}};
+    dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, -1.0, 0.0, h->flag_d, h->sstate_d, 0, 0};
+    for (int i = 0; i < n; ++i) {   // tol < 0: every launch is a full sweep
         stop.sweep_index = i;
-        DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), F.map_u[h->cur], nullptr, F.u[1 - h->cur],
-                                      F.tmask, stop, h->prm.robin_p, h->prm.local_cg_iters, st));
+        DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), pair, nullptr, F.tmask, stop,
+                                      h->prm.robin_p, h->prm.local_cg_iters, st));
         h->cur = 1 - h->cur;
     }
     if (n > 0) {

@@ -35,7 +35,7 @@ namespace {
 
 constexpr long long kMaxIterElems = 1LL << 22;   // C * H * pitch of one iterate buffer
 constexpr long long kMaxTiles = 16384;           // blocks per channel
-constexpr long long kMaxTileWords = kMaxTiles * 2 * 128;   // block masks (up to 128 threads per block)
+constexpr long long kMaxTileWords = kMaxTiles * 2 * 256;   // block masks (up to 256 threads per block)
 constexpr long long kMaxPartials = (long long)DD_MAX_STAT_CHANNELS * dd::kSweepSlots;   // per-CTA residual sums
 constexpr long long kMaxResBlocks = 65536;       // C * blocks of the FP64 residual pass
 constexpr int kMaxChannels = DD_MAX_STAT_CHANNELS;
@@ -48,9 +48,10 @@ constexpr size_t kOffPartial = kOffTmask + align256(kMaxTileWords * 4);
 constexpr size_t kOffResPart = kOffPartial + align256(kMaxPartials * 4);
 constexpr size_t kOffResOut = kOffResPart + align256(kMaxResBlocks * 16);
 constexpr size_t kOffNorms = kOffResOut + align256(kMaxChannels * 16);
-constexpr size_t kOffRef = kOffNorms + align256(2 * kMaxChannels * 8);
+constexpr size_t kOffRef = kOffNorms + align256((2 * kMaxChannels + 2) * 8);
 constexpr size_t kOffFlag = kOffRef + align256(kMaxChannels * 8);
-constexpr size_t kOffCount = kOffFlag + align256(4 * 4);
+constexpr size_t kOffState = kOffFlag + align256(4 * 4);
+constexpr size_t kOffCount = kOffState + align256(4 * 4);
 constexpr size_t kScratchBytes = kOffCount + align256(8);
 
 }  // namespace
@@ -118,12 +119,12 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     dd_params p;
     if (params) p = *params; else dd_params_default(&p);
     if (!dd::block_supported(p.block) || p.overlap < 0 || p.overlap >= p.block || p.local_cg_iters < 1 ||
-        p.max_sweeps < 0)
+        p.max_sweeps < 0 || (p.tile_warps != 0 && !dd::tile_warps_supported(p.block, p.tile_warps)))
         return fail(DD_EINVAL, "bad params");
     if (C > kMaxChannels) return fail(DD_EINVAL, "C exceeds the static scratch capacity (16 channels)");
     const int P = (W + 31) / 32 * 32;
     const long long elems = (long long)C * H * P;
-    const dd::TileGeom g = dd::make_geom(H, W, P, p.block, p.overlap);
+    const dd::TileGeom g = dd::make_geom(H, W, P, p.block, p.overlap, p.tile_warps);
     const int nblk = dd::res64_blocks(H, W);
     if (elems > kMaxIterElems || g.ntiles > kMaxTiles || (long long)nblk * C > kMaxResBlocks ||
         (long long)dd::tmask_words(g) > kMaxTileWords)
@@ -141,6 +142,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     double* norms2 = reinterpret_cast<double*>(base + kOffNorms);
     double* ref_d = reinterpret_cast<double*>(base + kOffRef);
     int* flag = reinterpret_cast<int*>(base + kOffFlag);
+    int* sstate = reinterpret_cast<int*>(base + kOffState);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long plane = (long long)H * P;
 
@@ -171,39 +173,35 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     }
     SS_CK(cudaMemcpyAsync(ref_d, ref, sizeof(double) * C, cudaMemcpyHostToDevice, st));
 
-    // sweeps with the device-side stop test, read back every 8 sweeps
+    // sweeps with the device-side stop test, read back every 8 launches
     int cur = 0, done = 0;
     double target = tol;
     bool converged = false;
+    const dd::SweepPair pair{{&maps[0], &maps[1]}, {u[0], u[1]}};
     for (int attempt = 0; attempt < 4 && !converged; ++attempt) {
-        SS_CK(cudaMemsetAsync(flag, 0, 4 * sizeof(int), st));
-        dd::SweepStop stop{partial, dd::kSweepSlots, norms2, ref_d, target, 0.0, flag, 0};
+        SS_CK(dd::launch_reset_sweep_state(sstate, flag, cur, st));
+        dd::SweepStop stop{partial, dd::kSweepSlots, norms2, ref_d, target, 0.0, flag, sstate, 0, 0};
         const int start = done;
-        int hflag[3] = {0, 0, 0};
+        int launched = 0;
+        int hflag[3] = {0, 0, 0}, hstate[2] = {cur, 0};
         while (true) {
-            const int n = std::min(8, p.max_sweeps - done + 1);
+            const bool last_probe = done >= p.max_sweeps;
+            const int n = last_probe ? 1 : std::min(8, p.max_sweeps - done);
             for (int i = 0; i < n; ++i) {
-                const int idx = done + i;
-                const int k = idx < p.max_sweeps ? p.local_cg_iters : 1;
-                stop.sweep_index = idx - start;
-                SS_CK(dd::launch_sweep(dd::Store::F32, g, C, plane, maps[(cur + idx - start) & 1], nullptr,
-                                       u[(cur + idx - start + 1) & 1], tmask, stop, pr, k, st));
+                stop.sweep_index = launched + i;
+                stop.force_probe = last_probe ? 1 : 0;
+                SS_CK(dd::launch_sweep(dd::Store::F32, g, C, plane, pair, nullptr, tmask, stop, pr,
+                                       p.local_cg_iters, st));
             }
+            launched += n;
             SS_CK(cudaMemcpyAsync(hflag, flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            SS_CK(cudaMemcpyAsync(hstate, sstate, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
             SS_CK(cudaStreamSynchronize(st));
             if (hflag[2] != 0) return fail(DD_ETIMEOUT, "a bounded device wait for a staged tile gave up");
             if (hflag[0] == 2) return fail(DD_ENUMERIC, "non-finite residual norm");
-            if (hflag[0] == 1) {
-                cur = (cur + hflag[1]) & 1;
-                done = start + hflag[1];
-                break;
-            }
-            done += n;
-            if (done > p.max_sweeps) {
-                cur = (cur + (p.max_sweeps - start)) & 1;
-                done = p.max_sweeps;
-                break;
-            }
+            cur = hstate[0];
+            done = start + hstate[1];
+            if (hflag[0] == 1 || last_probe) break;
         }
         // verify in FP64 on the iterate that is returned
         if (int rc = res_norms(H, W, C, u[cur], P, mask, res_part, nblk, res_out, h_res, st); rc != DD_OK) return rc;

@@ -113,9 +113,23 @@ struct Cfg {
     static_assert(PX % 2 == 0 && PX * PY <= 32 && BW == BH && 32 % LX == 0, "bad tile shape");
 };
 
-using Cfg16 = Cfg<2, 4, 8, 1>;   // 16 x 16 block, one warp, 8 px per lane
-using Cfg32 = Cfg<4, 8, 8, 1>;   // 32 x 32 block, one warp, 32 px per lane
-using Cfg64 = Cfg<4, 8, 16, 4>;  // 64 x 64 block, four warps of 64 x 16, 32 px per lane
+using Cfg16 = Cfg<2, 4, 8, 1>;     // 16 x 16 block, one warp, 8 px per lane
+using Cfg32 = Cfg<4, 8, 8, 1>;     // 32 x 32 block, one warp, 32 px per lane
+using Cfg32w2 = Cfg<4, 4, 8, 2>;   // 32 x 32 block, two warps of 32 x 16, 16 px per lane
+using Cfg32w4 = Cfg<4, 2, 8, 4>;   // 32 x 32 block, four warps of 32 x 8, 8 px per lane
+using Cfg64 = Cfg<4, 8, 16, 4>;    // 64 x 64 block, four warps of 64 x 16, 32 px per lane
+using Cfg64w8 = Cfg<4, 4, 16, 8>;  // 64 x 64 block, eight warps of 64 x 8, 16 px per lane
+
+// Calls f(Cfg{}) for the tile layout of block side b with nw warps per block.
+template <class F>
+cudaError_t with_cfg(int b, int nw, F&& f) {
+    switch (b) {
+        case 16: return nw == 1 ? f(Cfg16{}) : cudaErrorInvalidValue;
+        case 32: return nw == 1 ? f(Cfg32{}) : nw == 2 ? f(Cfg32w2{}) : nw == 4 ? f(Cfg32w4{}) : cudaErrorInvalidValue;
+        case 64: return nw == 4 ? f(Cfg64{}) : nw == 8 ? f(Cfg64w8{}) : cudaErrorInvalidValue;
+    }
+    return cudaErrorInvalidValue;
+}
 
 // Shared-memory tile: block plus one-pixel halo; the TMA box starts at a
 // 16-byte aligned column at or left of x0 - 1, so it is BX >= BW + 2 + (align - 1) wide.
@@ -131,7 +145,7 @@ struct Box {
 
 template <typename T>
 struct SweepArgs {
-    T* u_out;
+    T* u_buf[2];
     const uint32_t* tmask;
     SweepStop stop;
     int H, W, pitch, C;
@@ -158,10 +172,36 @@ __device__ __forceinline__ float tile_sum(float v, float* red, int wt, int lane)
     }
 }
 
+// Two sums over the threads of one tile in one butterfly.
+template <class CF>
+__device__ __forceinline__ float2 tile_sum2(float2 v, float* red_a, float* red_b, int wt, int lane) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        v.x += __shfl_xor_sync(FULL, v.x, m);
+        v.y += __shfl_xor_sync(FULL, v.y, m);
+    }
+    if constexpr (CF::NW == 1) {
+        return v;
+    } else {
+        if (lane == 0) {
+            red_a[wt] = v.x;
+            red_b[wt] = v.y;
+        }
+        __syncthreads();
+        float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < CF::NW; ++w) {
+            t.x += red_a[w];
+            t.y += red_b[w];
+        }
+        return t;
+    }
+}
+
 template <class CF, typename T>
 __global__ void __launch_bounds__(CF::NT)
-oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_g,
-                  const SweepArgs<T> a) {
+oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_constant__ CUtensorMap map_u1,
+                  const __grid_constant__ CUtensorMap map_g, const SweepArgs<T> a) {
     constexpr int PX = CF::PX, PY = CF::PY, LX = CF::LX, LY = CF::LY, NW = CF::NW;
     constexpr int BW = CF::BW, BH = CF::BH, NP = CF::NP, NT = CF::NT;
     using BOX = Box<CF, T>;
@@ -175,6 +215,13 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
 
     int* const flag = a.stop.flag;                  // [0] stop/skip, [1] conv_at, [2] err, [3] ticket
     if (flag[0] != 0) return;                        // converged or failed earlier: uniform no-op
+    // the current iterate and the kind of launch are device state (read before
+    // the last CTA of this launch updates them)
+    const int cur = a.stop.state[0];
+    const bool probe = a.stop.force_probe != 0 || a.stop.state[2] != 0;
+    const CUtensorMap* const map_u = cur ? &map_u1 : &map_u0;
+    T* const u_out = a.u_buf[cur ^ 1];
+    const int kcg = probe ? 0 : a.k;
     const long long total = (long long)a.ntiles * a.C;
     long long t = blockIdx.x;
     if (t >= total) return;
@@ -201,7 +248,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
         const int xs = ((x0 - 1) >= 0 ? (x0 - 1) / BOX::ALIGN : -1) * BOX::ALIGN;
         fence_proxy_async();
         mbar_expect_tx(&mbar[buf], tx_bytes);
-        tma_load_3d(stage(buf, 0), &map_u, xs, y0 - 1, c, &mbar[buf]);
+        tma_load_3d(stage(buf, 0), map_u, xs, y0 - 1, c, &mbar[buf]);
         if (a.has_g) tma_load_3d(stage(buf, 1), &map_g, xs, y0 - 1, c, &mbar[buf]);
     };
 
@@ -245,11 +292,51 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
         const T* __restrict__ U = stage(buf, 0);
         const T* __restrict__ G = stage(buf, 1);
 
+        // ---- local operator coefficients -----------------------------------------
+        float2 rpn[PY];     // -(vertical part of dd), both halves equal
+        float2 cpn[NP];     // -(horizontal part of dd)
+        float2 w2[PY][NP];  // 1 on unknown in-block pixels, else 0
+        float2 mN[PY], mS[PY], mW[NP], mE[NP];   // 1 where the neighbour is inside the image
+#pragma unroll
+        for (int i = 0; i < PY; ++i) {
+            const int ry = ry0 + i, y = y0 + ry;
+            const float up = ry > 0 ? 1.f : (y > 0 ? pr : 0.f);
+            const float dn = ry < th - 1 ? 1.f : (y < H - 1 ? pr : 0.f);
+            rpn[i] = make_float2(-(up + dn), -(up + dn));
+            const float n = y > 0 ? 1.f : 0.f, sv = y < H - 1 ? 1.f : 0.f;
+            mN[i] = make_float2(n, n);
+            mS[i] = make_float2(sv, sv);
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            float v[2], wv[2], ev[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int rx = rx0 + 2 * j + e, x = x0 + rx;
+                const float lf = rx > 0 ? 1.f : (x > 0 ? pr : 0.f);
+                const float rt = rx < tw - 1 ? 1.f : (x < W - 1 ? pr : 0.f);
+                v[e] = -(lf + rt);
+                wv[e] = x > 0 ? 1.f : 0.f;
+                ev[e] = x < W - 1 ? 1.f : 0.f;
+            }
+            cpn[j] = make_float2(v[0], v[1]);
+            mW[j] = make_float2(wv[0], wv[1]);
+            mE[j] = make_float2(ev[0], ev[1]);
+        }
+#pragma unroll
+        for (int i = 0; i < PY; ++i)
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+                w2[i][j] = make_float2(((kb >> (i * PX + 2 * j)) & 1u) ? 0.f : 1.f,
+                                       ((kb >> (i * PX + 2 * j + 1)) & 1u) ? 0.f : 1.f);
+
         // ---- local residual R_i (b - A u^n) and the owned residual norm ----------
-        // The patch and its one-pixel ring are read from the staged tile once;
-        // neighbours outside the image are never used (reflecting boundary).
+        // The patch and its one-pixel ring are read from the staged tile once.
+        // r_p = g_p + sum over in-image neighbours q of (u_q - u_p): each
+        // difference is exact for close values, and a neighbour outside the image
+        // (reflecting boundary; the staged tile holds zero there) gets weight 0.
         float2 r2[PY][NP];
-        float s2 = 0.f;
+        float s2 = 0.f, rr0 = 0.f;
         {
             const int o0 = (1 + ry0) * BX + cx + rx0;
             float uu[PY + 2][PX + 2];
@@ -263,23 +350,52 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
 #pragma unroll
             for (int i = 0; i < PY; ++i)
 #pragma unroll
-                for (int j = 0; j < PX; ++j) {
-                    float res = 0.f;
-                    if (!((kb >> (i * PX + j)) & 1u)) {            // unknown and inside the block
-                        const int y = y0 + ry0 + i, x = x0 + rx0 + j;
-                        const float uc = uu[i + 1][j + 1];
-                        float acc = a.has_g ? to_f(G[o0 + i * BX + j]) : 0.f;
-                        if (y > 0) acc += uu[i][j + 1] - uc;
-                        if (y < H - 1) acc += uu[i + 2][j + 1] - uc;
-                        if (x > 0) acc += uu[i + 1][j] - uc;
-                        if (x < W - 1) acc += uu[i + 1][j + 2] - uc;
-                        res = acc;
-                        if ((ob >> (i * PX + j)) & 1u) s2 = fmaf(res, res, s2);
-                    }
-                    if (j & 1) r2[i][j >> 1].y = res; else r2[i][j >> 1].x = res;
+                for (int j = 0; j < NP; ++j) {
+                    const float2 uc = make_float2(uu[i + 1][2 * j + 1], uu[i + 1][2 * j + 2]);
+                    const float2 nuc = make_float2(-uc.x, -uc.y);
+                    float2 acc = a.has_g ? make_float2(to_f(G[o0 + i * BX + 2 * j]), to_f(G[o0 + i * BX + 2 * j + 1]))
+                                         : make_float2(0.f, 0.f);
+                    acc = fma2(mN[i], add2(make_float2(uu[i][2 * j + 1], uu[i][2 * j + 2]), nuc), acc);
+                    acc = fma2(mS[i], add2(make_float2(uu[i + 2][2 * j + 1], uu[i + 2][2 * j + 2]), nuc), acc);
+                    acc = fma2(mW[j], add2(make_float2(uu[i + 1][2 * j], uu[i + 1][2 * j + 1]), nuc), acc);
+                    acc = fma2(mE[j], add2(make_float2(uu[i + 1][2 * j + 2], uu[i + 1][2 * j + 3]), nuc), acc);
+                    const float2 res = mul2(w2[i][j], acc);
+                    r2[i][j] = res;
+                    rr0 = fmaf(res.x, res.x, fmaf(res.y, res.y, rr0));
+                    const bool o_x = (ob >> (i * PX + 2 * j)) & 1u, o_y = (ob >> (i * PX + 2 * j + 1)) & 1u;
+                    s2 = fmaf(o_x ? res.x : 0.f, res.x, fmaf(o_y ? res.y : 0.f, res.y, s2));
                 }
         }
-        s2 = tile_sum<CF>(s2, red[0], wt, lane);
+        // ---- k CG steps from v = 0 (Saad, the CG algorithm of Ch. 6) --------------
+        float2 v2[PY][NP], p2[PY][NP], q2[PY][NP];
+        float rr;
+        {
+#pragma unroll
+            for (int i = 0; i < PY; ++i)
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    v2[i][j] = make_float2(0.f, 0.f);
+                    p2[i][j] = r2[i][j];
+                }
+            if constexpr (NW > 1) {   // boundary rows of r (= p) for the neighbouring warps
+                if (ly == 0)
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        xch[0][wt][rx0 + 2 * j] = r2[0][j].x;
+                        xch[0][wt][rx0 + 2 * j + 1] = r2[0][j].y;
+                    }
+                if (ly == LY - 1)
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        xch[1][wt][rx0 + 2 * j] = r2[PY - 1][j].x;
+                        xch[1][wt][rx0 + 2 * j + 1] = r2[PY - 1][j].y;
+                    }
+            }
+            // owned ||r||^2 and the initial (r, r) in one butterfly (a barrier when NW > 1)
+            const float2 both = tile_sum2<CF>(make_float2(s2, rr0), red[0], red[1], wt, lane);
+            s2 = both.x;
+            rr = both.y;
+        }
         if (c != cur_c) {   // tiles of one CTA visit channels in increasing order
             if (tt == 0) {
                 if (cur_c >= 0) part[(size_t)cur_c * slots + blockIdx.x] = acc_c;
@@ -289,53 +405,19 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
             acc_c = 0.f;
         }
         acc_c += s2;
-
-        // ---- local operator coefficients -----------------------------------------
-        float2 rpn[PY];     // -(vertical part of dd), both halves equal
-        float2 cpn[NP];     // -(horizontal part of dd)
-        float2 w2[PY][NP];  // 1 on unknown in-block pixels, else 0
-#pragma unroll
-        for (int i = 0; i < PY; ++i) {
-            const int ry = ry0 + i, y = y0 + ry;
-            const float up = ry > 0 ? 1.f : (y > 0 ? pr : 0.f);
-            const float dn = ry < th - 1 ? 1.f : (y < H - 1 ? pr : 0.f);
-            rpn[i] = make_float2(-(up + dn), -(up + dn));
-        }
+        // p rows of the neighbouring warps next to this warp's top / bottom row
+        float2 nbN[NP], nbS[NP];
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            float v[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int rx = rx0 + 2 * j + e, x = x0 + rx;
-                const float lf = rx > 0 ? 1.f : (x > 0 ? pr : 0.f);
-                const float rt = rx < tw - 1 ? 1.f : (x < W - 1 ? pr : 0.f);
-                v[e] = -(lf + rt);
+            nbN[j] = make_float2(0.f, 0.f);
+            nbS[j] = make_float2(0.f, 0.f);
+            if constexpr (NW > 1) {
+                if (ly == 0 && wt > 0) nbN[j] = make_float2(xch[1][wt - 1][rx0 + 2 * j], xch[1][wt - 1][rx0 + 2 * j + 1]);
+                if (ly == LY - 1 && wt < NW - 1)
+                    nbS[j] = make_float2(xch[0][wt + 1][rx0 + 2 * j], xch[0][wt + 1][rx0 + 2 * j + 1]);
             }
-            cpn[j] = make_float2(v[0], v[1]);
         }
-#pragma unroll
-        for (int i = 0; i < PY; ++i)
-#pragma unroll
-            for (int j = 0; j < NP; ++j)
-                w2[i][j] = make_float2(((kb >> (i * PX + 2 * j)) & 1u) ? 0.f : 1.f,
-                                       ((kb >> (i * PX + 2 * j + 1)) & 1u) ? 0.f : 1.f);
-
-        // ---- k CG steps from v = 0 (Saad, the CG algorithm of Ch. 6) --------------
-        float2 v2[PY][NP], p2[PY][NP], q2[PY][NP];
-        float rr;
-        {
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int i = 0; i < PY; ++i)
-#pragma unroll
-                for (int j = 0; j < NP; ++j) {
-                    v2[i][j] = make_float2(0.f, 0.f);
-                    p2[i][j] = r2[i][j];
-                    acc = fma2(r2[i][j], r2[i][j], acc);
-                }
-            rr = tile_sum<CF>(acc.x + acc.y, red[1], wt, lane);
-        }
-        for (int kk = 0; kk < a.k; ++kk) {
+        for (int kk = 0; kk < kcg; ++kk) {
             if (!(rr > 0.f)) break;
             float pW[PY], pE[PY];
 #pragma unroll
@@ -351,43 +433,13 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
                 pS[j].x = __shfl_down_sync(FULL, p2[0][j].x, LX);
                 pS[j].y = __shfl_down_sync(FULL, p2[0][j].y, LX);
             }
-            if constexpr (NW > 1) {
-                if (ly == 0) {
+            if (ly == 0) {
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        xch[0][wt][rx0 + 2 * j] = p2[0][j].x;
-                        xch[0][wt][rx0 + 2 * j + 1] = p2[0][j].y;
-                    }
-                }
-                if (ly == LY - 1) {
+                for (int j = 0; j < NP; ++j) pN[j] = nbN[j];
+            }
+            if (ly == LY - 1) {
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        xch[1][wt][rx0 + 2 * j] = p2[PY - 1][j].x;
-                        xch[1][wt][rx0 + 2 * j + 1] = p2[PY - 1][j].y;
-                    }
-                }
-                __syncthreads();
-                if (ly == 0) {
-#pragma unroll
-                    for (int j = 0; j < NP; ++j)
-                        pN[j] = wt > 0 ? make_float2(xch[1][wt - 1][rx0 + 2 * j], xch[1][wt - 1][rx0 + 2 * j + 1])
-                                       : make_float2(0.f, 0.f);
-                }
-                if (ly == LY - 1) {
-#pragma unroll
-                    for (int j = 0; j < NP; ++j)
-                        pS[j] = wt < NW - 1 ? make_float2(xch[0][wt + 1][rx0 + 2 * j], xch[0][wt + 1][rx0 + 2 * j + 1])
-                                            : make_float2(0.f, 0.f);
-                }
-            } else {
-                if (ly == 0) {
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) pN[j] = make_float2(0.f, 0.f);
-                }
-                if (ly == LY - 1) {
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) pS[j] = make_float2(0.f, 0.f);
-                }
+                for (int j = 0; j < NP; ++j) pS[j] = nbS[j];
             }
             // q' = -(A_i p), and (p, q'); two independent accumulator chains
             float2 pqa = make_float2(0.f, 0.f), pqb = make_float2(0.f, 0.f);
@@ -419,6 +471,20 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
                     r2[i][j] = fma2(a2, q2[i][j], r2[i][j]);     // r - alpha A p
                     if (i & 1) rrb = fma2(r2[i][j], r2[i][j], rrb); else rra = fma2(r2[i][j], r2[i][j], rra);
                 }
+            if constexpr (NW > 1) {   // new boundary rows of r for the neighbouring warps
+                if (ly == 0)
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        xch[0][wt][rx0 + 2 * j] = r2[0][j].x;
+                        xch[0][wt][rx0 + 2 * j + 1] = r2[0][j].y;
+                    }
+                if (ly == LY - 1)
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        xch[1][wt][rx0 + 2 * j] = r2[PY - 1][j].x;
+                        xch[1][wt][rx0 + 2 * j + 1] = r2[PY - 1][j].y;
+                    }
+            }
             const float rr_new = tile_sum<CF>((rra.x + rra.y) + (rrb.x + rrb.y), red3[kk & 1][1], wt, lane);
             const float beta = rr_new / rr;
             const float2 b2 = make_float2(beta, beta);
@@ -426,11 +492,22 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
             for (int i = 0; i < PY; ++i)
 #pragma unroll
                 for (int j = 0; j < NP; ++j) p2[i][j] = fma2(b2, p2[i][j], r2[i][j]);
+            if constexpr (NW > 1) {   // the neighbours' new p rows, formed exactly as they form them
+                if (ly == 0 && wt > 0)
+#pragma unroll
+                    for (int j = 0; j < NP; ++j)
+                        nbN[j] = fma2(b2, nbN[j], make_float2(xch[1][wt - 1][rx0 + 2 * j], xch[1][wt - 1][rx0 + 2 * j + 1]));
+                if (ly == LY - 1 && wt < NW - 1)
+#pragma unroll
+                    for (int j = 0; j < NP; ++j)
+                        nbS[j] = fma2(b2, nbS[j], make_float2(xch[0][wt + 1][rx0 + 2 * j], xch[0][wt + 1][rx0 + 2 * j + 1]));
+            }
             rr = rr_new;
         }
 
         // ---- restricted add-back on the owned core -------------------------------
-        T* __restrict__ uout = a.u_out + (size_t)c * a.plane;
+        T* __restrict__ uout = u_out + (size_t)c * a.plane;
+        if (!probe)
 #pragma unroll
         for (int i = 0; i < PY; ++i)
 #pragma unroll
@@ -441,7 +518,8 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
                     uout[(size_t)(y0 + ry0 + i) * P + (x0 + rx0 + j)] = from_f<T>(to_f(U[o]) + v);
                 }
             }
-        __syncthreads();   // the staged tile may now be refilled
+        if constexpr (NW > 1) __syncthreads();   // the staged tile may now be refilled
+        else __syncwarp();
     }
     if (tt == 0 && !s_ok) {
         // a copy timed out: wait (bounded) for the other buffer's copy before leaving
@@ -477,16 +555,27 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_consta
                     best_ratio = fmin(best_ratio, prev > 0.0 ? sqrt(v / prev) : 0.0);
                 }
                 sp.norms2[c] = v;
-                sp.norms2[a.C + c] = v;
+                if (!probe) sp.norms2[a.C + c] = v;
             }
         }
         if (lane == 0) {
+            int* const state = sp.state;
             if (bad) { flag[0] = 2; flag[1] = sp.sweep_index; }
             else if (worst <= sp.tol) { flag[0] = 1; flag[1] = sp.sweep_index; }
             else if (sp.stall > 0.0 && sp.sweep_index > 0 && best_ratio > sp.stall) {
                 flag[0] = 3;
                 flag[1] = sp.sweep_index;
+            } else if (!probe) {
+                // the output of this sweep becomes the current iterate; probe it
+                // next if the last residual ratio predicts it meets tol
+                const double prev_worst = sp.norms2[2 * a.C];
+                state[0] = cur ^ 1;
+                state[1] += 1;
+                state[2] = (sp.tol > 0.0 && prev_worst > 0.0 && worst * (worst / prev_worst) <= sp.tol) ? 1 : 0;
+            } else {
+                state[2] = 0;   // the probe failed: sweep the same iterate in full
             }
+            if (!probe) sp.norms2[2 * a.C] = worst;
             flag[3] = 0;   // ticket ready for the next launch
         }
     }
@@ -558,11 +647,11 @@ int persistent_grid(bool has_g) {
 }
 
 template <class CF, typename T>
-cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const CUtensorMap& mu, const CUtensorMap* mg,
-                      void* u_out, const uint32_t* tmask, const SweepStop& stop, float p_robin, int k,
-                      cudaStream_t st) {
+cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const SweepPair& pr2, const CUtensorMap* mg,
+                      const uint32_t* tmask, const SweepStop& stop, float p_robin, int k, cudaStream_t st) {
     SweepArgs<T> a;
-    a.u_out = static_cast<T*>(u_out);
+    a.u_buf[0] = static_cast<T*>(pr2.u[0]);
+    a.u_buf[1] = static_cast<T*>(pr2.u[1]);
     a.tmask = tmask;
     a.stop = stop;
     a.H = g.H; a.W = g.W; a.pitch = g.pitch; a.C = C;
@@ -575,21 +664,22 @@ cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const CUtensorM
     const long long grid = std::min<long long>(std::min<long long>(work, persistent_grid<CF, T>(a.has_g)),
                                                (long long)stop.slots);
     const size_t smem = sweep_smem_bytes<CF, T>(a.has_g);
-    oras_sweep_kernel<CF, T><<<(unsigned)grid, CF::NT, smem, st>>>(mu, mg ? *mg : mu, a);
+    oras_sweep_kernel<CF, T><<<(unsigned)grid, CF::NT, smem, st>>>(*pr2.map[0], *pr2.map[1], mg ? *mg : *pr2.map[0],
+                                                                    a);
     return cudaGetLastError();
 }
 
 template <class CF>
-cudaError_t sweep_store(Store s, const TileGeom& g, int C, long long plane, const CUtensorMap& mu,
-                        const CUtensorMap* mg, void* u_out, const uint32_t* tmask, const SweepStop& stop,
-                        float p_robin, int k, cudaStream_t st) {
+cudaError_t sweep_store(Store s, const TileGeom& g, int C, long long plane, const SweepPair& pr2,
+                        const CUtensorMap* mg, const uint32_t* tmask, const SweepStop& stop, float p_robin, int k,
+                        cudaStream_t st) {
     switch (s) {
         case Store::F32:
-            return sweep_cfg<CF, float>(g, C, plane, mu, mg, u_out, tmask, stop, p_robin, k, st);
+            return sweep_cfg<CF, float>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, st);
         case Store::F16:
-            return sweep_cfg<CF, __half>(g, C, plane, mu, mg, u_out, tmask, stop, p_robin, k, st);
+            return sweep_cfg<CF, __half>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, st);
         case Store::BF16:
-            return sweep_cfg<CF, __nv_bfloat16>(g, C, plane, mu, mg, u_out, tmask, stop, p_robin, k, st);
+            return sweep_cfg<CF, __nv_bfloat16>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -639,10 +729,11 @@ int axis_blocks(int n, int b, int o) {
     return cnt < 1 ? 1 : cnt;
 }
 
-TileGeom make_geom(int H, int W, int pitch, int b, int o) {
+TileGeom make_geom(int H, int W, int pitch, int b, int o, int nw) {
     TileGeom g;
     g.H = H; g.W = W; g.pitch = pitch;
     g.b = b; g.o = o; g.s = b - o; g.half_o = o / 2;
+    g.nw = nw > 0 ? nw : default_tile_warps(b);
     g.ntx = axis_blocks(W, b, o);
     g.nty = axis_blocks(H, b, o);
     g.ntiles = g.ntx * g.nty;
@@ -651,33 +742,35 @@ TileGeom make_geom(int H, int W, int pitch, int b, int o) {
 
 bool block_supported(int b) { return b == 16 || b == 32 || b == 64; }
 
-int tile_threads(int b) {
-    switch (b) {
-        case 16: return Cfg16::NT;
-        case 32: return Cfg32::NT;
-        case 64: return Cfg64::NT;
-    }
-    return 0;
+int default_tile_warps(int b) { return b == 64 ? 4 : 1; }
+
+bool tile_warps_supported(int b, int nw) {
+    return with_cfg(b, nw, [](auto) { return cudaSuccess; }) == cudaSuccess;
 }
 
-size_t tmask_words(const TileGeom& g) { return (size_t)g.ntiles * 2 * tile_threads(g.b); }
+int tile_threads(int b, int nw) {
+    int nt = 0;
+    with_cfg(b, nw, [&](auto cfg) {
+        nt = decltype(cfg)::NT;
+        return cudaSuccess;
+    });
+    return nt;
+}
+
+size_t tmask_words(const TileGeom& g) { return (size_t)g.ntiles * 2 * tile_threads(g.b, g.nw); }
 
 cudaError_t make_tile_map(CUtensorMap* out, Store s, const void* base, int H, int W, int pitch, int C, int b) {
     int bx = 0, by = 0;
-    auto pick = [&](auto cfg) {
+    const cudaError_t e = with_cfg(b, default_tile_warps(b), [&](auto cfg) {
         using CF = decltype(cfg);
         switch (s) {
             case Store::F32: box_dims<CF, float>(&bx, &by); break;
             case Store::F16: box_dims<CF, __half>(&bx, &by); break;
             case Store::BF16: box_dims<CF, __nv_bfloat16>(&bx, &by); break;
         }
-    };
-    switch (b) {
-        case 16: pick(Cfg16{}); break;
-        case 32: pick(Cfg32{}); break;
-        case 64: pick(Cfg64{}); break;
-        default: return cudaErrorInvalidValue;
-    }
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     auto fn = encode_fn();
     if (fn == nullptr) return cudaErrorNotSupported;
     const size_t es = store_bytes(s);
@@ -696,36 +789,24 @@ cudaError_t make_tile_map(CUtensorMap* out, Store s, const void* base, int H, in
 
 cudaError_t launch_build_tmask(const TileGeom& g, const uint8_t* mask, int mp, uint32_t* tmask,
                                cudaStream_t st) {
-    switch (g.b) {
-        case 16: return tmask_cfg<Cfg16>(g, mask, mp, tmask, st);
-        case 32: return tmask_cfg<Cfg32>(g, mask, mp, tmask, st);
-        case 64: return tmask_cfg<Cfg64>(g, mask, mp, tmask, st);
-    }
-    return cudaErrorInvalidValue;
+    return with_cfg(g.b, g.nw, [&](auto cfg) { return tmask_cfg<decltype(cfg)>(g, mask, mp, tmask, st); });
 }
 
 cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsigned long long* out,
                                  cudaStream_t st) {
-    switch (g.b) {
-        case 16: return count_cfg<Cfg16>(g, tmask, out, st);
-        case 32: return count_cfg<Cfg32>(g, tmask, out, st);
-        case 64: return count_cfg<Cfg64>(g, tmask, out, st);
-    }
-    return cudaErrorInvalidValue;
+    return with_cfg(g.b, g.nw, [&](auto cfg) { return count_cfg<decltype(cfg)>(g, tmask, out, st); });
 }
 
-cudaError_t launch_sweep(Store s, const TileGeom& g, int C, long long plane, const CUtensorMap& map_in,
-                         const CUtensorMap* map_g, void* u_out, const uint32_t* tmask, const SweepStop& stop,
-                         float p_robin, int k, cudaStream_t st) {
+cudaError_t launch_sweep(Store s, const TileGeom& g, int C, long long plane, const SweepPair& pair,
+                         const CUtensorMap* map_g, const uint32_t* tmask, const SweepStop& stop, float p_robin,
+                         int k, cudaStream_t st) {
     if (stop.slots < 1 || stop.partial == nullptr || stop.flag == nullptr || stop.norms2 == nullptr ||
-        stop.ref == nullptr)
+        stop.ref == nullptr || stop.state == nullptr || pair.map[0] == nullptr || pair.map[1] == nullptr ||
+        pair.u[0] == nullptr || pair.u[1] == nullptr)
         return cudaErrorInvalidValue;
-    switch (g.b) {
-        case 16: return sweep_store<Cfg16>(s, g, C, plane, map_in, map_g, u_out, tmask, stop, p_robin, k, st);
-        case 32: return sweep_store<Cfg32>(s, g, C, plane, map_in, map_g, u_out, tmask, stop, p_robin, k, st);
-        case 64: return sweep_store<Cfg64>(s, g, C, plane, map_in, map_g, u_out, tmask, stop, p_robin, k, st);
-    }
-    return cudaErrorInvalidValue;
+    return with_cfg(g.b, g.nw, [&](auto cfg) {
+        return sweep_store<decltype(cfg)>(s, g, C, plane, pair, map_g, tmask, stop, p_robin, k, st);
+    });
 }
 
 }  // namespace dd

@@ -83,22 +83,27 @@ def test_residual_norms_match_oracle():
 
 
 SWEEP_CASES = [
-    # H, W, C, block, overlap, k, p_robin, density, pattern
-    (64, 64, 1, 32, 4, 8, 0.3, 0.05, "uniform"),
-    (100, 83, 2, 32, 6, 16, 0.25, 0.03, "edge"),       # ragged last blocks
-    (45, 70, 1, 16, 3, 6, 1.0, 0.08, "uniform"),       # RAS, odd overlap
-    (150, 140, 1, 64, 4, 12, 0.3, 0.04, "edge"),       # multi-warp tiles
-    (20, 24, 1, 32, 6, 5, 0.3, 0.1, "uniform"),        # image smaller than a block
+    # H, W, C, block, overlap, k, p_robin, density, pattern, warps per block tile
+    (64, 64, 1, 32, 4, 8, 0.3, 0.05, "uniform", 1),
+    (100, 83, 2, 32, 6, 16, 0.25, 0.03, "edge", 1),       # ragged last blocks
+    (100, 83, 2, 32, 6, 16, 0.25, 0.03, "edge", 2),       # two warps per block
+    (100, 83, 2, 32, 3, 16, 0.15, 0.03, "edge", 4),       # four warps per block
+    (45, 70, 1, 16, 3, 6, 1.0, 0.08, "uniform", 1),       # RAS, odd overlap
+    (150, 140, 1, 64, 4, 12, 0.3, 0.04, "edge", 4),       # multi-warp tiles
+    (150, 140, 1, 64, 5, 12, 0.3, 0.04, "edge", 8),
+    (20, 24, 1, 32, 6, 5, 0.3, 0.1, "uniform", 1),        # image smaller than a block
+    (20, 24, 1, 32, 6, 5, 0.3, 0.1, "uniform", 4),
 ]
 
 
-@pytest.mark.parametrize("H,W,C,b,o,k,p,d,pat", SWEEP_CASES)
-def test_single_and_triple_sweep_match_oracle(H, W, C, b, o, k, p, d, pat):
+@pytest.mark.parametrize("H,W,C,b,o,k,p,d,pat,nw", SWEEP_CASES)
+def test_single_and_triple_sweep_match_oracle(H, W, C, b, o, k, p, d, pat, nw):
     """Max error bound 2e-3: k FP32 CG steps on |v| <= 255 with local
     condition numbers <= ~100 lose ~k * kappa * 2^-24 * 255 <= 1e-3."""
     f, m = synth.make_frame(H, W, C, d, pat, 17)
     u0 = ref.initial_guess(f, m)
-    with Inpainter(m, f, block=b, overlap=o, local_cg_iters=k, robin_p=p, levels=1, precision="fp32") as ip:
+    with Inpainter(m, f, block=b, overlap=o, local_cg_iters=k, robin_p=p, levels=1, precision="fp32",
+                   tile_warps=nw) as ip:
         ip.set_iterate(u0.astype(np.float32))
         norms = ip.sweep(1)
         u1 = ip.get_iterate().cpu().numpy()
