@@ -18,6 +18,8 @@ def main():
     ap.add_argument("--block", type=int, default=None)
     ap.add_argument("--overlap", type=int, default=None)
     ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--robin", type=float, default=0.0)
+    ap.add_argument("--tile-warps", type=int, default=0)
     ap.add_argument("--sweeps", type=int, default=3)
     a = ap.parse_args()
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -31,7 +33,8 @@ def main():
     dev = torch.device("cuda", 0)
     fd, md = torch.as_tensor(f).to(dev), torch.as_tensor(m).to(dev)
     with Inpainter(md, fd, device=dev, block=a.block or w.block, overlap=a.overlap if a.overlap is not None
-                   else w.overlap, local_cg_iters=a.k, levels=1, precision=a.precision) as ip:
+                   else w.overlap, local_cg_iters=a.k, levels=1, precision=a.precision, robin_p=a.robin,
+                   tile_warps=a.tile_warps) as ip:
         ip.set_iterate(fd * (md != 0))
         for _ in range(a.sweeps):
             ip.sweep(1)
