@@ -51,6 +51,7 @@ extern "C" {
 #define DD_ENUMERIC       5  /* NaN or Inf met in a residual norm */
 #define DD_ECUDA          6  /* a CUDA runtime call failed (message: dd_last_error) */
 #define DD_ETIMEOUT       7  /* a bounded device-side wait gave up */
+#define DD_EAGAIN         8  /* asynchronous work not finished yet (dd_inpaint_query) */
 
 /* multilevel modes */
 #define DD_ML_CASCADE     0  /* coarse-to-fine initialisation (Sec. 4) */
@@ -63,6 +64,7 @@ extern "C" {
 #define DD_PREC_BF16_REF  3  /* BF16 storage inner solves + FP64 outer residual correction */
 
 typedef struct dd_inpaint *dd_handle;
+typedef struct dd_batch *dd_batch_handle;
 
 typedef struct dd_params {
     int    block;            /* block side in pixels: 16, 32 or 64 (default 32, Sec. 4) */
@@ -151,6 +153,69 @@ int dd_inpaint_set_data(dd_handle h, const uint8_t *mask, const float *values, i
 
 /* Copy the statistics of the last solve.  Errors: DD_EINVAL. */
 int dd_inpaint_stats(dd_handle h, dd_stats *out);
+
+/* ---------------------------------------------------------------------------
+ * Asynchronous use (precision DD_PREC_FP32 only).  The solve is split into an
+ * enqueue that returns at once and a finish that waits for the result, so one
+ * host thread can keep several handles (on several streams) busy and data
+ * copies can overlap solves.  Sec. 3-4 of the paper (the same method).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * As dd_inpaint_set_data, but only enqueued on stream (host inputs must be
+ * pinned for the copy to be asynchronous).  The empty-mask test is reported
+ * by the next dd_inpaint_solve_finish (DD_EEMPTYMASK).  Errors: DD_EINVAL
+ * (NULL pointers, a solve in flight), DD_ECUDA.
+ */
+int dd_inpaint_set_data_async(dd_handle h, const uint8_t *mask, const float *values, int keep_iterate,
+                              void *stream);
+
+/*
+ * Enqueue a solve to relative residual tol on stream: the multilevel
+ * initialisation, up to 16 fine sweeps under the device stop test, the output
+ * of the resolved iterate to u_out (DEVICE, C*H*W floats) and its residual.
+ * Returns without waiting.  Errors: DD_EINVAL (not FP32, a solve in flight),
+ * DD_EEMPTYMASK, DD_ECUDA.
+ */
+int dd_inpaint_solve_async(dd_handle h, float *u_out, double tol, void *stream);
+
+/* DD_OK if the enqueued solve's device work is done, DD_EAGAIN if not (or if
+ * it was started by a batch launch), DD_EINVAL if none is in flight. */
+int dd_inpaint_query(dd_handle h);
+
+/*
+ * Wait for the enqueued solve and return its status as dd_inpaint_solve would.
+ * If the first 16 fine sweeps did not reach tol, the remaining sweeps run here
+ * on stream under host control and u_out is rewritten.
+ */
+int dd_inpaint_solve_finish(dd_handle h, void *stream);
+
+/*
+ * Batched solves in one CUDA graph: the FP32 solves of n handles, each on its
+ * own forked stream, are captured once and replayed by dd_batch_launch, so
+ * frames of different sizes run concurrently and the whole batch is one graph
+ * launch.  handles: n distinct FP32 handles; u_out[i]: DEVICE output of handle
+ * i (C*H*W floats, fixed for the life of the batch); tol baked into the graph.
+ * Each launch solves the data currently loaded in every handle, starting from
+ * the multilevel initialisation.  kernels_per_launch (may be NULL) receives
+ * the number of kernels in the graph.  Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA.
+ */
+int dd_batch_create(int n, const dd_handle *handles, float *const *u_out, double tol, dd_batch_handle *out,
+                    long long *kernels_per_launch);
+
+/* Launch the batch graph on stream (returns at once).  Errors: DD_EINVAL
+ * (previous launch not finished), DD_EEMPTYMASK, DD_ECUDA. */
+int dd_batch_launch(dd_batch_handle b, void *stream);
+
+/*
+ * Wait for the launch and finish every handle's solve (unconverged ones
+ * continue on stream).  status (may be NULL): n per-handle codes.  Returns the
+ * first non-DD_OK code, else DD_OK.  Statistics are then per handle.
+ */
+int dd_batch_finish(dd_batch_handle b, void *stream, int *status);
+
+/* Release the batch (waits for a launch in flight).  NULL-safe. */
+int dd_batch_destroy(dd_batch_handle b);
 
 /* ---------------------------------------------------------------------------
  * Step-level entry points (one step of the method on caller device buffers;

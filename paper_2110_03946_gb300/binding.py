@@ -14,7 +14,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdd_inpaint.so")
 
-DD_OK, DD_EINVAL, DD_EEMPTYMASK, DD_ENOMEM, DD_ENOTCONVERGED, DD_ENUMERIC, DD_ECUDA, DD_ETIMEOUT = range(8)
+DD_OK, DD_EINVAL, DD_EEMPTYMASK, DD_ENOMEM, DD_ENOTCONVERGED, DD_ENUMERIC, DD_ECUDA, DD_ETIMEOUT, DD_EAGAIN = range(9)
 DD_ML_CASCADE, DD_ML_CORRECTION = 0, 1
 DD_PREC_FP32, DD_PREC_FP32_REF, DD_PREC_FP16_REF, DD_PREC_BF16_REF = 0, 1, 2, 3
 DD_MAX_STAT_CHANNELS = 16
@@ -26,6 +26,8 @@ EXPORTS = (
     "dd_inpaint_create", "dd_inpaint_solve", "dd_inpaint_destroy", "dd_inpaint_set_data",
     "dd_inpaint_stats", "dd_inpaint_set_iterate", "dd_inpaint_get_iterate", "dd_inpaint_sweep",
     "dd_restrict", "dd_prolong", "dd_residual_norms", "dd_inpaint_solve_static",
+    "dd_inpaint_set_data_async", "dd_inpaint_solve_async", "dd_inpaint_query", "dd_inpaint_solve_finish",
+    "dd_batch_create", "dd_batch_launch", "dd_batch_finish", "dd_batch_destroy",
 )
 
 
@@ -82,6 +84,15 @@ def load(path: str | None = None):
         "dd_prolong": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P]),
         "dd_residual_norms": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
         "dd_inpaint_solve_static": (_I, [_I, _I, _I, _P, _P, _P, ctypes.POINTER(dd_params), _D, _P]),
+        "dd_inpaint_set_data_async": (_I, [_P, _P, _P, _I, _P]),
+        "dd_inpaint_solve_async": (_I, [_P, _P, _D, _P]),
+        "dd_inpaint_query": (_I, [_P]),
+        "dd_inpaint_solve_finish": (_I, [_P, _P]),
+        "dd_batch_create": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, ctypes.POINTER(_P),
+                                 ctypes.POINTER(ctypes.c_longlong)]),
+        "dd_batch_launch": (_I, [_P, _P]),
+        "dd_batch_finish": (_I, [_P, _P, ctypes.POINTER(_I)]),
+        "dd_batch_destroy": (_I, [_P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -193,3 +204,45 @@ def dd_residual_norms(H, W, C, mask_ptr, f_ptr, u_ptr, stream=None):
     r = (ctypes.c_double * C)()
     rc = load().dd_residual_norms(H, W, C, mask_ptr, f_ptr, u_ptr, n, r, _stream(stream))
     return rc, list(n), list(r)
+
+
+def dd_inpaint_set_data_async(h, mask_ptr: int, values_ptr: int, keep_iterate: int, stream=None) -> int:
+    return load().dd_inpaint_set_data_async(h, mask_ptr, values_ptr, int(keep_iterate), _stream(stream))
+
+
+def dd_inpaint_solve_async(h, u_out_ptr: int, tol: float, stream=None) -> int:
+    return load().dd_inpaint_solve_async(h, u_out_ptr, tol, _stream(stream))
+
+
+def dd_inpaint_query(h) -> int:
+    return load().dd_inpaint_query(h)
+
+
+def dd_inpaint_solve_finish(h, stream=None) -> int:
+    return load().dd_inpaint_solve_finish(h, _stream(stream))
+
+
+def dd_batch_create(handles, out_ptrs, tol: float):
+    """Returns (code, batch handle, kernels per launch)."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    outs = (ctypes.c_void_p * n)(*out_ptrs)
+    b = ctypes.c_void_p()
+    k = ctypes.c_longlong(0)
+    rc = load().dd_batch_create(n, hs, outs, tol, ctypes.byref(b), ctypes.byref(k))
+    return rc, b, k.value
+
+
+def dd_batch_launch(b, stream=None) -> int:
+    return load().dd_batch_launch(b, _stream(stream))
+
+
+def dd_batch_finish(b, n: int, stream=None):
+    """Returns (code, list of n per-handle codes)."""
+    st = (ctypes.c_int * n)()
+    rc = load().dd_batch_finish(b, _stream(stream), st)
+    return rc, list(st)
+
+
+def dd_batch_destroy(b) -> int:
+    return load().dd_batch_destroy(b)

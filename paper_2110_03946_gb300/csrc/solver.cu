@@ -104,6 +104,15 @@ struct dd_inpaint {
     double* h_small = nullptr;      // 3*C doubles scratch
     int* h_flag = nullptr;
     int* h_state = nullptr;         // 4 ints per level
+    double* h_ref = nullptr;        // C: fine-level reference norms read back with a solve
+    unsigned long long* h_cnt = nullptr;   // [0] unknown block pixels, [1] known pixels
+    // asynchronous solve in flight (dd_inpaint_solve_async / _finish)
+    bool pending = false;
+    bool pending_cascaded = false;
+    bool counts_pending = false;    // set_data_async: pixel counts not read yet
+    bool ev_recorded = false;       // ev0/ev1 bracket the pending solve
+    float* pending_out = nullptr;
+    double pending_tol = 0.0;
     std::vector<void*> allocs;
     size_t bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -178,7 +187,7 @@ float robin_default(int b, int o) {
 // work is enqueued on st; the only host synchronisation reads back the pixel
 // counts and reference norms once at the end.  Returns DD_EEMPTYMASK if no
 // pixel is known.
-int load_data(dd_inpaint* h, const uint8_t* mask, const float* values, cudaStream_t st) {
+int load_data(dd_inpaint* h, const uint8_t* mask, const float* values, cudaStream_t st, bool sync = true) {
     Level& L0 = h->lv[0];
     const size_t npx = (size_t)h->H * h->W;
     const float* dvals = values;
@@ -217,10 +226,15 @@ int load_data(dd_inpaint* h, const uint8_t* mask, const float* values, cudaStrea
         DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, nblk, h->C, h->res_out + (size_t)l * h->C, st));
         DD_LAUNCH(h, dd::launch_sqrt_sums(h->res_out + (size_t)l * h->C, L.ref_d, h->C, st));
     }
-    unsigned long long cnt[2] = {0, 0};
-    DD_CK(cudaMemcpyAsync(cnt, h->count_d, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if (!sync) {   // counts and reference norms are read back with the next solve
+        h->counts_pending = true;
+        return DD_OK;
+    }
+    h->counts_pending = false;
     DD_CK(cudaMemcpyAsync(h->h_res, h->res_out, sizeof(double2) * h->C * nl, cudaMemcpyDeviceToHost, st));
     DD_CK(cudaStreamSynchronize(st));
+    const unsigned long long cnt[2] = {h->h_cnt[0], h->h_cnt[1]};
     h->local_unknowns = (long long)cnt[0];
     for (int l = 0; l < nl; ++l) {
         Level& L = h->lv[l];
@@ -433,7 +447,132 @@ void take_level_stats(dd_inpaint* h) {
     for (size_t l = 1; l < h->lv.size(); ++l) h->stats.sweeps_total += h->h_state[4 * l + 1];
 }
 
+// FP32 path, part 1: enqueue the cascade, the first fine chunk, the output of
+// the resolved buffer, its residual and the read-back of everything the host
+// needs.  No host synchronisation.  capture = 1 inside a stream capture
+// (no events, no timing).
+int fp32_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool capture) {
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    h->stats.channels = h->C;
+    h->stats.device_bytes = h->bytes;
+    const int nl = (int)h->lv.size();
+    Level& F = h->lv[0];
+    h->ev_recorded = !capture;
+    if (!capture) DD_CK(cudaEventRecord(h->ev0, st));
+    h->pending_cascaded = !h->warm;
+    if (!h->warm) {
+        DD_TRY(cascade(h, st));
+    } else if (h->cur != 0) {
+        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[1], F.P, F.plane(), F.u[0], F.P, F.plane(), st));
+        h->cur = 0;
+    }
+    h->warm = false;
+    const long long dense_plane = (long long)F.H * F.W;
+    const int n1 = std::min(dd_inpaint::kFirst, h->prm.max_sweeps);
+    DD_TRY(enqueue_sweeps(h, F, n1, tol, st, h->prm.timing != 0 && !capture));
+    DD_LAUNCH(h, dd::launch_copy2d_sel(F.H, F.W, h->C, F.u[0], F.u[1], F.state_d, F.P, F.plane(), u_out, F.W,
+                                       dense_plane, st));
+    DD_TRY(residual_of(h, u_out, F.W, dense_plane, st));
+    DD_CK(cudaMemcpyAsync(h->h_state, F.state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    for (int l = 1; l < nl; ++l)
+        DD_CK(cudaMemcpyAsync(h->h_state + 4 * l, h->lv[l].state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_ref, F.ref_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if (!capture) DD_CK(cudaEventRecord(h->ev1, st));
+    h->pending = true;
+    h->pending_out = u_out;
+    h->pending_tol = tol;
+    return DD_OK;
+}
+
+// FP32 path, part 2: wait for the enqueued work, read the result and, if the
+// first chunk did not reach tol (or the FP32 fused estimate was optimistic),
+// continue under host control on st.
+int fp32_finish(dd_inpaint* h, cudaStream_t st) {
+    if (!h->pending) { set_error("no solve in flight"); return DD_EINVAL; }
+    h->pending = false;
+    Level& F = h->lv[0];
+    const int nl = (int)h->lv.size();
+    float* u_out = h->pending_out;
+    const double tol = h->pending_tol;
+    if (h->ev_recorded) DD_CK(cudaEventSynchronize(h->ev1));
+    else DD_CK(cudaStreamSynchronize(st));
+    // pixel counts and reference norms of the data this solve used
+    h->local_unknowns = (long long)h->h_cnt[0];
+    h->stats.local_unknowns = h->local_unknowns;
+    if (h->counts_pending) {
+        h->counts_pending = false;
+        if (h->h_cnt[1] == 0) { h->valid = false; set_error("empty mask"); return DD_EEMPTYMASK; }
+    }
+    F.ref.assign(h->h_ref, h->h_ref + h->C);
+    if (h->h_flag[2] != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
+    if (h->pending_cascaded) take_level_stats(h);
+    const int status = h->h_state[2], applied = h->h_state[1];
+    if (status == 2) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
+    const int n1 = std::min(dd_inpaint::kFirst, h->prm.max_sweeps);
+    if (h->prm.timing != 0 && h->ev_recorded) {
+        for (int i = 0; i < applied && i < n1; ++i) {
+            float ms = 0.f;
+            DD_CK(cudaEventElapsedTime(&ms, h->sw_ev[2 * i], h->sw_ev[2 * i + 1]));
+            h->stats.fine_sweep_ms += ms;
+            h->stats.fine_sweep_launches += 1;
+        }
+    }
+    int fine_sweeps = applied;
+    h->cur = h->h_state[0];
+    std::vector<double> rel, rmax, rnorm;
+    DD_TRY(rel_from_h_res(h, rel, rmax, rnorm));
+    double worst = *std::max_element(rel.begin(), rel.end());
+    bool converged = false;
+    if (status == 1 && worst <= tol) {
+        converged = true;
+    } else {
+        double target = status == 1 ? tol * 0.5 : tol;
+        for (int attempt = 0; attempt < 4 && fine_sweeps < h->prm.max_sweeps; ++attempt) {
+            int app = 0;
+            bool conv = false;
+            void* bufs[2] = {F.u[0], F.u[1]};
+            DD_TRY(run_sweeps(h, F.geom, Store::F32, bufs, F.map_u, h->cur, nullptr, F.tmask, F.partial, F.ref_d,
+                              target, 0.0, h->prm.max_sweeps - fine_sweeps, st, &app, &conv, true));
+            fine_sweeps += app;
+            DD_TRY(fine_residual64(h, st, rel, rmax, rnorm));
+            worst = *std::max_element(rel.begin(), rel.end());
+            if (worst <= tol) { converged = true; break; }
+            if (!conv) break;
+            target *= 0.5;
+        }
+        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), u_out, F.W,
+                                       (long long)F.H * F.W, st));
+        DD_CK(cudaStreamSynchronize(st));
+    }
+    (void)nl;
+    h->stats.sweeps_per_level[0] = fine_sweeps;
+    h->stats.sweeps_total += fine_sweeps;
+    h->stats.converged = converged ? 1 : 0;
+    for (int c = 0; c < h->C && c < DD_MAX_STAT_CHANNELS; ++c) h->stats.rel_residual[c] = rel[c];
+    if (h->ev_recorded) {
+        float ms = 0.f;
+        if (cudaEventQuery(h->ev1) == cudaSuccess) DD_CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        h->stats.ms_total = ms;
+    }
+    h->stats.kernel_launches = h->launches;
+    return converged ? DD_OK : DD_ENOTCONVERGED;
+}
+
 int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
+    if (h->prm.precision == DD_PREC_FP32) {
+        DD_TRY(fp32_enqueue(h, u_out, tol, st, false));
+        return fp32_finish(h, st);
+    }
+    if (h->counts_pending) {   // data loaded asynchronously: check it before the correction loop
+        DD_CK(cudaStreamSynchronize(st));
+        h->counts_pending = false;
+        if (h->h_cnt[1] == 0) { h->valid = false; set_error("empty mask"); return DD_EEMPTYMASK; }
+        h->local_unknowns = (long long)h->h_cnt[0];
+        DD_CK(cudaMemcpy(h->h_ref, h->lv[0].ref_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost));
+        h->lv[0].ref.assign(h->h_ref, h->h_ref + h->C);
+    }
     std::memset(&h->stats, 0, sizeof(h->stats));
     h->stats.channels = h->C;
     h->stats.device_bytes = h->bytes;
@@ -452,61 +591,8 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
     std::vector<double> rel, rmax, rnorm;
     int fine_sweeps = 0;
     bool converged = false;
-    bool output_written = false;
     const long long dense_plane = (long long)F.H * F.W;
-    if (h->prm.precision == DD_PREC_FP32) {
-        // device-controlled first chunk: sweeps, output of the resolved buffer,
-        // its residual, and one read-back
-        const int n1 = std::min(dd_inpaint::kFirst, h->prm.max_sweeps);
-        const bool timed = h->prm.timing != 0;
-        DD_TRY(enqueue_sweeps(h, F, n1, tol, st, timed));
-        DD_LAUNCH(h, dd::launch_copy2d_sel(F.H, F.W, h->C, F.u[0], F.u[1], F.state_d, F.P, F.plane(), u_out, F.W,
-                                           dense_plane, st));
-        DD_TRY(residual_of(h, u_out, F.W, dense_plane, st));
-        DD_CK(cudaMemcpyAsync(h->h_state, F.state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        for (int l = 1; l < nl; ++l)
-            DD_CK(cudaMemcpyAsync(h->h_state + 4 * l, h->lv[l].state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        DD_CK(cudaStreamSynchronize(st));
-        if (h->h_flag[2] != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
-        if (cascaded) take_level_stats(h);
-        const int status = h->h_state[2], applied = h->h_state[1];
-        if (status == 2) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
-        if (timed) {
-            for (int i = 0; i < applied && i < n1; ++i) {
-                float ms = 0.f;
-                DD_CK(cudaEventElapsedTime(&ms, h->sw_ev[2 * i], h->sw_ev[2 * i + 1]));
-                h->stats.fine_sweep_ms += ms;
-                h->stats.fine_sweep_launches += 1;
-            }
-        }
-        fine_sweeps = applied;
-        h->cur = h->h_state[0];
-        DD_TRY(rel_from_h_res(h, rel, rmax, rnorm));
-        double worst = *std::max_element(rel.begin(), rel.end());
-        output_written = true;
-        if (status == 1 && worst <= tol) {
-            converged = true;
-        } else {
-            // not converged in the first chunk (or the FP32 fused estimate was
-            // optimistic): continue under host control
-            double target = status == 1 ? tol * 0.5 : tol;
-            for (int attempt = 0; attempt < 4 && fine_sweeps < h->prm.max_sweeps; ++attempt) {
-                int app = 0;
-                bool conv = false;
-                void* bufs[2] = {F.u[0], F.u[1]};
-                DD_TRY(run_sweeps(h, F.geom, Store::F32, bufs, F.map_u, h->cur, nullptr, F.tmask, F.partial, F.ref_d,
-                                  target, 0.0, h->prm.max_sweeps - fine_sweeps, st, &app, &conv, true));
-                fine_sweeps += app;
-                DD_TRY(fine_residual64(h, st, rel, rmax, rnorm));
-                worst = *std::max_element(rel.begin(), rel.end());
-                if (worst <= tol) { converged = true; break; }
-                if (!conv) break;
-                target *= 0.5;
-            }
-            output_written = false;
-        }
-    } else {
+    {
         const Store lt = h->lowst;
         for (int corr = 0;; ++corr) {
             DD_TRY(fine_residual64(h, st, rel, rmax, rnorm));
@@ -549,8 +635,7 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
     h->stats.sweeps_total += fine_sweeps;
     h->stats.converged = converged ? 1 : 0;
     for (int c = 0; c < h->C && c < DD_MAX_STAT_CHANNELS; ++c) h->stats.rel_residual[c] = rel.empty() ? 0 : rel[c];
-    if (!output_written)
-        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), u_out, F.W, dense_plane, st));
+    DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), u_out, F.W, dense_plane, st));
     DD_CK(cudaEventRecord(h->ev1, st));
     DD_CK(cudaEventSynchronize(h->ev1));
     float ms = 0.f;
@@ -567,6 +652,8 @@ void free_all(dd_inpaint* h) {
     if (h->h_small) cudaFreeHost(h->h_small);
     if (h->h_flag) cudaFreeHost(h->h_flag);
     if (h->h_state) cudaFreeHost(h->h_state);
+    if (h->h_ref) cudaFreeHost(h->h_ref);
+    if (h->h_cnt) cudaFreeHost(h->h_cnt);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     for (auto& e : h->sw_ev)
@@ -652,6 +739,8 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if ((rc = dalloc_t(h, &h->flag_d, 4)) != DD_OK) return fail(rc);
     if (cudaMallocHost(&h->h_res, sizeof(double2) * C * DD_MAX_LEVELS) != cudaSuccess ||
         cudaMallocHost(&h->h_state, sizeof(int) * 4 * DD_MAX_LEVELS) != cudaSuccess ||
+        cudaMallocHost(&h->h_ref, sizeof(double) * C) != cudaSuccess ||
+        cudaMallocHost(&h->h_cnt, sizeof(unsigned long long) * 2) != cudaSuccess ||
         cudaMallocHost(&h->h_small, sizeof(double) * 3 * C) != cudaSuccess ||
         cudaMallocHost(&h->h_flag, sizeof(int) * 8) != cudaSuccess) {
         set_error("cudaMallocHost failed");
@@ -714,6 +803,7 @@ const char* dd_strerror(int code) {
         case DD_ENUMERIC: return "non-finite residual";
         case DD_ECUDA: return "CUDA error";
         case DD_ETIMEOUT: return "device wait timed out";
+        case DD_EAGAIN: return "not finished yet";
     }
     return "unknown error";
 }
@@ -769,6 +859,47 @@ int dd_inpaint_stats(dd_handle h, dd_stats* out) {
     if (!h || !out) { set_error("NULL argument"); return DD_EINVAL; }
     *out = h->stats;
     return DD_OK;
+}
+
+int dd_inpaint_set_data_async(dd_handle h, const uint8_t* mask, const float* values, int keep_iterate,
+                              void* stream) {
+    if (!h || !mask || !values) { set_error("NULL argument"); return DD_EINVAL; }
+    if (h->pending) { set_error("a solve is in flight: finish it first"); return DD_EINVAL; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Level& F = h->lv[0];
+    if (keep_iterate && h->cur != 0)
+        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[1], F.P, F.plane(), F.u[0], F.P, F.plane(), st));
+    h->cur = 0;
+    h->valid = true;   // the empty-mask test is done when the next solve finishes
+    DD_TRY(load_data(h, mask, values, st, false));
+    if (keep_iterate)
+        DD_LAUNCH(h, dd::launch_reset_known(F.H, F.W, h->C, F.u[0], F.P, F.plane(), F.mask, F.W, F.f, F.P,
+                                            F.plane(), st));
+    h->warm = keep_iterate != 0;
+    return DD_OK;
+}
+
+int dd_inpaint_solve_async(dd_handle h, float* u_out, double tol, void* stream) {
+    if (!h || !u_out || !(tol > 0.0)) { set_error("bad solve arguments"); return DD_EINVAL; }
+    if (h->prm.precision != DD_PREC_FP32) { set_error("asynchronous solves need precision DD_PREC_FP32"); return DD_EINVAL; }
+    if (h->pending) { set_error("a solve is already in flight"); return DD_EINVAL; }
+    if (!h->valid) { set_error("no valid data (the last set_data failed)"); return DD_EEMPTYMASK; }
+    return fp32_enqueue(h, u_out, tol, static_cast<cudaStream_t>(stream), false);
+}
+
+int dd_inpaint_query(dd_handle h) {
+    if (!h || !h->pending) { set_error("no solve in flight"); return DD_EINVAL; }
+    if (!h->ev_recorded) return DD_EAGAIN;
+    const cudaError_t e = cudaEventQuery(h->ev1);
+    if (e == cudaSuccess) return DD_OK;
+    if (e == cudaErrorNotReady) return DD_EAGAIN;
+    set_error(std::string("cudaEventQuery: ") + cudaGetErrorString(e));
+    return DD_ECUDA;
+}
+
+int dd_inpaint_solve_finish(dd_handle h, void* stream) {
+    if (!h) { set_error("NULL argument"); return DD_EINVAL; }
+    return fp32_finish(h, static_cast<cudaStream_t>(stream));
 }
 
 int dd_inpaint_set_iterate(dd_handle h, const float* u, void* stream) {
@@ -880,6 +1011,137 @@ int dd_residual_norms(int H, int W, int C, const uint8_t* mask, const float* f, 
         for (int c = 0; c < C; ++c) dst[c] = std::sqrt(hout[c].x);
     }
     cleanup();
+    return DD_OK;
+}
+
+// ------------------------------------------------------------------ batches
+struct dd_batch {
+    std::vector<dd_handle> hs;
+    std::vector<float*> outs;
+    double tol = 0.0;
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> evs;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    long long kernels = 0;
+    bool launched = false;
+};
+
+static void batch_free(dd_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto e : b->evs) cudaEventDestroy(e);
+    for (auto s2 : b->side) cudaStreamDestroy(s2);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->done) cudaEventDestroy(b->done);
+    delete b;
+}
+
+int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double tol, dd_batch_handle* out,
+                    long long* kernels_per_launch) {
+    if (n <= 0 || !handles || !u_out || !out || !(tol > 0.0)) { set_error("bad batch arguments"); return DD_EINVAL; }
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!handles[i] || !u_out[i]) { set_error("NULL handle or output"); return DD_EINVAL; }
+        if (handles[i]->prm.precision != DD_PREC_FP32) { set_error("batches need precision DD_PREC_FP32"); return DD_EINVAL; }
+        if (handles[i]->pending) { set_error("a handle has a solve in flight"); return DD_EINVAL; }
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == handles[i]) { set_error("a handle appears twice"); return DD_EINVAL; }
+    }
+    dd_batch* b = new (std::nothrow) dd_batch();
+    if (!b) { set_error("host allocation"); return DD_ENOMEM; }
+    b->hs.assign(handles, handles + n);
+    b->outs.assign(u_out, u_out + n);
+    b->tol = tol;
+    auto bail = [&](const char* what, cudaError_t e) {
+        set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        batch_free(b);
+        return DD_ECUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
+    if ((e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
+    b->side.resize(n, nullptr);
+    b->evs.resize(2 * n + 1, nullptr);
+    for (int i = 0; i < n; ++i)
+        if ((e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
+    for (auto& ev : b->evs)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
+    // capture: fork one stream per frame, enqueue each frame's solve, join
+    long long before = 0;
+    for (auto h : b->hs) before += h->launches;
+    if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return bail("capture", e);
+    int rc = DD_OK;
+    if ((e = cudaEventRecord(b->evs[2 * n], b->cap)) != cudaSuccess) rc = DD_ECUDA;
+    for (int i = 0; i < n && rc == DD_OK; ++i) {
+        if (cudaStreamWaitEvent(b->side[i], b->evs[2 * n], 0) != cudaSuccess) { rc = DD_ECUDA; break; }
+        b->hs[i]->warm = false;   // a captured solve always starts with the cascade
+        rc = fp32_enqueue(b->hs[i], b->outs[i], tol, b->side[i], true);
+        b->hs[i]->pending = false;
+        if (rc == DD_OK && cudaEventRecord(b->evs[2 * i], b->side[i]) != cudaSuccess) rc = DD_ECUDA;
+        if (rc == DD_OK && cudaStreamWaitEvent(b->cap, b->evs[2 * i], 0) != cudaSuccess) rc = DD_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    b->graph = g;
+    if (rc != DD_OK || e != cudaSuccess) {
+        if (rc == DD_OK) set_error(std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        batch_free(b);
+        return rc == DD_OK ? DD_ECUDA : rc;
+    }
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return bail("cudaGraphInstantiate", e);
+    long long after = 0;
+    for (auto h : b->hs) after += h->launches;
+    b->kernels = after - before;
+    if (kernels_per_launch) *kernels_per_launch = b->kernels;
+    *out = b;
+    return DD_OK;
+}
+
+int dd_batch_launch(dd_batch_handle b, void* stream) {
+    if (!b) { set_error("NULL batch"); return DD_EINVAL; }
+    if (b->launched) { set_error("the previous launch has not been finished"); return DD_EINVAL; }
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        dd_handle h = b->hs[i];
+        if (h->pending) { set_error("a handle of the batch has a solve in flight"); return DD_EINVAL; }
+        if (!h->valid) { set_error("a handle of the batch has no valid data"); return DD_EEMPTYMASK; }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DD_CK(cudaGraphLaunch(b->exec, st));
+    DD_CK(cudaEventRecord(b->done, st));
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        dd_handle h = b->hs[i];
+        h->pending = true;
+        h->pending_out = b->outs[i];
+        h->pending_tol = b->tol;
+        h->pending_cascaded = true;
+        h->ev_recorded = false;
+        h->warm = false;
+    }
+    b->launched = true;
+    return DD_OK;
+}
+
+int dd_batch_finish(dd_batch_handle b, void* stream, int* status) {
+    if (!b || !b->launched) { set_error("no batch launch in flight"); return DD_EINVAL; }
+    b->launched = false;
+    DD_CK(cudaEventSynchronize(b->done));
+    int worst = DD_OK;
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        const int rc = fp32_finish(b->hs[i], static_cast<cudaStream_t>(stream));
+        if (status) status[i] = rc;
+        if (rc != DD_OK && worst == DD_OK) worst = rc;
+    }
+    return worst;
+}
+
+int dd_batch_destroy(dd_batch_handle b) {
+    if (!b) return DD_OK;
+    if (b->launched) cudaEventSynchronize(b->done);
+    for (auto h : b->hs) h->pending = false;
+    batch_free(b);
     return DD_OK;
 }
 

@@ -1,0 +1,107 @@
+"""Asynchronous solves and CUDA-graph batches through the C ABI.
+
+The asynchronous and batched paths run the same kernels with the same
+parameters as dd_inpaint_solve, so their outputs must equal the synchronous
+ones bit for bit, and match the oracle within the FP32 solve tolerance."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import inpaint_ref as ref
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2110_03946_gb300 import binding as B  # noqa: E402
+from paper_2110_03946_gb300.inpaint import Inpainter  # noqa: E402
+
+DEV = torch.device("cuda:0")
+TOL_U = 0.05
+PRM = dict(block=32, overlap=3, local_cg_iters=16, robin_p=0.15, levels=3, coarse_tol=3e-3, precision="fp32")
+SHAPES = [(120, 170, 3, 0.05, "uniform"), (96, 64, 1, 0.08, "edge"), (257, 190, 3, 0.03, "edge"),
+          (40, 300, 2, 0.06, "uniform")]
+
+
+def _frames(seed0):
+    return [synth.make_frame(H, W, C, d, pat, seed0 + i) for i, (H, W, C, d, pat) in enumerate(SHAPES)]
+
+
+def _sync_solve(f, m):
+    with Inpainter(m, f, **PRM) as ip:
+        return ip.solve(1e-6).cpu().numpy()
+
+
+def test_async_solves_on_several_streams_match_sync():
+    frames = _frames(700)
+    ips = [Inpainter(m, f, **PRM) for f, m in frames]
+    streams = [torch.cuda.Stream(DEV) for _ in frames]
+    outs = [torch.empty(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames]
+    dev_in = [(torch.as_tensor(m).to(DEV), torch.as_tensor(f).to(DEV)) for f, m in frames]
+    torch.cuda.synchronize()
+    for ip, s, (md, fd), o in zip(ips, streams, dev_in, outs):
+        B.check(B.dd_inpaint_set_data_async(ip._h, md.data_ptr(), fd.data_ptr(), 0, s), "set_data_async")
+        B.check(B.dd_inpaint_solve_async(ip._h, o.data_ptr(), 1e-6, s), "solve_async")
+    for ip, s in zip(ips, streams):
+        B.check(B.dd_inpaint_solve_finish(ip._h, s), "finish")
+        assert B.dd_inpaint_query(ip._h) == B.DD_EINVAL          # nothing in flight any more
+    for (f, m), o, ip in zip(frames, outs, ips):
+        u = o.cpu().numpy()
+        assert np.array_equal(u, _sync_solve(f, m))
+        assert np.max(np.abs(u - ref.solve_direct(f, m))) <= TOL_U
+        assert np.all(ref.rel_residual(u.astype(np.float64), f, m) <= 1e-6)
+        ip.close()
+
+
+def test_async_empty_mask_reported_at_finish():
+    f, m = synth.make_frame(64, 64, 1, 0.05, "uniform", 3)
+    with Inpainter(m, f, **PRM) as ip:
+        z = torch.zeros((64, 64), dtype=torch.uint8, device=DEV)
+        fd = torch.as_tensor(f).to(DEV)
+        out = torch.empty((1, 64, 64), dtype=torch.float32, device=DEV)
+        B.check(B.dd_inpaint_set_data_async(ip._h, z.data_ptr(), fd.data_ptr(), 0, None), "set_data_async")
+        B.check(B.dd_inpaint_solve_async(ip._h, out.data_ptr(), 1e-6, None), "solve_async")
+        assert B.dd_inpaint_solve_finish(ip._h, None) == B.DD_EEMPTYMASK
+        assert B.dd_inpaint_solve(ip._h, out.data_ptr(), 1e-6, None) == B.DD_EEMPTYMASK
+        md = torch.as_tensor(m).to(DEV)
+        B.check(B.dd_inpaint_set_data(ip._h, md.data_ptr(), fd.data_ptr(), 0), "set_data")
+        B.check(B.dd_inpaint_solve(ip._h, out.data_ptr(), 1e-6, None), "solve")
+
+
+def test_batch_graph_matches_independent_solves():
+    frames_a, frames_b = _frames(800), _frames(900)
+    ips = [Inpainter(m, f, **PRM) for f, m in frames_a]
+    outs = [torch.empty(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames_a]
+    rc, b, kernels = B.dd_batch_create([ip._h for ip in ips], [o.data_ptr() for o in outs], 1e-6)
+    B.check(rc, "dd_batch_create")
+    assert kernels > len(ips)
+    try:
+        for frames in (frames_a, frames_b):       # second launch: new data in the same handles
+            dev_in = [(torch.as_tensor(m).to(DEV), torch.as_tensor(f).to(DEV)) for f, m in frames]
+            for ip, (md, fd) in zip(ips, dev_in):
+                B.check(B.dd_inpaint_set_data(ip._h, md.data_ptr(), fd.data_ptr(), 0), "set_data")
+            stream = torch.cuda.current_stream(DEV)
+            B.check(B.dd_batch_launch(b, stream), "dd_batch_launch")
+            rc, status = B.dd_batch_finish(b, len(ips), stream)
+            assert rc == B.DD_OK and all(sc == B.DD_OK for sc in status)
+            for (f, m), o, ip in zip(frames, outs, ips):
+                u = o.cpu().numpy()
+                assert np.array_equal(u, _sync_solve(f, m))
+                assert np.max(np.abs(u - ref.solve_direct(f, m))) <= TOL_U
+                assert ip.stats()["converged"]
+    finally:
+        B.dd_batch_destroy(b)
+        for ip in ips:
+            ip.close()
+
+
+def test_batch_rejects_bad_input():
+    f, m = synth.make_frame(64, 64, 1, 0.05, "uniform", 4)
+    with Inpainter(m, f, precision="fp16_ref") as ip16, Inpainter(m, f, **PRM) as ip:
+        o = torch.empty((1, 64, 64), dtype=torch.float32, device=DEV)
+        rc, b, _ = B.dd_batch_create([ip16._h], [o.data_ptr()], 1e-6)
+        assert rc == B.DD_EINVAL and not b.value
+        rc, b, _ = B.dd_batch_create([ip._h, ip._h], [o.data_ptr(), o.data_ptr()], 1e-6)
+        assert rc == B.DD_EINVAL
