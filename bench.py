@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP16-storage measurement")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving measurements")
     return ap.parse_args()
 
 
@@ -237,6 +238,88 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------- extras
+def run_batch48(dev, params):
+    """48 frames of mixed sizes (512x512, 1280x720, 1920x1080, 3840x2160 RGB;
+    mask density U[1%, 10%], half uniform, half edge-clustered) solved to 1e-6
+    as one CUDA-graph launch (dd_batch_*), against the same frames solved one
+    after another."""
+    import torch
+
+    import synth
+    from paper_2110_03946_gb300 import binding as B
+    from paper_2110_03946_gb300.inpaint import make_params
+    rng = np.random.default_rng(4000)
+    sizes = [(512, 512), (720, 1280), (1080, 1920), (2160, 3840)]
+    frames = []
+    for j in range(48):
+        H, W = sizes[rng.integers(4)]
+        d = rng.uniform(0.01, 0.10)
+        pat = "uniform" if j % 2 == 0 else "edge"
+        f, m = synth.make_frame(H, W, 3, d, pat, 4000 + j)
+        frames.append((torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev)))
+    p = make_params(precision="fp32", inputs_on_device=1, **params)
+    hs, outs = [], []
+    for m, f in frames:
+        C, H, W = f.shape
+        rc, h = B.dd_inpaint_create(H, W, C, m.data_ptr(), f.data_ptr(), p)
+        B.check(rc, "create")
+        hs.append(h)
+        outs.append(torch.empty((C, H, W), dtype=torch.float32, device=dev))
+    stream = torch.cuda.current_stream(dev)
+    try:
+        # one after another (synchronous solves)
+        for h, o in zip(hs, outs):
+            B.check(B.dd_inpaint_solve(h, o.data_ptr(), TOL, stream), "solve")
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for h, o in zip(hs, outs):
+            B.check(B.dd_inpaint_solve(h, o.data_ptr(), TOL, stream), "solve")
+        torch.cuda.synchronize(dev)
+        seq_s = time.perf_counter() - t0
+        rc, b, kernels = B.dd_batch_create(hs, [o.data_ptr() for o in outs], TOL)
+        B.check(rc, "dd_batch_create")
+        try:
+            reps = 3
+            B.check(B.dd_batch_launch(b, stream), "launch")
+            rc, st = B.dd_batch_finish(b, len(hs), stream)
+            B.check(rc, "finish")
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                B.check(B.dd_batch_launch(b, stream), "launch")
+                rc, st = B.dd_batch_finish(b, len(hs), stream)
+                B.check(rc, "finish")
+            batch_s = (time.perf_counter() - t0) / reps
+        finally:
+            B.dd_batch_destroy(b)
+        mpx = sum(f.shape[1] * f.shape[2] for _, f in frames) / 1e6
+        return {"frames": 48, "megapixels_rgb": round(mpx, 1),
+                "batched_graph_frames_per_s": 48 / batch_s, "sequential_frames_per_s": 48 / seq_s,
+                "speedup": seq_s / batch_s, "kernels_per_graph_launch": kernels,
+                "note": "one CUDA graph launch per batch; wall clock incl. host finish"}
+    finally:
+        for h in hs:
+            B.dd_inpaint_destroy(h)
+
+
+def run_serving(dev, params):
+    """Poisson arrivals at 60 requests/s for 4 s: 70 % 4K, 20 % 1080p, 10 %
+    720p RGB video sequences of 30 frames (shift 1..3 px + noise, warm start
+    from the previous frame), uniform masks of density U[2 %, 8 %], pinned host
+    inputs and outputs, 40 GB HBM budget."""
+    from paper_2110_03946_gb300.serve import CudaBackend, Server, make_pool, poisson_stream
+    shapes = [(2160, 3840, 3), (1080, 1920, 3), (720, 1280, 3)]
+    pool = make_pool(shapes, n_frames=6, n_masks=4, density_range=(0.02, 0.08), seed=5000)
+    reqs = poisson_stream(60.0, 4.0, shapes, [0.7, 0.2, 0.1], 30, 5001, pool)
+    srv = Server(CudaBackend(params, tol=TOL, device=dev), hbm_budget=40 << 30)
+    try:
+        res, m = srv.run(reqs, realtime=True)
+    finally:
+        srv.close()
+    m["offered_rate_req_per_s"] = 60.0
+    return m
+
+
 # ----------------------------------------------------------------------- ours
 def run_ours(args):
     import torch
@@ -391,6 +474,17 @@ def run_ours(args):
                      "corrections_last": mst["corrections"], "fine_sweeps_last": mst["sweeps_per_level"][0],
                      "rel_residual_last": max(mst["rel_residual"][:C])}
 
+    batch48 = serving = None
+    if world == 1 and not args.no_extras:
+        try:
+            batch48 = run_batch48(dev, tuned)
+        except Exception as e:  # reported in the line, never fatal for the headline
+            batch48 = {"error": repr(e)[:300]}
+        try:
+            serving = run_serving(dev, tuned)
+        except Exception as e:
+            serving = {"error": repr(e)[:300]}
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -449,6 +543,8 @@ def run_ours(args):
         "clocks": clk,
         "plain_fp32_oras": plain,
         "mixed_fp16_oras": mixed,
+        "batch48_mixed_sizes": batch48,
+        "serving_60rps": serving,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -858,6 +858,8 @@ int dd_inpaint_set_data(dd_handle h, const uint8_t* mask, const float* values, i
 int dd_inpaint_stats(dd_handle h, dd_stats* out) {
     if (!h || !out) { set_error("NULL argument"); return DD_EINVAL; }
     *out = h->stats;
+    out->device_bytes = h->bytes;   // valid from create on, before any solve
+    out->channels = h->C;
     return DD_OK;
 }
 
