@@ -320,6 +320,76 @@ def run_serving(dev, params):
     return m
 
 
+def run_studies(dev, params):
+    """The paper's remaining experiments on synthetic frames (one stream,
+    synchronous solves): runtime vs image size (Fig. 3: log-log slope), RAS
+    (Robin weight 1) vs ORAS (tuned weight) at 4K (Sec. 3), and PSNR against
+    the synthetic ground truth vs the relative residual reached (Fig. 2(b); the
+    PSNR averages the MSE over the three channels)."""
+    import torch
+
+    import synth
+    from paper_2110_03946_gb300.inpaint import Inpainter
+    out = {}
+
+    def timed(ip, reps=3):
+        o = torch.empty((ip.C, ip.H, ip.W), dtype=torch.float32, device=dev)
+        ip.solve(TOL, out=o)
+        ts = []
+        for _ in range(reps):
+            ip.solve(TOL, out=o)
+            ts.append(ip.stats()["ms_total"])
+        return float(np.median(ts)), ip.stats(), o
+
+    sizes = [(540, 960), (1080, 1920), (1440, 2560), (2160, 3840)]
+    rows = []
+    for k, (H, W) in enumerate(sizes):
+        f, m = synth.make_frame(H, W, 3, 0.03, "edge", 6000 + k)
+        with Inpainter(torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev), device=dev, precision="fp32",
+                       **params) as ip:
+            ms, st, _ = timed(ip)
+        rows.append({"H": H, "W": W, "ms": ms, "fine_sweeps": st["sweeps_per_level"][0]})
+    px = np.log([r["H"] * r["W"] for r in rows])
+    ms = np.log([r["ms"] for r in rows])
+    out["scaling"] = {"rows": rows, "loglog_slope": float(np.polyfit(px, ms, 1)[0])}
+
+    f, m = synth.workload_frame(WORKLOAD, 0)
+    md, fd = torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev)
+    ras = {}
+    for name, pr in [("ras_p1", 1.0), ("oras_tuned", params.get("robin_p", 0.0))]:
+        with Inpainter(md, fd, device=dev, precision="fp32", **dict(params, robin_p=pr)) as ip:
+            ms_, st, _ = timed(ip)
+        ras[name] = {"robin_p": pr, "ms": ms_, "fine_sweeps": st["sweeps_per_level"][0]}
+    out["ras_vs_oras"] = ras
+
+    ps = []
+    truth = fd.to(torch.float64)
+    for tol in [1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6]:
+        with Inpainter(md, fd, device=dev, precision="fp32", **params) as ip:
+            u = ip.solve(tol)
+            st = ip.stats()
+        mse = float(((u.to(torch.float64) - truth) ** 2).mean())
+        ps.append({"tol": tol, "rel_residual": max(st["rel_residual"][:3]),
+                   "psnr_db": 10 * np.log10(255.0 ** 2 / mse), "ms": st["ms_total"]})
+    out["psnr_vs_residual"] = ps
+
+    # the paper's comparison solvers on the same 4K frame: single-level and
+    # multilevel conjugate gradients against multilevel ORAS (Sec. 5, Fig. 2(a))
+    cmp_ = {}
+    for name, prm_ in [("ml_oras", dict(params)),
+                       ("ml_cg", dict(levels=params.get("levels", 4), solver="cg", max_sweeps=4000,
+                                      coarse_sweeps=400, coarse_tol=params.get("coarse_tol", 3e-3))),
+                       ("cg_single_level", dict(levels=1, solver="cg", max_sweeps=4000))]:
+        with Inpainter(md, fd, device=dev, precision="fp32", **prm_) as ip:
+            ms_, st, _ = timed(ip, reps=2)
+        cmp_[name] = {"ms": ms_, "fine_iterations": st["sweeps_per_level"][0],
+                      "iterations_per_level": st["sweeps_per_level"][:prm_.get("levels", 1)],
+                      "rel_residual": max(st["rel_residual"][:3])}
+    cmp_["speedup_ml_oras_vs_ml_cg"] = cmp_["ml_cg"]["ms"] / cmp_["ml_oras"]["ms"]
+    out["oras_vs_cg"] = cmp_
+    return out
+
+
 # ----------------------------------------------------------------------- ours
 def run_ours(args):
     import torch
@@ -559,8 +629,12 @@ def run_ours(args):
                      "corrections_last": mst["corrections"], "fine_sweeps_last": mst["sweeps_per_level"][0],
                      "rel_residual_last": max(mst["rel_residual"][:C])}
 
-    batch48 = serving = None
+    batch48 = serving = studies = None
     if world == 1 and not args.no_extras:
+        try:
+            studies = run_studies(dev, tuned)
+        except Exception as e:
+            studies = {"error": repr(e)[:300]}
         try:
             batch48 = run_batch48(dev, tuned)
         except Exception as e:  # reported in the line, never fatal for the headline
@@ -638,6 +712,7 @@ def run_ours(args):
         "mixed_fp16_oras": mixed,
         "batch48_mixed_sizes": batch48,
         "serving_60rps": serving,
+        "studies": studies,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -53,6 +53,11 @@ extern "C" {
 #define DD_ETIMEOUT       7  /* a bounded device-side wait gave up */
 #define DD_EAGAIN         8  /* asynchronous work not finished yet (dd_inpaint_query) */
 
+/* level solvers */
+#define DD_SOLVER_ORAS    0  /* restricted additive Schwarz with Robin interfaces (Sec. 3-4) */
+#define DD_SOLVER_CG      1  /* conjugate gradients on the whole image: the comparison solver of
+                                Sec. 5 (with levels > 1: multilevel CG of Bornemann & Deuflhard) */
+
 /* multilevel modes */
 #define DD_ML_CASCADE     0  /* coarse-to-fine initialisation (Sec. 4) */
 #define DD_ML_CORRECTION  1  /* two-level: coarse residual correction after each fine sweep */
@@ -85,6 +90,8 @@ typedef struct dd_params {
     int    timing;           /* 1: time every fine-level sweep launch with CUDA events (dd_stats) */
     int    tile_warps;       /* warps holding one block tile: 0 = default; block 16: 1;
                                 block 32: 1, 2 or 4; block 64: 4 or 8 */
+    int    solver;           /* DD_SOLVER_ORAS (default) or DD_SOLVER_CG (needs DD_PREC_FP32);
+                                with CG, max_sweeps / coarse_sweeps count CG iterations */
 } dd_params;
 
 #define DD_MAX_STAT_CHANNELS 16

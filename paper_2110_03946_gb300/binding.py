@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libdd_inpaint.so")
 
 DD_OK, DD_EINVAL, DD_EEMPTYMASK, DD_ENOMEM, DD_ENOTCONVERGED, DD_ENUMERIC, DD_ECUDA, DD_ETIMEOUT, DD_EAGAIN = range(9)
 DD_ML_CASCADE, DD_ML_CORRECTION = 0, 1
+DD_SOLVER_ORAS, DD_SOLVER_CG = 0, 1
 DD_PREC_FP32, DD_PREC_FP32_REF, DD_PREC_FP16_REF, DD_PREC_BF16_REF = 0, 1, 2, 3
 DD_MAX_STAT_CHANNELS = 16
 DD_MAX_LEVELS = 8
@@ -38,7 +39,7 @@ class dd_params(ctypes.Structure):
         ("robin_p", ctypes.c_float), ("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
         ("inputs_on_device", ctypes.c_int), ("coarse_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
         ("max_corrections", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("timing", ctypes.c_int),
-        ("tile_warps", ctypes.c_int),
+        ("tile_warps", ctypes.c_int), ("solver", ctypes.c_int),
     ]
 
 

@@ -167,6 +167,31 @@ cudaError_t launch_count_nonzero(const uint8_t* m, long long n, unsigned long lo
 // out[c] = sqrt(in[c].x)
 cudaError_t launch_sqrt_sums(const double2* in, double* out, int C, cudaStream_t st);
 
+// ---- conjugate gradients on the whole image (cg.cu) ---------------------------------
+struct CGArgs {
+    int H, W, P, C, mp;
+    long long plane;
+    const uint8_t* mask;
+    float* x;            // iterate (known pixels hold f)
+    float* r;            // residual on unknown pixels
+    const float* p_old;  // search direction of the previous iteration
+    float* p_new;        // search direction of this iteration
+    float* q;            // A p
+    double* part;        // C x cg_blocks partial sums
+    double* scal;        // [0,C) (r,r), [C,2C) alpha, [2C,3C) beta
+    const double* ref;   // per-channel ||b - A u0||
+    int* flag;           // [0] stop flag, [1] stopping iteration, [3] ticket
+    int* state;          // [1] counts iterations
+    int iter;
+    int first;           // 1: beta = 0 (first iteration of a run)
+    double tol;
+};
+int cg_blocks(int H, int W);
+// scal <- {(r, r) from res_out[c].x, alpha = beta = 0}
+cudaError_t launch_cg_init(const double2* res_out, double* scal, int C, cudaStream_t st);
+// one CG iteration (two kernels) under the device stop flag
+cudaError_t launch_cg_iteration(const CGArgs& a, cudaStream_t st);
+
 // Default Robin weight for block side b and overlap o (the value create uses).
 float default_robin(int b, int o);
 // Record the text returned by dd_last_error() on this thread.

@@ -72,6 +72,12 @@ struct Level {
     double* ref_d = nullptr;   // C
     std::vector<double> ref;   // C (host copy, read after load_data's single sync)
     int* state_d = nullptr;    // resolve() output of this level's last sweep sequence
+    // conjugate-gradient solver (DD_SOLVER_CG): residual, two search directions, A p
+    float* cg_r = nullptr;
+    float* cg_p[2] = {nullptr, nullptr};
+    float* cg_q = nullptr;
+    double* cg_part = nullptr;   // C x cg_blocks
+    double* cg_scal = nullptr;   // 3C
     long long plane() const { return (long long)H * P; }
 };
 
@@ -90,6 +96,7 @@ struct dd_inpaint {
     void* g = nullptr;
     CUtensorMap map_e[2], map_g;
     double* inner_ref_d = nullptr;  // C
+    double* ones_d = nullptr;       // C ones (residual pass without scaling)
     double* scale_d = nullptr;      // C
     double* scale_inv_d = nullptr;  // C
     // residual / stop-test scratch
@@ -159,6 +166,11 @@ int validate(int H, int W, int C, const dd_params& p) {
     if (H <= 0 || W <= 0 || C <= 0) { set_error("H, W and C must be positive"); return DD_EINVAL; }
     if ((long long)H * W > (1LL << 31) / 4) { set_error("image too large"); return DD_EINVAL; }
     if (!dd::block_supported(p.block)) { set_error("block must be 16, 32 or 64"); return DD_EINVAL; }
+    if (p.solver != DD_SOLVER_ORAS && p.solver != DD_SOLVER_CG) { set_error("bad solver"); return DD_EINVAL; }
+    if (p.solver == DD_SOLVER_CG && p.precision != DD_PREC_FP32) {
+        set_error("DD_SOLVER_CG needs precision DD_PREC_FP32");
+        return DD_EINVAL;
+    }
     if (p.tile_warps != 0 && !dd::tile_warps_supported(p.block, p.tile_warps)) {
         set_error("tile_warps: 16 -> 1; 32 -> 1, 2 or 4; 64 -> 4 or 8");
         return DD_EINVAL;
@@ -380,6 +392,49 @@ int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, 
     return DD_OK;
 }
 
+// Enqueue n CG iterations on level L from the iterate in u[0] (the residual is
+// formed afresh, so this also restarts CG), then record the result (always in
+// u[0]) into L.state_d.  No host synchronisation.
+int enqueue_cg(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st) {
+    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, st));
+    const int nblk = dd::res64_blocks(L.H, L.W);
+    dd::Res64Args ra{};
+    ra.H = L.H; ra.W = L.W; ra.C = h->C;
+    ra.u = L.u[0]; ra.up = L.P; ra.uplane = L.plane();
+    ra.mask = L.mask; ra.mp = L.W;
+    ra.g_out = L.cg_r; ra.gst = Store::F32; ra.gp = L.P; ra.gplane = L.plane();
+    ra.scale_inv = h->ones_d;
+    ra.part = h->res_part; ra.nblk = nblk;
+    DD_LAUNCH(h, dd::launch_res64(ra, st));
+    DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, nblk, h->C, h->res_out, st));
+    DD_LAUNCH(h, dd::launch_cg_init(h->res_out, L.cg_scal, h->C, st));
+    DD_CK(cudaMemsetAsync(L.cg_p[0], 0, sizeof(float) * (size_t)h->C * L.plane(), st));
+    dd::CGArgs a{};
+    a.H = L.H; a.W = L.W; a.P = L.P; a.C = h->C; a.mp = L.W;
+    a.plane = L.plane();
+    a.mask = L.mask;
+    a.x = L.u[0]; a.r = L.cg_r; a.q = L.cg_q;
+    a.part = L.cg_part; a.scal = L.cg_scal; a.ref = L.ref_d;
+    a.flag = h->flag_d; a.state = h->sstate_d;
+    a.tol = tol;
+    for (int i = 0; i < n; ++i) {
+        a.p_old = L.cg_p[i & 1];
+        a.p_new = L.cg_p[(i + 1) & 1];
+        a.iter = i;
+        a.first = i == 0 ? 1 : 0;
+        DD_CK(dd::launch_cg_iteration(a, st));
+        h->launches += 2;
+    }
+    DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, L.state_d, st));
+    return DD_OK;
+}
+
+// A level solve under the device stop test: ORAS sweeps or CG iterations.
+int enqueue_level(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed) {
+    if (h->prm.solver == DD_SOLVER_CG) return enqueue_cg(h, L, n, tol, st);
+    return enqueue_sweeps(h, L, n, tol, st, timed);
+}
+
 // Coarse-to-fine initialisation (Sec. 4): coarsest level from u0 = C f, each
 // level swept to coarse_tol (at most coarse_sweeps sweeps) and prolonged as the
 // next level's start; the fine level's start is left in u[0].  Everything is
@@ -397,7 +452,7 @@ int cascade(dd_inpaint* h, cudaStream_t st) {
                                                 Cc.plane(), L.mask, L.W, L.f, L.P, L.plane(), L.u[0], L.P,
                                                 L.plane(), st));
         }
-        DD_TRY(enqueue_sweeps(h, L, h->prm.coarse_sweeps, h->prm.coarse_tol, st, false));
+        DD_TRY(enqueue_level(h, L, h->prm.coarse_sweeps, h->prm.coarse_tol, st, false));
     }
     Level& F = h->lv[0];
     if (nl > 1) {
@@ -447,6 +502,12 @@ void take_level_stats(dd_inpaint* h) {
     for (size_t l = 1; l < h->lv.size(); ++l) h->stats.sweeps_total += h->h_state[4 * l + 1];
 }
 
+// Fine-level launches enqueued before the first read-back.
+int first_chunk(const dd_inpaint* h) {
+    const int n = h->prm.solver == DD_SOLVER_CG ? 256 : dd_inpaint::kFirst;
+    return std::min(n, h->prm.max_sweeps);
+}
+
 // FP32 path, part 1: enqueue the cascade, the first fine chunk, the output of
 // the resolved buffer, its residual and the read-back of everything the host
 // needs.  No host synchronisation.  capture = 1 inside a stream capture
@@ -468,8 +529,8 @@ int fp32_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool 
     }
     h->warm = false;
     const long long dense_plane = (long long)F.H * F.W;
-    const int n1 = std::min(dd_inpaint::kFirst, h->prm.max_sweeps);
-    DD_TRY(enqueue_sweeps(h, F, n1, tol, st, h->prm.timing != 0 && !capture));
+    const int n1 = first_chunk(h);
+    DD_TRY(enqueue_level(h, F, n1, tol, st, h->prm.timing != 0 && !capture));
     DD_LAUNCH(h, dd::launch_copy2d_sel(F.H, F.W, h->C, F.u[0], F.u[1], F.state_d, F.P, F.plane(), u_out, F.W,
                                        dense_plane, st));
     DD_TRY(residual_of(h, u_out, F.W, dense_plane, st));
@@ -510,8 +571,8 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
     if (h->pending_cascaded) take_level_stats(h);
     const int status = h->h_state[2], applied = h->h_state[1];
     if (status == 2) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
-    const int n1 = std::min(dd_inpaint::kFirst, h->prm.max_sweeps);
-    if (h->prm.timing != 0 && h->ev_recorded) {
+    const int n1 = first_chunk(h);
+    if (h->prm.timing != 0 && h->ev_recorded && h->prm.solver == DD_SOLVER_ORAS) {
         for (int i = 0; i < applied && i < n1; ++i) {
             float ms = 0.f;
             DD_CK(cudaEventElapsedTime(&ms, h->sw_ev[2 * i], h->sw_ev[2 * i + 1]));
@@ -532,9 +593,23 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
         for (int attempt = 0; attempt < 4 && fine_sweeps < h->prm.max_sweeps; ++attempt) {
             int app = 0;
             bool conv = false;
-            void* bufs[2] = {F.u[0], F.u[1]};
-            DD_TRY(run_sweeps(h, F.geom, Store::F32, bufs, F.map_u, h->cur, nullptr, F.tmask, F.partial, F.ref_d,
-                              target, 0.0, h->prm.max_sweeps - fine_sweeps, st, &app, &conv, true));
+            if (h->prm.solver == DD_SOLVER_CG) {
+                // restart CG from the current iterate (fresh residual), read back once per chunk
+                while (!conv && fine_sweeps + app < h->prm.max_sweeps) {
+                    const int n = std::min(64, h->prm.max_sweeps - fine_sweeps - app);
+                    DD_TRY(enqueue_cg(h, F, n, target, st));
+                    DD_CK(cudaMemcpyAsync(h->h_state, F.state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                    DD_CK(cudaStreamSynchronize(st));
+                    app += h->h_state[1];
+                    conv = h->h_state[2] == 1;
+                    if (h->h_state[2] == 2) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
+                }
+                h->cur = 0;
+            } else {
+                void* bufs[2] = {F.u[0], F.u[1]};
+                DD_TRY(run_sweeps(h, F.geom, Store::F32, bufs, F.map_u, h->cur, nullptr, F.tmask, F.partial,
+                                  F.ref_d, target, 0.0, h->prm.max_sweeps - fine_sweeps, st, &app, &conv, true));
+            }
             fine_sweeps += app;
             DD_TRY(fine_residual64(h, st, rel, rmax, rnorm));
             worst = *std::max_element(rel.begin(), rel.end());
@@ -702,6 +777,14 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         if ((rc = dalloc_t(h, &L.partial, (size_t)C * dd::kSweepSlots)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &L.ref_d, (size_t)C)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &L.state_d, 4)) != DD_OK) return fail(rc);
+        if (p.solver == DD_SOLVER_CG) {
+            if ((rc = dalloc(h, (void**)&L.cg_r, plane_bytes)) != DD_OK) return fail(rc);
+            for (int b = 0; b < 2; ++b)
+                if ((rc = dalloc(h, (void**)&L.cg_p[b], plane_bytes)) != DD_OK) return fail(rc);
+            if ((rc = dalloc(h, (void**)&L.cg_q, plane_bytes)) != DD_OK) return fail(rc);
+            if ((rc = dalloc_t(h, &L.cg_part, (size_t)C * dd::cg_blocks(hh, ww))) != DD_OK) return fail(rc);
+            if ((rc = dalloc_t(h, &L.cg_scal, (size_t)3 * C)) != DD_OK) return fail(rc);
+        }
         hh = (hh + 1) / 2; ww = (ww + 1) / 2;
     }
     Level& F = h->lv[0];
@@ -734,6 +817,14 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if ((rc = dalloc_t(h, &h->norms2_d, (size_t)2 * C + 2)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->sstate_d, 4)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->inner_ref_d, (size_t)C)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->ones_d, (size_t)C)) != DD_OK) return fail(rc);
+    {
+        std::vector<double> ones(C, 1.0);
+        if (cudaMemcpy(h->ones_d, ones.data(), sizeof(double) * C, cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_error("cudaMemcpy");
+            return fail(DD_ECUDA);
+        }
+    }
     if ((rc = dalloc_t(h, &h->scale_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->scale_inv_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->flag_d, 4)) != DD_OK) return fail(rc);
@@ -791,6 +882,7 @@ void dd_params_default(dd_params* p) {
     p->coarse_sweeps = 12;
     p->timing = 0;
     p->tile_warps = 0;
+    p->solver = DD_SOLVER_ORAS;
 }
 
 const char* dd_strerror(int code) {
@@ -924,6 +1016,7 @@ int dd_inpaint_get_iterate(dd_handle h, float* u_out, void* stream) {
 
 int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     if (!h || n < 0) { set_error("bad sweep arguments"); return DD_EINVAL; }
+    if (h->prm.solver != DD_SOLVER_ORAS) { set_error("dd_inpaint_sweep needs DD_SOLVER_ORAS"); return DD_EINVAL; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Level& F = h->lv[0];
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, h->cur, st));

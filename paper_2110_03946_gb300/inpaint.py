@@ -18,7 +18,7 @@ ML_MODES = {"cascade": B.DD_ML_CASCADE, "correction": B.DD_ML_CORRECTION}
 def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_mode=None,
                 robin_p=None, precision=None, max_sweeps=None, coarse_tol=None, inner_tol=None,
                 max_corrections=None, coarse_sweeps=None, inputs_on_device=1, timing=None,
-                tile_warps=None) -> B.dd_params:
+                tile_warps=None, solver=None) -> B.dd_params:
     p = B.dd_params_default()
     if block is not None: p.block = int(block)
     if overlap is not None: p.overlap = int(overlap)
@@ -35,6 +35,8 @@ def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_m
     if coarse_sweeps is not None: p.coarse_sweeps = int(coarse_sweeps)
     if timing is not None: p.timing = int(timing)
     if tile_warps is not None: p.tile_warps = int(tile_warps)
+    if solver is not None:
+        p.solver = {"oras": B.DD_SOLVER_ORAS, "cg": B.DD_SOLVER_CG}[solver] if isinstance(solver, str) else int(solver)
     p.inputs_on_device = int(inputs_on_device)
     return p
 

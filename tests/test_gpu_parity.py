@@ -128,6 +128,9 @@ SOLVE_CASES = [
     ("rgb_bf16ref", 200, 330, 3, dict(block=32, overlap=6, levels=3, precision="bf16_ref")),
     ("rgb_b64", 190, 260, 3, dict(block=64, overlap=4, levels=2, precision="fp32_ref")),
     ("rgb_b16", 190, 260, 2, dict(block=16, overlap=2, levels=2, precision="fp32")),
+    ("gray256_cg_1level", 256, 256, 1, dict(levels=1, precision="fp32", solver="cg", max_sweeps=2000)),
+    ("rgb_mlcg_3level", 200, 330, 3, dict(levels=3, precision="fp32", solver="cg", max_sweeps=2000,
+                                          coarse_sweeps=200, coarse_tol=1e-3)),
 ]
 
 
