@@ -332,12 +332,12 @@ def run_studies(dev, params):
     from paper_2110_03946_gb300.inpaint import Inpainter
     out = {}
 
-    def timed(ip, reps=3):
+    def timed(ip, reps=3, tol=TOL):
         o = torch.empty((ip.C, ip.H, ip.W), dtype=torch.float32, device=dev)
-        ip.solve(TOL, out=o)
+        ip.solve(tol, out=o)
         ts = []
         for _ in range(reps):
-            ip.solve(TOL, out=o)
+            ip.solve(tol, out=o)
             ts.append(ip.stats()["ms_total"])
         return float(np.median(ts)), ip.stats(), o
 
@@ -374,18 +374,24 @@ def run_studies(dev, params):
     out["psnr_vs_residual"] = ps
 
     # the paper's comparison solvers on the same 4K frame: single-level and
-    # multilevel conjugate gradients against multilevel ORAS (Sec. 5, Fig. 2(a))
+    # multilevel conjugate gradients against multilevel ORAS (Sec. 5, Fig. 2(a)),
+    # at the paper's comparison tolerance 1e-3 and at the bench tolerance
     cmp_ = {}
-    for name, prm_ in [("ml_oras", dict(params)),
-                       ("ml_cg", dict(levels=params.get("levels", 4), solver="cg", max_sweeps=4000,
-                                      coarse_sweeps=400, coarse_tol=params.get("coarse_tol", 3e-3))),
-                       ("cg_single_level", dict(levels=1, solver="cg", max_sweeps=4000))]:
-        with Inpainter(md, fd, device=dev, precision="fp32", **prm_) as ip:
-            ms_, st, _ = timed(ip, reps=2)
-        cmp_[name] = {"ms": ms_, "fine_iterations": st["sweeps_per_level"][0],
-                      "iterations_per_level": st["sweeps_per_level"][:prm_.get("levels", 1)],
-                      "rel_residual": max(st["rel_residual"][:3])}
-    cmp_["speedup_ml_oras_vs_ml_cg"] = cmp_["ml_cg"]["ms"] / cmp_["ml_oras"]["ms"]
+    for tol in (1e-3, TOL):
+        row = {}
+        for name, prm_ in [("ml_oras", dict(params)),
+                           ("ml_cg", dict(levels=params.get("levels", 4), solver="cg", max_sweeps=4000,
+                                          coarse_sweeps=400, coarse_tol=params.get("coarse_tol", 3e-3))),
+                           ("cg_single_level", dict(levels=1, solver="cg", max_sweeps=4000))]:
+            with Inpainter(md, fd, device=dev, precision="fp32", **prm_) as ip:
+                ms_, st, _ = timed(ip, reps=2, tol=tol)
+            row[name] = {"ms": ms_, "fine_iterations": st["sweeps_per_level"][0],
+                         "iterations_per_level": st["sweeps_per_level"][:prm_.get("levels", 1)],
+                         "rel_residual": max(st["rel_residual"][:3])}
+        row["speedup_ml_oras_vs_ml_cg"] = row["ml_cg"]["ms"] / row["ml_oras"]["ms"]
+        row["cg_ms_per_fine_iteration"] = row["cg_single_level"]["ms"] / max(
+            1, row["cg_single_level"]["fine_iterations"])
+        cmp_[f"tol_{tol:g}"] = row
     out["oras_vs_cg"] = cmp_
     return out
 
@@ -407,7 +413,10 @@ def run_ours(args):
     dmask = [torch.as_tensor(m).to(dev) for _, m in frames]
     dvals = [torch.as_tensor(f).to(dev) for f, _ in frames]
     tuned, tuned_src = solver_params(args, args.precision)
-    prm = dict(tuned, precision=args.precision, timing=1)
+    # device loops (the default) in the timed region; the roofline pass below
+    # times every fine sweep launch with CUDA events (timing=1: launches)
+    prm = dict(tuned, precision=args.precision)
+    prm_timed = dict(prm, timing=1)
     stream = torch.cuda.current_stream(dev)
 
     # Frames resident in HBM.  With FP32 storage two solver handles on two
@@ -484,8 +493,6 @@ def run_ours(args):
     elapsed = t_start.elapsed_time(t_end) / 1e3
     lat = sorted(e0.elapsed_time(e1) for e0, e1 in lat_ev.values())
     launches = sum(ip.stats()["kernel_launches"] for ip in ips) - launches0
-    sweep_ms = sum(st_["fine_sweep_ms"] for st_ in stats)
-    sweep_n = sum(st_["fine_sweep_launches"] for st_ in stats)
     if world > 1:
         t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -502,7 +509,7 @@ def run_ours(args):
     # sweeps share the SMs, which stretches each launch; the roofline uses
     # single-stream solves of the same frames right after the timed region.
     iso_ms, iso_n = 0.0, 0
-    with Inpainter(dmask[0], dvals[0], device=dev, **prm) as ipi:
+    with Inpainter(dmask[0], dvals[0], device=dev, **prm_timed) as ipi:
         for i in range(6):
             j = i % args.frames
             B.check(B.dd_inpaint_set_data(ipi._h, dmask[j].data_ptr(), dvals[j].data_ptr(), 0), "set_data")
@@ -550,7 +557,7 @@ def run_ours(args):
         if pipelined:
             B.check(B.dd_inpaint_solve_finish(hs2[k], e_streams[k]), "solve_finish")
             rc_, st_ = B.dd_inpaint_stats(hs2[k])
-            if st_.sweeps_per_level[0] > 16:          # the finish continued: copy the final result
+            if st_.host_continued:          # the finish rewrote the output: copy the final result
                 houts[k].copy_(douts[k])
         e_streams[k].synchronize()
 
@@ -652,7 +659,6 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (fine-level ORAS sweep) ---------------
     st = stats[-1]
     avg_sweep_s = (iso_ms / iso_n) / 1e3 if iso_n else None
-    avg_sweep_region_s = (sweep_ms / sweep_n) / 1e3 if sweep_n else None
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FP32 FMA at max clock
@@ -668,11 +674,8 @@ def run_ours(args):
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "kernel": "oras_sweep_kernel (fine level)", "launches_timed": iso_n,
                 "avg_launch_ms": avg_sweep_s * 1e3 if avg_sweep_s else None,
-                "timing": "CUDA events around each fine sweep launch of single-stream solves of the bench frames",
-                "in_timed_region": {"launches": sweep_n,
-                                    "avg_launch_ms": avg_sweep_region_s * 1e3 if avg_sweep_region_s else None,
-                                    "frac": (flops / avg_sweep_region_s / 1e12 / alu_peak) if avg_sweep_region_s else None,
-                                    "note": "two frames in flight share the SMs, so launches are longer"},
+                "timing": "CUDA events around each fine sweep launch of single-stream solves of the bench frames "
+                          "(launch path; the timed region runs the same kernel inside device graph loops)",
                 "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                                f"{sm_max:.0f} MHz (sm_max_mhz of measured peaks)",
                 "hbm": {"achieved_gbs": hbm_alg / avg_sweep_s / 1e9 if avg_sweep_s else None,

@@ -85,13 +85,17 @@ typedef struct dd_params {
     double coarse_tol;       /* relative residual that ends a coarse level (default 1e-2) */
     double inner_tol;        /* relative residual decrease per outer correction (default 3e-3) */
     int    max_corrections;  /* outer FP64 corrections limit (default 30) */
-    int    coarse_sweeps;    /* sweeps launched per coarse level (default 12); launches after the
-                                coarse tolerance is met do no work */
+    int    coarse_sweeps;    /* sweep limit per coarse level (default 12) */
     int    timing;           /* 1: time every fine-level sweep launch with CUDA events (dd_stats) */
     int    tile_warps;       /* warps holding one block tile: 0 = default; block 16: 1;
                                 block 32: 1, 2 or 4; block 64: 4 or 8 */
     int    solver;           /* DD_SOLVER_ORAS (default) or DD_SOLVER_CG (needs DD_PREC_FP32);
                                 with CG, max_sweeps / coarse_sweeps count CG iterations */
+    int    device_loop;      /* 1 (default): a level's sweeps (or CG iterations) repeat inside a
+                                CUDA graph loop on the device until its stop test or sweep limit,
+                                no launch after the stop; 0: launched in fixed chunks whose launches
+                                after the stop do no work.  Timing (timing = 1) and stream
+                                capture (dd_batch) always use launches */
 } dd_params;
 
 #define DD_MAX_STAT_CHANNELS 16
@@ -104,13 +108,19 @@ typedef struct dd_stats {
     int    converged;                          /* 1 if the stop test held */
     int    channels;
     double rel_residual[DD_MAX_STAT_CHANNELS]; /* FP64 ||b-Au||/||b-Au0|| of the output, u0 = Cf */
-    double ms_total;                           /* device time of the last solve (CUDA events) */
+    double ms_total;                           /* time of the last solve on its stream (CUDA events
+                                                  around all of its work, a host-controlled
+                                                  continuation included) */
     size_t device_bytes;                       /* device memory owned by the handle */
     long long kernel_launches;                 /* CUDA kernels launched through the handle since create */
     long long local_unknowns;                  /* unknown pixels summed over the fine level's blocks,
                                                   one channel (work of one local problem set) */
     int    fine_sweep_launches;                /* timed fine-level sweep launches (params.timing) */
     double fine_sweep_ms;                      /* their summed device time */
+    int    host_continued;                     /* 1: the enqueued part of the solve ended above tol and
+                                                  dd_inpaint_solve_finish continued under host control,
+                                                  rewriting u_out (work enqueued on the stream after
+                                                  dd_inpaint_solve_async saw the earlier result) */
 } dd_stats;
 
 /* Fill *p with the defaults listed above. */

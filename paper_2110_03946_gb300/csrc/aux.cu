@@ -238,10 +238,12 @@ __global__ void count_nonzero_kernel(const uint8_t* __restrict__ m, long long n,
 
 // ---- device-side control of a sweep sequence ------------------------------------------
 // After a sweep sequence: out = {buffer holding the result, full sweeps applied, flag value}.
-__global__ void resolve_kernel(const int* __restrict__ flag, const int* __restrict__ ss, int* __restrict__ out) {
+__global__ void resolve_kernel(const int* __restrict__ flag, const int* __restrict__ ss, const int* __restrict__ ctl,
+                               int* __restrict__ out) {
     out[0] = ss[0];
     out[1] = ss[1];
     out[2] = flag[0];
+    out[3] = ctl ? ctl[0] : 0;
 }
 
 __global__ void reset_sweep_state_kernel(int* __restrict__ state, int* __restrict__ flag, int cur) {
@@ -249,6 +251,14 @@ __global__ void reset_sweep_state_kernel(int* __restrict__ state, int* __restric
         state[threadIdx.x] = threadIdx.x == 0 ? cur : 0;
         flag[threadIdx.x] = 0;
     }
+}
+
+__global__ void loop_ctl_kernel(const int* __restrict__ flag, const int* __restrict__ state, int* __restrict__ ctl,
+                                int cap, int max_passes, cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0) return;
+    const int passes = ctl[0] + 1;
+    ctl[0] = passes;
+    if (flag[0] != 0 || state[1] >= cap || passes >= max_passes) cudaGraphSetConditional(cond, 0);
 }
 
 __global__ void prolong_sel_kernel(int Hc, int Wc, int H, int W, const float* __restrict__ uc0,
@@ -395,13 +405,19 @@ cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long upla
 
 namespace dd {
 
-cudaError_t launch_resolve(const int* flag, const int* sweep_state, int* out, cudaStream_t st) {
-    resolve_kernel<<<1, 1, 0, st>>>(flag, sweep_state, out);
+cudaError_t launch_resolve(const int* flag, const int* sweep_state, const int* ctl, int* out, cudaStream_t st) {
+    resolve_kernel<<<1, 1, 0, st>>>(flag, sweep_state, ctl, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, cudaStream_t st) {
     reset_sweep_state_kernel<<<1, 32, 0, st>>>(state, flag, cur);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_ctl(const int* flag, const int* state, int* ctl, int cap, int max_passes,
+                            cudaGraphConditionalHandle cond, cudaStream_t st) {
+    loop_ctl_kernel<<<1, 32, 0, st>>>(flag, state, ctl, cap, max_passes, cond);
     return cudaGetLastError();
 }
 

@@ -8,6 +8,9 @@
 //   cg_apply:  p <- r + beta p (formed on the fly for the pixel and its four
 //              neighbours, written to the other p buffer), q = A p, (p, q);
 //   cg_update: x += alpha p, r -= alpha q, (r, r).
+// The iteration index (and with it beta = 0 on the first iteration and the
+// choice of p buffers) is read from device state, so an iteration's two
+// launches are the same every time and can repeat in a graph loop.
 // Each kernel's last block (atomic ticket) reduces the per-block partials of
 // every channel in a fixed order and computes alpha, or beta and the stop test
 // (max over channels of sqrt((r, r)) / ||b - A u0|| <= tol), so iterations run
@@ -20,7 +23,9 @@ namespace dd {
 
 namespace {
 
-constexpr int CG_TX = 32, CG_TY = 8, CG_ROWS = 8;   // a block covers 32 x 64 pixels
+// A thread owns 4 consecutive pixels (one float4; the pitch is a multiple of 32
+// floats) in each of CG_ROWS rows; a warp covers 128 columns, a block 128 x 64.
+constexpr int CG_TX = 32, CG_TY = 8, CG_ROWS = 8, CG_VEC = 4;
 constexpr int CG_THREADS = CG_TX * CG_TY;
 
 // sum over the block of v (double), result valid in thread 0
@@ -56,48 +61,76 @@ __device__ double channel_sum(const double* part, int c, int nblk, double* sh) {
     return s;   // valid in thread 0
 }
 
+// Known pixels carry r = p = q = 0 throughout (the residual pass writes r = 0
+// there and both kernels preserve it), so p = r + beta p_old needs no mask; the
+// mask only zeroes q.  Columns at or beyond W are zeroed explicitly, whatever
+// the pitch padding holds.
 __global__ void __launch_bounds__(CG_THREADS) cg_apply_kernel(CGArgs a) {
     if (a.flag[0] != 0) return;
     const int c = blockIdx.z;
-    const int x = blockIdx.x * CG_TX + threadIdx.x;
-    const int yb = blockIdx.y * (CG_TY * CG_ROWS) + threadIdx.y * CG_ROWS;
-    const float beta = a.first ? 0.f : (float)a.scal[2 * a.C + c];
+    const int x0 = (blockIdx.x * CG_TX + threadIdx.x) * CG_VEC;
+    const int yb = (blockIdx.y * CG_TY + threadIdx.y) * CG_ROWS;
+    const int it = __ldcg(a.state + 1);   // iterations applied before this one
+    const float beta = it == 0 ? 0.f : (float)a.scal[2 * a.C + c];
     const long long base = (long long)c * a.plane;
     const float* __restrict__ r = a.r + base;
-    const float* __restrict__ po = a.p_old + base;
-    float* __restrict__ pn = a.p_new + base;
+    const float* __restrict__ po = a.p[it & 1] + base;
+    float* __restrict__ pn = a.p[(it + 1) & 1] + base;
     float* __restrict__ q = a.q + base;
-    const bool xin = x < a.W;
-    // p = r + beta p_old for this column, rows yb-1 .. yb+CG_ROWS (0 outside the
-    // image and on known pixels); horizontal neighbours come from the next lanes
-    auto pval = [&](int y, int xx) -> float {
+    const bool xin = x0 < a.W;
+    auto prow = [&](int y) -> float4 {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (xin && y >= 0 && y < a.H) {
+            const size_t o = (size_t)y * a.P + x0;
+            const float4 rv = *reinterpret_cast<const float4*>(r + o);
+            const float4 pv = *reinterpret_cast<const float4*>(po + o);
+            v.x = fmaf(beta, pv.x, rv.x);
+            v.y = x0 + 1 < a.W ? fmaf(beta, pv.y, rv.y) : 0.f;
+            v.z = x0 + 2 < a.W ? fmaf(beta, pv.z, rv.z) : 0.f;
+            v.w = x0 + 3 < a.W ? fmaf(beta, pv.w, rv.w) : 0.f;
+        }
+        return v;
+    };
+    auto pone = [&](int y, int xx) -> float {
         if (y < 0 || y >= a.H || xx < 0 || xx >= a.W) return 0.f;
         const size_t o = (size_t)y * a.P + xx;
-        return a.mask[(size_t)y * a.mp + xx] ? 0.f : fmaf(beta, po[o], r[o]);
+        return fmaf(beta, po[o], r[o]);
     };
-    float col[CG_ROWS + 2];
+    float4 col[CG_ROWS + 2];
 #pragma unroll
-    for (int k = 0; k < CG_ROWS + 2; ++k) col[k] = xin ? pval(yb - 1 + k, x) : 0.f;
+    for (int k = 0; k < CG_ROWS + 2; ++k) col[k] = prow(yb - 1 + k);
+    const float dx0 = (float)((x0 > 0) + (x0 < a.W - 1));
+    const float dx1 = (float)(1 + (x0 + 1 < a.W - 1));
+    const float dx2 = (float)(1 + (x0 + 2 < a.W - 1));
+    const float dx3 = (float)(1 + (x0 + 3 < a.W - 1));
     float pq = 0.f;
 #pragma unroll
     for (int k = 0; k < CG_ROWS; ++k) {
         const int y = yb + k;
-        const float pc = col[k + 1];
-        float left = __shfl_up_sync(0xffffffffu, pc, 1);
-        float right = __shfl_down_sync(0xffffffffu, pc, 1);
-        if (threadIdx.x == 0) left = pval(y, x - 1);
-        if (threadIdx.x == CG_TX - 1) right = pval(y, x + 1);
+        const float4 pc = col[k + 1], pu = col[k], pd = col[k + 2];
+        float left = __shfl_up_sync(0xffffffffu, pc.w, 1);
+        float right = __shfl_down_sync(0xffffffffu, pc.x, 1);
+        if (threadIdx.x == 0) left = pone(y, x0 - 1);
+        if (threadIdx.x == CG_TX - 1) right = pone(y, x0 + CG_VEC);
         if (!xin || y >= a.H) continue;
-        const size_t o = (size_t)y * a.P + x;
-        pn[o] = pc;
-        if (a.mask[(size_t)y * a.mp + x]) {
-            q[o] = 0.f;
-            continue;
-        }
-        const float deg = (float)((y > 0) + (y < a.H - 1) + (x > 0) + (x < a.W - 1));
-        const float qv = fmaf(deg, pc, -((col[k] + col[k + 2]) + (left + right)));
-        q[o] = qv;
-        pq = fmaf(pc, qv, pq);
+        const float dy = (float)((y > 0) + (y < a.H - 1));
+        const unsigned char* mr = a.mask + (size_t)y * a.mp + x0;
+        const bool u0 = !mr[0];
+        const bool u1 = x0 + 1 < a.W && !mr[1];
+        const bool u2 = x0 + 2 < a.W && !mr[2];
+        const bool u3 = x0 + 3 < a.W && !mr[3];
+        float4 qv;
+        qv.x = u0 ? fmaf(dy + dx0, pc.x, -((pu.x + pd.x) + (left + pc.y))) : 0.f;
+        qv.y = u1 ? fmaf(dy + dx1, pc.y, -((pu.y + pd.y) + (pc.x + pc.z))) : 0.f;
+        qv.z = u2 ? fmaf(dy + dx2, pc.z, -((pu.z + pd.z) + (pc.y + pc.w))) : 0.f;
+        qv.w = u3 ? fmaf(dy + dx3, pc.w, -((pu.w + pd.w) + (pc.z + right))) : 0.f;
+        const size_t o = (size_t)y * a.P + x0;
+        *reinterpret_cast<float4*>(pn + o) = pc;
+        *reinterpret_cast<float4*>(q + o) = qv;
+        pq = fmaf(pc.x, qv.x, pq);
+        pq = fmaf(pc.y, qv.y, pq);
+        pq = fmaf(pc.z, qv.z, pq);
+        pq = fmaf(pc.w, qv.w, pq);
     }
     __shared__ double sh[CG_THREADS / 32];
     __shared__ int s_last;
@@ -116,28 +149,42 @@ __global__ void __launch_bounds__(CG_THREADS) cg_apply_kernel(CGArgs a) {
     if (threadIdx.x == 0 && threadIdx.y == 0) a.flag[3] = 0;
 }
 
+// x += alpha p, r -= alpha q on whole float4s: on known pixels p = q = 0 leaves
+// x and r (= 0) as they are; columns at or beyond W stay out of (r, r).
 __global__ void __launch_bounds__(CG_THREADS) cg_update_kernel(CGArgs a) {
     if (a.flag[0] != 0) return;
     const int c = blockIdx.z;
-    const int x = blockIdx.x * CG_TX + threadIdx.x;
-    const int yb = blockIdx.y * (CG_TY * CG_ROWS) + threadIdx.y * CG_ROWS;
+    const int x0 = (blockIdx.x * CG_TX + threadIdx.x) * CG_VEC;
+    const int yb = (blockIdx.y * CG_TY + threadIdx.y) * CG_ROWS;
+    const int it = __ldcg(a.state + 1);   // incremented by this launch's last block
     const float alpha = (float)a.scal[a.C + c];
     const long long base = (long long)c * a.plane;
     float* __restrict__ xv = a.x + base;
     float* __restrict__ r = a.r + base;
-    const float* __restrict__ p = a.p_new + base;
+    const float* __restrict__ p = a.p[(it + 1) & 1] + base;
     const float* __restrict__ q = a.q + base;
     float rr = 0.f;
-    if (x < a.W) {
+    if (x0 < a.W) {
+        const bool in1 = x0 + 1 < a.W, in2 = x0 + 2 < a.W, in3 = x0 + 3 < a.W;
+#pragma unroll
         for (int k = 0; k < CG_ROWS; ++k) {
             const int y = yb + k;
             if (y >= a.H) break;
-            if (a.mask[(size_t)y * a.mp + x]) continue;
-            const size_t o = (size_t)y * a.P + x;
-            xv[o] = fmaf(alpha, p[o], xv[o]);
-            const float rn = fmaf(-alpha, q[o], r[o]);
-            r[o] = rn;
-            rr = fmaf(rn, rn, rr);
+            const size_t o = (size_t)y * a.P + x0;
+            float4 xo = *reinterpret_cast<const float4*>(xv + o);
+            float4 ro = *reinterpret_cast<const float4*>(r + o);
+            const float4 pv = *reinterpret_cast<const float4*>(p + o);
+            const float4 qv = *reinterpret_cast<const float4*>(q + o);
+            xo.x = fmaf(alpha, pv.x, xo.x); xo.y = fmaf(alpha, pv.y, xo.y);
+            xo.z = fmaf(alpha, pv.z, xo.z); xo.w = fmaf(alpha, pv.w, xo.w);
+            ro.x = fmaf(-alpha, qv.x, ro.x); ro.y = fmaf(-alpha, qv.y, ro.y);
+            ro.z = fmaf(-alpha, qv.z, ro.z); ro.w = fmaf(-alpha, qv.w, ro.w);
+            *reinterpret_cast<float4*>(xv + o) = xo;
+            *reinterpret_cast<float4*>(r + o) = ro;
+            rr = fmaf(ro.x, ro.x, rr);
+            rr = in1 ? fmaf(ro.y, ro.y, rr) : rr;
+            rr = in2 ? fmaf(ro.z, ro.z, rr) : rr;
+            rr = in3 ? fmaf(ro.w, ro.w, rr) : rr;
         }
     }
     __shared__ double sh[CG_THREADS / 32];
@@ -161,9 +208,9 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update_kernel(CGArgs a) {
         }
     }
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-        a.state[1] += 1;   // iterations applied
-        if (bad) { a.flag[0] = 2; a.flag[1] = a.iter; }
-        else if (worst <= a.tol) { a.flag[0] = 1; a.flag[1] = a.iter; }
+        a.state[1] = it + 1;   // iterations applied
+        if (bad) { a.flag[0] = 2; a.flag[1] = it; }
+        else if (worst <= a.tol) { a.flag[0] = 1; a.flag[1] = it; }
         a.flag[3] = 0;
     }
 }
@@ -179,7 +226,8 @@ __global__ void cg_init_kernel(const double2* __restrict__ res_out, double* __re
 }
 
 dim3 cg_grid(int H, int W, int C) {
-    return dim3((W + CG_TX - 1) / CG_TX, (H + CG_TY * CG_ROWS - 1) / (CG_TY * CG_ROWS), C);
+    const int cols = CG_TX * CG_VEC, rows = CG_TY * CG_ROWS;
+    return dim3((W + cols - 1) / cols, (H + rows - 1) / rows, C);
 }
 
 }  // namespace

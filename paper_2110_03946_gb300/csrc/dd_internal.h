@@ -60,13 +60,16 @@ cudaError_t make_tile_map(CUtensorMap* out, Store st, const void* base, int H, i
 //   1 when max_c sqrt(norms2[c]) / ref[c] <= tol (tol < 0: never),
 //   2 on NaN/Inf, 3 when stall > 0 and every channel's residual fell by less
 //   than the factor 1/stall since the previous full sweep;
-// flag[1] = sweep_index then.  flag[0] != 0 makes later launches no-ops.
+// flag[1] = the launch index (state[3]) then.  flag[0] != 0 makes later launches no-ops.
 // flag[2] is set if a bounded wait for a staged tile gave up; flag[3] is the
 // completion ticket (0 between launches).  slots >= the launch grid.
 // The iterate pair is chosen on the device: state[0] is the buffer holding the
 // current iterate (the launch reads it and writes the other one), state[1]
 // counts full sweeps, state[2] = 1 makes the next launch a probe that only
-// evaluates the residual of the current iterate (no CG, no write-back).  After
+// evaluates the residual of the current iterate (no CG, no write-back), and
+// state[3] counts the launches that ran (the stall test needs a previous
+// sweep), so that a launch needs no per-launch argument and the same launch
+// can repeat inside a graph loop.  After
 // a full sweep the last CTA requests a probe when the residual ratio of the
 // last two sweeps predicts that the new iterate meets tol.  norms2 holds
 // 2C + 2 doubles: current norms, norms of the previous full sweep, and the
@@ -80,7 +83,6 @@ struct SweepStop {
     double stall;
     int* flag;
     int* state;
-    int sweep_index;
     int force_probe;   // 1: this launch is a probe whatever state[2] says
 };
 constexpr int kSweepSlots = 4096;   // per-channel partial slots that cover any persistent grid
@@ -99,8 +101,20 @@ cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, co
                          const CUtensorMap* map_g, const uint32_t* tmask, const SweepStop& stop, float p_robin,
                          int k, cudaStream_t stream);
 
+// Kernel attributes and occupancy of the sweep for (s, g, has_g), queried once
+// per process; call before capturing a sweep launch into a graph.
+cudaError_t prepare_sweep(Store s, const TileGeom& g, bool has_g);
+
 // state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..3] = 0.
 cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, cudaStream_t st);
+
+// Loop control at the end of each pass of a graph WHILE loop (one thread):
+// ctl[0] counts the passes; the loop's condition is cleared when flag[0] != 0
+// (stopped, converged or failed), when state[1] (full sweeps or CG iterations
+// applied) reaches cap, or after max_passes passes, which bounds the loop
+// whatever the solver kernels do.
+cudaError_t launch_loop_ctl(const int* flag, const int* state, int* ctl, int cap, int max_passes,
+                            cudaGraphConditionalHandle cond, cudaStream_t st);
 
 // ---- auxiliary passes (aux.cu) ----------------------------------------------------
 // dst[c][y][x] (pitch dp) = mask ? src[c][y][x] : 0  (src pitch sp)
@@ -153,8 +167,9 @@ cudaError_t launch_convert(int H, int W, int C, const float* src, int sp, long l
 
 // Summary of a sweep sequence for later steps: out[0] = buffer holding the
 // result, out[1] = full sweeps applied, out[2] = the stop flag (0: not
-// stopped, 1: converged, 2: NaN/Inf, 3: stalled).
-cudaError_t launch_resolve(const int* flag, const int* sweep_state, int* out, cudaStream_t st);
+// stopped, 1: converged, 2: NaN/Inf, 3: stalled), out[3] = passes of the
+// device loop (ctl[0]; 0 without ctl).
+cudaError_t launch_resolve(const int* flag, const int* sweep_state, const int* ctl, int* out, cudaStream_t st);
 // Prolongation / copy reading the source buffer uc0 or uc1 chosen by *sel on the device.
 cudaError_t launch_prolong_sel(int Hc, int Wc, int H, int W, int C, const float* uc0, const float* uc1,
                                const int* sel, int ucp, long long ucplane, const uint8_t* mask, int mp,
@@ -174,16 +189,15 @@ struct CGArgs {
     const uint8_t* mask;
     float* x;            // iterate (known pixels hold f)
     float* r;            // residual on unknown pixels
-    const float* p_old;  // search direction of the previous iteration
-    float* p_new;        // search direction of this iteration
+    float* p[2];         // search directions: iteration i reads p[i & 1] (the previous
+                         // one; zero before the first) and writes p[(i + 1) & 1]
     float* q;            // A p
     double* part;        // C x cg_blocks partial sums
     double* scal;        // [0,C) (r,r), [C,2C) alpha, [2C,3C) beta
     const double* ref;   // per-channel ||b - A u0||
     int* flag;           // [0] stop flag, [1] stopping iteration, [3] ticket
-    int* state;          // [1] counts iterations
-    int iter;
-    int first;           // 1: beta = 0 (first iteration of a run)
+    int* state;          // [1] = i, the iterations applied since the reset (read on
+                         // the device, so one iteration's launches can repeat in a graph loop)
     double tol;
 };
 int cg_blocks(int H, int W);

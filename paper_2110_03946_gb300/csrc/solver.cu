@@ -46,10 +46,20 @@ void set_error(const std::string& s) { g_last_error = s; }
     } while (0)
 
 // A kernel launch through the handle: checked and counted.
-#define DD_LAUNCH(h, call)   \
-    do {                     \
-        DD_CK(call);         \
-        ++(h)->launches;     \
+// A launch wrapper reports (and clears) an error left pending by an earlier
+// unchecked runtime call before the launch, so the error names its real origin
+// rather than the next kernel.
+#define DD_LAUNCH(h, call)                                                                      \
+    do {                                                                                        \
+        const cudaError_t pend_ = cudaPeekAtLastError();                                        \
+        if (pend_ != cudaSuccess) {                                                             \
+            (void)cudaGetLastError();                                                           \
+            set_error(std::string("CUDA error pending before ") + #call + ": " +                 \
+                      cudaGetErrorString(pend_));                                               \
+            return DD_ECUDA;                                                                    \
+        }                                                                                       \
+        DD_CK(call);                                                                            \
+        ++(h)->launches;                                                                        \
     } while (0)
 
 #define DD_TRY(expr)                \
@@ -59,6 +69,24 @@ void set_error(const std::string& s) { g_last_error = s; }
     } while (0)
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// A level's iteration as a CUDA graph: a memset resets the pass counter, then a
+// WHILE node repeats one pass (one ORAS sweep or probe, or one CG iteration,
+// followed by the loop-control kernel) until the stop test, the sweep limit
+// `cap` or the pass bound clears its condition.  Built for one (cap, tol) and
+// rebuilt when either changes.
+struct LoopGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int cap = 0;
+    double tol = 0.0;
+};
+
+void destroy_loop(LoopGraph& G) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G = LoopGraph{};
+}
 
 struct Level {
     int H = 0, W = 0, P = 0;
@@ -78,6 +106,8 @@ struct Level {
     float* cg_q = nullptr;
     double* cg_part = nullptr;   // C x cg_blocks
     double* cg_scal = nullptr;   // 3C
+    LoopGraph loop;              // device loop of this level's iteration (params.device_loop)
+    bool loop_pending = false;   // a loop ran since the launch count was last updated
     long long plane() const { return (long long)H * P; }
 };
 
@@ -105,7 +135,9 @@ struct dd_inpaint {
     double2* res_out = nullptr;     // C
     double* norms2_d = nullptr;     // C
     int* flag_d = nullptr;          // [0] stop flag, [1] conv_at, [2] device wait timed out, [3] ticket
-    int* sstate_d = nullptr;        // sweep state: current buffer, full sweeps, probe request
+    int* sstate_d = nullptr;        // sweep state: current buffer, full sweeps, probe request, launches
+    int* ctl_d = nullptr;           // device-loop pass counter (4 ints)
+    cudaStream_t cap_stream = nullptr;   // private stream on which loop bodies are captured
     // pinned host mirrors
     double2* h_res = nullptr;
     double* h_small = nullptr;      // 3*C doubles scratch
@@ -176,6 +208,7 @@ int validate(int H, int W, int C, const dd_params& p) {
         return DD_EINVAL;
     }
     if (p.overlap < 0 || p.overlap >= p.block) { set_error("need 0 <= overlap < block"); return DD_EINVAL; }
+    if (p.device_loop != 0 && p.device_loop != 1) { set_error("device_loop must be 0 or 1"); return DD_EINVAL; }
     if (p.local_cg_iters < 1 || p.local_cg_iters > 4096) { set_error("local_cg_iters out of range"); return DD_EINVAL; }
     if (p.levels < 1 || p.levels > DD_MAX_LEVELS) { set_error("levels must be 1..8"); return DD_EINVAL; }
     if (p.ml_mode != DD_ML_CASCADE) { set_error("ml_mode: only DD_ML_CASCADE is implemented"); return DD_EINVAL; }
@@ -284,21 +317,19 @@ int run_sweeps(dd_inpaint* h, const TileGeom& g, Store st_t, void* const bufs[2]
     *applied = 0;
     const bool timed = fine && h->prm.timing != 0;
     const dd::SweepPair pair{{&maps[0], &maps[1]}, {bufs[0], bufs[1]}};
-    dd::SweepStop stop{partial, dd::kSweepSlots, h->norms2_d, ref_d, tol, stall, h->flag_d, h->sstate_d, 0, 0};
-    int full_done = 0, launched = 0;
+    dd::SweepStop stop{partial, dd::kSweepSlots, h->norms2_d, ref_d, tol, stall, h->flag_d, h->sstate_d, 0};
+    int full_done = 0;
     while (true) {
         // full sweeps until max_sweeps; then one probe evaluates the last iterate
         const bool last_probe = full_done >= max_sweeps;
         const int n = last_probe ? 1 : std::min(dd_inpaint::kChunk, max_sweeps - full_done);
         for (int i = 0; i < n; ++i) {
-            stop.sweep_index = launched + i;
             stop.force_probe = last_probe ? 1 : 0;
             if (timed && !last_probe) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
             DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, pair, map_g, tmask, stop, h->prm.robin_p,
                                           h->prm.local_cg_iters, st));
             if (timed && !last_probe) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
         }
-        launched += n;
         DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DD_CK(cudaMemcpyAsync(h->h_flag + 4, h->sstate_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         DD_CK(cudaStreamSynchronize(st));
@@ -372,30 +403,139 @@ int write_scaled_residual(dd_inpaint* h, cudaStream_t st) {
     return DD_OK;
 }
 
-// Enqueue n launches on level L starting from u[0] under the device stop test
-// (tol), then record which buffer holds the result into L.state_d.  No host
-// synchronisation: launches after the stop are no-ops, and a launch that the
-// previous one predicts to be the last only probes the residual.  With timing,
-// fine-level launches are bracketed by events (read after the next sync).
-int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed) {
-    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, st));
-    const dd::SweepPair pair{{&L.map_u[0], &L.map_u[1]}, {L.u[0], L.u[1]}};
-    dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, tol, 0.0, h->flag_d, h->sstate_d, 0, 0};
-    for (int i = 0; i < n; ++i) {
-        stop.sweep_index = i;
-        if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
-        DD_LAUNCH(h, dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), pair, nullptr, L.tmask, stop,
-                                      h->prm.robin_p, h->prm.local_cg_iters, st));
-        if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
+// Whether a level's iteration runs as a device loop (a graph WHILE node) rather
+// than as plain launches: per-sweep event timing and stream capture need the
+// launches.
+bool loop_mode(const dd_inpaint* h, bool capture, bool timed) {
+    return h->prm.device_loop != 0 && !capture && !timed;
+}
+
+// Kernels per pass of a device loop: the sweep (or CG's two) and the loop control.
+int pass_kernels(const dd_inpaint* h) { return h->prm.solver == DD_SOLVER_CG ? 3 : 2; }
+
+dd::CGArgs cg_args(const dd_inpaint* h, const Level& L, double tol) {
+    dd::CGArgs a{};
+    a.H = L.H; a.W = L.W; a.P = L.P; a.C = h->C; a.mp = L.W;
+    a.plane = L.plane();
+    a.mask = L.mask;
+    a.x = L.u[0]; a.r = L.cg_r; a.q = L.cg_q;
+    a.p[0] = L.cg_p[0]; a.p[1] = L.cg_p[1];
+    a.part = L.cg_part; a.scal = L.cg_scal; a.ref = L.ref_d;
+    a.flag = h->flag_d; a.state = h->sstate_d;
+    a.tol = tol;
+    return a;
+}
+
+// One pass of level L's iteration: an ORAS sweep (or probe) from the buffer
+// the device state names, or one CG iteration.
+int enqueue_pass(dd_inpaint* h, Level& L, double tol, cudaStream_t st) {
+    if (h->prm.solver == DD_SOLVER_CG) {
+        DD_CK(dd::launch_cg_iteration(cg_args(h, L, tol), st));
+        return DD_OK;
     }
-    DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, L.state_d, st));
+    const dd::SweepPair pair{{&L.map_u[0], &L.map_u[1]}, {L.u[0], L.u[1]}};
+    const dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, tol, 0.0, h->flag_d, h->sstate_d, 0};
+    DD_CK(dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), pair, nullptr, L.tmask, stop, h->prm.robin_p,
+                           h->prm.local_cg_iters, st));
     return DD_OK;
 }
 
-// Enqueue n CG iterations on level L from the iterate in u[0] (the residual is
+// Level L's loop graph for (cap, tol), built on first use (the body is
+// captured on the handle's private stream) and kept while both stay the same.
+// The pass bound: CG applies an iteration in every pass; ORAS follows a failed
+// probe by a full sweep, so at most 2 cap + 1 passes reach cap full sweeps.
+int loop_graph(dd_inpaint* h, Level& L, int cap, double tol, cudaGraphExec_t* out) {
+    LoopGraph& G = L.loop;
+    if (G.exec != nullptr && G.cap == cap && G.tol == tol) {
+        *out = G.exec;
+        return DD_OK;
+    }
+    destroy_loop(G);
+    if (h->prm.solver == DD_SOLVER_ORAS) DD_CK(dd::prepare_sweep(Store::F32, L.geom, false));
+    DD_CK(cudaGraphCreate(&G.graph, 0));
+    cudaGraphConditionalHandle cond;
+    DD_CK(cudaGraphConditionalHandleCreate(&cond, G.graph, 1, cudaGraphCondAssignDefault));
+    cudaMemsetParams ms{};
+    ms.dst = h->ctl_d;
+    ms.value = 0;
+    ms.elementSize = sizeof(int);
+    ms.width = 4;
+    ms.height = 1;
+    cudaGraphNode_t reset = nullptr, loop = nullptr;
+    DD_CK(cudaGraphAddMemsetNode(&reset, G.graph, nullptr, 0, &ms));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    DD_CK(cudaGraphAddNode(&loop, G.graph, &reset, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    DD_CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const int max_passes = h->prm.solver == DD_SOLVER_CG ? cap + 1 : 2 * cap + 2;
+    const int rc = enqueue_pass(h, L, tol, h->cap_stream);
+    const cudaError_t el = rc == DD_OK ? dd::launch_loop_ctl(h->flag_d, h->sstate_d, h->ctl_d, cap, max_passes, cond,
+                                                             h->cap_stream)
+                                       : cudaSuccess;
+    cudaGraph_t captured = body;
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &captured);
+    if (rc != DD_OK) {
+        destroy_loop(G);
+        return rc;
+    }
+    DD_CK(el);
+    DD_CK(ec);
+    DD_CK(cudaGraphInstantiate(&G.exec, G.graph, 0));
+    G.cap = cap;
+    G.tol = tol;
+    *out = G.exec;
+    return DD_OK;
+}
+
+// Run level L's loop graph on st and resolve its result into L.state_d.
+int run_loop(dd_inpaint* h, Level& L, int cap, double tol, cudaStream_t st) {
+    if (cap > 0) {   // (a WHILE body runs at least once)
+        cudaGraphExec_t ex = nullptr;
+        DD_TRY(loop_graph(h, L, cap, tol, &ex));
+        DD_CK(cudaGraphLaunch(ex, st));
+    } else {
+        DD_CK(cudaMemsetAsync(h->ctl_d, 0, 4 * sizeof(int), st));
+    }
+    DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, h->ctl_d, L.state_d, st));
+    L.loop_pending = true;
+    return DD_OK;
+}
+
+// After the level states have been read back (h_state, 4 ints per level):
+// add the kernels the device loops ran to the launch count.
+void count_loop_launches(dd_inpaint* h) {
+    for (size_t l = 0; l < h->lv.size() && l < DD_MAX_LEVELS; ++l) {
+        if (!h->lv[l].loop_pending) continue;
+        h->lv[l].loop_pending = false;
+        h->launches += (long long)h->h_state[4 * l + 3] * pass_kernels(h);
+    }
+}
+
+// ORAS on level L from the iterate in u[0], at most n full sweeps, under the
+// device stop test; the result is resolved into L.state_d.  No host
+// synchronisation.  Plain launches (loop = false): n launches, those after the
+// stop do no work.
+int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed, bool loop) {
+    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, st));
+    if (loop) return run_loop(h, L, n, tol, st);
+    for (int i = 0; i < n; ++i) {
+        if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
+        DD_TRY(enqueue_pass(h, L, tol, st));
+        ++h->launches;
+        if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
+    }
+    DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, nullptr, L.state_d, st));
+    return DD_OK;
+}
+
+// At most n CG iterations on level L from the iterate in u[0] (the residual is
 // formed afresh, so this also restarts CG), then record the result (always in
 // u[0]) into L.state_d.  No host synchronisation.
-int enqueue_cg(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st) {
+int enqueue_cg(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool loop) {
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, st));
     const int nblk = dd::res64_blocks(L.H, L.W);
     dd::Res64Args ra{};
@@ -409,30 +549,20 @@ int enqueue_cg(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st) {
     DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, nblk, h->C, h->res_out, st));
     DD_LAUNCH(h, dd::launch_cg_init(h->res_out, L.cg_scal, h->C, st));
     DD_CK(cudaMemsetAsync(L.cg_p[0], 0, sizeof(float) * (size_t)h->C * L.plane(), st));
-    dd::CGArgs a{};
-    a.H = L.H; a.W = L.W; a.P = L.P; a.C = h->C; a.mp = L.W;
-    a.plane = L.plane();
-    a.mask = L.mask;
-    a.x = L.u[0]; a.r = L.cg_r; a.q = L.cg_q;
-    a.part = L.cg_part; a.scal = L.cg_scal; a.ref = L.ref_d;
-    a.flag = h->flag_d; a.state = h->sstate_d;
-    a.tol = tol;
+    if (loop) return run_loop(h, L, n, tol, st);
     for (int i = 0; i < n; ++i) {
-        a.p_old = L.cg_p[i & 1];
-        a.p_new = L.cg_p[(i + 1) & 1];
-        a.iter = i;
-        a.first = i == 0 ? 1 : 0;
-        DD_CK(dd::launch_cg_iteration(a, st));
+        DD_TRY(enqueue_pass(h, L, tol, st));
         h->launches += 2;
     }
-    DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, L.state_d, st));
+    DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, nullptr, L.state_d, st));
     return DD_OK;
 }
 
 // A level solve under the device stop test: ORAS sweeps or CG iterations.
-int enqueue_level(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed) {
-    if (h->prm.solver == DD_SOLVER_CG) return enqueue_cg(h, L, n, tol, st);
-    return enqueue_sweeps(h, L, n, tol, st, timed);
+int enqueue_level(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed, bool capture) {
+    const bool loop = loop_mode(h, capture, timed);
+    if (h->prm.solver == DD_SOLVER_CG) return enqueue_cg(h, L, n, tol, st, loop);
+    return enqueue_sweeps(h, L, n, tol, st, timed, loop);
 }
 
 // Coarse-to-fine initialisation (Sec. 4): coarsest level from u0 = C f, each
@@ -440,7 +570,7 @@ int enqueue_level(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, b
 // next level's start; the fine level's start is left in u[0].  Everything is
 // enqueued without host synchronisation: each level's result buffer is chosen
 // on the device.
-int cascade(dd_inpaint* h, cudaStream_t st) {
+int cascade(dd_inpaint* h, cudaStream_t st, bool capture) {
     const int nl = (int)h->lv.size();
     for (int l = nl - 1; l >= 1; --l) {
         Level& L = h->lv[l];
@@ -452,7 +582,7 @@ int cascade(dd_inpaint* h, cudaStream_t st) {
                                                 Cc.plane(), L.mask, L.W, L.f, L.P, L.plane(), L.u[0], L.P,
                                                 L.plane(), st));
         }
-        DD_TRY(enqueue_level(h, L, h->prm.coarse_sweeps, h->prm.coarse_tol, st, false));
+        DD_TRY(enqueue_level(h, L, h->prm.coarse_sweeps, h->prm.coarse_tol, st, false, capture));
     }
     Level& F = h->lv[0];
     if (nl > 1) {
@@ -522,15 +652,17 @@ int fp32_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool 
     if (!capture) DD_CK(cudaEventRecord(h->ev0, st));
     h->pending_cascaded = !h->warm;
     if (!h->warm) {
-        DD_TRY(cascade(h, st));
+        DD_TRY(cascade(h, st, capture));
     } else if (h->cur != 0) {
         DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[1], F.P, F.plane(), F.u[0], F.P, F.plane(), st));
         h->cur = 0;
     }
     h->warm = false;
     const long long dense_plane = (long long)F.H * F.W;
-    const int n1 = first_chunk(h);
-    DD_TRY(enqueue_level(h, F, n1, tol, st, h->prm.timing != 0 && !capture));
+    // a device loop runs to the sweep limit; launches stop at the first chunk
+    const bool timed = h->prm.timing != 0 && !capture;
+    const int n1 = loop_mode(h, capture, timed) ? h->prm.max_sweeps : first_chunk(h);
+    DD_TRY(enqueue_level(h, F, n1, tol, st, timed, capture));
     DD_LAUNCH(h, dd::launch_copy2d_sel(F.H, F.W, h->C, F.u[0], F.u[1], F.state_d, F.P, F.plane(), u_out, F.W,
                                        dense_plane, st));
     DD_TRY(residual_of(h, u_out, F.W, dense_plane, st));
@@ -569,6 +701,7 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
     F.ref.assign(h->h_ref, h->h_ref + h->C);
     if (h->h_flag[2] != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
     if (h->pending_cascaded) take_level_stats(h);
+    count_loop_launches(h);
     const int status = h->h_state[2], applied = h->h_state[1];
     if (status == 2) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
     const int n1 = first_chunk(h);
@@ -586,20 +719,24 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
     DD_TRY(rel_from_h_res(h, rel, rmax, rnorm));
     double worst = *std::max_element(rel.begin(), rel.end());
     bool converged = false;
-    if (status == 1 && worst <= tol) {
+    if (worst <= tol) {   // the FP64-accurate residual of the output decides
         converged = true;
     } else {
+        h->stats.host_continued = 1;
         double target = status == 1 ? tol * 0.5 : tol;
         for (int attempt = 0; attempt < 4 && fine_sweeps < h->prm.max_sweeps; ++attempt) {
             int app = 0;
             bool conv = false;
             if (h->prm.solver == DD_SOLVER_CG) {
                 // restart CG from the current iterate (fresh residual), read back once per chunk
+                const bool loop = loop_mode(h, false, false);
                 while (!conv && fine_sweeps + app < h->prm.max_sweeps) {
-                    const int n = std::min(64, h->prm.max_sweeps - fine_sweeps - app);
-                    DD_TRY(enqueue_cg(h, F, n, target, st));
+                    const int left = h->prm.max_sweeps - fine_sweeps - app;
+                    const int n = loop ? left : std::min(64, left);
+                    DD_TRY(enqueue_cg(h, F, n, target, st, loop));
                     DD_CK(cudaMemcpyAsync(h->h_state, F.state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
                     DD_CK(cudaStreamSynchronize(st));
+                    count_loop_launches(h);
                     app += h->h_state[1];
                     conv = h->h_state[2] == 1;
                     if (h->h_state[2] == 2) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
@@ -619,6 +756,7 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
         }
         DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[h->cur], F.P, F.plane(), u_out, F.W,
                                        (long long)F.H * F.W, st));
+        if (h->ev_recorded) DD_CK(cudaEventRecord(h->ev1, st));   // ms_total spans the continuation
         DD_CK(cudaStreamSynchronize(st));
     }
     (void)nl;
@@ -656,7 +794,7 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
     DD_CK(cudaEventRecord(h->ev0, st));
     Level& F = h->lv[0];
     if (!h->warm) {
-        DD_TRY(cascade(h, st));
+        DD_TRY(cascade(h, st, false));
     } else if (h->cur != 0) {
         DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[1], F.P, F.plane(), F.u[0], F.P, F.plane(), st));
         h->cur = 0;
@@ -677,6 +815,7 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
                                           cudaMemcpyDeviceToHost, st));
                 DD_CK(cudaStreamSynchronize(st));
                 take_level_stats(h);
+                count_loop_launches(h);
             }
             const double worst = *std::max_element(rel.begin(), rel.end());
             if (worst <= tol) { converged = true; break; }
@@ -721,6 +860,8 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
 }
 
 void free_all(dd_inpaint* h) {
+    for (Level& L : h->lv) destroy_loop(L.loop);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->h_res) cudaFreeHost(h->h_res);
@@ -828,6 +969,11 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if ((rc = dalloc_t(h, &h->scale_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->scale_inv_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->flag_d, 4)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->ctl_d, 4)) != DD_OK) return fail(rc);
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("cudaStreamCreateWithFlags failed");
+        return fail(DD_ECUDA);
+    }
     if (cudaMallocHost(&h->h_res, sizeof(double2) * C * DD_MAX_LEVELS) != cudaSuccess ||
         cudaMallocHost(&h->h_state, sizeof(int) * 4 * DD_MAX_LEVELS) != cudaSuccess ||
         cudaMallocHost(&h->h_ref, sizeof(double) * C) != cudaSuccess ||
@@ -883,6 +1029,7 @@ void dd_params_default(dd_params* p) {
     p->timing = 0;
     p->tile_warps = 0;
     p->solver = DD_SOLVER_ORAS;
+    p->device_loop = 1;
 }
 
 const char* dd_strerror(int code) {
@@ -1021,9 +1168,8 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     Level& F = h->lv[0];
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, h->cur, st));
     const dd::SweepPair pair{{&F.map_u[0], &F.map_u[1]}, {F.u[0], F.u[1]}};
-    dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, -1.0, 0.0, h->flag_d, h->sstate_d, 0, 0};
+    const dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, -1.0, 0.0, h->flag_d, h->sstate_d, 0};
     for (int i = 0; i < n; ++i) {   // tol < 0: every launch is a full sweep
-        stop.sweep_index = i;
         DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), pair, nullptr, F.tmask, stop,
                                       h->prm.robin_p, h->prm.local_cg_iters, st));
         h->cur = 1 - h->cur;

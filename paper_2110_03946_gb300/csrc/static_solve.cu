@@ -180,7 +180,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     const dd::SweepPair pair{{&maps[0], &maps[1]}, {u[0], u[1]}};
     for (int attempt = 0; attempt < 4 && !converged; ++attempt) {
         SS_CK(dd::launch_reset_sweep_state(sstate, flag, cur, st));
-        dd::SweepStop stop{partial, dd::kSweepSlots, norms2, ref_d, target, 0.0, flag, sstate, 0, 0};
+        dd::SweepStop stop{partial, dd::kSweepSlots, norms2, ref_d, target, 0.0, flag, sstate, 0};
         const int start = done;
         int launched = 0;
         int hflag[3] = {0, 0, 0}, hstate[2] = {cur, 0};
@@ -188,7 +188,6 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
             const bool last_probe = done >= p.max_sweeps;
             const int n = last_probe ? 1 : std::min(8, p.max_sweeps - done);
             for (int i = 0; i < n; ++i) {
-                stop.sweep_index = launched + i;
                 stop.force_probe = last_probe ? 1 : 0;
                 SS_CK(dd::launch_sweep(dd::Store::F32, g, C, plane, pair, nullptr, tmask, stop, pr,
                                        p.local_cg_iters, st));

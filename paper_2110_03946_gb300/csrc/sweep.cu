@@ -539,6 +539,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     if (s_last && wt == 0) {
         __threadfence();
         const SweepStop& sp = a.stop;
+        const int sweep_index = __ldcg(sp.state + 3);   // launches before this one
         double worst = 0.0, best_ratio = 1e300;
         int bad = 0;
         for (int c = 0; c < a.C; ++c) {
@@ -550,7 +551,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                 if (!isfinite(v)) bad = 1;
                 const double den = sp.ref[c] > 0.0 ? sp.ref[c] : 1.0;
                 worst = fmax(worst, sqrt(v) / den);
-                if (sp.sweep_index > 0) {
+                if (sweep_index > 0) {
                     const double prev = sp.norms2[a.C + c];
                     best_ratio = fmin(best_ratio, prev > 0.0 ? sqrt(v / prev) : 0.0);
                 }
@@ -560,11 +561,11 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         }
         if (lane == 0) {
             int* const state = sp.state;
-            if (bad) { flag[0] = 2; flag[1] = sp.sweep_index; }
-            else if (worst <= sp.tol) { flag[0] = 1; flag[1] = sp.sweep_index; }
-            else if (sp.stall > 0.0 && sp.sweep_index > 0 && best_ratio > sp.stall) {
+            if (bad) { flag[0] = 2; flag[1] = sweep_index; }
+            else if (worst <= sp.tol) { flag[0] = 1; flag[1] = sweep_index; }
+            else if (sp.stall > 0.0 && sweep_index > 0 && best_ratio > sp.stall) {
                 flag[0] = 3;
-                flag[1] = sp.sweep_index;
+                flag[1] = sweep_index;
             } else if (!probe) {
                 // the output of this sweep becomes the current iterate; probe it
                 // next if the last residual ratio predicts it meets tol
@@ -576,6 +577,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                 state[2] = 0;   // the probe failed: sweep the same iterate in full
             }
             if (!probe) sp.norms2[2 * a.C] = worst;
+            state[3] = sweep_index + 1;
             flag[3] = 0;   // ticket ready for the next launch
         }
     }
@@ -632,15 +634,22 @@ size_t sweep_smem_bytes(bool has_g) {
 template <class CF, typename T>
 int persistent_grid(bool has_g) {
     // CTAs per SM from the occupancy calculator, cached per instantiation and shape
+    // (0 on a failed query: the caller reports the error).  The kernel's
+    // dynamic shared-memory limit is one attribute for both variants, so it is
+    // always set to the larger (with g): setting it to the smaller variant's
+    // size would make later launches of the larger one fail.
     static int cached[2] = {0, 0};
     int& slot = cached[has_g ? 1 : 0];
     if (slot == 0) {
         int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const size_t smem = sweep_smem_bytes<CF, T>(has_g);
-        cudaFuncSetAttribute(oras_sweep_kernel<CF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oras_sweep_kernel<CF, T>, CF::NT, smem);
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaFuncSetAttribute(oras_sweep_kernel<CF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sweep_smem_bytes<CF, T>(true)) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oras_sweep_kernel<CF, T>, CF::NT, smem) !=
+                cudaSuccess)
+            return 0;
         slot = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
     }
     return slot;
@@ -661,12 +670,24 @@ cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const SweepPair
     a.p_robin = p_robin;
     a.k = k;
     const long long work = (long long)g.ntiles * C;
-    const long long grid = std::min<long long>(std::min<long long>(work, persistent_grid<CF, T>(a.has_g)),
-                                               (long long)stop.slots);
+    const int resident = persistent_grid<CF, T>(a.has_g);
+    if (resident == 0) return cudaGetLastError();
+    const long long grid = std::min<long long>(std::min<long long>(work, resident), (long long)stop.slots);
     const size_t smem = sweep_smem_bytes<CF, T>(a.has_g);
     oras_sweep_kernel<CF, T><<<(unsigned)grid, CF::NT, smem, st>>>(*pr2.map[0], *pr2.map[1], mg ? *mg : *pr2.map[0],
                                                                     a);
     return cudaGetLastError();
+}
+
+template <class CF>
+cudaError_t prepare_store(Store s, bool has_g) {
+    int n = 0;
+    switch (s) {
+        case Store::F32: n = persistent_grid<CF, float>(has_g); break;
+        case Store::F16: n = persistent_grid<CF, __half>(has_g); break;
+        case Store::BF16: n = persistent_grid<CF, __nv_bfloat16>(has_g); break;
+    }
+    return n > 0 ? cudaSuccess : cudaGetLastError();
 }
 
 template <class CF>
@@ -795,6 +816,10 @@ cudaError_t launch_build_tmask(const TileGeom& g, const uint8_t* mask, int mp, u
 cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsigned long long* out,
                                  cudaStream_t st) {
     return with_cfg(g.b, g.nw, [&](auto cfg) { return count_cfg<decltype(cfg)>(g, tmask, out, st); });
+}
+
+cudaError_t prepare_sweep(Store s, const TileGeom& g, bool has_g) {
+    return with_cfg(g.b, g.nw, [&](auto cfg) { return prepare_store<decltype(cfg)>(s, has_g); });
 }
 
 cudaError_t launch_sweep(Store s, const TileGeom& g, int C, long long plane, const SweepPair& pair,

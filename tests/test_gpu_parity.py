@@ -155,14 +155,23 @@ def test_solve_matches_oracle(name, H, W, C, params):
     assert np.array_equal(u[:, m != 0], f[:, m != 0].astype(np.float32))
 
 
-@pytest.mark.parametrize("H,W", [(1, 40), (40, 1), (5, 5), (33, 17), (2, 2)])
-def test_degenerate_shapes(H, W):
+@pytest.mark.parametrize("solver", ["oras", "cg"])
+@pytest.mark.parametrize("H,W", [(1, 40), (40, 1), (5, 5), (33, 17), (2, 2), (70, 131)])
+def test_degenerate_shapes(H, W, solver):
+    """Single rows and columns, tiny images and widths that are not a multiple
+    of 4 (the CG kernels work on float4 groups of columns)."""
     rng = np.random.default_rng(H * 100 + W)
     f = rng.uniform(0, 255, size=(1, H, W)).astype(np.float32)
     m = np.zeros((H, W), dtype=np.uint8)
     m.flat[rng.choice(H * W, size=max(1, H * W // 10), replace=False)] = 1
-    with Inpainter(m, f, levels=3, precision="fp32_ref") as ip:
+    if solver == "cg":
+        prm = dict(levels=2, precision="fp32", solver="cg", max_sweeps=4000, coarse_sweeps=2000)
+    else:
+        prm = dict(levels=3, precision="fp32_ref")
+    with Inpainter(m, f, **prm) as ip:
         u = ip.solve(1e-6).cpu().numpy()
+        st = ip.stats()
+    assert st["converged"]
     assert np.max(np.abs(u - ref.solve_direct(f, m))) <= TOL_U
 
 
@@ -237,3 +246,38 @@ def test_repeatable_bitwise():
         a = ip.solve(1e-6).cpu().numpy()
         b = ip.solve(1e-6).cpu().numpy()
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("solver", ["oras", "cg"])
+def test_device_loop_matches_launches(solver):
+    """The level iterations repeated in a CUDA graph loop on the device give the
+    launch path's answer: the same kernels run in the same order until the
+    stop test, so equal sweep counts mean bitwise-equal results."""
+    f, m = synth.make_frame(180, 230, 3, 0.04, "edge", 41)
+    prm = dict(levels=3, precision="fp32", solver=solver, max_sweeps=3000 if solver == "cg" else 400,
+               coarse_sweeps=400 if solver == "cg" else 12)
+    out = {}
+    for loop in (0, 1):
+        with Inpainter(m, f, device_loop=loop, **prm) as ip:
+            out[loop] = (ip.solve(1e-6).cpu().numpy(), ip.stats())
+    (u0, s0), (u1, s1) = out[0], out[1]
+    exact = ref.solve_direct(f, m)
+    for u, st in ((u0, s0), (u1, s1)):
+        assert st["converged"]
+        assert np.max(np.abs(u - exact)) <= TOL_U
+    if s0["sweeps_per_level"] == s1["sweeps_per_level"]:
+        assert np.array_equal(u0, u1)
+
+
+def test_device_loop_graph_reused_across_solves():
+    """A second solve with the same tolerance reuses the level loop graphs and
+    gives the bitwise-same answer; a new tolerance rebuilds them."""
+    f, m = synth.make_frame(140, 150, 2, 0.05, "uniform", 43)
+    with Inpainter(m, f, levels=3, precision="fp32") as ip:
+        a = ip.solve(1e-6).cpu().numpy()
+        b = ip.solve(1e-6).cpu().numpy()
+        c = ip.solve(1e-4)
+        st = ip.stats()
+        d = ip.solve(1e-6).cpu().numpy()
+    assert np.array_equal(a, b) and np.array_equal(a, d)
+    assert max(st["rel_residual"][:2]) <= 1e-4 and torch.isfinite(c).all()
