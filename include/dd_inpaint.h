@@ -202,8 +202,11 @@ int dd_inpaint_query(dd_handle h);
 
 /*
  * Wait for the enqueued solve and return its status as dd_inpaint_solve would.
- * If the first 16 fine sweeps did not reach tol, the remaining sweeps run here
- * on stream under host control and u_out is rewritten.
+ * If the enqueued part did not reach tol (with params.device_loop = 0: the
+ * first 16 fine sweeps; with device loops: the sweep limit, or an FP32 stop
+ * test that the FP64-accurate residual overrules), the remaining sweeps run
+ * here on stream under host control, u_out is rewritten and
+ * stats.host_continued is set.
  */
 int dd_inpaint_solve_finish(dd_handle h, void *stream);
 
@@ -214,8 +217,11 @@ int dd_inpaint_solve_finish(dd_handle h, void *stream);
  * launch.  handles: n distinct FP32 handles; u_out[i]: DEVICE output of handle
  * i (C*H*W floats, fixed for the life of the batch); tol baked into the graph.
  * Each launch solves the data currently loaded in every handle, starting from
- * the multilevel initialisation.  kernels_per_launch (may be NULL) receives
- * the number of kernels in the graph.  Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA.
+ * the multilevel initialisation.  With params.device_loop = 1 every level's
+ * sweeps run in a WHILE node of the batch graph (the pass count is known after
+ * dd_batch_finish and enters each handle's kernel_launches); kernels_per_launch
+ * (may be NULL) receives the number of kernel nodes outside those loops.
+ * Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA.
  */
 int dd_batch_create(int n, const dd_handle *handles, float *const *u_out, double tol, dd_batch_handle *out,
                     long long *kernels_per_launch);

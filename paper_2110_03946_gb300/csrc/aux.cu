@@ -246,11 +246,13 @@ __global__ void resolve_kernel(const int* __restrict__ flag, const int* __restri
     out[3] = ctl ? ctl[0] : 0;
 }
 
-__global__ void reset_sweep_state_kernel(int* __restrict__ state, int* __restrict__ flag, int cur) {
+__global__ void reset_sweep_state_kernel(int* __restrict__ state, int* __restrict__ flag, int cur,
+                                         double* __restrict__ tol_d, double tol) {
     if (threadIdx.x < 4) {
         state[threadIdx.x] = threadIdx.x == 0 ? cur : 0;
         flag[threadIdx.x] = 0;
     }
+    if (threadIdx.x == 0) *tol_d = tol;
 }
 
 __global__ void loop_ctl_kernel(const int* __restrict__ flag, const int* __restrict__ state, int* __restrict__ ctl,
@@ -410,8 +412,8 @@ cudaError_t launch_resolve(const int* flag, const int* sweep_state, const int* c
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, cudaStream_t st) {
-    reset_sweep_state_kernel<<<1, 32, 0, st>>>(state, flag, cur);
+cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, double* tol_d, double tol, cudaStream_t st) {
+    reset_sweep_state_kernel<<<1, 32, 0, st>>>(state, flag, cur, tol_d, tol);
     return cudaGetLastError();
 }
 

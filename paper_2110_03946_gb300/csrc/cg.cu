@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update_kernel(CGArgs a) {
     __threadfence();
     double worst = 0.0;
     int bad = 0;
+    const double tol = __ldcg(a.tol);
     for (int cc = 0; cc < a.C; ++cc) {
         const double rrn = channel_sum(a.part, cc, nblk, sh);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(CG_THREADS) cg_update_kernel(CGArgs a) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         a.state[1] = it + 1;   // iterations applied
         if (bad) { a.flag[0] = 2; a.flag[1] = it; }
-        else if (worst <= a.tol) { a.flag[0] = 1; a.flag[1] = it; }
+        else if (worst <= tol) { a.flag[0] = 1; a.flag[1] = it; }
         a.flag[3] = 0;
     }
 }

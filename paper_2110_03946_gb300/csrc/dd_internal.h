@@ -79,7 +79,8 @@ struct SweepStop {
     int slots;
     double* norms2;
     const double* ref;
-    double tol;
+    const double* tol;   // device: the tolerance (set by launch_reset_sweep_state), so a
+                         // captured launch does not depend on it
     double stall;
     int* flag;
     int* state;
@@ -105,8 +106,9 @@ cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, co
 // per process; call before capturing a sweep launch into a graph.
 cudaError_t prepare_sweep(Store s, const TileGeom& g, bool has_g);
 
-// state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..3] = 0.
-cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, cudaStream_t st);
+// state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..3] = 0; *tol_d = tol
+// (the stop tolerance the following sweeps or CG iterations read).
+cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, double* tol_d, double tol, cudaStream_t st);
 
 // Loop control at the end of each pass of a graph WHILE loop (one thread):
 // ctl[0] counts the passes; the loop's condition is cleared when flag[0] != 0
@@ -198,7 +200,7 @@ struct CGArgs {
     int* flag;           // [0] stop flag, [1] stopping iteration, [3] ticket
     int* state;          // [1] = i, the iterations applied since the reset (read on
                          // the device, so one iteration's launches can repeat in a graph loop)
-    double tol;
+    const double* tol;   // device: the stop tolerance (set by launch_reset_sweep_state)
 };
 int cg_blocks(int H, int W);
 // scal <- {(r, r) from res_out[c].x, alpha = beta = 0}

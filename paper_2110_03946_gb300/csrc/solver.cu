@@ -73,13 +73,12 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 // A level's iteration as a CUDA graph: a memset resets the pass counter, then a
 // WHILE node repeats one pass (one ORAS sweep or probe, or one CG iteration,
 // followed by the loop-control kernel) until the stop test, the sweep limit
-// `cap` or the pass bound clears its condition.  Built for one (cap, tol) and
-// rebuilt when either changes.
+// `cap` or the pass bound clears its condition.  The tolerance is read from
+// device memory, so the graph depends on cap only.
 struct LoopGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int cap = 0;
-    double tol = 0.0;
 };
 
 void destroy_loop(LoopGraph& G) {
@@ -137,6 +136,7 @@ struct dd_inpaint {
     int* flag_d = nullptr;          // [0] stop flag, [1] conv_at, [2] device wait timed out, [3] ticket
     int* sstate_d = nullptr;        // sweep state: current buffer, full sweeps, probe request, launches
     int* ctl_d = nullptr;           // device-loop pass counter (4 ints)
+    double* tol_d = nullptr;        // stop tolerance of the running level (set by each reset)
     cudaStream_t cap_stream = nullptr;   // private stream on which loop bodies are captured
     // pinned host mirrors
     double2* h_res = nullptr;
@@ -312,12 +312,12 @@ int run_sweeps(dd_inpaint* h, const TileGeom& g, Store st_t, void* const bufs[2]
                double tol, double stall, int max_sweeps, cudaStream_t st, int* applied, bool* converged,
                bool fine = false) {
     const long long plane = (long long)g.H * g.pitch;
-    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, cur, st));
+    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, cur, h->tol_d, tol, st));
     *converged = false;
     *applied = 0;
     const bool timed = fine && h->prm.timing != 0;
     const dd::SweepPair pair{{&maps[0], &maps[1]}, {bufs[0], bufs[1]}};
-    dd::SweepStop stop{partial, dd::kSweepSlots, h->norms2_d, ref_d, tol, stall, h->flag_d, h->sstate_d, 0};
+    dd::SweepStop stop{partial, dd::kSweepSlots, h->norms2_d, ref_d, h->tol_d, stall, h->flag_d, h->sstate_d, 0};
     int full_done = 0;
     while (true) {
         // full sweeps until max_sweeps; then one probe evaluates the last iterate
@@ -404,16 +404,13 @@ int write_scaled_residual(dd_inpaint* h, cudaStream_t st) {
 }
 
 // Whether a level's iteration runs as a device loop (a graph WHILE node) rather
-// than as plain launches: per-sweep event timing and stream capture need the
-// launches.
-bool loop_mode(const dd_inpaint* h, bool capture, bool timed) {
-    return h->prm.device_loop != 0 && !capture && !timed;
-}
+// than as plain launches: per-sweep event timing needs the launches.
+bool loop_mode(const dd_inpaint* h, bool timed) { return h->prm.device_loop != 0 && !timed; }
 
 // Kernels per pass of a device loop: the sweep (or CG's two) and the loop control.
 int pass_kernels(const dd_inpaint* h) { return h->prm.solver == DD_SOLVER_CG ? 3 : 2; }
 
-dd::CGArgs cg_args(const dd_inpaint* h, const Level& L, double tol) {
+dd::CGArgs cg_args(const dd_inpaint* h, const Level& L) {
     dd::CGArgs a{};
     a.H = L.H; a.W = L.W; a.P = L.P; a.C = h->C; a.mp = L.W;
     a.plane = L.plane();
@@ -422,80 +419,112 @@ dd::CGArgs cg_args(const dd_inpaint* h, const Level& L, double tol) {
     a.p[0] = L.cg_p[0]; a.p[1] = L.cg_p[1];
     a.part = L.cg_part; a.scal = L.cg_scal; a.ref = L.ref_d;
     a.flag = h->flag_d; a.state = h->sstate_d;
-    a.tol = tol;
+    a.tol = h->tol_d;
     return a;
 }
 
 // One pass of level L's iteration: an ORAS sweep (or probe) from the buffer
 // the device state names, or one CG iteration.
-int enqueue_pass(dd_inpaint* h, Level& L, double tol, cudaStream_t st) {
+int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st) {
     if (h->prm.solver == DD_SOLVER_CG) {
-        DD_CK(dd::launch_cg_iteration(cg_args(h, L, tol), st));
+        DD_CK(dd::launch_cg_iteration(cg_args(h, L), st));
         return DD_OK;
     }
     const dd::SweepPair pair{{&L.map_u[0], &L.map_u[1]}, {L.u[0], L.u[1]}};
-    const dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, tol, 0.0, h->flag_d, h->sstate_d, 0};
+    const dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, h->tol_d, 0.0, h->flag_d, h->sstate_d, 0};
     DD_CK(dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), pair, nullptr, L.tmask, stop, h->prm.robin_p,
                            h->prm.local_cg_iters, st));
     return DD_OK;
 }
 
-// Level L's loop graph for (cap, tol), built on first use (the body is
-// captured on the handle's private stream) and kept while both stay the same.
+// Add level L's loop to graph g after the nodes deps: a memset of the pass
+// counter, then the WHILE node whose body (one pass and the loop control) is
+// captured on the handle's private stream.  *last = the WHILE node.
 // The pass bound: CG applies an iteration in every pass; ORAS follows a failed
 // probe by a full sweep, so at most 2 cap + 1 passes reach cap full sweeps.
-int loop_graph(dd_inpaint* h, Level& L, int cap, double tol, cudaGraphExec_t* out) {
-    LoopGraph& G = L.loop;
-    if (G.exec != nullptr && G.cap == cap && G.tol == tol) {
-        *out = G.exec;
-        return DD_OK;
-    }
-    destroy_loop(G);
+int add_loop(dd_inpaint* h, Level& L, int cap, cudaGraph_t g, const cudaGraphNode_t* deps,
+             const cudaGraphEdgeData* edges, size_t ndeps, cudaGraphNode_t* last) {
     if (h->prm.solver == DD_SOLVER_ORAS) DD_CK(dd::prepare_sweep(Store::F32, L.geom, false));
-    DD_CK(cudaGraphCreate(&G.graph, 0));
     cudaGraphConditionalHandle cond;
-    DD_CK(cudaGraphConditionalHandleCreate(&cond, G.graph, 1, cudaGraphCondAssignDefault));
-    cudaMemsetParams ms{};
-    ms.dst = h->ctl_d;
-    ms.value = 0;
-    ms.elementSize = sizeof(int);
-    ms.width = 4;
-    ms.height = 1;
+    DD_CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams mp{};
+    mp.type = cudaGraphNodeTypeMemset;
+    mp.memset.dst = h->ctl_d;
+    mp.memset.value = 0;
+    mp.memset.elementSize = sizeof(int);
+    mp.memset.width = 4;
+    mp.memset.height = 1;
     cudaGraphNode_t reset = nullptr, loop = nullptr;
-    DD_CK(cudaGraphAddMemsetNode(&reset, G.graph, nullptr, 0, &ms));
+    DD_CK(cudaGraphAddNode(&reset, g, deps, edges, ndeps, &mp));
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = cond;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    DD_CK(cudaGraphAddNode(&loop, G.graph, &reset, nullptr, 1, &cp));
+    DD_CK(cudaGraphAddNode(&loop, g, &reset, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     DD_CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const int max_passes = h->prm.solver == DD_SOLVER_CG ? cap + 1 : 2 * cap + 2;
-    const int rc = enqueue_pass(h, L, tol, h->cap_stream);
+    const int rc = enqueue_pass(h, L, h->cap_stream);
     const cudaError_t el = rc == DD_OK ? dd::launch_loop_ctl(h->flag_d, h->sstate_d, h->ctl_d, cap, max_passes, cond,
                                                              h->cap_stream)
                                        : cudaSuccess;
     cudaGraph_t captured = body;
     const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &captured);
+    if (rc != DD_OK) return rc;
+    DD_CK(el);
+    DD_CK(ec);
+    *last = loop;
+    return DD_OK;
+}
+
+// Level L's loop as a graph of its own for (cap, tol), built on first use and
+// kept while both stay the same.
+int loop_graph(dd_inpaint* h, Level& L, int cap, cudaGraphExec_t* out) {
+    LoopGraph& G = L.loop;
+    if (G.exec != nullptr && G.cap == cap) {
+        *out = G.exec;
+        return DD_OK;
+    }
+    destroy_loop(G);
+    DD_CK(cudaGraphCreate(&G.graph, 0));
+    cudaGraphNode_t last = nullptr;
+    const int rc = add_loop(h, L, cap, G.graph, nullptr, nullptr, 0, &last);
     if (rc != DD_OK) {
         destroy_loop(G);
         return rc;
     }
-    DD_CK(el);
-    DD_CK(ec);
     DD_CK(cudaGraphInstantiate(&G.exec, G.graph, 0));
     G.cap = cap;
-    G.tol = tol;
     *out = G.exec;
     return DD_OK;
 }
 
-// Run level L's loop graph on st and resolve its result into L.state_d.
-int run_loop(dd_inpaint* h, Level& L, int cap, double tol, cudaStream_t st) {
-    if (cap > 0) {   // (a WHILE body runs at least once)
+// Run level L's loop on st and resolve its result into L.state_d.  Outside a
+// capture the level's own graph is launched; inside a stream capture (a
+// dd_batch graph) the loop's nodes join the graph being captured.
+int run_loop(dd_inpaint* h, Level& L, int cap, cudaStream_t st, bool capture) {
+    if (cap > 0 && capture) {   // (a WHILE body runs at least once)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* edges = nullptr;
+        size_t nd = 0;
+        DD_CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &edges, &nd));
+        if (cs != cudaStreamCaptureStatusActive) {
+            set_error("device loop: the stream is not capturing");
+            return DD_ECUDA;
+        }
+        // the arrays returned above are valid until the next capture call on st
+        std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+        std::vector<cudaGraphEdgeData> ev;
+        if (edges) ev.assign(edges, edges + nd);
+        cudaGraphNode_t last = nullptr;
+        DD_TRY(add_loop(h, L, cap, cg, dv.data(), edges ? ev.data() : nullptr, nd, &last));
+        DD_CK(cudaStreamUpdateCaptureDependencies(st, &last, nullptr, 1, cudaStreamSetCaptureDependencies));
+    } else if (cap > 0) {
         cudaGraphExec_t ex = nullptr;
-        DD_TRY(loop_graph(h, L, cap, tol, &ex));
+        DD_TRY(loop_graph(h, L, cap, &ex));
         DD_CK(cudaGraphLaunch(ex, st));
     } else {
         DD_CK(cudaMemsetAsync(h->ctl_d, 0, 4 * sizeof(int), st));
@@ -519,12 +548,13 @@ void count_loop_launches(dd_inpaint* h) {
 // device stop test; the result is resolved into L.state_d.  No host
 // synchronisation.  Plain launches (loop = false): n launches, those after the
 // stop do no work.
-int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed, bool loop) {
-    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, st));
-    if (loop) return run_loop(h, L, n, tol, st);
+int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed, bool loop,
+                   bool capture) {
+    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, h->tol_d, tol, st));
+    if (loop) return run_loop(h, L, n, st, capture);
     for (int i = 0; i < n; ++i) {
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
-        DD_TRY(enqueue_pass(h, L, tol, st));
+        DD_TRY(enqueue_pass(h, L, st));
         ++h->launches;
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
     }
@@ -535,8 +565,8 @@ int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, 
 // At most n CG iterations on level L from the iterate in u[0] (the residual is
 // formed afresh, so this also restarts CG), then record the result (always in
 // u[0]) into L.state_d.  No host synchronisation.
-int enqueue_cg(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool loop) {
-    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, st));
+int enqueue_cg(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool loop, bool capture) {
+    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, h->tol_d, tol, st));
     const int nblk = dd::res64_blocks(L.H, L.W);
     dd::Res64Args ra{};
     ra.H = L.H; ra.W = L.W; ra.C = h->C;
@@ -549,9 +579,9 @@ int enqueue_cg(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool
     DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, nblk, h->C, h->res_out, st));
     DD_LAUNCH(h, dd::launch_cg_init(h->res_out, L.cg_scal, h->C, st));
     DD_CK(cudaMemsetAsync(L.cg_p[0], 0, sizeof(float) * (size_t)h->C * L.plane(), st));
-    if (loop) return run_loop(h, L, n, tol, st);
+    if (loop) return run_loop(h, L, n, st, capture);
     for (int i = 0; i < n; ++i) {
-        DD_TRY(enqueue_pass(h, L, tol, st));
+        DD_TRY(enqueue_pass(h, L, st));
         h->launches += 2;
     }
     DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, nullptr, L.state_d, st));
@@ -560,9 +590,9 @@ int enqueue_cg(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool
 
 // A level solve under the device stop test: ORAS sweeps or CG iterations.
 int enqueue_level(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed, bool capture) {
-    const bool loop = loop_mode(h, capture, timed);
-    if (h->prm.solver == DD_SOLVER_CG) return enqueue_cg(h, L, n, tol, st, loop);
-    return enqueue_sweeps(h, L, n, tol, st, timed, loop);
+    const bool loop = loop_mode(h, timed);
+    if (h->prm.solver == DD_SOLVER_CG) return enqueue_cg(h, L, n, tol, st, loop, capture);
+    return enqueue_sweeps(h, L, n, tol, st, timed, loop, capture);
 }
 
 // Coarse-to-fine initialisation (Sec. 4): coarsest level from u0 = C f, each
@@ -661,7 +691,7 @@ int fp32_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool 
     const long long dense_plane = (long long)F.H * F.W;
     // a device loop runs to the sweep limit; launches stop at the first chunk
     const bool timed = h->prm.timing != 0 && !capture;
-    const int n1 = loop_mode(h, capture, timed) ? h->prm.max_sweeps : first_chunk(h);
+    const int n1 = loop_mode(h, timed) ? h->prm.max_sweeps : first_chunk(h);
     DD_TRY(enqueue_level(h, F, n1, tol, st, timed, capture));
     DD_LAUNCH(h, dd::launch_copy2d_sel(F.H, F.W, h->C, F.u[0], F.u[1], F.state_d, F.P, F.plane(), u_out, F.W,
                                        dense_plane, st));
@@ -729,11 +759,11 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
             bool conv = false;
             if (h->prm.solver == DD_SOLVER_CG) {
                 // restart CG from the current iterate (fresh residual), read back once per chunk
-                const bool loop = loop_mode(h, false, false);
+                const bool loop = loop_mode(h, false);
                 while (!conv && fine_sweeps + app < h->prm.max_sweeps) {
                     const int left = h->prm.max_sweeps - fine_sweeps - app;
                     const int n = loop ? left : std::min(64, left);
-                    DD_TRY(enqueue_cg(h, F, n, target, st, loop));
+                    DD_TRY(enqueue_cg(h, F, n, target, st, loop, false));
                     DD_CK(cudaMemcpyAsync(h->h_state, F.state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
                     DD_CK(cudaStreamSynchronize(st));
                     count_loop_launches(h);
@@ -970,6 +1000,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if ((rc = dalloc_t(h, &h->scale_inv_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->flag_d, 4)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->ctl_d, 4)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->tol_d, 1)) != DD_OK) return fail(rc);
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         set_error("cudaStreamCreateWithFlags failed");
         return fail(DD_ECUDA);
@@ -994,6 +1025,15 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if ((rc = load_data(h, mask, values, st)) != DD_OK) return fail(rc);
     h->valid = true;
     if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("sync"); return fail(DD_ECUDA); }
+    // the device loops of every level, instantiated now rather than in the first solve
+    // (with FP32_REF / FP16_REF / BF16_REF the fine level sweeps under host control)
+    if (p.device_loop != 0) {
+        for (size_t l = 0; l < h->lv.size(); ++l) {
+            if (l == 0 && p.precision != DD_PREC_FP32) continue;
+            cudaGraphExec_t ex = nullptr;
+            if ((rc = loop_graph(h, h->lv[l], l == 0 ? p.max_sweeps : p.coarse_sweeps, &ex)) != DD_OK) return fail(rc);
+        }
+    }
     *out = h;
     return DD_OK;
 }
@@ -1166,9 +1206,9 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     if (h->prm.solver != DD_SOLVER_ORAS) { set_error("dd_inpaint_sweep needs DD_SOLVER_ORAS"); return DD_EINVAL; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Level& F = h->lv[0];
-    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, h->cur, st));
+    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, h->cur, h->tol_d, -1.0, st));
     const dd::SweepPair pair{{&F.map_u[0], &F.map_u[1]}, {F.u[0], F.u[1]}};
-    const dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, -1.0, 0.0, h->flag_d, h->sstate_d, 0};
+    const dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, h->tol_d, 0.0, h->flag_d, h->sstate_d, 0};
     for (int i = 0; i < n; ++i) {   // tol < 0: every launch is a full sweep
         DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), pair, nullptr, F.tmask, stop,
                                       h->prm.robin_p, h->prm.local_cg_iters, st));
@@ -1334,7 +1374,10 @@ int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double
     }
     if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return bail("cudaGraphInstantiate", e);
     long long after = 0;
-    for (auto h : b->hs) after += h->launches;
+    for (auto h : b->hs) {
+        after += h->launches;
+        for (Level& L : h->lv) L.loop_pending = false;   // captured, not run
+    }
     b->kernels = after - before;
     if (kernels_per_launch) *kernels_per_launch = b->kernels;
     *out = b;
@@ -1360,6 +1403,7 @@ int dd_batch_launch(dd_batch_handle b, void* stream) {
         h->pending_cascaded = true;
         h->ev_recorded = false;
         h->warm = false;
+        for (Level& L : h->lv) L.loop_pending = h->prm.device_loop != 0;   // passes counted at finish
     }
     b->launched = true;
     return DD_OK;

@@ -51,7 +51,8 @@ constexpr size_t kOffNorms = kOffResOut + align256(kMaxChannels * 16);
 constexpr size_t kOffRef = kOffNorms + align256((2 * kMaxChannels + 2) * 8);
 constexpr size_t kOffFlag = kOffRef + align256(kMaxChannels * 8);
 constexpr size_t kOffState = kOffFlag + align256(4 * 4);
-constexpr size_t kOffCount = kOffState + align256(4 * 4);
+constexpr size_t kOffTol = kOffState + align256(4 * 4);
+constexpr size_t kOffCount = kOffTol + align256(8);
 constexpr size_t kScratchBytes = kOffCount + align256(8);
 
 }  // namespace
@@ -143,6 +144,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     double* ref_d = reinterpret_cast<double*>(base + kOffRef);
     int* flag = reinterpret_cast<int*>(base + kOffFlag);
     int* sstate = reinterpret_cast<int*>(base + kOffState);
+    double* tol_d = reinterpret_cast<double*>(base + kOffTol);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long plane = (long long)H * P;
 
@@ -179,8 +181,8 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     bool converged = false;
     const dd::SweepPair pair{{&maps[0], &maps[1]}, {u[0], u[1]}};
     for (int attempt = 0; attempt < 4 && !converged; ++attempt) {
-        SS_CK(dd::launch_reset_sweep_state(sstate, flag, cur, st));
-        dd::SweepStop stop{partial, dd::kSweepSlots, norms2, ref_d, target, 0.0, flag, sstate, 0};
+        SS_CK(dd::launch_reset_sweep_state(sstate, flag, cur, tol_d, target, st));
+        dd::SweepStop stop{partial, dd::kSweepSlots, norms2, ref_d, tol_d, 0.0, flag, sstate, 0};
         const int start = done;
         int launched = 0;
         int hflag[3] = {0, 0, 0}, hstate[2] = {cur, 0};

@@ -540,6 +540,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         __threadfence();
         const SweepStop& sp = a.stop;
         const int sweep_index = __ldcg(sp.state + 3);   // launches before this one
+        const double tol = __ldcg(sp.tol);
         double worst = 0.0, best_ratio = 1e300;
         int bad = 0;
         for (int c = 0; c < a.C; ++c) {
@@ -562,7 +563,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         if (lane == 0) {
             int* const state = sp.state;
             if (bad) { flag[0] = 2; flag[1] = sweep_index; }
-            else if (worst <= sp.tol) { flag[0] = 1; flag[1] = sweep_index; }
+            else if (worst <= tol) { flag[0] = 1; flag[1] = sweep_index; }
             else if (sp.stall > 0.0 && sweep_index > 0 && best_ratio > sp.stall) {
                 flag[0] = 3;
                 flag[1] = sweep_index;
@@ -572,7 +573,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                 const double prev_worst = sp.norms2[2 * a.C];
                 state[0] = cur ^ 1;
                 state[1] += 1;
-                state[2] = (sp.tol > 0.0 && prev_worst > 0.0 && worst * (worst / prev_worst) <= sp.tol) ? 1 : 0;
+                state[2] = (tol > 0.0 && prev_worst > 0.0 && worst * (worst / prev_worst) <= tol) ? 1 : 0;
             } else {
                 state[2] = 0;   // the probe failed: sweep the same iterate in full
             }

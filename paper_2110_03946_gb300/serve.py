@@ -126,11 +126,34 @@ class Server:
         self.peak_bytes = max(self.peak_bytes, self.bytes_in_use)
         return s
 
+    def prewarm(self, requests, per_shape: int = 1) -> int:
+        """Create idle slots before traffic arrives: per_shape slots for each
+        distinct shape among requests (loaded with the first request of that
+        shape), as far as the HBM budget and the slot limit allow without
+        evicting.  The first requests of a shape then find a slot whose
+        allocations and device-loop graphs already exist.  Returns the number
+        of slots created."""
+        first = {}
+        for r in requests:
+            first.setdefault(r.shape, r)
+        made = 0
+        for shape, r in first.items():
+            for _ in range(per_shape):
+                need = self.b.bytes_for(shape)
+                if self.bytes_in_use + need > self.budget or len(self.slots) >= self.max_slots:
+                    break
+                if self._new_slot(r) is None:
+                    break
+                made += 1
+        return made
+
     # -- main loop -----------------------------------------------------------------
     def run(self, requests, realtime: bool = True, on_result=None):
         """Serve all requests; returns (results sorted by rid, metrics).
         on_result(result) is called at each completion, while result.output
         (the slot's buffer) still holds that request's image."""
+        for s in self.slots:   # sequence ids are local to one run
+            s.seq, s.t = None, -1
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         waiting: list[Request] = []
         results: list[Result] = []

@@ -121,6 +121,19 @@ def test_offline_mode_skips_idle_time():
     assert res[1].latency == pytest.approx(0.010)
 
 
+def test_prewarm_creates_idle_slots_within_budget():
+    b = FakeBackend()
+    one = 8 * 8 * 16
+    srv = Server(b, hbm_budget=3 * one + 16 * 16 * 16)
+    reqs = [_req(0, 0.0), _req(1, 0.0, 16, 16), _req(2, 0.0), _req(3, 0.05)]
+    made = srv.prewarm(reqs, per_shape=2)
+    assert made == 3 and b.created == 3              # 2 small + 1 large fill the budget; no eviction
+    assert srv.bytes_in_use <= srv.budget and srv.evictions == 0
+    res, m = srv.run(reqs, realtime=True)
+    assert m["failures"] == 0 and b.created == 3     # the stream found its slots already created
+    assert [r.rid for r in res] == [0, 1, 2, 3]
+
+
 def test_shard_covers_all_frames_once():
     items = list(range(11))
     parts = [replicas.shard(items, r, 3) for r in range(3)]
