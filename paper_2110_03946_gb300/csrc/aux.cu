@@ -29,22 +29,6 @@ constexpr int TX = 32, TY = 8;   // 2-D pass block: one warp per row segment
 
 dim3 grid2d(int H, int W, int C) { return dim3((W + TX - 1) / TX, (H + TY - 1) / TY, C); }
 
-__global__ void masked_copy_kernel(int H, int W, const float* __restrict__ src, int sp, long long splane,
-                                   const uint8_t* __restrict__ mask, int mp, float* __restrict__ dst,
-                                   int dp, long long dplane) {
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
-    if (x >= W || y >= H) return;
-    const float v = mask[(size_t)y * mp + x] ? src[c * splane + (size_t)y * sp + x] : 0.f;
-    dst[c * dplane + (size_t)y * dp + x] = v;
-}
-
-__global__ void copy2d_kernel(int H, int W, const float* __restrict__ src, int sp, long long splane,
-                              float* __restrict__ dst, int dp, long long dplane) {
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
-    if (x >= W || y >= H) return;
-    dst[c * dplane + (size_t)y * dp + x] = src[c * splane + (size_t)y * sp + x];
-}
-
 __global__ void reset_known_kernel(int H, int W, float* __restrict__ u, int up, long long uplane,
                                    const uint8_t* __restrict__ mask, int mp, const float* __restrict__ f,
                                    int fp, long long fplane) {
@@ -70,9 +54,6 @@ __global__ void convert_kernel(int H, int W, const float* __restrict__ src, int 
 // s + e by TwoSum (Knuth), and the four pairs are accumulated as a
 // double-single number (hi, lo) with a ~48-bit significand, the accuracy FP64
 // gives here.  Per-block sums of r^2 are written as doubles.
-constexpr int RES_TPB = 256;
-constexpr int RES_ROWS = 4;   // rows per block
-
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
@@ -88,58 +69,348 @@ __device__ __forceinline__ void ds_add(float& hi, float& lo, float s, float e) {
     lo = __fsub_rn(l, __fsub_rn(hi, t));
 }
 
+// Vectorised streaming layout: a thread owns 4 consecutive columns (one
+// float4 where the row is 16-byte aligned) in V_ROWS rows; a block of 32 x 8
+// threads covers 128 columns x 32 rows, so a warp moves 512 contiguous bytes
+// per row and each thread keeps several independent 16-byte loads in flight.
+constexpr int V_TX = 32, V_TY = 8, V_ROWS = 4;
+constexpr int V_TPB = V_TX * V_TY;
+constexpr int V_COLS = V_TX * 4, V_BROWS = V_TY * V_ROWS;
+
+dim3 gridv(int H, int W, int C) { return dim3((W + V_COLS - 1) / V_COLS, (H + V_BROWS - 1) / V_BROWS, C); }
+
+// rows of pitch `pitch` elements of `elem` bytes (planes `plane` elements
+// apart) from p start on 16-byte boundaries
+bool vec_ok(const void* p, long long pitch, long long plane, int elem) {
+    return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && (pitch * elem) % 16 == 0 && (plane * elem) % 16 == 0;
+}
+
+__device__ __forceinline__ void ld4(const float* __restrict__ row, int x0, int W, bool vec, float (&v)[4]) {
+    if (vec && x0 + 3 < W) {
+        const float4 t = *reinterpret_cast<const float4*>(row + x0);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = x0 + j < W ? row[x0 + j] : 0.f;
+    }
+}
+
+__device__ __forceinline__ void st4(float* __restrict__ row, int x0, int W, bool vec, const float (&v)[4]) {
+    if (vec && x0 + 3 < W) {
+        *reinterpret_cast<float4*>(row + x0) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (x0 + j < W) row[x0 + j] = v[j];
+    }
+}
+
+__device__ __forceinline__ void ldm4(const uint8_t* __restrict__ row, int x0, int W, bool vec, bool (&m)[4]) {
+    if (vec && x0 + 3 < W) {
+        const uchar4 t = *reinterpret_cast<const uchar4*>(row + x0);
+        m[0] = t.x != 0; m[1] = t.y != 0; m[2] = t.z != 0; m[3] = t.w != 0;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m[j] = x0 + j < W && row[x0 + j] != 0;
+    }
+}
+
+struct ResVec {
+    bool u, m, g;   // float4 / uchar4 access to u, mask, g_out (F32 only)
+};
+
+// Per pixel p the four in-image neighbour differences u_q - u_p are added in
+// the order N, S, W, E as TwoSum pairs; r = 0 on known pixels.  Each thread
+// accumulates r^2 (FP32) and max |r| over its pixels; warp butterflies, then
+// the block's warps in order, give one double2 partial per block.  With
+// a.out, the last block (atomic ticket) reduces the partials of every channel
+// in block order into out[c] = {sum r^2, max |r|} and sqrt_out[c] = sqrt(sum).
 template <typename T>
-__global__ void __launch_bounds__(RES_TPB) res64_kernel(Res64Args a) {
-    // block (bx, by, c) covers columns [bx*RES_TPB, +RES_TPB) and rows [by*RES_ROWS, +RES_ROWS)
-    const int x = blockIdx.x * RES_TPB + threadIdx.x;
+__global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
     const int c = blockIdx.z;
+    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    const int H = a.H, W = a.W;
     const float* __restrict__ u = a.u + c * a.uplane;
-    float s = 0.f, m = 0.f;
     const float sinv = a.g_out ? (float)a.scale_inv[c] : 0.f;
-    if (x < a.W) {
-        for (int rr = 0; rr < RES_ROWS; ++rr) {
-            const int y = blockIdx.y * RES_ROWS + rr;
-            if (y >= a.H) break;
-            float r = 0.f;
-            if (!a.mask[(size_t)y * a.mp + x]) {
-                const size_t o = (size_t)y * a.up + x;
-                const float uc = u[o];
-                float hi = 0.f, lo = 0.f, d, e;
-                if (y > 0) { two_sum(u[o - a.up], -uc, d, e); ds_add(hi, lo, d, e); }
-                if (y < a.H - 1) { two_sum(u[o + a.up], -uc, d, e); ds_add(hi, lo, d, e); }
-                if (x > 0) { two_sum(u[o - 1], -uc, d, e); ds_add(hi, lo, d, e); }
-                if (x < a.W - 1) { two_sum(u[o + 1], -uc, d, e); ds_add(hi, lo, d, e); }
-                r = __fadd_rn(hi, lo);
-            }
-            s = fmaf(r, r, s);
-            m = fmaxf(m, fabsf(r));
-            if (a.g_out) {
-                T* g = static_cast<T*>(a.g_out) + c * a.gplane;
-                g[(size_t)y * a.gp + x] = from_f<T>(r * sinv);
+    const bool xin = x0 < W;
+    float rows[V_ROWS + 2][4];
+#pragma unroll
+    for (int k = 0; k < V_ROWS + 2; ++k) {
+        const int y = yb - 1 + k;
+        if (xin && y >= 0 && y < H) {
+            ld4(u + (size_t)y * a.up, x0, W, vec.u, rows[k]);
+        } else {
+            rows[k][0] = rows[k][1] = rows[k][2] = rows[k][3] = 0.f;
+        }
+    }
+    float s = 0.f, mx = 0.f;
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        const int y = yb + k;
+        const float* rw = rows[k + 1];
+        float left = __shfl_up_sync(0xffffffffu, rw[3], 1);
+        float right = __shfl_down_sync(0xffffffffu, rw[0], 1);
+        if (!xin || y >= H) continue;
+        if (threadIdx.x == 0) left = x0 > 0 ? u[(size_t)y * a.up + x0 - 1] : 0.f;
+        if (threadIdx.x == V_TX - 1) right = x0 + 4 < W ? u[(size_t)y * a.up + x0 + 4] : 0.f;
+        bool known[4];
+        ldm4(a.mask + (size_t)y * a.mp, x0, W, vec.m, known);
+        float r[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = x0 + j;
+            const float uc = rw[j];
+            const float wv = j > 0 ? rw[j - 1] : left;
+            const float ev = j < 3 ? rw[j + 1] : right;
+            float hi = 0.f, lo = 0.f, d, e;
+            if (y > 0) { two_sum(rows[k][j], -uc, d, e); ds_add(hi, lo, d, e); }
+            if (y < H - 1) { two_sum(rows[k + 2][j], -uc, d, e); ds_add(hi, lo, d, e); }
+            if (x > 0) { two_sum(wv, -uc, d, e); ds_add(hi, lo, d, e); }
+            if (x < W - 1) { two_sum(ev, -uc, d, e); ds_add(hi, lo, d, e); }
+            r[j] = (x < W && !known[j]) ? __fadd_rn(hi, lo) : 0.f;
+            s = fmaf(r[j], r[j], s);
+            mx = fmaxf(mx, fabsf(r[j]));
+        }
+        if (a.g_out) {
+            T* g = static_cast<T*>(a.g_out) + c * a.gplane + (size_t)y * a.gp;
+            if constexpr (sizeof(T) == 4) {
+                const float gv[4] = {r[0] * sinv, r[1] * sinv, r[2] * sinv, r[3] * sinv};
+                st4(reinterpret_cast<float*>(g), x0, W, vec.g, gv);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (x0 + j < W) g[x0 + j] = from_f<T>(r[j] * sinv);
             }
         }
     }
-    // fixed-order block reduction: warp butterflies, then the 8 warp results
+    // fixed-order block reduction: warp butterflies, then the warps in order
 #pragma unroll
     for (int k = 16; k >= 1; k >>= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, k);
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, k));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, k));
     }
-    __shared__ float ss[RES_TPB / 32], sm[RES_TPB / 32];
-    if ((threadIdx.x & 31) == 0) {
-        ss[threadIdx.x >> 5] = s;
-        sm[threadIdx.x >> 5] = m;
+    __shared__ float ss[V_TPB / 32], sm[V_TPB / 32];
+    __shared__ int s_last;
+    const int tid = threadIdx.y * V_TX + threadIdx.x;
+    if ((tid & 31) == 0) {
+        ss[tid >> 5] = s;
+        sm[tid >> 5] = mx;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         double ts = 0.0;
         float tm = 0.f;
-        for (int w = 0; w < RES_TPB / 32; ++w) {
+        for (int w = 0; w < V_TPB / 32; ++w) {
             ts += (double)ss[w];
             tm = fmaxf(tm, sm[w]);
         }
-        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-        a.part[(size_t)c * a.nblk + blk] = make_double2(ts, (double)tm);
+        a.part[(size_t)c * a.nblk + blockIdx.y * gridDim.x + blockIdx.x] = make_double2(ts, (double)tm);
+    }
+    if (a.out == nullptr) return;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.y * gridDim.z - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    __shared__ double rs[V_TPB];
+    __shared__ double rm[V_TPB];
+    for (int cc = 0; cc < a.C; ++cc) {
+        double sv = 0.0, mv = 0.0;
+        for (int i = tid; i < a.nblk; i += V_TPB) {
+            const double2 v = __ldcg(a.part + (size_t)cc * a.nblk + i);
+            sv += v.x;
+            mv = fmax(mv, v.y);
+        }
+        rs[tid] = sv;
+        rm[tid] = mv;
+        __syncthreads();
+        for (int hh = V_TPB / 2; hh > 0; hh >>= 1) {
+            if (tid < hh) {
+                rs[tid] += rs[tid + hh];
+                rm[tid] = fmax(rm[tid], rm[tid + hh]);
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            a.out[cc] = make_double2(rs[0], rm[0]);
+            if (a.sqrt_out) a.sqrt_out[cc] = sqrt(rs[0]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *a.ticket = 0u;
+}
+
+// ---- streaming passes (vectorised layout above) -----------------------------------------
+struct CopyVec {
+    bool src, dst, m;
+};
+
+// dst = mask ? src : 0 (mask may be null: plain copy)
+__global__ void __launch_bounds__(V_TPB) masked_copy_kernel(int H, int W, const float* __restrict__ src, int sp,
+                                                            long long splane, const uint8_t* __restrict__ mask,
+                                                            int mp, float* __restrict__ dst, int dp,
+                                                            long long dplane, CopyVec vec) {
+    const int c = blockIdx.z;
+    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    if (x0 >= W) return;
+    const float* __restrict__ s = src + c * splane;
+    float* __restrict__ d = dst + c * dplane;
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        const int y = yb + k;
+        if (y >= H) break;
+        float v[4];
+        ld4(s + (size_t)y * sp, x0, W, vec.src, v);
+        if (mask != nullptr) {
+            bool m[4];
+            ldm4(mask + (size_t)y * mp, x0, W, vec.m, m);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = m[j] ? v[j] : 0.f;
+        }
+        st4(d + (size_t)y * dp, x0, W, vec.dst, v);
+    }
+}
+
+// dst = (sel[0] ? s1 : s0), the buffer chosen on the device
+__global__ void __launch_bounds__(V_TPB) copy2d_sel_kernel(int H, int W, const float* __restrict__ s0,
+                                                           const float* __restrict__ s1, const int* __restrict__ sel,
+                                                           int sp, long long splane, float* __restrict__ dst, int dp,
+                                                           long long dplane, CopyVec vec) {
+    const int c = blockIdx.z;
+    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    if (x0 >= W) return;
+    const float* __restrict__ s = (sel[0] ? s1 : s0) + c * splane;
+    float* __restrict__ d = dst + c * dplane;
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        const int y = yb + k;
+        if (y >= H) break;
+        float v[4];
+        ld4(s + (size_t)y * sp, x0, W, vec.src, v);
+        st4(d + (size_t)y * dp, x0, W, vec.dst, v);
+    }
+}
+
+// Bilinear cell-centred prolongation of the coarse iterate (Sec. 4) on
+// unknown pixels, f on known ones (mask may be null: everywhere bilinear).
+// The coarse source is sel[0] ? uc1 : uc0 (sel may be null: uc0).
+__global__ void __launch_bounds__(V_TPB) prolong_kernel(int Hc, int Wc, int H, int W, const float* __restrict__ uc0,
+                                                        const float* __restrict__ uc1, const int* __restrict__ sel,
+                                                        int ucp, long long ucplane, const uint8_t* __restrict__ mask,
+                                                        int mp, const float* __restrict__ f, int fp, long long fplane,
+                                                        float* __restrict__ u, int up, long long uplane, CopyVec vec) {
+    const int c = blockIdx.z;
+    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    if (x0 >= W) return;
+    const float* __restrict__ p = ((sel != nullptr && sel[0]) ? uc1 : uc0) + c * ucplane;
+    int xa[4], xb[4];
+    float wx[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float tx = fminf(fmaxf((x0 + j - 0.5f) * 0.5f, 0.f), (float)(Wc - 1));
+        xa[j] = (int)floorf(tx);
+        xb[j] = min(xa[j] + 1, Wc - 1);
+        wx[j] = tx - (float)xa[j];
+    }
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        const int y = yb + k;
+        if (y >= H) break;
+        const float ty = fminf(fmaxf((y - 0.5f) * 0.5f, 0.f), (float)(Hc - 1));
+        const int ya = (int)floorf(ty), yb1 = min(ya + 1, Hc - 1);
+        const float wy = ty - (float)ya;
+        const float* __restrict__ ra = p + (size_t)ya * ucp;
+        const float* __restrict__ rb = p + (size_t)yb1 * ucp;
+        bool m[4] = {false, false, false, false};
+        float fv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (mask != nullptr) {
+            ldm4(mask + (size_t)y * mp, x0, W, vec.m, m);
+            ld4(f + c * fplane + (size_t)y * fp, x0, W, vec.src, fv);
+        }
+        float out[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (m[j]) {
+                out[j] = fv[j];
+            } else if (x0 + j < W) {
+                const float top = ra[xa[j]] * (1.f - wx[j]) + ra[xb[j]] * wx[j];
+                const float bot = rb[xa[j]] * (1.f - wx[j]) + rb[xb[j]] * wx[j];
+                out[j] = top * (1.f - wy) + bot * wy;
+            } else {
+                out[j] = 0.f;
+            }
+        }
+        st4(u + c * uplane + (size_t)y * up, x0, W, vec.dst, out);
+    }
+}
+
+// Dyadic restriction (Sec. 4): coarse pixel (X, Y) is known if any of its 2x2
+// fine pixels is, with the mean of their known values.  A thread owns 4
+// coarse columns (8 fine columns) in V_ROWS coarse rows.
+__global__ void __launch_bounds__(V_TPB) restrict_kernel(int H, int W, int Hc, int Wc, const uint8_t* __restrict__ mask,
+                                                         int mp, const float* __restrict__ f, int fp,
+                                                         long long fplane, uint8_t* __restrict__ mask_c, int mcp,
+                                                         float* __restrict__ f_c, int fcp, long long fcplane,
+                                                         CopyVec vec) {
+    const int c = blockIdx.z;
+    const int X0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int Yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    if (X0 >= Wc) return;
+    const float* __restrict__ fc = f + c * fplane;
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        const int Y = Yb + k;
+        if (Y >= Hc) break;
+        float fv[2][8];
+        bool mv[2][8];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int y = 2 * Y + dy;
+            if (y < H) {
+                float a4[4], b4[4];
+                bool ma[4], mb[4];
+                ld4(fc + (size_t)y * fp, 2 * X0, W, vec.src, a4);
+                ld4(fc + (size_t)y * fp, 2 * X0 + 4, W, vec.src, b4);
+                ldm4(mask + (size_t)y * mp, 2 * X0, W, vec.m, ma);
+                ldm4(mask + (size_t)y * mp, 2 * X0 + 4, W, vec.m, mb);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    fv[dy][j] = a4[j]; fv[dy][j + 4] = b4[j];
+                    mv[dy][j] = ma[j]; mv[dy][j + 4] = mb[j];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) { fv[dy][j] = 0.f; mv[dy][j] = false; }
+            }
+        }
+        float out[4];
+        uint8_t mo[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int cnt = 0;
+            float acc = 0.f;
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx)
+                    if (mv[dy][2 * j + dx]) {
+                        ++cnt;
+                        acc += fv[dy][2 * j + dx];
+                    }
+            out[j] = cnt > 0 ? acc / (float)cnt : 0.f;
+            mo[j] = cnt > 0 ? 1 : 0;
+        }
+        st4(f_c + c * fcplane + (size_t)Y * fcp, X0, Wc, vec.dst, out);
+        if (c == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (X0 + j < Wc) mask_c[(size_t)Y * mcp + X0 + j] = mo[j];
+        }
     }
 }
 
@@ -169,51 +440,6 @@ __global__ void __launch_bounds__(RED_TPB) reduce_part_kernel(const double2* __r
 }
 
 // ---- multilevel ----------------------------------------------------------------------
-__global__ void restrict_kernel(int H, int W, int Hc, int Wc, const uint8_t* __restrict__ mask, int mp,
-                                const float* __restrict__ f, int fp, long long fplane,
-                                uint8_t* __restrict__ mask_c, int mcp, float* __restrict__ f_c, int fcp,
-                                long long fcplane) {
-    const int X = blockIdx.x * TX + threadIdx.x, Y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
-    if (X >= Wc || Y >= Hc) return;
-    int cnt = 0;
-    float acc = 0.f;
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-            const int y = 2 * Y + dy, x = 2 * X + dx;
-            if (y < H && x < W && mask[(size_t)y * mp + x]) {
-                ++cnt;
-                acc += f[c * fplane + (size_t)y * fp + x];
-            }
-        }
-    if (c == 0) mask_c[(size_t)Y * mcp + X] = cnt > 0 ? 1 : 0;
-    f_c[c * fcplane + (size_t)Y * fcp + X] = cnt > 0 ? acc / (float)cnt : 0.f;
-}
-
-__global__ void prolong_kernel(int Hc, int Wc, int H, int W, const float* __restrict__ uc, int ucp,
-                               long long ucplane, const uint8_t* __restrict__ mask, int mp,
-                               const float* __restrict__ f, int fp, long long fplane, float* __restrict__ u,
-                               int up, long long uplane) {
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
-    if (x >= W || y >= H) return;
-    float out;
-    if (mask != nullptr && mask[(size_t)y * mp + x]) {
-        out = f[c * fplane + (size_t)y * fp + x];
-    } else {
-        const float ty = fminf(fmaxf((y - 0.5f) * 0.5f, 0.f), (float)(Hc - 1));
-        const float tx = fminf(fmaxf((x - 0.5f) * 0.5f, 0.f), (float)(Wc - 1));
-        const int y0 = (int)floorf(ty), x0 = (int)floorf(tx);
-        const int y1 = min(y0 + 1, Hc - 1), x1 = min(x0 + 1, Wc - 1);
-        const float wy = ty - (float)y0, wx = tx - (float)x0;
-        const float* p = uc + c * ucplane;
-        const float top = p[(size_t)y0 * ucp + x0] * (1.f - wx) + p[(size_t)y0 * ucp + x1] * wx;
-        const float bot = p[(size_t)y1 * ucp + x0] * (1.f - wx) + p[(size_t)y1 * ucp + x1] * wx;
-        out = top * (1.f - wy) + bot * wy;
-    }
-    u[c * uplane + (size_t)y * up + x] = out;
-}
-
 template <typename T>
 __global__ void correct_kernel(int H, int W, float* __restrict__ u, int up, long long uplane,
                                const T* __restrict__ e, int ep, long long eplane,
@@ -263,40 +489,6 @@ __global__ void loop_ctl_kernel(const int* __restrict__ flag, const int* __restr
     if (flag[0] != 0 || state[1] >= cap || passes >= max_passes) cudaGraphSetConditional(cond, 0);
 }
 
-__global__ void prolong_sel_kernel(int Hc, int Wc, int H, int W, const float* __restrict__ uc0,
-                                   const float* __restrict__ uc1, const int* __restrict__ sel, int ucp,
-                                   long long ucplane, const uint8_t* __restrict__ mask, int mp,
-                                   const float* __restrict__ f, int fp, long long fplane, float* __restrict__ u,
-                                   int up, long long uplane) {
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
-    if (x >= W || y >= H) return;
-    const float* __restrict__ uc = sel[0] ? uc1 : uc0;
-    float out;
-    if (mask[(size_t)y * mp + x]) {
-        out = f[c * fplane + (size_t)y * fp + x];
-    } else {
-        const float ty = fminf(fmaxf((y - 0.5f) * 0.5f, 0.f), (float)(Hc - 1));
-        const float tx = fminf(fmaxf((x - 0.5f) * 0.5f, 0.f), (float)(Wc - 1));
-        const int y0 = (int)floorf(ty), x0 = (int)floorf(tx);
-        const int y1 = min(y0 + 1, Hc - 1), x1 = min(x0 + 1, Wc - 1);
-        const float wy = ty - (float)y0, wx = tx - (float)x0;
-        const float* p = uc + c * ucplane;
-        const float top = p[(size_t)y0 * ucp + x0] * (1.f - wx) + p[(size_t)y0 * ucp + x1] * wx;
-        const float bot = p[(size_t)y1 * ucp + x0] * (1.f - wx) + p[(size_t)y1 * ucp + x1] * wx;
-        out = top * (1.f - wy) + bot * wy;
-    }
-    u[c * uplane + (size_t)y * up + x] = out;
-}
-
-__global__ void copy2d_sel_kernel(int H, int W, const float* __restrict__ s0, const float* __restrict__ s1,
-                                  const int* __restrict__ sel, int sp, long long splane, float* __restrict__ dst,
-                                  int dp, long long dplane) {
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
-    if (x >= W || y >= H) return;
-    const float* __restrict__ src = sel[0] ? s1 : s0;
-    dst[c * dplane + (size_t)y * dp + x] = src[c * splane + (size_t)y * sp + x];
-}
-
 __global__ void sqrt_sums_kernel(const double2* __restrict__ in, double* __restrict__ out, int C) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < C) out[c] = sqrt(in[c].x);
@@ -307,13 +499,17 @@ __global__ void sqrt_sums_kernel(const double2* __restrict__ in, double* __restr
 cudaError_t launch_masked_copy(int H, int W, int C, const float* src, int sp, long long splane,
                                const uint8_t* mask, int mp, float* dst, int dp, long long dplane,
                                cudaStream_t st) {
-    masked_copy_kernel<<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(H, W, src, sp, splane, mask, mp, dst, dp, dplane);
+    const CopyVec v{vec_ok(src, sp, splane, 4), vec_ok(dst, dp, dplane, 4), vec_ok(mask, mp, 0, 1)};
+    masked_copy_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(H, W, src, sp, splane, mask, mp, dst, dp,
+                                                                    dplane, v);
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy2d(int H, int W, int C, const float* src, int sp, long long splane, float* dst,
                           int dp, long long dplane, cudaStream_t st) {
-    copy2d_kernel<<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(H, W, src, sp, splane, dst, dp, dplane);
+    const CopyVec v{vec_ok(src, sp, splane, 4), vec_ok(dst, dp, dplane, 4), false};
+    masked_copy_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(H, W, src, sp, splane, nullptr, 0, dst, dp,
+                                                                    dplane, v);
     return cudaGetLastError();
 }
 
@@ -347,16 +543,23 @@ cudaError_t launch_convert(int H, int W, int C, const float* src, int sp, long l
 }
 
 int res64_blocks(int H, int W) {
-    return ((W + RES_TPB - 1) / RES_TPB) * ((H + RES_ROWS - 1) / RES_ROWS);
+    const dim3 g = gridv(H, W, 1);
+    return (int)(g.x * g.y);
 }
 
 cudaError_t launch_res64(const Res64Args& a, cudaStream_t st) {
-    dim3 grid((a.W + RES_TPB - 1) / RES_TPB, (a.H + RES_ROWS - 1) / RES_ROWS, a.C);
+    const dim3 grid = gridv(a.H, a.W, a.C);
     if (a.nblk != (int)(grid.x * grid.y)) return cudaErrorInvalidValue;
+    if (a.out != nullptr && a.ticket == nullptr) return cudaErrorInvalidValue;
+    ResVec v;
+    v.u = vec_ok(a.u, a.up, a.uplane, 4);
+    v.m = vec_ok(a.mask, a.mp, 0, 1);
+    v.g = a.g_out != nullptr && a.gst == Store::F32 && vec_ok(a.g_out, a.gp, a.gplane, 4);
+    const dim3 block(V_TX, V_TY);
     switch (a.gst) {
-        case Store::F32: res64_kernel<float><<<grid, RES_TPB, 0, st>>>(a); break;
-        case Store::F16: res64_kernel<__half><<<grid, RES_TPB, 0, st>>>(a); break;
-        case Store::BF16: res64_kernel<__nv_bfloat16><<<grid, RES_TPB, 0, st>>>(a); break;
+        case Store::F32: res64_kernel<float><<<grid, block, 0, st>>>(a, v); break;
+        case Store::F16: res64_kernel<__half><<<grid, block, 0, st>>>(a, v); break;
+        case Store::BF16: res64_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(a, v); break;
     }
     return cudaGetLastError();
 }
@@ -370,16 +573,19 @@ cudaError_t launch_restrict(int H, int W, int C, const uint8_t* mask, int mp, co
                             long long fplane, uint8_t* mask_c, int mcp, float* f_c, int fcp, long long fcplane,
                             cudaStream_t st) {
     const int Hc = (H + 1) / 2, Wc = (W + 1) / 2;
-    restrict_kernel<<<grid2d(Hc, Wc, C), dim3(TX, TY), 0, st>>>(H, W, Hc, Wc, mask, mp, f, fp, fplane, mask_c,
-                                                                mcp, f_c, fcp, fcplane);
+    const CopyVec v{vec_ok(f, fp, fplane, 4), vec_ok(f_c, fcp, fcplane, 4), vec_ok(mask, mp, 0, 1)};
+    restrict_kernel<<<gridv(Hc, Wc, C), dim3(V_TX, V_TY), 0, st>>>(H, W, Hc, Wc, mask, mp, f, fp, fplane, mask_c,
+                                                                   mcp, f_c, fcp, fcplane, v);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prolong(int Hc, int Wc, int H, int W, int C, const float* uc, int ucp, long long ucplane,
                            const uint8_t* mask, int mp, const float* f, int fp, long long fplane, float* u, int up,
                            long long uplane, cudaStream_t st) {
-    prolong_kernel<<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(Hc, Wc, H, W, uc, ucp, ucplane, mask, mp, f, fp,
-                                                             fplane, u, up, uplane);
+    const CopyVec v{mask != nullptr && vec_ok(f, fp, fplane, 4), vec_ok(u, up, uplane, 4),
+                    mask != nullptr && vec_ok(mask, mp, 0, 1)};
+    prolong_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(Hc, Wc, H, W, uc, uc, nullptr, ucp, ucplane, mask,
+                                                                mp, f, fp, fplane, u, up, uplane, v);
     return cudaGetLastError();
 }
 
@@ -427,14 +633,17 @@ cudaError_t launch_prolong_sel(int Hc, int Wc, int H, int W, int C, const float*
                                const int* sel, int ucp, long long ucplane, const uint8_t* mask, int mp,
                                const float* f, int fp, long long fplane, float* u, int up, long long uplane,
                                cudaStream_t st) {
-    prolong_sel_kernel<<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(Hc, Wc, H, W, uc0, uc1, sel, ucp, ucplane, mask,
-                                                                 mp, f, fp, fplane, u, up, uplane);
+    const CopyVec v{vec_ok(f, fp, fplane, 4), vec_ok(u, up, uplane, 4), vec_ok(mask, mp, 0, 1)};
+    prolong_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(Hc, Wc, H, W, uc0, uc1, sel, ucp, ucplane, mask,
+                                                                mp, f, fp, fplane, u, up, uplane, v);
     return cudaGetLastError();
 }
 
 cudaError_t launch_copy2d_sel(int H, int W, int C, const float* s0, const float* s1, const int* sel, int sp,
                               long long splane, float* dst, int dp, long long dplane, cudaStream_t st) {
-    copy2d_sel_kernel<<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(H, W, s0, s1, sel, sp, splane, dst, dp, dplane);
+    const CopyVec v{vec_ok(s0, sp, splane, 4) && vec_ok(s1, sp, splane, 4), vec_ok(dst, dp, dplane, 4), false};
+    copy2d_sel_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(H, W, s0, s1, sel, sp, splane, dst, dp, dplane,
+                                                                   v);
     return cudaGetLastError();
 }
 

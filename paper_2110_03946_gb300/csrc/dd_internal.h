@@ -143,7 +143,10 @@ struct Res64Args {
     const uint8_t* mask; int mp;
     void* g_out; Store gst; int gp; long long gplane;
     const double* scale_inv;   // device, per channel (only with g_out)
-    double2* part; int nblk;
+    double2* part; int nblk;   // nblk = res64_blocks(H, W) per channel
+    // optional, fused: the last block writes out[c] = {sum r^2, max |r|} (and
+    // sqrt_out[c] = sqrt(sum) if given); ticket: a zero device counter, left zero
+    double2* out; double* sqrt_out; unsigned int* ticket;
 };
 int res64_blocks(int H, int W);
 cudaError_t launch_res64(const Res64Args& a, cudaStream_t st);

@@ -131,7 +131,8 @@ struct dd_inpaint {
     // residual / stop-test scratch
     double2* res_part = nullptr;
     int res_nblk = 0;
-    double2* res_out = nullptr;     // C
+    double2* res_out = nullptr;     // C per level
+    unsigned int* res_ticket = nullptr;   // completion ticket of the fused residual reduction (zero)
     double* norms2_d = nullptr;     // C
     int* flag_d = nullptr;          // [0] stop flag, [1] conv_at, [2] device wait timed out, [3] ticket
     int* sstate_d = nullptr;        // sweep state: current buffer, full sweeps, probe request, launches
@@ -267,9 +268,8 @@ int load_data(dd_inpaint* h, const uint8_t* mask, const float* values, cudaStrea
         a.mask = L.mask; a.mp = L.W;
         a.g_out = nullptr; a.gst = Store::F32;
         a.part = h->res_part; a.nblk = nblk;
+        a.out = h->res_out + (size_t)l * h->C; a.sqrt_out = L.ref_d; a.ticket = h->res_ticket;
         DD_LAUNCH(h, dd::launch_res64(a, st));
-        DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, nblk, h->C, h->res_out + (size_t)l * h->C, st));
-        DD_LAUNCH(h, dd::launch_sqrt_sums(h->res_out + (size_t)l * h->C, L.ref_d, h->C, st));
     }
     DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     if (!sync) {   // counts and reference norms are read back with the next solve
@@ -373,8 +373,8 @@ int fine_residual64(dd_inpaint* h, cudaStream_t st, std::vector<double>& rel, st
     a.mask = L.mask; a.mp = L.W;
     a.g_out = nullptr; a.gst = h->lowst;
     a.part = h->res_part; a.nblk = h->res_nblk;
+    a.out = h->res_out; a.ticket = h->res_ticket;
     DD_LAUNCH(h, dd::launch_res64(a, st));
-    DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, h->res_nblk, h->C, h->res_out, st));
     DD_CK(cudaMemcpyAsync(h->h_res, h->res_out, sizeof(double2) * h->C, cudaMemcpyDeviceToHost, st));
     DD_CK(cudaStreamSynchronize(st));
     rel.assign(h->C, 0.0);
@@ -575,8 +575,8 @@ int enqueue_cg(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool
     ra.g_out = L.cg_r; ra.gst = Store::F32; ra.gp = L.P; ra.gplane = L.plane();
     ra.scale_inv = h->ones_d;
     ra.part = h->res_part; ra.nblk = nblk;
+    ra.out = h->res_out; ra.ticket = h->res_ticket;
     DD_LAUNCH(h, dd::launch_res64(ra, st));
-    DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, nblk, h->C, h->res_out, st));
     DD_LAUNCH(h, dd::launch_cg_init(h->res_out, L.cg_scal, h->C, st));
     DD_CK(cudaMemsetAsync(L.cg_p[0], 0, sizeof(float) * (size_t)h->C * L.plane(), st));
     if (loop) return run_loop(h, L, n, st, capture);
@@ -636,8 +636,8 @@ int residual_of(dd_inpaint* h, const float* u, int up, long long uplane, cudaStr
     a.mask = L.mask; a.mp = L.W;
     a.g_out = nullptr; a.gst = Store::F32;
     a.part = h->res_part; a.nblk = h->res_nblk;
+    a.out = h->res_out; a.ticket = h->res_ticket;
     DD_LAUNCH(h, dd::launch_res64(a, st));
-    DD_LAUNCH(h, dd::launch_reduce_part(h->res_part, h->res_nblk, h->C, h->res_out, st));
     DD_CK(cudaMemcpyAsync(h->h_res, h->res_out, sizeof(double2) * h->C, cudaMemcpyDeviceToHost, st));
     return DD_OK;
 }
@@ -1001,6 +1001,11 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if ((rc = dalloc_t(h, &h->flag_d, 4)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->ctl_d, 4)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->tol_d, 1)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->res_ticket, 1)) != DD_OK) return fail(rc);
+    if (cudaMemset(h->res_ticket, 0, sizeof(unsigned int)) != cudaSuccess) {
+        set_error("cudaMemset");
+        return fail(DD_ECUDA);
+    }
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         set_error("cudaStreamCreateWithFlags failed");
         return fail(DD_ECUDA);
