@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP16-storage measurement")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving measurements")
+    ap.add_argument("--device-loop", type=int, default=1, choices=[0, 1],
+                    help="1: level iterations in CUDA graph loops (default); 0: plain launches, which ncu can "
+                         "list kernel by kernel")
     return ap.parse_args()
 
 
@@ -80,6 +83,9 @@ def solver_params(args, precision):
         if val is not None:
             prm[key] = val
             src += f"; {key} overridden"
+    if getattr(args, "device_loop", 1) == 0:
+        prm["device_loop"] = 0
+        src += "; device loops off"
     return prm, src
 
 
@@ -707,6 +713,7 @@ def run_ours(args):
                    "block": prm["block"], "overlap": prm["overlap"], "local_cg_iters": prm["local_cg_iters"],
                    "levels": prm["levels"], "robin_p": prm["robin_p"], "coarse_tol": prm["coarse_tol"],
                    "params_source": tuned_src, "precision": args.precision, "frames_resident": args.frames,
+                   "device_loop": args.device_loop,
                    "l2": "inputs larger than L2 (each frame's working set ~0.5 GB, frames cycled)",
                    "parallelism": f"replicas x{world}"},
         "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))],

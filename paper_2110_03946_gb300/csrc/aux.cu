@@ -116,27 +116,34 @@ __device__ __forceinline__ void ldm4(const uint8_t* __restrict__ row, int x0, in
 }
 
 struct ResVec {
-    bool u, m, g;   // float4 / uchar4 access to u, mask, g_out (F32 only)
+    bool u, m, g, cp;   // float4 / uchar4 access to u (and u1), mask, g_out (F32 only), copy_out
 };
 
-// Per pixel p the four in-image neighbour differences u_q - u_p are added in
-// the order N, S, W, E as TwoSum pairs; r = 0 on known pixels.  Each thread
+// Per pixel p, r_p = sum over in-image neighbours q of (u_q - u_p), formed
+// with TwoSum so that only the final rounding to FP32 remains; r = 0 on known
+// pixels.  Each thread
 // accumulates r^2 (FP32) and max |r| over its pixels; warp butterflies, then
 // the block's warps in order, give one double2 partial per block.  With
 // a.out, the last block (atomic ticket) reduces the partials of every channel
 // in block order into out[c] = {sum r^2, max |r|} and sqrt_out[c] = sqrt(sum).
+// 4 rows per thread (a block covers 128 x 32 pixels): many short blocks keep
+// every SM busy to the end of the pass; only thread 0 fences and takes the ticket
+constexpr int R_ROWS = 4, R_BROWS = V_TY * R_ROWS;
+
+dim3 grid_res(int H, int W, int C) { return dim3((W + V_COLS - 1) / V_COLS, (H + R_BROWS - 1) / R_BROWS, C); }
+
 template <typename T>
 __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
     const int c = blockIdx.z;
     const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
-    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    const int yb = (blockIdx.y * V_TY + threadIdx.y) * R_ROWS;
     const int H = a.H, W = a.W;
-    const float* __restrict__ u = a.u + c * a.uplane;
+    const float* __restrict__ u = ((a.sel != nullptr && a.sel[0]) ? a.u1 : a.u) + c * a.uplane;
     const float sinv = a.g_out ? (float)a.scale_inv[c] : 0.f;
     const bool xin = x0 < W;
-    float rows[V_ROWS + 2][4];
+    float rows[R_ROWS + 2][4];
 #pragma unroll
-    for (int k = 0; k < V_ROWS + 2; ++k) {
+    for (int k = 0; k < R_ROWS + 2; ++k) {
         const int y = yb - 1 + k;
         if (xin && y >= 0 && y < H) {
             ld4(u + (size_t)y * a.up, x0, W, vec.u, rows[k]);
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
     }
     float s = 0.f, mx = 0.f;
 #pragma unroll
-    for (int k = 0; k < V_ROWS; ++k) {
+    for (int k = 0; k < R_ROWS; ++k) {
         const int y = yb + k;
         const float* rw = rows[k + 1];
         float left = __shfl_up_sync(0xffffffffu, rw[3], 1);
@@ -157,21 +164,42 @@ __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
         bool known[4];
         ldm4(a.mask + (size_t)y * a.mp, x0, W, vec.m, known);
         float r[4];
+        // all four pixels away from the image border: one branch per row group
+        if (y > 0 && y < H - 1 && x0 > 0 && x0 + 4 < W) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                // (N + S) + (W + E) - 4 u_p by TwoSum steps (4 u_p is exact), the
+                // rounding errors summed in FP32: ~48-bit accurate before the one
+                // final rounding, as the general path below
+                float s1, e1, s2, e2, t, e3, dd, e4;
+                two_sum(rows[k][j], rows[k + 2][j], s1, e1);
+                two_sum(j > 0 ? rw[j - 1] : left, j < 3 ? rw[j + 1] : right, s2, e2);
+                two_sum(s1, s2, t, e3);
+                two_sum(t, -4.f * rw[j], dd, e4);
+                const float rv = __fadd_rn(dd, __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, e4)));
+                r[j] = known[j] ? 0.f : rv;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                // the in-image neighbour differences u_q - u_p, each split exactly
+                // by TwoSum, accumulated double-single
+                const int x = x0 + j;
+                const float uc = rw[j];
+                float hi = 0.f, lo = 0.f, d, e;
+                if (y > 0) { two_sum(rows[k][j], -uc, d, e); ds_add(hi, lo, d, e); }
+                if (y < H - 1) { two_sum(rows[k + 2][j], -uc, d, e); ds_add(hi, lo, d, e); }
+                if (x > 0) { two_sum(j > 0 ? rw[j - 1] : left, -uc, d, e); ds_add(hi, lo, d, e); }
+                if (x < W - 1) { two_sum(j < 3 ? rw[j + 1] : right, -uc, d, e); ds_add(hi, lo, d, e); }
+                r[j] = (x < W && !known[j]) ? __fadd_rn(hi, lo) : 0.f;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int x = x0 + j;
-            const float uc = rw[j];
-            const float wv = j > 0 ? rw[j - 1] : left;
-            const float ev = j < 3 ? rw[j + 1] : right;
-            float hi = 0.f, lo = 0.f, d, e;
-            if (y > 0) { two_sum(rows[k][j], -uc, d, e); ds_add(hi, lo, d, e); }
-            if (y < H - 1) { two_sum(rows[k + 2][j], -uc, d, e); ds_add(hi, lo, d, e); }
-            if (x > 0) { two_sum(wv, -uc, d, e); ds_add(hi, lo, d, e); }
-            if (x < W - 1) { two_sum(ev, -uc, d, e); ds_add(hi, lo, d, e); }
-            r[j] = (x < W && !known[j]) ? __fadd_rn(hi, lo) : 0.f;
             s = fmaf(r[j], r[j], s);
             mx = fmaxf(mx, fabsf(r[j]));
         }
+        if (a.copy_out) st4(a.copy_out + c * a.cplane + (size_t)y * a.cp, x0, W, vec.cp, rows[k + 1]);
         if (a.g_out) {
             T* g = static_cast<T*>(a.g_out) + c * a.gplane + (size_t)y * a.gp;
             if constexpr (sizeof(T) == 4) {
@@ -206,11 +234,12 @@ __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
             tm = fmaxf(tm, sm[w]);
         }
         a.part[(size_t)c * a.nblk + blockIdx.y * gridDim.x + blockIdx.x] = make_double2(ts, (double)tm);
+        if (a.out != nullptr) {   // the partial is visible before the ticket is taken
+            __threadfence();
+            s_last = atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.y * gridDim.z - 1;
+        }
     }
     if (a.out == nullptr) return;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.y * gridDim.z - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -543,16 +572,18 @@ cudaError_t launch_convert(int H, int W, int C, const float* src, int sp, long l
 }
 
 int res64_blocks(int H, int W) {
-    const dim3 g = gridv(H, W, 1);
+    const dim3 g = grid_res(H, W, 1);
     return (int)(g.x * g.y);
 }
 
 cudaError_t launch_res64(const Res64Args& a, cudaStream_t st) {
-    const dim3 grid = gridv(a.H, a.W, a.C);
+    const dim3 grid = grid_res(a.H, a.W, a.C);
     if (a.nblk != (int)(grid.x * grid.y)) return cudaErrorInvalidValue;
     if (a.out != nullptr && a.ticket == nullptr) return cudaErrorInvalidValue;
+    if (a.sel != nullptr && a.u1 == nullptr) return cudaErrorInvalidValue;
     ResVec v;
-    v.u = vec_ok(a.u, a.up, a.uplane, 4);
+    v.u = vec_ok(a.u, a.up, a.uplane, 4) && (a.u1 == nullptr || vec_ok(a.u1, a.up, a.uplane, 4));
+    v.cp = a.copy_out != nullptr && vec_ok(a.copy_out, a.cp, a.cplane, 4);
     v.m = vec_ok(a.mask, a.mp, 0, 1);
     v.g = a.g_out != nullptr && a.gst == Store::F32 && vec_ok(a.g_out, a.gp, a.gplane, 4);
     const dim3 block(V_TX, V_TY);

@@ -42,11 +42,14 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Whether this block is the last of the grid to finish (ticket in *ticket).
+// Called after thread 0 wrote the block's partial: its fence orders that write
+// before the ticket.
 __device__ __forceinline__ bool last_block(int* ticket, int* s_last) {
-    __threadfence();
-    __syncthreads();
     const int t = threadIdx.y * CG_TX + threadIdx.x;
-    if (t == 0) *s_last = atomicAdd(ticket, 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
+    if (t == 0) {
+        __threadfence();
+        *s_last = atomicAdd(ticket, 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
+    }
     __syncthreads();
     return *s_last != 0;
 }

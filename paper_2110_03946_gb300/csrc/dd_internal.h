@@ -147,6 +147,10 @@ struct Res64Args {
     // optional, fused: the last block writes out[c] = {sum r^2, max |r|} (and
     // sqrt_out[c] = sqrt(sum) if given); ticket: a zero device counter, left zero
     double2* out; double* sqrt_out; unsigned int* ticket;
+    // optional: the iterate is (sel[0] ? u1 : u), chosen on the device (u1 has
+    // u's pitch and plane), and is also copied to copy_out (pitch cp, plane cplane)
+    const float* u1; const int* sel;
+    float* copy_out; int cp; long long cplane;
 };
 int res64_blocks(int H, int W);
 cudaError_t launch_res64(const Res64Args& a, cudaStream_t st);

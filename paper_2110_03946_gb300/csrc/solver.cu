@@ -627,16 +627,19 @@ int cascade(dd_inpaint* h, cudaStream_t st, bool capture) {
     return DD_OK;
 }
 
-// Residual norms of a dense FP32 image u (pitch W) at level 0 into h_res[0..C).
-int residual_of(dd_inpaint* h, const float* u, int up, long long uplane, cudaStream_t st) {
+// The fine level's result (the buffer lv[0].state_d names) copied to the
+// dense output u_out by the residual pass, which also forms its FP64-accurate
+// residual norms into h_res[0..C) (read back on st).
+int output_and_residual(dd_inpaint* h, float* u_out, cudaStream_t st) {
     Level& L = h->lv[0];
     dd::Res64Args a{};
     a.H = L.H; a.W = L.W; a.C = h->C;
-    a.u = u; a.up = up; a.uplane = uplane;
+    a.u = L.u[0]; a.u1 = L.u[1]; a.sel = L.state_d; a.up = L.P; a.uplane = L.plane();
     a.mask = L.mask; a.mp = L.W;
     a.g_out = nullptr; a.gst = Store::F32;
     a.part = h->res_part; a.nblk = h->res_nblk;
     a.out = h->res_out; a.ticket = h->res_ticket;
+    a.copy_out = u_out; a.cp = L.W; a.cplane = (long long)L.H * L.W;
     DD_LAUNCH(h, dd::launch_res64(a, st));
     DD_CK(cudaMemcpyAsync(h->h_res, h->res_out, sizeof(double2) * h->C, cudaMemcpyDeviceToHost, st));
     return DD_OK;
@@ -688,14 +691,11 @@ int fp32_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool 
         h->cur = 0;
     }
     h->warm = false;
-    const long long dense_plane = (long long)F.H * F.W;
     // a device loop runs to the sweep limit; launches stop at the first chunk
     const bool timed = h->prm.timing != 0 && !capture;
     const int n1 = loop_mode(h, timed) ? h->prm.max_sweeps : first_chunk(h);
     DD_TRY(enqueue_level(h, F, n1, tol, st, timed, capture));
-    DD_LAUNCH(h, dd::launch_copy2d_sel(F.H, F.W, h->C, F.u[0], F.u[1], F.state_d, F.P, F.plane(), u_out, F.W,
-                                       dense_plane, st));
-    DD_TRY(residual_of(h, u_out, F.W, dense_plane, st));
+    DD_TRY(output_and_residual(h, u_out, st));
     DD_CK(cudaMemcpyAsync(h->h_state, F.state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     for (int l = 1; l < nl; ++l)
         DD_CK(cudaMemcpyAsync(h->h_state + 4 * l, h->lv[l].state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
