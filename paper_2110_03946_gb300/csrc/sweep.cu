@@ -418,7 +418,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             }
         }
         for (int kk = 0; kk < kcg; ++kk) {
-            if (!(rr > 0.f)) break;
+            if (!(rr > 1e-30f)) break;   // converged locally (and keeps the quotients below finite)
             float pW[PY], pE[PY];
 #pragma unroll
             for (int i = 0; i < PY; ++i) {
@@ -459,8 +459,10 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                     if (i & 1) pqb = fma2(p2[i][j], q, pqb); else pqa = fma2(p2[i][j], q, pqa);
                 }
             const float pq = -tile_sum<CF>((pqa.x + pqa.y) + (pqb.x + pqb.y), red3[kk & 1][0], wt, lane);
-            if (!(pq > 0.f)) break;
-            const float alpha = rr / pq;
+            if (!(pq > 1e-30f)) break;
+            // approximate quotients (2 ulp): the divisors lie in [1e-30, 2^126) here,
+            // where __fdividef is finite, and they shorten the step's dependency chain
+            const float alpha = __fdividef(rr, pq);
             const float2 a2 = make_float2(alpha, alpha);
             float2 rra = make_float2(0.f, 0.f), rrb = make_float2(0.f, 0.f);
 #pragma unroll
@@ -486,7 +488,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                     }
             }
             const float rr_new = tile_sum<CF>((rra.x + rra.y) + (rrb.x + rrb.y), red3[kk & 1][1], wt, lane);
-            const float beta = rr_new / rr;
+            const float beta = __fdividef(rr_new, rr);
             const float2 b2 = make_float2(beta, beta);
 #pragma unroll
             for (int i = 0; i < PY; ++i)
