@@ -38,6 +38,11 @@ namespace dd {
 
 namespace {
 
+// Residual contraction per ORAS sweep assumed before a level has two full
+// sweeps of history (probe prediction only: it decides whether the next launch
+// probes or sweeps, never whether the level has converged).
+constexpr double kFirstContraction = 0.3;
+
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls (a TMA copy takes ~1 us)
 
@@ -571,11 +576,15 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                 flag[1] = sweep_index;
             } else if (!probe) {
                 // the output of this sweep becomes the current iterate; probe it
-                // next if the last residual ratio predicts it meets tol
+                // next if the residual ratio of this level's last two full sweeps
+                // (before its second full sweep: an assumed contraction of
+                // kFirstContraction) predicts that it meets tol
                 const double prev_worst = sp.norms2[2 * a.C];
+                const bool history = state[1] > 0 && prev_worst > 0.0;
+                const double pred = history ? worst * (worst / prev_worst) : worst * kFirstContraction;
                 state[0] = cur ^ 1;
                 state[1] += 1;
-                state[2] = (tol > 0.0 && prev_worst > 0.0 && worst * (worst / prev_worst) <= tol) ? 1 : 0;
+                state[2] = (tol > 0.0 && pred <= tol) ? 1 : 0;
             } else {
                 state[2] = 0;   // the probe failed: sweep the same iterate in full
             }
