@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP16-storage measurement")
     ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving measurements")
+    ap.add_argument("--inflight", type=int, default=3, help="frames in flight in the timed region and the e2e leg (FP32)")
     ap.add_argument("--device-loop", type=int, default=1, choices=[0, 1],
                     help="1: level iterations in CUDA graph loops (default); 0: plain launches, which ncu can "
                          "list kernel by kernel")
@@ -432,12 +433,13 @@ def run_ours(args):
     prm_timed = dict(prm, timing=1)
     stream = torch.cuda.current_stream(dev)
 
-    # Frames resident in HBM.  With FP32 storage two solver handles on two
-    # streams alternate (asynchronous C ABI): while one frame's solve waits for
-    # its read-back, the other keeps the GPU busy.  Per-frame latency is timed
-    # with CUDA events on each frame's own stream.
+    # Frames resident in HBM.  With FP32 storage --inflight solver handles on as
+    # many streams take turns (asynchronous C ABI): while one frame's solve waits
+    # for its read-back, or runs a coarse level too small to fill the GPU, the
+    # others keep the SMs busy.  Per-frame latency is timed with CUDA events on
+    # each frame's own stream.
     pipelined_main = args.precision == "fp32"
-    nmain = 2 if pipelined_main else 1
+    nmain = max(1, args.inflight) if pipelined_main else 1
     ips = [Inpainter(dmask[0], dvals[0], device=dev, **prm) for _ in range(nmain)]
     m_streams = [torch.cuda.Stream(dev) for _ in range(nmain)] if pipelined_main else [stream]
     outs_main = [torch.empty((C, H, W), dtype=torch.float32, device=dev) for _ in range(nmain)]
@@ -518,9 +520,9 @@ def run_ours(args):
     for ip_ in ips:
         ip_.close()
 
-    # The sweep kernel timed alone: with two frames in flight the timed region's
-    # sweeps share the SMs, which stretches each launch; the roofline uses
-    # single-stream solves of the same frames right after the timed region.
+    # The sweep kernel timed alone: with several frames in flight the timed
+    # region's sweeps share the SMs, which stretches each launch; the roofline
+    # uses single-stream solves of the same frames right after the timed region.
     iso_ms, iso_n = 0.0, 0
     with Inpainter(dmask[0], dvals[0], device=dev, **prm_timed) as ipi:
         for i in range(6):
@@ -535,14 +537,14 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers -------------------
     # Every step copies its mask and values from pinned host memory to the
     # device and its result back to pinned host memory inside the timed region.
-    # Two handles on two streams alternate (asynchronous C ABI), so the copies
-    # of one frame overlap the solve of the next.
+    # --inflight handles on as many streams take turns (asynchronous C ABI), so
+    # the copies of one frame overlap the solves of the others.
     pm = [torch.as_tensor(m).pin_memory() for _, m in frames]
     pv = [torch.as_tensor(f).pin_memory() for f, _ in frames]
     from paper_2110_03946_gb300.inpaint import make_params
     p = make_params(precision=args.precision, inputs_on_device=0, **tuned)
     pipelined = args.precision == "fp32"
-    nh = 2 if pipelined else 1
+    nh = max(1, args.inflight) if pipelined else 1
     hs2, e_streams, douts, houts, evs = [], [], [], [], []
     for k in range(nh):
         rc, hk = B.dd_inpaint_create(H, W, C, pm[0].data_ptr(), pv[0].data_ptr(), p)
