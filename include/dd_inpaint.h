@@ -60,7 +60,8 @@ extern "C" {
 
 /* multilevel modes */
 #define DD_ML_CASCADE     0  /* coarse-to-fine initialisation (Sec. 4) */
-#define DD_ML_CORRECTION  1  /* two-level: coarse residual correction after each fine sweep */
+#define DD_ML_CORRECTION  1  /* cascade initialisation, then a coarse-grid correction of the residual
+                                after each fine sweep (FP32, ORAS, levels >= 2) */
 
 /* precision modes (storage of the Schwarz iterate; arithmetic is FP32) */
 #define DD_PREC_FP32      0  /* plain FP32 ORAS on u, FP64-verified stop test */
@@ -77,7 +78,8 @@ typedef struct dd_params {
     int    local_cg_iters;   /* CG steps per local problem and sweep, >= 1 (default 16) */
     int    levels;           /* resolution levels, 1..8 (default 3, Sec. 4) */
     int    ml_mode;          /* DD_ML_CASCADE (default) or DD_ML_CORRECTION */
-    int    coarse_factor;    /* DD_ML_CORRECTION only: 2^(levels-1) is used; kept for ABI */
+    int    coarse_factor;    /* kept for ABI; DD_ML_CORRECTION corrects on the coarsest level,
+                                2^(levels-1) times coarser than the image */
     float  robin_p;          /* Robin interface weight p > 0 (1 = RAS); <= 0 selects the default */
     int    precision;        /* DD_PREC_* (default DD_PREC_FP32_REF) */
     int    max_sweeps;       /* fine-level sweep limit per solve (default 400) */
@@ -91,6 +93,8 @@ typedef struct dd_params {
                                 block 32: 1, 2 or 4; block 64: 4 or 8 */
     int    solver;           /* DD_SOLVER_ORAS (default) or DD_SOLVER_CG (needs DD_PREC_FP32);
                                 with CG, max_sweeps / coarse_sweeps count CG iterations */
+    int    correction_sweeps; /* DD_ML_CORRECTION: ORAS sweeps on the coarse correction equation
+                                after each fine sweep, from zero (default 2) */
     int    device_loop;      /* 1 (default): a level's sweeps (or CG iterations) repeat inside a
                                 CUDA graph loop on the device until its stop test or sweep limit,
                                 no launch after the stop; 0: launched in fixed chunks whose launches
@@ -258,9 +262,10 @@ int dd_inpaint_get_iterate(dd_handle h, float *u_out, void *stream);
 /*
  * Apply n ORAS sweeps (Sec. 3, u^{n+1} = u^n + sum_i R_i^T D_i v_i^n) to the
  * finest-level iterate, in FP32 storage, with the handle's block, overlap,
- * Robin weight and CG step count.  If rnorm_out is not NULL it receives C
- * values: ||b - A u^n||_2 of the INPUT iterate of the last sweep (FP32 terms,
- * FP64 accumulation); the call then synchronises stream.
+ * Robin weight and CG step count; with DD_ML_CORRECTION each sweep is followed
+ * by the coarse-grid correction (one pass of that mode).  If rnorm_out is not
+ * NULL it receives C values: ||b - A u^n||_2 of the INPUT iterate of the last
+ * sweep (FP32 terms, FP64 accumulation); the call then synchronises stream.
  * Errors: DD_EINVAL, DD_ECUDA.
  */
 int dd_inpaint_sweep(dd_handle h, int n, double *rnorm_out, void *stream);

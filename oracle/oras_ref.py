@@ -49,7 +49,7 @@ from . import inpaint_ref as ref
 __all__ = [
     "axis_blocks", "block_count", "owner_of", "subdomains", "local_matrix",
     "cg_fixed", "oras_sweep", "oras_solve", "restrict_level", "prolong_bilinear",
-    "robin_default", "build_hierarchy", "cascade_solve",
+    "robin_default", "build_hierarchy", "cascade_solve", "restrict_sum", "correction_pass",
 ]
 
 
@@ -288,3 +288,49 @@ def cascade_solve(f, mask, levels, b, o, p_robin, k, tol, max_sweeps, coarse_tol
         u, n = oras_solve(fl, ml, b, o, p_robin, k, t, max_sweeps, u0=u)
         counts.append(n)
     return u, counts
+
+
+# ------------------------------------------ coarse-grid correction (two-level)
+def restrict_sum(r):
+    """Sum of a fine grid over each 2x2 block {2Y, 2Y+1} x {2X, 2X+1} (the parts
+    inside the image); ceil(n/2) coarse pixels per axis.  With the h = 1
+    stencil the coarse operator represents the Laplacian times 4, so the sum
+    (4 x the block mean) is the restricted right-hand side."""
+    r3 = np.asarray(r, dtype=np.float64)
+    two_d = r3.ndim == 2
+    r3 = r3[None] if two_d else r3
+    C, H, W = r3.shape
+    out = np.zeros((C, (H + 1) // 2, (W + 1) // 2))
+    for dy in (0, 1):
+        for dx in (0, 1):
+            part = r3[:, dy::2, dx::2]
+            out[:, :part.shape[1], :part.shape[2]] += part
+    return out[0] if two_d else out
+
+
+def correction_pass(u, f, mask, hier, b, o, p_robin, k, m):
+    """One fine ORAS sweep followed by a coarse-grid correction on the coarsest
+    level of hier (from build_hierarchy): the fine residual r = b - A u (zero
+    on known pixels) is summed down to that level, the correction equation
+    A_c e = R r (e = 0 on coarse-known pixels) gets m ORAS sweeps from e = 0,
+    and e, prolonged bilinearly level by level, is added on unknown fine
+    pixels.  Returns (u_next, ||r^n|| of the input per channel)."""
+    mask = np.asarray(mask)
+    u1, rn = oras_sweep(u, f, mask, b, o, p_robin, k)
+    two_d = np.asarray(u1).ndim == 2
+    u3 = u1[None] if two_d else u1
+    f3 = np.asarray(f, dtype=np.float64)
+    f3 = f3[None] if f3.ndim == 2 else f3
+    r = ref.residual(u3, f3, mask)
+    for _ in range(len(hier) - 1):
+        r = restrict_sum(r)
+    _, mask_c = hier[-1]
+    e = np.zeros_like(r)
+    for _ in range(m):
+        e, _ = oras_sweep(e, np.zeros_like(r), mask_c, b, o, p_robin, k, g=r)
+    for lvl in range(len(hier) - 2, -1, -1):
+        H, W = np.asarray(hier[lvl][1]).shape
+        e = prolong_bilinear(e, H, W)
+    out = u3 + (mask == 0) * e
+    return (out[0] if two_d else out), rn
+

@@ -39,7 +39,8 @@ class dd_params(ctypes.Structure):
         ("robin_p", ctypes.c_float), ("precision", ctypes.c_int), ("max_sweeps", ctypes.c_int),
         ("inputs_on_device", ctypes.c_int), ("coarse_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
         ("max_corrections", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("timing", ctypes.c_int),
-        ("tile_warps", ctypes.c_int), ("solver", ctypes.c_int), ("device_loop", ctypes.c_int),
+        ("tile_warps", ctypes.c_int), ("solver", ctypes.c_int), ("correction_sweeps", ctypes.c_int),
+        ("device_loop", ctypes.c_int),
     ]
 
 

@@ -134,6 +134,7 @@ dim3 grid_res(int H, int W, int C) { return dim3((W + V_COLS - 1) / V_COLS, (H +
 
 template <typename T>
 __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
+    if (a.skip != nullptr && *a.skip != 0) return;   // uniform: no partial, no ticket
     const int c = blockIdx.z;
     const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
     const int yb = (blockIdx.y * V_TY + threadIdx.y) * R_ROWS;
@@ -443,6 +444,91 @@ __global__ void __launch_bounds__(V_TPB) restrict_kernel(int H, int W, int Hc, i
     }
 }
 
+// ---- two-level coarse correction (DD_ML_CORRECTION) -------------------------------------
+// Coarse right-hand side: g_c(X, Y) = sum of the fine values over the 2x2
+// block {2Y, 2Y+1} x {2X, 2X+1} inside the image.  The h = 1 stencil on a grid
+// twice as coarse represents the Laplacian times 4, so summing (4 x the mean)
+// gives the coarse equation of the restricted residual.  No-op if *skip != 0.
+__global__ void __launch_bounds__(V_TPB) restrict_sum_kernel(int H, int W, int Hc, int Wc, const float* __restrict__ src,
+                                                             int sp, long long splane, float* __restrict__ dst, int dp,
+                                                             long long dplane, const int* __restrict__ skip, CopyVec vec) {
+    if (skip != nullptr && *skip != 0) return;
+    const int c = blockIdx.z;
+    const int X0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int Yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    if (X0 >= Wc) return;
+    const float* __restrict__ s = src + c * splane;
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        const int Y = Yb + k;
+        if (Y >= Hc) break;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int y = 2 * Y + dy;
+            if (y >= H) break;
+            float a4[4], b4[4];
+            ld4(s + (size_t)y * sp, 2 * X0, W, vec.src, a4);
+            ld4(s + (size_t)y * sp, 2 * X0 + 4, W, vec.src, b4);
+            acc[0] += a4[0] + a4[1];
+            acc[1] += a4[2] + a4[3];
+            acc[2] += b4[0] + b4[1];
+            acc[3] += b4[2] + b4[3];
+        }
+        st4(dst + c * dplane + (size_t)Y * dp, X0, Wc, vec.dst, acc);
+    }
+}
+
+// u (the buffer sel_u[0] names) += cell-centred bilinear prolongation of the
+// coarse correction (the buffer sel_c[0] names; sel_c may be null), on unknown
+// fine pixels.  No-op if *skip != 0.
+__global__ void __launch_bounds__(V_TPB) prolong_add_kernel(int Hc, int Wc, int H, int W, const float* __restrict__ ec0,
+                                                            const float* __restrict__ ec1, const int* __restrict__ sel_c,
+                                                            int ecp, long long ecplane, const uint8_t* __restrict__ mask,
+                                                            int mp, float* __restrict__ u0, float* __restrict__ u1,
+                                                            const int* __restrict__ sel_u, int up, long long uplane,
+                                                            const int* __restrict__ skip, CopyVec vec) {
+    if (skip != nullptr && *skip != 0) return;
+    const int c = blockIdx.z;
+    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    if (x0 >= W) return;
+    const float* __restrict__ p = ((sel_c != nullptr && sel_c[0]) ? ec1 : ec0) + c * ecplane;
+    float* __restrict__ u = (sel_u[0] ? u1 : u0) + c * uplane;
+    int xa[4], xb[4];
+    float wx[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float tx = fminf(fmaxf((x0 + j - 0.5f) * 0.5f, 0.f), (float)(Wc - 1));
+        xa[j] = (int)floorf(tx);
+        xb[j] = min(xa[j] + 1, Wc - 1);
+        wx[j] = tx - (float)xa[j];
+    }
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        const int y = yb + k;
+        if (y >= H) break;
+        const float ty = fminf(fmaxf((y - 0.5f) * 0.5f, 0.f), (float)(Hc - 1));
+        const int ya = (int)floorf(ty), yb1 = min(ya + 1, Hc - 1);
+        const float wy = ty - (float)ya;
+        const float* __restrict__ ra = p + (size_t)ya * ecp;
+        const float* __restrict__ rb = p + (size_t)yb1 * ecp;
+        bool m[4];
+        ldm4(mask + (size_t)y * mp, x0, W, vec.m, m);
+        float v[4];
+        ld4(u + (size_t)y * up, x0, W, vec.dst, v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!m[j] && x0 + j < W) {
+                const float top = ra[xa[j]] * (1.f - wx[j]) + ra[xb[j]] * wx[j];
+                const float bot = rb[xa[j]] * (1.f - wx[j]) + rb[xb[j]] * wx[j];
+                v[j] += top * (1.f - wy) + bot * wy;
+            }
+        }
+        st4(u + (size_t)y * up, x0, W, vec.dst, v);
+    }
+}
+
 constexpr int RED_TPB = 512;
 
 __global__ void __launch_bounds__(RED_TPB) reduce_part_kernel(const double2* __restrict__ part, int nblk,
@@ -502,10 +588,11 @@ __global__ void resolve_kernel(const int* __restrict__ flag, const int* __restri
 }
 
 __global__ void reset_sweep_state_kernel(int* __restrict__ state, int* __restrict__ flag, int cur,
-                                         double* __restrict__ tol_d, double tol) {
+                                         double* __restrict__ tol_d, double tol, const int* __restrict__ skip_if) {
+    const bool skip = skip_if != nullptr && *skip_if != 0;
     if (threadIdx.x < 4) {
         state[threadIdx.x] = threadIdx.x == 0 ? cur : 0;
-        flag[threadIdx.x] = 0;
+        flag[threadIdx.x] = (threadIdx.x == 0 && skip) ? 4 : 0;   // 4: sequence skipped
     }
     if (threadIdx.x == 0) *tol_d = tol;
 }
@@ -649,8 +736,28 @@ cudaError_t launch_resolve(const int* flag, const int* sweep_state, const int* c
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, double* tol_d, double tol, cudaStream_t st) {
-    reset_sweep_state_kernel<<<1, 32, 0, st>>>(state, flag, cur, tol_d, tol);
+cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, double* tol_d, double tol, cudaStream_t st,
+                                     const int* skip_if) {
+    reset_sweep_state_kernel<<<1, 32, 0, st>>>(state, flag, cur, tol_d, tol, skip_if);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_sum(int H, int W, int C, const float* src, int sp, long long splane, float* dst, int dp,
+                                long long dplane, const int* skip, cudaStream_t st) {
+    const int Hc = (H + 1) / 2, Wc = (W + 1) / 2;
+    const CopyVec v{vec_ok(src, sp, splane, 4), vec_ok(dst, dp, dplane, 4), false};
+    restrict_sum_kernel<<<gridv(Hc, Wc, C), dim3(V_TX, V_TY), 0, st>>>(H, W, Hc, Wc, src, sp, splane, dst, dp, dplane,
+                                                                       skip, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(int Hc, int Wc, int H, int W, int C, const float* ec0, const float* ec1,
+                               const int* sel_c, int ecp, long long ecplane, const uint8_t* mask, int mp, float* u0,
+                               float* u1, const int* sel_u, int up, long long uplane, const int* skip,
+                               cudaStream_t st) {
+    const CopyVec v{false, vec_ok(u0, up, uplane, 4) && vec_ok(u1, up, uplane, 4), vec_ok(mask, mp, 0, 1)};
+    prolong_add_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(Hc, Wc, H, W, ec0, ec1, sel_c, ecp, ecplane, mask,
+                                                                    mp, u0, u1, sel_u, up, uplane, skip, v);
     return cudaGetLastError();
 }
 

@@ -107,8 +107,23 @@ cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, co
 cudaError_t prepare_sweep(Store s, const TileGeom& g, bool has_g);
 
 // state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..3] = 0; *tol_d = tol
-// (the stop tolerance the following sweeps or CG iterations read).
-cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, double* tol_d, double tol, cudaStream_t st);
+// (the stop tolerance the following sweeps or CG iterations read).  With
+// skip_if and *skip_if != 0, flag[0] = 4 instead: the following sweeps are
+// no-ops.
+cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, double* tol_d, double tol, cudaStream_t st,
+                                     const int* skip_if = nullptr);
+
+// Two-level coarse correction (DD_ML_CORRECTION), each a no-op if *skip != 0
+// (skip may be null):
+// dst (ceil(H/2) x ceil(W/2)) = sum of src over each 2x2 block inside the image.
+cudaError_t launch_restrict_sum(int H, int W, int C, const float* src, int sp, long long splane, float* dst, int dp,
+                                long long dplane, const int* skip, cudaStream_t st);
+// (sel_u[0] ? u1 : u0) += bilinear prolongation of (sel_c && sel_c[0] ? ec1 : ec0)
+// on pixels with mask == 0.
+cudaError_t launch_prolong_add(int Hc, int Wc, int H, int W, int C, const float* ec0, const float* ec1,
+                               const int* sel_c, int ecp, long long ecplane, const uint8_t* mask, int mp, float* u0,
+                               float* u1, const int* sel_u, int up, long long uplane, const int* skip,
+                               cudaStream_t st);
 
 // Loop control at the end of each pass of a graph WHILE loop (one thread):
 // ctl[0] counts the passes; the loop's condition is cleared when flag[0] != 0
@@ -151,6 +166,7 @@ struct Res64Args {
     // u's pitch and plane), and is also copied to copy_out (pitch cp, plane cplane)
     const float* u1; const int* sel;
     float* copy_out; int cp; long long cplane;
+    const int* skip;   // optional: the pass is a no-op if *skip != 0
 };
 int res64_blocks(int H, int W);
 cudaError_t launch_res64(const Res64Args& a, cudaStream_t st);

@@ -106,6 +106,10 @@ struct Level {
     double* cg_part = nullptr;   // C x cg_blocks
     double* cg_scal = nullptr;   // 3C
     LoopGraph loop;              // device loop of this level's iteration (params.device_loop)
+    // DD_ML_CORRECTION (levels >= 1): restricted residual / prolonged correction
+    // scratch; on the coarsest level also the source of the correction solve
+    float* corr_g = nullptr;     // C x H x P
+    CUtensorMap map_cg;          // TMA descriptor of corr_g (coarsest level)
     bool loop_pending = false;   // a loop ran since the launch count was last updated
     long long plane() const { return (long long)H * P; }
 };
@@ -138,6 +142,12 @@ struct dd_inpaint {
     int* sstate_d = nullptr;        // sweep state: current buffer, full sweeps, probe request, launches
     int* ctl_d = nullptr;           // device-loop pass counter (4 ints)
     double* tol_d = nullptr;        // stop tolerance of the running level (set by each reset)
+    // DD_ML_CORRECTION: fine residual, and the stop state of the coarse correction solve
+    float* corr_r = nullptr;        // C x H x P (level 0)
+    int* flag_c = nullptr;          // 4 ints
+    int* state_c = nullptr;         // 4 ints
+    double* norms2_c = nullptr;     // 2C + 2
+    double* tol_c = nullptr;        // 1
     cudaStream_t cap_stream = nullptr;   // private stream on which loop bodies are captured
     // pinned host mirrors
     double2* h_res = nullptr;
@@ -212,7 +222,12 @@ int validate(int H, int W, int C, const dd_params& p) {
     if (p.device_loop != 0 && p.device_loop != 1) { set_error("device_loop must be 0 or 1"); return DD_EINVAL; }
     if (p.local_cg_iters < 1 || p.local_cg_iters > 4096) { set_error("local_cg_iters out of range"); return DD_EINVAL; }
     if (p.levels < 1 || p.levels > DD_MAX_LEVELS) { set_error("levels must be 1..8"); return DD_EINVAL; }
-    if (p.ml_mode != DD_ML_CASCADE) { set_error("ml_mode: only DD_ML_CASCADE is implemented"); return DD_EINVAL; }
+    if (p.ml_mode != DD_ML_CASCADE && p.ml_mode != DD_ML_CORRECTION) { set_error("bad ml_mode"); return DD_EINVAL; }
+    if (p.ml_mode == DD_ML_CORRECTION &&
+        (p.precision != DD_PREC_FP32 || p.solver != DD_SOLVER_ORAS || p.levels < 2 || p.correction_sweeps < 1)) {
+        set_error("DD_ML_CORRECTION needs DD_PREC_FP32, DD_SOLVER_ORAS, levels >= 2 and correction_sweeps >= 1");
+        return DD_EINVAL;
+    }
     if (p.precision < DD_PREC_FP32 || p.precision > DD_PREC_BF16_REF) { set_error("bad precision"); return DD_EINVAL; }
     if (p.max_sweeps < 0 || p.coarse_sweeps < 0 || p.max_corrections < 0) { set_error("negative limit"); return DD_EINVAL; }
     if (!(p.coarse_tol > 0.0) || !(p.inner_tol > 0.0) || !(p.inner_tol < 1.0)) { set_error("bad tolerance"); return DD_EINVAL; }
@@ -408,7 +423,19 @@ int write_scaled_residual(dd_inpaint* h, cudaStream_t st) {
 bool loop_mode(const dd_inpaint* h, bool timed) { return h->prm.device_loop != 0 && !timed; }
 
 // Kernels per pass of a device loop: the sweep (or CG's two) and the loop control.
-int pass_kernels(const dd_inpaint* h) { return h->prm.solver == DD_SOLVER_CG ? 3 : 2; }
+// Whether fine passes end with the coarse-grid correction.
+bool corrects(const dd_inpaint* h) { return h->prm.ml_mode == DD_ML_CORRECTION && h->lv.size() >= 2; }
+
+// Kernels of the coarse-grid correction after one fine sweep.
+int correction_kernels(const dd_inpaint* h) {
+    const int nl = (int)h->lv.size();
+    return 1 + (nl - 1) + 1 + h->prm.correction_sweeps + (nl - 2) + 1;
+}
+
+int pass_kernels_of(const dd_inpaint* h, const Level& L) {
+    if (h->prm.solver == DD_SOLVER_CG) return 3;
+    return 2 + ((&L == &h->lv[0] && corrects(h)) ? correction_kernels(h) : 0);
+}
 
 dd::CGArgs cg_args(const dd_inpaint* h, const Level& L) {
     dd::CGArgs a{};
@@ -425,6 +452,67 @@ dd::CGArgs cg_args(const dd_inpaint* h, const Level& L) {
 
 // One pass of level L's iteration: an ORAS sweep (or probe) from the buffer
 // the device state names, or one CG iteration.
+// Coarse-grid correction of the fine iterate (the buffer sstate_d[0] names),
+// all on st, each step a no-op once the fine stop flag is set:
+//   r   = b - A u on the fine level (FP64-accurate residual pass),
+//   g_c = r summed over 2x2 blocks down to the coarsest level (the h = 1
+//         stencil there carries the factor 4 per level),
+//   e_c = correction_sweeps ORAS sweeps on A_c e_c = g_c from e_c = 0, with
+//         e_c = 0 on coarse-known pixels,
+//   u  += e_c prolonged bilinearly level by level, on unknown fine pixels.
+int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
+    const int nl = (int)h->lv.size();
+    Level& F = h->lv[0];
+    Level& Lc = h->lv[nl - 1];
+    const int* skip = h->flag_d;
+    dd::Res64Args a{};
+    a.H = F.H; a.W = F.W; a.C = h->C;
+    a.u = F.u[0]; a.u1 = F.u[1]; a.sel = h->sstate_d; a.up = F.P; a.uplane = F.plane();
+    a.mask = F.mask; a.mp = F.W;
+    a.g_out = h->corr_r; a.gst = Store::F32; a.gp = F.P; a.gplane = F.plane();
+    a.scale_inv = h->ones_d;
+    a.part = h->res_part; a.nblk = h->res_nblk;
+    a.skip = skip;
+    DD_CK(dd::launch_res64(a, st));
+    const float* src = h->corr_r;
+    int sp = F.P;
+    long long splane = F.plane();
+    for (int l = 1; l < nl; ++l) {
+        Level& L = h->lv[l];
+        const Level& Lf = h->lv[l - 1];
+        DD_CK(dd::launch_restrict_sum(Lf.H, Lf.W, h->C, src, sp, splane, L.corr_g, L.P, L.plane(), skip, st));
+        src = L.corr_g;
+        sp = L.P;
+        splane = L.plane();
+    }
+    const size_t cbytes = sizeof(float) * (size_t)h->C * Lc.plane();
+    DD_CK(cudaMemsetAsync(Lc.u[0], 0, cbytes, st));
+    DD_CK(cudaMemsetAsync(Lc.u[1], 0, cbytes, st));
+    DD_CK(dd::launch_reset_sweep_state(h->state_c, h->flag_c, 0, h->tol_c, -1.0, st, skip));
+    const dd::SweepPair pair{{&Lc.map_u[0], &Lc.map_u[1]}, {Lc.u[0], Lc.u[1]}};
+    const dd::SweepStop stop{Lc.partial, dd::kSweepSlots, h->norms2_c, Lc.ref_d, h->tol_c, 0.0, h->flag_c, h->state_c, 0};
+    for (int i = 0; i < h->prm.correction_sweeps; ++i)
+        DD_CK(dd::launch_sweep(Store::F32, Lc.geom, h->C, Lc.plane(), pair, &Lc.map_cg, Lc.tmask, stop,
+                               h->prm.robin_p, h->prm.local_cg_iters, st));
+    const float* e0 = Lc.u[0];
+    const float* e1 = Lc.u[1];
+    const int* sel = h->state_c;
+    int eH = Lc.H, eW = Lc.W, ep = Lc.P;
+    long long eplane = Lc.plane();
+    for (int l = nl - 2; l >= 1; --l) {
+        Level& L = h->lv[l];
+        DD_CK(dd::launch_prolong_sel(eH, eW, L.H, L.W, h->C, e0, e1, sel, ep, eplane, nullptr, L.W, nullptr, L.P,
+                                     L.plane(), L.corr_g, L.P, L.plane(), st));
+        e0 = e1 = L.corr_g;
+        sel = nullptr;
+        eH = L.H; eW = L.W; ep = L.P;
+        eplane = L.plane();
+    }
+    DD_CK(dd::launch_prolong_add(eH, eW, F.H, F.W, h->C, e0, e1, sel, ep, eplane, F.mask, F.W, F.u[0], F.u[1],
+                                 h->sstate_d, F.P, F.plane(), skip, st));
+    return DD_OK;
+}
+
 int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st) {
     if (h->prm.solver == DD_SOLVER_CG) {
         DD_CK(dd::launch_cg_iteration(cg_args(h, L), st));
@@ -434,6 +522,7 @@ int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st) {
     const dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, h->tol_d, 0.0, h->flag_d, h->sstate_d, 0};
     DD_CK(dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), pair, nullptr, L.tmask, stop, h->prm.robin_p,
                            h->prm.local_cg_iters, st));
+    if (&L == &h->lv[0] && corrects(h)) DD_TRY(enqueue_correction(h, st));
     return DD_OK;
 }
 
@@ -540,7 +629,7 @@ void count_loop_launches(dd_inpaint* h) {
     for (size_t l = 0; l < h->lv.size() && l < DD_MAX_LEVELS; ++l) {
         if (!h->lv[l].loop_pending) continue;
         h->lv[l].loop_pending = false;
-        h->launches += (long long)h->h_state[4 * l + 3] * pass_kernels(h);
+        h->launches += (long long)h->h_state[4 * l + 3] * pass_kernels_of(h, h->lv[l]);
     }
 }
 
@@ -555,7 +644,7 @@ int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, 
     for (int i = 0; i < n; ++i) {
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
         DD_TRY(enqueue_pass(h, L, st));
-        ++h->launches;
+        h->launches += pass_kernels_of(h, L) - 1;
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
     }
     DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, nullptr, L.state_d, st));
@@ -982,6 +1071,23 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
             return fail(DD_ECUDA);
         }
     }
+    if (corrects(h)) {   // coarse-grid correction buffers
+        const size_t fb = sizeof(float) * (size_t)C * F.plane();
+        if ((rc = dalloc(h, (void**)&h->corr_r, fb)) != DD_OK) return fail(rc);
+        for (size_t l = 1; l < h->lv.size(); ++l) {
+            Level& L = h->lv[l];
+            if ((rc = dalloc(h, (void**)&L.corr_g, sizeof(float) * (size_t)C * L.plane())) != DD_OK) return fail(rc);
+        }
+        Level& Lc = h->lv.back();
+        if (dd::make_tile_map(&Lc.map_cg, Store::F32, Lc.corr_g, Lc.H, Lc.W, Lc.P, C, p.block) != cudaSuccess) {
+            set_error("cuTensorMapEncodeTiled failed");
+            return fail(DD_ECUDA);
+        }
+        if ((rc = dalloc_t(h, &h->flag_c, 4)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &h->state_c, 4)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &h->norms2_c, (size_t)2 * C + 2)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &h->tol_c, 1)) != DD_OK) return fail(rc);
+    }
     h->res_nblk = dd::res64_blocks(H, W);
     if ((rc = dalloc_t(h, &h->res_part, (size_t)C * h->res_nblk)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->res_out, (size_t)C * DD_MAX_LEVELS)) != DD_OK) return fail(rc);
@@ -1075,6 +1181,7 @@ void dd_params_default(dd_params* p) {
     p->tile_warps = 0;
     p->solver = DD_SOLVER_ORAS;
     p->device_loop = 1;
+    p->correction_sweeps = 2;
 }
 
 const char* dd_strerror(int code) {
@@ -1217,6 +1324,10 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     for (int i = 0; i < n; ++i) {   // tol < 0: every launch is a full sweep
         DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), pair, nullptr, F.tmask, stop,
                                       h->prm.robin_p, h->prm.local_cg_iters, st));
+        if (corrects(h)) {   // one pass of DD_ML_CORRECTION: the sweep, then the coarse-grid correction
+            DD_TRY(enqueue_correction(h, st));
+            h->launches += correction_kernels(h);
+        }
         h->cur = 1 - h->cur;
     }
     if (n > 0) {

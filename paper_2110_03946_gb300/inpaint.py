@@ -18,7 +18,7 @@ ML_MODES = {"cascade": B.DD_ML_CASCADE, "correction": B.DD_ML_CORRECTION}
 def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_mode=None,
                 robin_p=None, precision=None, max_sweeps=None, coarse_tol=None, inner_tol=None,
                 max_corrections=None, coarse_sweeps=None, inputs_on_device=1, timing=None,
-                tile_warps=None, solver=None, device_loop=None) -> B.dd_params:
+                tile_warps=None, solver=None, device_loop=None, correction_sweeps=None) -> B.dd_params:
     p = B.dd_params_default()
     if block is not None: p.block = int(block)
     if overlap is not None: p.overlap = int(overlap)
@@ -38,6 +38,7 @@ def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_m
     if solver is not None:
         p.solver = {"oras": B.DD_SOLVER_ORAS, "cg": B.DD_SOLVER_CG}[solver] if isinstance(solver, str) else int(solver)
     if device_loop is not None: p.device_loop = int(device_loop)
+    if correction_sweeps is not None: p.correction_sweeps = int(correction_sweeps)
     p.inputs_on_device = int(inputs_on_device)
     return p
 

@@ -131,6 +131,9 @@ SOLVE_CASES = [
     ("gray256_cg_1level", 256, 256, 1, dict(levels=1, precision="fp32", solver="cg", max_sweeps=2000)),
     ("rgb_mlcg_3level", 200, 330, 3, dict(levels=3, precision="fp32", solver="cg", max_sweeps=2000,
                                           coarse_sweeps=200, coarse_tol=1e-3)),
+    ("rgb_correction_3level", 200, 330, 3, dict(levels=3, precision="fp32", ml_mode="correction")),
+    ("gray256_correction_2level_launches", 256, 256, 1, dict(levels=2, precision="fp32", ml_mode="correction",
+                                                             correction_sweeps=3, device_loop=0)),
 ]
 
 
@@ -281,3 +284,22 @@ def test_device_loop_graph_reused_across_solves():
         d = ip.solve(1e-6).cpu().numpy()
     assert np.array_equal(a, b) and np.array_equal(a, d)
     assert max(st["rel_residual"][:2]) <= 1e-4 and torch.isfinite(c).all()
+
+
+@pytest.mark.parametrize("levels,m", [(2, 1), (3, 2)])
+def test_correction_pass_matches_oracle(levels, m):
+    """One pass of DD_ML_CORRECTION (a fine sweep, then the coarse-grid
+    correction) against the oracle's pass from the same iterate."""
+    b, o, k, p = 16, 4, 8, 0.3
+    f, msk = synth.make_frame(70, 90, 2, 0.04, "edge", 31 + levels)
+    with Inpainter(msk, f, block=b, overlap=o, local_cg_iters=k, robin_p=p, levels=levels, precision="fp32",
+                   ml_mode="correction", correction_sweeps=m) as ip:
+        u0 = ref.initial_guess(f, msk).astype(np.float32)
+        ip.set_iterate(torch.as_tensor(u0))
+        ip.sweep(1)
+        u1 = ip.get_iterate().cpu().numpy()
+    hier = oras.build_hierarchy(f, msk, levels)
+    e1, _ = oras.correction_pass(u0.astype(np.float64), f, msk, hier, b, o, p, k, m)
+    assert np.max(np.abs(u1 - e1)) <= 2e-3
+    assert np.array_equal(u1[:, msk != 0], f[:, msk != 0].astype(np.float32))
+

@@ -188,3 +188,52 @@ def test_cascade_converges_to_solution():
     u, counts = oras.cascade_solve(f, m, 3, 16, 4, 0.3, 8, 1e-8, 200, 1e-2)
     assert len(counts) == 3
     assert np.max(np.abs(u - ref.solve_direct(f, m))) <= 1e-4
+
+
+# ------------------------------------------- coarse-grid correction (two-level)
+def test_restrict_sum_hand_example():
+    """3x5 -> 2x3: each coarse pixel sums its 2x2 block inside the image."""
+    r = np.arange(15, dtype=float).reshape(3, 5)
+    exp = np.array([[0 + 1 + 5 + 6, 2 + 3 + 7 + 8, 4 + 9],
+                    [10 + 11, 12 + 13, 14]], dtype=float)
+    assert np.array_equal(oras.restrict_sum(r), exp)
+
+
+@pytest.mark.parametrize("H,W", [(8, 8), (7, 9), (1, 5), (5, 1)])
+def test_restrict_sum_conserves_total(rng, H, W):
+    r = rng.normal(size=(2, H, W))
+    rc = oras.restrict_sum(r)
+    assert rc.shape == (2, (H + 1) // 2, (W + 1) // 2)
+    assert np.allclose(rc.sum(axis=(1, 2)), r.sum(axis=(1, 2)), rtol=0, atol=1e-12)
+
+
+def test_correction_pass_keeps_the_solution(rng):
+    """The exact solution has r = 0, so the coarse correction adds nothing and
+    the sweep leaves it unchanged: it is a fixed point of the corrected pass."""
+    f, m = _case(rng, 36, 44, 0.06)
+    hier = oras.build_hierarchy(f, m, 3)
+    us = ref.solve_direct(f, m)
+    u1, _ = oras.correction_pass(us, f, m, hier, 12, 3, 0.3, 8, 2)
+    assert np.max(np.abs(u1 - us)) <= 1e-8
+
+
+def test_correction_pass_converges_and_helps_in_large_holes():
+    """Corrected passes converge to the direct solution; on a sparse mask with
+    large unsampled regions (low-frequency error that the local solves spread
+    slowly) they need fewer fine passes than plain sweeps (soft check)."""
+    import synth
+    f, m = synth.make_frame(64, 64, 1, 0.01, "uniform", 21)
+    hier = oras.build_hierarchy(f, m, 3)
+    us = ref.solve_direct(f, m)
+    u_c = ref.initial_guess(f, m)
+    u_p = u_c.copy()
+    A = ref.assemble_A(m)
+    for _ in range(6):
+        u_c, _ = oras.correction_pass(u_c, f, m, hier, 16, 4, 0.3, 8, 3)
+        u_p, _ = oras.oras_sweep(u_p, f, m, 16, 4, 0.3, 8, A=A)
+    err_c = np.max(np.abs(u_c - us))
+    err_p = np.max(np.abs(u_p - us))
+    assert err_c < 0.5 * err_p
+    for _ in range(30):
+        u_c, _ = oras.correction_pass(u_c, f, m, hier, 16, 4, 0.3, 8, 3)
+    assert np.max(np.abs(u_c - us)) <= 1e-4
