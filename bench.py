@@ -407,6 +407,19 @@ def run_studies(dev, params):
             1, row["cg_single_level"]["fine_iterations"])
         cmp_[f"tol_{tol:g}"] = row
     out["oras_vs_cg"] = cmp_
+
+    # multilevel variants at the bench tolerance: the paper's cascade against a
+    # coarse-grid correction after every fine sweep (DD_ML_CORRECTION)
+    ml = {}
+    for name, prm_ in [("cascade", dict(params)),
+                       ("correction_L2", dict(params, levels=2, ml_mode="correction", correction_sweeps=2)),
+                       ("correction_L3", dict(params, levels=3, ml_mode="correction", correction_sweeps=2)),
+                       ("correction_L4", dict(params, levels=4, ml_mode="correction", correction_sweeps=2))]:
+        with Inpainter(md, fd, device=dev, precision="fp32", **prm_) as ip:
+            ms_, st, _ = timed(ip, reps=2)
+        ml[name] = {"ms": ms_, "fine_passes": st["sweeps_per_level"][0], "rel_residual": max(st["rel_residual"][:3]),
+                    "converged": st["converged"]}
+    out["cascade_vs_correction"] = ml
     return out
 
 

@@ -313,8 +313,11 @@ def correction_pass(u, f, mask, hier, b, o, p_robin, k, m):
     level of hier (from build_hierarchy): the fine residual r = b - A u (zero
     on known pixels) is summed down to that level, the correction equation
     A_c e = R r (e = 0 on coarse-known pixels) gets m ORAS sweeps from e = 0,
-    and e, prolonged bilinearly level by level, is added on unknown fine
-    pixels.  Returns (u_next, ||r^n|| of the input per channel)."""
+    and e, prolonged bilinearly level by level to d (zero on known fine
+    pixels), is added with the step omega = (r, d) / (d, A d) per channel: the
+    minimiser of the A-norm of the error along d (A is SPD on the unknowns;
+    the rediscretised coarse problem is not the Galerkin one, so the plain
+    step can overshoot).  Returns (u_next, ||r^n|| of the input per channel)."""
     mask = np.asarray(mask)
     u1, rn = oras_sweep(u, f, mask, b, o, p_robin, k)
     two_d = np.asarray(u1).ndim == 2
@@ -331,6 +334,12 @@ def correction_pass(u, f, mask, hier, b, o, p_robin, k, m):
     for lvl in range(len(hier) - 2, -1, -1):
         H, W = np.asarray(hier[lvl][1]).shape
         e = prolong_bilinear(e, H, W)
-    out = u3 + (mask == 0) * e
+    r0 = ref.residual(u3, f3, mask)
+    d = (mask == 0) * e
+    Ad = ref.apply_A(d, mask)
+    num = (r0 * d).reshape(d.shape[0], -1).sum(axis=1)
+    den = (d * Ad).reshape(d.shape[0], -1).sum(axis=1)
+    omega = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+    out = u3 + omega[:, None, None] * d
     return (out[0] if two_d else out), rn
 

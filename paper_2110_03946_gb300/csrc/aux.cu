@@ -529,6 +529,192 @@ __global__ void __launch_bounds__(V_TPB) prolong_add_kernel(int Hc, int Wc, int 
     }
 }
 
+// ---- energy-optimal step of the coarse correction ---------------------------------------
+// The prolonged correction d is scaled by omega = (r, d) / (d, A d) per
+// channel, the step that minimises the A-norm of the error along d (A is SPD
+// on the unknowns), so a correction from an approximate, non-Galerkin coarse
+// problem can never increase that error.  Three streaming passes:
+//   dir:   d = P e_c on unknown pixels (0 on known), written over r, and (r, d);
+//   curv:  (d, A d) with (A d)_p = sum over in-image neighbours q of (d_p - d_q);
+//          its last block also forms omega;
+//   step:  u += omega d.
+// Each pass's blocks write double partials in block order; the last block
+// (atomic ticket) reduces them in a fixed order.  All are no-ops if *skip != 0.
+struct DotTail {
+    double* part;        // C x nblk
+    int nblk;
+    unsigned int* ticket;
+    double* out;         // C: the reduced sums
+    const double* num;   // curv only: (r, d) per channel, for omega
+    double* omega;       // curv only: C
+};
+
+__device__ void dot_tail(float s, int c, const DotTail& t, int C) {
+    __shared__ float ss[V_TPB / 32];
+    __shared__ int s_last;
+    __shared__ double rs[V_TPB];
+    const int tid = threadIdx.y * V_TX + threadIdx.x;
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+    if ((tid & 31) == 0) ss[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+        double ts = 0.0;
+        for (int w = 0; w < V_TPB / 32; ++w) ts += (double)ss[w];
+        t.part[(size_t)c * t.nblk + blockIdx.y * gridDim.x + blockIdx.x] = ts;
+        __threadfence();
+        s_last = atomicAdd(t.ticket, 1u) == gridDim.x * gridDim.y * gridDim.z - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int cc = 0; cc < C; ++cc) {
+        double sv = 0.0;
+        for (int i = tid; i < t.nblk; i += V_TPB) sv += __ldcg(t.part + (size_t)cc * t.nblk + i);
+        rs[tid] = sv;
+        __syncthreads();
+        for (int hh = V_TPB / 2; hh > 0; hh >>= 1) {
+            if (tid < hh) rs[tid] += rs[tid + hh];
+            __syncthreads();
+        }
+        if (tid == 0) {
+            t.out[cc] = rs[0];
+            if (t.omega) {
+                const double num = t.num[cc], den = rs[0];
+                t.omega[cc] = (den > 0.0 && isfinite(num) && isfinite(den)) ? num / den : 0.0;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *t.ticket = 0u;
+}
+
+// d = bilinear prolongation of (sel_c && sel_c[0] ? ec1 : ec0) on unknown fine
+// pixels (0 on known), written over r; (r, d) per channel.
+__global__ void __launch_bounds__(V_TPB) corr_dir_kernel(int Hc, int Wc, int H, int W, int C, const float* __restrict__ ec0,
+                                                         const float* __restrict__ ec1, const int* __restrict__ sel_c,
+                                                         int ecp, long long ecplane, const uint8_t* __restrict__ mask,
+                                                         int mp, float* __restrict__ rd, int rp, long long rplane,
+                                                         const int* __restrict__ skip, DotTail t, CopyVec vec) {
+    if (skip != nullptr && *skip != 0) return;
+    const int c = blockIdx.z;
+    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    float s = 0.f;
+    if (x0 < W) {
+        const float* __restrict__ p = ((sel_c != nullptr && sel_c[0]) ? ec1 : ec0) + c * ecplane;
+        float* __restrict__ rr = rd + c * rplane;
+        int xa[4], xb[4];
+        float wx[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float tx = fminf(fmaxf((x0 + j - 0.5f) * 0.5f, 0.f), (float)(Wc - 1));
+            xa[j] = (int)floorf(tx);
+            xb[j] = min(xa[j] + 1, Wc - 1);
+            wx[j] = tx - (float)xa[j];
+        }
+#pragma unroll
+        for (int k = 0; k < V_ROWS; ++k) {
+            const int y = yb + k;
+            if (y >= H) break;
+            const float ty = fminf(fmaxf((y - 0.5f) * 0.5f, 0.f), (float)(Hc - 1));
+            const int ya = (int)floorf(ty), yb1 = min(ya + 1, Hc - 1);
+            const float wy = ty - (float)ya;
+            const float* __restrict__ ra = p + (size_t)ya * ecp;
+            const float* __restrict__ rb = p + (size_t)yb1 * ecp;
+            bool m[4];
+            ldm4(mask + (size_t)y * mp, x0, W, vec.m, m);
+            float r[4], d[4];
+            ld4(rr + (size_t)y * rp, x0, W, vec.dst, r);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                d[j] = 0.f;
+                if (!m[j] && x0 + j < W) {
+                    const float top = ra[xa[j]] * (1.f - wx[j]) + ra[xb[j]] * wx[j];
+                    const float bot = rb[xa[j]] * (1.f - wx[j]) + rb[xb[j]] * wx[j];
+                    d[j] = top * (1.f - wy) + bot * wy;
+                }
+                s = fmaf(r[j], d[j], s);
+            }
+            st4(rr + (size_t)y * rp, x0, W, vec.dst, d);
+        }
+    }
+    dot_tail(s, c, t, C);
+}
+
+// (d, A d) per channel, and omega = (r, d) / (d, A d) in the last block.
+__global__ void __launch_bounds__(V_TPB) corr_curv_kernel(int H, int W, int C, const float* __restrict__ dd, int dp,
+                                                          long long dplane, const int* __restrict__ skip, DotTail t,
+                                                          CopyVec vec) {
+    if (skip != nullptr && *skip != 0) return;
+    const int c = blockIdx.z;
+    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    const bool xin = x0 < W;
+    const float* __restrict__ d = dd + c * dplane;
+    float rows[V_ROWS + 2][4];
+#pragma unroll
+    for (int k = 0; k < V_ROWS + 2; ++k) {
+        const int y = yb - 1 + k;
+        if (xin && y >= 0 && y < H) {
+            ld4(d + (size_t)y * dp, x0, W, vec.src, rows[k]);
+        } else {
+            rows[k][0] = rows[k][1] = rows[k][2] = rows[k][3] = 0.f;
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        const int y = yb + k;
+        const float* rw = rows[k + 1];
+        float left = __shfl_up_sync(0xffffffffu, rw[3], 1);
+        float right = __shfl_down_sync(0xffffffffu, rw[0], 1);
+        if (!xin || y >= H) continue;
+        if (threadIdx.x == 0) left = x0 > 0 ? d[(size_t)y * dp + x0 - 1] : 0.f;
+        if (threadIdx.x == V_TX - 1) right = x0 + 4 < W ? d[(size_t)y * dp + x0 + 4] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = x0 + j;
+            if (x >= W) continue;
+            const float dc = rw[j];   // 0 on known pixels: their rows drop out
+            float ad = 0.f;
+            if (y > 0) ad += dc - rows[k][j];
+            if (y < H - 1) ad += dc - rows[k + 2][j];
+            if (x > 0) ad += dc - (j > 0 ? rw[j - 1] : left);
+            if (x < W - 1) ad += dc - (j < 3 ? rw[j + 1] : right);
+            s = fmaf(dc, ad, s);
+        }
+    }
+    dot_tail(s, c, t, C);
+}
+
+// (sel_u[0] ? u1 : u0) += omega[c] d
+__global__ void __launch_bounds__(V_TPB) corr_step_kernel(int H, int W, const float* __restrict__ dd, int dp,
+                                                          long long dplane, const double* __restrict__ omega,
+                                                          float* __restrict__ u0, float* __restrict__ u1,
+                                                          const int* __restrict__ sel_u, int up, long long uplane,
+                                                          const int* __restrict__ skip, CopyVec vec) {
+    if (skip != nullptr && *skip != 0) return;
+    const int c = blockIdx.z;
+    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    if (x0 >= W) return;
+    const float w = (float)omega[c];
+    const float* __restrict__ d = dd + c * dplane;
+    float* __restrict__ u = (sel_u[0] ? u1 : u0) + c * uplane;
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        const int y = yb + k;
+        if (y >= H) break;
+        float dv[4], uv[4];
+        ld4(d + (size_t)y * dp, x0, W, vec.src, dv);
+        ld4(u + (size_t)y * up, x0, W, vec.dst, uv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) uv[j] = fmaf(w, dv[j], uv[j]);
+        st4(u + (size_t)y * up, x0, W, vec.dst, uv);
+    }
+}
+
 constexpr int RED_TPB = 512;
 
 __global__ void __launch_bounds__(RED_TPB) reduce_part_kernel(const double2* __restrict__ part, int nblk,
@@ -748,6 +934,66 @@ cudaError_t launch_restrict_sum(int H, int W, int C, const float* src, int sp, l
     const CopyVec v{vec_ok(src, sp, splane, 4), vec_ok(dst, dp, dplane, 4), false};
     restrict_sum_kernel<<<gridv(Hc, Wc, C), dim3(V_TX, V_TY), 0, st>>>(H, W, Hc, Wc, src, sp, splane, dst, dp, dplane,
                                                                        skip, v);
+    return cudaGetLastError();
+}
+
+// gate[0] = 1 if this pass's correction is skipped: the fine stop flag is set,
+// or corrections were switched off; gate[1] = off.  Corrections are switched
+// off once the fine residual (the worst relative residual of the latest full
+// sweep's input, norms2[2C]) fell by less than the factor kGateRatio since
+// the previous pass.  prev[0] holds that previous residual.
+constexpr double kGateRatio = 0.7;
+
+__global__ void corr_gate_kernel(const int* __restrict__ flag, const double* __restrict__ norms2, int C,
+                                 int* __restrict__ gate, double* __restrict__ prev) {
+    if (threadIdx.x != 0) return;
+    int skip = flag[0] != 0 || gate[1] != 0;
+    if (!skip) {
+        const double w = norms2[2 * C];
+        if (prev[0] > 0.0 && !(w <= kGateRatio * prev[0])) {
+            gate[1] = 1;
+            skip = 1;
+        }
+        prev[0] = w;
+    }
+    gate[0] = skip;
+}
+
+cudaError_t launch_corr_gate(const int* flag, const double* norms2, int C, int* gate, double* prev, cudaStream_t st) {
+    corr_gate_kernel<<<1, 32, 0, st>>>(flag, norms2, C, gate, prev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corr_dir(int Hc, int Wc, int H, int W, int C, const float* ec0, const float* ec1, const int* sel_c,
+                            int ecp, long long ecplane, const uint8_t* mask, int mp, float* rd, int rp,
+                            long long rplane, const int* skip, double* part, int nblk, unsigned int* ticket,
+                            double* out, cudaStream_t st) {
+    const dim3 grid = gridv(H, W, C);
+    if (nblk != (int)(grid.x * grid.y)) return cudaErrorInvalidValue;
+    const CopyVec v{false, vec_ok(rd, rp, rplane, 4), vec_ok(mask, mp, 0, 1)};
+    const DotTail t{part, nblk, ticket, out, nullptr, nullptr};
+    corr_dir_kernel<<<grid, dim3(V_TX, V_TY), 0, st>>>(Hc, Wc, H, W, C, ec0, ec1, sel_c, ecp, ecplane, mask, mp, rd, rp,
+                                                       rplane, skip, t, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corr_curv(int H, int W, int C, const float* d, int dp, long long dplane, const int* skip,
+                             double* part, int nblk, unsigned int* ticket, double* out, const double* num,
+                             double* omega, cudaStream_t st) {
+    const dim3 grid = gridv(H, W, C);
+    if (nblk != (int)(grid.x * grid.y)) return cudaErrorInvalidValue;
+    const CopyVec v{vec_ok(d, dp, dplane, 4), false, false};
+    const DotTail t{part, nblk, ticket, out, num, omega};
+    corr_curv_kernel<<<grid, dim3(V_TX, V_TY), 0, st>>>(H, W, C, d, dp, dplane, skip, t, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corr_step(int H, int W, int C, const float* d, int dp, long long dplane, const double* omega,
+                             float* u0, float* u1, const int* sel_u, int up, long long uplane, const int* skip,
+                             cudaStream_t st) {
+    const CopyVec v{vec_ok(d, dp, dplane, 4), vec_ok(u0, up, uplane, 4) && vec_ok(u1, up, uplane, 4), false};
+    corr_step_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(H, W, d, dp, dplane, omega, u0, u1, sel_u, up,
+                                                                  uplane, skip, v);
     return cudaGetLastError();
 }
 

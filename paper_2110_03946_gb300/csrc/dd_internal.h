@@ -118,6 +118,31 @@ cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, double* tol
 // dst (ceil(H/2) x ceil(W/2)) = sum of src over each 2x2 block inside the image.
 cudaError_t launch_restrict_sum(int H, int W, int C, const float* src, int sp, long long splane, float* dst, int dp,
                                 long long dplane, const int* skip, cudaStream_t st);
+// Safeguard of the correction: gate[0] = 1 (this pass's correction is skipped)
+// if flag[0] != 0 or corrections are off (gate[1]); corrections are switched
+// off for the rest of the solve once the fine residual norms2[2C] fell by less
+// than a factor 0.7 since the previous pass (prev[0]).  gate and prev are reset
+// (to 0) before a solve's fine loop.
+cudaError_t launch_corr_gate(const int* flag, const double* norms2, int C, int* gate, double* prev, cudaStream_t st);
+
+// Energy-optimal step of the correction (omega = (r, d) / (d, A d) per channel):
+// corr_dir: d = bilinear prolongation of the coarse correction on mask == 0
+//   pixels (0 elsewhere), written over r (pitch rp); out[c] = (r, d);
+// corr_curv: out[c] = (d, A d) with A the reduced operator; omega[c] =
+//   num[c] / out[c] (0 if not positive);
+// corr_step: (sel_u[0] ? u1 : u0) += omega[c] d.
+// part (C x nblk doubles, nblk = res64_blocks(H, W)) and ticket (zero, left
+// zero) are reduction scratch.
+cudaError_t launch_corr_dir(int Hc, int Wc, int H, int W, int C, const float* ec0, const float* ec1, const int* sel_c,
+                            int ecp, long long ecplane, const uint8_t* mask, int mp, float* rd, int rp,
+                            long long rplane, const int* skip, double* part, int nblk, unsigned int* ticket,
+                            double* out, cudaStream_t st);
+cudaError_t launch_corr_curv(int H, int W, int C, const float* d, int dp, long long dplane, const int* skip,
+                             double* part, int nblk, unsigned int* ticket, double* out, const double* num,
+                             double* omega, cudaStream_t st);
+cudaError_t launch_corr_step(int H, int W, int C, const float* d, int dp, long long dplane, const double* omega,
+                             float* u0, float* u1, const int* sel_u, int up, long long uplane, const int* skip,
+                             cudaStream_t st);
 // (sel_u[0] ? u1 : u0) += bilinear prolongation of (sel_c && sel_c[0] ? ec1 : ec0)
 // on pixels with mask == 0.
 cudaError_t launch_prolong_add(int Hc, int Wc, int H, int W, int C, const float* ec0, const float* ec1,

@@ -148,6 +148,9 @@ struct dd_inpaint {
     int* state_c = nullptr;         // 4 ints
     double* norms2_c = nullptr;     // 2C + 2
     double* tol_c = nullptr;        // 1
+    double* corr_dots = nullptr;    // 3C: (r, d), (d, A d), omega
+    int* corr_gate = nullptr;       // [0] skip this pass's correction, [1] corrections off
+    double* corr_prev = nullptr;    // the fine residual at the previous pass
     cudaStream_t cap_stream = nullptr;   // private stream on which loop bodies are captured
     // pinned host mirrors
     double2* h_res = nullptr;
@@ -429,7 +432,7 @@ bool corrects(const dd_inpaint* h) { return h->prm.ml_mode == DD_ML_CORRECTION &
 // Kernels of the coarse-grid correction after one fine sweep.
 int correction_kernels(const dd_inpaint* h) {
     const int nl = (int)h->lv.size();
-    return 1 + (nl - 1) + 1 + h->prm.correction_sweeps + (nl - 2) + 1;
+    return 1 + 1 + (nl - 1) + 1 + h->prm.correction_sweeps + (nl - 2) + 3;
 }
 
 int pass_kernels_of(const dd_inpaint* h, const Level& L) {
@@ -459,12 +462,21 @@ dd::CGArgs cg_args(const dd_inpaint* h, const Level& L) {
 //         stencil there carries the factor 4 per level),
 //   e_c = correction_sweeps ORAS sweeps on A_c e_c = g_c from e_c = 0, with
 //         e_c = 0 on coarse-known pixels,
-//   u  += e_c prolonged bilinearly level by level, on unknown fine pixels.
+//   d   = e_c prolonged bilinearly level by level, on unknown fine pixels,
+//   u  += omega d with omega = (r, d) / (d, A d) per channel, the step that
+//         minimises the A-norm of the error along d: the rediscretised coarse
+//         problem is not the Galerkin one, and its plain correction can
+//         overshoot.
+// A gate skips the correction once the fine stop flag is set, and switches
+// corrections off for the rest of the solve once a pass reduced the fine
+// residual by less than a factor 0.7: with the non-symmetric ORAS smoother
+// the corrected iteration can still grow slowly, where plain ORAS converges.
 int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
     const int nl = (int)h->lv.size();
     Level& F = h->lv[0];
     Level& Lc = h->lv[nl - 1];
-    const int* skip = h->flag_d;
+    DD_CK(dd::launch_corr_gate(h->flag_d, h->norms2_d, h->C, h->corr_gate, h->corr_prev, st));
+    const int* skip = h->corr_gate;
     dd::Res64Args a{};
     a.H = F.H; a.W = F.W; a.C = h->C;
     a.u = F.u[0]; a.u1 = F.u[1]; a.sel = h->sstate_d; a.up = F.P; a.uplane = F.plane();
@@ -508,8 +520,21 @@ int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
         eH = L.H; eW = L.W; ep = L.P;
         eplane = L.plane();
     }
-    DD_CK(dd::launch_prolong_add(eH, eW, F.H, F.W, h->C, e0, e1, sel, ep, eplane, F.mask, F.W, F.u[0], F.u[1],
-                                 h->sstate_d, F.P, F.plane(), skip, st));
+    // energy-optimal step along the prolonged correction d (written over r)
+    double* part = reinterpret_cast<double*>(h->res_part);
+    DD_CK(dd::launch_corr_dir(eH, eW, F.H, F.W, h->C, e0, e1, sel, ep, eplane, F.mask, F.W, h->corr_r, F.P,
+                              F.plane(), skip, part, h->res_nblk, h->res_ticket, h->corr_dots, st));
+    DD_CK(dd::launch_corr_curv(F.H, F.W, h->C, h->corr_r, F.P, F.plane(), skip, part, h->res_nblk, h->res_ticket,
+                               h->corr_dots + h->C, h->corr_dots, h->corr_dots + 2 * h->C, st));
+    DD_CK(dd::launch_corr_step(F.H, F.W, h->C, h->corr_r, F.P, F.plane(), h->corr_dots + 2 * h->C, F.u[0], F.u[1],
+                               h->sstate_d, F.P, F.plane(), skip, st));
+    return DD_OK;
+}
+
+// Corrections on, no residual history: before a solve's fine iterations.
+int reset_correction(dd_inpaint* h, cudaStream_t st) {
+    DD_CK(cudaMemsetAsync(h->corr_gate, 0, 2 * sizeof(int), st));
+    DD_CK(cudaMemsetAsync(h->corr_prev, 0, sizeof(double), st));
     return DD_OK;
 }
 
@@ -640,6 +665,7 @@ void count_loop_launches(dd_inpaint* h) {
 int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, bool timed, bool loop,
                    bool capture) {
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, h->tol_d, tol, st));
+    if (&L == &h->lv[0] && corrects(h)) DD_TRY(reset_correction(h, st));
     if (loop) return run_loop(h, L, n, st, capture);
     for (int i = 0; i < n; ++i) {
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
@@ -1087,6 +1113,9 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         if ((rc = dalloc_t(h, &h->state_c, 4)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &h->norms2_c, (size_t)2 * C + 2)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &h->tol_c, 1)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &h->corr_dots, (size_t)3 * C)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &h->corr_gate, 2)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &h->corr_prev, 1)) != DD_OK) return fail(rc);
     }
     h->res_nblk = dd::res64_blocks(H, W);
     if ((rc = dalloc_t(h, &h->res_part, (size_t)C * h->res_nblk)) != DD_OK) return fail(rc);
@@ -1321,6 +1350,7 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, h->cur, h->tol_d, -1.0, st));
     const dd::SweepPair pair{{&F.map_u[0], &F.map_u[1]}, {F.u[0], F.u[1]}};
     const dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, h->tol_d, 0.0, h->flag_d, h->sstate_d, 0};
+    if (corrects(h)) DD_TRY(reset_correction(h, st));
     for (int i = 0; i < n; ++i) {   // tol < 0: every launch is a full sweep
         DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), pair, nullptr, F.tmask, stop,
                                       h->prm.robin_p, h->prm.local_cg_iters, st));

@@ -237,3 +237,21 @@ def test_correction_pass_converges_and_helps_in_large_holes():
     for _ in range(30):
         u_c, _ = oras.correction_pass(u_c, f, m, hier, 16, 4, 0.3, 8, 3)
     assert np.max(np.abs(u_c - us)) <= 1e-4
+
+
+def test_correction_step_never_raises_the_energy_error(rng):
+    """omega = (r, d) / (d, A d) minimises ||u* - u - omega d||_A, so the
+    corrected iterate is never worse in the A-norm than the swept one."""
+    f, m = _case(rng, 40, 52, 0.03)
+    hier = oras.build_hierarchy(f, m, 3)
+    us = ref.solve_direct(f, m)
+
+    def energy(u):
+        e = (us - u) * (m == 0)
+        return float((e * ref.apply_A(e, m)).sum())
+
+    u = ref.initial_guess(f, m)
+    for _ in range(4):
+        swept, _ = oras.oras_sweep(u, f, m, 12, 3, 0.3, 6)
+        u, _ = oras.correction_pass(u, f, m, hier, 12, 3, 0.3, 6, 1)
+        assert energy(u) <= energy(swept) * (1 + 1e-12) + 1e-18
