@@ -160,12 +160,14 @@ def make_frames(n: int, seed_offset: int):
     return [synth.make_frame(w.H, w.W, w.C, w.density, w.pattern, w.seed_base + seed_offset + j) for j in range(n)]
 
 
-def sweep_flops(local_unknowns: int, C: int, k: int) -> float:
-    """Algorithmic FP32 flops of one fine-level sweep launch: per unknown pixel
-    of every local problem, the residual (4 differences, 3 sums: 8 flops incl.
-    the source term), k CG steps of 15 flops (5-point operator 5, two dot
-    products 4, three vector updates 6) and the add-back (1)."""
-    return float(local_unknowns) * C * (15.0 * k + 9.0)
+def sweep_flops(pixel_steps: float, unknowns: float) -> float:
+    """Algorithmic FP32 flops of fine-level sweeps: per unknown pixel of every
+    local problem, the residual (4 differences, 3 sums: 8 flops incl. the
+    source term) and the add-back (1), plus 15 flops per local CG step taken
+    (5-point operator 5, two dot products 4, three vector updates 6).
+    pixel_steps = sum over local problems of unknown pixels x CG steps (the
+    kernel counts them: the relative local stop ends some early)."""
+    return 15.0 * float(pixel_steps) + 9.0 * float(unknowns)
 
 
 def sweep_hbm_bytes(H: int, W: int, C: int, store_bytes: int, with_source: bool) -> float:
@@ -536,7 +538,7 @@ def run_ours(args):
     # The sweep kernel timed alone: with several frames in flight the timed
     # region's sweeps share the SMs, which stretches each launch; the roofline
     # uses single-stream solves of the same frames right after the timed region.
-    iso_ms, iso_n = 0.0, 0
+    iso_ms, iso_n, iso_work, iso_unk, iso_full = 0.0, 0, 0, 0, 0
     with Inpainter(dmask[0], dvals[0], device=dev, **prm_timed) as ipi:
         for i in range(6):
             j = i % args.frames
@@ -546,6 +548,9 @@ def run_ours(args):
                 sti = ipi.stats()
                 iso_ms += sti["fine_sweep_ms"]
                 iso_n += sti["fine_sweep_launches"]
+                iso_work += sti["fine_cg_pixel_steps"]
+                iso_unk += sti["fine_swept_unknowns"]
+                iso_full += sti["sweeps_per_level"][0]
 
     # ---- end to end through the public API with host buffers -------------------
     # Every step copies its mask and values from pinned host memory to the
@@ -690,8 +695,8 @@ def run_ours(args):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FP32 FMA at max clock
-    k_used = prm["local_cg_iters"]
-    flops = sweep_flops(st["local_unknowns"], C, k_used)
+    # algorithmic work of an average fine sweep, from the kernel's own counts
+    flops = sweep_flops(iso_work, iso_unk) / max(1, iso_full)
     achieved = flops / avg_sweep_s / 1e12 if avg_sweep_s else None
     sbytes = 4 if args.precision in ("fp32", "fp32_ref") else 2
     hbm_alg = sweep_hbm_bytes(H, W, C, sbytes, args.precision != "fp32")
@@ -726,6 +731,7 @@ def run_ours(args):
         "config": {"workload": "rgb4k_edge3: 3840x2160x3, 3% edge-clustered mask, rel-res 1e-6",
                    "frames_in_flight": nmain,
                    "block": prm["block"], "overlap": prm["overlap"], "local_cg_iters": prm["local_cg_iters"],
+                   "local_rtol": prm.get("local_rtol", 0.0),
                    "levels": prm["levels"], "robin_p": prm["robin_p"], "coarse_tol": prm["coarse_tol"],
                    "params_source": tuned_src, "precision": args.precision, "frames_resident": args.frames,
                    "device_loop": args.device_loop,

@@ -95,6 +95,8 @@ typedef struct dd_params {
                                 with CG, max_sweeps / coarse_sweeps count CG iterations */
     int    correction_sweeps; /* DD_ML_CORRECTION: ORAS sweeps on the coarse correction equation
                                 after each fine sweep, from zero (default 2) */
+    double local_rtol;       /* in [0, 1): a block's local CG also stops once its residual fell by this
+                                factor (default 0: always local_cg_iters steps, as in the paper) */
     int    device_loop;      /* 1 (default): a level's sweeps (or CG iterations) repeat inside a
                                 CUDA graph loop on the device until its stop test or sweep limit,
                                 no launch after the stop; 0: launched in fixed chunks whose launches
@@ -121,6 +123,9 @@ typedef struct dd_stats {
                                                   one channel (work of one local problem set) */
     int    fine_sweep_launches;                /* timed fine-level sweep launches (params.timing) */
     double fine_sweep_ms;                      /* their summed device time */
+    long long fine_cg_pixel_steps;             /* params.timing: over the fine level's full sweeps, the sum
+                                                  of unknown block pixels x local CG steps taken */
+    long long fine_swept_unknowns;             /* params.timing: unknown block pixels of those sweeps */
     int    host_continued;                     /* 1: the enqueued part of the solve ended above tol and
                                                   dd_inpaint_solve_finish continued under host control,
                                                   rewriting u_out (work enqueued on the stream after

@@ -124,9 +124,10 @@ def local_matrix(A, mask, blk, p_robin: float):
     return idx, M.tocsr()
 
 
-def cg_fixed(M, rhs, k):
+def cg_fixed(M, rhs, k, rtol=0.0):
     """Conjugate gradients (Saad 2003, the CG algorithm of Ch. 6) from x = 0
-    for k iterations; stops early if (r, r) or (p, Ap) is not positive.
+    for k iterations; stops early if (r, r) or (p, Ap) is not positive, or,
+    with rtol > 0, once ||r|| <= rtol ||r_0|| (checked before each step).
     k = None solves exactly."""
     if k is None:
         if rhs.size == 0:
@@ -136,8 +137,9 @@ def cg_fixed(M, rhs, k):
     r = rhs.copy()
     p = r.copy()
     rr = float(r @ r)
+    rr_stop = rtol * rtol * rr
     for _ in range(k):
-        if not rr > 0.0:
+        if not rr > 0.0 or rr <= rr_stop:
             break
         Ap = M @ p
         pAp = float(p @ Ap)
@@ -153,12 +155,14 @@ def cg_fixed(M, rhs, k):
     return x
 
 
-def oras_sweep(u, f, mask, b, o, p_robin, k, g=None, A=None):
+def oras_sweep(u, f, mask, b, o, p_robin, k, g=None, A=None, local_rtol=0.0):
     """One ORAS iteration: returns (u_next, ||r^n|| per channel).
 
     u, f: (C, H, W).  g (optional, (C,H,W)): extra source term on unknown
     pixels, i.e. the sweep solves A u = C f + (I - C) g (used for correction
-    equations).  r^n is the residual of the INPUT iterate u^n."""
+    equations).  r^n is the residual of the INPUT iterate u^n.  local_rtol > 0
+    lets each local CG stop once its residual fell by that factor (the paper
+    runs a fixed number of steps; 0 keeps that)."""
     u = np.asarray(u, dtype=np.float64)
     two_d = u.ndim == 2
     u3 = u[None] if two_d else u
@@ -191,7 +195,7 @@ def oras_sweep(u, f, mask, b, o, p_robin, k, g=None, A=None):
             v = np.zeros(idx.size)
             v[known] = rl[known]               # identity rows of A
             rhs = rl[unk] - Muk @ v[known]
-            v[unk] = cg_fixed(Muu, rhs, k)
+            v[unk] = cg_fixed(Muu, rhs, k, local_rtol)
             out[c, idx[own]] += v[own]
     out = out.reshape(C, H, W)
     return (out[0] if two_d else out), rn

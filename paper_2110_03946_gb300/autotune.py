@@ -1,7 +1,7 @@
 """Autotuner for the ORAS solver parameters.
 
-Searches block side, overlap, local CG steps, Robin weight, number of levels
-and coarse tolerance for the smallest device time to a relative residual
+Searches block side, overlap, local CG steps and their relative stop, Robin
+weight, number of levels and coarse tolerance for the smallest device time to a relative residual
 ``tol`` on sample frames: for every block side a coordinate descent (one
 parameter at a time over its candidates, repeated while something improves and
 time is left), keeping the best result over block sides.  Every trial
@@ -27,12 +27,14 @@ from .inpaint import PRECISIONS, make_params
 SPACE = {
     "block": [16, 32, 64],
     "overlap": [1, 2, 3, 4, 5, 6, 8],
-    "local_cg_iters": [8, 10, 12, 14, 16, 18, 20, 24],
+    "local_cg_iters": [8, 10, 12, 14, 16, 18, 20, 24, 28, 32],
+    "local_rtol": [0.0, 0.01, 0.02, 0.03, 0.05, 0.1],   # 0.0 = always local_cg_iters steps
     "robin_p": [0.0, 0.1, 0.15, 0.2, 0.3, 0.5, 1.0],   # 0.0 = library default
     "levels": [1, 2, 3, 4, 5, 6],
     "coarse_tol": [1e-1, 1e-2, 3e-3, 1e-3, 3e-4],
 }
-START = {"block": 32, "overlap": 6, "local_cg_iters": 16, "robin_p": 0.0, "levels": 3, "coarse_tol": 1e-2}
+START = {"block": 32, "overlap": 6, "local_cg_iters": 16, "local_rtol": 0.0, "robin_p": 0.0, "levels": 3,
+         "coarse_tol": 1e-2}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 
@@ -146,6 +148,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--budget", type=float, default=120.0, help="seconds")
+    ap.add_argument("--blocks", default="16,32,64", help="block sides to search")
+    ap.add_argument("--start", default=None, help="JSON start point (default: the cached entry, else START)")
     ap.add_argument("--out", default=DEFAULT_CACHE)
     a = ap.parse_args()
     import synth
@@ -155,7 +159,12 @@ def main():
     for j in range(a.frames):
         f, m = synth.make_frame(w.H, w.W, w.C, w.density, w.pattern, w.seed_base + 50 + j)
         frames.append((torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev)))
-    best, ms, seen = autotune(frames, a.precision, a.tol, a.budget, log=lambda s: print(s, flush=True))
+    space = dict(SPACE, block=[int(b) for b in a.blocks.split(",")])
+    start = json.loads(a.start) if a.start else lookup(w.H, w.W, w.C, w.density, a.precision, a.tol, a.out)
+    if start:
+        start = dict(START, **start)
+    best, ms, seen = autotune(frames, a.precision, a.tol, a.budget, space=space, start=start,
+                              log=lambda s: print(s, flush=True))
     cache = load_cache(a.out)
     cache[cache_key(w.H, w.W, w.C, w.density, a.precision, a.tol)] = {
         "params": best, "ms_per_frame": ms, "trials": len(seen), "workload": a.workload,

@@ -40,7 +40,7 @@ class dd_params(ctypes.Structure):
         ("inputs_on_device", ctypes.c_int), ("coarse_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
         ("max_corrections", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("timing", ctypes.c_int),
         ("tile_warps", ctypes.c_int), ("solver", ctypes.c_int), ("correction_sweeps", ctypes.c_int),
-        ("device_loop", ctypes.c_int),
+        ("local_rtol", ctypes.c_double), ("device_loop", ctypes.c_int),
     ]
 
 
@@ -51,7 +51,9 @@ class dd_stats(ctypes.Structure):
         ("rel_residual", ctypes.c_double * DD_MAX_STAT_CHANNELS), ("ms_total", ctypes.c_double),
         ("device_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_longlong),
         ("local_unknowns", ctypes.c_longlong), ("fine_sweep_launches", ctypes.c_int),
-        ("fine_sweep_ms", ctypes.c_double), ("host_continued", ctypes.c_int),
+        ("fine_sweep_ms", ctypes.c_double),
+        ("fine_cg_pixel_steps", ctypes.c_longlong), ("fine_swept_unknowns", ctypes.c_longlong),
+        ("host_continued", ctypes.c_int),
     ]
 
 

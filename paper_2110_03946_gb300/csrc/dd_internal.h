@@ -85,6 +85,9 @@ struct SweepStop {
     int* flag;
     int* state;
     int force_probe;   // 1: this launch is a probe whatever state[2] says
+    // optional work counters of full sweeps: work[0] += sum over blocks of
+    // (unknown block pixels) x (local CG steps taken), work[1] += unknown block pixels
+    unsigned long long* work;
 };
 constexpr int kSweepSlots = 4096;   // per-channel partial slots that cover any persistent grid
 
@@ -98,9 +101,11 @@ struct SweepPair {
 // elements apart), from buffer state[0] of `pair` into the other buffer.
 //   map_g: optional source g on unknown pixels (solves A u = C f + (I - C) g
 //   with u = f held on known pixels).
+//   local_rtol in [0, 1): a block's local CG also stops once its residual fell
+//   by that factor (0: always k steps).
 cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, const SweepPair& pair,
                          const CUtensorMap* map_g, const uint32_t* tmask, const SweepStop& stop, float p_robin,
-                         int k, cudaStream_t stream);
+                         int k, cudaStream_t stream, float local_rtol = 0.f);
 
 // Kernel attributes and occupancy of the sweep for (s, g, has_g), queried once
 // per process; call before capturing a sweep launch into a graph.

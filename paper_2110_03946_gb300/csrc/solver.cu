@@ -142,6 +142,8 @@ struct dd_inpaint {
     int* sstate_d = nullptr;        // sweep state: current buffer, full sweeps, probe request, launches
     int* ctl_d = nullptr;           // device-loop pass counter (4 ints)
     double* tol_d = nullptr;        // stop tolerance of the running level (set by each reset)
+    unsigned long long* work_d = nullptr;   // timed fine sweeps: [0] pixel x CG steps, [1] pixels
+    unsigned long long* h_work = nullptr;   // pinned mirror
     // DD_ML_CORRECTION: fine residual, and the stop state of the coarse correction solve
     float* corr_r = nullptr;        // C x H x P (level 0)
     int* flag_c = nullptr;          // 4 ints
@@ -234,6 +236,7 @@ int validate(int H, int W, int C, const dd_params& p) {
     if (p.precision < DD_PREC_FP32 || p.precision > DD_PREC_BF16_REF) { set_error("bad precision"); return DD_EINVAL; }
     if (p.max_sweeps < 0 || p.coarse_sweeps < 0 || p.max_corrections < 0) { set_error("negative limit"); return DD_EINVAL; }
     if (!(p.coarse_tol > 0.0) || !(p.inner_tol > 0.0) || !(p.inner_tol < 1.0)) { set_error("bad tolerance"); return DD_EINVAL; }
+    if (!(p.local_rtol >= 0.0) || !(p.local_rtol < 1.0)) { set_error("local_rtol must be in [0, 1)"); return DD_EINVAL; }
     return DD_OK;
 }
 
@@ -345,7 +348,7 @@ int run_sweeps(dd_inpaint* h, const TileGeom& g, Store st_t, void* const bufs[2]
             stop.force_probe = last_probe ? 1 : 0;
             if (timed && !last_probe) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
             DD_LAUNCH(h, dd::launch_sweep(st_t, g, h->C, plane, pair, map_g, tmask, stop, h->prm.robin_p,
-                                          h->prm.local_cg_iters, st));
+                                          h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
             if (timed && !last_probe) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
         }
         DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -505,7 +508,7 @@ int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
     const dd::SweepStop stop{Lc.partial, dd::kSweepSlots, h->norms2_c, Lc.ref_d, h->tol_c, 0.0, h->flag_c, h->state_c, 0};
     for (int i = 0; i < h->prm.correction_sweeps; ++i)
         DD_CK(dd::launch_sweep(Store::F32, Lc.geom, h->C, Lc.plane(), pair, &Lc.map_cg, Lc.tmask, stop,
-                               h->prm.robin_p, h->prm.local_cg_iters, st));
+                               h->prm.robin_p, h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
     const float* e0 = Lc.u[0];
     const float* e1 = Lc.u[1];
     const int* sel = h->state_c;
@@ -538,15 +541,16 @@ int reset_correction(dd_inpaint* h, cudaStream_t st) {
     return DD_OK;
 }
 
-int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st) {
+int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st, bool count_work = false) {
     if (h->prm.solver == DD_SOLVER_CG) {
         DD_CK(dd::launch_cg_iteration(cg_args(h, L), st));
         return DD_OK;
     }
     const dd::SweepPair pair{{&L.map_u[0], &L.map_u[1]}, {L.u[0], L.u[1]}};
-    const dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, h->tol_d, 0.0, h->flag_d, h->sstate_d, 0};
+    const dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, h->tol_d, 0.0, h->flag_d, h->sstate_d, 0,
+                             count_work ? h->work_d : nullptr};
     DD_CK(dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), pair, nullptr, L.tmask, stop, h->prm.robin_p,
-                           h->prm.local_cg_iters, st));
+                           h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
     if (&L == &h->lv[0] && corrects(h)) DD_TRY(enqueue_correction(h, st));
     return DD_OK;
 }
@@ -667,9 +671,10 @@ int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, 
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, h->tol_d, tol, st));
     if (&L == &h->lv[0] && corrects(h)) DD_TRY(reset_correction(h, st));
     if (loop) return run_loop(h, L, n, st, capture);
+    if (timed) DD_CK(cudaMemsetAsync(h->work_d, 0, 2 * sizeof(unsigned long long), st));
     for (int i = 0; i < n; ++i) {
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
-        DD_TRY(enqueue_pass(h, L, st));
+        DD_TRY(enqueue_pass(h, L, st, timed));
         h->launches += pass_kernels_of(h, L) - 1;
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
     }
@@ -817,6 +822,7 @@ int fp32_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool 
     DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_ref, F.ref_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if (timed) DD_CK(cudaMemcpyAsync(h->h_work, h->work_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     if (!capture) DD_CK(cudaEventRecord(h->ev1, st));
     h->pending = true;
     h->pending_out = u_out;
@@ -851,6 +857,8 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
     if (status == 2) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
     const int n1 = first_chunk(h);
     if (h->prm.timing != 0 && h->ev_recorded && h->prm.solver == DD_SOLVER_ORAS) {
+        h->stats.fine_cg_pixel_steps = (long long)h->h_work[0];
+        h->stats.fine_swept_unknowns = (long long)h->h_work[1];
         for (int i = 0; i < applied && i < n1; ++i) {
             float ms = 0.f;
             DD_CK(cudaEventElapsedTime(&ms, h->sw_ev[2 * i], h->sw_ev[2 * i + 1]));
@@ -1015,6 +1023,7 @@ void free_all(dd_inpaint* h) {
     if (h->h_state) cudaFreeHost(h->h_state);
     if (h->h_ref) cudaFreeHost(h->h_ref);
     if (h->h_cnt) cudaFreeHost(h->h_cnt);
+    if (h->h_work) cudaFreeHost(h->h_work);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     for (auto& e : h->sw_ev)
@@ -1137,6 +1146,11 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if ((rc = dalloc_t(h, &h->ctl_d, 4)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->tol_d, 1)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->res_ticket, 1)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->work_d, 2)) != DD_OK) return fail(rc);
+    if (cudaMallocHost(&h->h_work, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        set_error("cudaMallocHost failed");
+        return fail(DD_ENOMEM);
+    }
     if (cudaMemset(h->res_ticket, 0, sizeof(unsigned int)) != cudaSuccess) {
         set_error("cudaMemset");
         return fail(DD_ECUDA);
@@ -1211,6 +1225,7 @@ void dd_params_default(dd_params* p) {
     p->solver = DD_SOLVER_ORAS;
     p->device_loop = 1;
     p->correction_sweeps = 2;
+    p->local_rtol = 0.0;
 }
 
 const char* dd_strerror(int code) {
@@ -1353,7 +1368,7 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     if (corrects(h)) DD_TRY(reset_correction(h, st));
     for (int i = 0; i < n; ++i) {   // tol < 0: every launch is a full sweep
         DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), pair, nullptr, F.tmask, stop,
-                                      h->prm.robin_p, h->prm.local_cg_iters, st));
+                                      h->prm.robin_p, h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
         if (corrects(h)) {   // one pass of DD_ML_CORRECTION: the sweep, then the coarse-grid correction
             DD_TRY(enqueue_correction(h, st));
             h->launches += correction_kernels(h);

@@ -192,7 +192,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
             for (int i = 0; i < n; ++i) {
                 stop.force_probe = last_probe ? 1 : 0;
                 SS_CK(dd::launch_sweep(dd::Store::F32, g, C, plane, pair, nullptr, tmask, stop, pr,
-                                       p.local_cg_iters, st));
+                                       p.local_cg_iters, st, (float)p.local_rtol));
             }
             launched += n;
             SS_CK(cudaMemcpyAsync(hflag, flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -159,6 +159,7 @@ struct SweepArgs {
     long long plane;
     float p_robin;
     int k;
+    float local_rtol2;   // local CG stops once (r, r) <= local_rtol2 * (r0, r0) (0: after k steps)
 };
 
 // Sum over the threads of one tile; identical result in every thread.
@@ -271,6 +272,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     const int slots = a.stop.slots;
     int cur_c = -1;        // channel whose owned residual sum is being accumulated
     float acc_c = 0.f;
+    uint32_t work_us = 0, work_u = 0;   // optional work counters (per lane)
     int it = 0;
     for (; t < total; t += gridDim.x, ++it) {
         const int buf = it & 1;
@@ -373,7 +375,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         }
         // ---- k CG steps from v = 0 (Saad, the CG algorithm of Ch. 6) --------------
         float2 v2[PY][NP], p2[PY][NP], q2[PY][NP];
-        float rr;
+        float rr, rr_stop;
         {
 #pragma unroll
             for (int i = 0; i < PY; ++i)
@@ -400,6 +402,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             const float2 both = tile_sum2<CF>(make_float2(s2, rr0), red[0], red[1], wt, lane);
             s2 = both.x;
             rr = both.y;
+            rr_stop = a.local_rtol2 * rr;
         }
         if (c != cur_c) {   // tiles of one CTA visit channels in increasing order
             if (tt == 0) {
@@ -422,8 +425,10 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                     nbS[j] = make_float2(xch[0][wt + 1][rx0 + 2 * j], xch[0][wt + 1][rx0 + 2 * j + 1]);
             }
         }
-        for (int kk = 0; kk < kcg; ++kk) {
-            if (!(rr > 1e-30f)) break;   // converged locally (and keeps the quotients below finite)
+        int kk = 0;
+        for (; kk < kcg; ++kk) {
+            // converged locally (the bound also keeps the quotients below finite)
+            if (!(rr > 1e-30f) || rr <= rr_stop) break;
             float pW[PY], pE[PY];
 #pragma unroll
             for (int i = 0; i < PY; ++i) {
@@ -512,6 +517,13 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             rr = rr_new;
         }
 
+        if (a.stop.work != nullptr && !probe) {   // work actually done (the local stop shortens it)
+            constexpr int LB = PX * PY;
+            const uint32_t un = (uint32_t)LB - (uint32_t)__popc(kb & (LB == 32 ? 0xffffffffu : ((1u << LB) - 1u)));
+            work_us += un * (uint32_t)kk;
+            work_u += un;
+        }
+
         // ---- restricted add-back on the owned core -------------------------------
         T* __restrict__ uout = u_out + (size_t)c * a.plane;
         if (!probe)
@@ -527,6 +539,13 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             }
         if constexpr (NW > 1) __syncthreads();   // the staged tile may now be refilled
         else __syncwarp();
+    }
+    if (a.stop.work != nullptr) {
+        const uint32_t ws = __reduce_add_sync(FULL, work_us), wu = __reduce_add_sync(FULL, work_u);
+        if (lane == 0) {
+            atomicAdd(a.stop.work, (unsigned long long)ws);
+            atomicAdd(a.stop.work + 1, (unsigned long long)wu);
+        }
     }
     if (tt == 0 && !s_ok) {
         // a copy timed out: wait (bounded) for the other buffer's copy before leaving
@@ -669,7 +688,8 @@ int persistent_grid(bool has_g) {
 
 template <class CF, typename T>
 cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const SweepPair& pr2, const CUtensorMap* mg,
-                      const uint32_t* tmask, const SweepStop& stop, float p_robin, int k, cudaStream_t st) {
+                      const uint32_t* tmask, const SweepStop& stop, float p_robin, int k, float local_rtol2,
+                      cudaStream_t st) {
     SweepArgs<T> a;
     a.u_buf[0] = static_cast<T*>(pr2.u[0]);
     a.u_buf[1] = static_cast<T*>(pr2.u[1]);
@@ -681,6 +701,7 @@ cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const SweepPair
     a.plane = plane;
     a.p_robin = p_robin;
     a.k = k;
+    a.local_rtol2 = local_rtol2;
     const long long work = (long long)g.ntiles * C;
     const int resident = persistent_grid<CF, T>(a.has_g);
     if (resident == 0) return cudaGetLastError();
@@ -705,14 +726,14 @@ cudaError_t prepare_store(Store s, bool has_g) {
 template <class CF>
 cudaError_t sweep_store(Store s, const TileGeom& g, int C, long long plane, const SweepPair& pr2,
                         const CUtensorMap* mg, const uint32_t* tmask, const SweepStop& stop, float p_robin, int k,
-                        cudaStream_t st) {
+                        float r2, cudaStream_t st) {
     switch (s) {
         case Store::F32:
-            return sweep_cfg<CF, float>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, st);
+            return sweep_cfg<CF, float>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, r2, st);
         case Store::F16:
-            return sweep_cfg<CF, __half>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, st);
+            return sweep_cfg<CF, __half>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, r2, st);
         case Store::BF16:
-            return sweep_cfg<CF, __nv_bfloat16>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, st);
+            return sweep_cfg<CF, __nv_bfloat16>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, r2, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -836,13 +857,15 @@ cudaError_t prepare_sweep(Store s, const TileGeom& g, bool has_g) {
 
 cudaError_t launch_sweep(Store s, const TileGeom& g, int C, long long plane, const SweepPair& pair,
                          const CUtensorMap* map_g, const uint32_t* tmask, const SweepStop& stop, float p_robin,
-                         int k, cudaStream_t st) {
+                         int k, cudaStream_t st, float local_rtol) {
+    if (!(local_rtol >= 0.f) || !(local_rtol < 1.f)) return cudaErrorInvalidValue;
     if (stop.slots < 1 || stop.partial == nullptr || stop.flag == nullptr || stop.norms2 == nullptr ||
         stop.ref == nullptr || stop.state == nullptr || pair.map[0] == nullptr || pair.map[1] == nullptr ||
         pair.u[0] == nullptr || pair.u[1] == nullptr)
         return cudaErrorInvalidValue;
     return with_cfg(g.b, g.nw, [&](auto cfg) {
-        return sweep_store<decltype(cfg)>(s, g, C, plane, pair, map_g, tmask, stop, p_robin, k, st);
+        return sweep_store<decltype(cfg)>(s, g, C, plane, pair, map_g, tmask, stop, p_robin, k,
+                                          local_rtol * local_rtol, st);
     });
 }
 

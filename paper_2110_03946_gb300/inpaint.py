@@ -18,7 +18,8 @@ ML_MODES = {"cascade": B.DD_ML_CASCADE, "correction": B.DD_ML_CORRECTION}
 def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_mode=None,
                 robin_p=None, precision=None, max_sweeps=None, coarse_tol=None, inner_tol=None,
                 max_corrections=None, coarse_sweeps=None, inputs_on_device=1, timing=None,
-                tile_warps=None, solver=None, device_loop=None, correction_sweeps=None) -> B.dd_params:
+                tile_warps=None, solver=None, device_loop=None, correction_sweeps=None,
+                local_rtol=None) -> B.dd_params:
     p = B.dd_params_default()
     if block is not None: p.block = int(block)
     if overlap is not None: p.overlap = int(overlap)
@@ -39,6 +40,7 @@ def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_m
         p.solver = {"oras": B.DD_SOLVER_ORAS, "cg": B.DD_SOLVER_CG}[solver] if isinstance(solver, str) else int(solver)
     if device_loop is not None: p.device_loop = int(device_loop)
     if correction_sweeps is not None: p.correction_sweeps = int(correction_sweeps)
+    if local_rtol is not None: p.local_rtol = float(local_rtol)
     p.inputs_on_device = int(inputs_on_device)
     return p
 
@@ -123,6 +125,8 @@ class Inpainter:
             "local_unknowns": int(s.local_unknowns),
             "fine_sweep_launches": int(s.fine_sweep_launches),
             "fine_sweep_ms": float(s.fine_sweep_ms),
+            "fine_cg_pixel_steps": int(s.fine_cg_pixel_steps),
+            "fine_swept_unknowns": int(s.fine_swept_unknowns),
             "host_continued": bool(s.host_continued),
         }
 

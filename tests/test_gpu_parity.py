@@ -303,3 +303,19 @@ def test_correction_pass_matches_oracle(levels, m):
     assert np.max(np.abs(u1 - e1)) <= 2e-3
     assert np.array_equal(u1[:, msk != 0], f[:, msk != 0].astype(np.float32))
 
+
+
+@pytest.mark.parametrize("rtol", [0.1, 0.02])
+def test_sweep_with_local_rtol_matches_oracle(rtol):
+    """Local CG with the relative stop: the block's CG ends once its residual
+    fell by rtol (decided on the kernel's FP32 (r, r), on the oracle's FP64)."""
+    b, o, k, p = 32, 6, 16, 0.25
+    f, m = synth.make_frame(100, 83, 2, 0.03, "edge", 17)
+    u0 = ref.initial_guess(f, m)
+    with Inpainter(m, f, block=b, overlap=o, local_cg_iters=k, robin_p=p, levels=1, precision="fp32",
+                   local_rtol=rtol) as ip:
+        ip.set_iterate(u0.astype(np.float32))
+        ip.sweep(1)
+        u1 = ip.get_iterate().cpu().numpy()
+    e1, _ = oras.oras_sweep(u0, f, m, b, o, p, k, local_rtol=rtol)
+    assert np.max(np.abs(u1 - e1)) <= 2e-3

@@ -255,3 +255,29 @@ def test_correction_step_never_raises_the_energy_error(rng):
         swept, _ = oras.oras_sweep(u, f, m, 12, 3, 0.3, 6)
         u, _ = oras.correction_pass(u, f, m, hier, 12, 3, 0.3, 6, 1)
         assert energy(u) <= energy(swept) * (1 + 1e-12) + 1e-18
+
+
+def test_cg_relative_stop(rng):
+    """rtol = 0 is the fixed-step CG; rtol > 0 stops at the first iterate whose
+    residual fell by the factor rtol, which the fixed-step run passes through."""
+    n = 60
+    Mr = rng.normal(size=(n, n))
+    M = sp.csr_matrix(Mr @ Mr.T + n * np.eye(n))
+    rhs = rng.normal(size=n)
+    x_fixed = oras.cg_fixed(M, rhs, 12)
+    assert np.array_equal(oras.cg_fixed(M, rhs, 12, 0.0), x_fixed)
+    x_rel = oras.cg_fixed(M, rhs, 12, 1e-3)
+    res = np.linalg.norm(rhs - M @ x_rel) / np.linalg.norm(rhs)
+    assert res <= 1e-3
+    steps = [oras.cg_fixed(M, rhs, j) for j in range(13)]
+    hit = next(j for j, xj in enumerate(steps) if np.linalg.norm(rhs - M @ xj) <= 1e-3 * np.linalg.norm(rhs))
+    assert np.allclose(x_rel, steps[hit], rtol=0, atol=1e-12)
+
+
+def test_local_rtol_sweep_still_converges(rng):
+    f, m = _case(rng, 40, 36, 0.06)
+    A = ref.assemble_A(m)
+    u = ref.initial_guess(f, m)
+    for _ in range(60):
+        u, _ = oras.oras_sweep(u, f, m, 12, 3, 0.3, 16, A=A, local_rtol=0.05)
+    assert np.max(np.abs(u - ref.solve_direct(f, m))) <= 1e-6
