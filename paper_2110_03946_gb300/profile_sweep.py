@@ -2,7 +2,7 @@
 launch sequence for profilers (e.g. ``ncu -k regex:oras_sweep -s 1 -c 1``).
 
 python -m paper_2110_03946_gb300.profile_sweep [--workload rgb4k_edge3]
-       [--precision fp32] [--k 16] [--sweeps 3]
+       [--precision fp32] [--k 16] [--local-rtol 0] [--sweeps 3]
 """
 from __future__ import annotations
 
@@ -20,6 +20,7 @@ def main():
     ap.add_argument("--k", type=int, default=16)
     ap.add_argument("--robin", type=float, default=0.0)
     ap.add_argument("--tile-warps", type=int, default=0)
+    ap.add_argument("--local-rtol", type=float, default=0.0)
     ap.add_argument("--sweeps", type=int, default=3)
     a = ap.parse_args()
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -34,7 +35,7 @@ def main():
     fd, md = torch.as_tensor(f).to(dev), torch.as_tensor(m).to(dev)
     with Inpainter(md, fd, device=dev, block=a.block or w.block, overlap=a.overlap if a.overlap is not None
                    else w.overlap, local_cg_iters=a.k, levels=1, precision=a.precision, robin_p=a.robin,
-                   tile_warps=a.tile_warps) as ip:
+                   tile_warps=a.tile_warps, local_rtol=a.local_rtol) as ip:
         ip.set_iterate(fd * (md != 0))
         for _ in range(a.sweeps):
             ip.sweep(1)
