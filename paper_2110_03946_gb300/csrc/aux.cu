@@ -743,14 +743,65 @@ __global__ void __launch_bounds__(RED_TPB) reduce_part_kernel(const double2* __r
 // ---- multilevel ----------------------------------------------------------------------
 template <typename T>
 __global__ void correct_kernel(int H, int W, float* __restrict__ u, int up, long long uplane,
-                               const T* __restrict__ e, int ep, long long eplane,
-                               const uint8_t* __restrict__ mask, int mp, const double* __restrict__ scale) {
+                               const T* __restrict__ e0, const T* __restrict__ e1, const int* __restrict__ sel,
+                               int ep, long long eplane, const uint8_t* __restrict__ mask, int mp,
+                               const double* __restrict__ scale, const int* __restrict__ skip) {
+    if (skip != nullptr && *skip != 0) return;
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
     if (x >= W || y >= H) return;
     if (mask[(size_t)y * mp + x]) return;
+    const T* __restrict__ e = (sel != nullptr && sel[0]) ? e1 : e0;
     float* pu = u + c * uplane + (size_t)y * up + x;
     const double v = (double)*pu + scale[c] * (double)to_f(e[c * eplane + (size_t)y * ep + x]);
     *pu = (float)v;
+}
+
+// Outer control of the device-driven correction loop (one thread), after the
+// FP64-accurate residual of u (res_out[c] = {sum r^2, max |r|}).  ctl: [0]
+// corrections applied, [1] inner sweeps applied, [2] outcome (0 running,
+// 1 converged, 2 limit reached, 3 NaN/Inf), [3] outer passes, [4] inner loop
+// passes, [5] skip (the rest of this pass does nothing).  First the previous
+// inner solve is added up (inner_state[1] full sweeps, inner_ctl[0] passes);
+// then either the loop ends (condition cleared) or the next correction's
+// scales are set: scale = max |r|, scale_inv = 1 / scale, inner_ref =
+// ||r|| / scale (the inner solve's reference norm).
+__global__ void ref_outer_ctl_kernel(const double2* __restrict__ res_out, const double* __restrict__ ref, int C,
+                                     const double* __restrict__ tol, int max_corr, int max_sweeps,
+                                     const int* __restrict__ inner_state, const int* __restrict__ inner_ctl,
+                                     int* __restrict__ ctl, double* __restrict__ scale,
+                                     double* __restrict__ scale_inv, double* __restrict__ inner_ref,
+                                     cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0) return;
+    const int passes = ctl[3] + 1;
+    ctl[3] = passes;
+    if (ctl[0] > 0) {
+        ctl[1] += inner_state[1];
+        ctl[4] += inner_ctl[0];
+    }
+    double worst = 0.0;
+    bool bad = false;
+    for (int c = 0; c < C; ++c) {
+        const double s = res_out[c].x;
+        if (!isfinite(s)) bad = true;
+        const double den = ref[c] > 0.0 ? ref[c] : 1.0;
+        worst = fmax(worst, sqrt(s) / den);
+    }
+    int done = 0;
+    if (bad) done = 3;
+    else if (worst <= *tol) done = 1;
+    else if (ctl[0] >= max_corr || ctl[1] >= max_sweeps || passes > max_corr + 1) done = 2;
+    if (done == 0) {
+        for (int c = 0; c < C; ++c) {
+            const double sc = res_out[c].y > 0.0 ? res_out[c].y : 1.0;
+            scale[c] = sc;
+            scale_inv[c] = 1.0 / sc;
+            inner_ref[c] = sqrt(res_out[c].x) / sc;
+        }
+        ctl[0] += 1;
+    }
+    ctl[2] = done;
+    ctl[5] = done != 0;
+    if (done != 0) cudaGraphSetConditional(cond, 0);
 }
 
 __global__ void count_nonzero_kernel(const uint8_t* __restrict__ m, long long n,
@@ -781,6 +832,14 @@ __global__ void reset_sweep_state_kernel(int* __restrict__ state, int* __restric
         flag[threadIdx.x] = (threadIdx.x == 0 && skip) ? 4 : 0;   // 4: sequence skipped
     }
     if (threadIdx.x == 0) *tol_d = tol;
+}
+
+// Entry of a device loop: pass counter to 0 and the loop's condition to 1.  A
+// graph resets conditions to their default only when it is launched, so a
+// loop nested in another loop's body is re-armed here on every entry.
+__global__ void loop_begin_kernel(int* __restrict__ ctl, cudaGraphConditionalHandle cond) {
+    if (threadIdx.x < 4) ctl[threadIdx.x] = 0;
+    if (threadIdx.x == 0) cudaGraphSetConditional(cond, 1);
 }
 
 __global__ void loop_ctl_kernel(const int* __restrict__ flag, const int* __restrict__ state, int* __restrict__ ctl,
@@ -895,21 +954,34 @@ cudaError_t launch_prolong(int Hc, int Wc, int H, int W, int C, const float* uc,
 
 cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long uplane, const void* e, Store est,
                            int ep, long long eplane, const uint8_t* mask, int mp, const double* scale,
-                           cudaStream_t st) {
+                           cudaStream_t st, const void* e1, const int* sel, const int* skip) {
+    if (e1 == nullptr) e1 = e;
     switch (est) {
         case Store::F32:
             correct_kernel<float><<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(
-                H, W, u, up, uplane, static_cast<const float*>(e), ep, eplane, mask, mp, scale);
+                H, W, u, up, uplane, static_cast<const float*>(e), static_cast<const float*>(e1), sel, ep, eplane,
+                mask, mp, scale, skip);
             break;
         case Store::F16:
             correct_kernel<__half><<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(
-                H, W, u, up, uplane, static_cast<const __half*>(e), ep, eplane, mask, mp, scale);
+                H, W, u, up, uplane, static_cast<const __half*>(e), static_cast<const __half*>(e1), sel, ep, eplane,
+                mask, mp, scale, skip);
             break;
         case Store::BF16:
             correct_kernel<__nv_bfloat16><<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(
-                H, W, u, up, uplane, static_cast<const __nv_bfloat16*>(e), ep, eplane, mask, mp, scale);
+                H, W, u, up, uplane, static_cast<const __nv_bfloat16*>(e), static_cast<const __nv_bfloat16*>(e1), sel,
+                ep, eplane, mask, mp, scale, skip);
             break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ref_outer_ctl(const double2* res_out, const double* ref, int C, const double* tol, int max_corr,
+                                 int max_sweeps, const int* inner_state, const int* inner_ctl, int* ctl,
+                                 double* scale, double* scale_inv, double* inner_ref,
+                                 cudaGraphConditionalHandle cond, cudaStream_t st) {
+    ref_outer_ctl_kernel<<<1, 32, 0, st>>>(res_out, ref, C, tol, max_corr, max_sweeps, inner_state, inner_ctl, ctl,
+                                           scale, scale_inv, inner_ref, cond);
     return cudaGetLastError();
 }
 
@@ -1006,6 +1078,8 @@ cudaError_t launch_prolong_add(int Hc, int Wc, int H, int W, int C, const float*
                                                                     mp, u0, u1, sel_u, up, uplane, skip, v);
     return cudaGetLastError();
 }
+
+const void* loop_begin_kernel_fn() { return reinterpret_cast<const void*>(&loop_begin_kernel); }
 
 cudaError_t launch_loop_ctl(const int* flag, const int* state, int* ctl, int cap, int max_passes,
                             cudaGraphConditionalHandle cond, cudaStream_t st) {

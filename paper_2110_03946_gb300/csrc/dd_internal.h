@@ -162,6 +162,10 @@ cudaError_t launch_prolong_add(int Hc, int Wc, int H, int W, int C, const float*
 // whatever the solver kernels do.
 cudaError_t launch_loop_ctl(const int* flag, const int* state, int* ctl, int cap, int max_passes,
                             cudaGraphConditionalHandle cond, cudaStream_t st);
+// Kernel (one block of 32 threads, arguments (int* ctl, cudaGraphConditionalHandle
+// cond)) that zeroes ctl[0..3] and sets cond to 1: the first node of a device
+// loop, so that a loop nested in another loop's body is re-armed on every entry.
+const void* loop_begin_kernel_fn();
 
 // ---- auxiliary passes (aux.cu) ----------------------------------------------------
 // dst[c][y][x] (pitch dp) = mask ? src[c][y][x] : 0  (src pitch sp)
@@ -215,7 +219,14 @@ cudaError_t launch_prolong(int Hc, int Wc, int H, int W, int C, const float* uc,
 // u = fl32(u + s_c * e) on unknown pixels (FP64 arithmetic), e in storage `est`.
 cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long uplane, const void* e,
                            Store est, int ep, long long eplane, const uint8_t* mask, int mp,
-                           const double* scale, cudaStream_t st);
+                           const double* scale, cudaStream_t st, const void* e1 = nullptr,
+                           const int* sel = nullptr, const int* skip = nullptr);
+// The outer control of the device-driven FP64 correction loop (one thread, see
+// aux.cu): ctl[8] ints; clears cond when the loop ends.
+cudaError_t launch_ref_outer_ctl(const double2* res_out, const double* ref, int C, const double* tol, int max_corr,
+                                 int max_sweeps, const int* inner_state, const int* inner_ctl, int* ctl,
+                                 double* scale, double* scale_inv, double* inner_ref,
+                                 cudaGraphConditionalHandle cond, cudaStream_t st);
 // Store-typed copy from float with conversion (used to seed low-precision iterates).
 cudaError_t launch_convert(int H, int W, int C, const float* src, int sp, long long splane,
                            void* dst, Store dst_t, int dp, long long dplane, cudaStream_t st);

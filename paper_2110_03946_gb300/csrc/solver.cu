@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -154,6 +155,12 @@ struct dd_inpaint {
     int* corr_gate = nullptr;       // [0] skip this pass's correction, [1] corrections off
     double* corr_prev = nullptr;    // the fine residual at the previous pass
     cudaStream_t cap_stream = nullptr;   // private stream on which loop bodies are captured
+    cudaStream_t cap_stream2 = nullptr;  // ... and the bodies of loops nested in them
+    // device-driven FP64 correction loop (precision != FP32, device_loop = 1)
+    int* ref_ctl_d = nullptr;       // 8 ints, see ref_outer_ctl_kernel
+    double* ref_tol_d = nullptr;    // the solve's tolerance
+    int* h_ref_ctl = nullptr;       // pinned mirror (8 ints)
+    LoopGraph ref_loop;             // the outer loop as a graph of its own
     // pinned host mirrors
     double2* h_res = nullptr;
     double* h_small = nullptr;      // 3*C doubles scratch
@@ -555,25 +562,27 @@ int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st, bool count_work = fal
     return DD_OK;
 }
 
-// Add level L's loop to graph g after the nodes deps: a memset of the pass
-// counter, then the WHILE node whose body (one pass and the loop control) is
-// captured on the handle's private stream.  *last = the WHILE node.
-// The pass bound: CG applies an iteration in every pass; ORAS follows a failed
-// probe by a full sweep, so at most 2 cap + 1 passes reach cap full sweeps.
-int add_loop(dd_inpaint* h, Level& L, int cap, cudaGraph_t g, const cudaGraphNode_t* deps,
-             const cudaGraphEdgeData* edges, size_t ndeps, cudaGraphNode_t* last) {
-    if (h->prm.solver == DD_SOLVER_ORAS) DD_CK(dd::prepare_sweep(Store::F32, L.geom, false));
+// Add a device loop to graph g after the nodes deps: an entry kernel (pass
+// counter 0, condition 1), then a WHILE node whose body (pass(body_stream),
+// then the loop control) is captured on body_stream.  *last = the WHILE node.  The loop ends
+// when flag_d[0] is set, when sstate_d[1] reaches cap or after max_passes.
+int add_loop_fn(dd_inpaint* h, int cap, int max_passes, cudaGraph_t g, const cudaGraphNode_t* deps,
+                const cudaGraphEdgeData* edges, size_t ndeps, cudaStream_t body_stream,
+                const std::function<int(cudaStream_t)>& pass, cudaGraphNode_t* last) {
     cudaGraphConditionalHandle cond;
     DD_CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams mp{};
-    mp.type = cudaGraphNodeTypeMemset;
-    mp.memset.dst = h->ctl_d;
-    mp.memset.value = 0;
-    mp.memset.elementSize = sizeof(int);
-    mp.memset.width = 4;
-    mp.memset.height = 1;
+    // entry node: pass counter 0, condition 1 (re-armed on every entry when nested)
+    int* ctl = h->ctl_d;
+    void* kargs[2] = {&ctl, &cond};
+    cudaGraphNodeParams kp{};
+    kp.type = cudaGraphNodeTypeKernel;
+    kp.kernel.func = const_cast<void*>(dd::loop_begin_kernel_fn());
+    kp.kernel.gridDim = dim3(1, 1, 1);
+    kp.kernel.blockDim = dim3(32, 1, 1);
+    kp.kernel.sharedMemBytes = 0;
+    kp.kernel.kernelParams = kargs;
     cudaGraphNode_t reset = nullptr, loop = nullptr;
-    DD_CK(cudaGraphAddNode(&reset, g, deps, edges, ndeps, &mp));
+    DD_CK(cudaGraphAddNode(&reset, g, deps, edges, ndeps, &kp));
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = cond;
@@ -581,18 +590,52 @@ int add_loop(dd_inpaint* h, Level& L, int cap, cudaGraph_t g, const cudaGraphNod
     cp.conditional.size = 1;
     DD_CK(cudaGraphAddNode(&loop, g, &reset, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    DD_CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    const int max_passes = h->prm.solver == DD_SOLVER_CG ? cap + 1 : 2 * cap + 2;
-    const int rc = enqueue_pass(h, L, h->cap_stream);
+    DD_CK(cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const int rc = pass(body_stream);
     const cudaError_t el = rc == DD_OK ? dd::launch_loop_ctl(h->flag_d, h->sstate_d, h->ctl_d, cap, max_passes, cond,
-                                                             h->cap_stream)
+                                                             body_stream)
                                        : cudaSuccess;
     cudaGraph_t captured = body;
-    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &captured);
+    const cudaError_t ec = cudaStreamEndCapture(body_stream, &captured);
     if (rc != DD_OK) return rc;
     DD_CK(el);
     DD_CK(ec);
     *last = loop;
+    return DD_OK;
+}
+
+// Level L's loop (its sweeps or CG iterations).  The pass bound: CG applies an
+// iteration in every pass; ORAS follows a failed probe by a full sweep, so at
+// most 2 cap + 1 passes reach cap full sweeps.
+int add_loop(dd_inpaint* h, Level& L, int cap, cudaGraph_t g, const cudaGraphNode_t* deps,
+             const cudaGraphEdgeData* edges, size_t ndeps, cudaGraphNode_t* last) {
+    if (h->prm.solver == DD_SOLVER_ORAS) DD_CK(dd::prepare_sweep(Store::F32, L.geom, false));
+    const int max_passes = h->prm.solver == DD_SOLVER_CG ? cap + 1 : 2 * cap + 2;
+    return add_loop_fn(h, cap, max_passes, g, deps, edges, ndeps, h->cap_stream,
+                       [&](cudaStream_t bs) { return enqueue_pass(h, L, bs); }, last);
+}
+
+// Append nodes to the graph that st is capturing, after st's current
+// dependencies (add(graph, deps, edges, n, &last)); st then continues from last.
+int capture_append(cudaStream_t st, const std::function<int(cudaGraph_t, const cudaGraphNode_t*,
+                                                            const cudaGraphEdgeData*, size_t, cudaGraphNode_t*)>& add) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    DD_CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &edges, &nd));
+    if (cs != cudaStreamCaptureStatusActive) {
+        set_error("device loop: the stream is not capturing");
+        return DD_ECUDA;
+    }
+    // the arrays returned above are valid until the next capture call on st
+    std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+    std::vector<cudaGraphEdgeData> ev;
+    if (edges) ev.assign(edges, edges + nd);
+    cudaGraphNode_t last = nullptr;
+    DD_TRY(add(cg, dv.data(), edges ? ev.data() : nullptr, nd, &last));
+    DD_CK(cudaStreamUpdateCaptureDependencies(st, &last, nullptr, 1, cudaStreamSetCaptureDependencies));
     return DD_OK;
 }
 
@@ -623,23 +666,8 @@ int loop_graph(dd_inpaint* h, Level& L, int cap, cudaGraphExec_t* out) {
 // dd_batch graph) the loop's nodes join the graph being captured.
 int run_loop(dd_inpaint* h, Level& L, int cap, cudaStream_t st, bool capture) {
     if (cap > 0 && capture) {   // (a WHILE body runs at least once)
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        cudaGraph_t cg = nullptr;
-        const cudaGraphNode_t* deps = nullptr;
-        const cudaGraphEdgeData* edges = nullptr;
-        size_t nd = 0;
-        DD_CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &edges, &nd));
-        if (cs != cudaStreamCaptureStatusActive) {
-            set_error("device loop: the stream is not capturing");
-            return DD_ECUDA;
-        }
-        // the arrays returned above are valid until the next capture call on st
-        std::vector<cudaGraphNode_t> dv(deps, deps + nd);
-        std::vector<cudaGraphEdgeData> ev;
-        if (edges) ev.assign(edges, edges + nd);
-        cudaGraphNode_t last = nullptr;
-        DD_TRY(add_loop(h, L, cap, cg, dv.data(), edges ? ev.data() : nullptr, nd, &last));
-        DD_CK(cudaStreamUpdateCaptureDependencies(st, &last, nullptr, 1, cudaStreamSetCaptureDependencies));
+        DD_TRY(capture_append(st, [&](cudaGraph_t cg, const cudaGraphNode_t* d, const cudaGraphEdgeData* e, size_t n,
+                                      cudaGraphNode_t* last) { return add_loop(h, L, cap, cg, d, e, n, last); }));
     } else if (cap > 0) {
         cudaGraphExec_t ex = nullptr;
         DD_TRY(loop_graph(h, L, cap, &ex));
@@ -926,10 +954,203 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
     return converged ? DD_OK : DD_ENOTCONVERGED;
 }
 
+// ---- device-driven FP64 correction loop (precision != FP32, device_loop = 1) ----------
+// One inner pass: a sweep of the correction equation A e = g_hat on the fine
+// level in the low storage type, from the e buffer the device state names.
+int ref_pass(dd_inpaint* h, cudaStream_t st) {
+    Level& F = h->lv[0];
+    const dd::SweepPair pair{{&h->map_e[0], &h->map_e[1]}, {h->e[0], h->e[1]}};
+    const double stall = h->lowst == Store::F32 ? 0.0 : 0.7;
+    const dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, h->inner_ref_d, h->tol_d, stall, h->flag_d,
+                             h->sstate_d, 0};
+    DD_CK(dd::launch_sweep(h->lowst, F.geom, h->C, F.plane(), pair, &h->map_g, F.tmask, stop, h->prm.robin_p,
+                           h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
+    return DD_OK;
+}
+
+// The outer loop (WHILE node) of the correction scheme, added to g after deps.
+// Its body, captured on cap_stream, is one correction:
+//   res64(u) -> ref_outer_ctl (stop, or the scales of this correction) ->
+//   scaled residual g_hat in the low type -> e = 0 -> the inner sweeps as a
+//   nested device loop (bodies on cap_stream2) to inner_tol ->
+//   u += scale * e (FP64 arithmetic);
+// every step after the control is skipped once the loop has ended.
+int add_ref_outer(dd_inpaint* h, cudaGraph_t g, const cudaGraphNode_t* deps, const cudaGraphEdgeData* edges,
+                  size_t ndeps, cudaGraphNode_t* last) {
+    Level& F = h->lv[0];
+    DD_CK(dd::prepare_sweep(h->lowst, F.geom, true));
+    cudaGraphConditionalHandle cond;
+    DD_CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop = nullptr;
+    DD_CK(cudaGraphAddNode(&loop, g, deps, edges, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t bs = h->cap_stream;
+    DD_CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const int* skip = h->ref_ctl_d + 5;
+    auto steps = [&]() -> int {
+        dd::Res64Args a{};
+        a.H = F.H; a.W = F.W; a.C = h->C;
+        a.u = F.u[0]; a.up = F.P; a.uplane = F.plane();
+        a.mask = F.mask; a.mp = F.W;
+        a.g_out = nullptr; a.gst = Store::F32;
+        a.part = h->res_part; a.nblk = h->res_nblk;
+        a.out = h->res_out; a.ticket = h->res_ticket;
+        DD_CK(dd::launch_res64(a, bs));
+        DD_CK(dd::launch_ref_outer_ctl(h->res_out, F.ref_d, h->C, h->ref_tol_d, h->prm.max_corrections,
+                                       h->prm.max_sweeps, h->sstate_d, h->ctl_d, h->ref_ctl_d, h->scale_d,
+                                       h->scale_inv_d, h->inner_ref_d, cond, bs));
+        dd::Res64Args b{};
+        b.H = F.H; b.W = F.W; b.C = h->C;
+        b.u = F.u[0]; b.up = F.P; b.uplane = F.plane();
+        b.mask = F.mask; b.mp = F.W;
+        b.g_out = h->g; b.gst = h->lowst; b.gp = F.P; b.gplane = F.plane();
+        b.scale_inv = h->scale_inv_d;
+        b.part = h->res_part; b.nblk = h->res_nblk;
+        b.skip = skip;
+        DD_CK(dd::launch_res64(b, bs));
+        DD_CK(cudaMemsetAsync(h->e[0], 0, dd::store_bytes(h->lowst) * (size_t)h->C * F.plane(), bs));
+        DD_CK(dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, h->tol_d, h->prm.inner_tol, bs, skip));
+        const int cap = h->prm.max_sweeps;
+        DD_TRY(capture_append(bs, [&](cudaGraph_t cg, const cudaGraphNode_t* d, const cudaGraphEdgeData* e, size_t n,
+                                      cudaGraphNode_t* l) {
+            return add_loop_fn(h, cap, 2 * cap + 2, cg, d, e, n, h->cap_stream2,
+                               [&](cudaStream_t s2) { return ref_pass(h, s2); }, l);
+        }));
+        DD_CK(dd::launch_correct(F.H, F.W, h->C, F.u[0], F.P, F.plane(), h->e[0], h->lowst, F.P, F.plane(), F.mask,
+                                 F.W, h->scale_d, bs, h->e[1], h->sstate_d, skip));
+        return DD_OK;
+    };
+    const int rc = steps();
+    cudaGraph_t captured = body;
+    const cudaError_t ec = cudaStreamEndCapture(bs, &captured);
+    if (rc != DD_OK) return rc;
+    DD_CK(ec);
+    *last = loop;
+    return DD_OK;
+}
+
+// The outer loop as a graph of its own (built when the handle is created).
+int ref_graph(dd_inpaint* h, cudaGraphExec_t* out) {
+    LoopGraph& G = h->ref_loop;
+    if (G.exec != nullptr) {
+        *out = G.exec;
+        return DD_OK;
+    }
+    destroy_loop(G);
+    DD_CK(cudaGraphCreate(&G.graph, 0));
+    cudaGraphNode_t last = nullptr;
+    const int rc = add_ref_outer(h, G.graph, nullptr, nullptr, 0, &last);
+    if (rc != DD_OK) {
+        destroy_loop(G);
+        return rc;
+    }
+    DD_CK(cudaGraphInstantiate(&G.exec, G.graph, 0));
+    *out = G.exec;
+    return DD_OK;
+}
+
+// Correction modes, part 1: the cascade, the whole correction loop on the
+// device, the output copy and the read-back of everything the host needs.
+// No host synchronisation.
+int ref_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool capture) {
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    h->stats.channels = h->C;
+    h->stats.device_bytes = h->bytes;
+    const int nl = (int)h->lv.size();
+    Level& F = h->lv[0];
+    h->ev_recorded = !capture;
+    if (!capture) DD_CK(cudaEventRecord(h->ev0, st));
+    h->pending_cascaded = !h->warm;
+    if (!h->warm) {
+        DD_TRY(cascade(h, st, capture));
+    } else if (h->cur != 0) {
+        DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[1], F.P, F.plane(), F.u[0], F.P, F.plane(), st));
+        h->cur = 0;
+    }
+    h->warm = false;
+    // ref_ctl[0..7] = 0 and the tolerance (the sweep-state reset kernel on the control words)
+    DD_LAUNCH(h, dd::launch_reset_sweep_state(h->ref_ctl_d, h->ref_ctl_d + 4, 0, h->ref_tol_d, tol, st));
+    if (capture) {
+        DD_TRY(capture_append(st, [&](cudaGraph_t cg, const cudaGraphNode_t* d, const cudaGraphEdgeData* e, size_t n,
+                                      cudaGraphNode_t* l) { return add_ref_outer(h, cg, d, e, n, l); }));
+    } else {
+        cudaGraphExec_t ex = nullptr;
+        DD_TRY(ref_graph(h, &ex));
+        DD_CK(cudaGraphLaunch(ex, st));
+    }
+    DD_LAUNCH(h, dd::launch_copy2d(F.H, F.W, h->C, F.u[0], F.P, F.plane(), u_out, F.W, (long long)F.H * F.W, st));
+    DD_CK(cudaMemcpyAsync(h->h_res, h->res_out, sizeof(double2) * h->C, cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_ref_ctl, h->ref_ctl_d, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    for (int l = 1; l < nl; ++l)
+        DD_CK(cudaMemcpyAsync(h->h_state + 4 * l, h->lv[l].state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_ref, F.ref_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if (!capture) DD_CK(cudaEventRecord(h->ev1, st));
+    h->pending = true;
+    h->pending_out = u_out;
+    h->pending_tol = tol;
+    return DD_OK;
+}
+
+// Correction modes, part 2: wait, read the outcome and the statistics.
+int ref_finish(dd_inpaint* h, cudaStream_t st) {
+    if (!h->pending) { set_error("no solve in flight"); return DD_EINVAL; }
+    h->pending = false;
+    Level& F = h->lv[0];
+    if (h->ev_recorded) DD_CK(cudaEventSynchronize(h->ev1));
+    else DD_CK(cudaStreamSynchronize(st));
+    h->local_unknowns = (long long)h->h_cnt[0];
+    h->stats.local_unknowns = h->local_unknowns;
+    if (h->counts_pending) {
+        h->counts_pending = false;
+        if (h->h_cnt[1] == 0) { h->valid = false; set_error("empty mask"); return DD_EEMPTYMASK; }
+    }
+    F.ref.assign(h->h_ref, h->h_ref + h->C);
+    if (h->h_flag[2] != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
+    if (h->pending_cascaded) take_level_stats(h);
+    count_loop_launches(h);
+    const int* c = h->h_ref_ctl;
+    // per outer pass: residual, control, scaled residual, reset, correction;
+    // per inner pass: the sweep and the loop control
+    h->launches += 5LL * c[3] + 2LL * c[4];
+    h->stats.corrections = c[0];
+    h->stats.sweeps_per_level[0] = c[1];
+    h->stats.sweeps_total += c[1];
+    std::vector<double> rel, rmax, rnorm;
+    if (c[2] == 3) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
+    DD_TRY(rel_from_h_res(h, rel, rmax, rnorm));
+    const bool converged = c[2] == 1;
+    h->stats.converged = converged ? 1 : 0;
+    for (int ch = 0; ch < h->C && ch < DD_MAX_STAT_CHANNELS; ++ch) h->stats.rel_residual[ch] = rel[ch];
+    if (h->ev_recorded) {
+        float ms = 0.f;
+        if (cudaEventQuery(h->ev1) == cudaSuccess) DD_CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        h->stats.ms_total = ms;
+    }
+    h->stats.kernel_launches = h->launches;
+    return converged ? DD_OK : DD_ENOTCONVERGED;
+}
+
+// The solve as an enqueue (no host synchronisation) and a finish, for every
+// precision: FP32 iterate, or the device-driven correction loop.
+bool device_ref(const dd_inpaint* h) { return h->prm.precision != DD_PREC_FP32 && h->prm.device_loop != 0; }
+
+int enqueue_solve(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool capture) {
+    return device_ref(h) ? ref_enqueue(h, u_out, tol, st, capture) : fp32_enqueue(h, u_out, tol, st, capture);
+}
+
+int finish_solve(dd_inpaint* h, cudaStream_t st) { return device_ref(h) ? ref_finish(h, st) : fp32_finish(h, st); }
+
 int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
-    if (h->prm.precision == DD_PREC_FP32) {
-        DD_TRY(fp32_enqueue(h, u_out, tol, st, false));
-        return fp32_finish(h, st);
+    if (h->prm.precision == DD_PREC_FP32 || device_ref(h)) {
+        DD_TRY(enqueue_solve(h, u_out, tol, st, false));
+        return finish_solve(h, st);
     }
     if (h->counts_pending) {   // data loaded asynchronously: check it before the correction loop
         DD_CK(cudaStreamSynchronize(st));
@@ -1014,7 +1235,10 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
 
 void free_all(dd_inpaint* h) {
     for (Level& L : h->lv) destroy_loop(L.loop);
+    destroy_loop(h->ref_loop);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+    if (h->h_ref_ctl) cudaFreeHost(h->h_ref_ctl);
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->h_res) cudaFreeHost(h->h_res);
@@ -1147,6 +1371,12 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if ((rc = dalloc_t(h, &h->tol_d, 1)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->res_ticket, 1)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->work_d, 2)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->ref_ctl_d, 8)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->ref_tol_d, 1)) != DD_OK) return fail(rc);
+    if (cudaMallocHost(&h->h_ref_ctl, 8 * sizeof(int)) != cudaSuccess) {
+        set_error("cudaMallocHost failed");
+        return fail(DD_ENOMEM);
+    }
     if (cudaMallocHost(&h->h_work, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         return fail(DD_ENOMEM);
@@ -1155,7 +1385,8 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         set_error("cudaMemset");
         return fail(DD_ECUDA);
     }
-    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking) != cudaSuccess) {
         set_error("cudaStreamCreateWithFlags failed");
         return fail(DD_ECUDA);
     }
@@ -1186,6 +1417,10 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
             if (l == 0 && p.precision != DD_PREC_FP32) continue;
             cudaGraphExec_t ex = nullptr;
             if ((rc = loop_graph(h, h->lv[l], l == 0 ? p.max_sweeps : p.coarse_sweeps, &ex)) != DD_OK) return fail(rc);
+        }
+        if (p.precision != DD_PREC_FP32) {   // the correction loop with its nested inner loop
+            cudaGraphExec_t ex = nullptr;
+            if ((rc = ref_graph(h, &ex)) != DD_OK) return fail(rc);
         }
     }
     *out = h;
@@ -1318,10 +1553,13 @@ int dd_inpaint_set_data_async(dd_handle h, const uint8_t* mask, const float* val
 
 int dd_inpaint_solve_async(dd_handle h, float* u_out, double tol, void* stream) {
     if (!h || !u_out || !(tol > 0.0)) { set_error("bad solve arguments"); return DD_EINVAL; }
-    if (h->prm.precision != DD_PREC_FP32) { set_error("asynchronous solves need precision DD_PREC_FP32"); return DD_EINVAL; }
+    if (h->prm.precision != DD_PREC_FP32 && !device_ref(h)) {
+        set_error("asynchronous correction-mode solves need device_loop = 1");
+        return DD_EINVAL;
+    }
     if (h->pending) { set_error("a solve is already in flight"); return DD_EINVAL; }
     if (!h->valid) { set_error("no valid data (the last set_data failed)"); return DD_EEMPTYMASK; }
-    return fp32_enqueue(h, u_out, tol, static_cast<cudaStream_t>(stream), false);
+    return enqueue_solve(h, u_out, tol, static_cast<cudaStream_t>(stream), false);
 }
 
 int dd_inpaint_query(dd_handle h) {
@@ -1336,7 +1574,7 @@ int dd_inpaint_query(dd_handle h) {
 
 int dd_inpaint_solve_finish(dd_handle h, void* stream) {
     if (!h) { set_error("NULL argument"); return DD_EINVAL; }
-    return fp32_finish(h, static_cast<cudaStream_t>(stream));
+    return finish_solve(h, static_cast<cudaStream_t>(stream));
 }
 
 int dd_inpaint_set_iterate(dd_handle h, const float* u, void* stream) {
@@ -1487,7 +1725,10 @@ int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
         if (!handles[i] || !u_out[i]) { set_error("NULL handle or output"); return DD_EINVAL; }
-        if (handles[i]->prm.precision != DD_PREC_FP32) { set_error("batches need precision DD_PREC_FP32"); return DD_EINVAL; }
+        if (handles[i]->prm.precision != DD_PREC_FP32 && !device_ref(handles[i])) {
+            set_error("batches of correction-mode handles need device_loop = 1");
+            return DD_EINVAL;
+        }
         if (handles[i]->pending) { set_error("a handle has a solve in flight"); return DD_EINVAL; }
         for (int j = 0; j < i; ++j)
             if (handles[j] == handles[i]) { set_error("a handle appears twice"); return DD_EINVAL; }
@@ -1520,7 +1761,7 @@ int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double
     for (int i = 0; i < n && rc == DD_OK; ++i) {
         if (cudaStreamWaitEvent(b->side[i], b->evs[2 * n], 0) != cudaSuccess) { rc = DD_ECUDA; break; }
         b->hs[i]->warm = false;   // a captured solve always starts with the cascade
-        rc = fp32_enqueue(b->hs[i], b->outs[i], tol, b->side[i], true);
+        rc = enqueue_solve(b->hs[i], b->outs[i], tol, b->side[i], true);
         b->hs[i]->pending = false;
         if (rc == DD_OK && cudaEventRecord(b->evs[2 * i], b->side[i]) != cudaSuccess) rc = DD_ECUDA;
         if (rc == DD_OK && cudaStreamWaitEvent(b->cap, b->evs[2 * i], 0) != cudaSuccess) rc = DD_ECUDA;
@@ -1576,7 +1817,7 @@ int dd_batch_finish(dd_batch_handle b, void* stream, int* status) {
     DD_CK(cudaEventSynchronize(b->done));
     int worst = DD_OK;
     for (size_t i = 0; i < b->hs.size(); ++i) {
-        const int rc = fp32_finish(b->hs[i], static_cast<cudaStream_t>(stream));
+        const int rc = finish_solve(b->hs[i], static_cast<cudaStream_t>(stream));
         if (status) status[i] = rc;
         if (rc != DD_OK && worst == DD_OK) worst = rc;
     }

@@ -99,9 +99,72 @@ def test_batch_graph_matches_independent_solves():
 
 def test_batch_rejects_bad_input():
     f, m = synth.make_frame(64, 64, 1, 0.05, "uniform", 4)
-    with Inpainter(m, f, precision="fp16_ref") as ip16, Inpainter(m, f, **PRM) as ip:
+    with Inpainter(m, f, precision="fp16_ref", device_loop=0) as ip16, Inpainter(m, f, **PRM) as ip:
         o = torch.empty((1, 64, 64), dtype=torch.float32, device=DEV)
+        # the host-driven correction loop cannot be captured
         rc, b, _ = B.dd_batch_create([ip16._h], [o.data_ptr()], 1e-6)
         assert rc == B.DD_EINVAL and not b.value
         rc, b, _ = B.dd_batch_create([ip._h, ip._h], [o.data_ptr(), o.data_ptr()], 1e-6)
         assert rc == B.DD_EINVAL
+
+
+PRM16 = dict(block=32, overlap=4, local_cg_iters=18, local_rtol=0.05, levels=3, coarse_tol=3e-3, precision="fp16_ref")
+
+
+def test_mixed_precision_async_and_batch():
+    """FP16 inner storage with the FP64-accurate outer correction, driven on the
+    device: asynchronous solves on several streams and a batch graph give the
+    synchronous solve's result bit for bit, within tolerance of the oracle."""
+    frames = _frames(1000)
+    sync = []
+    for f, m in frames:
+        with Inpainter(m, f, **PRM16) as ip:
+            sync.append(ip.solve(1e-6).cpu().numpy())
+            st = ip.stats()
+            assert st["converged"] and st["corrections"] >= 1
+    ips = [Inpainter(m, f, **PRM16) for f, m in frames]
+    streams = [torch.cuda.Stream(DEV) for _ in frames]
+    outs = [torch.empty(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames]
+    try:
+        for ip, s, o in zip(ips, streams, outs):
+            B.check(B.dd_inpaint_solve_async(ip._h, o.data_ptr(), 1e-6, s), "solve_async")
+        for ip, s in zip(ips, streams):
+            B.check(B.dd_inpaint_solve_finish(ip._h, s), "finish")
+        for (f, m), o, u0 in zip(frames, outs, sync):
+            u = o.cpu().numpy()
+            assert np.array_equal(u, u0)
+            assert np.max(np.abs(u - ref.solve_direct(f, m))) <= TOL_U
+            assert np.all(ref.rel_residual(u.astype(np.float64), f, m) <= 1e-6)
+        rc, b, _ = B.dd_batch_create([ip._h for ip in ips], [o.data_ptr() for o in outs], 1e-6)
+        B.check(rc, "dd_batch_create")
+        try:
+            for o in outs:
+                o.zero_()
+            stream = torch.cuda.current_stream(DEV)
+            B.check(B.dd_batch_launch(b, stream), "dd_batch_launch")
+            rc, status = B.dd_batch_finish(b, len(ips), stream)
+            assert rc == B.DD_OK and all(sc == B.DD_OK for sc in status)
+            for o, u0 in zip(outs, sync):
+                assert np.array_equal(o.cpu().numpy(), u0)
+        finally:
+            B.dd_batch_destroy(b)
+    finally:
+        for ip in ips:
+            ip.close()
+
+
+@pytest.mark.parametrize("precision", ["fp16_ref", "bf16_ref", "fp32_ref"])
+def test_correction_loop_on_device_and_on_host(precision):
+    """The device-driven correction loop and the host-driven one both reach the
+    tolerance and the oracle's solution."""
+    f, m = synth.make_frame(150, 210, 3, 0.04, "edge", 1101)
+    exact = ref.solve_direct(f, m)
+    for loop in (1, 0):
+        with Inpainter(m, f, **dict(PRM16, precision=precision, device_loop=loop)) as ip:
+            u = ip.solve(1e-6).cpu().numpy()
+            st = ip.stats()
+        assert st["converged"]
+        assert np.max(np.abs(u - exact)) <= TOL_U
+        assert np.all(ref.rel_residual(u.astype(np.float64), f, m) <= 1e-6)
+        assert np.array_equal(u[:, m != 0], f[:, m != 0].astype(np.float32))
+
