@@ -37,14 +37,6 @@ __global__ void reset_known_kernel(int H, int W, float* __restrict__ u, int up, 
     if (mask[(size_t)y * mp + x]) u[c * uplane + (size_t)y * up + x] = f[c * fplane + (size_t)y * fp + x];
 }
 
-template <typename T>
-__global__ void convert_kernel(int H, int W, const float* __restrict__ src, int sp, long long splane,
-                               T* __restrict__ dst, int dp, long long dplane) {
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
-    if (x >= W || y >= H) return;
-    dst[c * dplane + (size_t)y * dp + x] = from_f<T>(src[c * splane + (size_t)y * sp + x]);
-}
-
 // ---- residual of the outer correction -----------------------------------------------
 // r = b - A u on unknown pixels, i.e. r_p = sum over in-image neighbours q of
 // (u_q - u_p) for an FP32 iterate u.  GB300 executes FP64 at a small fraction
@@ -304,27 +296,6 @@ __global__ void __launch_bounds__(V_TPB) masked_copy_kernel(int H, int W, const 
     }
 }
 
-// dst = (sel[0] ? s1 : s0), the buffer chosen on the device
-__global__ void __launch_bounds__(V_TPB) copy2d_sel_kernel(int H, int W, const float* __restrict__ s0,
-                                                           const float* __restrict__ s1, const int* __restrict__ sel,
-                                                           int sp, long long splane, float* __restrict__ dst, int dp,
-                                                           long long dplane, CopyVec vec) {
-    const int c = blockIdx.z;
-    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
-    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
-    if (x0 >= W) return;
-    const float* __restrict__ s = (sel[0] ? s1 : s0) + c * splane;
-    float* __restrict__ d = dst + c * dplane;
-#pragma unroll
-    for (int k = 0; k < V_ROWS; ++k) {
-        const int y = yb + k;
-        if (y >= H) break;
-        float v[4];
-        ld4(s + (size_t)y * sp, x0, W, vec.src, v);
-        st4(d + (size_t)y * dp, x0, W, vec.dst, v);
-    }
-}
-
 // Bilinear cell-centred prolongation of the coarse iterate (Sec. 4) on
 // unknown pixels, f on known ones (mask may be null: everywhere bilinear).
 // The coarse source is sel[0] ? uc1 : uc0 (sel may be null: uc0).
@@ -476,56 +447,6 @@ __global__ void __launch_bounds__(V_TPB) restrict_sum_kernel(int H, int W, int H
             acc[3] += b4[2] + b4[3];
         }
         st4(dst + c * dplane + (size_t)Y * dp, X0, Wc, vec.dst, acc);
-    }
-}
-
-// u (the buffer sel_u[0] names) += cell-centred bilinear prolongation of the
-// coarse correction (the buffer sel_c[0] names; sel_c may be null), on unknown
-// fine pixels.  No-op if *skip != 0.
-__global__ void __launch_bounds__(V_TPB) prolong_add_kernel(int Hc, int Wc, int H, int W, const float* __restrict__ ec0,
-                                                            const float* __restrict__ ec1, const int* __restrict__ sel_c,
-                                                            int ecp, long long ecplane, const uint8_t* __restrict__ mask,
-                                                            int mp, float* __restrict__ u0, float* __restrict__ u1,
-                                                            const int* __restrict__ sel_u, int up, long long uplane,
-                                                            const int* __restrict__ skip, CopyVec vec) {
-    if (skip != nullptr && *skip != 0) return;
-    const int c = blockIdx.z;
-    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
-    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
-    if (x0 >= W) return;
-    const float* __restrict__ p = ((sel_c != nullptr && sel_c[0]) ? ec1 : ec0) + c * ecplane;
-    float* __restrict__ u = (sel_u[0] ? u1 : u0) + c * uplane;
-    int xa[4], xb[4];
-    float wx[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float tx = fminf(fmaxf((x0 + j - 0.5f) * 0.5f, 0.f), (float)(Wc - 1));
-        xa[j] = (int)floorf(tx);
-        xb[j] = min(xa[j] + 1, Wc - 1);
-        wx[j] = tx - (float)xa[j];
-    }
-#pragma unroll
-    for (int k = 0; k < V_ROWS; ++k) {
-        const int y = yb + k;
-        if (y >= H) break;
-        const float ty = fminf(fmaxf((y - 0.5f) * 0.5f, 0.f), (float)(Hc - 1));
-        const int ya = (int)floorf(ty), yb1 = min(ya + 1, Hc - 1);
-        const float wy = ty - (float)ya;
-        const float* __restrict__ ra = p + (size_t)ya * ecp;
-        const float* __restrict__ rb = p + (size_t)yb1 * ecp;
-        bool m[4];
-        ldm4(mask + (size_t)y * mp, x0, W, vec.m, m);
-        float v[4];
-        ld4(u + (size_t)y * up, x0, W, vec.dst, v);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!m[j] && x0 + j < W) {
-                const float top = ra[xa[j]] * (1.f - wx[j]) + ra[xb[j]] * wx[j];
-                const float bot = rb[xa[j]] * (1.f - wx[j]) + rb[xb[j]] * wx[j];
-                v[j] += top * (1.f - wy) + bot * wy;
-            }
-        }
-        st4(u + (size_t)y * up, x0, W, vec.dst, v);
     }
 }
 
@@ -850,11 +771,6 @@ __global__ void loop_ctl_kernel(const int* __restrict__ flag, const int* __restr
     if (flag[0] != 0 || state[1] >= cap || passes >= max_passes) cudaGraphSetConditional(cond, 0);
 }
 
-__global__ void sqrt_sums_kernel(const double2* __restrict__ in, double* __restrict__ out, int C) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < C) out[c] = sqrt(in[c].x);
-}
-
 }  // namespace
 
 cudaError_t launch_masked_copy(int H, int W, int C, const float* src, int sp, long long splane,
@@ -881,25 +797,6 @@ cudaError_t launch_fill_zero(Store s, void* dst, size_t n, cudaStream_t st) {
 cudaError_t launch_reset_known(int H, int W, int C, float* u, int up, long long uplane, const uint8_t* mask,
                                int mp, const float* f, int fp, long long fplane, cudaStream_t st) {
     reset_known_kernel<<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(H, W, u, up, uplane, mask, mp, f, fp, fplane);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_convert(int H, int W, int C, const float* src, int sp, long long splane, void* dst,
-                           Store t, int dp, long long dplane, cudaStream_t st) {
-    switch (t) {
-        case Store::F32:
-            convert_kernel<float><<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(H, W, src, sp, splane,
-                                                                             static_cast<float*>(dst), dp, dplane);
-            break;
-        case Store::F16:
-            convert_kernel<__half><<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(H, W, src, sp, splane,
-                                                                              static_cast<__half*>(dst), dp, dplane);
-            break;
-        case Store::BF16:
-            convert_kernel<__nv_bfloat16><<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(
-                H, W, src, sp, splane, static_cast<__nv_bfloat16*>(dst), dp, dplane);
-            break;
-    }
     return cudaGetLastError();
 }
 
@@ -1069,16 +966,6 @@ cudaError_t launch_corr_step(int H, int W, int C, const float* d, int dp, long l
     return cudaGetLastError();
 }
 
-cudaError_t launch_prolong_add(int Hc, int Wc, int H, int W, int C, const float* ec0, const float* ec1,
-                               const int* sel_c, int ecp, long long ecplane, const uint8_t* mask, int mp, float* u0,
-                               float* u1, const int* sel_u, int up, long long uplane, const int* skip,
-                               cudaStream_t st) {
-    const CopyVec v{false, vec_ok(u0, up, uplane, 4) && vec_ok(u1, up, uplane, 4), vec_ok(mask, mp, 0, 1)};
-    prolong_add_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(Hc, Wc, H, W, ec0, ec1, sel_c, ecp, ecplane, mask,
-                                                                    mp, u0, u1, sel_u, up, uplane, skip, v);
-    return cudaGetLastError();
-}
-
 const void* loop_begin_kernel_fn() { return reinterpret_cast<const void*>(&loop_begin_kernel); }
 
 cudaError_t launch_loop_ctl(const int* flag, const int* state, int* ctl, int cap, int max_passes,
@@ -1094,19 +981,6 @@ cudaError_t launch_prolong_sel(int Hc, int Wc, int H, int W, int C, const float*
     const CopyVec v{vec_ok(f, fp, fplane, 4), vec_ok(u, up, uplane, 4), vec_ok(mask, mp, 0, 1)};
     prolong_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(Hc, Wc, H, W, uc0, uc1, sel, ucp, ucplane, mask,
                                                                 mp, f, fp, fplane, u, up, uplane, v);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_copy2d_sel(int H, int W, int C, const float* s0, const float* s1, const int* sel, int sp,
-                              long long splane, float* dst, int dp, long long dplane, cudaStream_t st) {
-    const CopyVec v{vec_ok(s0, sp, splane, 4) && vec_ok(s1, sp, splane, 4), vec_ok(dst, dp, dplane, 4), false};
-    copy2d_sel_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(H, W, s0, s1, sel, sp, splane, dst, dp, dplane,
-                                                                   v);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sqrt_sums(const double2* in, double* out, int C, cudaStream_t st) {
-    sqrt_sums_kernel<<<(C + 127) / 128, 128, 0, st>>>(in, out, C);
     return cudaGetLastError();
 }
 

@@ -148,13 +148,6 @@ cudaError_t launch_corr_curv(int H, int W, int C, const float* d, int dp, long l
 cudaError_t launch_corr_step(int H, int W, int C, const float* d, int dp, long long dplane, const double* omega,
                              float* u0, float* u1, const int* sel_u, int up, long long uplane, const int* skip,
                              cudaStream_t st);
-// (sel_u[0] ? u1 : u0) += bilinear prolongation of (sel_c && sel_c[0] ? ec1 : ec0)
-// on pixels with mask == 0.
-cudaError_t launch_prolong_add(int Hc, int Wc, int H, int W, int C, const float* ec0, const float* ec1,
-                               const int* sel_c, int ecp, long long ecplane, const uint8_t* mask, int mp, float* u0,
-                               float* u1, const int* sel_u, int up, long long uplane, const int* skip,
-                               cudaStream_t st);
-
 // Loop control at the end of each pass of a graph WHILE loop (one thread):
 // ctl[0] counts the passes; the loop's condition is cleared when flag[0] != 0
 // (stopped, converged or failed), when state[1] (full sweeps or CG iterations
@@ -175,7 +168,7 @@ cudaError_t launch_masked_copy(int H, int W, int C, const float* src, int sp, lo
 // plain strided copy (float)
 cudaError_t launch_copy2d(int H, int W, int C, const float* src, int sp, long long splane,
                           float* dst, int dp, long long dplane, cudaStream_t st);
-// convert between storage types / set: dst (Store) = (float)src, or zero
+// zero n elements of storage type s
 cudaError_t launch_fill_zero(Store s, void* dst, size_t n, cudaStream_t st);
 // dst = keep known: u[c][y][x] = mask ? f : u   (float, pitched)
 cudaError_t launch_reset_known(int H, int W, int C, float* u, int up, long long uplane,
@@ -227,10 +220,6 @@ cudaError_t launch_ref_outer_ctl(const double2* res_out, const double* ref, int 
                                  int max_sweeps, const int* inner_state, const int* inner_ctl, int* ctl,
                                  double* scale, double* scale_inv, double* inner_ref,
                                  cudaGraphConditionalHandle cond, cudaStream_t st);
-// Store-typed copy from float with conversion (used to seed low-precision iterates).
-cudaError_t launch_convert(int H, int W, int C, const float* src, int sp, long long splane,
-                           void* dst, Store dst_t, int dp, long long dplane, cudaStream_t st);
-
 // Summary of a sweep sequence for later steps: out[0] = buffer holding the
 // result, out[1] = full sweeps applied, out[2] = the stop flag (0: not
 // stopped, 1: converged, 2: NaN/Inf, 3: stalled), out[3] = passes of the
@@ -241,13 +230,8 @@ cudaError_t launch_prolong_sel(int Hc, int Wc, int H, int W, int C, const float*
                                const int* sel, int ucp, long long ucplane, const uint8_t* mask, int mp,
                                const float* f, int fp, long long fplane, float* u, int up, long long uplane,
                                cudaStream_t st);
-cudaError_t launch_copy2d_sel(int H, int W, int C, const float* s0, const float* s1, const int* sel, int sp,
-                              long long splane, float* dst, int dp, long long dplane, cudaStream_t st);
 // *out += number of nonzero bytes of m[0..n)
 cudaError_t launch_count_nonzero(const uint8_t* m, long long n, unsigned long long* out, cudaStream_t st);
-// out[c] = sqrt(in[c].x)
-cudaError_t launch_sqrt_sums(const double2* in, double* out, int C, cudaStream_t st);
-
 // ---- conjugate gradients on the whole image (cg.cu) ---------------------------------
 struct CGArgs {
     int H, W, P, C, mp;
