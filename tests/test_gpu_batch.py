@@ -168,3 +168,43 @@ def test_correction_loop_on_device_and_on_host(precision):
         assert np.all(ref.rel_residual(u.astype(np.float64), f, m) <= 1e-6)
         assert np.array_equal(u[:, m != 0], f[:, m != 0].astype(np.float32))
 
+
+def test_correction_mode_async_and_batch():
+    """DD_ML_CORRECTION passes (fine sweep + coarse-grid correction) inside the
+    device loops: asynchronous solves and a batch graph give the synchronous
+    result bit for bit."""
+    prm = dict(PRM, ml_mode="correction", correction_sweeps=2, levels=3)
+    frames = _frames(1200)
+    sync = []
+    for f, m in frames:
+        with Inpainter(m, f, **prm) as ip:
+            sync.append(ip.solve(1e-6).cpu().numpy())
+            assert ip.stats()["converged"]
+    ips = [Inpainter(m, f, **prm) for f, m in frames]
+    streams = [torch.cuda.Stream(DEV) for _ in frames]
+    outs = [torch.empty(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames]
+    try:
+        for ip, s, o in zip(ips, streams, outs):
+            B.check(B.dd_inpaint_solve_async(ip._h, o.data_ptr(), 1e-6, s), "solve_async")
+        for ip, s in zip(ips, streams):
+            B.check(B.dd_inpaint_solve_finish(ip._h, s), "finish")
+        for (f, m), o, u0 in zip(frames, outs, sync):
+            u = o.cpu().numpy()
+            assert np.array_equal(u, u0)
+            assert np.max(np.abs(u - ref.solve_direct(f, m))) <= TOL_U
+        rc, b, _ = B.dd_batch_create([ip._h for ip in ips], [o.data_ptr() for o in outs], 1e-6)
+        B.check(rc, "dd_batch_create")
+        try:
+            for o in outs:
+                o.zero_()
+            stream = torch.cuda.current_stream(DEV)
+            B.check(B.dd_batch_launch(b, stream), "dd_batch_launch")
+            rc, status = B.dd_batch_finish(b, len(ips), stream)
+            assert rc == B.DD_OK and all(sc == B.DD_OK for sc in status)
+            for o, u0 in zip(outs, sync):
+                assert np.array_equal(o.cpu().numpy(), u0)
+        finally:
+            B.dd_batch_destroy(b)
+    finally:
+        for ip in ips:
+            ip.close()
