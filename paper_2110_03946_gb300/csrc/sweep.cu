@@ -14,10 +14,11 @@
 // bounded and a timeout sets an error word).  The block is then held in
 // registers by NW warps: lane (lx, ly) of warp wt owns a PX x PY patch (PX
 // columns as PX/2 packed FP32 pairs).  Values across patch borders move by
-// warp shuffles and, between the NW warps, through shared memory.  CG dot
-// products are xor-butterfly warp sums (bitwise identical on every lane, so all
-// break decisions are uniform) plus a fixed-order sum over warps.  Packed pair
-// arithmetic (__ffma2_rn and friends, sm_100+) halves the issue slots.
+// warp shuffles and, between the NW warps, through shared memory.  Each CG step
+// has one tile-wide reduction of three dot products: xor-butterfly warp sums
+// (bitwise identical on every lane, so all break decisions are uniform) plus a
+// fixed-order sum over warps.  Packed pair arithmetic (__ffma2_rn and friends,
+// sm_100+) halves the issue slots.
 //
 // Local operator (unknown pixel p of the block):
 //   (A_i v)_p = dd_p v_p - sum_{q in N(p), q in block} v_q,
@@ -58,12 +59,6 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(FULL, v, m);
-    return v;
-}
 
 // ---- TMA / mbarrier primitives (PTX ISA: mbarrier, cp.async.bulk.tensor) ----------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -162,22 +157,6 @@ struct SweepArgs {
     float local_rtol2;   // local CG stops once (r, r) <= local_rtol2 * (r0, r0) (0: after k steps)
 };
 
-// Sum over the threads of one tile; identical result in every thread.
-template <class CF>
-__device__ __forceinline__ float tile_sum(float v, float* red, int wt, int lane) {
-    v = warp_sum(v);
-    if constexpr (CF::NW == 1) {
-        return v;
-    } else {
-        if (lane == 0) red[wt] = v;
-        __syncthreads();
-        float t = 0.f;
-#pragma unroll
-        for (int w = 0; w < CF::NW; ++w) t += red[w];
-        return t;
-    }
-}
-
 // Two sums over the threads of one tile in one butterfly.
 template <class CF>
 __device__ __forceinline__ float2 tile_sum2(float2 v, float* red_a, float* red_b, int wt, int lane) {
@@ -204,6 +183,35 @@ __device__ __forceinline__ float2 tile_sum2(float2 v, float* red_a, float* red_b
     }
 }
 
+// Three sums over the threads of one tile in one butterfly (red: 3 x NW floats).
+template <class CF>
+__device__ __forceinline__ float3 tile_sum3(float3 v, float* red, int wt, int lane) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        v.x += __shfl_xor_sync(FULL, v.x, m);
+        v.y += __shfl_xor_sync(FULL, v.y, m);
+        v.z += __shfl_xor_sync(FULL, v.z, m);
+    }
+    if constexpr (CF::NW == 1) {
+        return v;
+    } else {
+        if (lane == 0) {
+            red[wt] = v.x;
+            red[CF::NW + wt] = v.y;
+            red[2 * CF::NW + wt] = v.z;
+        }
+        __syncthreads();
+        float3 t = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < CF::NW; ++w) {
+            t.x += red[w];
+            t.y += red[CF::NW + w];
+            t.z += red[2 * CF::NW + w];
+        }
+        return t;
+    }
+}
+
 template <class CF, typename T>
 __global__ void __launch_bounds__(CF::NT)
 oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_constant__ CUtensorMap map_u1,
@@ -216,8 +224,9 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ int s_ok;
     __shared__ float red[3][NW];
-    __shared__ float red3[2][2][NW];   // CG reductions (p,Ap) and (r,r), alternating by step parity
-    __shared__ float xch[2][NW][BW];
+    __shared__ float red3[2][3][NW];   // CG reductions (p,Ap), (Ap,Ap), (r,r), alternating by step parity
+    __shared__ float xch[2][NW][BW];      // initial boundary rows of r
+    __shared__ float xq[2][2][NW][BW];    // boundary rows of q', alternating by step parity
 
     int* const flag = a.stop.flag;                  // [0] stop/skip, [1] conv_at, [2] err, [3] ticket
     if (flag[0] != 0) return;                        // converged or failed earlier: uniform no-op
@@ -376,6 +385,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         // ---- k CG steps from v = 0 (Saad, the CG algorithm of Ch. 6) --------------
         float2 v2[PY][NP], p2[PY][NP], q2[PY][NP];
         float rr, rr_stop;
+        float rrp = rr0;   // this thread's part of (r, r), summed again in the first CG step
         {
 #pragma unroll
             for (int i = 0; i < PY; ++i)
@@ -414,7 +424,9 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         }
         acc_c += s2;
         // p rows of the neighbouring warps next to this warp's top / bottom row
-        float2 nbN[NP], nbS[NP];
+        // (and their r rows: each warp advances its neighbours' boundary rows of r
+        // and p itself, from their q rows, exactly as the neighbours do)
+        float2 nbN[NP], nbS[NP], nrN[NP], nrS[NP];
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             nbN[j] = make_float2(0.f, 0.f);
@@ -424,16 +436,26 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                 if (ly == LY - 1 && wt < NW - 1)
                     nbS[j] = make_float2(xch[0][wt + 1][rx0 + 2 * j], xch[0][wt + 1][rx0 + 2 * j + 1]);
             }
+            nrN[j] = nbN[j];
+            nrS[j] = nbS[j];
         }
+        // One tile-wide reduction per step: (p, Ap), (Ap, Ap) and this step's
+        // measured (r, r) are summed together. alpha = (r, r) / (p, Ap) uses the
+        // measured value; (r', r') for beta and for the local stop comes from the
+        // recurrence |r - alpha Ap|^2 = alpha^2 (Ap, Ap) - (r, r), which holds
+        // because (r, Ap) = (p, Ap) for A-conjugate directions. Exact CG in exact
+        // arithmetic; the next step measures (r', r') again, so the recurrence
+        // error does not accumulate.
+        float rr_j = rr;   // (r, r) of the current step: measured at step 0, then by the recurrence
         int kk = 0;
         for (; kk < kcg; ++kk) {
             // converged locally (the bound also keeps the quotients below finite)
-            if (!(rr > 1e-30f) || rr <= rr_stop) break;
+            if (!(rr_j > 1e-30f) || rr_j <= rr_stop) break;
             float pW[PY], pE[PY];
 #pragma unroll
             for (int i = 0; i < PY; ++i) {
-                pW[i] = fW * __shfl_up_sync(FULL, p2[i][NP - 1].y, 1, LX);
-                pE[i] = fE * __shfl_down_sync(FULL, p2[i][0].x, 1, LX);
+                pW[i] = __shfl_up_sync(FULL, p2[i][NP - 1].y, 1, LX);
+                pE[i] = __shfl_down_sync(FULL, p2[i][0].x, 1, LX);
             }
             float2 pN[NP], pS[NP];
 #pragma unroll
@@ -451,29 +473,56 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
 #pragma unroll
                 for (int j = 0; j < NP; ++j) pS[j] = nbS[j];
             }
-            // q' = -(A_i p), and (p, q'); two independent accumulator chains
+            // q' = -(A_i p), with (p, q') and (q', q') on two accumulator chains each
             float2 pqa = make_float2(0.f, 0.f), pqb = make_float2(0.f, 0.f);
+            float2 qqa = make_float2(0.f, 0.f), qqb = make_float2(0.f, 0.f);
 #pragma unroll
             for (int i = 0; i < PY; ++i)
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
                     const float2 n = i > 0 ? p2[i - 1][j] : pN[j];
                     const float2 s = i < PY - 1 ? p2[i + 1][j] : pS[j];
-                    const float left = j > 0 ? p2[i][j - 1].y : pW[i];
-                    const float right = j < NP - 1 ? p2[i][j + 1].x : pE[i];
-                    const float2 h = make_float2(left + p2[i][j].y, p2[i][j].x + right);
+                    const float hx = j > 0 ? p2[i][j - 1].y + p2[i][j].y : fmaf(fW, pW[i], p2[i][j].y);
+                    const float hy = j < NP - 1 ? p2[i][j].x + p2[i][j + 1].x : fmaf(fE, pE[i], p2[i][j].x);
+                    const float2 h = make_float2(hx, hy);
                     const float2 sum = add2(add2(n, s), h);
                     const float2 nd = add2(rpn[i], cpn[j]);
                     const float2 q = mul2(w2[i][j], fma2(nd, p2[i][j], sum));
                     q2[i][j] = q;
-                    if (i & 1) pqb = fma2(p2[i][j], q, pqb); else pqa = fma2(p2[i][j], q, pqa);
+                    if (i & 1) {
+                        pqb = fma2(p2[i][j], q, pqb);
+                        qqb = fma2(q, q, qqb);
+                    } else {
+                        pqa = fma2(p2[i][j], q, pqa);
+                        qqa = fma2(q, q, qqa);
+                    }
                 }
-            const float pq = -tile_sum<CF>((pqa.x + pqa.y) + (pqb.x + pqb.y), red3[kk & 1][0], wt, lane);
-            if (!(pq > 1e-30f)) break;
-            // approximate quotients (2 ulp): the divisors lie in [1e-30, 2^126) here,
-            // where __fdividef is finite, and they shorten the step's dependency chain
-            const float alpha = __fdividef(rr, pq);
-            const float2 a2 = make_float2(alpha, alpha);
+            if constexpr (NW > 1) {   // boundary rows of q' for the neighbouring warps
+                if (ly == 0)
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        xq[kk & 1][0][wt][rx0 + 2 * j] = q2[0][j].x;
+                        xq[kk & 1][0][wt][rx0 + 2 * j + 1] = q2[0][j].y;
+                    }
+                if (ly == LY - 1)
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        xq[kk & 1][1][wt][rx0 + 2 * j] = q2[PY - 1][j].x;
+                        xq[kk & 1][1][wt][rx0 + 2 * j + 1] = q2[PY - 1][j].y;
+                    }
+            }
+            const float3 sums = tile_sum3<CF>(make_float3((pqa.x + pqa.y) + (pqb.x + pqb.y),
+                                                          (qqa.x + qqa.y) + (qqb.x + qqb.y), rrp),
+                                              &red3[kk & 1][0][0], wt, lane);
+            const float pq = -sums.x, qq = sums.y, rr = sums.z;
+            if (!(pq > 1e-30f) || !(rr > 1e-30f)) break;
+            // approximate quotient (2 ulp): pq lies in [1e-30, 2^126) here, where
+            // __fdividef is finite, and it shortens the step's dependency chain
+            const float inv = __fdividef(1.f, pq);
+            const float alpha = rr * inv;
+            const float beta = fmaf(alpha, qq * inv, -1.f);   // (r', r') / (r, r)
+            rr_j = beta * rr;
+            const float2 a2 = make_float2(alpha, alpha), b2 = make_float2(beta, beta);
             float2 rra = make_float2(0.f, 0.f), rrb = make_float2(0.f, 0.f);
 #pragma unroll
             for (int i = 0; i < PY; ++i)
@@ -483,38 +532,28 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                     r2[i][j] = fma2(a2, q2[i][j], r2[i][j]);     // r - alpha A p
                     if (i & 1) rrb = fma2(r2[i][j], r2[i][j], rrb); else rra = fma2(r2[i][j], r2[i][j], rra);
                 }
-            if constexpr (NW > 1) {   // new boundary rows of r for the neighbouring warps
-                if (ly == 0)
+            rrp = (rra.x + rra.y) + (rrb.x + rrb.y);
+            if (kk + 1 < kcg)
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        xch[0][wt][rx0 + 2 * j] = r2[0][j].x;
-                        xch[0][wt][rx0 + 2 * j + 1] = r2[0][j].y;
-                    }
-                if (ly == LY - 1)
+                for (int i = 0; i < PY; ++i)
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        xch[1][wt][rx0 + 2 * j] = r2[PY - 1][j].x;
-                        xch[1][wt][rx0 + 2 * j + 1] = r2[PY - 1][j].y;
-                    }
-            }
-            const float rr_new = tile_sum<CF>((rra.x + rra.y) + (rrb.x + rrb.y), red3[kk & 1][1], wt, lane);
-            const float beta = __fdividef(rr_new, rr);
-            const float2 b2 = make_float2(beta, beta);
-#pragma unroll
-            for (int i = 0; i < PY; ++i)
-#pragma unroll
-                for (int j = 0; j < NP; ++j) p2[i][j] = fma2(b2, p2[i][j], r2[i][j]);
-            if constexpr (NW > 1) {   // the neighbours' new p rows, formed exactly as they form them
+                    for (int j = 0; j < NP; ++j) p2[i][j] = fma2(b2, p2[i][j], r2[i][j]);
+            if constexpr (NW > 1) {   // the neighbours' rows of r and p, from their q' rows (read after the barrier)
                 if (ly == 0 && wt > 0)
 #pragma unroll
-                    for (int j = 0; j < NP; ++j)
-                        nbN[j] = fma2(b2, nbN[j], make_float2(xch[1][wt - 1][rx0 + 2 * j], xch[1][wt - 1][rx0 + 2 * j + 1]));
+                    for (int j = 0; j < NP; ++j) {
+                        const float2 qn = make_float2(xq[kk & 1][1][wt - 1][rx0 + 2 * j], xq[kk & 1][1][wt - 1][rx0 + 2 * j + 1]);
+                        nrN[j] = fma2(a2, qn, nrN[j]);
+                        nbN[j] = fma2(b2, nbN[j], nrN[j]);
+                    }
                 if (ly == LY - 1 && wt < NW - 1)
 #pragma unroll
-                    for (int j = 0; j < NP; ++j)
-                        nbS[j] = fma2(b2, nbS[j], make_float2(xch[0][wt + 1][rx0 + 2 * j], xch[0][wt + 1][rx0 + 2 * j + 1]));
+                    for (int j = 0; j < NP; ++j) {
+                        const float2 qs = make_float2(xq[kk & 1][0][wt + 1][rx0 + 2 * j], xq[kk & 1][0][wt + 1][rx0 + 2 * j + 1]);
+                        nrS[j] = fma2(a2, qs, nrS[j]);
+                        nbS[j] = fma2(b2, nbS[j], nrS[j]);
+                    }
             }
-            rr = rr_new;
         }
 
         if (a.stop.work != nullptr && !probe) {   // work actually done (the local stop shortens it)
