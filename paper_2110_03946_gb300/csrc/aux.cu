@@ -748,10 +748,8 @@ __global__ void resolve_kernel(const int* __restrict__ flag, const int* __restri
 __global__ void reset_sweep_state_kernel(int* __restrict__ state, int* __restrict__ flag, int cur,
                                          double* __restrict__ tol_d, double tol, const int* __restrict__ skip_if) {
     const bool skip = skip_if != nullptr && *skip_if != 0;
-    if (threadIdx.x < 4) {
-        state[threadIdx.x] = threadIdx.x == 0 ? cur : 0;
-        flag[threadIdx.x] = (threadIdx.x == 0 && skip) ? 4 : 0;   // 4: sequence skipped
-    }
+    if (threadIdx.x < 4) state[threadIdx.x] = threadIdx.x == 0 ? cur : 0;
+    if (threadIdx.x < 5) flag[threadIdx.x] = (threadIdx.x == 0 && skip) ? 4 : 0;   // 4: sequence skipped
     if (threadIdx.x == 0) *tol_d = tol;
 }
 

@@ -53,16 +53,22 @@ cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsig
 // is the block tile plus halo of block side b: built once per buffer.
 cudaError_t make_tile_map(CUtensorMap* out, Store st, const void* base, int H, int W, int pitch, int C, int b);
 
-// Residual norms and stop test fused into the sweep.  Each CTA writes its
-// per-channel sum of squared owned residuals of the input iterate to
-// partial[c * slots + cta]; the last CTA to finish sums them in a fixed order
-// into norms2[c] and sets flag[0]:
+// Residual norms and stop test fused into the sweep.  Tiles are handed to the
+// persistent CTAs in increasing order by an atomic counter (flag[4]), so which
+// CTA takes which tile varies from run to run; the sums do not: each tile's FP32
+// sum of squared owned residuals of the input iterate is added exactly into a
+// 128-bit fixed-point accumulator (unit 2^-80 ref[c]^2, saturating at
+// 2^32 ref[c]^2, values below the unit truncated), and integer addition does
+// not depend on the order.  Each CTA writes its per-channel accumulator to
+// partial[2 * (c * slots + cta) + {0: low, 1: high word}]; the last CTA to
+// finish adds them into norms2[c] (bitwise repeatable) and sets flag[0]:
 //   1 when max_c sqrt(norms2[c]) / ref[c] <= tol (tol < 0: never),
 //   2 on NaN/Inf, 3 when stall > 0 and every channel's residual fell by less
 //   than the factor 1/stall since the previous full sweep;
 // flag[1] = the launch index (state[3]) then.  flag[0] != 0 makes later launches no-ops.
 // flag[2] is set if a bounded wait for a staged tile gave up; flag[3] is the
-// completion ticket (0 between launches).  slots >= the launch grid.
+// completion ticket and flag[4] the tile counter (both 0 between launches).
+// slots >= the launch grid.
 // The iterate pair is chosen on the device: state[0] is the buffer holding the
 // current iterate (the launch reads it and writes the other one), state[1]
 // counts full sweeps, state[2] = 1 makes the next launch a probe that only
@@ -74,8 +80,9 @@ cudaError_t make_tile_map(CUtensorMap* out, Store st, const void* base, int H, i
 // last two sweeps predicts that the new iterate meets tol.  norms2 holds
 // 2C + 2 doubles: current norms, norms of the previous full sweep, and the
 // previous full sweep's worst relative residual.
+constexpr int kFlagWords = 8;     // flag array length (5 used)
 struct SweepStop {
-    float* partial;
+    unsigned long long* partial;   // 2 x C x slots words
     int slots;
     double* norms2;
     const double* ref;
@@ -111,7 +118,7 @@ cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, co
 // per process; call before capturing a sweep launch into a graph.
 cudaError_t prepare_sweep(Store s, const TileGeom& g, bool has_g);
 
-// state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..3] = 0; *tol_d = tol
+// state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..4] = 0; *tol_d = tol
 // (the stop tolerance the following sweeps or CG iterations read).  With
 // skip_if and *skip_if != 0, flag[0] = 4 instead: the following sweeps are
 // no-ops.

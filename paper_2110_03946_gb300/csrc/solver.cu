@@ -96,7 +96,7 @@ struct Level {
     uint32_t* tmask = nullptr;
     float* u[2] = {nullptr, nullptr};
     CUtensorMap map_u[2];      // TMA descriptors of u[0], u[1]
-    float* partial = nullptr;  // C x kSweepSlots per-CTA residual sums
+    unsigned long long* partial = nullptr;  // 2 x C x kSweepSlots per-CTA residual sums (128-bit fixed point)
     double* ref_d = nullptr;   // C
     std::vector<double> ref;   // C (host copy, read after load_data's single sync)
     int* state_d = nullptr;    // resolve() output of this level's last sweep sequence
@@ -139,7 +139,8 @@ struct dd_inpaint {
     double2* res_out = nullptr;     // C per level
     unsigned int* res_ticket = nullptr;   // completion ticket of the fused residual reduction (zero)
     double* norms2_d = nullptr;     // C
-    int* flag_d = nullptr;          // [0] stop flag, [1] conv_at, [2] device wait timed out, [3] ticket
+    int* flag_d = nullptr;          // [0] stop flag, [1] conv_at, [2] device wait timed out, [3] ticket,
+                                    // [4] tile counter (kFlagWords ints)
     int* sstate_d = nullptr;        // sweep state: current buffer, full sweeps, probe request, launches
     int* ctl_d = nullptr;           // device-loop pass counter (4 ints)
     double* tol_d = nullptr;        // stop tolerance of the running level (set by each reset)
@@ -147,7 +148,7 @@ struct dd_inpaint {
     unsigned long long* h_work = nullptr;   // pinned mirror
     // DD_ML_CORRECTION: fine residual, and the stop state of the coarse correction solve
     float* corr_r = nullptr;        // C x H x P (level 0)
-    int* flag_c = nullptr;          // 4 ints
+    int* flag_c = nullptr;          // kFlagWords ints
     int* state_c = nullptr;         // 4 ints
     double* norms2_c = nullptr;     // 2C + 2
     double* tol_c = nullptr;        // 1
@@ -157,7 +158,7 @@ struct dd_inpaint {
     cudaStream_t cap_stream = nullptr;   // private stream on which loop bodies are captured
     cudaStream_t cap_stream2 = nullptr;  // ... and the bodies of loops nested in them
     // device-driven FP64 correction loop (precision != FP32, device_loop = 1)
-    int* ref_ctl_d = nullptr;       // 8 ints, see ref_outer_ctl_kernel
+    int* ref_ctl_d = nullptr;       // 4 + kFlagWords ints, see ref_outer_ctl_kernel
     double* ref_tol_d = nullptr;    // the solve's tolerance
     int* h_ref_ctl = nullptr;       // pinned mirror (8 ints)
     LoopGraph ref_loop;             // the outer loop as a graph of its own
@@ -207,6 +208,20 @@ int dalloc_t(dd_inpaint* h, T** p, size_t count) {
     int rc = dalloc(h, &v, count * sizeof(T));
     *p = static_cast<T*>(v);
     return rc;
+}
+
+int dzero(void* p, size_t n) {
+    if (cudaMemset(p, 0, n) != cudaSuccess) {
+        set_error("cudaMemset failed");
+        return DD_ECUDA;
+    }
+    return DD_OK;
+}
+
+// Stop-flag words of a sweep sequence, zeroed (the tile counter must start at 0).
+int alloc_flag(dd_inpaint* h, int** f) {
+    int rc = dalloc_t(h, f, dd::kFlagWords);
+    return rc != DD_OK ? rc : dzero(*f, dd::kFlagWords * sizeof(int));
 }
 
 Store low_store(int precision) {
@@ -336,9 +351,9 @@ int count_known(const uint8_t* mask, size_t n, bool on_device, long long* out) {
 // current iterate, measured against ref_d, is <= tol, or max_sweeps sweeps.
 // bufs[cur] holds the input; on return cur indexes the result.
 int run_sweeps(dd_inpaint* h, const TileGeom& g, Store st_t, void* const bufs[2], const CUtensorMap* maps,
-               int& cur, const CUtensorMap* map_g, const uint32_t* tmask, float* partial, const double* ref_d,
-               double tol, double stall, int max_sweeps, cudaStream_t st, int* applied, bool* converged,
-               bool fine = false) {
+               int& cur, const CUtensorMap* map_g, const uint32_t* tmask, unsigned long long* partial,
+               const double* ref_d, double tol, double stall, int max_sweeps, cudaStream_t st, int* applied,
+               bool* converged, bool fine = false) {
     const long long plane = (long long)g.H * g.pitch;
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, cur, h->tol_d, tol, st));
     *converged = false;
@@ -1073,7 +1088,7 @@ int ref_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool c
         h->cur = 0;
     }
     h->warm = false;
-    // ref_ctl[0..7] = 0 and the tolerance (the sweep-state reset kernel on the control words)
+    // ref_ctl[0..8] = 0 and the tolerance (the sweep-state reset kernel on the control words)
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->ref_ctl_d, h->ref_ctl_d + 4, 0, h->ref_tol_d, tol, st));
     if (capture) {
         DD_TRY(capture_append(st, [&](cudaGraph_t cg, const cudaGraphNode_t* d, const cudaGraphEdgeData* e, size_t n,
@@ -1293,7 +1308,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         if ((rc = dalloc_t(h, &L.tmask, dd::tmask_words(L.geom))) != DD_OK) return fail(rc);
         for (int b = 0; b < 2; ++b)
             if ((rc = dalloc(h, (void**)&L.u[b], plane_bytes)) != DD_OK) return fail(rc);
-        if ((rc = dalloc_t(h, &L.partial, (size_t)C * dd::kSweepSlots)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &L.partial, (size_t)2 * C * dd::kSweepSlots)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &L.ref_d, (size_t)C)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &L.state_d, 4)) != DD_OK) return fail(rc);
         if (p.solver == DD_SOLVER_CG) {
@@ -1342,7 +1357,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
             set_error("cuTensorMapEncodeTiled failed");
             return fail(DD_ECUDA);
         }
-        if ((rc = dalloc_t(h, &h->flag_c, 4)) != DD_OK) return fail(rc);
+        if ((rc = alloc_flag(h, &h->flag_c)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &h->state_c, 4)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &h->norms2_c, (size_t)2 * C + 2)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &h->tol_c, 1)) != DD_OK) return fail(rc);
@@ -1366,12 +1381,12 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     }
     if ((rc = dalloc_t(h, &h->scale_d, (size_t)C)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->scale_inv_d, (size_t)C)) != DD_OK) return fail(rc);
-    if ((rc = dalloc_t(h, &h->flag_d, 4)) != DD_OK) return fail(rc);
+    if ((rc = alloc_flag(h, &h->flag_d)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->ctl_d, 4)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->tol_d, 1)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->res_ticket, 1)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->work_d, 2)) != DD_OK) return fail(rc);
-    if ((rc = dalloc_t(h, &h->ref_ctl_d, 8)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->ref_ctl_d, 4 + dd::kFlagWords)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->ref_tol_d, 1)) != DD_OK) return fail(rc);
     if (cudaMallocHost(&h->h_ref_ctl, 8 * sizeof(int)) != cudaSuccess) {
         set_error("cudaMallocHost failed");

@@ -36,7 +36,7 @@ namespace {
 constexpr long long kMaxIterElems = 1LL << 22;   // C * H * pitch of one iterate buffer
 constexpr long long kMaxTiles = 16384;           // blocks per channel
 constexpr long long kMaxTileWords = kMaxTiles * 2 * 256;   // block masks (up to 256 threads per block)
-constexpr long long kMaxPartials = (long long)DD_MAX_STAT_CHANNELS * dd::kSweepSlots;   // per-CTA residual sums
+constexpr long long kMaxPartials = 2LL * DD_MAX_STAT_CHANNELS * dd::kSweepSlots;   // per-CTA residual sums (words)
 constexpr long long kMaxResBlocks = 65536;       // C * blocks of the FP64 residual pass
 constexpr int kMaxChannels = DD_MAX_STAT_CHANNELS;
 
@@ -45,12 +45,12 @@ constexpr size_t kOffU0 = 0;
 constexpr size_t kOffU1 = kOffU0 + align256(kMaxIterElems * 4);
 constexpr size_t kOffTmask = kOffU1 + align256(kMaxIterElems * 4);
 constexpr size_t kOffPartial = kOffTmask + align256(kMaxTileWords * 4);
-constexpr size_t kOffResPart = kOffPartial + align256(kMaxPartials * 4);
+constexpr size_t kOffResPart = kOffPartial + align256(kMaxPartials * 8);
 constexpr size_t kOffResOut = kOffResPart + align256(kMaxResBlocks * 16);
 constexpr size_t kOffNorms = kOffResOut + align256(kMaxChannels * 16);
 constexpr size_t kOffRef = kOffNorms + align256((2 * kMaxChannels + 2) * 8);
 constexpr size_t kOffFlag = kOffRef + align256(kMaxChannels * 8);
-constexpr size_t kOffState = kOffFlag + align256(4 * 4);
+constexpr size_t kOffState = kOffFlag + align256(dd::kFlagWords * 4);
 constexpr size_t kOffTol = kOffState + align256(4 * 4);
 constexpr size_t kOffCount = kOffTol + align256(8);
 constexpr size_t kScratchBytes = kOffCount + align256(8);
@@ -137,7 +137,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     if (int rc = scratch_base(&base); rc != DD_OK) return rc;
     float* u[2] = {reinterpret_cast<float*>(base + kOffU0), reinterpret_cast<float*>(base + kOffU1)};
     uint32_t* tmask = reinterpret_cast<uint32_t*>(base + kOffTmask);
-    float* partial = reinterpret_cast<float*>(base + kOffPartial);
+    unsigned long long* partial = reinterpret_cast<unsigned long long*>(base + kOffPartial);
     double2* res_part = reinterpret_cast<double2*>(base + kOffResPart);
     double2* res_out = reinterpret_cast<double2*>(base + kOffResOut);
     double* norms2 = reinterpret_cast<double*>(base + kOffNorms);

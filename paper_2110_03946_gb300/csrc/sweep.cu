@@ -93,6 +93,44 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+// Exact, order-independent sums of non-negative FP32 values: a 128-bit
+// fixed-point accumulator with the unit 2^eu.  A value's bits below the unit
+// are dropped and values of 2^(eu + 104) or more saturate there; both depend on
+// the value alone, so a set of values has the same sum in any order (and up to
+// 2^24 values cannot overflow).  Non-finite values are flagged by the caller.
+struct Fix128 {
+    unsigned long long lo, hi;
+};
+__device__ __forceinline__ void fix_add(Fix128& acc, float v, int eu) {
+    const unsigned bits = __float_as_uint(v);
+    const int be = (int)((bits >> 23) & 0xffu);
+    if (!(v > 0.f) || be == 0xff) return;
+    unsigned long long m = (bits & 0x7fffffu) | (be != 0 ? 0x800000u : 0u);
+    int sh = (be != 0 ? be : 1) - 150 - eu;   // v = m 2^(sh + eu)
+    if (sh < 0) {
+        if (sh <= -24) return;
+        m >>= -sh;
+        sh = 0;
+    }
+    if (sh > 80) {
+        m = 0xffffffull;
+        sh = 80;
+    }
+    const unsigned long long lo = sh < 64 ? m << sh : 0ull;
+    const unsigned long long hi = sh == 0 ? 0ull : (sh < 64 ? m >> (64 - sh) : m << (sh - 64));
+    acc.lo += lo;
+    acc.hi += hi + (acc.lo < lo ? 1ull : 0ull);
+}
+__device__ __forceinline__ void fix_add(Fix128& acc, unsigned long long lo, unsigned long long hi) {
+    acc.lo += lo;
+    acc.hi += hi + (acc.lo < lo ? 1ull : 0ull);
+}
+// The accumulator unit of a channel with reference norm ref: 2^-72 ref^2, so
+// sums from about 2^-72 to 2^32 times ref^2 are exact before the final rounding.
+__device__ __forceinline__ int fix_unit(double ref) {
+    return 2 * ilogb(ref > 0.0 && isfinite(ref) ? ref : 1.0) - 72;
+}
+constexpr unsigned long long kFixBad = ~0ull;   // high word of a partial that saw NaN/Inf
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
@@ -223,12 +261,13 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ int s_ok;
+    __shared__ long long s_next[2];    // next tile, by iteration parity
     __shared__ float red[3][NW];
     __shared__ float red3[2][3][NW];   // CG reductions (p,Ap), (Ap,Ap), (r,r), alternating by step parity
     __shared__ float xch[2][NW][BW];      // initial boundary rows of r
     __shared__ float xq[2][2][NW][BW];    // boundary rows of q', alternating by step parity
 
-    int* const flag = a.stop.flag;                  // [0] stop/skip, [1] conv_at, [2] err, [3] ticket
+    int* const flag = a.stop.flag;   // [0] stop/skip, [1] conv_at, [2] err, [3] ticket, [4] tile counter
     if (flag[0] != 0) return;                        // converged or failed earlier: uniform no-op
     // the current iterate and the kind of launch are device state (read before
     // the last CTA of this launch updates them)
@@ -277,16 +316,27 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
 
     const float pr = a.p_robin;
     const float fW = lx > 0 ? 1.f : 0.f, fE = lx < LX - 1 ? 1.f : 0.f;
-    float* const part = a.stop.partial;
+    // thread 0: this CTA's exact residual sum of the channel it is in (tiles
+    // come in increasing order, so channels too)
+    unsigned long long* const part = a.stop.partial;
     const int slots = a.stop.slots;
-    int cur_c = -1;        // channel whose owned residual sum is being accumulated
-    float acc_c = 0.f;
+    auto put = [&](int cc, const Fix128& v, bool bad) {
+        part[2 * ((size_t)cc * slots + blockIdx.x)] = v.lo;
+        part[2 * ((size_t)cc * slots + blockIdx.x) + 1] = bad ? kFixBad : v.hi;
+    };
+    int cur_c = -1, eu = 0;
+    Fix128 acc{0ull, 0ull};
+    bool acc_bad = false;
     uint32_t work_us = 0, work_u = 0;   // optional work counters (per lane)
     int it = 0;
-    for (; t < total; t += gridDim.x, ++it) {
+    for (; t < total; ++it) {
         const int buf = it & 1;
         const uint32_t parity = (uint32_t)((it >> 1) & 1);
-        if (tt == 0 && t + gridDim.x < total) issue(t + gridDim.x, buf ^ 1);
+        if (tt == 0) {   // claim the next tile and stage it while this one is solved
+            const long long tn = (long long)atomicAdd(reinterpret_cast<unsigned*>(flag + 4), 1u) + gridDim.x;
+            s_next[buf] = tn;
+            if (tn < total) issue(tn, buf ^ 1);
+        }
 
         const int c = (int)(t / a.ntiles);
         const int tile = (int)(t - (long long)c * a.ntiles);
@@ -414,15 +464,18 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             rr = both.y;
             rr_stop = a.local_rtol2 * rr;
         }
-        if (c != cur_c) {   // tiles of one CTA visit channels in increasing order
-            if (tt == 0) {
-                if (cur_c >= 0) part[(size_t)cur_c * slots + blockIdx.x] = acc_c;
-                for (int cc = cur_c + 1; cc < c; ++cc) part[(size_t)cc * slots + blockIdx.x] = 0.f;
+        if (tt == 0) {
+            if (c != cur_c) {
+                if (cur_c >= 0) put(cur_c, acc, acc_bad);
+                for (int cc = cur_c + 1; cc < c; ++cc) put(cc, Fix128{0ull, 0ull}, false);
+                cur_c = c;
+                acc = Fix128{0ull, 0ull};
+                acc_bad = false;
+                eu = fix_unit(a.stop.ref[c]);
             }
-            cur_c = c;
-            acc_c = 0.f;
+            if (isfinite(s2)) fix_add(acc, s2, eu);
+            else acc_bad = true;
         }
-        acc_c += s2;
         // p rows of the neighbouring warps next to this warp's top / bottom row
         // (and their r rows: each warp advances its neighbours' boundary rows of r
         // and p itself, from their q rows, exactly as the neighbours do)
@@ -578,6 +631,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             }
         if constexpr (NW > 1) __syncthreads();   // the staged tile may now be refilled
         else __syncwarp();
+        t = s_next[buf];
     }
     if (a.stop.work != nullptr) {
         const uint32_t ws = __reduce_add_sync(FULL, work_us), wu = __reduce_add_sync(FULL, work_u);
@@ -593,8 +647,8 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
 
     // ---- per-channel residual norms of u^n and the stop test (last CTA) -----------
     if (tt == 0) {
-        if (cur_c >= 0) part[(size_t)cur_c * slots + blockIdx.x] = acc_c;
-        for (int cc = cur_c + 1; cc < a.C; ++cc) part[(size_t)cc * slots + blockIdx.x] = 0.f;
+        if (cur_c >= 0) put(cur_c, acc, acc_bad);
+        for (int cc = cur_c + 1; cc < a.C; ++cc) put(cc, Fix128{0ull, 0ull}, false);
     }
     __threadfence();
     __syncthreads();
@@ -609,12 +663,24 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         double worst = 0.0, best_ratio = 1e300;
         int bad = 0;
         for (int c = 0; c < a.C; ++c) {
-            double v = 0.0;
-            for (int i = lane; i < (int)gridDim.x; i += 32) v += (double)__ldcg(part + (size_t)c * slots + i);
+            Fix128 f{0ull, 0ull};
+            int nf = 0;
+            for (int i = lane; i < (int)gridDim.x; i += 32) {
+                const unsigned long long lo = __ldcg(part + 2 * ((size_t)c * slots + i));
+                const unsigned long long hi = __ldcg(part + 2 * ((size_t)c * slots + i) + 1);
+                if (hi == kFixBad) nf = 1;
+                else fix_add(f, lo, hi);
+            }
 #pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(FULL, v, m);
+            for (int m = 16; m >= 1; m >>= 1) {
+                const unsigned long long lo = __shfl_xor_sync(FULL, f.lo, m), hi = __shfl_xor_sync(FULL, f.hi, m);
+                fix_add(f, lo, hi);
+            }
+            nf = __any_sync(FULL, nf);
+            const int ec = fix_unit(sp.ref[c]);
+            const double v = ldexp((double)f.hi, 64 + ec) + ldexp((double)f.lo, ec);
             if (lane == 0) {
-                if (!isfinite(v)) bad = 1;
+                if (nf || !isfinite(v)) bad = 1;
                 const double den = sp.ref[c] > 0.0 ? sp.ref[c] : 1.0;
                 worst = fmax(worst, sqrt(v) / den);
                 if (sweep_index > 0) {
@@ -648,7 +714,8 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             }
             if (!probe) sp.norms2[2 * a.C] = worst;
             state[3] = sweep_index + 1;
-            flag[3] = 0;   // ticket ready for the next launch
+            flag[3] = 0;   // ticket and tile counter ready for the next launch
+            flag[4] = 0;
         }
     }
 }

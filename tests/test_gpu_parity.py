@@ -251,6 +251,35 @@ def test_repeatable_bitwise():
     assert np.array_equal(a, b)
 
 
+def test_repeatable_bitwise_under_concurrency():
+    """Tiles go to the persistent CTAs through an atomic counter, so which CTA
+    solves which tile differs between runs, most of all when other solves share
+    the GPU; the residual sums are exact fixed-point sums, so the norms, every
+    stop decision and the output must not change."""
+    f, m = synth.make_frame(720, 1280, 3, 0.03, "edge", 37)
+    prm = dict(block=32, overlap=3, local_cg_iters=20, local_rtol=0.05, robin_p=0.15, levels=3, precision="fp32")
+    with Inpainter(m, f, **prm) as ip:
+        alone = ip.solve(1e-6).cpu().numpy()
+        st0 = ip.stats()
+    ips = [Inpainter(m, f, **prm) for _ in range(4)]
+    streams = [torch.cuda.Stream(DEV) for _ in ips]
+    outs = [torch.empty(f.shape, dtype=torch.float32, device=DEV) for _ in ips]
+    try:
+        for _ in range(2):
+            for ip, s, o in zip(ips, streams, outs):
+                B.check(B.dd_inpaint_solve_async(ip._h, o.data_ptr(), 1e-6, s), "solve_async")
+            for ip, s in zip(ips, streams):
+                B.check(B.dd_inpaint_solve_finish(ip._h, s), "finish")
+            for ip, o in zip(ips, outs):
+                st = ip.stats()
+                assert np.array_equal(o.cpu().numpy(), alone)
+                assert st["rel_residual"] == st0["rel_residual"]
+                assert st["sweeps_per_level"] == st0["sweeps_per_level"]
+    finally:
+        for ip in ips:
+            ip.close()
+
+
 @pytest.mark.parametrize("solver", ["oras", "cg"])
 def test_device_loop_matches_launches(solver):
     """The level iterations repeated in a CUDA graph loop on the device give the
