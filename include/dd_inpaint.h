@@ -315,7 +315,7 @@ int dd_residual_norms(int H, int W, int C, const uint8_t *mask, const float *f,
  * latency or failure is not acceptable.  This call runs the same one-level FP32
  * ORAS sweeps as dd_inpaint_solve with levels = 1 and precision = DD_PREC_FP32,
  * but takes all its scratch from one fixed-size device array that is part of
- * the library (about 37 MiB, present on every GPU that loads the library until
+ * the library (about 42 MiB, present on every GPU that loads the library until
  * the process exits).  It calls no cudaMalloc, cudaFree or other allocating
  * routine.
  *   mask (H*W bytes), values (C*H*W floats), u_out (C*H*W floats): DEVICE;
@@ -323,7 +323,9 @@ int dd_residual_norms(int H, int W, int C, const uint8_t *mask, const float *f,
  *   max_sweeps are used, levels and precision are ignored;
  *   tol: relative residual target as in dd_inpaint_solve (FP64-verified).
  * Capacity: C <= 16, C*H*roundup(W,32) <= 4194304, at most 16384 blocks per
- * channel and 65536 blocks over all channels; larger inputs return DD_EINVAL
+ * channel, blocks x threads per block <= 1048576 (32 threads per block for
+ * block = 16 or 32 with one warp, up to 256 for block = 64) and 65536 blocks
+ * of the residual pass over all channels; larger inputs return DD_EINVAL
  * (dd_last_error() says which limit) before any GPU work.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream

@@ -11,7 +11,7 @@
 // device array of fixed size.  The caller still passes inputs and the output.
 //
 // Properties a caller must know:
-//  * the array (kScratchBytes, about 37 MiB) exists on every GPU that loads
+//  * the array (kScratchBytes, about 42 MiB) exists on every GPU that loads
 //    the library, for the life of the process;
 //  * the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (once per device, with that device current); make
@@ -35,7 +35,7 @@ namespace {
 
 constexpr long long kMaxIterElems = 1LL << 22;   // C * H * pitch of one iterate buffer
 constexpr long long kMaxTiles = 16384;           // blocks per channel
-constexpr long long kMaxTileWords = kMaxTiles * 2 * 256;   // block masks (up to 256 threads per block)
+constexpr long long kMaxTileWords = kMaxTiles * 2 * 64;    // block masks: 2 words per thread, blocks x threads <= 2^20
 constexpr long long kMaxPartials = 2LL * DD_MAX_STAT_CHANNELS * dd::kSweepSlots;   // per-CTA residual sums (words)
 constexpr long long kMaxResBlocks = 65536;       // C * blocks of the FP64 residual pass
 constexpr int kMaxChannels = DD_MAX_STAT_CHANNELS;

@@ -61,3 +61,16 @@ def test_static_rejects_oversized_input():
     rc = B.dd_inpaint_solve_static(H, W, C, mask_d.data_ptr(), vals_d.data_ptr(), out.data_ptr(), None, 1e-6, None)
     assert rc == B.DD_EINVAL
     assert "capacity" in B.dd_last_error()
+
+
+def test_static_rejects_block_masks_beyond_capacity():
+    # 64 x 64 blocks of eight warps at stride 16: about 15000 blocks of 256 threads, whose
+    # masks (2 words per thread) exceed the 2^20 block-thread capacity of the shared array
+    H, W, C = 2048, 2016, 1
+    mask_d = torch.ones((H, W), dtype=torch.uint8, device=DEV)
+    vals_d = torch.zeros((C, H, W), dtype=torch.float32, device=DEV)
+    out = torch.empty((C, H, W), dtype=torch.float32, device=DEV)
+    p = make_params(block=64, overlap=48, tile_warps=8, levels=1, precision="fp32")
+    rc = B.dd_inpaint_solve_static(H, W, C, mask_d.data_ptr(), vals_d.data_ptr(), out.data_ptr(), p, 1e-6, None)
+    assert rc == B.DD_EINVAL
+    assert "capacity" in B.dd_last_error()
