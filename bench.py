@@ -212,6 +212,26 @@ def cpu_oracle_sample(f, mask):
     return 1.0 / (C * dt), ocg.threads(), dt
 
 
+def oracle_error(dev, md, fd, f, mask, legs):
+    """Error of the GPU results against the FP64 oracle on channel 0 of one
+    frame (part of the CPU leg, untimed): the oracle CG to rel-res 1e-12, and
+    for each (name, Inpainter parameters) the GPU solve at the bench tolerance;
+    max |u - u*| and RMS on the 0-255 scale."""
+    import numpy as np
+    from oracle import cg as ocg
+    from paper_2110_03946_gb300.inpaint import Inpainter
+    t0 = time.perf_counter()
+    ustar, it, _ = ocg.solve_cg(f[0], mask, tol=1e-12)
+    out = {"channel": 0, "oracle": f"FP64 CG to rel-res 1e-12 ({int(it[0])} iterations, "
+                                   f"{time.perf_counter() - t0:.1f} s, untimed)"}
+    for name, prm in legs:
+        with Inpainter(md, fd, device=dev, **prm) as ip:
+            u = ip.solve(TOL).cpu().numpy()[0].astype(np.float64)
+        d = u - ustar
+        out[name] = {"max_abs": float(np.max(np.abs(d))), "rms": float(np.sqrt(np.mean(d * d)))}
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -750,6 +770,10 @@ def run_ours(args):
         cpu = {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"channel 0 of one 3840x2160 frame, FP64 oracle CG to rel-res {TOL:g} "
                          f"({secs:.1f} s), scaled to 3 channels per frame"}
+        legs = [("fp32", prm)]
+        if args.precision == "fp32" and not args.no_mixed:
+            legs.append(("fp16_ref", dict(solver_params(args, "fp16_ref")[0], precision="fp16_ref")))
+        cpu["error_vs_oracle"] = oracle_error(dev, dmask[0], dvals[0], f0, m0, legs)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
