@@ -420,9 +420,10 @@ __global__ void __launch_bounds__(V_TPB) restrict_kernel(int H, int W, int Hc, i
 // block {2Y, 2Y+1} x {2X, 2X+1} inside the image.  The h = 1 stencil on a grid
 // twice as coarse represents the Laplacian times 4, so summing (4 x the mean)
 // gives the coarse equation of the restricted residual.  No-op if *skip != 0.
-__global__ void __launch_bounds__(V_TPB) restrict_sum_kernel(int H, int W, int Hc, int Wc, const float* __restrict__ src,
-                                                             int sp, long long splane, float* __restrict__ dst, int dp,
-                                                             long long dplane, const int* __restrict__ skip, CopyVec vec) {
+__global__ void __launch_bounds__(V_TPB) restrict_sum_kernel(int H, int W, int Hc, int Wc,
+                                                             const float* __restrict__ src, int sp, long long splane,
+                                                             float* __restrict__ dst, int dp, long long dplane,
+                                                             const int* __restrict__ skip, CopyVec vec) {
     if (skip != nullptr && *skip != 0) return;
     const int c = blockIdx.z;
     const int X0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
@@ -512,7 +513,8 @@ __device__ void dot_tail(float s, int c, const DotTail& t, int C) {
 
 // d = bilinear prolongation of (sel_c && sel_c[0] ? ec1 : ec0) on unknown fine
 // pixels (0 on known), written over r; (r, d) per channel.
-__global__ void __launch_bounds__(V_TPB) corr_dir_kernel(int Hc, int Wc, int H, int W, int C, const float* __restrict__ ec0,
+__global__ void __launch_bounds__(V_TPB) corr_dir_kernel(int Hc, int Wc, int H, int W, int C,
+                                                         const float* __restrict__ ec0,
                                                          const float* __restrict__ ec1, const int* __restrict__ sel_c,
                                                          int ecp, long long ecplane, const uint8_t* __restrict__ mask,
                                                          int mp, float* __restrict__ rd, int rp, long long rplane,

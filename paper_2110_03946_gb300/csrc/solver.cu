@@ -256,9 +256,18 @@ int validate(int H, int W, int C, const dd_params& p) {
         return DD_EINVAL;
     }
     if (p.precision < DD_PREC_FP32 || p.precision > DD_PREC_BF16_REF) { set_error("bad precision"); return DD_EINVAL; }
-    if (p.max_sweeps < 0 || p.coarse_sweeps < 0 || p.max_corrections < 0) { set_error("negative limit"); return DD_EINVAL; }
-    if (!(p.coarse_tol > 0.0) || !(p.inner_tol > 0.0) || !(p.inner_tol < 1.0)) { set_error("bad tolerance"); return DD_EINVAL; }
-    if (!(p.local_rtol >= 0.0) || !(p.local_rtol < 1.0)) { set_error("local_rtol must be in [0, 1)"); return DD_EINVAL; }
+    if (p.max_sweeps < 0 || p.coarse_sweeps < 0 || p.max_corrections < 0) {
+        set_error("negative limit");
+        return DD_EINVAL;
+    }
+    if (!(p.coarse_tol > 0.0) || !(p.inner_tol > 0.0) || !(p.inner_tol < 1.0)) {
+        set_error("bad tolerance");
+        return DD_EINVAL;
+    }
+    if (!(p.local_rtol >= 0.0) || !(p.local_rtol < 1.0)) {
+        set_error("local_rtol must be in [0, 1)");
+        return DD_EINVAL;
+    }
     return DD_OK;
 }
 
@@ -527,7 +536,8 @@ int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
     DD_CK(cudaMemsetAsync(Lc.u[1], 0, cbytes, st));
     DD_CK(dd::launch_reset_sweep_state(h->state_c, h->flag_c, 0, h->tol_c, -1.0, st, skip));
     const dd::SweepPair pair{{&Lc.map_u[0], &Lc.map_u[1]}, {Lc.u[0], Lc.u[1]}};
-    const dd::SweepStop stop{Lc.partial, dd::kSweepSlots, h->norms2_c, Lc.ref_d, h->tol_c, 0.0, h->flag_c, h->state_c, 0};
+    const dd::SweepStop stop{Lc.partial, dd::kSweepSlots, h->norms2_c, Lc.ref_d, h->tol_c, 0.0, h->flag_c, h->state_c,
+                             0};
     for (int i = 0; i < h->prm.correction_sweeps; ++i)
         DD_CK(dd::launch_sweep(Store::F32, Lc.geom, h->C, Lc.plane(), pair, &Lc.map_cg, Lc.tmask, stop,
                                h->prm.robin_p, h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
@@ -1216,7 +1226,8 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
                 h->h_small[2 * h->C + c] = rnorm[c] / sc;
             }
             DD_CK(cudaMemcpyAsync(h->scale_d, h->h_small, sizeof(double) * h->C, cudaMemcpyHostToDevice, st));
-            DD_CK(cudaMemcpyAsync(h->scale_inv_d, h->h_small + h->C, sizeof(double) * h->C, cudaMemcpyHostToDevice, st));
+            DD_CK(cudaMemcpyAsync(h->scale_inv_d, h->h_small + h->C, sizeof(double) * h->C, cudaMemcpyHostToDevice,
+                                  st));
             DD_CK(cudaMemcpyAsync(h->inner_ref_d, h->h_small + 2 * h->C, sizeof(double) * h->C,
                                   cudaMemcpyHostToDevice, st));
             DD_TRY(write_scaled_residual(h, st));
@@ -1531,7 +1542,8 @@ int dd_inpaint_set_data(dd_handle h, const uint8_t* mask, const float* values, i
     DD_TRY(load_data(h, mask, values, st));
     h->valid = true;
     if (keep_iterate) {
-        DD_LAUNCH(h, dd::launch_reset_known(F.H, F.W, h->C, F.u[0], F.P, F.plane(), F.mask, F.W, F.f, F.P, F.plane(), st));
+        DD_LAUNCH(h, dd::launch_reset_known(F.H, F.W, h->C, F.u[0], F.P, F.plane(), F.mask, F.W, F.f, F.P, F.plane(),
+                                            st));
         h->warm = true;
     } else {
         h->warm = false;
@@ -1617,7 +1629,8 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     Level& F = h->lv[0];
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, h->cur, h->tol_d, -1.0, st));
     const dd::SweepPair pair{{&F.map_u[0], &F.map_u[1]}, {F.u[0], F.u[1]}};
-    const dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, h->tol_d, 0.0, h->flag_d, h->sstate_d, 0};
+    const dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, h->tol_d, 0.0, h->flag_d, h->sstate_d,
+                             0};
     if (corrects(h)) DD_TRY(reset_correction(h, st));
     for (int i = 0; i < n; ++i) {   // tol < 0: every launch is a full sweep
         DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), pair, nullptr, F.tmask, stop,
@@ -1764,13 +1777,15 @@ int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double
     b->side.resize(n, nullptr);
     b->evs.resize(2 * n + 1, nullptr);
     for (int i = 0; i < n; ++i)
-        if ((e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
+        if ((e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking)) != cudaSuccess)
+            return bail("stream", e);
     for (auto& ev : b->evs)
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
     // capture: fork one stream per frame, enqueue each frame's solve, join
     long long before = 0;
     for (auto h : b->hs) before += h->launches;
-    if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return bail("capture", e);
+    if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail("capture", e);
     int rc = DD_OK;
     if ((e = cudaEventRecord(b->evs[2 * n], b->cap)) != cudaSuccess) rc = DD_ECUDA;
     for (int i = 0; i < n && rc == DD_OK; ++i) {
