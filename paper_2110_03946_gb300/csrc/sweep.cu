@@ -7,8 +7,9 @@
 // core only (u^{n+1} = u^n + sum_i R_i^T D_i v_i, D_i 0/1).  All blocks read
 // u^n and write u^{n+1} into a second buffer (additive Schwarz).
 //
-// GPU mapping.  Persistent CTAs walk the (channel, block) list.  Thread 0
-// stages the next block's tile plus a one-pixel halo (and the correction
+// GPU mapping.  Persistent CTAs take (channel, block) tiles in increasing
+// order from an atomic counter, so CTAs whose local problems stop early take
+// more tiles.  Thread 0 stages the next block's tile plus a one-pixel halo (and the correction
 // source, if any) into shared memory with a TMA tensor copy while the CTA
 // works on the current block (two buffers, one mbarrier each; every wait is
 // bounded and a timeout sets an error word).  The block is then held in
