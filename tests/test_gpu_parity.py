@@ -280,6 +280,22 @@ def test_repeatable_bitwise_under_concurrency():
             ip.close()
 
 
+def test_many_channels_more_tiles_than_ctas():
+    """16 channels of 300 x 290 pixels: 1760 tiles of 32 x 32 at stride 29, more
+    than the persistent CTAs, so CTAs take tiles of several channels and each
+    channel's exact residual sum collects partials from many CTAs."""
+    f, m = synth.make_frame(290, 300, 16, 0.04, "edge", 41)
+    prm = dict(block=32, overlap=3, local_cg_iters=20, local_rtol=0.05, robin_p=0.15, levels=2, precision="fp32")
+    with Inpainter(m, f, **prm) as ip:
+        u = ip.solve(1e-6).cpu().numpy()
+        st = ip.stats()
+        u2 = ip.solve(1e-6).cpu().numpy()
+        assert ip.stats()["rel_residual"] == st["rel_residual"]
+    assert st["converged"] and np.array_equal(u, u2)
+    assert np.max(np.abs(u - ref.solve_direct(f, m))) <= TOL_U
+    assert np.all(ref.rel_residual(u.astype(np.float64), f, m) <= 1e-6)
+
+
 @pytest.mark.parametrize("solver", ["oras", "cg"])
 def test_device_loop_matches_launches(solver):
     """The level iterations repeated in a CUDA graph loop on the device give the
