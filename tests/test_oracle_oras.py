@@ -281,3 +281,40 @@ def test_local_rtol_sweep_still_converges(rng):
     for _ in range(60):
         u, _ = oras.oras_sweep(u, f, m, 12, 3, 0.3, 16, A=A, local_rtol=0.05)
     assert np.max(np.abs(u - ref.solve_direct(f, m))) <= 1e-6
+
+
+def _cg_one_reduction(M, rhs, k):
+    """The CUDA sweep's form of the local CG, written here in FP64: each step
+    forms (p, Ap), (Ap, Ap) and the measured (r, r) together; alpha uses the
+    measured (r, r), beta = alpha (Ap, Ap)/(p, Ap) - 1 (the recurrence
+    |r - alpha Ap|^2 = alpha^2 (Ap, Ap) - (r, r), valid since (r, Ap) = (p, Ap))."""
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    p = r.copy()
+    for _ in range(k):
+        Ap = M @ p
+        pq, qq, rr = float(p @ Ap), float(Ap @ Ap), float(r @ r)
+        if not (pq > 0.0 and rr > 0.0):
+            break
+        alpha = rr / pq
+        beta = alpha * qq / pq - 1.0
+        x += alpha * p
+        r -= alpha * Ap
+        p = r + beta * p
+    return x
+
+
+def test_one_reduction_cg_step_equals_textbook_cg(rng):
+    """The kernel's one-reduction step gives the textbook CG iterates (Saad,
+    the oracle's cg_fixed) to rounding, on ORAS local problems with Robin
+    interfaces and scattered known pixels, for every step count."""
+    f, m = _case(rng, 40, 40, 0.05)
+    A = ref.assemble_A(m)
+    for blk in oras.subdomains(40, 40, 16, 3)[:4]:
+        idx, M = oras.local_matrix(A, m, blk, 0.15)
+        unk = m.ravel()[idx] == 0
+        Muu = M[unk][:, unk].tocsr()
+        rhs = rng.normal(size=int(unk.sum()))
+        for k in (1, 2, 5, 10, 20):
+            a, b = oras.cg_fixed(Muu, rhs, k), _cg_one_reduction(Muu, rhs, k)
+            assert np.max(np.abs(a - b)) <= 1e-9 * max(1.0, np.max(np.abs(a)))
