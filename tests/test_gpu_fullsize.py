@@ -1,0 +1,111 @@
+"""Parity at the workloads' full sizes, in the launch configuration of bench.py.
+
+The 4K RGB workload (3840 x 2160 x 3, 3 % edge-clustered mask) runs with the
+autotuned parameters the bench uses:
+- in FP32, three frames in flight on three streams through the asynchronous
+  C ABI, as in the bench's timed region;
+- with FP16 inner storage and the FP64-accurate outer correction.
+The 1080p workload (1920 x 1080 x 3, 4 % edge-clustered) runs with 64 x 64
+blocks at overlap 4 and a 1/8 coarsest grid (4 dyadic levels).
+
+Frame 0 of each is compared pixel by pixel with the oracle's FP64 CG solution
+to rel-res 1e-12: max|du| <= 0.05 on the 0-255 scale, the bound for
+FP32-output solves.  Every frame is also checked for properties that hold at
+any size:
+- the oracle-evaluated relative residual <= tol;
+- known pixels reproduced exactly;
+- the discrete maximum principle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import cg as ocg
+from oracle import inpaint_ref as ref
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2110_03946_gb300 import autotune  # noqa: E402
+from paper_2110_03946_gb300 import binding as B  # noqa: E402
+from paper_2110_03946_gb300.inpaint import Inpainter  # noqa: E402
+
+DEV = torch.device("cuda:0")
+TOL = 1e-6
+TOL_U = 0.05
+FALLBACK = dict(block=32, overlap=6, local_cg_iters=16, robin_p=0.0, levels=3, coarse_tol=1e-2)
+
+
+def _params(name, precision):
+    w = synth.WORKLOADS[name]
+    tuned = autotune.lookup(w.H, w.W, w.C, w.density, precision, TOL)
+    return dict(tuned if tuned else FALLBACK, precision=precision)
+
+
+def _check_properties(u, f, m):
+    known = m != 0
+    assert np.isfinite(u).all()
+    assert np.all(ref.rel_residual(u.astype(np.float64), f, m) <= TOL)
+    assert np.array_equal(u[:, known], f[:, known].astype(np.float32))
+    for c in range(f.shape[0]):
+        lo, hi = f[c][known].min(), f[c][known].max()
+        assert lo - TOL_U <= u[c].min() and u[c].max() <= hi + TOL_U
+
+
+@pytest.fixture(scope="module")
+def frames4k():
+    return [synth.workload_frame("rgb4k_edge3", j) for j in range(3)]
+
+
+@pytest.fixture(scope="module")
+def exact4k(frames4k):
+    f, m = frames4k[0]
+    u, _, rel = ocg.solve_cg(f, m, tol=1e-12)
+    assert np.all(rel <= 1e-10)
+    return u
+
+
+def test_rgb4k_fp32_three_in_flight(frames4k, exact4k):
+    prm = _params("rgb4k_edge3", "fp32")
+    dm = [torch.as_tensor(m).to(DEV) for _, m in frames4k]
+    dv = [torch.as_tensor(f).to(DEV) for f, _ in frames4k]
+    ips = [Inpainter(dm[0], dv[0], device=DEV, **prm) for _ in frames4k]
+    streams = [torch.cuda.Stream(DEV) for _ in frames4k]
+    outs = [torch.empty(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames4k]
+    try:
+        for ip, s, md, vd, o in zip(ips, streams, dm, dv, outs):
+            B.check(B.dd_inpaint_set_data_async(ip._h, md.data_ptr(), vd.data_ptr(), 0, s), "set_data_async")
+            B.check(B.dd_inpaint_solve_async(ip._h, o.data_ptr(), TOL, s), "solve_async")
+        for ip, s in zip(ips, streams):
+            B.check(B.dd_inpaint_solve_finish(ip._h, s), "finish")
+        us = [o.cpu().numpy() for o in outs]
+    finally:
+        for ip in ips:
+            ip.close()
+    assert np.max(np.abs(us[0] - exact4k)) <= TOL_U
+    for u, (f, m) in zip(us, frames4k):
+        _check_properties(u, f, m)
+
+
+def test_rgb4k_fp16_storage_with_fp64_correction(frames4k, exact4k):
+    f, m = frames4k[0]
+    with Inpainter(m, f, device=DEV, **_params("rgb4k_edge3", "fp16_ref")) as ip:
+        u = ip.solve(TOL).cpu().numpy()
+        assert ip.stats()["corrections"] >= 1
+    assert np.max(np.abs(u - exact4k)) <= TOL_U
+    _check_properties(u, f, m)
+
+
+def test_rgb1080p_blocks64_overlap4_eighth_coarse_grid():
+    f, m = synth.workload_frame("rgb1080p_edge4", 0)
+    prm = dict(block=64, overlap=4, local_cg_iters=20, local_rtol=0.05, robin_p=0.15, levels=4, coarse_tol=3e-3,
+               precision="fp32")
+    with Inpainter(m, f, device=DEV, **prm) as ip:
+        u = ip.solve(TOL).cpu().numpy()
+        assert ip.stats()["converged"]
+    exact, _, rel = ocg.solve_cg(f, m, tol=1e-12)
+    assert np.all(rel <= 1e-10)
+    assert np.max(np.abs(u - exact)) <= TOL_U
+    _check_properties(u, f, m)
