@@ -109,3 +109,44 @@ def test_rgb1080p_blocks64_overlap4_eighth_coarse_grid():
     assert np.all(rel <= 1e-10)
     assert np.max(np.abs(u - exact)) <= TOL_U
     _check_properties(u, f, m)
+
+
+def test_batch_of_48_mixed_frames_one_graph():
+    """The bench's batch: 48 frames of 512x512, 1280x720, 1920x1080 and
+    3840x2160 RGB (mask density U[1 %, 10 %], uniform and edge-clustered in
+    turn, the same seeds) solved by one CUDA-graph launch with the 4K FP32
+    parameters.  Every frame converges and meets the properties; the 512x512
+    frames are also compared with the oracle's direct solution."""
+    rng = np.random.default_rng(4000)
+    sizes = [(512, 512), (720, 1280), (1080, 1920), (2160, 3840)]
+    frames = []
+    for j in range(48):
+        H, W = sizes[rng.integers(4)]
+        d = rng.uniform(0.01, 0.10)
+        frames.append(synth.make_frame(H, W, 3, d, "uniform" if j % 2 == 0 else "edge", 4000 + j))
+    prm = _params("rgb4k_edge3", "fp32")
+    ips = [Inpainter(m, f, device=DEV, **prm) for f, m in frames]
+    outs = [torch.empty(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames]
+    try:
+        rc, b, _ = B.dd_batch_create([ip._h for ip in ips], [o.data_ptr() for o in outs], TOL)
+        B.check(rc, "dd_batch_create")
+        try:
+            stream = torch.cuda.current_stream(DEV)
+            B.check(B.dd_batch_launch(b, stream), "dd_batch_launch")
+            rc, status = B.dd_batch_finish(b, len(ips), stream)
+            assert rc == B.DD_OK and all(sc == B.DD_OK for sc in status)
+        finally:
+            B.dd_batch_destroy(b)
+        for ip in ips:
+            assert ip.stats()["converged"]
+        us = [o.cpu().numpy() for o in outs]
+    finally:
+        for ip in ips:
+            ip.close()
+    small = 0
+    for u, (f, m) in zip(us, frames):
+        _check_properties(u, f, m)
+        if f.shape[1:] == (512, 512):
+            assert np.max(np.abs(u - ref.solve_direct(f, m))) <= TOL_U
+            small += 1
+    assert small > 0
