@@ -150,3 +150,36 @@ def test_batch_of_48_mixed_frames_one_graph():
             assert np.max(np.abs(u - ref.solve_direct(f, m))) <= TOL_U
             small += 1
     assert small > 0
+
+
+def test_serving_stream_full_size_alone_and_in_the_mix():
+    """The bench's serving mix at full size: Poisson arrivals at 60 requests/s,
+    70 % 4K, 20 % 1080p and 10 % 720p RGB video sequences warm-started from the
+    previous frame, 4K FP32 parameters, 40 GB HBM budget.  Each result equals
+    the same frame solved alone (bit for bit when cold, within the FP32 bound
+    when warm) and meets the residual and property checks."""
+    from paper_2110_03946_gb300.serve import CudaBackend, Server, make_pool, poisson_stream
+    shapes = [(2160, 3840, 3), (1080, 1920, 3), (720, 1280, 3)]
+    pool = make_pool(shapes, n_frames=3, n_masks=2, density_range=(0.02, 0.08), seed=5000)
+    reqs = poisson_stream(60.0, 0.4, shapes, [0.7, 0.2, 0.1], 30, 5001, pool)
+    assert len(reqs) >= 8
+    w = synth.WORKLOADS["rgb4k_edge3"]
+    prm = autotune.lookup(w.H, w.W, w.C, w.density, "fp32", TOL) or FALLBACK
+    srv = Server(CudaBackend(prm, tol=TOL, device=DEV), hbm_budget=40 << 30)
+    got = {}
+    try:
+        _, met = srv.run(reqs, realtime=False, on_result=lambda r: got.__setitem__(r.rid, (r.output.clone(), r.warm)))
+    finally:
+        srv.close()
+    assert met["failures"] == 0 and len(got) == len(reqs) and met["warm_starts"] > 0
+    for rq in reqs:
+        u, warm = got[rq.rid]
+        u = u.numpy()
+        f, mask = rq.values.numpy(), rq.mask.numpy()
+        with Inpainter(mask, f, device=DEV, precision="fp32", **prm) as ip:
+            alone = ip.solve(TOL).cpu().numpy()
+        if warm:
+            assert np.max(np.abs(u - alone)) <= TOL_U
+        else:
+            assert np.array_equal(u, alone)
+        _check_properties(u, f.astype(np.float32), mask)
