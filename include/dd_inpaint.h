@@ -156,10 +156,15 @@ int dd_inpaint_create(int H, int W, int C, const uint8_t *mask, const float *val
 /*
  * Solve to relative residual `tol` (per channel ||b - A u|| / ||b - A u0||,
  * u0 = C f; stop when the maximum over channels is <= tol) and write the
- * solution to u_out (DEVICE, C*H*W floats, caller-owned).  The stop test is
- * read back each sweep chunk, so the call synchronises `stream`.  Starts from
- * the handle's iterate if dd_inpaint_set_data(..., keep_iterate=1) asked for a
- * warm start, else from the multilevel initialisation.
+ * solution to u_out (DEVICE, C*H*W floats, caller-owned).  With device_loop
+ * = 1 (the default) each level's sweeps repeat on the device until its stop
+ * test and the host reads the result once; with device_loop = 0 the stop test
+ * is read back after each chunk of launches.  Either way the call synchronises
+ * `stream`.  Starts from the handle's iterate if dd_inpaint_set_data(...,
+ * keep_iterate=1) asked for a warm start, else from the multilevel
+ * initialisation.  For the same inputs and parameters the result, the sweep
+ * counts and the residual norms are bitwise repeatable, whatever else runs on
+ * the GPU (the residual sums are exact fixed-point sums).
  * Errors: DD_EINVAL, DD_ENOTCONVERGED (u_out still holds the best iterate),
  * DD_ENUMERIC, DD_ETIMEOUT, DD_ECUDA.
  */
