@@ -212,6 +212,27 @@ def cpu_oracle_sample(f, mask):
     return 1.0 / (C * dt), ocg.threads(), dt
 
 
+def cpu_oracle_single_thread(f, mask):
+    """The same oracle sample (channel 0 to rel-res TOL) on one host thread:
+    a fresh interpreter with OMP_NUM_THREADS=1 (no CUDA state is forked);
+    returns (frames/s scaled to the frame's channels, seconds)."""
+    import tempfile
+
+    import numpy as np
+    with tempfile.TemporaryDirectory() as td:
+        np.save(os.path.join(td, "f.npy"), np.ascontiguousarray(f[0]))
+        np.save(os.path.join(td, "m.npy"), np.ascontiguousarray(mask))
+        code = ("import sys, time, numpy as np; sys.path.insert(0, sys.argv[1]); from oracle import cg; "
+                "f = np.load(sys.argv[2]); m = np.load(sys.argv[3]); t = time.perf_counter(); "
+                "cg.solve_cg(f, m, tol=float(sys.argv[4])); print(time.perf_counter() - t, cg.threads())")
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, "-c", code, ROOT, os.path.join(td, "f.npy"),
+                              os.path.join(td, "m.npy"), repr(TOL)], env=env, check=True,
+                             capture_output=True, text=True).stdout.split()
+    secs, nthr = float(out[0]), int(out[1])
+    return 1.0 / (f.shape[0] * secs), secs, nthr
+
+
 def oracle_error(dev, md, fd, f, mask, legs):
     """Error of the GPU results against the FP64 oracle on channel 0 of one
     frame (part of the CPU leg, untimed): the oracle CG to rel-res 1e-12, and
@@ -770,6 +791,8 @@ def run_ours(args):
         cpu = {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"channel 0 of one 3840x2160 frame, FP64 oracle CG to rel-res {TOL:g} "
                          f"({secs:.1f} s), scaled to 3 channels per frame"}
+        fps1, secs1, nthr1 = cpu_oracle_single_thread(f0, m0)
+        cpu["single_thread"] = {"value": fps1, "unit": UNIT, "cores": nthr1, "seconds_channel0": secs1}
         legs = [("fp32", prm)]
         if args.precision == "fp32" and not args.no_mixed:
             legs.append(("fp16_ref", dict(solver_params(args, "fp16_ref")[0], precision="fp16_ref")))
