@@ -76,10 +76,14 @@ typedef struct dd_params {
     int    block;            /* block side in pixels: 16, 32 or 64 (default 32, Sec. 4) */
     int    overlap;          /* overlap in pixels, 0 <= overlap < block (default 6, Sec. 4) */
     int    local_cg_iters;   /* CG steps per local problem and sweep, >= 1 (default 16) */
-    int    levels;           /* resolution levels, 1..8 (default 3, Sec. 4) */
+    int    levels;           /* solved resolution levels, 1..8 (default 3, Sec. 4) */
     int    ml_mode;          /* DD_ML_CASCADE (default) or DD_ML_CORRECTION */
-    int    coarse_factor;    /* kept for ABI; DD_ML_CORRECTION corrects on the coarsest level,
-                                2^(levels-1) times coarser than the image */
+    int    coarse_factor;    /* 2 (default; 0 also means 2), 4 or 8: each solved level is this many
+                                times coarser per axis than the next finer one.  With 4 or 8 the
+                                dyadic levels in between are built by the 2x2 restriction and
+                                passed through by the prolongation, without sweeps; at most 8
+                                dyadic levels in all.  DD_ML_CORRECTION corrects on the coarsest
+                                level */
     float  robin_p;          /* Robin interface weight p > 0 (1 = RAS); <= 0 selects the default */
     int    precision;        /* DD_PREC_* (default DD_PREC_FP32_REF) */
     int    max_sweeps;       /* fine-level sweep limit per solve (default 400) */
@@ -100,8 +104,14 @@ typedef struct dd_params {
     int    device_loop;      /* 1 (default): a level's sweeps (or CG iterations) repeat inside a
                                 CUDA graph loop on the device until its stop test or sweep limit,
                                 no launch after the stop; 0: launched in fixed chunks whose launches
-                                after the stop do no work.  Timing (timing = 1) and stream
-                                capture (dd_batch) always use launches */
+                                after the stop do no work.  Timing (timing = 1) always uses
+                                launches */
+    int    test_stall_polls; /* tests only, 0 (default) = off.  > 0: in every sweep launch, each
+                                CTA's first wait for a staged tile polls a barrier that no copy
+                                ever completes, this many times, and then gives up as it would
+                                for a hung copy.  The solve then ends with DD_ETIMEOUT (the
+                                copies in flight are waited for, nothing faults) and the handle
+                                stays usable.  It exercises the timeout path without a fault */
 } dd_params;
 
 #define DD_MAX_STAT_CHANNELS 16
@@ -109,7 +119,8 @@ typedef struct dd_params {
 
 typedef struct dd_stats {
     int    sweeps_total;                       /* ORAS sweeps of the last solve, all levels */
-    int    sweeps_per_level[DD_MAX_LEVELS];    /* level 0 = finest */
+    int    sweeps_per_level[DD_MAX_LEVELS];    /* per dyadic level, 0 = finest (with coarse_factor
+                                                  4 or 8 the pass-through levels show 0) */
     int    corrections;                        /* FP64 outer corrections applied */
     int    converged;                          /* 1 if the stop test held */
     int    channels;
@@ -186,10 +197,12 @@ int dd_inpaint_set_data(dd_handle h, const uint8_t *mask, const float *values, i
 int dd_inpaint_stats(dd_handle h, dd_stats *out);
 
 /* ---------------------------------------------------------------------------
- * Asynchronous use (precision DD_PREC_FP32 only).  The solve is split into an
- * enqueue that returns at once and a finish that waits for the result, so one
- * host thread can keep several handles (on several streams) busy and data
- * copies can overlap solves.  Sec. 3-4 of the paper (the same method).
+ * Asynchronous use (precision DD_PREC_FP32, or any DD_PREC_*_REF precision with
+ * device_loop = 1, whose correction loop then runs on the device).  The solve
+ * is split into an enqueue that returns at once and a finish that waits for
+ * the result, so one host thread can keep several handles (on several streams)
+ * busy and data copies can overlap solves.  Sec. 3-4 of the paper (the same
+ * method).
  * ------------------------------------------------------------------------- */
 
 /*
@@ -203,9 +216,11 @@ int dd_inpaint_set_data_async(dd_handle h, const uint8_t *mask, const float *val
 
 /*
  * Enqueue a solve to relative residual tol on stream: the multilevel
- * initialisation, up to 16 fine sweeps under the device stop test, the output
- * of the resolved iterate to u_out (DEVICE, C*H*W floats) and its residual.
- * Returns without waiting.  Errors: DD_EINVAL (not FP32, a solve in flight),
+ * initialisation, the fine sweeps under the device stop test (with
+ * device_loop = 0: the first 16; with a correction precision: the whole
+ * correction loop), the output of the resolved iterate to u_out (DEVICE,
+ * C*H*W floats) and its residual.  Returns without waiting.  Errors:
+ * DD_EINVAL (a correction precision with device_loop = 0, a solve in flight),
  * DD_EEMPTYMASK, DD_ECUDA.
  */
 int dd_inpaint_solve_async(dd_handle h, float *u_out, double tol, void *stream);
@@ -320,12 +335,18 @@ int dd_residual_norms(int H, int W, int C, const uint8_t *mask, const float *f,
  * latency or failure is not acceptable.  This call runs the same one-level FP32
  * ORAS sweeps as dd_inpaint_solve with levels = 1 and precision = DD_PREC_FP32,
  * but takes all its scratch from one fixed-size device array that is part of
- * the library (about 42 MiB, present on every GPU that loads the library until
- * the process exits).  It calls no cudaMalloc, cudaFree or other allocating
- * routine.
+ * the library (about 42 MiB).  The array is committed on a device when the
+ * library's module is loaded there: under CUDA's default lazy module loading
+ * that is this call's first use on the device, which then pays the load
+ * latency and can fail with DD_ECUDA if device memory is short, so a real-time
+ * caller should make one warm-up call at start-up.  The array stays until the
+ * process exits.  The call itself runs no cudaMalloc, cudaFree or other
+ * allocating routine.
  *   mask (H*W bytes), values (C*H*W floats), u_out (C*H*W floats): DEVICE;
- *   params: NULL = defaults; block, overlap, local_cg_iters, robin_p and
- *   max_sweeps are used, levels and precision are ignored;
+ *   params: NULL = defaults; block, overlap, local_cg_iters, local_rtol,
+ *   robin_p, tile_warps, max_sweeps and test_stall_polls are used; solver must
+ *   be DD_SOLVER_ORAS; levels, ml_mode, coarse_factor, precision and the
+ *   other fields are ignored;
  *   tol: relative residual target as in dd_inpaint_solve (FP64-verified).
  * Capacity: C <= 16, C*H*roundup(W,32) <= 4194304, at most 16384 blocks per
  * channel, blocks x threads per block <= 1048576 (32 threads per block for
@@ -342,6 +363,34 @@ int dd_residual_norms(int H, int W, int C, const uint8_t *mask, const float *f,
  */
 int dd_inpaint_solve_static(int H, int W, int C, const uint8_t *mask, const float *values, float *u_out,
                             const dd_params *params, double tol, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Device budget and measurement (the paper has no counterpart).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Cap the device memory that all live handles of this process may hold
+ * together (bytes; 0, the default, means no cap beyond the GPU's own).  An
+ * allocation that would exceed the cap fails as an out-of-memory would:
+ * dd_inpaint_create returns DD_ENOMEM and makes no handle.  Existing handles
+ * are not affected.  Thread-safe.
+ */
+void dd_set_device_budget(size_t bytes);
+
+/* Device bytes held by all live handles of this process (dd_stats.device_bytes
+ * summed).  Thread-safe. */
+size_t dd_device_bytes_in_use(void);
+
+/*
+ * FP32 FMA throughput of the current device, measured: a grid of the maximum
+ * resident warps per SM runs independent chains of packed FP32 FMAs
+ * (__ffma2_rn), timed with CUDA events on stream, best of `reps` launches
+ * after one warm-up.  *tflops receives TFLOP/s (2 flops per FMA); *sm_count
+ * (may be NULL) the device's SM count.  This is the denominator of the sweep
+ * kernel's roofline.  Allocates and frees a few KB of device memory.
+ * Synchronises stream.  Errors: DD_EINVAL, DD_ENOMEM, DD_ECUDA.
+ */
+int dd_fp32_fma_peak(int reps, double *tflops, int *sm_count, void *stream);
 
 #ifdef __cplusplus
 }

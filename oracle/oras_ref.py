@@ -38,7 +38,6 @@ Readings taken where the text is silent or garbled:
 """
 from __future__ import annotations
 
-import math
 
 import numpy as np
 import scipy.sparse as sp
@@ -49,7 +48,7 @@ from . import inpaint_ref as ref
 __all__ = [
     "axis_blocks", "block_count", "owner_of", "subdomains", "local_matrix",
     "cg_fixed", "oras_sweep", "oras_solve", "restrict_level", "prolong_bilinear",
-    "robin_default", "build_hierarchy", "cascade_solve", "restrict_sum", "correction_pass",
+    "build_hierarchy", "cascade_solve", "restrict_sum", "correction_pass",
 ]
 
 
@@ -88,14 +87,6 @@ def subdomains(H: int, W: int, b: int, o: int):
         for (x0, x1, ox0, ox1) in axis_blocks(W, b, o):
             out.append((y0, y1, x0, x1, oy0, oy1, ox0, ox1))
     return out
-
-
-def robin_default(b: int, o: int) -> float:
-    """Robin parameter of the optimised overlapping Schwarz method (Gander,
-    'Optimized Schwarz methods', SIAM J. Numer. Anal. 44, 2006): for overlap L
-    and smallest frequency k_min, p = 2^(-1/3) k_min^(2/3) L^(-1/3).  Here
-    k_min = pi / b and L = max(o, 1), in pixel units."""
-    return 2.0 ** (-1.0 / 3.0) * (math.pi / b) ** (2.0 / 3.0) * max(o, 1) ** (-1.0 / 3.0)
 
 
 # ------------------------------------------------------ local problem (Sec. 3)

@@ -29,6 +29,7 @@ EXPORTS = (
     "dd_restrict", "dd_prolong", "dd_residual_norms", "dd_inpaint_solve_static",
     "dd_inpaint_set_data_async", "dd_inpaint_solve_async", "dd_inpaint_query", "dd_inpaint_solve_finish",
     "dd_batch_create", "dd_batch_launch", "dd_batch_finish", "dd_batch_destroy",
+    "dd_set_device_budget", "dd_device_bytes_in_use", "dd_fp32_fma_peak",
 )
 
 
@@ -40,7 +41,7 @@ class dd_params(ctypes.Structure):
         ("inputs_on_device", ctypes.c_int), ("coarse_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
         ("max_corrections", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("timing", ctypes.c_int),
         ("tile_warps", ctypes.c_int), ("solver", ctypes.c_int), ("correction_sweeps", ctypes.c_int),
-        ("local_rtol", ctypes.c_double), ("device_loop", ctypes.c_int),
+        ("local_rtol", ctypes.c_double), ("device_loop", ctypes.c_int), ("test_stall_polls", ctypes.c_int),
     ]
 
 
@@ -97,6 +98,9 @@ def load(path: str | None = None):
         "dd_batch_launch": (_I, [_P, _P]),
         "dd_batch_finish": (_I, [_P, _P, ctypes.POINTER(_I)]),
         "dd_batch_destroy": (_I, [_P]),
+        "dd_set_device_budget": (None, [ctypes.c_size_t]),
+        "dd_device_bytes_in_use": (ctypes.c_size_t, []),
+        "dd_fp32_fma_peak": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -250,3 +254,19 @@ def dd_batch_finish(b, n: int, stream=None):
 
 def dd_batch_destroy(b) -> int:
     return load().dd_batch_destroy(b)
+
+
+def dd_set_device_budget(nbytes: int) -> None:
+    load().dd_set_device_budget(int(nbytes))
+
+
+def dd_device_bytes_in_use() -> int:
+    return int(load().dd_device_bytes_in_use())
+
+
+def dd_fp32_fma_peak(reps: int = 5, stream=None):
+    """Returns (code, TFLOP/s, SM count)."""
+    t = ctypes.c_double(0.0)
+    n = ctypes.c_int(0)
+    rc = load().dd_fp32_fma_peak(int(reps), ctypes.byref(t), ctypes.byref(n), _stream(stream))
+    return rc, t.value, n.value

@@ -682,7 +682,8 @@ __global__ void correct_kernel(int H, int W, float* __restrict__ u, int up, long
 // Outer control of the device-driven correction loop (one thread), after the
 // FP64-accurate residual of u (res_out[c] = {sum r^2, max |r|}).  ctl: [0]
 // corrections applied, [1] inner sweeps applied, [2] outcome (0 running,
-// 1 converged, 2 limit reached, 3 NaN/Inf), [3] outer passes, [4] inner loop
+// 1 converged, 2 limit reached, 3 NaN/Inf, 4 a bounded wait gave up: *err != 0),
+// [3] outer passes, [4] inner loop
 // passes, [5] skip (the rest of this pass does nothing).  First the previous
 // inner solve is added up (inner_state[1] full sweeps, inner_ctl[0] passes);
 // then either the loop ends (condition cleared) or the next correction's
@@ -691,7 +692,7 @@ __global__ void correct_kernel(int H, int W, float* __restrict__ u, int up, long
 __global__ void ref_outer_ctl_kernel(const double2* __restrict__ res_out, const double* __restrict__ ref, int C,
                                      const double* __restrict__ tol, int max_corr, int max_sweeps,
                                      const int* __restrict__ inner_state, const int* __restrict__ inner_ctl,
-                                     int* __restrict__ ctl, double* __restrict__ scale,
+                                     const int* __restrict__ err, int* __restrict__ ctl, double* __restrict__ scale,
                                      double* __restrict__ scale_inv, double* __restrict__ inner_ref,
                                      cudaGraphConditionalHandle cond) {
     if (threadIdx.x != 0) return;
@@ -710,7 +711,8 @@ __global__ void ref_outer_ctl_kernel(const double2* __restrict__ res_out, const 
         worst = fmax(worst, sqrt(s) / den);
     }
     int done = 0;
-    if (bad) done = 3;
+    if (*err != 0) done = 4;
+    else if (bad) done = 3;
     else if (worst <= *tol) done = 1;
     else if (ctl[0] >= max_corr || ctl[1] >= max_sweeps || passes > max_corr + 1) done = 2;
     if (done == 0) {
@@ -874,11 +876,11 @@ cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long upla
 }
 
 cudaError_t launch_ref_outer_ctl(const double2* res_out, const double* ref, int C, const double* tol, int max_corr,
-                                 int max_sweeps, const int* inner_state, const int* inner_ctl, int* ctl,
-                                 double* scale, double* scale_inv, double* inner_ref,
+                                 int max_sweeps, const int* inner_state, const int* inner_ctl, const int* err,
+                                 int* ctl, double* scale, double* scale_inv, double* inner_ref,
                                  cudaGraphConditionalHandle cond, cudaStream_t st) {
-    ref_outer_ctl_kernel<<<1, 32, 0, st>>>(res_out, ref, C, tol, max_corr, max_sweeps, inner_state, inner_ctl, ctl,
-                                           scale, scale_inv, inner_ref, cond);
+    ref_outer_ctl_kernel<<<1, 32, 0, st>>>(res_out, ref, C, tol, max_corr, max_sweeps, inner_state, inner_ctl, err,
+                                           ctl, scale, scale_inv, inner_ref, cond);
     return cudaGetLastError();
 }
 

@@ -57,17 +57,18 @@ cudaError_t make_tile_map(CUtensorMap* out, Store st, const void* base, int H, i
 // persistent CTAs in increasing order by an atomic counter (flag[4]), so which
 // CTA takes which tile varies from run to run; the sums do not: each tile's FP32
 // sum of squared owned residuals of the input iterate is added exactly into a
-// 128-bit fixed-point accumulator (unit 2^-80 ref[c]^2, saturating at
+// 128-bit fixed-point accumulator (unit about 2^-72 ref[c]^2, saturating at
 // 2^32 ref[c]^2, values below the unit truncated), and integer addition does
 // not depend on the order.  Each CTA writes its per-channel accumulator to
 // partial[2 * (c * slots + cta) + {0: low, 1: high word}]; the last CTA to
 // finish adds them into norms2[c] (bitwise repeatable) and sets flag[0]:
 //   1 when max_c sqrt(norms2[c]) / ref[c] <= tol (tol < 0: never),
 //   2 on NaN/Inf, 3 when stall > 0 and every channel's residual fell by less
-//   than the factor 1/stall since the previous full sweep;
+//   than the factor 1/stall since the previous full sweep, 5 when a bounded
+//   wait of this or an earlier launch gave up (*err != 0);
 // flag[1] = the launch index (state[3]) then.  flag[0] != 0 makes later launches no-ops.
-// flag[2] is set if a bounded wait for a staged tile gave up; flag[3] is the
-// completion ticket and flag[4] the tile counter (both 0 between launches).
+// flag[3] is the completion ticket and flag[4] the tile counter (both 0
+// between launches); flag[2] is unused.
 // slots >= the launch grid.
 // The iterate pair is chosen on the device: state[0] is the buffer holding the
 // current iterate (the launch reads it and writes the other one), state[1]
@@ -80,7 +81,7 @@ cudaError_t make_tile_map(CUtensorMap* out, Store st, const void* base, int H, i
 // last two sweeps predicts that the new iterate meets tol.  norms2 holds
 // 2C + 2 doubles: current norms, norms of the previous full sweep, and the
 // previous full sweep's worst relative residual.
-constexpr int kFlagWords = 8;     // flag array length (5 used)
+constexpr int kFlagWords = 8;     // flag array length (words 0, 1, 3, 4 per sequence; 5 the sticky error word)
 struct SweepStop {
     unsigned long long* partial;   // 2 x C x slots words
     int slots;
@@ -93,9 +94,20 @@ struct SweepStop {
     int* state;
     int force_probe;   // 1: this launch is a probe whatever state[2] says
     // optional work counters of full sweeps: work[0] += sum over blocks of
-    // (unknown block pixels) x (local CG steps taken), work[1] += unknown block pixels
+    // (unknown block pixels) x (local CG steps taken), work[1] += unknown block
+    // pixels, and work[2 + i] = 1 if launch i since the reset (i < kTimedLaunches)
+    // was a full sweep (0: a probe, or not run because the stop flag was set)
     unsigned long long* work;
+    // sticky error word of the handle: set to 1 when a bounded wait for a
+    // staged tile gives up (reset words of a sweep sequence do not clear it);
+    // the last CTA then sets flag[0] = 5, which ends the sequence
+    int* err;
+    // test hook (0: off): the first staged-tile wait of every CTA polls an
+    // mbarrier that no copy completes, stall_polls times, and then gives up as
+    // a hung copy would (the DD_ETIMEOUT path, exercised without a fault)
+    int stall_polls;
 };
+constexpr int kTimedLaunches = 64;   // launches per sequence whose kind work[2 + i] records
 constexpr int kSweepSlots = 4096;   // per-channel partial slots that cover any persistent grid
 
 // The two iterate buffers of a level and their TMA descriptors.
@@ -118,7 +130,8 @@ cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, co
 // per process; call before capturing a sweep launch into a graph.
 cudaError_t prepare_sweep(Store s, const TileGeom& g, bool has_g);
 
-// state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..4] = 0; *tol_d = tol
+// state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..4] = 0 (flag[5],
+// the sticky error word of a handle's flag array, is left alone); *tol_d = tol
 // (the stop tolerance the following sweeps or CG iterations read).  With
 // skip_if and *skip_if != 0, flag[0] = 4 instead: the following sweeps are
 // no-ops.
@@ -222,10 +235,10 @@ cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long upla
                            const double* scale, cudaStream_t st, const void* e1 = nullptr,
                            const int* sel = nullptr, const int* skip = nullptr);
 // The outer control of the device-driven FP64 correction loop (one thread, see
-// aux.cu): ctl[8] ints; clears cond when the loop ends.
+// aux.cu): ctl[8] ints; clears cond when the loop ends (also once *err != 0).
 cudaError_t launch_ref_outer_ctl(const double2* res_out, const double* ref, int C, const double* tol, int max_corr,
-                                 int max_sweeps, const int* inner_state, const int* inner_ctl, int* ctl,
-                                 double* scale, double* scale_inv, double* inner_ref,
+                                 int max_sweeps, const int* inner_state, const int* inner_ctl, const int* err,
+                                 int* ctl, double* scale, double* scale_inv, double* inner_ref,
                                  cudaGraphConditionalHandle cond, cudaStream_t st);
 // Summary of a sweep sequence for later steps: out[0] = buffer holding the
 // result, out[1] = full sweeps applied, out[2] = the stop flag (0: not

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <functional>
 #include <chrono>
 #include <cmath>
@@ -90,6 +91,8 @@ void destroy_loop(LoopGraph& G) {
 
 struct Level {
     int H = 0, W = 0, P = 0;
+    bool solved = true;        // false: a dyadic level between solved ones (coarse_factor 4 or 8), which
+                               // only carries the restriction and the prolongation
     TileGeom geom;
     uint8_t* mask = nullptr;   // H x W dense
     float* f = nullptr;        // C x H x P, known values, 0 elsewhere
@@ -139,12 +142,13 @@ struct dd_inpaint {
     double2* res_out = nullptr;     // C per level
     unsigned int* res_ticket = nullptr;   // completion ticket of the fused residual reduction (zero)
     double* norms2_d = nullptr;     // C
-    int* flag_d = nullptr;          // [0] stop flag, [1] conv_at, [2] device wait timed out, [3] ticket,
-                                    // [4] tile counter (kFlagWords ints)
+    int* flag_d = nullptr;          // [0] stop flag, [1] conv_at, [3] ticket, [4] tile counter, [5] sticky
+                                    // error word of every sweep sequence of the handle (kFlagWords ints)
     int* sstate_d = nullptr;        // sweep state: current buffer, full sweeps, probe request, launches
     int* ctl_d = nullptr;           // device-loop pass counter (4 ints)
     double* tol_d = nullptr;        // stop tolerance of the running level (set by each reset)
-    unsigned long long* work_d = nullptr;   // timed fine sweeps: [0] pixel x CG steps, [1] pixels
+    unsigned long long* work_d = nullptr;   // timed fine sweeps: [0] pixel x CG steps, [1] pixels,
+                                            // [2 + i] launch i was a full sweep (kWorkWords words)
     unsigned long long* h_work = nullptr;   // pinned mirror
     // DD_ML_CORRECTION: fine residual, and the stop state of the coarse correction solve
     float* corr_r = nullptr;        // C x H x P (level 0)
@@ -165,7 +169,7 @@ struct dd_inpaint {
     // pinned host mirrors
     double2* h_res = nullptr;
     double* h_small = nullptr;      // 3*C doubles scratch
-    int* h_flag = nullptr;
+    int* h_flag = nullptr;          // [0..2] flag words, [3] error word, [4..5] sweep state
     int* h_state = nullptr;         // 4 ints per level
     double* h_ref = nullptr;        // C: fine-level reference norms read back with a solve
     unsigned long long* h_cnt = nullptr;   // [0] unknown block pixels, [1] known pixels
@@ -190,10 +194,24 @@ struct dd_inpaint {
 
 namespace {
 
+// Device bytes held by all live handles, and the caller's cap on them (0: none).
+std::atomic<unsigned long long> g_bytes_in_use{0};
+std::atomic<unsigned long long> g_budget{0};
+
 int dalloc(dd_inpaint* h, void** p, size_t n) {
     if (n == 0) n = 16;
+    const unsigned long long cap = g_budget.load();
+    const unsigned long long held = g_bytes_in_use.fetch_add(n) + n;
+    if (cap != 0 && held > cap) {
+        g_bytes_in_use.fetch_sub(n);
+        *p = nullptr;
+        set_error("the device budget set by dd_set_device_budget would be exceeded");
+        return DD_ENOMEM;
+    }
     cudaError_t e = cudaMalloc(p, n);
     if (e != cudaSuccess) {
+        g_bytes_in_use.fetch_sub(n);
+        (void)cudaGetLastError();
         set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
         return DD_ENOMEM;
     }
@@ -222,6 +240,26 @@ int dzero(void* p, size_t n) {
 int alloc_flag(dd_inpaint* h, int** f) {
     int rc = dalloc_t(h, f, dd::kFlagWords);
     return rc != DD_OK ? rc : dzero(*f, dd::kFlagWords * sizeof(int));
+}
+
+// Words of the work counters of timed sweeps: two sums and one kind per launch.
+constexpr int kWorkWords = 2 + dd::kTimedLaunches;
+
+// The sticky error word shared by all sweep sequences of a handle.
+int* err_word(dd_inpaint* h) { return h->flag_d + 5; }
+
+// A sweep sequence's stop words on the handle's flag array, with the handle's
+// error word and test hook.
+dd::SweepStop make_stop(dd_inpaint* h, unsigned long long* partial, const double* ref_d, double stall,
+                        unsigned long long* work = nullptr) {
+    return dd::SweepStop{partial, dd::kSweepSlots, h->norms2_d, ref_d, h->tol_d, stall, h->flag_d, h->sstate_d, 0,
+                         work, err_word(h), h->prm.test_stall_polls};
+}
+
+// Clear the error word at the start of a solve (enqueued, so it also works in a capture).
+int clear_error(dd_inpaint* h, cudaStream_t st) {
+    DD_CK(cudaMemsetAsync(err_word(h), 0, sizeof(int), st));
+    return DD_OK;
 }
 
 Store low_store(int precision) {
@@ -256,6 +294,11 @@ int validate(int H, int W, int C, const dd_params& p) {
         return DD_EINVAL;
     }
     if (p.precision < DD_PREC_FP32 || p.precision > DD_PREC_BF16_REF) { set_error("bad precision"); return DD_EINVAL; }
+    if (p.coarse_factor != 0 && p.coarse_factor != 2 && p.coarse_factor != 4 && p.coarse_factor != 8) {
+        set_error("coarse_factor must be 2, 4 or 8");
+        return DD_EINVAL;
+    }
+    if (p.test_stall_polls < 0) { set_error("test_stall_polls must be >= 0"); return DD_EINVAL; }
     if (p.max_sweeps < 0 || p.coarse_sweeps < 0 || p.max_corrections < 0) {
         set_error("negative limit");
         return DD_EINVAL;
@@ -369,8 +412,9 @@ int run_sweeps(dd_inpaint* h, const TileGeom& g, Store st_t, void* const bufs[2]
     *applied = 0;
     const bool timed = fine && h->prm.timing != 0;
     const dd::SweepPair pair{{&maps[0], &maps[1]}, {bufs[0], bufs[1]}};
-    dd::SweepStop stop{partial, dd::kSweepSlots, h->norms2_d, ref_d, h->tol_d, stall, h->flag_d, h->sstate_d, 0};
-    int full_done = 0;
+    dd::SweepStop stop = make_stop(h, partial, ref_d, stall, timed ? h->work_d : nullptr);
+    if (timed) DD_CK(cudaMemsetAsync(h->work_d + 2, 0, sizeof(unsigned long long) * dd::kTimedLaunches, st));
+    int full_done = 0, launched = 0;
     while (true) {
         // full sweeps until max_sweeps; then one probe evaluates the last iterate
         const bool last_probe = full_done >= max_sweeps;
@@ -383,22 +427,28 @@ int run_sweeps(dd_inpaint* h, const TileGeom& g, Store st_t, void* const bufs[2]
             if (timed && !last_probe) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
         }
         DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaMemcpyAsync(h->h_flag + 3, err_word(h), sizeof(int), cudaMemcpyDeviceToHost, st));
         DD_CK(cudaMemcpyAsync(h->h_flag + 4, h->sstate_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (timed)
+            DD_CK(cudaMemcpyAsync(h->h_work, h->work_d, sizeof(unsigned long long) * kWorkWords,
+                                  cudaMemcpyDeviceToHost, st));
         DD_CK(cudaStreamSynchronize(st));
-        if (h->h_flag[2] != 0) {
+        if (h->h_flag[3] != 0) {
             set_error("a bounded device wait for a staged tile gave up");
             return DD_ETIMEOUT;
         }
         const int new_full = h->h_flag[5];
         if (timed && !last_probe) {
-            // launches of this chunk that were full sweeps
-            for (int i = 0; i < n && i < new_full - full_done; ++i) {
+            // the launches of this chunk that ran as full sweeps (not probes)
+            for (int i = 0; i < n && launched + i < dd::kTimedLaunches; ++i) {
+                if (h->h_work[2 + launched + i] == 0) continue;
                 float ms = 0.f;
                 DD_CK(cudaEventElapsedTime(&ms, h->sw_ev[2 * i], h->sw_ev[2 * i + 1]));
                 h->stats.fine_sweep_ms += ms;
                 h->stats.fine_sweep_launches += 1;
             }
         }
+        launched += n;
         full_done = new_full;
         cur = h->h_flag[4];
         *applied = full_done;
@@ -537,7 +587,7 @@ int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
     DD_CK(dd::launch_reset_sweep_state(h->state_c, h->flag_c, 0, h->tol_c, -1.0, st, skip));
     const dd::SweepPair pair{{&Lc.map_u[0], &Lc.map_u[1]}, {Lc.u[0], Lc.u[1]}};
     const dd::SweepStop stop{Lc.partial, dd::kSweepSlots, h->norms2_c, Lc.ref_d, h->tol_c, 0.0, h->flag_c, h->state_c,
-                             0};
+                             0, nullptr, err_word(h), h->prm.test_stall_polls};
     for (int i = 0; i < h->prm.correction_sweeps; ++i)
         DD_CK(dd::launch_sweep(Store::F32, Lc.geom, h->C, Lc.plane(), pair, &Lc.map_cg, Lc.tmask, stop,
                                h->prm.robin_p, h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
@@ -579,8 +629,7 @@ int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st, bool count_work = fal
         return DD_OK;
     }
     const dd::SweepPair pair{{&L.map_u[0], &L.map_u[1]}, {L.u[0], L.u[1]}};
-    const dd::SweepStop stop{L.partial, dd::kSweepSlots, h->norms2_d, L.ref_d, h->tol_d, 0.0, h->flag_d, h->sstate_d, 0,
-                             count_work ? h->work_d : nullptr};
+    const dd::SweepStop stop = make_stop(h, L.partial, L.ref_d, 0.0, count_work ? h->work_d : nullptr);
     DD_CK(dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), pair, nullptr, L.tmask, stop, h->prm.robin_p,
                            h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
     if (&L == &h->lv[0] && corrects(h)) DD_TRY(enqueue_correction(h, st));
@@ -724,7 +773,7 @@ int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, 
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, 0, h->tol_d, tol, st));
     if (&L == &h->lv[0] && corrects(h)) DD_TRY(reset_correction(h, st));
     if (loop) return run_loop(h, L, n, st, capture);
-    if (timed) DD_CK(cudaMemsetAsync(h->work_d, 0, 2 * sizeof(unsigned long long), st));
+    if (timed) DD_CK(cudaMemsetAsync(h->work_d, 0, sizeof(unsigned long long) * kWorkWords, st));
     for (int i = 0; i < n; ++i) {
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
         DD_TRY(enqueue_pass(h, L, st, timed));
@@ -785,7 +834,11 @@ int cascade(dd_inpaint* h, cudaStream_t st, bool capture) {
                                                 Cc.plane(), L.mask, L.W, L.f, L.P, L.plane(), L.u[0], L.P,
                                                 L.plane(), st));
         }
-        DD_TRY(enqueue_level(h, L, h->prm.coarse_sweeps, h->prm.coarse_tol, st, false, capture));
+        if (L.solved) {
+            DD_TRY(enqueue_level(h, L, h->prm.coarse_sweeps, h->prm.coarse_tol, st, false, capture));
+        } else {   // pass-through level: its result is the prolonged start in u[0], no sweeps
+            DD_CK(cudaMemsetAsync(L.state_d, 0, 4 * sizeof(int), st));
+        }
     }
     Level& F = h->lv[0];
     if (nl > 1) {
@@ -856,6 +909,7 @@ int fp32_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool 
     Level& F = h->lv[0];
     h->ev_recorded = !capture;
     if (!capture) DD_CK(cudaEventRecord(h->ev0, st));
+    DD_TRY(clear_error(h, st));
     h->pending_cascaded = !h->warm;
     if (!h->warm) {
         DD_TRY(cascade(h, st, capture));
@@ -873,9 +927,12 @@ int fp32_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool 
     for (int l = 1; l < nl; ++l)
         DD_CK(cudaMemcpyAsync(h->h_state + 4 * l, h->lv[l].state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_flag + 3, err_word(h), sizeof(int), cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_ref, F.ref_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    if (timed) DD_CK(cudaMemcpyAsync(h->h_work, h->work_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if (timed)
+        DD_CK(cudaMemcpyAsync(h->h_work, h->work_d, sizeof(unsigned long long) * kWorkWords, cudaMemcpyDeviceToHost,
+                              st));
     if (!capture) DD_CK(cudaEventRecord(h->ev1, st));
     h->pending = true;
     h->pending_out = u_out;
@@ -903,7 +960,7 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
         if (h->h_cnt[1] == 0) { h->valid = false; set_error("empty mask"); return DD_EEMPTYMASK; }
     }
     F.ref.assign(h->h_ref, h->h_ref + h->C);
-    if (h->h_flag[2] != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
+    if (h->h_flag[3] != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
     if (h->pending_cascaded) take_level_stats(h);
     count_loop_launches(h);
     const int status = h->h_state[2], applied = h->h_state[1];
@@ -912,7 +969,8 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
     if (h->prm.timing != 0 && h->ev_recorded && h->prm.solver == DD_SOLVER_ORAS) {
         h->stats.fine_cg_pixel_steps = (long long)h->h_work[0];
         h->stats.fine_swept_unknowns = (long long)h->h_work[1];
-        for (int i = 0; i < applied && i < n1; ++i) {
+        for (int i = 0; i < n1 && i < dd::kTimedLaunches; ++i) {   // the launches that ran as full sweeps
+            if (h->h_work[2 + i] == 0) continue;
             float ms = 0.f;
             DD_CK(cudaEventElapsedTime(&ms, h->sw_ev[2 * i], h->sw_ev[2 * i + 1]));
             h->stats.fine_sweep_ms += ms;
@@ -986,8 +1044,7 @@ int ref_pass(dd_inpaint* h, cudaStream_t st) {
     Level& F = h->lv[0];
     const dd::SweepPair pair{{&h->map_e[0], &h->map_e[1]}, {h->e[0], h->e[1]}};
     const double stall = h->lowst == Store::F32 ? 0.0 : 0.7;
-    const dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, h->inner_ref_d, h->tol_d, stall, h->flag_d,
-                             h->sstate_d, 0};
+    const dd::SweepStop stop = make_stop(h, F.partial, h->inner_ref_d, stall);
     DD_CK(dd::launch_sweep(h->lowst, F.geom, h->C, F.plane(), pair, &h->map_g, F.tmask, stop, h->prm.robin_p,
                            h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
     return DD_OK;
@@ -1027,8 +1084,8 @@ int add_ref_outer(dd_inpaint* h, cudaGraph_t g, const cudaGraphNode_t* deps, con
         a.out = h->res_out; a.ticket = h->res_ticket;
         DD_CK(dd::launch_res64(a, bs));
         DD_CK(dd::launch_ref_outer_ctl(h->res_out, F.ref_d, h->C, h->ref_tol_d, h->prm.max_corrections,
-                                       h->prm.max_sweeps, h->sstate_d, h->ctl_d, h->ref_ctl_d, h->scale_d,
-                                       h->scale_inv_d, h->inner_ref_d, cond, bs));
+                                       h->prm.max_sweeps, h->sstate_d, h->ctl_d, err_word(h), h->ref_ctl_d,
+                                       h->scale_d, h->scale_inv_d, h->inner_ref_d, cond, bs));
         dd::Res64Args b{};
         b.H = F.H; b.W = F.W; b.C = h->C;
         b.u = F.u[0]; b.up = F.P; b.uplane = F.plane();
@@ -1090,6 +1147,7 @@ int ref_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool c
     Level& F = h->lv[0];
     h->ev_recorded = !capture;
     if (!capture) DD_CK(cudaEventRecord(h->ev0, st));
+    DD_TRY(clear_error(h, st));
     h->pending_cascaded = !h->warm;
     if (!h->warm) {
         DD_TRY(cascade(h, st, capture));
@@ -1114,6 +1172,7 @@ int ref_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool c
     for (int l = 1; l < nl; ++l)
         DD_CK(cudaMemcpyAsync(h->h_state + 4 * l, h->lv[l].state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_flag + 3, err_word(h), sizeof(int), cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_ref, F.ref_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     if (!capture) DD_CK(cudaEventRecord(h->ev1, st));
@@ -1137,7 +1196,7 @@ int ref_finish(dd_inpaint* h, cudaStream_t st) {
         if (h->h_cnt[1] == 0) { h->valid = false; set_error("empty mask"); return DD_EEMPTYMASK; }
     }
     F.ref.assign(h->h_ref, h->h_ref + h->C);
-    if (h->h_flag[2] != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
+    if (h->h_flag[3] != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
     if (h->pending_cascaded) take_level_stats(h);
     count_loop_launches(h);
     const int* c = h->h_ref_ctl;
@@ -1191,6 +1250,7 @@ int solve_impl(dd_inpaint* h, float* u_out, double tol, cudaStream_t st) {
     h->stats.local_unknowns = h->local_unknowns;
     const int nl = (int)h->lv.size();
     DD_CK(cudaEventRecord(h->ev0, st));
+    DD_TRY(clear_error(h, st));
     Level& F = h->lv[0];
     if (!h->warm) {
         DD_TRY(cascade(h, st, false));
@@ -1267,6 +1327,8 @@ void free_all(dd_inpaint* h) {
     if (h->h_ref_ctl) cudaFreeHost(h->h_ref_ctl);
     for (void* p : h->allocs) cudaFree(p);
     h->allocs.clear();
+    g_bytes_in_use.fetch_sub(h->bytes);
+    h->bytes = 0;
     if (h->h_res) cudaFreeHost(h->h_res);
     if (h->h_small) cudaFreeHost(h->h_small);
     if (h->h_flag) cudaFreeHost(h->h_flag);
@@ -1300,14 +1362,18 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     h->lowst = low_store(p.precision);
     auto fail = [&](int rc) { free_all(h); delete h; return rc; };
     int rc = DD_OK;
-    // levels: stop halving once a dimension would fall below 2 pixels
-    int nl = p.levels;
+    // dyadic levels: (levels - 1) log2(coarse_factor) halvings, at most DD_MAX_LEVELS
+    // levels in all, stopping once a dimension would fall below 2 pixels; the
+    // solved levels are every log2(coarse_factor)-th one and the coarsest
+    const int fstep = p.coarse_factor == 8 ? 3 : p.coarse_factor == 4 ? 2 : 1;
+    int nl = std::min(DD_MAX_LEVELS, (p.levels - 1) * fstep + 1);
     {
         int hh = H, ww = W, l = 1;
         while (l < nl && hh > 2 && ww > 2) { hh = (hh + 1) / 2; ww = (ww + 1) / 2; ++l; }
         nl = l;
     }
     h->lv.resize(nl);
+    for (int l = 0; l < nl; ++l) h->lv[l].solved = (l % fstep == 0) || l == nl - 1;
     int hh = H, ww = W;
     for (int l = 0; l < nl; ++l) {
         Level& L = h->lv[l];
@@ -1396,14 +1462,14 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     if ((rc = dalloc_t(h, &h->ctl_d, 4)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->tol_d, 1)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->res_ticket, 1)) != DD_OK) return fail(rc);
-    if ((rc = dalloc_t(h, &h->work_d, 2)) != DD_OK) return fail(rc);
+    if ((rc = dalloc_t(h, &h->work_d, kWorkWords)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->ref_ctl_d, 4 + dd::kFlagWords)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->ref_tol_d, 1)) != DD_OK) return fail(rc);
     if (cudaMallocHost(&h->h_ref_ctl, 8 * sizeof(int)) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         return fail(DD_ENOMEM);
     }
-    if (cudaMallocHost(&h->h_work, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMallocHost(&h->h_work, kWorkWords * sizeof(unsigned long long)) != cudaSuccess) {
         set_error("cudaMallocHost failed");
         return fail(DD_ENOMEM);
     }
@@ -1440,7 +1506,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
     // (with FP32_REF / FP16_REF / BF16_REF the fine level sweeps under host control)
     if (p.device_loop != 0) {
         for (size_t l = 0; l < h->lv.size(); ++l) {
-            if (l == 0 && p.precision != DD_PREC_FP32) continue;
+            if ((l == 0 && p.precision != DD_PREC_FP32) || !h->lv[l].solved) continue;
             cudaGraphExec_t ex = nullptr;
             if ((rc = loop_graph(h, h->lv[l], l == 0 ? p.max_sweeps : p.coarse_sweeps, &ex)) != DD_OK) return fail(rc);
         }
@@ -1505,6 +1571,10 @@ const char* dd_strerror(int code) {
 }
 
 const char* dd_last_error(void) { return g_last_error.c_str(); }
+
+void dd_set_device_budget(size_t bytes) { g_budget.store((unsigned long long)bytes); }
+
+size_t dd_device_bytes_in_use(void) { return (size_t)g_bytes_in_use.load(); }
 
 int dd_inpaint_create(int H, int W, int C, const uint8_t* mask, const float* values, const dd_params* params,
                       dd_handle* out) {
@@ -1628,9 +1698,9 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Level& F = h->lv[0];
     DD_LAUNCH(h, dd::launch_reset_sweep_state(h->sstate_d, h->flag_d, h->cur, h->tol_d, -1.0, st));
+    DD_TRY(clear_error(h, st));
     const dd::SweepPair pair{{&F.map_u[0], &F.map_u[1]}, {F.u[0], F.u[1]}};
-    const dd::SweepStop stop{F.partial, dd::kSweepSlots, h->norms2_d, F.ref_d, h->tol_d, 0.0, h->flag_d, h->sstate_d,
-                             0};
+    const dd::SweepStop stop = make_stop(h, F.partial, F.ref_d, 0.0);
     if (corrects(h)) DD_TRY(reset_correction(h, st));
     for (int i = 0; i < n; ++i) {   // tol < 0: every launch is a full sweep
         DD_LAUNCH(h, dd::launch_sweep(Store::F32, F.geom, h->C, F.plane(), pair, nullptr, F.tmask, stop,
@@ -1643,7 +1713,7 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
     }
     if (n > 0) {
         int err = 0;
-        DD_CK(cudaMemcpyAsync(&err, h->flag_d + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaMemcpyAsync(&err, err_word(h), sizeof(int), cudaMemcpyDeviceToHost, st));
         DD_CK(cudaStreamSynchronize(st));
         if (err != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
     }

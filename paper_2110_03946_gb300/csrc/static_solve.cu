@@ -11,8 +11,12 @@
 // device array of fixed size.  The caller still passes inputs and the output.
 //
 // Properties a caller must know:
-//  * the array (kScratchBytes, about 42 MiB) exists on every GPU that loads
-//    the library, for the life of the process;
+//  * the array (kScratchBytes, about 42 MiB) is committed on a device when the
+//    library's module is loaded there; with CUDA's default lazy module loading
+//    that is the first call on that device (its cudaGetSymbolAddress), which can
+//    then fail with DD_ECUDA when device memory is short and pays the load
+//    latency, so a real-time caller makes one warm-up call at start-up; the
+//    array stays until the process exits;
 //  * the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (once per device, with that device current); make
 //    that first call before any stream capture;
@@ -120,8 +124,11 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     dd_params p;
     if (params) p = *params; else dd_params_default(&p);
     if (!dd::block_supported(p.block) || p.overlap < 0 || p.overlap >= p.block || p.local_cg_iters < 1 ||
-        p.max_sweeps < 0 || (p.tile_warps != 0 && !dd::tile_warps_supported(p.block, p.tile_warps)))
+        p.local_cg_iters > 4096 || p.max_sweeps < 0 || p.test_stall_polls < 0 ||
+        (p.tile_warps != 0 && !dd::tile_warps_supported(p.block, p.tile_warps)))
         return fail(DD_EINVAL, "bad params");
+    if (!(p.local_rtol >= 0.0) || !(p.local_rtol < 1.0)) return fail(DD_EINVAL, "local_rtol must be in [0, 1)");
+    if (p.solver != DD_SOLVER_ORAS) return fail(DD_EINVAL, "dd_inpaint_solve_static runs DD_SOLVER_ORAS only");
     if (C > kMaxChannels) return fail(DD_EINVAL, "C exceeds the static scratch capacity (16 channels)");
     const int P = (W + 31) / 32 * 32;
     const long long elems = (long long)C * H * P;
@@ -153,7 +160,8 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
         if (dd::make_tile_map(&maps[b], dd::Store::F32, u[b], H, W, P, C, p.block) != cudaSuccess)
             return fail(DD_ECUDA, "cuTensorMapEncodeTiled failed");
 
-    // u0 = C f, block masks, reference norms ||b - A u0||
+    // the error word starts clear; u0 = C f, block masks, reference norms ||b - A u0||
+    SS_CK(cudaMemsetAsync(flag + 5, 0, sizeof(int), st));
     SS_CK(dd::launch_masked_copy(H, W, C, values, W, (long long)H * W, mask, W, u[0], P, plane, st));
     SS_CK(dd::launch_build_tmask(g, mask, W, tmask, st));
     double2 h_res[kMaxChannels];
@@ -182,10 +190,11 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     const dd::SweepPair pair{{&maps[0], &maps[1]}, {u[0], u[1]}};
     for (int attempt = 0; attempt < 4 && !converged; ++attempt) {
         SS_CK(dd::launch_reset_sweep_state(sstate, flag, cur, tol_d, target, st));
-        dd::SweepStop stop{partial, dd::kSweepSlots, norms2, ref_d, tol_d, 0.0, flag, sstate, 0};
+        dd::SweepStop stop{partial, dd::kSweepSlots, norms2, ref_d, tol_d, 0.0, flag, sstate, 0,
+                           nullptr, flag + 5, p.test_stall_polls};
         const int start = done;
         int launched = 0;
-        int hflag[3] = {0, 0, 0}, hstate[2] = {cur, 0};
+        int hflag[3] = {0, 0, 0}, herr = 0, hstate[2] = {cur, 0};
         while (true) {
             const bool last_probe = done >= p.max_sweeps;
             const int n = last_probe ? 1 : std::min(8, p.max_sweeps - done);
@@ -196,9 +205,10 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
             }
             launched += n;
             SS_CK(cudaMemcpyAsync(hflag, flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            SS_CK(cudaMemcpyAsync(&herr, flag + 5, sizeof(int), cudaMemcpyDeviceToHost, st));
             SS_CK(cudaMemcpyAsync(hstate, sstate, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
             SS_CK(cudaStreamSynchronize(st));
-            if (hflag[2] != 0) return fail(DD_ETIMEOUT, "a bounded device wait for a staged tile gave up");
+            if (herr != 0) return fail(DD_ETIMEOUT, "a bounded device wait for a staged tile gave up");
             if (hflag[0] == 2) return fail(DD_ENUMERIC, "non-finite residual norm");
             cur = hstate[0];
             done = start + hstate[1];

@@ -89,8 +89,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (int n = 0; n < kWaitLimit; ++n)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int limit = kWaitLimit) {
+    for (int n = 0; n < limit; ++n)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -260,7 +260,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     using BOX = Box<CF, T>;
     constexpr int BX = BOX::BX;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[3];   // [2]: never completed (the stalled-wait test hook)
     __shared__ int s_ok;
     __shared__ long long s_next[2];    // next tile, by iteration parity
     __shared__ float red[3][NW];
@@ -268,7 +268,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     __shared__ float xch[2][NW][BW];      // initial boundary rows of r
     __shared__ float xq[2][2][NW][BW];    // boundary rows of q', alternating by step parity
 
-    int* const flag = a.stop.flag;   // [0] stop/skip, [1] conv_at, [2] err, [3] ticket, [4] tile counter
+    int* const flag = a.stop.flag;   // [0] stop/skip, [1] conv_at, [3] ticket, [4] tile counter
     if (flag[0] != 0) return;                        // converged or failed earlier: uniform no-op
     // the current iterate and the kind of launch are device state (read before
     // the last CTA of this launch updates them)
@@ -310,6 +310,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     if (tt == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
+        mbar_init(&mbar[2], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -349,9 +350,10 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         const uint32_t ob = a.tmask[(size_t)tile * 2 * NT + NT + tt];
 
         if (tt == 0) {
-            const bool ok = mbar_wait_bounded(&mbar[buf], parity);
+            const bool ok = (it == 0 && a.stop.stall_polls > 0) ? mbar_wait_bounded(&mbar[2], 0u, a.stop.stall_polls)
+                                                                : mbar_wait_bounded(&mbar[buf], parity);
             s_ok = ok ? 1 : 0;
-            if (!ok) atomicExch(flag + 2, 1);
+            if (!ok) atomicExch(a.stop.err, 1);
         }
         __syncthreads();
         if (!s_ok) break;                               // uniform
@@ -642,8 +644,11 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         }
     }
     if (tt == 0 && !s_ok) {
-        // a copy timed out: wait (bounded) for the other buffer's copy before leaving
-        mbar_wait_bounded(&mbar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        // a wait gave up: before leaving, wait (bounded) for this CTA's copies
+        // still in flight, the one waited for and the next tile's, if issued
+        const int b = it & 1;
+        mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1));
+        if (s_next[b] < total) mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
     }
 
     // ---- per-channel residual norms of u^n and the stop test (last CTA) -----------
@@ -694,7 +699,9 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         }
         if (lane == 0) {
             int* const state = sp.state;
-            if (bad) { flag[0] = 2; flag[1] = sweep_index; }
+            if (sp.work != nullptr && sweep_index < kTimedLaunches) sp.work[2 + sweep_index] = probe ? 0ull : 1ull;
+            if (__ldcg(sp.err) != 0) { flag[0] = 5; flag[1] = sweep_index; }
+            else if (bad) { flag[0] = 2; flag[1] = sweep_index; }
             else if (worst <= tol) { flag[0] = 1; flag[1] = sweep_index; }
             else if (sp.stall > 0.0 && sweep_index > 0 && best_ratio > sp.stall) {
                 flag[0] = 3;
@@ -967,7 +974,8 @@ cudaError_t launch_sweep(Store s, const TileGeom& g, int C, long long plane, con
                          int k, cudaStream_t st, float local_rtol) {
     if (!(local_rtol >= 0.f) || !(local_rtol < 1.f)) return cudaErrorInvalidValue;
     if (stop.slots < 1 || stop.partial == nullptr || stop.flag == nullptr || stop.norms2 == nullptr ||
-        stop.ref == nullptr || stop.state == nullptr || pair.map[0] == nullptr || pair.map[1] == nullptr ||
+        stop.ref == nullptr || stop.state == nullptr || stop.err == nullptr || stop.stall_polls < 0 ||
+        pair.map[0] == nullptr || pair.map[1] == nullptr ||
         pair.u[0] == nullptr || pair.u[1] == nullptr)
         return cudaErrorInvalidValue;
     return with_cfg(g.b, g.nw, [&](auto cfg) {

@@ -19,7 +19,7 @@ def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_m
                 robin_p=None, precision=None, max_sweeps=None, coarse_tol=None, inner_tol=None,
                 max_corrections=None, coarse_sweeps=None, inputs_on_device=1, timing=None,
                 tile_warps=None, solver=None, device_loop=None, correction_sweeps=None,
-                local_rtol=None) -> B.dd_params:
+                local_rtol=None, coarse_factor=None, test_stall_polls=None) -> B.dd_params:
     p = B.dd_params_default()
     if block is not None: p.block = int(block)
     if overlap is not None: p.overlap = int(overlap)
@@ -41,6 +41,8 @@ def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_m
     if device_loop is not None: p.device_loop = int(device_loop)
     if correction_sweeps is not None: p.correction_sweeps = int(correction_sweeps)
     if local_rtol is not None: p.local_rtol = float(local_rtol)
+    if coarse_factor is not None: p.coarse_factor = int(coarse_factor)
+    if test_stall_polls is not None: p.test_stall_polls = int(test_stall_polls)
     p.inputs_on_device = int(inputs_on_device)
     return p
 

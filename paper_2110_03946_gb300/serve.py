@@ -119,6 +119,13 @@ class Server:
         if not self._make_room(need, req.shape):
             return None
         handle, nbytes = self.b.create(req)
+        if nbytes > need:
+            # the slot holds more than estimated (the backend's estimate is
+            # raised for the next time): make room for the actual size, else
+            # give the slot up and let the request wait
+            if nbytes > self.budget or not self._make_room(nbytes, req.shape):
+                self.b.destroy(handle)
+                return None
         s = _Slot(self._next_sid, req.shape, handle, nbytes)
         self._next_sid += 1
         self.slots.append(s)
@@ -270,6 +277,9 @@ class CudaBackend:
         time.sleep(0)
 
     def bytes_for(self, shape) -> int:
+        """Device bytes of one slot: the handle (an estimate until a slot of
+        this shape has been created, then the handle's own count) and the
+        slot's output buffer."""
         if shape not in self._bytes_cache:
             H, W, C = shape
             # pitched FP32 planes: f and two iterates per level, levels shrink by 4
@@ -277,7 +287,8 @@ class CudaBackend:
             lv = 4.0 / 3.0
             est = int(C * H * P * 4 * 3 * lv + H * W * 2 + (1 << 22))
             self._bytes_cache[shape] = est
-        return self._bytes_cache[shape]
+        H, W, C = shape
+        return self._bytes_cache[shape] + C * H * W * 4
 
     def create(self, req: Request):
         torch, B = self.torch, self.B
@@ -292,7 +303,7 @@ class CudaBackend:
         host = torch.empty((C, H, W), dtype=torch.float32).pin_memory() if self.host_output else None
         self._state[h.value] = {"stream": stream, "out": out, "host": host, "inputs": None}
         self._bytes_cache[(H, W, C)] = max(self._bytes_cache.get((H, W, C), 0), int(st.device_bytes))
-        return h, int(st.device_bytes)
+        return h, int(st.device_bytes) + out.numel() * out.element_size()
 
     def destroy(self, h):
         self.torch.cuda.synchronize(self.dev)
@@ -325,8 +336,8 @@ class CudaBackend:
         s = self._state[h.value]
         rc = B.dd_inpaint_solve_finish(h, s["stream"])
         rcs, st = B.dd_inpaint_stats(h)
-        if s["host"] is not None and st.sweeps_per_level[0] > 16:
-            s["host"].copy_(s["out"])         # the finish continued the sweeps: copy the final result
+        if s["host"] is not None and st.host_continued:
+            s["host"].copy_(s["out"])         # the finish rewrote the output: copy the final result
         s["inputs"] = None
         return rc, (s["host"] if s["host"] is not None else s["out"])
 

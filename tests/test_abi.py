@@ -69,7 +69,8 @@ def test_defaults_and_strings(lib):
 
 @pytest.mark.parametrize("field,value", [("block", 24), ("overlap", 32), ("overlap", -1), ("levels", 0),
                                          ("levels", 9), ("precision", 7), ("local_cg_iters", 0),
-                                         ("ml_mode", 5), ("inner_tol", 1.5)])
+                                         ("ml_mode", 5), ("inner_tol", 1.5), ("coarse_factor", 3),
+                                         ("coarse_factor", 16), ("test_stall_polls", -1)])
 def test_invalid_params_rejected_on_host(lib, field, value):
     from paper_2110_03946_gb300 import binding as B
     p = B.dd_params_default()
@@ -104,3 +105,21 @@ def test_library_has_no_cpu_fallback_symbols(lib):
                                    os.path.join(ROOT, "paper_2110_03946_gb300", "libdd_inpaint.so")]).decode()
     exported = sorted({l.split()[-1] for l in out.splitlines() if " T " in l and l.split()[-1].startswith("dd_")})
     assert exported == _declared()
+
+
+def test_device_budget_accounting_without_handles(lib):
+    # no handle is alive in this process on the CPU: nothing is held, and the
+    # budget setter takes any value (0 restores "no cap")
+    from paper_2110_03946_gb300 import binding as B
+    assert B.dd_device_bytes_in_use() == 0
+    B.dd_set_device_budget(1 << 20)
+    B.dd_set_device_budget(0)
+    assert B.dd_device_bytes_in_use() == 0
+
+
+def test_fma_peak_rejects_bad_arguments(lib):
+    import ctypes as ct
+    from paper_2110_03946_gb300 import binding as B
+    t = ct.c_double(0.0)
+    assert lib.dd_fp32_fma_peak(0, ct.byref(t), None, None) == B.DD_EINVAL
+    assert lib.dd_fp32_fma_peak(3, None, None, None) == B.DD_EINVAL

@@ -134,6 +134,9 @@ SOLVE_CASES = [
     ("rgb_correction_3level", 200, 330, 3, dict(levels=3, precision="fp32", ml_mode="correction")),
     ("gray256_correction_2level_launches", 256, 256, 1, dict(levels=2, precision="fp32", ml_mode="correction",
                                                              correction_sweeps=3, device_loop=0)),
+    # two solved levels with a 1/8 coarse grid (two pass-through dyadic levels between them)
+    ("rgb_2level_coarse8", 270, 480, 3, dict(block=64, overlap=4, levels=2, coarse_factor=8, precision="fp32")),
+    ("rgb_2level_coarse4_launches", 200, 330, 3, dict(levels=2, coarse_factor=4, precision="fp32", device_loop=0)),
 ]
 
 
@@ -156,6 +159,10 @@ def test_solve_matches_oracle(name, H, W, C, params):
     assert np.all(rel <= tol)
     assert np.allclose(st["rel_residual"][:C], rel, rtol=1e-5, atol=1e-12)
     assert np.array_equal(u[:, m != 0], f[:, m != 0].astype(np.float32))
+    if params.get("coarse_factor", 2) > 2:   # only the solved levels sweep
+        step = {4: 2, 8: 3}[params["coarse_factor"]]
+        per = st["sweeps_per_level"]
+        assert all(per[l] == 0 for l in range(1, step)) and per[step] > 0
 
 
 @pytest.mark.parametrize("solver", ["oras", "cg"])

@@ -75,6 +75,41 @@ def test_all_served_with_metrics():
     assert m["peak_hbm_bytes"] <= 10 * 8 * 8 * 16
 
 
+class GreedyBackend(FakeBackend):
+    """A backend whose slots turn out larger than its estimate."""
+
+    def __init__(self, actual_factor=1.5, **kw):
+        super().__init__(**kw)
+        self.factor = actual_factor
+
+    def create(self, req):
+        h, n = super().create(req)
+        return h, int(n * self.factor)
+
+
+def test_budget_holds_when_slots_exceed_their_estimate():
+    # estimate 1024 B per slot, actual 1536 B: the budget of 4096 B fits 2 actual
+    # slots, though 4 estimated ones would seem to fit; admission must hold it
+    b = GreedyBackend(actual_factor=1.5)
+    budget = 4 * 8 * 8 * 16
+    srv = Server(b, hbm_budget=budget)
+    reqs = [_req(i, 0.0) for i in range(12)]
+    res, m = srv.run(reqs, realtime=True)
+    assert m["failures"] == 0 and len(res) == 12
+    assert m["peak_hbm_bytes"] <= budget
+    assert len(b.live) <= 2
+
+
+def test_slot_larger_than_the_budget_waits_instead_of_overrunning():
+    # a slot that is actually larger than the whole budget is given up at once
+    b = GreedyBackend(actual_factor=3.0)
+    budget = 2 * 8 * 8 * 16
+    srv = Server(b, hbm_budget=budget)
+    with pytest.raises(RuntimeError, match="cannot be admitted"):
+        srv.run([_req(0, 0.0)], realtime=True)
+    assert not b.live and srv.peak_bytes <= budget
+
+
 def test_concurrent_slots_overlap():
     b = FakeBackend()
     srv = Server(b, hbm_budget=3 * 8 * 8 * 16)

@@ -45,12 +45,64 @@ def test_static_matches_allocating_entry_point(H, W, C, seed):
     vals_d = torch.as_tensor(f).to(DEV)
     p = make_params(**prm)
     u1 = _static_solve(mask_d, vals_d, p, 1e-6)
-    u2 = _static_solve(mask_d, vals_d, p, 1e-6)       # second call reuses the scratch
+    # the second call reuses the scratch left by the first, and allocates no
+    # device memory: the output buffer is made before the free memory is read
+    out = torch.full((C, H, W), float("nan"), dtype=torch.float32, device=DEV)
+    torch.cuda.synchronize(DEV)
+    free0, reserved0 = torch.cuda.mem_get_info(DEV)[0], torch.cuda.memory_reserved(DEV)
+    rc = B.dd_inpaint_solve_static(H, W, C, mask_d.data_ptr(), vals_d.data_ptr(), out.data_ptr(), p, 1e-6,
+                                   torch.cuda.current_stream(DEV))
+    B.check(rc, "dd_inpaint_solve_static (second call)")
+    torch.cuda.synchronize(DEV)
+    assert torch.cuda.mem_get_info(DEV)[0] == free0
+    assert torch.cuda.memory_reserved(DEV) == reserved0
+    u2 = out.cpu().numpy()
     for u in (u1, u2):
         assert np.isfinite(u).all()
         assert np.max(np.abs(u - u_ref)) <= TOL_U
         assert np.all(ref.rel_residual(u.astype(np.float64), f, m) <= 1e-6)
         assert np.array_equal(u[:, m != 0], f[:, m != 0].astype(np.float32))
+
+
+def test_static_empty_mask():
+    # no known pixel: A is singular; the call finds it from its own block-mask count
+    H, W, C = 96, 130, 2
+    mask_d = torch.zeros((H, W), dtype=torch.uint8, device=DEV)
+    vals_d = torch.rand((C, H, W), dtype=torch.float32, device=DEV) * 255
+    out = torch.empty((C, H, W), dtype=torch.float32, device=DEV)
+    rc = B.dd_inpaint_solve_static(H, W, C, mask_d.data_ptr(), vals_d.data_ptr(), out.data_ptr(), None, 1e-6,
+                                   torch.cuda.current_stream(DEV))
+    assert rc == B.DD_EEMPTYMASK
+
+
+def test_static_not_converged_still_writes_output():
+    # one sweep cannot reach 1e-6: DD_ENOTCONVERGED, and u_out holds the iterate
+    # reached (finite, known pixels equal to the data)
+    f, m = synth.make_frame(128, 160, 3, 0.05, "uniform", 11)
+    mask_d = torch.as_tensor(m).to(DEV)
+    vals_d = torch.as_tensor(f).to(DEV)
+    C, H, W = f.shape
+    out = torch.full((C, H, W), float("nan"), dtype=torch.float32, device=DEV)
+    p = make_params(block=32, overlap=6, local_cg_iters=8, levels=1, precision="fp32", max_sweeps=1)
+    rc = B.dd_inpaint_solve_static(H, W, C, mask_d.data_ptr(), vals_d.data_ptr(), out.data_ptr(), p, 1e-6,
+                                   torch.cuda.current_stream(DEV))
+    assert rc == B.DD_ENOTCONVERGED
+    u = out.cpu().numpy()
+    assert np.isfinite(u).all()
+    assert np.array_equal(u[:, m != 0], f[:, m != 0].astype(np.float32))
+    rel = ref.rel_residual(u.astype(np.float64), f, m)
+    assert np.all(rel < 1.0) and np.any(rel > 1e-6)
+
+
+def test_static_rejects_bad_params():
+    H, W, C = 64, 64, 1
+    mask_d = torch.ones((H, W), dtype=torch.uint8, device=DEV)
+    vals_d = torch.zeros((C, H, W), dtype=torch.float32, device=DEV)
+    out = torch.empty((C, H, W), dtype=torch.float32, device=DEV)
+    for bad in (dict(local_rtol=1.5), dict(local_cg_iters=5000), dict(solver="cg")):
+        p = make_params(levels=1, precision="fp32", **bad)
+        rc = B.dd_inpaint_solve_static(H, W, C, mask_d.data_ptr(), vals_d.data_ptr(), out.data_ptr(), p, 1e-6, None)
+        assert rc == B.DD_EINVAL, bad
 
 
 def test_static_rejects_oversized_input():
