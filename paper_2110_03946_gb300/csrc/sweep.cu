@@ -47,6 +47,7 @@ constexpr double kFirstContraction = 0.3;
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls (a TMA copy takes ~1 us)
+constexpr int kDynamicRounds = 4;     // tiles per CTA (average) claimed dynamically at the end of a sweep
 
 template <typename T> __device__ __forceinline__ float to_f(T v);
 template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
@@ -139,6 +140,13 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
 // Tile shape: LX x LY lanes per warp, PX x PY pixels per lane, NW warps stacked
 // vertically; one block tile per CTA at a time.
 template <int PX_, int PY_, int LX_, int NW_>
@@ -170,6 +178,12 @@ cudaError_t with_cfg(int b, int nw, F&& f) {
     return cudaErrorInvalidValue;
 }
 
+// Mask words of one block tile (known bits, owned bits: one word each per thread).
+template <class CF>
+constexpr int mask_bytes() {
+    return 2 * CF::NT * 4;
+}
+
 // Shared-memory tile: block plus one-pixel halo; the TMA box starts at a
 // 16-byte aligned column at or left of x0 - 1, so it is BX >= BW + 2 + (align - 1) wide.
 template <class CF, typename T>
@@ -182,6 +196,21 @@ struct Box {
     static_assert(BX <= 256 && BY <= 256, "TMA box too large");
 };
 
+// Division by a divisor fixed for the launch (n < 2^31): the round-up method of
+// Granlund & Montgomery (PLDI 1994), q = (umulhi(n, m) + n) >> s with
+// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1, computed on the host.
+struct FastDiv {
+    uint32_t m, s;
+};
+FastDiv make_fastdiv(uint32_t d) {
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    return FastDiv{(uint32_t)(((1ull << 32) * ((1ull << s) - d)) / d + 1), s};
+}
+__device__ __forceinline__ int fdiv(int n, FastDiv f) {
+    return (int)(((unsigned long long)__umulhi((uint32_t)n, f.m) + (uint32_t)n) >> f.s);
+}
+
 template <typename T>
 struct SweepArgs {
     T* u_buf[2];
@@ -189,6 +218,10 @@ struct SweepArgs {
     SweepStop stop;
     int H, W, pitch, C;
     int s, ntx, ntiles;
+    int total;            // ntiles * C (< 2^31)
+    int static_end;       // tiles below this go round-robin to the CTAs; the rest are claimed
+    FastDiv dv_tiles;     // division by ntiles (tile -> channel)
+    FastDiv dv_ntx;       // division by ntx (block -> block row)
     int has_g;
     long long plane;
     float p_robin;
@@ -251,7 +284,21 @@ __device__ __forceinline__ float3 tile_sum3(float3 v, float* red, int wt, int la
     }
 }
 
-template <class CF, typename T>
+// Exact sum of the 32 lanes' fixed-point accumulators (integer adds with
+// carry, so the result does not depend on the order); every lane gets it.
+__device__ __forceinline__ Fix128 warp_fix_sum(Fix128 f) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        const unsigned long long lo = __shfl_xor_sync(FULL, f.lo, m), hi = __shfl_xor_sync(FULL, f.hi, m);
+        fix_add(f, lo, hi);
+    }
+    return f;
+}
+
+// ALN: every block starts at a column that is a multiple of 4 (stride s % 4 == 0,
+// FP32 storage, 4 pixels per lane row), so a lane's 4 pixels of a row are one
+// 16-byte vector in the staged tile and in the iterate.
+template <class CF, typename T, bool ALN>
 __global__ void __launch_bounds__(CF::NT)
 oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_constant__ CUtensorMap map_u1,
                   const __grid_constant__ CUtensorMap map_g, const SweepArgs<T> a) {
@@ -259,10 +306,11 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     constexpr int BW = CF::BW, BH = CF::BH, NP = CF::NP, NT = CF::NT;
     using BOX = Box<CF, T>;
     constexpr int BX = BOX::BX;
+    static_assert(!ALN || (PX == 4 && sizeof(T) == 4 && BX % 4 == 0), "aligned path: 4 FP32 pixels per lane row");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[3];   // [2]: never completed (the stalled-wait test hook)
     __shared__ int s_ok;
-    __shared__ long long s_next[2];    // next tile, by iteration parity
+    __shared__ int s_next[2];          // next tile, by iteration parity
     __shared__ float red[3][NW];
     __shared__ float red3[2][3][NW];   // CG reductions (p,Ap), (Ap,Ap), (r,r), alternating by step parity
     __shared__ float xch[2][NW][BW];      // initial boundary rows of r
@@ -277,8 +325,8 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     const CUtensorMap* const map_u = cur ? &map_u1 : &map_u0;
     T* const u_out = a.u_buf[cur ^ 1];
     const int kcg = probe ? 0 : a.k;
-    const long long total = (long long)a.ntiles * a.C;
-    long long t = blockIdx.x;
+    const int total = a.total;
+    int t = blockIdx.x;
     if (t >= total) return;
 
     const int tt = threadIdx.x;
@@ -287,7 +335,8 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     const int ry0 = (wt * LY + ly) * PY, rx0 = lx * PX;
     const int H = a.H, W = a.W, P = a.pitch;
     const int narr = a.has_g ? 2 : 1;
-    const uint32_t tx_bytes = (uint32_t)(BOX::BYTES * narr);
+    constexpr int MB = mask_bytes<CF>();
+    const uint32_t tx_bytes = (uint32_t)(BOX::BYTES * narr + MB);
     // TMA destinations must be 128-byte aligned: round the dynamic base up
     // (the launch reserves 128 bytes of slack for this).
     unsigned char* const smem =
@@ -295,16 +344,23 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     auto stage = [&](int buf, int which) {
         return reinterpret_cast<T*>(smem + (size_t)(buf * narr + which) * BOX::STRIDE);
     };
-    auto issue = [&](long long tn, int buf) {   // thread 0 only
-        const int c = (int)(tn / a.ntiles);
-        const int tile = (int)(tn - (long long)c * a.ntiles);
-        const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+    // the staged tile's mask words (after the 2 x narr arrays)
+    auto stage_mask = [&](int buf) {
+        return reinterpret_cast<uint32_t*>(smem + (size_t)2 * narr * BOX::STRIDE + (size_t)buf * MB);
+    };
+    // the TMA box of a block starts at the 16-byte aligned column at or left of x0 - 1
+    auto box_x = [](int x0) { return ((x0 - 1) >= 0 ? (x0 - 1) / BOX::ALIGN : -1) * BOX::ALIGN; };
+    auto issue = [&](int tn, int buf) {   // thread 0 only
+        const int c = fdiv(tn, a.dv_tiles);
+        const int tile = tn - c * a.ntiles;
+        const int ty = fdiv(tile, a.dv_ntx), tx = tile - ty * a.ntx;
         const int x0 = tx * a.s, y0 = ty * a.s;
-        const int xs = ((x0 - 1) >= 0 ? (x0 - 1) / BOX::ALIGN : -1) * BOX::ALIGN;
+        const int xs = box_x(x0);
         fence_proxy_async();
         mbar_expect_tx(&mbar[buf], tx_bytes);
         tma_load_3d(stage(buf, 0), map_u, xs, y0 - 1, c, &mbar[buf]);
         if (a.has_g) tma_load_3d(stage(buf, 1), &map_g, xs, y0 - 1, c, &mbar[buf]);
+        bulk_load(stage_mask(buf), a.tmask + (size_t)tile * 2 * NT, (uint32_t)MB, &mbar[buf]);
     };
 
     if (tt == 0) {
@@ -314,40 +370,78 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         fence_mbar_init();
     }
     __syncthreads();
-    if (tt == 0) issue(t, 0);
+    // Tile order: the tiles below static_end go round-robin (CTA b takes b,
+    // b + G, ...); after its last one a CTA claims further tiles from an atomic
+    // counter, so CTAs whose local problems stopped early take more of the
+    // tail.  Thread 0 claims one iteration ahead of the staging.  A CTA's tiles
+    // come in increasing order either way.
+    const int G = (int)gridDim.x;
+    auto next_of = [&](int tcur) {   // thread 0 only
+        return tcur + G < a.static_end
+                   ? tcur + G
+                   : (int)atomicAdd(reinterpret_cast<unsigned*>(flag + 4), 1u) + a.static_end;
+    };
+    int claim = 0;
+    if (tt == 0) {
+        issue(t, 0);
+        claim = next_of(t);
+    }
 
     const float pr = a.p_robin;
     const float fW = lx > 0 ? 1.f : 0.f, fE = lx < LX - 1 ? 1.f : 0.f;
-    // thread 0: this CTA's exact residual sum of the channel it is in (tiles
-    // come in increasing order, so channels too)
+    // NW == 1: a lane of the block's top (bottom) lane row has no north (south)
+    // neighbour lane; its shuffled value is weighted 0
+    const float2 fN2 = make_float2(ly > 0 ? 1.f : 0.f, ly > 0 ? 1.f : 0.f);
+    const float2 fS2 = make_float2(ly < LY - 1 ? 1.f : 0.f, ly < LY - 1 ? 1.f : 0.f);
+    // Residual sums of the input iterate per channel, exact (Fix128): lane
+    // (it mod 32) holds the owned ||r||^2 of this CTA's tile it until every 32
+    // tiles (or a change of channel) all lanes add their value into their own
+    // accumulator at once; the lanes' accumulators are summed when a channel's
+    // partial is written.  Tiles come in increasing order, so channels too.
     unsigned long long* const part = a.stop.partial;
     const int slots = a.stop.slots;
-    auto put = [&](int cc, const Fix128& v, bool bad) {
+    auto put = [&](int cc, const Fix128& v, bool bad) {   // thread 0 only
         part[2 * ((size_t)cc * slots + blockIdx.x)] = v.lo;
         part[2 * ((size_t)cc * slots + blockIdx.x) + 1] = bad ? kFixBad : v.hi;
     };
     int cur_c = -1, eu = 0;
     Fix128 acc{0ull, 0ull};
-    bool acc_bad = false;
+    float pend = 0.f;
+    bool acc_bad = false;   // the same on every lane (it follows the tile-uniform sums)
+    // channel cur_c done: add the pending values, sum the lanes, write (and zero
+    // the partials of the channels in [cur_c + 1, upto) that this CTA skipped)
+    auto flush = [&](int upto) {
+        if (cur_c >= 0) {
+            fix_add(acc, pend, eu);
+            const Fix128 f = warp_fix_sum(acc);
+            if (tt == 0) put(cur_c, f, acc_bad);
+        }
+        if (tt == 0)
+            for (int cc = cur_c + 1; cc < upto; ++cc) put(cc, Fix128{0ull, 0ull}, false);
+        acc = Fix128{0ull, 0ull};
+        pend = 0.f;
+        acc_bad = false;
+    };
     uint32_t work_us = 0, work_u = 0;   // optional work counters (per lane)
     int it = 0;
     for (; t < total; ++it) {
         const int buf = it & 1;
         const uint32_t parity = (uint32_t)((it >> 1) & 1);
-        if (tt == 0) {   // claim the next tile and stage it while this one is solved
-            const long long tn = (long long)atomicAdd(reinterpret_cast<unsigned*>(flag + 4), 1u) + gridDim.x;
+        if (tt == 0) {   // stage the next tile while this one is solved, and claim the one after
+            const int tn = claim;
             s_next[buf] = tn;
-            if (tn < total) issue(tn, buf ^ 1);
+            if (tn < total) {
+                issue(tn, buf ^ 1);
+                claim = next_of(tn);
+            }
         }
 
-        const int c = (int)(t / a.ntiles);
-        const int tile = (int)(t - (long long)c * a.ntiles);
-        const int ty = tile / a.ntx, tx = tile - ty * a.ntx;
+        const int c = fdiv(t, a.dv_tiles);
+        const int tile = t - c * a.ntiles;
+        const int ty = fdiv(tile, a.dv_ntx), tx = tile - ty * a.ntx;
         const int y0 = ty * a.s, x0 = tx * a.s;
         const int th = min(BH, H - y0), tw = min(BW, W - x0);
-        const int cx = x0 - ((x0 - 1) >= 0 ? (x0 - 1) / BOX::ALIGN : -1) * BOX::ALIGN;   // smem column of x0
-        const uint32_t kb = a.tmask[(size_t)tile * 2 * NT + tt];
-        const uint32_t ob = a.tmask[(size_t)tile * 2 * NT + NT + tt];
+        const int cx = ALN ? 4 : x0 - box_x(x0);   // smem column of x0
 
         if (tt == 0) {
             const bool ok = (it == 0 && a.stop.stall_polls > 0) ? mbar_wait_bounded(&mbar[2], 0u, a.stop.stall_polls)
@@ -360,6 +454,8 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         if (tt != 0) mbar_wait_bounded(&mbar[buf], parity);   // phase already complete: returns at once
         const T* __restrict__ U = stage(buf, 0);
         const T* __restrict__ G = stage(buf, 1);
+        const uint32_t kb = stage_mask(buf)[tt];
+        const uint32_t ob = stage_mask(buf)[NT + tt];
 
         // ---- local operator coefficients -----------------------------------------
         float2 rpn[PY];     // -(vertical part of dd), both halves equal
@@ -410,25 +506,35 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             const int o0 = (1 + ry0) * BX + cx + rx0;
             float uu[PY + 2][PX + 2];
 #pragma unroll
-            for (int i = 0; i < PY + 2; ++i)
+            for (int i = 0; i < PY + 2; ++i) {
+                const T* row = U + o0 + (i - 1) * BX;
+                if constexpr (ALN) {   // columns 0..3 as one vector, -1 and 4 as scalars
+                    const float4 q4 = *reinterpret_cast<const float4*>(row);
+                    uu[i][1] = q4.x; uu[i][2] = q4.y; uu[i][3] = q4.z; uu[i][4] = q4.w;
+                    const bool edge_row = i == 0 || i == PY + 1;
+                    uu[i][0] = edge_row ? 0.f : to_f(row[-1]);
+                    uu[i][PX + 1] = edge_row ? 0.f : to_f(row[PX]);
+                } else {
 #pragma unroll
-                for (int j = 0; j < PX + 2; ++j) {
-                    const bool corner = (i == 0 || i == PY + 1) && (j == 0 || j == PX + 1);
-                    uu[i][j] = corner ? 0.f : to_f(U[o0 + (i - 1) * BX + (j - 1)]);
+                    for (int j = 0; j < PX + 2; ++j) {
+                        const bool corner = (i == 0 || i == PY + 1) && (j == 0 || j == PX + 1);
+                        uu[i][j] = corner ? 0.f : to_f(row[j - 1]);
+                    }
                 }
+            }
 #pragma unroll
             for (int i = 0; i < PY; ++i)
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
                     const float2 uc = make_float2(uu[i + 1][2 * j + 1], uu[i + 1][2 * j + 2]);
                     const float2 nuc = make_float2(-uc.x, -uc.y);
-                    float2 acc = a.has_g ? make_float2(to_f(G[o0 + i * BX + 2 * j]), to_f(G[o0 + i * BX + 2 * j + 1]))
-                                         : make_float2(0.f, 0.f);
-                    acc = fma2(mN[i], add2(make_float2(uu[i][2 * j + 1], uu[i][2 * j + 2]), nuc), acc);
-                    acc = fma2(mS[i], add2(make_float2(uu[i + 2][2 * j + 1], uu[i + 2][2 * j + 2]), nuc), acc);
-                    acc = fma2(mW[j], add2(make_float2(uu[i + 1][2 * j], uu[i + 1][2 * j + 1]), nuc), acc);
-                    acc = fma2(mE[j], add2(make_float2(uu[i + 1][2 * j + 2], uu[i + 1][2 * j + 3]), nuc), acc);
-                    const float2 res = mul2(w2[i][j], acc);
+                    float2 acc2 = a.has_g ? make_float2(to_f(G[o0 + i * BX + 2 * j]), to_f(G[o0 + i * BX + 2 * j + 1]))
+                                          : make_float2(0.f, 0.f);
+                    acc2 = fma2(mN[i], add2(make_float2(uu[i][2 * j + 1], uu[i][2 * j + 2]), nuc), acc2);
+                    acc2 = fma2(mS[i], add2(make_float2(uu[i + 2][2 * j + 1], uu[i + 2][2 * j + 2]), nuc), acc2);
+                    acc2 = fma2(mW[j], add2(make_float2(uu[i + 1][2 * j], uu[i + 1][2 * j + 1]), nuc), acc2);
+                    acc2 = fma2(mE[j], add2(make_float2(uu[i + 1][2 * j + 2], uu[i + 1][2 * j + 3]), nuc), acc2);
+                    const float2 res = mul2(w2[i][j], acc2);
                     r2[i][j] = res;
                     rr0 = fmaf(res.x, res.x, fmaf(res.y, res.y, rr0));
                     const bool o_x = (ob >> (i * PX + 2 * j)) & 1u, o_y = (ob >> (i * PX + 2 * j + 1)) & 1u;
@@ -467,17 +573,17 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             rr = both.y;
             rr_stop = a.local_rtol2 * rr;
         }
-        if (tt == 0) {
-            if (c != cur_c) {
-                if (cur_c >= 0) put(cur_c, acc, acc_bad);
-                for (int cc = cur_c + 1; cc < c; ++cc) put(cc, Fix128{0ull, 0ull}, false);
-                cur_c = c;
-                acc = Fix128{0ull, 0ull};
-                acc_bad = false;
-                eu = fix_unit(a.stop.ref[c]);
-            }
-            if (isfinite(s2)) fix_add(acc, s2, eu);
-            else acc_bad = true;
+        // the owned residual sum of this tile into the lane-batched accumulators
+        if (c != cur_c) {
+            flush(c);
+            cur_c = c;
+            eu = fix_unit(a.stop.ref[c]);
+        }
+        if (!isfinite(s2)) acc_bad = true;
+        if (lane == (it & 31)) pend = s2;
+        if ((it & 31) == 31) {
+            fix_add(acc, pend, eu);
+            pend = 0.f;
         }
         // p rows of the neighbouring warps next to this warp's top / bottom row
         // (and their r rows: each warp advances its neighbours' boundary rows of r
@@ -521,13 +627,15 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                 pS[j].x = __shfl_down_sync(FULL, p2[0][j].x, LX);
                 pS[j].y = __shfl_down_sync(FULL, p2[0][j].y, LX);
             }
-            if (ly == 0) {
+            if constexpr (NW > 1) {   // the block's warp boundaries: rows held by the neighbouring warps
+                if (ly == 0) {
 #pragma unroll
-                for (int j = 0; j < NP; ++j) pN[j] = nbN[j];
-            }
-            if (ly == LY - 1) {
+                    for (int j = 0; j < NP; ++j) pN[j] = nbN[j];
+                }
+                if (ly == LY - 1) {
 #pragma unroll
-                for (int j = 0; j < NP; ++j) pS[j] = nbS[j];
+                    for (int j = 0; j < NP; ++j) pS[j] = nbS[j];
+                }
             }
             // q' = -(A_i p), with (p, q') and (q', q') on two accumulator chains each
             float2 pqa = make_float2(0.f, 0.f), pqb = make_float2(0.f, 0.f);
@@ -536,12 +644,18 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             for (int i = 0; i < PY; ++i)
 #pragma unroll
                 for (int j = 0; j < NP; ++j) {
-                    const float2 n = i > 0 ? p2[i - 1][j] : pN[j];
-                    const float2 s = i < PY - 1 ? p2[i + 1][j] : pS[j];
+                    // north + south; with one warp per block the block's top and bottom
+                    // lane rows weight the shuffled (wrapped) value by 0
+                    float2 ns;
+                    if (i > 0 && i < PY - 1) ns = add2(p2[i - 1][j], p2[i + 1][j]);
+                    else if constexpr (NW > 1) ns = add2(i > 0 ? p2[i - 1][j] : pN[j], i < PY - 1 ? p2[i + 1][j] : pS[j]);
+                    else if (i == 0 && PY > 1) ns = fma2(fN2, pN[j], p2[i + 1][j]);
+                    else if (PY > 1) ns = fma2(fS2, pS[j], p2[i - 1][j]);
+                    else ns = fma2(fN2, pN[j], mul2(fS2, pS[j]));
                     const float hx = j > 0 ? p2[i][j - 1].y + p2[i][j].y : fmaf(fW, pW[i], p2[i][j].y);
                     const float hy = j < NP - 1 ? p2[i][j].x + p2[i][j + 1].x : fmaf(fE, pE[i], p2[i][j].x);
                     const float2 h = make_float2(hx, hy);
-                    const float2 sum = add2(add2(n, s), h);
+                    const float2 sum = add2(ns, h);
                     const float2 nd = add2(rpn[i], cpn[j]);
                     const float2 q = mul2(w2[i][j], fma2(nd, p2[i][j], sum));
                     q2[i][j] = q;
@@ -621,17 +735,31 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
 
         // ---- restricted add-back on the owned core -------------------------------
         T* __restrict__ uout = u_out + (size_t)c * a.plane;
-        if (!probe)
+        if (!probe) {
 #pragma unroll
-        for (int i = 0; i < PY; ++i)
+            for (int i = 0; i < PY; ++i) {
+                const int o = (1 + ry0 + i) * BX + cx + rx0;
+                T* const grow = uout + (size_t)(y0 + ry0 + i) * P + (x0 + rx0);
+                if constexpr (ALN) {
+                    const float4 u4 = *reinterpret_cast<const float4*>(U + o);
+                    const float2 lo = add2(make_float2(u4.x, u4.y), v2[i][0]);
+                    const float2 hi = add2(make_float2(u4.z, u4.w), v2[i][1]);
+                    const uint32_t rb = ob >> (i * PX);
+                    if (rb & 1u) grow[0] = lo.x;
+                    if (rb & 2u) grow[1] = lo.y;
+                    if (rb & 4u) grow[2] = hi.x;
+                    if (rb & 8u) grow[3] = hi.y;
+                } else {
 #pragma unroll
-            for (int j = 0; j < PX; ++j) {
-                if ((ob >> (i * PX + j)) & 1u) {
-                    const int o = (1 + ry0 + i) * BX + cx + rx0 + j;
-                    const float v = (j & 1) ? v2[i][j >> 1].y : v2[i][j >> 1].x;
-                    uout[(size_t)(y0 + ry0 + i) * P + (x0 + rx0 + j)] = from_f<T>(to_f(U[o]) + v);
+                    for (int j = 0; j < PX; ++j) {
+                        if ((ob >> (i * PX + j)) & 1u) {
+                            const float v = (j & 1) ? v2[i][j >> 1].y : v2[i][j >> 1].x;
+                            grow[j] = from_f<T>(to_f(U[o + j]) + v);
+                        }
+                    }
                 }
             }
+        }
         if constexpr (NW > 1) __syncthreads();   // the staged tile may now be refilled
         else __syncwarp();
         t = s_next[buf];
@@ -652,10 +780,8 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     }
 
     // ---- per-channel residual norms of u^n and the stop test (last CTA) -----------
-    if (tt == 0) {
-        if (cur_c >= 0) put(cur_c, acc, acc_bad);
-        for (int cc = cur_c + 1; cc < a.C; ++cc) put(cc, Fix128{0ull, 0ull}, false);
-    }
+    flush(a.C);
+
     __threadfence();
     __syncthreads();
     __shared__ int s_last;
@@ -773,10 +899,10 @@ __global__ void count_unknown_kernel(const uint32_t* __restrict__ tmask, int nti
 
 template <class CF, typename T>
 size_t sweep_smem_bytes(bool has_g) {
-    return (size_t)Box<CF, T>::STRIDE * 2 * (has_g ? 2 : 1) + 128;
+    return (size_t)Box<CF, T>::STRIDE * 2 * (has_g ? 2 : 1) + 2 * mask_bytes<CF>() + 128;
 }
 
-template <class CF, typename T>
+template <class CF, typename T, bool ALN>
 int persistent_grid(bool has_g) {
     // CTAs per SM from the occupancy calculator, cached per instantiation and shape
     // (0 on a failed query: the caller reports the error).  The kernel's
@@ -790,9 +916,9 @@ int persistent_grid(bool has_g) {
         const size_t smem = sweep_smem_bytes<CF, T>(has_g);
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaFuncSetAttribute(oras_sweep_kernel<CF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(oras_sweep_kernel<CF, T, ALN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sweep_smem_bytes<CF, T>(true)) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oras_sweep_kernel<CF, T>, CF::NT, smem) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oras_sweep_kernel<CF, T, ALN>, CF::NT, smem) !=
                 cudaSuccess)
             return 0;
         slot = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
@@ -800,10 +926,38 @@ int persistent_grid(bool has_g) {
     return slot;
 }
 
+// The aligned variant runs when every block starts on a multiple of 4 columns
+// (stride % 4 == 0) with FP32 storage and 4 pixels per lane row.
+template <class CF, typename T>
+constexpr bool has_aligned_variant() {
+    return CF::PX == 4 && sizeof(T) == 4;
+}
+template <class CF, typename T>
+bool use_aligned(const TileGeom& g) {
+    return has_aligned_variant<CF, T>() && g.s % 4 == 0;
+}
+
+template <class CF, typename T, bool ALN>
+cudaError_t sweep_launch(const SweepArgs<T>& a, const SweepPair& pr2, const CUtensorMap* mg, int slots,
+                         cudaStream_t st) {
+    const long long work = a.total;
+    const int resident = persistent_grid<CF, T, ALN>(a.has_g);
+    if (resident == 0) return cudaGetLastError();
+    const long long grid = std::min<long long>(std::min<long long>(work, resident), (long long)slots);
+    const size_t smem = sweep_smem_bytes<CF, T>(a.has_g);
+    // the last kDynamicRounds tiles per CTA (on average) are claimed dynamically
+    SweepArgs<T> b = a;
+    b.static_end = (int)std::max<long long>(grid, work - kDynamicRounds * grid);
+    oras_sweep_kernel<CF, T, ALN><<<(unsigned)grid, CF::NT, smem, st>>>(*pr2.map[0], *pr2.map[1],
+                                                                         mg ? *mg : *pr2.map[0], b);
+    return cudaGetLastError();
+}
+
 template <class CF, typename T>
 cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const SweepPair& pr2, const CUtensorMap* mg,
                       const uint32_t* tmask, const SweepStop& stop, float p_robin, int k, float local_rtol2,
                       cudaStream_t st) {
+    if ((long long)g.ntiles * C >= (1LL << 31)) return cudaErrorInvalidValue;
     SweepArgs<T> a;
     a.u_buf[0] = static_cast<T*>(pr2.u[0]);
     a.u_buf[1] = static_cast<T*>(pr2.u[1]);
@@ -811,28 +965,35 @@ cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const SweepPair
     a.stop = stop;
     a.H = g.H; a.W = g.W; a.pitch = g.pitch; a.C = C;
     a.s = g.s; a.ntx = g.ntx; a.ntiles = g.ntiles;
+    a.total = g.ntiles * C;
+    a.dv_tiles = make_fastdiv((uint32_t)g.ntiles);
+    a.dv_ntx = make_fastdiv((uint32_t)g.ntx);
     a.has_g = mg != nullptr;
     a.plane = plane;
     a.p_robin = p_robin;
     a.k = k;
     a.local_rtol2 = local_rtol2;
-    const long long work = (long long)g.ntiles * C;
-    const int resident = persistent_grid<CF, T>(a.has_g);
-    if (resident == 0) return cudaGetLastError();
-    const long long grid = std::min<long long>(std::min<long long>(work, resident), (long long)stop.slots);
-    const size_t smem = sweep_smem_bytes<CF, T>(a.has_g);
-    oras_sweep_kernel<CF, T><<<(unsigned)grid, CF::NT, smem, st>>>(*pr2.map[0], *pr2.map[1], mg ? *mg : *pr2.map[0],
-                                                                    a);
-    return cudaGetLastError();
+    if constexpr (has_aligned_variant<CF, T>()) {
+        if (use_aligned<CF, T>(g)) return sweep_launch<CF, T, true>(a, pr2, mg, stop.slots, st);
+    }
+    return sweep_launch<CF, T, false>(a, pr2, mg, stop.slots, st);
+}
+
+template <class CF, typename T>
+int prepare_grid(const TileGeom& g, bool has_g) {
+    if constexpr (has_aligned_variant<CF, T>()) {
+        if (use_aligned<CF, T>(g)) return persistent_grid<CF, T, true>(has_g);
+    }
+    return persistent_grid<CF, T, false>(has_g);
 }
 
 template <class CF>
-cudaError_t prepare_store(Store s, bool has_g) {
+cudaError_t prepare_store(Store s, const TileGeom& g, bool has_g) {
     int n = 0;
     switch (s) {
-        case Store::F32: n = persistent_grid<CF, float>(has_g); break;
-        case Store::F16: n = persistent_grid<CF, __half>(has_g); break;
-        case Store::BF16: n = persistent_grid<CF, __nv_bfloat16>(has_g); break;
+        case Store::F32: n = prepare_grid<CF, float>(g, has_g); break;
+        case Store::F16: n = prepare_grid<CF, __half>(g, has_g); break;
+        case Store::BF16: n = prepare_grid<CF, __nv_bfloat16>(g, has_g); break;
     }
     return n > 0 ? cudaSuccess : cudaGetLastError();
 }
@@ -966,7 +1127,7 @@ cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsig
 }
 
 cudaError_t prepare_sweep(Store s, const TileGeom& g, bool has_g) {
-    return with_cfg(g.b, g.nw, [&](auto cfg) { return prepare_store<decltype(cfg)>(s, has_g); });
+    return with_cfg(g.b, g.nw, [&](auto cfg) { return prepare_store<decltype(cfg)>(s, g, has_g); });
 }
 
 cudaError_t launch_sweep(Store s, const TileGeom& g, int C, long long plane, const SweepPair& pair,
