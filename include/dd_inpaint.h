@@ -240,7 +240,8 @@ int dd_inpaint_query(dd_handle h);
 int dd_inpaint_solve_finish(dd_handle h, void *stream);
 
 /*
- * Batched solves in one CUDA graph: the FP32 solves of n handles, each on its
+ * Batched solves in one CUDA graph (mode DD_BATCH_GRAPH, see
+ * dd_batch_create_mode): the FP32 solves of n handles, each on its
  * own forked stream, are captured once and replayed by dd_batch_launch, so
  * frames of different sizes run concurrently and the whole batch is one graph
  * launch.  handles: n distinct FP32 handles; u_out[i]: DEVICE output of handle
@@ -254,6 +255,26 @@ int dd_inpaint_solve_finish(dd_handle h, void *stream);
  */
 int dd_batch_create(int n, const dd_handle *handles, float *const *u_out, double tol, dd_batch_handle *out,
                     long long *kernels_per_launch);
+
+/* batch modes */
+#define DD_BATCH_GRAPH       0  /* each frame's solve on a stream of its own, all in one graph */
+#define DD_BATCH_PERSISTENT  1  /* level by level: one persistent launch per sweep over the blocks of all
+                                   frames (their channels and uneven boundary blocks included), each
+                                   frame with its own stop test, in one graph */
+
+/*
+ * As dd_batch_create, with the batch mode.  DD_BATCH_PERSISTENT needs
+ * DD_PREC_FP32 / DD_SOLVER_ORAS / DD_ML_CASCADE handles with device_loop = 1,
+ * timing 0 and the same block, overlap and tile_warps (sizes, masks, level
+ * counts and the other parameters may differ); at most 1024 handles.  Every
+ * level of the cascade is then one graph loop whose passes each sweep all
+ * frames still iterating on that level in a single persistent launch; a frame
+ * drops out at its own stop test or sweep limit.  The results are those of the
+ * frames' solves alone (the same kernel arithmetic per block).
+ * Errors: DD_EINVAL (mode or handle requirements), DD_ENOMEM, DD_ECUDA.
+ */
+int dd_batch_create_mode(int n, const dd_handle *handles, float *const *u_out, double tol, int mode,
+                         dd_batch_handle *out, long long *kernels_per_launch);
 
 /* Launch the batch graph on stream (returns at once).  Errors: DD_EINVAL
  * (previous launch not finished), DD_EEMPTYMASK, DD_ECUDA. */

@@ -18,6 +18,7 @@ DD_OK, DD_EINVAL, DD_EEMPTYMASK, DD_ENOMEM, DD_ENOTCONVERGED, DD_ENUMERIC, DD_EC
 DD_ML_CASCADE, DD_ML_CORRECTION = 0, 1
 DD_SOLVER_ORAS, DD_SOLVER_CG = 0, 1
 DD_PREC_FP32, DD_PREC_FP32_REF, DD_PREC_FP16_REF, DD_PREC_BF16_REF = 0, 1, 2, 3
+DD_BATCH_GRAPH, DD_BATCH_PERSISTENT = 0, 1
 DD_MAX_STAT_CHANNELS = 16
 DD_MAX_LEVELS = 8
 
@@ -28,7 +29,7 @@ EXPORTS = (
     "dd_inpaint_stats", "dd_inpaint_set_iterate", "dd_inpaint_get_iterate", "dd_inpaint_sweep",
     "dd_restrict", "dd_prolong", "dd_residual_norms", "dd_inpaint_solve_static",
     "dd_inpaint_set_data_async", "dd_inpaint_solve_async", "dd_inpaint_query", "dd_inpaint_solve_finish",
-    "dd_batch_create", "dd_batch_launch", "dd_batch_finish", "dd_batch_destroy",
+    "dd_batch_create", "dd_batch_create_mode", "dd_batch_launch", "dd_batch_finish", "dd_batch_destroy",
     "dd_set_device_budget", "dd_device_bytes_in_use", "dd_fp32_fma_peak",
 )
 
@@ -95,6 +96,8 @@ def load(path: str | None = None):
         "dd_inpaint_solve_finish": (_I, [_P, _P]),
         "dd_batch_create": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, ctypes.POINTER(_P),
                                  ctypes.POINTER(ctypes.c_longlong)]),
+        "dd_batch_create_mode": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(_P),
+                                      ctypes.POINTER(ctypes.c_longlong)]),
         "dd_batch_launch": (_I, [_P, _P]),
         "dd_batch_finish": (_I, [_P, _P, ctypes.POINTER(_I)]),
         "dd_batch_destroy": (_I, [_P]),
@@ -230,14 +233,18 @@ def dd_inpaint_solve_finish(h, stream=None) -> int:
     return load().dd_inpaint_solve_finish(h, _stream(stream))
 
 
-def dd_batch_create(handles, out_ptrs, tol: float):
-    """Returns (code, batch handle, kernels per launch)."""
+def dd_batch_create(handles, out_ptrs, tol: float, mode: int | None = None):
+    """Returns (code, batch handle, kernels per launch); mode None = the
+    library's default (dd_batch_create), else dd_batch_create_mode."""
     n = len(handles)
     hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
     outs = (ctypes.c_void_p * n)(*out_ptrs)
     b = ctypes.c_void_p()
     k = ctypes.c_longlong(0)
-    rc = load().dd_batch_create(n, hs, outs, tol, ctypes.byref(b), ctypes.byref(k))
+    if mode is None:
+        rc = load().dd_batch_create(n, hs, outs, tol, ctypes.byref(b), ctypes.byref(k))
+    else:
+        rc = load().dd_batch_create_mode(n, hs, outs, tol, int(mode), ctypes.byref(b), ctypes.byref(k))
     return rc, b, k.value
 
 

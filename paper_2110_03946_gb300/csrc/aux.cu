@@ -754,6 +754,7 @@ __global__ void reset_sweep_state_kernel(int* __restrict__ state, int* __restric
     const bool skip = skip_if != nullptr && *skip_if != 0;
     if (threadIdx.x < 4) state[threadIdx.x] = threadIdx.x == 0 ? cur : 0;
     if (threadIdx.x < 5) flag[threadIdx.x] = (threadIdx.x == 0 && skip) ? 4 : 0;   // 4: sequence skipped
+    if (threadIdx.x == 6) flag[6] = 0;
     if (threadIdx.x == 0) *tol_d = tol;
 }
 

@@ -53,38 +53,38 @@ cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsig
 // is the block tile plus halo of block side b: built once per buffer.
 cudaError_t make_tile_map(CUtensorMap* out, Store st, const void* base, int H, int W, int pitch, int C, int b);
 
-// Residual norms and stop test fused into the sweep.  Tiles are handed to the
-// persistent CTAs in increasing order by an atomic counter (flag[4]), so which
-// CTA takes which tile varies from run to run; the sums do not: each tile's FP32
-// sum of squared owned residuals of the input iterate is added exactly into a
-// 128-bit fixed-point accumulator (unit about 2^-72 ref[c]^2, saturating at
-// 2^32 ref[c]^2, values below the unit truncated), and integer addition does
-// not depend on the order.  Each CTA writes its per-channel accumulator to
-// partial[2 * (c * slots + cta) + {0: low, 1: high word}]; the last CTA to
-// finish adds them into norms2[c] (bitwise repeatable) and sets flag[0]:
+// Residual norms and stop test fused into the sweep.  Each tile's FP32 sum of
+// squared owned residuals of the input iterate is added exactly into a 128-bit
+// fixed-point sum (unit about 2^-72 ref[c]^2, saturating at 2^32 ref[c]^2,
+// values below the unit truncated): the lanes of a CTA batch their tiles' sums,
+// and a CTA adds its sums into acc[2c], acc[2c + 1] (low, high word) with
+// integer atomics when it leaves a channel.  Integer addition does not depend on
+// the order, so the norms and every decision made from them are bitwise
+// repeatable, whichever CTA takes which tile.  flag[2] counts the tiles whose
+// sums are in acc; the CTA that completes the count (all C x ntiles tiles) forms
+// norms2[c] and sets flag[0]:
 //   1 when max_c sqrt(norms2[c]) / ref[c] <= tol (tol < 0: never),
-//   2 on NaN/Inf, 3 when stall > 0 and every channel's residual fell by less
-//   than the factor 1/stall since the previous full sweep, 5 when a bounded
-//   wait of this or an earlier launch gave up (*err != 0);
-// flag[1] = the launch index (state[3]) then.  flag[0] != 0 makes later launches no-ops.
-// flag[3] is the completion ticket and flag[4] the tile counter (both 0
-// between launches); flag[2] is unused.
-// slots >= the launch grid.
+//   2 on NaN/Inf (flag[6] set by a CTA that saw one), 3 when stall > 0 and
+//   every channel's residual fell by less than the factor 1/stall since the
+//   previous full sweep, 5 when a bounded wait of this or an earlier launch
+//   gave up (*err != 0);
+// flag[1] = the launch index (state[3]) then, and acc, flag[2], flag[6] are
+// zeroed for the next sweep.  flag[0] != 0 makes later launches no-ops.
+// flag[3] (the launch's completion ticket) and flag[4] (its tile counter) are
+// 0 between single-frame launches.
 // The iterate pair is chosen on the device: state[0] is the buffer holding the
 // current iterate (the launch reads it and writes the other one), state[1]
 // counts full sweeps, state[2] = 1 makes the next launch a probe that only
 // evaluates the residual of the current iterate (no CG, no write-back), and
 // state[3] counts the launches that ran (the stall test needs a previous
 // sweep), so that a launch needs no per-launch argument and the same launch
-// can repeat inside a graph loop.  After
-// a full sweep the last CTA requests a probe when the residual ratio of the
-// last two sweeps predicts that the new iterate meets tol.  norms2 holds
-// 2C + 2 doubles: current norms, norms of the previous full sweep, and the
-// previous full sweep's worst relative residual.
-constexpr int kFlagWords = 8;     // flag array length (words 0, 1, 3, 4 per sequence; 5 the sticky error word)
+// can repeat inside a graph loop.  After a full sweep the stop test requests a
+// probe when the residual ratio of the last two sweeps predicts that the new
+// iterate meets tol.  norms2 holds 2C + 2 doubles: current norms, norms of the
+// previous full sweep, and the previous full sweep's worst relative residual.
+constexpr int kFlagWords = 8;     // flag array length: words 0-4 and 6 per sequence, 5 the sticky error word
 struct SweepStop {
-    unsigned long long* partial;   // 2 x C x slots words
-    int slots;
+    unsigned long long* acc;   // 2 x C words, zero between sweeps
     double* norms2;
     const double* ref;
     const double* tol;   // device: the tolerance (set by launch_reset_sweep_state), so a
@@ -100,7 +100,7 @@ struct SweepStop {
     unsigned long long* work;
     // sticky error word of the handle: set to 1 when a bounded wait for a
     // staged tile gives up (reset words of a sweep sequence do not clear it);
-    // the last CTA then sets flag[0] = 5, which ends the sequence
+    // the stop test then sets flag[0] = 5, which ends the sequence
     int* err;
     // test hook (0: off): the first staged-tile wait of every CTA polls an
     // mbarrier that no copy completes, stall_polls times, and then gives up as
@@ -108,7 +108,43 @@ struct SweepStop {
     int stall_polls;
 };
 constexpr int kTimedLaunches = 64;   // launches per sequence whose kind work[2 + i] records
-constexpr int kSweepSlots = 4096;   // per-channel partial slots that cover any persistent grid
+
+// Division by a divisor fixed for a launch (dividend < 2^31): the round-up
+// method of Granlund & Montgomery (PLDI 1994), q = (umulhi(n, m) + n) >> s
+// with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+    uint32_t m, s;
+};
+FastDiv make_fastdiv(uint32_t d);
+
+// A sweep's view of one frame (one level of one handle): the iterate pair and
+// its descriptors, the block masks, the geometry, the local solver's
+// parameters and the stop words.  Single-frame launches pass it by value;
+// batched launches read an array of them from device memory (64-byte aligned,
+// not modified while a launch runs).
+struct SweepFrame {   // aligned as CUtensorMap (at least 64 bytes)
+    CUtensorMap map_u[2];
+    CUtensorMap map_g;
+    void* u_buf[2];
+    const uint32_t* tmask;
+    unsigned long long* acc;
+    double* norms2;
+    const double* ref;
+    const double* tol;
+    int* flag;
+    int* state;
+    int* err;
+    unsigned long long* work;
+    int* resolve_out;          // batched levels: the level's result record (launch_batch_resolve)
+    double stall;
+    long long plane;
+    FastDiv dv_tiles, dv_ntx;
+    int H, W, pitch, C, s, ntx, ntiles, has_g;
+    float p_robin, local_rtol2;
+    int k, stall_polls, force_probe;
+    int cap;                   // batched levels: full sweeps after which the frame drops out
+    double level_tol;          // batched levels: the stop tolerance launch_batch_reset sets
+};
 
 // The two iterate buffers of a level and their TMA descriptors.
 struct SweepPair {
@@ -130,8 +166,42 @@ cudaError_t launch_sweep(Store st, const TileGeom& g, int C, long long plane, co
 // per process; call before capturing a sweep launch into a graph.
 cudaError_t prepare_sweep(Store s, const TileGeom& g, bool has_g);
 
-// state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..4] = 0 (flag[5],
-// the sticky error word of a handle's flag array, is left alone); *tol_d = tol
+// ---- batched sweeps (one persistent launch over the tiles of several frames) ----
+// The descriptor of a frame for batched launches (FP32 iterate, no source
+// term): as launch_sweep would use it, with the sweep limit cap of the level
+// and the level's resolve record.
+void fill_sweep_frame(SweepFrame* out, const TileGeom& g, int C, long long plane, const SweepPair& pair,
+                      const uint32_t* tmask, const SweepStop& stop, float p_robin, int k, float local_rtol, int cap,
+                      int* resolve_out);
+// The list of a batched launch: list[0] = n active frames, list[1 .. n] their
+// indices in the frame array, list[1 + n .. 1 + 2n] the prefix sums of their
+// tiles (C x blocks each; the last entry is the launch's tile total).
+// At most kBatchMaxFrames frames.
+constexpr int kBatchMaxFrames = 1024;
+constexpr int kBatchListWords = 2 + 2 * kBatchMaxFrames;
+// One sweep (or probe) of every frame in the list, all frames with the block
+// layout of g (the same block side, overlap and warps per tile).  bctl: 3
+// device ints (completion ticket, tile counter, a wait gave up), zero between
+// launches.  If any wait of the launch gives up, every frame of the launch gets
+// its error word set and its sequence ended (flag[0] = 5).
+cudaError_t launch_sweep_batch(const TileGeom& g, const SweepFrame* frames, const int* list, int* bctl,
+                               cudaStream_t st);
+cudaError_t prepare_sweep_batch(const TileGeom& g);
+// Loop control of a batched level (one thread), at the top of each pass of its
+// device loop: ctl[0] counts the passes; the list gets the frames whose
+// sequences run (flag[0] == 0 and state[1] < cap); the loop's condition is
+// cleared when none does or after max_passes passes (the pass then sweeps no frame).
+cudaError_t launch_batch_ctl(const SweepFrame* frames, int n, int* list, int* ctl, int max_passes,
+                             cudaGraphConditionalHandle cond, cudaStream_t st);
+// Before a batched level: every frame's state[0] = 0, state[1..3] = 0, flag[0..4]
+// and flag[6] = 0, *tol = level_tol.
+cudaError_t launch_batch_reset(const SweepFrame* frames, int n, cudaStream_t st);
+// After a batched level: each frame's resolve record = {state[0], state[1],
+// flag[0], ctl[0]} (as launch_resolve).
+cudaError_t launch_batch_resolve(const SweepFrame* frames, int n, const int* ctl, cudaStream_t st);
+
+// state[0] = cur, state[1] = state[2] = state[3] = 0; flag[0..4] = flag[6] = 0
+// (flag[5], the sticky error word of a handle's flag array, is left alone); *tol_d = tol
 // (the stop tolerance the following sweeps or CG iterations read).  With
 // skip_if and *skip_if != 0, flag[0] = 4 instead: the following sweeps are
 // no-ops.

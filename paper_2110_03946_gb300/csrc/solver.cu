@@ -99,7 +99,8 @@ struct Level {
     uint32_t* tmask = nullptr;
     float* u[2] = {nullptr, nullptr};
     CUtensorMap map_u[2];      // TMA descriptors of u[0], u[1]
-    unsigned long long* partial = nullptr;  // 2 x C x kSweepSlots per-CTA residual sums (128-bit fixed point)
+    unsigned long long* partial = nullptr;  // 2 x C words: exact 128-bit sums of a sweep's residual norms (zero
+                                            // between sweeps)
     double* ref_d = nullptr;   // C
     std::vector<double> ref;   // C (host copy, read after load_data's single sync)
     int* state_d = nullptr;    // resolve() output of this level's last sweep sequence
@@ -252,7 +253,7 @@ int* err_word(dd_inpaint* h) { return h->flag_d + 5; }
 // error word and test hook.
 dd::SweepStop make_stop(dd_inpaint* h, unsigned long long* partial, const double* ref_d, double stall,
                         unsigned long long* work = nullptr) {
-    return dd::SweepStop{partial, dd::kSweepSlots, h->norms2_d, ref_d, h->tol_d, stall, h->flag_d, h->sstate_d, 0,
+    return dd::SweepStop{partial, h->norms2_d, ref_d, h->tol_d, stall, h->flag_d, h->sstate_d, 0,
                          work, err_word(h), h->prm.test_stall_polls};
 }
 
@@ -586,7 +587,7 @@ int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
     DD_CK(cudaMemsetAsync(Lc.u[1], 0, cbytes, st));
     DD_CK(dd::launch_reset_sweep_state(h->state_c, h->flag_c, 0, h->tol_c, -1.0, st, skip));
     const dd::SweepPair pair{{&Lc.map_u[0], &Lc.map_u[1]}, {Lc.u[0], Lc.u[1]}};
-    const dd::SweepStop stop{Lc.partial, dd::kSweepSlots, h->norms2_c, Lc.ref_d, h->tol_c, 0.0, h->flag_c, h->state_c,
+    const dd::SweepStop stop{Lc.partial, h->norms2_c, Lc.ref_d, h->tol_c, 0.0, h->flag_c, h->state_c,
                              0, nullptr, err_word(h), h->prm.test_stall_polls};
     for (int i = 0; i < h->prm.correction_sweeps; ++i)
         DD_CK(dd::launch_sweep(Store::F32, Lc.geom, h->C, Lc.plane(), pair, &Lc.map_cg, Lc.tmask, stop,
@@ -897,6 +898,30 @@ int first_chunk(const dd_inpaint* h) {
     return std::min(n, h->prm.max_sweeps);
 }
 
+// The end of an enqueued FP32 solve: the output of the fine level's resolved
+// iterate with its FP64-accurate residual, and the read-back of everything the
+// finish step needs (level states, flags, reference norms, pixel counts).
+int enqueue_output_readback(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool capture, bool timed) {
+    const int nl = (int)h->lv.size();
+    Level& F = h->lv[0];
+    DD_TRY(output_and_residual(h, u_out, st));
+    DD_CK(cudaMemcpyAsync(h->h_state, F.state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    for (int l = 1; l < nl; ++l)
+        DD_CK(cudaMemcpyAsync(h->h_state + 4 * l, h->lv[l].state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_flag + 3, err_word(h), sizeof(int), cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_ref, F.ref_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
+    DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if (timed)
+        DD_CK(cudaMemcpyAsync(h->h_work, h->work_d, sizeof(unsigned long long) * kWorkWords, cudaMemcpyDeviceToHost,
+                              st));
+    if (!capture) DD_CK(cudaEventRecord(h->ev1, st));
+    h->pending = true;
+    h->pending_out = u_out;
+    h->pending_tol = tol;
+    return DD_OK;
+}
+
 // FP32 path, part 1: enqueue the cascade, the first fine chunk, the output of
 // the resolved buffer, its residual and the read-back of everything the host
 // needs.  No host synchronisation.  capture = 1 inside a stream capture
@@ -922,21 +947,8 @@ int fp32_enqueue(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool 
     const bool timed = h->prm.timing != 0 && !capture;
     const int n1 = loop_mode(h, timed) ? h->prm.max_sweeps : first_chunk(h);
     DD_TRY(enqueue_level(h, F, n1, tol, st, timed, capture));
-    DD_TRY(output_and_residual(h, u_out, st));
-    DD_CK(cudaMemcpyAsync(h->h_state, F.state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    for (int l = 1; l < nl; ++l)
-        DD_CK(cudaMemcpyAsync(h->h_state + 4 * l, h->lv[l].state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    DD_CK(cudaMemcpyAsync(h->h_flag, h->flag_d, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    DD_CK(cudaMemcpyAsync(h->h_flag + 3, err_word(h), sizeof(int), cudaMemcpyDeviceToHost, st));
-    DD_CK(cudaMemcpyAsync(h->h_ref, F.ref_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
-    DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    if (timed)
-        DD_CK(cudaMemcpyAsync(h->h_work, h->work_d, sizeof(unsigned long long) * kWorkWords, cudaMemcpyDeviceToHost,
-                              st));
-    if (!capture) DD_CK(cudaEventRecord(h->ev1, st));
-    h->pending = true;
-    h->pending_out = u_out;
-    h->pending_tol = tol;
+    DD_TRY(enqueue_output_readback(h, u_out, tol, st, capture, timed));
+    (void)nl;
     return DD_OK;
 }
 
@@ -1385,7 +1397,8 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         if ((rc = dalloc_t(h, &L.tmask, dd::tmask_words(L.geom))) != DD_OK) return fail(rc);
         for (int b = 0; b < 2; ++b)
             if ((rc = dalloc(h, (void**)&L.u[b], plane_bytes)) != DD_OK) return fail(rc);
-        if ((rc = dalloc_t(h, &L.partial, (size_t)2 * C * dd::kSweepSlots)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &L.partial, (size_t)2 * C)) != DD_OK) return fail(rc);
+        if ((rc = dzero(L.partial, sizeof(unsigned long long) * 2 * C)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &L.ref_d, (size_t)C)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &L.state_d, 4)) != DD_OK) return fail(rc);
         if (p.solver == DD_SOLVER_CG) {
@@ -1797,7 +1810,9 @@ struct dd_batch {
     std::vector<dd_handle> hs;
     std::vector<float*> outs;
     double tol = 0.0;
+    int mode = DD_BATCH_GRAPH;
     cudaStream_t cap = nullptr;
+    cudaStream_t body = nullptr;            // private stream on which batched loop bodies are captured
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> evs;
     cudaGraph_t graph = nullptr;
@@ -1805,6 +1820,15 @@ struct dd_batch {
     cudaEvent_t done = nullptr;
     long long kernels = 0;
     bool launched = false;
+    // DD_BATCH_PERSISTENT: per dyadic level (0 = finest) the descriptors of the
+    // frames that sweep there, the handles they belong to, and the batch's list
+    // and control words
+    std::vector<dd::SweepFrame*> frames_d;
+    std::vector<std::vector<int>> members;
+    std::vector<int> max_cap;
+    int* list_d = nullptr;                  // dd::kBatchListWords ints
+    int* bctl_d = nullptr;                  // [0, 3) launch ticket, tile counter, failed wait; [4, 8) loop passes
+    TileGeom geom;                          // the block layout shared by all frames
 };
 
 static void batch_free(dd_batch* b) {
@@ -1813,13 +1837,194 @@ static void batch_free(dd_batch* b) {
     for (auto e : b->evs) cudaEventDestroy(e);
     for (auto s2 : b->side) cudaStreamDestroy(s2);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->body) cudaStreamDestroy(b->body);
     if (b->done) cudaEventDestroy(b->done);
+    for (auto p : b->frames_d)
+        if (p) cudaFree(p);
+    if (b->list_d) cudaFree(b->list_d);
+    if (b->bctl_d) cudaFree(b->bctl_d);
     delete b;
 }
 
-int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double tol, dd_batch_handle* out,
-                    long long* kernels_per_launch) {
+namespace {
+
+// Persistent batches: the frames' requirements (FP32 ORAS cascade with device
+// loops and one block layout) and their per-level sweep descriptors.
+int batch_check_persistent(const std::vector<dd_handle>& hs) {
+    const dd_params& p0 = hs[0]->prm;
+    for (auto h : hs) {
+        const dd_params& p = h->prm;
+        if (p.precision != DD_PREC_FP32 || p.solver != DD_SOLVER_ORAS || p.ml_mode != DD_ML_CASCADE ||
+            p.device_loop != 1 || p.timing != 0) {
+            set_error("a persistent batch needs FP32 ORAS cascade handles with device loops and no timing");
+            return DD_EINVAL;
+        }
+        if (p.block != p0.block || p.overlap != p0.overlap || h->lv[0].geom.nw != hs[0]->lv[0].geom.nw) {
+            set_error("the handles of a persistent batch need the same block, overlap and tile warps");
+            return DD_EINVAL;
+        }
+    }
+    if ((int)hs.size() > dd::kBatchMaxFrames) { set_error("too many frames for one persistent batch"); return DD_EINVAL; }
+    return DD_OK;
+}
+
+int batch_build_frames(dd_batch* b) {
+    int nlev = 0;
+    for (auto h : b->hs) nlev = std::max(nlev, (int)h->lv.size());
+    b->frames_d.assign(nlev, nullptr);
+    b->members.assign(nlev, {});
+    b->max_cap.assign(nlev, 0);
+    for (int l = 0; l < nlev; ++l) {
+        std::vector<dd::SweepFrame> host;
+        for (int i = 0; i < (int)b->hs.size(); ++i) {
+            dd_handle h = b->hs[i];
+            if (l >= (int)h->lv.size() || !h->lv[l].solved) continue;
+            Level& L = h->lv[l];
+            const int cap = l == 0 ? h->prm.max_sweeps : h->prm.coarse_sweeps;
+            const dd::SweepPair pair{{&L.map_u[0], &L.map_u[1]}, {L.u[0], L.u[1]}};
+            dd::SweepFrame f;
+            dd::fill_sweep_frame(&f, L.geom, h->C, L.plane(), pair, L.tmask, make_stop(h, L.partial, L.ref_d, 0.0),
+                                 h->prm.robin_p, h->prm.local_cg_iters, (float)h->prm.local_rtol, cap, L.state_d);
+            if (f.flag == nullptr) { set_error("batch: bad sweep descriptor"); return DD_EINVAL; }
+            f.level_tol = l == 0 ? b->tol : h->prm.coarse_tol;
+            host.push_back(f);
+            b->members[l].push_back(i);
+            b->max_cap[l] = std::max(b->max_cap[l], cap);
+        }
+        if (host.empty()) continue;
+        DD_CK(cudaMalloc(&b->frames_d[l], sizeof(dd::SweepFrame) * host.size()));
+        DD_CK(cudaMemcpy(b->frames_d[l], host.data(), sizeof(dd::SweepFrame) * host.size(), cudaMemcpyHostToDevice));
+    }
+    DD_CK(cudaMalloc(&b->list_d, sizeof(int) * dd::kBatchListWords));
+    DD_CK(cudaMemset(b->list_d, 0, sizeof(int) * dd::kBatchListWords));
+    DD_CK(cudaMalloc(&b->bctl_d, sizeof(int) * 8));
+    DD_CK(cudaMemset(b->bctl_d, 0, sizeof(int) * 8));
+    b->geom = b->hs[0]->lv[0].geom;
+    DD_CK(dd::prepare_sweep_batch(b->geom));
+    return DD_OK;
+}
+
+// The batched loop of level l, appended to the graph being captured on st: an
+// entry kernel (pass counter 0, condition 1), then a WHILE node whose body is
+// the loop control (the list of the frames whose sequences run; condition
+// cleared when none does) followed by one batched sweep of those frames.
+int batch_add_loop(dd_batch* b, int l, cudaStream_t st) {
+    const int n = (int)b->members[l].size();
+    const int max_passes = 2 * b->max_cap[l] + 3;
+    int* const ctl = b->bctl_d + 4;
+    return capture_append(st, [&](cudaGraph_t g, const cudaGraphNode_t* deps, const cudaGraphEdgeData* edges,
+                                  size_t ndeps, cudaGraphNode_t* last) -> int {
+        cudaGraphConditionalHandle cond;
+        DD_CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+        int* ctl_arg = ctl;
+        void* kargs[2] = {&ctl_arg, &cond};
+        cudaGraphNodeParams kp{};
+        kp.type = cudaGraphNodeTypeKernel;
+        kp.kernel.func = const_cast<void*>(dd::loop_begin_kernel_fn());
+        kp.kernel.gridDim = dim3(1, 1, 1);
+        kp.kernel.blockDim = dim3(32, 1, 1);
+        kp.kernel.kernelParams = kargs;
+        cudaGraphNode_t entry = nullptr, loop = nullptr;
+        DD_CK(cudaGraphAddNode(&entry, g, deps, edges, ndeps, &kp));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        DD_CK(cudaGraphAddNode(&loop, g, &entry, nullptr, 1, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        DD_CK(cudaStreamBeginCaptureToGraph(b->body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = dd::launch_batch_ctl(b->frames_d[l], n, b->list_d, ctl, max_passes, cond, b->body);
+        cudaError_t e2 = e1 == cudaSuccess ? dd::launch_sweep_batch(b->geom, b->frames_d[l], b->list_d, b->bctl_d,
+                                                                    b->body)
+                                           : cudaSuccess;
+        cudaGraph_t captured = body;
+        const cudaError_t ec = cudaStreamEndCapture(b->body, &captured);
+        DD_CK(e1);
+        DD_CK(e2);
+        DD_CK(ec);
+        *last = loop;
+        return DD_OK;
+    });
+}
+
+// Fork from cap onto the side streams of the frames in idx, run per(i, stream)
+// on each, join back into cap.
+int batch_fork(dd_batch* b, const std::vector<int>& idx, const std::function<int(int, cudaStream_t)>& per) {
+    const int n = (int)b->hs.size();
+    DD_CK(cudaEventRecord(b->evs[2 * n], b->cap));
+    for (int i : idx) {
+        DD_CK(cudaStreamWaitEvent(b->side[i], b->evs[2 * n], 0));
+        DD_TRY(per(i, b->side[i]));
+        DD_CK(cudaEventRecord(b->evs[2 * i], b->side[i]));
+        DD_CK(cudaStreamWaitEvent(b->cap, b->evs[2 * i], 0));
+    }
+    return DD_OK;
+}
+
+// The whole batch on the capturing stream b->cap: per frame the coarsest
+// level's start; then, level by level from the coarsest, each frame's start
+// prolonged from the level below it (side streams), and one batched device
+// loop of sweeps over all frames that solve on the level; finally each frame's
+// output, FP64-accurate residual and read-back (side streams).
+int batch_enqueue_persistent(dd_batch* b) {
+    const int n = (int)b->hs.size();
+    const int nlev = (int)b->frames_d.size();
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    DD_TRY(batch_fork(b, all, [&](int i, cudaStream_t st) -> int {
+        dd_handle h = b->hs[i];
+        std::memset(&h->stats, 0, sizeof(h->stats));
+        h->stats.channels = h->C;
+        h->stats.device_bytes = h->bytes;
+        h->ev_recorded = false;
+        h->warm = false;
+        h->pending_cascaded = true;
+        DD_TRY(clear_error(h, st));
+        Level& Lc = h->lv.back();
+        DD_LAUNCH(h, dd::launch_copy2d(Lc.H, Lc.W, h->C, Lc.f, Lc.P, Lc.plane(), Lc.u[0], Lc.P, Lc.plane(), st));
+        return DD_OK;
+    }));
+    for (int l = nlev - 1; l >= 0; --l) {
+        // starts of level l prolonged from level l + 1; pass-through levels record buffer 0
+        std::vector<int> idx;
+        for (int i = 0; i < n; ++i) {
+            const int nli = (int)b->hs[i]->lv.size();   // frames with fewer levels join at their coarsest
+            if (l < nli - 1 || (l < nli && !b->hs[i]->lv[l].solved)) idx.push_back(i);
+        }
+        if (!idx.empty())
+            DD_TRY(batch_fork(b, idx, [&](int i, cudaStream_t st) -> int {
+                dd_handle h = b->hs[i];
+                Level& L = h->lv[l];
+                if (l < (int)h->lv.size() - 1) {
+                    Level& Cc = h->lv[l + 1];
+                    DD_LAUNCH(h, dd::launch_prolong_sel(Cc.H, Cc.W, L.H, L.W, h->C, Cc.u[0], Cc.u[1], Cc.state_d,
+                                                        Cc.P, Cc.plane(), L.mask, L.W, L.f, L.P, L.plane(), L.u[0],
+                                                        L.P, L.plane(), st));
+                }
+                if (!L.solved) DD_CK(cudaMemsetAsync(L.state_d, 0, 4 * sizeof(int), st));
+                return DD_OK;
+            }));
+        const int nf = (int)b->members[l].size();
+        if (nf == 0) continue;
+        DD_CK(dd::launch_batch_reset(b->frames_d[l], nf, b->cap));
+        DD_TRY(batch_add_loop(b, l, b->cap));
+        DD_CK(dd::launch_batch_resolve(b->frames_d[l], nf, b->bctl_d + 4, b->cap));
+        b->kernels += 3;
+    }
+    return batch_fork(b, all, [&](int i, cudaStream_t st) -> int {
+        dd_handle h = b->hs[i];
+        for (Level& L : h->lv) L.loop_pending = false;   // batched loops are counted by the batch
+        return enqueue_output_readback(h, b->outs[i], b->tol, st, true, false);
+    });
+}
+
+}  // namespace
+
+int dd_batch_create_mode(int n, const dd_handle* handles, float* const* u_out, double tol, int mode,
+                         dd_batch_handle* out, long long* kernels_per_launch) {
     if (n <= 0 || !handles || !u_out || !out || !(tol > 0.0)) { set_error("bad batch arguments"); return DD_EINVAL; }
+    if (mode != DD_BATCH_GRAPH && mode != DD_BATCH_PERSISTENT) { set_error("bad batch mode"); return DD_EINVAL; }
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
         if (!handles[i] || !u_out[i]) { set_error("NULL handle or output"); return DD_EINVAL; }
@@ -1831,11 +2036,14 @@ int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double
         for (int j = 0; j < i; ++j)
             if (handles[j] == handles[i]) { set_error("a handle appears twice"); return DD_EINVAL; }
     }
+    std::vector<dd_handle> hs(handles, handles + n);
+    if (mode == DD_BATCH_PERSISTENT) DD_TRY(batch_check_persistent(hs));
     dd_batch* b = new (std::nothrow) dd_batch();
     if (!b) { set_error("host allocation"); return DD_ENOMEM; }
-    b->hs.assign(handles, handles + n);
+    b->hs = hs;
     b->outs.assign(u_out, u_out + n);
     b->tol = tol;
+    b->mode = mode;
     auto bail = [&](const char* what, cudaError_t e) {
         set_error(std::string(what) + ": " + cudaGetErrorString(e));
         batch_free(b);
@@ -1843,6 +2051,7 @@ int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double
     };
     cudaError_t e;
     if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
+    if ((e = cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream", e);
     if ((e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
     b->side.resize(n, nullptr);
     b->evs.resize(2 * n + 1, nullptr);
@@ -1851,20 +2060,29 @@ int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double
             return bail("stream", e);
     for (auto& ev : b->evs)
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return bail("event", e);
-    // capture: fork one stream per frame, enqueue each frame's solve, join
+    if (mode == DD_BATCH_PERSISTENT) {
+        const int rcf = batch_build_frames(b);
+        if (rcf != DD_OK) { batch_free(b); return rcf; }
+    }
     long long before = 0;
     for (auto h : b->hs) before += h->launches;
     if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return bail("capture", e);
     int rc = DD_OK;
-    if ((e = cudaEventRecord(b->evs[2 * n], b->cap)) != cudaSuccess) rc = DD_ECUDA;
-    for (int i = 0; i < n && rc == DD_OK; ++i) {
-        if (cudaStreamWaitEvent(b->side[i], b->evs[2 * n], 0) != cudaSuccess) { rc = DD_ECUDA; break; }
-        b->hs[i]->warm = false;   // a captured solve always starts with the cascade
-        rc = enqueue_solve(b->hs[i], b->outs[i], tol, b->side[i], true);
-        b->hs[i]->pending = false;
-        if (rc == DD_OK && cudaEventRecord(b->evs[2 * i], b->side[i]) != cudaSuccess) rc = DD_ECUDA;
-        if (rc == DD_OK && cudaStreamWaitEvent(b->cap, b->evs[2 * i], 0) != cudaSuccess) rc = DD_ECUDA;
+    if (mode == DD_BATCH_PERSISTENT) {
+        rc = batch_enqueue_persistent(b);
+        for (auto h : b->hs) h->pending = false;
+    } else {
+        // fork one stream per frame, enqueue each frame's solve, join
+        if ((e = cudaEventRecord(b->evs[2 * n], b->cap)) != cudaSuccess) rc = DD_ECUDA;
+        for (int i = 0; i < n && rc == DD_OK; ++i) {
+            if (cudaStreamWaitEvent(b->side[i], b->evs[2 * n], 0) != cudaSuccess) { rc = DD_ECUDA; break; }
+            b->hs[i]->warm = false;   // a captured solve always starts with the cascade
+            rc = enqueue_solve(b->hs[i], b->outs[i], tol, b->side[i], true);
+            b->hs[i]->pending = false;
+            if (rc == DD_OK && cudaEventRecord(b->evs[2 * i], b->side[i]) != cudaSuccess) rc = DD_ECUDA;
+            if (rc == DD_OK && cudaStreamWaitEvent(b->cap, b->evs[2 * i], 0) != cudaSuccess) rc = DD_ECUDA;
+        }
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->cap, &g);
@@ -1874,16 +2092,32 @@ int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double
         batch_free(b);
         return rc == DD_OK ? DD_ECUDA : rc;
     }
-    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return bail("cudaGraphInstantiate", e);
+    {
+        cudaGraphInstantiateParams ip{};
+        ip.flags = 0;
+        if ((e = cudaGraphInstantiateWithParams(&b->exec, b->graph, &ip)) != cudaSuccess) {
+            cudaGraphNodeType t = cudaGraphNodeTypeEmpty;
+            if (ip.errNode_out) cudaGraphNodeGetType(ip.errNode_out, &t);
+            set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e) + " (result " +
+                      std::to_string((int)ip.result_out) + ", node type " + std::to_string((int)t) + ")");
+            batch_free(b);
+            return DD_ECUDA;
+        }
+    }
     long long after = 0;
     for (auto h : b->hs) {
         after += h->launches;
         for (Level& L : h->lv) L.loop_pending = false;   // captured, not run
     }
-    b->kernels = after - before;
+    b->kernels += after - before;
     if (kernels_per_launch) *kernels_per_launch = b->kernels;
     *out = b;
     return DD_OK;
+}
+
+int dd_batch_create(int n, const dd_handle* handles, float* const* u_out, double tol, dd_batch_handle* out,
+                    long long* kernels_per_launch) {
+    return dd_batch_create_mode(n, handles, u_out, tol, DD_BATCH_GRAPH, out, kernels_per_launch);
 }
 
 int dd_batch_launch(dd_batch_handle b, void* stream) {

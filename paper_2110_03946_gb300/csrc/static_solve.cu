@@ -40,7 +40,7 @@ namespace {
 constexpr long long kMaxIterElems = 1LL << 22;   // C * H * pitch of one iterate buffer
 constexpr long long kMaxTiles = 16384;           // blocks per channel
 constexpr long long kMaxTileWords = kMaxTiles * 2 * 64;    // block masks: 2 words per thread, blocks x threads <= 2^20
-constexpr long long kMaxPartials = 2LL * DD_MAX_STAT_CHANNELS * dd::kSweepSlots;   // per-CTA residual sums (words)
+constexpr long long kMaxPartials = 2LL * DD_MAX_STAT_CHANNELS;   // exact residual sums per channel (words)
 constexpr long long kMaxResBlocks = 65536;       // C * blocks of the FP64 residual pass
 constexpr int kMaxChannels = DD_MAX_STAT_CHANNELS;
 
@@ -162,6 +162,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
 
     // the error word starts clear; u0 = C f, block masks, reference norms ||b - A u0||
     SS_CK(cudaMemsetAsync(flag + 5, 0, sizeof(int), st));
+    SS_CK(cudaMemsetAsync(partial, 0, sizeof(unsigned long long) * 2 * C, st));
     SS_CK(dd::launch_masked_copy(H, W, C, values, W, (long long)H * W, mask, W, u[0], P, plane, st));
     SS_CK(dd::launch_build_tmask(g, mask, W, tmask, st));
     double2 h_res[kMaxChannels];
@@ -190,7 +191,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     const dd::SweepPair pair{{&maps[0], &maps[1]}, {u[0], u[1]}};
     for (int attempt = 0; attempt < 4 && !converged; ++attempt) {
         SS_CK(dd::launch_reset_sweep_state(sstate, flag, cur, tol_d, target, st));
-        dd::SweepStop stop{partial, dd::kSweepSlots, norms2, ref_d, tol_d, 0.0, flag, sstate, 0,
+        dd::SweepStop stop{partial, norms2, ref_d, tol_d, 0.0, flag, sstate, 0,
                            nullptr, flag + 5, p.test_stall_polls};
         const int start = done;
         int launched = 0;

@@ -33,6 +33,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "dd_internal.h"
 
@@ -132,7 +133,6 @@ __device__ __forceinline__ void fix_add(Fix128& acc, unsigned long long lo, unsi
 __device__ __forceinline__ int fix_unit(double ref) {
     return 2 * ilogb(ref > 0.0 && isfinite(ref) ? ref : 1.0) - 72;
 }
-constexpr unsigned long long kFixBad = ~0ull;   // high word of a partial that saw NaN/Inf
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
@@ -196,38 +196,9 @@ struct Box {
     static_assert(BX <= 256 && BY <= 256, "TMA box too large");
 };
 
-// Division by a divisor fixed for the launch (n < 2^31): the round-up method of
-// Granlund & Montgomery (PLDI 1994), q = (umulhi(n, m) + n) >> s with
-// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1, computed on the host.
-struct FastDiv {
-    uint32_t m, s;
-};
-FastDiv make_fastdiv(uint32_t d) {
-    uint32_t s = 0;
-    while ((1ull << s) < d) ++s;
-    return FastDiv{(uint32_t)(((1ull << 32) * ((1ull << s) - d)) / d + 1), s};
-}
 __device__ __forceinline__ int fdiv(int n, FastDiv f) {
     return (int)(((unsigned long long)__umulhi((uint32_t)n, f.m) + (uint32_t)n) >> f.s);
 }
-
-template <typename T>
-struct SweepArgs {
-    T* u_buf[2];
-    const uint32_t* tmask;
-    SweepStop stop;
-    int H, W, pitch, C;
-    int s, ntx, ntiles;
-    int total;            // ntiles * C (< 2^31)
-    int static_end;       // tiles below this go round-robin to the CTAs; the rest are claimed
-    FastDiv dv_tiles;     // division by ntiles (tile -> channel)
-    FastDiv dv_ntx;       // division by ntx (block -> block row)
-    int has_g;
-    long long plane;
-    float p_robin;
-    int k;
-    float local_rtol2;   // local CG stops once (r, r) <= local_rtol2 * (r0, r0) (0: after k steps)
-};
 
 // Two sums over the threads of one tile in one butterfly.
 template <class CF>
@@ -295,13 +266,83 @@ __device__ __forceinline__ Fix128 warp_fix_sum(Fix128 f) {
     return f;
 }
 
+// Add a 128-bit value exactly into a sum in global memory: the low word with
+// one atomic, its carry with the high word in a second.  The number of carries
+// over all adds is that of the total, so the final sum does not depend on the
+// order of the adds.
+__device__ __forceinline__ void fix_atomic_add(unsigned long long* dst, const Fix128& v) {
+    if (v.lo == 0ull && v.hi == 0ull) return;
+    const unsigned long long old = atomicAdd(dst, v.lo);
+    const unsigned long long carry = (old + v.lo < old) ? 1ull : 0ull;
+    if (v.hi + carry != 0ull) atomicAdd(dst + 1, v.hi + carry);
+}
+
+// The stop test of one frame's sweep (one thread, after all its tiles' sums
+// are in F.acc): norms, the stop flag and the sweep state for the next launch;
+// the sums and the tile count are zeroed for the next sweep.
+__device__ __forceinline__ void frame_stop_test(const SweepFrame& F, bool probe, int cur) {
+    __threadfence();
+    int* const flag = F.flag;
+    int* const state = F.state;
+    const int C = F.C;
+    const int sweep_index = __ldcg(state + 3);   // launches before this one
+    const double tol = __ldcg(F.tol);
+    double worst = 0.0, best_ratio = 1e300;
+    bool bad = __ldcg(flag + 6) != 0;
+    for (int c = 0; c < C; ++c) {
+        const unsigned long long lo = __ldcg(F.acc + 2 * c), hi = __ldcg(F.acc + 2 * c + 1);
+        F.acc[2 * c] = 0ull;
+        F.acc[2 * c + 1] = 0ull;
+        const double ref = F.ref[c];
+        const int ec = fix_unit(ref);
+        const double v = ldexp((double)hi, 64 + ec) + ldexp((double)lo, ec);
+        if (!isfinite(v)) bad = true;
+        const double den = ref > 0.0 ? ref : 1.0;
+        worst = fmax(worst, sqrt(v) / den);
+        if (sweep_index > 0) {
+            const double prev = F.norms2[C + c];
+            best_ratio = fmin(best_ratio, prev > 0.0 ? sqrt(v / prev) : 0.0);
+        }
+        F.norms2[c] = v;
+        if (!probe) F.norms2[C + c] = v;
+    }
+    flag[2] = 0;
+    flag[6] = 0;
+    if (F.work != nullptr && sweep_index < kTimedLaunches) F.work[2 + sweep_index] = probe ? 0ull : 1ull;
+    if (__ldcg(F.err) != 0) { flag[0] = 5; flag[1] = sweep_index; }
+    else if (bad) { flag[0] = 2; flag[1] = sweep_index; }
+    else if (worst <= tol) { flag[0] = 1; flag[1] = sweep_index; }
+    else if (F.stall > 0.0 && sweep_index > 0 && best_ratio > F.stall) {
+        flag[0] = 3;
+        flag[1] = sweep_index;
+    } else if (!probe) {
+        // the output of this sweep becomes the current iterate; probe it next
+        // if the residual ratio of this level's last two full sweeps (before its
+        // second full sweep: an assumed contraction of kFirstContraction)
+        // predicts that it meets tol
+        const double prev_worst = F.norms2[2 * C];
+        const bool history = state[1] > 0 && prev_worst > 0.0;
+        const double pred = history ? worst * (worst / prev_worst) : worst * kFirstContraction;
+        state[0] = cur ^ 1;
+        state[1] += 1;
+        state[2] = (tol > 0.0 && pred <= tol) ? 1 : 0;
+    } else {
+        state[2] = 0;   // the probe failed: sweep the same iterate in full
+    }
+    if (!probe) F.norms2[2 * C] = worst;
+    state[3] = sweep_index + 1;
+}
+
 // ALN: every block starts at a column that is a multiple of 4 (stride s % 4 == 0,
 // FP32 storage, 4 pixels per lane row), so a lane's 4 pixels of a row are one
-// 16-byte vector in the staged tile and in the iterate.
-template <class CF, typename T, bool ALN>
+// 16-byte vector in the staged tile.
+// BATCH: the tiles of several frames (the list written by batch_ctl_kernel) in
+// one launch; otherwise one frame, passed by value.  HASG: the frame solves
+// A u = C f + (I - C) g with a source g staged beside u (has_g).
+template <class CF, typename T, bool ALN, bool BATCH, bool HASG>
 __global__ void __launch_bounds__(CF::NT)
-oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_constant__ CUtensorMap map_u1,
-                  const __grid_constant__ CUtensorMap map_g, const SweepArgs<T> a) {
+oras_sweep_kernel(const __grid_constant__ SweepFrame one, const SweepFrame* __restrict__ many,
+                  const int* __restrict__ list, int* __restrict__ lctl) {
     constexpr int PX = CF::PX, PY = CF::PY, LX = CF::LX, LY = CF::LY, NW = CF::NW;
     constexpr int BW = CF::BW, BH = CF::BH, NP = CF::NP, NT = CF::NT;
     using BOX = Box<CF, T>;
@@ -316,25 +357,23 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     __shared__ float xch[2][NW][BW];      // initial boundary rows of r
     __shared__ float xq[2][2][NW][BW];    // boundary rows of q', alternating by step parity
 
-    int* const flag = a.stop.flag;   // [0] stop/skip, [1] conv_at, [3] ticket, [4] tile counter
-    if (flag[0] != 0) return;                        // converged or failed earlier: uniform no-op
-    // the current iterate and the kind of launch are device state (read before
-    // the last CTA of this launch updates them)
-    const int cur = a.stop.state[0];
-    const bool probe = a.stop.force_probe != 0 || a.stop.state[2] != 0;
-    const CUtensorMap* const map_u = cur ? &map_u1 : &map_u0;
-    T* const u_out = a.u_buf[cur ^ 1];
-    const int kcg = probe ? 0 : a.k;
-    const int total = a.total;
-    int t = blockIdx.x;
-    if (t >= total) return;
+    const int n_act = BATCH ? __ldg(list) : 1;
+    if (n_act <= 0) return;                        // uniform: no frame to sweep
+    if (!BATCH && one.flag[0] != 0) return;        // uniform: converged or failed earlier
+    const int total = BATCH ? __ldg(list + 1 + 2 * n_act) : one.ntiles * one.C;
+    int* const ticket = BATCH ? lctl : one.flag + 3;
+    int* const counter = BATCH ? lctl + 1 : one.flag + 4;
+    // frame slot q of the launch: its descriptor and its tiles [begin, end)
+    auto frame_at = [&](int q) -> const SweepFrame* { return BATCH ? many + __ldg(list + 1 + q) : &one; };
+    auto begin_at = [&](int q) { return BATCH ? __ldg(list + 1 + n_act + q) : 0; };
+    auto end_at = [&](int q) { return BATCH ? __ldg(list + 2 + n_act + q) : total; };
 
     const int tt = threadIdx.x;
     const int wt = tt >> 5, lane = tt & 31;
     const int lx = lane % LX, ly = lane / LX;
     const int ry0 = (wt * LY + ly) * PY, rx0 = lx * PX;
-    const int H = a.H, W = a.W, P = a.pitch;
-    const int narr = a.has_g ? 2 : 1;
+    static_assert(!(BATCH && HASG), "batched launches have no source term");
+    constexpr int narr = HASG ? 2 : 1;
     constexpr int MB = mask_bytes<CF>();
     const uint32_t tx_bytes = (uint32_t)(BOX::BYTES * narr + MB);
     // TMA destinations must be 128-byte aligned: round the dynamic base up
@@ -350,17 +389,22 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     };
     // the TMA box of a block starts at the 16-byte aligned column at or left of x0 - 1
     auto box_x = [](int x0) { return ((x0 - 1) >= 0 ? (x0 - 1) / BOX::ALIGN : -1) * BOX::ALIGN; };
+    int q_st = 0;   // thread 0: frame slot of the last staged tile (a CTA's tiles increase)
     auto issue = [&](int tn, int buf) {   // thread 0 only
-        const int c = fdiv(tn, a.dv_tiles);
-        const int tile = tn - c * a.ntiles;
-        const int ty = fdiv(tile, a.dv_ntx), tx = tile - ty * a.ntx;
-        const int x0 = tx * a.s, y0 = ty * a.s;
+        while (q_st + 1 < n_act && tn >= end_at(q_st)) ++q_st;
+        const SweepFrame* const F = frame_at(q_st);
+        const int local = tn - begin_at(q_st);
+        const int c = fdiv(local, F->dv_tiles);
+        const int tile = local - c * F->ntiles;
+        const int ty = fdiv(tile, F->dv_ntx), tx = tile - ty * F->ntx;
+        const int x0 = tx * F->s, y0 = ty * F->s;
         const int xs = box_x(x0);
+        const CUtensorMap* const map = __ldcg(F->state) ? &F->map_u[1] : &F->map_u[0];
         fence_proxy_async();
         mbar_expect_tx(&mbar[buf], tx_bytes);
-        tma_load_3d(stage(buf, 0), map_u, xs, y0 - 1, c, &mbar[buf]);
-        if (a.has_g) tma_load_3d(stage(buf, 1), &map_g, xs, y0 - 1, c, &mbar[buf]);
-        bulk_load(stage_mask(buf), a.tmask + (size_t)tile * 2 * NT, (uint32_t)MB, &mbar[buf]);
+        tma_load_3d(stage(buf, 0), map, xs, y0 - 1, c, &mbar[buf]);
+        if constexpr (HASG) tma_load_3d(stage(buf, 1), &F->map_g, xs, y0 - 1, c, &mbar[buf]);
+        bulk_load(stage_mask(buf), F->tmask + (size_t)tile * 2 * NT, (uint32_t)MB, &mbar[buf]);
     };
 
     if (tt == 0) {
@@ -374,55 +418,75 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
     // b + G, ...); after its last one a CTA claims further tiles from an atomic
     // counter, so CTAs whose local problems stopped early take more of the
     // tail.  Thread 0 claims one iteration ahead of the staging.  A CTA's tiles
-    // come in increasing order either way.
+    // come in increasing order either way (so frames and channels too).
     const int G = (int)gridDim.x;
+    const int static_end = max(G, total - kDynamicRounds * G);
     auto next_of = [&](int tcur) {   // thread 0 only
-        return tcur + G < a.static_end
-                   ? tcur + G
-                   : (int)atomicAdd(reinterpret_cast<unsigned*>(flag + 4), 1u) + a.static_end;
+        return tcur + G < static_end ? tcur + G : (int)atomicAdd(reinterpret_cast<unsigned*>(counter), 1u) + static_end;
     };
+    int t = blockIdx.x;
     int claim = 0;
-    if (tt == 0) {
+    if (tt == 0 && t < total) {
         issue(t, 0);
         claim = next_of(t);
     }
 
-    const float pr = a.p_robin;
     const float fW = lx > 0 ? 1.f : 0.f, fE = lx < LX - 1 ? 1.f : 0.f;
     // NW == 1: a lane of the block's top (bottom) lane row has no north (south)
     // neighbour lane; its shuffled value is weighted 0
     const float2 fN2 = make_float2(ly > 0 ? 1.f : 0.f, ly > 0 ? 1.f : 0.f);
     const float2 fS2 = make_float2(ly < LY - 1 ? 1.f : 0.f, ly < LY - 1 ? 1.f : 0.f);
+    // The frame being processed: its slot, descriptor and launch state (the
+    // iterate buffer and whether this launch probes it), read when the CTA
+    // meets the frame (before the frame's stop test can change them).
+    int q_pr = -1;
+    const SweepFrame* Fp = nullptr;
+    int f_cur = 0, f_kcg = 0, f_tiles = 0;
+    int f_probe = 0;   // (ints rather than bools for the state kept across tiles: fewer live predicates)
     // Residual sums of the input iterate per channel, exact (Fix128): lane
     // (it mod 32) holds the owned ||r||^2 of this CTA's tile it until every 32
     // tiles (or a change of channel) all lanes add their value into their own
-    // accumulator at once; the lanes' accumulators are summed when a channel's
-    // partial is written.  Tiles come in increasing order, so channels too.
-    unsigned long long* const part = a.stop.partial;
-    const int slots = a.stop.slots;
-    auto put = [&](int cc, const Fix128& v, bool bad) {   // thread 0 only
-        part[2 * ((size_t)cc * slots + blockIdx.x)] = v.lo;
-        part[2 * ((size_t)cc * slots + blockIdx.x) + 1] = bad ? kFixBad : v.hi;
-    };
+    // accumulator at once; the lanes' accumulators are summed and added to the
+    // frame's sums when the CTA leaves the channel.
     int cur_c = -1, eu = 0;
     Fix128 acc{0ull, 0ull};
     float pend = 0.f;
-    bool acc_bad = false;   // the same on every lane (it follows the tile-uniform sums)
-    // channel cur_c done: add the pending values, sum the lanes, write (and zero
-    // the partials of the channels in [cur_c + 1, upto) that this CTA skipped)
-    auto flush = [&](int upto) {
+    int acc_bad = 0;   // the same on every lane (it follows the tile-uniform sums)
+    uint32_t work_us = 0, work_u = 0;   // optional work counters (per lane)
+    auto flush_channel = [&]() {   // all threads
         if (cur_c >= 0) {
             fix_add(acc, pend, eu);
             const Fix128 f = warp_fix_sum(acc);
-            if (tt == 0) put(cur_c, f, acc_bad);
+            if (tt == 0) {
+                if (acc_bad) atomicExch(Fp->flag + 6, 1);
+                fix_atomic_add(Fp->acc + 2 * cur_c, f);
+            }
         }
-        if (tt == 0)
-            for (int cc = cur_c + 1; cc < upto; ++cc) put(cc, Fix128{0ull, 0ull}, false);
         acc = Fix128{0ull, 0ull};
         pend = 0.f;
-        acc_bad = false;
+        acc_bad = 0;
+        cur_c = -1;
     };
-    uint32_t work_us = 0, work_u = 0;   // optional work counters (per lane)
+    // leaving frame Fp: its sums, its work counters and its count of done tiles;
+    // the CTA that completes the count runs the frame's stop test
+    auto flush_frame = [&]() {   // all threads
+        flush_channel();
+        if (Fp->work != nullptr) {
+            const uint32_t ws = __reduce_add_sync(FULL, work_us), wu = __reduce_add_sync(FULL, work_u);
+            if (lane == 0 && wu != 0) {
+                atomicAdd(Fp->work, (unsigned long long)ws);
+                atomicAdd(Fp->work + 1, (unsigned long long)wu);
+            }
+        }
+        work_us = work_u = 0;
+        if constexpr (NW > 1) __syncthreads();   // every warp's work counters are in
+        if (tt == 0) {
+            __threadfence();
+            const int prev = atomicAdd(Fp->flag + 2, f_tiles);
+            if (prev + f_tiles == Fp->ntiles * Fp->C) frame_stop_test(*Fp, f_probe != 0, f_cur);
+        }
+        f_tiles = 0;
+    };
     int it = 0;
     for (; t < total; ++it) {
         const int buf = it & 1;
@@ -435,27 +499,42 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                 claim = next_of(tn);
             }
         }
-
-        const int c = fdiv(t, a.dv_tiles);
-        const int tile = t - c * a.ntiles;
-        const int ty = fdiv(tile, a.dv_ntx), tx = tile - ty * a.ntx;
-        const int y0 = ty * a.s, x0 = tx * a.s;
+        int q = q_pr < 0 ? 0 : q_pr;
+        while (q + 1 < n_act && t >= end_at(q)) ++q;
+        if (q != q_pr) {   // a new frame (uniform)
+            if (q_pr >= 0) flush_frame();
+            q_pr = q;
+            Fp = frame_at(q);
+            f_cur = __ldcg(Fp->state);
+            f_probe = (Fp->force_probe != 0 || __ldcg(Fp->state + 2) != 0) ? 1 : 0;
+            f_kcg = f_probe ? 0 : Fp->k;
+        }
+        const int local = t - begin_at(q);
+        const int c = fdiv(local, Fp->dv_tiles);
+        const int tile = local - c * Fp->ntiles;
+        const int ty = fdiv(tile, Fp->dv_ntx), tx = tile - ty * Fp->ntx;
+        const int y0 = ty * Fp->s, x0 = tx * Fp->s;
+        const int H = Fp->H, W = Fp->W;
         const int th = min(BH, H - y0), tw = min(BW, W - x0);
         const int cx = ALN ? 4 : x0 - box_x(x0);   // smem column of x0
 
         if (tt == 0) {
-            const bool ok = (it == 0 && a.stop.stall_polls > 0) ? mbar_wait_bounded(&mbar[2], 0u, a.stop.stall_polls)
-                                                                : mbar_wait_bounded(&mbar[buf], parity);
+            const bool ok = (it == 0 && Fp->stall_polls > 0) ? mbar_wait_bounded(&mbar[2], 0u, Fp->stall_polls)
+                                                             : mbar_wait_bounded(&mbar[buf], parity);
             s_ok = ok ? 1 : 0;
-            if (!ok) atomicExch(a.stop.err, 1);
+            if (!ok) {
+                atomicExch(Fp->err, 1);
+                if (BATCH) atomicExch(lctl + 2, 1);   // the whole batched launch is abandoned
+            }
         }
         __syncthreads();
         if (!s_ok) break;                               // uniform
         if (tt != 0) mbar_wait_bounded(&mbar[buf], parity);   // phase already complete: returns at once
         const T* __restrict__ U = stage(buf, 0);
-        const T* __restrict__ G = stage(buf, 1);
+        const T* __restrict__ G2 = stage(buf, 1);
         const uint32_t kb = stage_mask(buf)[tt];
         const uint32_t ob = stage_mask(buf)[NT + tt];
+        const float pr = Fp->p_robin;
 
         // ---- local operator coefficients -----------------------------------------
         float2 rpn[PY];     // -(vertical part of dd), both halves equal
@@ -528,8 +607,8 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
                 for (int j = 0; j < NP; ++j) {
                     const float2 uc = make_float2(uu[i + 1][2 * j + 1], uu[i + 1][2 * j + 2]);
                     const float2 nuc = make_float2(-uc.x, -uc.y);
-                    float2 acc2 = a.has_g ? make_float2(to_f(G[o0 + i * BX + 2 * j]), to_f(G[o0 + i * BX + 2 * j + 1]))
-                                          : make_float2(0.f, 0.f);
+                    float2 acc2 = make_float2(0.f, 0.f);
+                    if constexpr (HASG) acc2 = make_float2(to_f(G2[o0 + i * BX + 2 * j]), to_f(G2[o0 + i * BX + 2 * j + 1]));
                     acc2 = fma2(mN[i], add2(make_float2(uu[i][2 * j + 1], uu[i][2 * j + 2]), nuc), acc2);
                     acc2 = fma2(mS[i], add2(make_float2(uu[i + 2][2 * j + 1], uu[i + 2][2 * j + 2]), nuc), acc2);
                     acc2 = fma2(mW[j], add2(make_float2(uu[i + 1][2 * j], uu[i + 1][2 * j + 1]), nuc), acc2);
@@ -571,15 +650,16 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             const float2 both = tile_sum2<CF>(make_float2(s2, rr0), red[0], red[1], wt, lane);
             s2 = both.x;
             rr = both.y;
-            rr_stop = a.local_rtol2 * rr;
+            rr_stop = Fp->local_rtol2 * rr;
         }
         // the owned residual sum of this tile into the lane-batched accumulators
         if (c != cur_c) {
-            flush(c);
+            flush_channel();
             cur_c = c;
-            eu = fix_unit(a.stop.ref[c]);
+            eu = fix_unit(Fp->ref[c]);
         }
-        if (!isfinite(s2)) acc_bad = true;
+        ++f_tiles;
+        acc_bad |= isfinite(s2) ? 0 : 1;
         if (lane == (it & 31)) pend = s2;
         if ((it & 31) == 31) {
             fix_add(acc, pend, eu);
@@ -608,6 +688,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         // because (r, Ap) = (p, Ap) for A-conjugate directions. Exact CG in exact
         // arithmetic; the next step measures (r', r') again, so the recurrence
         // error does not accumulate.
+        const int kcg = f_kcg;
         float rr_j = rr;   // (r, r) of the current step: measured at step 0, then by the recurrence
         int kk = 0;
         for (; kk < kcg; ++kk) {
@@ -726,7 +807,7 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
             }
         }
 
-        if (a.stop.work != nullptr && !probe) {   // work actually done (the local stop shortens it)
+        if (Fp->work != nullptr && !f_probe) {   // work actually done (the local stop shortens it)
             constexpr int LB = PX * PY;
             const uint32_t un = (uint32_t)LB - (uint32_t)__popc(kb & (LB == 32 ? 0xffffffffu : ((1u << LB) - 1u)));
             work_us += un * (uint32_t)kk;
@@ -734,8 +815,9 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         }
 
         // ---- restricted add-back on the owned core -------------------------------
-        T* __restrict__ uout = u_out + (size_t)c * a.plane;
-        if (!probe) {
+        if (!f_probe) {
+            T* __restrict__ uout = static_cast<T*>(Fp->u_buf[f_cur ^ 1]) + (size_t)c * Fp->plane;
+            const int P = Fp->pitch;
 #pragma unroll
             for (int i = 0; i < PY; ++i) {
                 const int o = (1 + ry0 + i) * BX + cx + rx0;
@@ -764,93 +846,44 @@ oras_sweep_kernel(const __grid_constant__ CUtensorMap map_u0, const __grid_const
         else __syncwarp();
         t = s_next[buf];
     }
-    if (a.stop.work != nullptr) {
-        const uint32_t ws = __reduce_add_sync(FULL, work_us), wu = __reduce_add_sync(FULL, work_u);
-        if (lane == 0) {
-            atomicAdd(a.stop.work, (unsigned long long)ws);
-            atomicAdd(a.stop.work + 1, (unsigned long long)wu);
-        }
-    }
-    if (tt == 0 && !s_ok) {
+    if (tt == 0 && t < total && !s_ok) {
         // a wait gave up: before leaving, wait (bounded) for this CTA's copies
         // still in flight, the one waited for and the next tile's, if issued
         const int b = it & 1;
         mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1));
         if (s_next[b] < total) mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
     }
+    if (q_pr >= 0) flush_frame();
 
-    // ---- per-channel residual norms of u^n and the stop test (last CTA) -----------
-    flush(a.C);
-
-    __threadfence();
+    // ---- the launch's completion ticket: the last CTA resets the tile counter;
+    // a frame whose sweep was abandoned (a wait gave up, so its tiles never all
+    // completed; in a batched launch any wait abandons every frame's sweep,
+    // since the CTA that gave up leaves tiles of other frames undone) gets its
+    // error word set, its sequence ended and its sums cleared
     __syncthreads();
     __shared__ int s_last;
-    if (tt == 0) s_last = atomicAdd(flag + 3, 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (s_last && wt == 0) {
+    if (tt == 0) {
         __threadfence();
-        const SweepStop& sp = a.stop;
-        const int sweep_index = __ldcg(sp.state + 3);   // launches before this one
-        const double tol = __ldcg(sp.tol);
-        double worst = 0.0, best_ratio = 1e300;
-        int bad = 0;
-        for (int c = 0; c < a.C; ++c) {
-            Fix128 f{0ull, 0ull};
-            int nf = 0;
-            for (int i = lane; i < (int)gridDim.x; i += 32) {
-                const unsigned long long lo = __ldcg(part + 2 * ((size_t)c * slots + i));
-                const unsigned long long hi = __ldcg(part + 2 * ((size_t)c * slots + i) + 1);
-                if (hi == kFixBad) nf = 1;
-                else fix_add(f, lo, hi);
-            }
-#pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) {
-                const unsigned long long lo = __shfl_xor_sync(FULL, f.lo, m), hi = __shfl_xor_sync(FULL, f.hi, m);
-                fix_add(f, lo, hi);
-            }
-            nf = __any_sync(FULL, nf);
-            const int ec = fix_unit(sp.ref[c]);
-            const double v = ldexp((double)f.hi, 64 + ec) + ldexp((double)f.lo, ec);
-            if (lane == 0) {
-                if (nf || !isfinite(v)) bad = 1;
-                const double den = sp.ref[c] > 0.0 ? sp.ref[c] : 1.0;
-                worst = fmax(worst, sqrt(v) / den);
-                if (sweep_index > 0) {
-                    const double prev = sp.norms2[a.C + c];
-                    best_ratio = fmin(best_ratio, prev > 0.0 ? sqrt(v / prev) : 0.0);
-                }
-                sp.norms2[c] = v;
-                if (!probe) sp.norms2[a.C + c] = v;
+        s_last = atomicAdd(ticket, 1) == G - 1;
+    }
+    __syncthreads();
+    if (s_last && tt == 0) {
+        __threadfence();
+        const bool launch_failed = BATCH && __ldcg(lctl + 2) != 0;
+        for (int q = 0; q < n_act; ++q) {
+            const SweepFrame* const F = frame_at(q);
+            if ((launch_failed || __ldcg(F->err) != 0) && __ldcg(F->flag) == 0) {
+                F->err[0] = 1;
+                F->flag[0] = 5;
+                F->flag[1] = __ldcg(F->state + 3);
+                F->flag[2] = 0;
+                F->flag[6] = 0;
+                for (int c = 0; c < 2 * F->C; ++c) F->acc[c] = 0ull;
             }
         }
-        if (lane == 0) {
-            int* const state = sp.state;
-            if (sp.work != nullptr && sweep_index < kTimedLaunches) sp.work[2 + sweep_index] = probe ? 0ull : 1ull;
-            if (__ldcg(sp.err) != 0) { flag[0] = 5; flag[1] = sweep_index; }
-            else if (bad) { flag[0] = 2; flag[1] = sweep_index; }
-            else if (worst <= tol) { flag[0] = 1; flag[1] = sweep_index; }
-            else if (sp.stall > 0.0 && sweep_index > 0 && best_ratio > sp.stall) {
-                flag[0] = 3;
-                flag[1] = sweep_index;
-            } else if (!probe) {
-                // the output of this sweep becomes the current iterate; probe it
-                // next if the residual ratio of this level's last two full sweeps
-                // (before its second full sweep: an assumed contraction of
-                // kFirstContraction) predicts that it meets tol
-                const double prev_worst = sp.norms2[2 * a.C];
-                const bool history = state[1] > 0 && prev_worst > 0.0;
-                const double pred = history ? worst * (worst / prev_worst) : worst * kFirstContraction;
-                state[0] = cur ^ 1;
-                state[1] += 1;
-                state[2] = (tol > 0.0 && pred <= tol) ? 1 : 0;
-            } else {
-                state[2] = 0;   // the probe failed: sweep the same iterate in full
-            }
-            if (!probe) sp.norms2[2 * a.C] = worst;
-            state[3] = sweep_index + 1;
-            flag[3] = 0;   // ticket and tile counter ready for the next launch
-            flag[4] = 0;
-        }
+        *ticket = 0;
+        *counter = 0;
+        if (BATCH) lctl[2] = 0;
     }
 }
 
@@ -902,24 +935,21 @@ size_t sweep_smem_bytes(bool has_g) {
     return (size_t)Box<CF, T>::STRIDE * 2 * (has_g ? 2 : 1) + 2 * mask_bytes<CF>() + 128;
 }
 
-template <class CF, typename T, bool ALN>
-int persistent_grid(bool has_g) {
-    // CTAs per SM from the occupancy calculator, cached per instantiation and shape
-    // (0 on a failed query: the caller reports the error).  The kernel's
-    // dynamic shared-memory limit is one attribute for both variants, so it is
-    // always set to the larger (with g): setting it to the smaller variant's
-    // size would make later launches of the larger one fail.
-    static int cached[2] = {0, 0};
-    int& slot = cached[has_g ? 1 : 0];
+template <class CF, typename T, bool ALN, bool BATCH, bool HASG>
+int persistent_grid() {
+    // CTAs per SM from the occupancy calculator, cached per instantiation (0 on
+    // a failed query: the caller reports the error); also sets the kernel's
+    // dynamic shared-memory limit.
+    static int slot = 0;
     if (slot == 0) {
         int dev = 0, sms = 0, per = 0;
-        const size_t smem = sweep_smem_bytes<CF, T>(has_g);
+        const size_t smem = sweep_smem_bytes<CF, T>(HASG);
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaFuncSetAttribute(oras_sweep_kernel<CF, T, ALN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sweep_smem_bytes<CF, T>(true)) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oras_sweep_kernel<CF, T, ALN>, CF::NT, smem) !=
-                cudaSuccess)
+            cudaFuncSetAttribute(oras_sweep_kernel<CF, T, ALN, BATCH, HASG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oras_sweep_kernel<CF, T, ALN, BATCH, HASG>, CF::NT,
+                                                          smem) != cudaSuccess)
             return 0;
         slot = (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
     }
@@ -937,54 +967,41 @@ bool use_aligned(const TileGeom& g) {
     return has_aligned_variant<CF, T>() && g.s % 4 == 0;
 }
 
-template <class CF, typename T, bool ALN>
-cudaError_t sweep_launch(const SweepArgs<T>& a, const SweepPair& pr2, const CUtensorMap* mg, int slots,
-                         cudaStream_t st) {
-    const long long work = a.total;
-    const int resident = persistent_grid<CF, T, ALN>(a.has_g);
+template <class CF, typename T, bool ALN, bool HASG>
+cudaError_t sweep_launch(const SweepFrame& f, cudaStream_t st) {
+    const long long work = (long long)f.ntiles * f.C;
+    const int resident = persistent_grid<CF, T, ALN, false, HASG>();
     if (resident == 0) return cudaGetLastError();
-    const long long grid = std::min<long long>(std::min<long long>(work, resident), (long long)slots);
-    const size_t smem = sweep_smem_bytes<CF, T>(a.has_g);
-    // the last kDynamicRounds tiles per CTA (on average) are claimed dynamically
-    SweepArgs<T> b = a;
-    b.static_end = (int)std::max<long long>(grid, work - kDynamicRounds * grid);
-    oras_sweep_kernel<CF, T, ALN><<<(unsigned)grid, CF::NT, smem, st>>>(*pr2.map[0], *pr2.map[1],
-                                                                         mg ? *mg : *pr2.map[0], b);
+    const long long grid = std::min<long long>(work, resident);
+    const size_t smem = sweep_smem_bytes<CF, T>(HASG);
+    oras_sweep_kernel<CF, T, ALN, false, HASG><<<(unsigned)grid, CF::NT, smem, st>>>(f, nullptr, nullptr, nullptr);
     return cudaGetLastError();
 }
 
-template <class CF, typename T>
-cudaError_t sweep_cfg(const TileGeom& g, int C, long long plane, const SweepPair& pr2, const CUtensorMap* mg,
-                      const uint32_t* tmask, const SweepStop& stop, float p_robin, int k, float local_rtol2,
-                      cudaStream_t st) {
-    if ((long long)g.ntiles * C >= (1LL << 31)) return cudaErrorInvalidValue;
-    SweepArgs<T> a;
-    a.u_buf[0] = static_cast<T*>(pr2.u[0]);
-    a.u_buf[1] = static_cast<T*>(pr2.u[1]);
-    a.tmask = tmask;
-    a.stop = stop;
-    a.H = g.H; a.W = g.W; a.pitch = g.pitch; a.C = C;
-    a.s = g.s; a.ntx = g.ntx; a.ntiles = g.ntiles;
-    a.total = g.ntiles * C;
-    a.dv_tiles = make_fastdiv((uint32_t)g.ntiles);
-    a.dv_ntx = make_fastdiv((uint32_t)g.ntx);
-    a.has_g = mg != nullptr;
-    a.plane = plane;
-    a.p_robin = p_robin;
-    a.k = k;
-    a.local_rtol2 = local_rtol2;
+template <class CF, typename T, bool HASG>
+cudaError_t sweep_cfg_g(const SweepFrame& f, const TileGeom& g, cudaStream_t st) {
     if constexpr (has_aligned_variant<CF, T>()) {
-        if (use_aligned<CF, T>(g)) return sweep_launch<CF, T, true>(a, pr2, mg, stop.slots, st);
+        if (use_aligned<CF, T>(g)) return sweep_launch<CF, T, true, HASG>(f, st);
     }
-    return sweep_launch<CF, T, false>(a, pr2, mg, stop.slots, st);
+    return sweep_launch<CF, T, false, HASG>(f, st);
+}
+
+template <class CF, typename T>
+cudaError_t sweep_cfg(const SweepFrame& f, const TileGeom& g, cudaStream_t st) {
+    return f.has_g ? sweep_cfg_g<CF, T, true>(f, g, st) : sweep_cfg_g<CF, T, false>(f, g, st);
+}
+
+template <class CF, typename T, bool HASG>
+int prepare_grid_g(const TileGeom& g) {
+    if constexpr (has_aligned_variant<CF, T>()) {
+        if (use_aligned<CF, T>(g)) return persistent_grid<CF, T, true, false, HASG>();
+    }
+    return persistent_grid<CF, T, false, false, HASG>();
 }
 
 template <class CF, typename T>
 int prepare_grid(const TileGeom& g, bool has_g) {
-    if constexpr (has_aligned_variant<CF, T>()) {
-        if (use_aligned<CF, T>(g)) return persistent_grid<CF, T, true>(has_g);
-    }
-    return persistent_grid<CF, T, false>(has_g);
+    return has_g ? prepare_grid_g<CF, T, true>(g) : prepare_grid_g<CF, T, false>(g);
 }
 
 template <class CF>
@@ -999,18 +1016,85 @@ cudaError_t prepare_store(Store s, const TileGeom& g, bool has_g) {
 }
 
 template <class CF>
-cudaError_t sweep_store(Store s, const TileGeom& g, int C, long long plane, const SweepPair& pr2,
-                        const CUtensorMap* mg, const uint32_t* tmask, const SweepStop& stop, float p_robin, int k,
-                        float r2, cudaStream_t st) {
+cudaError_t sweep_store(Store s, const SweepFrame& f, const TileGeom& g, cudaStream_t st) {
     switch (s) {
-        case Store::F32:
-            return sweep_cfg<CF, float>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, r2, st);
-        case Store::F16:
-            return sweep_cfg<CF, __half>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, r2, st);
-        case Store::BF16:
-            return sweep_cfg<CF, __nv_bfloat16>(g, C, plane, pr2, mg, tmask, stop, p_robin, k, r2, st);
+        case Store::F32: return sweep_cfg<CF, float>(f, g, st);
+        case Store::F16: return sweep_cfg<CF, __half>(f, g, st);
+        case Store::BF16: return sweep_cfg<CF, __nv_bfloat16>(f, g, st);
     }
     return cudaErrorInvalidValue;
+}
+
+// batched launches: FP32 storage, no source term, the resident grid
+template <class CF>
+int batch_grid(const TileGeom& g) {
+    if constexpr (has_aligned_variant<CF, float>()) {
+        if (use_aligned<CF, float>(g)) return persistent_grid<CF, float, true, true, false>();
+    }
+    return persistent_grid<CF, float, false, true, false>();
+}
+
+template <class CF>
+cudaError_t sweep_batch_cfg(const TileGeom& g, const SweepFrame* frames, const int* list, int* bctl,
+                            cudaStream_t st) {
+    const int grid = batch_grid<CF>(g);
+    if (grid == 0) return cudaGetLastError();
+    const size_t smem = sweep_smem_bytes<CF, float>(false);
+    SweepFrame none{};
+    if constexpr (has_aligned_variant<CF, float>()) {
+        if (use_aligned<CF, float>(g)) {
+            oras_sweep_kernel<CF, float, true, true, false><<<(unsigned)grid, CF::NT, smem, st>>>(none, frames, list,
+                                                                                               bctl);
+            return cudaGetLastError();
+        }
+    }
+    oras_sweep_kernel<CF, float, false, true, false><<<(unsigned)grid, CF::NT, smem, st>>>(none, frames, list, bctl);
+    return cudaGetLastError();
+}
+
+// ---- batched levels: list building, resets and result records (one thread per frame or one thread) ----
+__global__ void batch_ctl_kernel(const SweepFrame* __restrict__ fr, int n, int* __restrict__ list,
+                                 int* __restrict__ ctl, int max_passes, cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0) return;
+    const int passes = ctl[0] + 1;
+    ctl[0] = passes;
+    int m = 0, tiles = 0;
+    if (passes <= max_passes)
+        for (int f = 0; f < n; ++f) {
+            const SweepFrame& F = fr[f];
+            if (F.flag[0] != 0 || F.state[1] >= F.cap) continue;
+            list[1 + m] = f;
+            ++m;
+        }
+    list[0] = m;
+    for (int q = 0; q < m; ++q) {
+        const SweepFrame& F = fr[list[1 + q]];
+        list[1 + m + q] = tiles;
+        tiles += F.ntiles * F.C;
+    }
+    list[1 + 2 * m] = tiles;
+    if (m == 0) cudaGraphSetConditional(cond, 0);
+}
+
+__global__ void batch_reset_kernel(const SweepFrame* __restrict__ fr, int n) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    const SweepFrame& F = fr[f];
+    for (int i = 0; i < 4; ++i) F.state[i] = 0;
+    for (int i = 0; i < 5; ++i) F.flag[i] = 0;
+    F.flag[6] = 0;
+    *const_cast<double*>(F.tol) = F.level_tol;
+}
+
+__global__ void batch_resolve_kernel(const SweepFrame* __restrict__ fr, int n, const int* __restrict__ ctl) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    const SweepFrame& F = fr[f];
+    int* const out = F.resolve_out;
+    out[0] = F.state[0];
+    out[1] = F.state[1];
+    out[2] = F.flag[0];
+    out[3] = ctl[0];
 }
 
 template <class CF>
@@ -1130,19 +1214,101 @@ cudaError_t prepare_sweep(Store s, const TileGeom& g, bool has_g) {
     return with_cfg(g.b, g.nw, [&](auto cfg) { return prepare_store<decltype(cfg)>(s, g, has_g); });
 }
 
+FastDiv make_fastdiv(uint32_t d) {
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    return FastDiv{(uint32_t)(((1ull << 32) * ((1ull << s) - d)) / d + 1), s};
+}
+
+namespace {
+
+// The descriptor of one frame's sweep: geometry, buffers and stop words.
+cudaError_t make_frame(SweepFrame* f, const TileGeom& g, int C, long long plane, const SweepPair& pair,
+                       const CUtensorMap* map_g, const uint32_t* tmask, const SweepStop& stop, float p_robin,
+                       int k, float local_rtol) {
+    if (!(local_rtol >= 0.f) || !(local_rtol < 1.f)) return cudaErrorInvalidValue;
+    if (stop.acc == nullptr || stop.flag == nullptr || stop.norms2 == nullptr || stop.ref == nullptr ||
+        stop.state == nullptr || stop.err == nullptr || stop.tol == nullptr || stop.stall_polls < 0 ||
+        pair.map[0] == nullptr || pair.map[1] == nullptr || pair.u[0] == nullptr || pair.u[1] == nullptr ||
+        tmask == nullptr || C < 1 || (long long)g.ntiles * C >= (1LL << 31))
+        return cudaErrorInvalidValue;
+    std::memset(static_cast<void*>(f), 0, sizeof(*f));
+    f->map_u[0] = *pair.map[0];
+    f->map_u[1] = *pair.map[1];
+    f->map_g = map_g ? *map_g : *pair.map[0];
+    f->u_buf[0] = pair.u[0];
+    f->u_buf[1] = pair.u[1];
+    f->tmask = tmask;
+    f->acc = stop.acc;
+    f->norms2 = stop.norms2;
+    f->ref = stop.ref;
+    f->tol = stop.tol;
+    f->flag = stop.flag;
+    f->state = stop.state;
+    f->err = stop.err;
+    f->work = stop.work;
+    f->stall = stop.stall;
+    f->plane = plane;
+    f->dv_tiles = make_fastdiv((uint32_t)g.ntiles);
+    f->dv_ntx = make_fastdiv((uint32_t)g.ntx);
+    f->H = g.H; f->W = g.W; f->pitch = g.pitch; f->C = C;
+    f->s = g.s; f->ntx = g.ntx; f->ntiles = g.ntiles;
+    f->has_g = map_g != nullptr ? 1 : 0;
+    f->p_robin = p_robin;
+    f->local_rtol2 = local_rtol * local_rtol;
+    f->k = k;
+    f->stall_polls = stop.stall_polls;
+    f->force_probe = stop.force_probe;
+    return cudaSuccess;
+}
+
+}  // namespace
+
 cudaError_t launch_sweep(Store s, const TileGeom& g, int C, long long plane, const SweepPair& pair,
                          const CUtensorMap* map_g, const uint32_t* tmask, const SweepStop& stop, float p_robin,
                          int k, cudaStream_t st, float local_rtol) {
-    if (!(local_rtol >= 0.f) || !(local_rtol < 1.f)) return cudaErrorInvalidValue;
-    if (stop.slots < 1 || stop.partial == nullptr || stop.flag == nullptr || stop.norms2 == nullptr ||
-        stop.ref == nullptr || stop.state == nullptr || stop.err == nullptr || stop.stall_polls < 0 ||
-        pair.map[0] == nullptr || pair.map[1] == nullptr ||
-        pair.u[0] == nullptr || pair.u[1] == nullptr)
-        return cudaErrorInvalidValue;
-    return with_cfg(g.b, g.nw, [&](auto cfg) {
-        return sweep_store<decltype(cfg)>(s, g, C, plane, pair, map_g, tmask, stop, p_robin, k,
-                                          local_rtol * local_rtol, st);
-    });
+    SweepFrame f;
+    const cudaError_t e = make_frame(&f, g, C, plane, pair, map_g, tmask, stop, p_robin, k, local_rtol);
+    if (e != cudaSuccess) return e;
+    return with_cfg(g.b, g.nw, [&](auto cfg) { return sweep_store<decltype(cfg)>(s, f, g, st); });
+}
+
+void fill_sweep_frame(SweepFrame* out, const TileGeom& g, int C, long long plane, const SweepPair& pair,
+                      const uint32_t* tmask, const SweepStop& stop, float p_robin, int k, float local_rtol, int cap,
+                      int* resolve_out) {
+    if (make_frame(out, g, C, plane, pair, nullptr, tmask, stop, p_robin, k, local_rtol) != cudaSuccess)
+        std::memset(static_cast<void*>(out), 0, sizeof(*out));
+    out->cap = cap;
+    out->resolve_out = resolve_out;
+}
+
+cudaError_t prepare_sweep_batch(const TileGeom& g) {
+    return with_cfg(g.b, g.nw, [&](auto cfg) { return batch_grid<decltype(cfg)>(g) > 0 ? cudaSuccess : cudaGetLastError(); });
+}
+
+cudaError_t launch_sweep_batch(const TileGeom& g, const SweepFrame* frames, const int* list, int* bctl,
+                               cudaStream_t st) {
+    if (frames == nullptr || list == nullptr || bctl == nullptr) return cudaErrorInvalidValue;
+    return with_cfg(g.b, g.nw, [&](auto cfg) { return sweep_batch_cfg<decltype(cfg)>(g, frames, list, bctl, st); });
+}
+
+cudaError_t launch_batch_ctl(const SweepFrame* frames, int n, int* list, int* ctl, int max_passes,
+                             cudaGraphConditionalHandle cond, cudaStream_t st) {
+    if (n < 0 || n > kBatchMaxFrames) return cudaErrorInvalidValue;
+    batch_ctl_kernel<<<1, 32, 0, st>>>(frames, n, list, ctl, max_passes, cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_reset(const SweepFrame* frames, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    batch_reset_kernel<<<(n + 127) / 128, 128, 0, st>>>(frames, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_resolve(const SweepFrame* frames, int n, const int* ctl, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    batch_resolve_kernel<<<(n + 127) / 128, 128, 0, st>>>(frames, n, ctl);
+    return cudaGetLastError();
 }
 
 }  // namespace dd

@@ -208,3 +208,114 @@ def test_correction_mode_async_and_batch():
     finally:
         for ip in ips:
             ip.close()
+
+
+# ---- persistent batches: one launch per sweep over the blocks of all frames ---------------
+MIXED = [(120, 170, 3, 0.05, "uniform"), (96, 64, 1, 0.08, "edge"), (257, 190, 3, 0.03, "edge"),
+         (40, 300, 2, 0.06, "uniform"), (5, 6, 1, 0.3, "uniform"), (2, 40, 3, 0.2, "uniform")]
+
+
+def _mixed(seed0):
+    return [synth.make_frame(H, W, C, d, pat, seed0 + i) for i, (H, W, C, d, pat) in enumerate(MIXED)]
+
+
+def _run_batch(ips, outs, mode):
+    rc, b, kernels = B.dd_batch_create([ip._h for ip in ips], [o.data_ptr() for o in outs], 1e-6, mode=mode)
+    B.check(rc, "dd_batch_create_mode")
+    try:
+        stream = torch.cuda.current_stream(DEV)
+        B.check(B.dd_batch_launch(b, stream), "dd_batch_launch")
+        rc, status = B.dd_batch_finish(b, len(ips), stream)
+    finally:
+        B.dd_batch_destroy(b)
+    return rc, status
+
+
+@pytest.mark.parametrize("prm", [PRM, dict(PRM, overlap=4), dict(PRM, overlap=4, coarse_factor=4, levels=2),
+                                 dict(PRM, block=64, overlap=4, levels=2)])
+def test_persistent_batch_equals_independent_solves(prm):
+    """Frames of different sizes, channel counts and level counts (the 5 x 6 and
+    2 x 40 frames have fewer levels) swept level by level in single persistent
+    launches: each result and each frame's sweep counts equal its solve alone,
+    bit for bit (the same per-block arithmetic and exact stop sums)."""
+    for seed in (1300, 1400):      # two launches of one batch, new data in the same handles
+        frames = _mixed(seed)
+        alone, stats = [], []
+        for f, m in frames:
+            with Inpainter(m, f, **prm) as ip:
+                alone.append(ip.solve(1e-6).cpu().numpy())
+                stats.append(ip.stats())
+        if seed == 1300:
+            ips = [Inpainter(m, f, **prm) for f, m in frames]
+            outs = [torch.zeros(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames]
+            rc, b, _ = B.dd_batch_create([ip._h for ip in ips], [o.data_ptr() for o in outs], 1e-6,
+                                         mode=B.DD_BATCH_PERSISTENT)
+            B.check(rc, "dd_batch_create_mode")
+        else:
+            for ip, (f, m) in zip(ips, frames):
+                md, fd = torch.as_tensor(m).to(DEV), torch.as_tensor(f).to(DEV)
+                B.check(B.dd_inpaint_set_data(ip._h, md.data_ptr(), fd.data_ptr(), 0), "set_data")
+        stream = torch.cuda.current_stream(DEV)
+        B.check(B.dd_batch_launch(b, stream), "dd_batch_launch")
+        rc, status = B.dd_batch_finish(b, len(ips), stream)
+        assert rc == B.DD_OK and all(sc == B.DD_OK for sc in status)
+        for (f, m), o, u0, st0, ip in zip(frames, outs, alone, stats, ips):
+            u = o.cpu().numpy()
+            assert np.array_equal(u, u0)
+            st = ip.stats()
+            assert st["converged"] and not st["host_continued"]
+            assert st["sweeps_per_level"] == st0["sweeps_per_level"]
+            assert np.max(np.abs(u - ref.solve_direct(f, m))) <= TOL_U
+            assert np.all(ref.rel_residual(u.astype(np.float64), f, m) <= 1e-6)
+    B.dd_batch_destroy(b)
+    for ip in ips:
+        ip.close()
+
+
+def test_persistent_batch_frame_with_nan_fails_alone():
+    frames = _mixed(1500)[:4]
+    f_bad, m_bad = frames[2]
+    f_bad = f_bad.copy()
+    ky, kx = np.argwhere(m_bad != 0)[5]
+    f_bad[0, ky, kx] = float("nan")
+    frames[2] = (f_bad, m_bad)
+    ips = [Inpainter(m, f, **PRM) for f, m in frames]
+    outs = [torch.zeros(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames]
+    try:
+        rc, status = _run_batch(ips, outs, B.DD_BATCH_PERSISTENT)
+        assert status[2] == B.DD_ENUMERIC and rc == B.DD_ENUMERIC
+        for i in (0, 1, 3):
+            f, m = frames[i]
+            assert status[i] == B.DD_OK
+            assert np.array_equal(outs[i].cpu().numpy(), _sync_solve(f, m))
+    finally:
+        for ip in ips:
+            ip.close()
+
+
+def test_persistent_batch_stalled_wait_reports_timeout_and_recovers():
+    frames = _mixed(1600)[:4]
+    ips = [Inpainter(m, f, **dict(PRM, test_stall_polls=(32 if i == 1 else 0))) for i, (f, m) in enumerate(frames)]
+    outs = [torch.zeros(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames]
+    try:
+        rc, status = _run_batch(ips, outs, B.DD_BATCH_PERSISTENT)
+        assert rc == B.DD_ETIMEOUT and status[1] == B.DD_ETIMEOUT
+        # the handles without the hook solve normally afterwards
+        for i in (0, 2, 3):
+            f, m = frames[i]
+            u = ips[i].solve(1e-6).cpu().numpy()
+            assert np.array_equal(u, _sync_solve(f, m))
+    finally:
+        for ip in ips:
+            ip.close()
+
+
+def test_persistent_batch_rejects_mixed_layouts_and_precisions():
+    f, m = synth.make_frame(64, 64, 1, 0.05, "uniform", 4)
+    with Inpainter(m, f, **PRM) as a, Inpainter(m, f, **dict(PRM, overlap=5)) as b_, \
+            Inpainter(m, f, **dict(PRM, precision="fp16_ref")) as c:
+        o = torch.empty((1, 64, 64), dtype=torch.float32, device=DEV)
+        for pair in ([a, b_], [a, c]):
+            rc, bb, _ = B.dd_batch_create([p._h for p in pair], [o.data_ptr(), o.data_ptr()], 1e-6,
+                                          mode=B.DD_BATCH_PERSISTENT)
+            assert rc == B.DD_EINVAL and not bb.value
