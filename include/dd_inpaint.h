@@ -73,7 +73,7 @@ typedef struct dd_inpaint *dd_handle;
 typedef struct dd_batch *dd_batch_handle;
 
 typedef struct dd_params {
-    int    block;            /* block side in pixels: 16, 32 or 64 (default 32, Sec. 4) */
+    int    block;            /* block side in pixels: 16, 32, 64 or 96 (default 32, Sec. 4) */
     int    overlap;          /* overlap in pixels, 0 <= overlap < block (default 6, Sec. 4) */
     int    local_cg_iters;   /* CG steps per local problem and sweep, >= 1 (default 16) */
     int    levels;           /* solved resolution levels, 1..8 (default 3, Sec. 4) */
@@ -94,7 +94,7 @@ typedef struct dd_params {
     int    coarse_sweeps;    /* sweep limit per coarse level (default 12) */
     int    timing;           /* 1: time every fine-level sweep launch with CUDA events (dd_stats) */
     int    tile_warps;       /* warps holding one block tile: 0 = default; block 16: 1;
-                                block 32: 1, 2 or 4; block 64: 4 or 8 */
+                                block 32: 1, 2 or 4; block 64: 4 or 8; block 96: 12 */
     int    solver;           /* DD_SOLVER_ORAS (default) or DD_SOLVER_CG (needs DD_PREC_FP32);
                                 with CG, max_sweeps / coarse_sweeps count CG iterations */
     int    correction_sweeps; /* DD_ML_CORRECTION: ORAS sweeps on the coarse correction equation

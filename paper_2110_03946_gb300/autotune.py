@@ -25,9 +25,9 @@ from . import binding as B
 from .inpaint import PRECISIONS, make_params
 
 SPACE = {
-    "block": [16, 32, 64],
+    "block": [16, 32, 64, 96],
     "overlap": [1, 2, 3, 4, 5, 6, 8],
-    "local_cg_iters": [8, 10, 12, 14, 16, 18, 20, 24, 28, 32],
+    "local_cg_iters": [2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 24, 28, 32],
     "local_rtol": [0.0, 0.01, 0.02, 0.03, 0.05, 0.1],   # 0.0 = always local_cg_iters steps
     "robin_p": [0.0, 0.1, 0.15, 0.2, 0.3, 0.5, 1.0],   # 0.0 = library default
     "levels": [1, 2, 3, 4, 5, 6],
@@ -50,9 +50,26 @@ def load_cache(path: str = DEFAULT_CACHE) -> dict:
         return {}
 
 
-def lookup(H, W, C, density, precision, tol, path: str = DEFAULT_CACHE):
-    """Tuned parameters for this shape/density/precision, or None."""
-    ent = load_cache(path).get(cache_key(H, W, C, density, precision, tol))
+def lookup(H, W, C, density, precision, tol, path: str = DEFAULT_CACHE, nearest: bool = True):
+    """Tuned parameters for this shape/density/precision, or None.  Without an
+    entry for the density's 1 % bucket, the entry of the same shape, precision
+    and tolerance with the nearest density (nearest=True)."""
+    cache = load_cache(path)
+    ent = cache.get(cache_key(H, W, C, density, precision, tol))
+    if ent is None and nearest:
+        prefix = f"{H}x{W}x{C}|d"
+        suffix = f"|{precision}|tol{tol:g}"
+        want = int(round(density * 100))
+        cands = []
+        for k, v in cache.items():
+            if k.startswith(prefix) and k.endswith(suffix):
+                try:
+                    d = int(k[len(prefix):-len(suffix)])
+                except ValueError:
+                    continue
+                cands.append((abs(d - want), d, v))
+        if cands:
+            ent = min(cands, key=lambda t: (t[0], t[1]))[2]
     return dict(ent["params"]) if ent else None
 
 
@@ -144,30 +161,44 @@ def _descend(trial, seen, best, space, budget_s, log):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="rgb4k_edge3")
+    ap.add_argument("--shape", default=None, help="HxWxC instead of the workload's shape")
+    ap.add_argument("--density", type=float, default=None, help="mask density instead of the workload's")
+    ap.add_argument("--pattern", default=None, choices=["uniform", "edge"])
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--budget", type=float, default=120.0, help="seconds")
-    ap.add_argument("--blocks", default="16,32,64", help="block sides to search")
+    ap.add_argument("--blocks", default="16,32,64,96", help="block sides to search")
     ap.add_argument("--start", default=None, help="JSON start point (default: the cached entry, else START)")
     ap.add_argument("--out", default=DEFAULT_CACHE)
     a = ap.parse_args()
+    import dataclasses
+
     import synth
     w = synth.WORKLOADS[a.workload]
+    if a.shape:
+        H, W, C = (int(v) for v in a.shape.lower().split("x"))
+        w = dataclasses.replace(w, name=f"{H}x{W}x{C}", H=H, W=W, C=C)
+    if a.density is not None:
+        w = dataclasses.replace(w, density=a.density)
+    if a.pattern:
+        w = dataclasses.replace(w, pattern=a.pattern)
     dev = torch.device("cuda", 0)
     frames = []
     for j in range(a.frames):
         f, m = synth.make_frame(w.H, w.W, w.C, w.density, w.pattern, w.seed_base + 50 + j)
         frames.append((torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev)))
     space = dict(SPACE, block=[int(b) for b in a.blocks.split(",")])
-    start = json.loads(a.start) if a.start else lookup(w.H, w.W, w.C, w.density, a.precision, a.tol, a.out)
+    start = json.loads(a.start) if a.start else lookup(w.H, w.W, w.C, w.density, a.precision, a.tol, a.out,
+                                                       nearest=False)
     if start:
         start = dict(START, **start)
     best, ms, seen = autotune(frames, a.precision, a.tol, a.budget, space=space, start=start,
                               log=lambda s: print(s, flush=True))
     cache = load_cache(a.out)
     cache[cache_key(w.H, w.W, w.C, w.density, a.precision, a.tol)] = {
-        "params": best, "ms_per_frame": ms, "trials": len(seen), "workload": a.workload,
+        "params": best, "ms_per_frame": ms, "trials": len(seen), "workload": w.name,
+        "pattern": w.pattern,
         "sample_seeds": [w.seed_base + 50 + j for j in range(a.frames)]}
     with open(a.out, "w") as fh:
         json.dump(cache, fh, indent=1, sort_keys=True)

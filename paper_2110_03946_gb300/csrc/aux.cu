@@ -124,7 +124,9 @@ constexpr int R_ROWS = 4, R_BROWS = V_TY * R_ROWS;
 
 dim3 grid_res(int H, int W, int C) { return dim3((W + V_COLS - 1) / V_COLS, (H + R_BROWS - 1) / R_BROWS, C); }
 
-template <typename T>
+// REF: u = u0 = C f is 0 on unknown pixels, so r_p = sum of the in-image
+// neighbours' values (those outside the image and the unknown ones are 0).
+template <typename T, bool REF>
 __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
     if (a.skip != nullptr && *a.skip != 0) return;   // uniform: no partial, no ticket
     const int c = blockIdx.z;
@@ -157,8 +159,14 @@ __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
         bool known[4];
         ldm4(a.mask + (size_t)y * a.mp, x0, W, vec.m, known);
         float r[4];
-        // all four pixels away from the image border: one branch per row group
-        if (y > 0 && y < H - 1 && x0 > 0 && x0 + 4 < W) {
+        if constexpr (REF) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float wv = j > 0 ? rw[j - 1] : left, ev = j < 3 ? rw[j + 1] : right;
+                r[j] = (x0 + j < W && !known[j]) ? (rows[k][j] + rows[k + 2][j]) + (wv + ev) : 0.f;
+            }
+        } else if (y > 0 && y < H - 1 && x0 > 0 && x0 + 4 < W) {
+            // all four pixels away from the image border: one branch per row group
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 // (N + S) + (W + E) - 4 u_p by TwoSum steps (4 u_p is exact), the
@@ -269,31 +277,55 @@ struct CopyVec {
     bool src, dst, m;
 };
 
-// dst = mask ? src : 0 (mask may be null: plain copy)
+// Sum of one unsigned value per thread over a block of V_TPB threads, added
+// to *count by thread 0 (one atomic per block).
+__device__ __forceinline__ void block_count_add(unsigned v, unsigned long long* count) {
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) v += __shfl_xor_sync(0xffffffffu, v, k);
+    __shared__ unsigned ws[V_TPB / 32];
+    const int tid = threadIdx.y * V_TX + threadIdx.x;
+    if ((tid & 31) == 0) ws[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < V_TPB / 32; ++w) t += ws[w];
+        if (t) atomicAdd(count, (unsigned long long)t);
+    }
+}
+
+// dst = mask ? src : 0 (mask may be null: plain copy); with count, the blocks
+// of channel 0 add the number of known pixels to *count.
 __global__ void __launch_bounds__(V_TPB) masked_copy_kernel(int H, int W, const float* __restrict__ src, int sp,
                                                             long long splane, const uint8_t* __restrict__ mask,
                                                             int mp, float* __restrict__ dst, int dp,
-                                                            long long dplane, CopyVec vec) {
+                                                            long long dplane, CopyVec vec,
+                                                            unsigned long long* __restrict__ count) {
     const int c = blockIdx.z;
     const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
     const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
-    if (x0 >= W) return;
     const float* __restrict__ s = src + c * splane;
     float* __restrict__ d = dst + c * dplane;
+    unsigned known = 0;
+    if (x0 < W) {
 #pragma unroll
-    for (int k = 0; k < V_ROWS; ++k) {
-        const int y = yb + k;
-        if (y >= H) break;
-        float v[4];
-        ld4(s + (size_t)y * sp, x0, W, vec.src, v);
-        if (mask != nullptr) {
-            bool m[4];
-            ldm4(mask + (size_t)y * mp, x0, W, vec.m, m);
+        for (int k = 0; k < V_ROWS; ++k) {
+            const int y = yb + k;
+            if (y >= H) break;
+            float v[4];
+            ld4(s + (size_t)y * sp, x0, W, vec.src, v);
+            if (mask != nullptr) {
+                bool m[4];
+                ldm4(mask + (size_t)y * mp, x0, W, vec.m, m);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = m[j] ? v[j] : 0.f;
+                for (int j = 0; j < 4; ++j) {
+                    v[j] = m[j] ? v[j] : 0.f;
+                    known += m[j] ? 1u : 0u;
+                }
+            }
+            st4(d + (size_t)y * dp, x0, W, vec.dst, v);
         }
-        st4(d + (size_t)y * dp, x0, W, vec.dst, v);
     }
+    if (count != nullptr && c == 0) block_count_add(known, count);   // uniform per block
 }
 
 // Bilinear cell-centred prolongation of the coarse iterate (Sec. 4) on
@@ -778,10 +810,10 @@ __global__ void loop_ctl_kernel(const int* __restrict__ flag, const int* __restr
 
 cudaError_t launch_masked_copy(int H, int W, int C, const float* src, int sp, long long splane,
                                const uint8_t* mask, int mp, float* dst, int dp, long long dplane,
-                               cudaStream_t st) {
+                               cudaStream_t st, unsigned long long* count) {
     const CopyVec v{vec_ok(src, sp, splane, 4), vec_ok(dst, dp, dplane, 4), vec_ok(mask, mp, 0, 1)};
     masked_copy_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(H, W, src, sp, splane, mask, mp, dst, dp,
-                                                                    dplane, v);
+                                                                    dplane, v, count);
     return cudaGetLastError();
 }
 
@@ -789,7 +821,7 @@ cudaError_t launch_copy2d(int H, int W, int C, const float* src, int sp, long lo
                           int dp, long long dplane, cudaStream_t st) {
     const CopyVec v{vec_ok(src, sp, splane, 4), vec_ok(dst, dp, dplane, 4), false};
     masked_copy_kernel<<<gridv(H, W, C), dim3(V_TX, V_TY), 0, st>>>(H, W, src, sp, splane, nullptr, 0, dst, dp,
-                                                                    dplane, v);
+                                                                    dplane, v, nullptr);
     return cudaGetLastError();
 }
 
@@ -819,10 +851,15 @@ cudaError_t launch_res64(const Res64Args& a, cudaStream_t st) {
     v.m = vec_ok(a.mask, a.mp, 0, 1);
     v.g = a.g_out != nullptr && a.gst == Store::F32 && vec_ok(a.g_out, a.gp, a.gplane, 4);
     const dim3 block(V_TX, V_TY);
+    if (a.u0_ref) {
+        if (a.g_out != nullptr || a.copy_out != nullptr || a.sel != nullptr) return cudaErrorInvalidValue;
+        res64_kernel<float, true><<<grid, block, 0, st>>>(a, v);
+        return cudaGetLastError();
+    }
     switch (a.gst) {
-        case Store::F32: res64_kernel<float><<<grid, block, 0, st>>>(a, v); break;
-        case Store::F16: res64_kernel<__half><<<grid, block, 0, st>>>(a, v); break;
-        case Store::BF16: res64_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(a, v); break;
+        case Store::F32: res64_kernel<float, false><<<grid, block, 0, st>>>(a, v); break;
+        case Store::F16: res64_kernel<__half, false><<<grid, block, 0, st>>>(a, v); break;
+        case Store::BF16: res64_kernel<__nv_bfloat16, false><<<grid, block, 0, st>>>(a, v); break;
     }
     return cudaGetLastError();
 }

@@ -33,7 +33,7 @@ TileGeom make_geom(int H, int W, int pitch, int b, int o, int nw = 0);
 // Kernel shape chosen for a block side and warps per tile: threads per
 // block-tile and the number of 32-bit mask words per tile (known bits +
 // owned bits per thread).  Supported: b = 16 (1 warp), 32 (1, 2 or 4 warps),
-// 64 (4 or 8 warps).
+// 64 (4 or 8 warps), 96 (12 warps).
 bool block_supported(int b);
 int default_tile_warps(int b);
 bool tile_warps_supported(int b, int nw);
@@ -42,8 +42,10 @@ size_t tmask_words(const TileGeom& g);
 
 // Per-tile, per-thread bit masks: bit set in word 0 = pixel known or outside
 // the tile, bit set in word 1 = pixel owned by the tile (restricted add-back).
+// With count, *count += the unknown in-tile pixels summed over all tiles (one
+// channel's local problem sizes).
 cudaError_t launch_build_tmask(const TileGeom& g, const uint8_t* mask, int mask_pitch,
-                               uint32_t* tmask, cudaStream_t st);
+                               uint32_t* tmask, cudaStream_t st, unsigned long long* count = nullptr);
 
 // *out += number of unknown in-tile pixels over all tiles (one channel).
 cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsigned long long* out,
@@ -251,10 +253,11 @@ cudaError_t launch_loop_ctl(const int* flag, const int* state, int* ctl, int cap
 const void* loop_begin_kernel_fn();
 
 // ---- auxiliary passes (aux.cu) ----------------------------------------------------
-// dst[c][y][x] (pitch dp) = mask ? src[c][y][x] : 0  (src pitch sp)
+// dst[c][y][x] (pitch dp) = mask ? src[c][y][x] : 0  (src pitch sp); with
+// count, *count += the number of known pixels
 cudaError_t launch_masked_copy(int H, int W, int C, const float* src, int sp, long long splane,
                                const uint8_t* mask, int mp, float* dst, int dp, long long dplane,
-                               cudaStream_t st);
+                               cudaStream_t st, unsigned long long* count = nullptr);
 // plain strided copy (float)
 cudaError_t launch_copy2d(int H, int W, int C, const float* src, int sp, long long splane,
                           float* dst, int dp, long long dplane, cudaStream_t st);
@@ -284,6 +287,11 @@ struct Res64Args {
     const float* u1; const int* sel;
     float* copy_out; int cp; long long cplane;
     const int* skip;   // optional: the pass is a no-op if *skip != 0
+    // 1: u is the initial iterate u0 = C f (known values, 0 on unknown pixels),
+    // whose residual on an unknown pixel is the plain sum of its known in-image
+    // neighbours' values (FP32, the sum of at most four values): the reference
+    // norms ||b - A u0|| without the error-free transformations
+    int u0_ref;
 };
 int res64_blocks(int H, int W);
 cudaError_t launch_res64(const Res64Args& a, cudaStream_t st);

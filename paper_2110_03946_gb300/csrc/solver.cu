@@ -274,14 +274,14 @@ Store low_store(int precision) {
 int validate(int H, int W, int C, const dd_params& p) {
     if (H <= 0 || W <= 0 || C <= 0) { set_error("H, W and C must be positive"); return DD_EINVAL; }
     if ((long long)H * W > (1LL << 31) / 4) { set_error("image too large"); return DD_EINVAL; }
-    if (!dd::block_supported(p.block)) { set_error("block must be 16, 32 or 64"); return DD_EINVAL; }
+    if (!dd::block_supported(p.block)) { set_error("block must be 16, 32, 64 or 96"); return DD_EINVAL; }
     if (p.solver != DD_SOLVER_ORAS && p.solver != DD_SOLVER_CG) { set_error("bad solver"); return DD_EINVAL; }
     if (p.solver == DD_SOLVER_CG && p.precision != DD_PREC_FP32) {
         set_error("DD_SOLVER_CG needs precision DD_PREC_FP32");
         return DD_EINVAL;
     }
     if (p.tile_warps != 0 && !dd::tile_warps_supported(p.block, p.tile_warps)) {
-        set_error("tile_warps: 16 -> 1; 32 -> 1, 2 or 4; 64 -> 4 or 8");
+        set_error("tile_warps: 16 -> 1; 32 -> 1, 2 or 4; 64 -> 4 or 8; 96 -> 12");
         return DD_EINVAL;
     }
     if (p.overlap < 0 || p.overlap >= p.block) { set_error("need 0 <= overlap < block"); return DD_EINVAL; }
@@ -341,18 +341,18 @@ int load_data(dd_inpaint* h, const uint8_t* mask, const float* values, cudaStrea
     } else {
         DD_CK(cudaMemcpyAsync(L0.mask, mask, npx, cudaMemcpyDeviceToDevice, st));
     }
+    // the pixel counts (unknown block pixels of level 0, known pixels) come with the passes
+    DD_CK(cudaMemsetAsync(h->count_d, 0, 2 * sizeof(unsigned long long), st));
     DD_LAUNCH(h, dd::launch_masked_copy(h->H, h->W, h->C, dvals, h->W, (long long)npx, L0.mask, h->W, L0.f, L0.P,
-                                        L0.plane(), st));
+                                        L0.plane(), st, h->count_d + 1));
     for (size_t l = 1; l < h->lv.size(); ++l) {
         Level& F = h->lv[l - 1];
         Level& Cc = h->lv[l];
         DD_LAUNCH(h, dd::launch_restrict(F.H, F.W, h->C, F.mask, F.W, F.f, F.P, F.plane(), Cc.mask, Cc.W, Cc.f,
                                          Cc.P, Cc.plane(), st));
     }
-    for (auto& L : h->lv) DD_LAUNCH(h, dd::launch_build_tmask(L.geom, L.mask, L.W, L.tmask, st));
-    DD_CK(cudaMemsetAsync(h->count_d, 0, 2 * sizeof(unsigned long long), st));
-    DD_LAUNCH(h, dd::launch_count_unknown(L0.geom, L0.tmask, h->count_d, st));
-    DD_LAUNCH(h, dd::launch_count_nonzero(L0.mask, (long long)npx, h->count_d + 1, st));
+    for (auto& L : h->lv)
+        DD_LAUNCH(h, dd::launch_build_tmask(L.geom, L.mask, L.W, L.tmask, st, &L == &L0 ? h->count_d : nullptr));
     // reference norms ||b - A u0||, u0 = C f, per level and channel, kept on the device
     const int nl = (int)h->lv.size();
     for (int l = 0; l < nl; ++l) {
@@ -365,6 +365,7 @@ int load_data(dd_inpaint* h, const uint8_t* mask, const float* values, cudaStrea
         a.g_out = nullptr; a.gst = Store::F32;
         a.part = h->res_part; a.nblk = nblk;
         a.out = h->res_out + (size_t)l * h->C; a.sqrt_out = L.ref_d; a.ticket = h->res_ticket;
+        a.u0_ref = 1;
         DD_LAUNCH(h, dd::launch_res64(a, st));
     }
     DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));

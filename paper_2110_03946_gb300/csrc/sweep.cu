@@ -166,6 +166,7 @@ using Cfg32w2 = Cfg<4, 4, 8, 2>;   // 32 x 32 block, two warps of 32 x 16, 16 px
 using Cfg32w4 = Cfg<4, 2, 8, 4>;   // 32 x 32 block, four warps of 32 x 8, 8 px per lane
 using Cfg64 = Cfg<4, 8, 16, 4>;    // 64 x 64 block, four warps of 64 x 16, 32 px per lane
 using Cfg64w8 = Cfg<4, 4, 16, 8>;  // 64 x 64 block, eight warps of 64 x 8, 16 px per lane
+using Cfg96 = Cfg<6, 4, 16, 12>;   // 96 x 96 block, twelve warps of 96 x 8, 24 px per lane
 
 // Calls f(Cfg{}) for the tile layout of block side b with nw warps per block.
 template <class F>
@@ -174,6 +175,7 @@ cudaError_t with_cfg(int b, int nw, F&& f) {
         case 16: return nw == 1 ? f(Cfg16{}) : cudaErrorInvalidValue;
         case 32: return nw == 1 ? f(Cfg32{}) : nw == 2 ? f(Cfg32w2{}) : nw == 4 ? f(Cfg32w4{}) : cudaErrorInvalidValue;
         case 64: return nw == 4 ? f(Cfg64{}) : nw == 8 ? f(Cfg64w8{}) : cudaErrorInvalidValue;
+        case 96: return nw == 12 ? f(Cfg96{}) : cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
 }
@@ -887,31 +889,49 @@ oras_sweep_kernel(const __grid_constant__ SweepFrame one, const SweepFrame* __re
     }
 }
 
+constexpr int kTmaskTPB = 256;
+
 template <class CF>
-__global__ void build_tmask_kernel(const uint8_t* __restrict__ mask, int mp, uint32_t* __restrict__ tmask,
-                                   int H, int W, int s, int half_o, int ntx, int nty, int ntiles) {
+__global__ void __launch_bounds__(kTmaskTPB)
+build_tmask_kernel(const uint8_t* __restrict__ mask, int mp, uint32_t* __restrict__ tmask, int H, int W, int s,
+                   int half_o, int ntx, int nty, int ntiles, unsigned long long* __restrict__ count) {
     constexpr int PX = CF::PX, PY = CF::PY, LX = CF::LX, LY = CF::LY, NT = CF::NT;
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (long long)ntiles * NT) return;
-    const int tile = (int)(gid / NT), tt = (int)(gid - (long long)tile * NT);
-    const int wt = tt >> 5, lane = tt & 31, lx = lane % LX, ly = lane / LX;
-    const int ty = tile / ntx, tx = tile - ty * ntx;
-    const int y0 = ty * s, x0 = tx * s;
-    const int th = min(CF::BH, H - y0), tw = min(CF::BW, W - x0);
-    const int oy0 = ty == 0 ? 0 : y0 + half_o, oy1 = ty == nty - 1 ? H : y0 + s + half_o;
-    const int ox0 = tx == 0 ? 0 : x0 + half_o, ox1 = tx == ntx - 1 ? W : x0 + s + half_o;
-    const int ry0 = (wt * LY + ly) * PY, rx0 = lx * PX;
-    uint32_t kb = 0, ob = 0;
-    for (int i = 0; i < PY; ++i)
-        for (int j = 0; j < PX; ++j) {
-            const int bit = i * PX + j;
-            const int y = y0 + ry0 + i, x = x0 + rx0 + j;
-            const bool in = (ry0 + i < th) && (rx0 + j < tw);
-            if (!in || mask[(size_t)y * mp + x] != 0) kb |= 1u << bit;
-            if (in && y >= oy0 && y < oy1 && x >= ox0 && x < ox1) ob |= 1u << bit;
+    unsigned unknown = 0;
+    if (gid < (long long)ntiles * NT) {
+        const int tile = (int)(gid / NT), tt = (int)(gid - (long long)tile * NT);
+        const int wt = tt >> 5, lane = tt & 31, lx = lane % LX, ly = lane / LX;
+        const int ty = tile / ntx, tx = tile - ty * ntx;
+        const int y0 = ty * s, x0 = tx * s;
+        const int th = min(CF::BH, H - y0), tw = min(CF::BW, W - x0);
+        const int oy0 = ty == 0 ? 0 : y0 + half_o, oy1 = ty == nty - 1 ? H : y0 + s + half_o;
+        const int ox0 = tx == 0 ? 0 : x0 + half_o, ox1 = tx == ntx - 1 ? W : x0 + s + half_o;
+        const int ry0 = (wt * LY + ly) * PY, rx0 = lx * PX;
+        uint32_t kb = 0, ob = 0;
+        for (int i = 0; i < PY; ++i)
+            for (int j = 0; j < PX; ++j) {
+                const int bit = i * PX + j;
+                const int y = y0 + ry0 + i, x = x0 + rx0 + j;
+                const bool in = (ry0 + i < th) && (rx0 + j < tw);
+                if (!in || mask[(size_t)y * mp + x] != 0) kb |= 1u << bit;
+                if (in && y >= oy0 && y < oy1 && x >= ox0 && x < ox1) ob |= 1u << bit;
+            }
+        tmask[(size_t)tile * 2 * NT + tt] = kb;
+        tmask[(size_t)tile * 2 * NT + NT + tt] = ob;
+        constexpr int LB = PX * PY;
+        unknown = (unsigned)LB - (unsigned)__popc(kb & (LB == 32 ? 0xffffffffu : ((1u << LB) - 1u)));
+    }
+    if (count != nullptr) {   // unknown in-tile pixels, one atomic per block (uniform per launch)
+        for (int m = 16; m >= 1; m >>= 1) unknown += __shfl_xor_sync(FULL, unknown, m);
+        __shared__ unsigned ws[kTmaskTPB / 32];
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = unknown;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned t = 0;
+            for (int w = 0; w < kTmaskTPB / 32; ++w) t += ws[w];
+            if (t) atomicAdd(count, (unsigned long long)t);
         }
-    tmask[(size_t)tile * 2 * NT + tt] = kb;
-    tmask[(size_t)tile * 2 * NT + NT + tt] = ob;
+    }
 }
 
 // Unknown in-block pixels summed over all blocks: each thread word has PX*PY
@@ -1098,11 +1118,11 @@ __global__ void batch_resolve_kernel(const SweepFrame* __restrict__ fr, int n, c
 }
 
 template <class CF>
-cudaError_t tmask_cfg(const TileGeom& g, const uint8_t* mask, int mp, uint32_t* tmask, cudaStream_t st) {
+cudaError_t tmask_cfg(const TileGeom& g, const uint8_t* mask, int mp, uint32_t* tmask, cudaStream_t st,
+                      unsigned long long* count) {
     const long long n = (long long)g.ntiles * CF::NT;
-    const int tpb = 256;
-    build_tmask_kernel<CF><<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
-        mask, mp, tmask, g.H, g.W, g.s, g.half_o, g.ntx, g.nty, g.ntiles);
+    build_tmask_kernel<CF><<<(unsigned)((n + kTmaskTPB - 1) / kTmaskTPB), kTmaskTPB, 0, st>>>(
+        mask, mp, tmask, g.H, g.W, g.s, g.half_o, g.ntx, g.nty, g.ntiles, count);
     return cudaGetLastError();
 }
 
@@ -1153,9 +1173,9 @@ TileGeom make_geom(int H, int W, int pitch, int b, int o, int nw) {
     return g;
 }
 
-bool block_supported(int b) { return b == 16 || b == 32 || b == 64; }
+bool block_supported(int b) { return b == 16 || b == 32 || b == 64 || b == 96; }
 
-int default_tile_warps(int b) { return b == 64 ? 4 : 1; }
+int default_tile_warps(int b) { return b == 96 ? 12 : b == 64 ? 4 : 1; }
 
 bool tile_warps_supported(int b, int nw) {
     return with_cfg(b, nw, [](auto) { return cudaSuccess; }) == cudaSuccess;
@@ -1201,8 +1221,8 @@ cudaError_t make_tile_map(CUtensorMap* out, Store s, const void* base, int H, in
 }
 
 cudaError_t launch_build_tmask(const TileGeom& g, const uint8_t* mask, int mp, uint32_t* tmask,
-                               cudaStream_t st) {
-    return with_cfg(g.b, g.nw, [&](auto cfg) { return tmask_cfg<decltype(cfg)>(g, mask, mp, tmask, st); });
+                               cudaStream_t st, unsigned long long* count) {
+    return with_cfg(g.b, g.nw, [&](auto cfg) { return tmask_cfg<decltype(cfg)>(g, mask, mp, tmask, st, count); });
 }
 
 cudaError_t launch_count_unknown(const TileGeom& g, const uint32_t* tmask, unsigned long long* out,

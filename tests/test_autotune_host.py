@@ -75,3 +75,18 @@ def test_committed_cache_has_the_bench_entries():
         prm = autotune.lookup(2160, 3840, 3, 0.03, precision, 1e-6)
         assert prm is not None and prm["overlap"] < prm["block"]
         assert set(prm) <= set(autotune.SPACE)
+
+
+def test_lookup_falls_back_to_the_nearest_density(tmp_path):
+    path = tmp_path / "tuned.json"
+    cache = {autotune.cache_key(720, 1280, 3, 0.02, "fp32", 1e-6): {"params": {"overlap": 2}},
+             autotune.cache_key(720, 1280, 3, 0.08, "fp32", 1e-6): {"params": {"overlap": 8}},
+             autotune.cache_key(720, 1280, 3, 0.05, "fp16_ref", 1e-6): {"params": {"overlap": 5}}}
+    path.write_text(json.dumps(cache))
+    look = lambda d, **kw: autotune.lookup(720, 1280, 3, d, "fp32", 1e-6, str(path), **kw)
+    assert look(0.02) == {"overlap": 2}                 # exact bucket
+    assert look(0.03) == {"overlap": 2}                 # nearest density
+    assert look(0.07) == {"overlap": 8}
+    assert look(0.05) == {"overlap": 2}                 # a tie goes to the lower density
+    assert look(0.03, nearest=False) is None
+    assert autotune.lookup(1080, 1920, 3, 0.03, "fp32", 1e-6, str(path)) is None   # other shape

@@ -115,8 +115,11 @@ def test_batch_of_48_mixed_frames_one_graph():
     """The bench's batch: 48 frames of 512x512, 1280x720, 1920x1080 and
     3840x2160 RGB (mask density U[1 %, 10 %], uniform and edge-clustered in
     turn, the same seeds) solved by one CUDA-graph launch with the 4K FP32
-    parameters.  Every frame converges and meets the properties; the 512x512
-    frames are also compared with the oracle's direct solution."""
+    parameters, first as a graph of per-frame solves, then with one persistent
+    launch per sweep over the blocks of all frames (DD_BATCH_PERSISTENT), which
+    gives the same images bit for bit.  Every frame converges and meets the
+    properties; the 512x512 frames are also compared with the oracle's direct
+    solution."""
     rng = np.random.default_rng(4000)
     sizes = [(512, 512), (720, 1280), (1080, 1920), (2160, 3840)]
     frames = []
@@ -127,22 +130,29 @@ def test_batch_of_48_mixed_frames_one_graph():
     prm = _params("rgb4k_edge3", "fp32")
     ips = [Inpainter(m, f, device=DEV, **prm) for f, m in frames]
     outs = [torch.empty(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames]
+    results = {}
     try:
-        rc, b, _ = B.dd_batch_create([ip._h for ip in ips], [o.data_ptr() for o in outs], TOL)
-        B.check(rc, "dd_batch_create")
-        try:
-            stream = torch.cuda.current_stream(DEV)
-            B.check(B.dd_batch_launch(b, stream), "dd_batch_launch")
-            rc, status = B.dd_batch_finish(b, len(ips), stream)
-            assert rc == B.DD_OK and all(sc == B.DD_OK for sc in status)
-        finally:
-            B.dd_batch_destroy(b)
-        for ip in ips:
-            assert ip.stats()["converged"]
-        us = [o.cpu().numpy() for o in outs]
+        for mode in (B.DD_BATCH_GRAPH, B.DD_BATCH_PERSISTENT):
+            for o in outs:
+                o.zero_()
+            rc, b, _ = B.dd_batch_create([ip._h for ip in ips], [o.data_ptr() for o in outs], TOL, mode=mode)
+            B.check(rc, "dd_batch_create_mode")
+            try:
+                stream = torch.cuda.current_stream(DEV)
+                B.check(B.dd_batch_launch(b, stream), "dd_batch_launch")
+                rc, status = B.dd_batch_finish(b, len(ips), stream)
+                assert rc == B.DD_OK and all(sc == B.DD_OK for sc in status)
+            finally:
+                B.dd_batch_destroy(b)
+            for ip in ips:
+                assert ip.stats()["converged"]
+            results[mode] = [o.cpu().numpy() for o in outs]
     finally:
         for ip in ips:
             ip.close()
+    us = results[B.DD_BATCH_PERSISTENT]
+    for a, b_ in zip(results[B.DD_BATCH_GRAPH], us):
+        assert np.array_equal(a, b_)
     small = 0
     for u, (f, m) in zip(us, frames):
         _check_properties(u, f, m)
