@@ -290,12 +290,23 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------- extras
+def shape_params(H, W, C, density, precision, fallback):
+    """The autotuner's parameters for a frame shape (nearest tuned density),
+    else the fallback."""
+    from paper_2110_03946_gb300 import autotune
+    t = autotune.lookup(H, W, C, density, precision, TOL)
+    return dict(t) if t else dict(fallback)
+
+
 def run_batch48(dev, params, precision="fp32"):
     """48 frames of mixed sizes (512x512, 1280x720, 1920x1080, 3840x2160 RGB;
     mask density U[1%, 10%], half uniform, half edge-clustered) solved to 1e-6
     as one CUDA-graph launch (dd_batch_*), against the same frames solved one
-    after another.  precision "fp16_ref": FP16 inner storage with the outer
-    FP64-accurate correction, whose loop runs inside the graph."""
+    after another, each frame with the autotuner's parameters for its shape.
+    The persistent mode (one launch per sweep over all frames' blocks) needs
+    one block layout: its leg uses the 4K parameters for every frame.
+    precision "fp16_ref": FP16 inner storage with the outer FP64-accurate
+    correction, whose loop runs inside the graph."""
     import torch
 
     import synth
@@ -303,21 +314,29 @@ def run_batch48(dev, params, precision="fp32"):
     from paper_2110_03946_gb300.inpaint import make_params
     rng = np.random.default_rng(4000)
     sizes = [(512, 512), (720, 1280), (1080, 1920), (2160, 3840)]
-    frames = []
+    frames, densities = [], []
     for j in range(48):
         H, W = sizes[rng.integers(4)]
         d = rng.uniform(0.01, 0.10)
         pat = "uniform" if j % 2 == 0 else "edge"
         f, m = synth.make_frame(H, W, 3, d, pat, 4000 + j)
         frames.append((torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev)))
-    p = make_params(precision=precision, inputs_on_device=1, **params)
-    hs, outs = [], []
-    for m, f in frames:
-        C, H, W = f.shape
-        rc, h = B.dd_inpaint_create(H, W, C, m.data_ptr(), f.data_ptr(), p)
-        B.check(rc, "create")
-        hs.append(h)
-        outs.append(torch.empty((C, H, W), dtype=torch.float32, device=dev))
+        densities.append(d)
+
+    def make_handles(per_shape):
+        hs_, outs_ = [], []
+        for (m, f), d in zip(frames, densities):
+            C, H, W = f.shape
+            prm_ = shape_params(H, W, C, d, precision, params) if per_shape else params
+            rc, h = B.dd_inpaint_create(H, W, C, m.data_ptr(), f.data_ptr(),
+                                        make_params(precision=precision, inputs_on_device=1, **prm_))
+            B.check(rc, "create")
+            hs_.append(h)
+            outs_.append(torch.empty((C, H, W), dtype=torch.float32, device=dev))
+        return hs_, outs_
+
+    hs, outs = make_handles(True)
+    hs_p = []
     stream = torch.cuda.current_stream(dev)
     try:
         # one after another (synchronous solves)
@@ -329,27 +348,30 @@ def run_batch48(dev, params, precision="fp32"):
             B.check(B.dd_inpaint_solve(h, o.data_ptr(), TOL, stream), "solve")
         torch.cuda.synchronize(dev)
         seq_s = time.perf_counter() - t0
-        modes = [("graph_of_solves", B.DD_BATCH_GRAPH)]
+        modes = [("graph_of_solves", B.DD_BATCH_GRAPH, hs, outs)]
+        outs_p = []
         if precision == "fp32":
-            modes.append(("persistent_per_sweep", B.DD_BATCH_PERSISTENT))
+            hs_p, outs_p = make_handles(False)
+            modes.append(("persistent_per_sweep", B.DD_BATCH_PERSISTENT, hs_p, outs_p))
         res = {}
-        for name, mode in modes:
-            rc, b, kernels = B.dd_batch_create(hs, [o.data_ptr() for o in outs], TOL, mode=mode)
+        for name, mode, hs_m, outs_m in modes:
+            rc, b, kernels = B.dd_batch_create(hs_m, [o.data_ptr() for o in outs_m], TOL, mode=mode)
             B.check(rc, "dd_batch_create_mode")
             try:
                 reps = 3
                 B.check(B.dd_batch_launch(b, stream), "launch")
-                rc, st = B.dd_batch_finish(b, len(hs), stream)
+                rc, st = B.dd_batch_finish(b, len(hs_m), stream)
                 B.check(rc, "finish")
                 t0 = time.perf_counter()
                 for _ in range(reps):
                     B.check(B.dd_batch_launch(b, stream), "launch")
-                    rc, st = B.dd_batch_finish(b, len(hs), stream)
+                    rc, st = B.dd_batch_finish(b, len(hs_m), stream)
                     B.check(rc, "finish")
                 batch_s = (time.perf_counter() - t0) / reps
             finally:
                 B.dd_batch_destroy(b)
-            res[name] = {"frames_per_s": 48 / batch_s, "kernel_nodes_outside_loops": kernels}
+            res[name] = {"frames_per_s": 48 / batch_s, "kernel_nodes_outside_loops": kernels,
+                         "params": "per frame shape (autotuner)" if mode == B.DD_BATCH_GRAPH else "4K parameters"}
         best = max(res, key=lambda k: res[k]["frames_per_s"])
         mpx = sum(f.shape[1] * f.shape[2] for _, f in frames) / 1e6
         return {"frames": 48, "precision": precision, "megapixels_rgb": round(mpx, 1),
@@ -357,7 +379,7 @@ def run_batch48(dev, params, precision="fp32"):
                 "sequential_frames_per_s": 48 / seq_s, "speedup": seq_s * res[best]["frames_per_s"] / 48,
                 "note": "one CUDA graph launch per batch; wall clock incl. host finish"}
     finally:
-        for h in hs:
+        for h in hs + hs_p:
             B.dd_inpaint_destroy(h)
 
 
@@ -372,7 +394,8 @@ def run_serving(dev, params):
     shapes = [(2160, 3840, 3), (1080, 1920, 3), (720, 1280, 3)]
     pool = make_pool(shapes, n_frames=6, n_masks=4, density_range=(0.02, 0.08), seed=5000)
     reqs = poisson_stream(60.0, 4.0, shapes, [0.7, 0.2, 0.1], 30, 5001, pool)
-    srv = Server(CudaBackend(params, tol=TOL, device=dev), hbm_budget=40 << 30)
+    per_shape = {s_: shape_params(s_[0], s_[1], s_[2], 0.05, "fp32", params) for s_ in shapes}
+    srv = Server(CudaBackend(params, tol=TOL, device=dev, per_shape=per_shape), hbm_budget=40 << 30)
     try:
         prewarmed = srv.prewarm(reqs, per_shape=2)   # slots created before the stream starts
         # a 1 s stream of other sequences first: the measured stream then sees a
@@ -411,10 +434,12 @@ def run_studies(dev, params):
     rows = []
     for k, (H, W) in enumerate(sizes):
         f, m = synth.make_frame(H, W, 3, 0.03, "edge", 6000 + k)
+        prm_k = shape_params(H, W, 3, 0.03, "fp32", params)
         with Inpainter(torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev), device=dev, precision="fp32",
-                       **params) as ip:
+                       **prm_k) as ip:
             ms, st, _ = timed(ip)
-        rows.append({"H": H, "W": W, "ms": ms, "fine_sweeps": st["sweeps_per_level"][0]})
+        rows.append({"H": H, "W": W, "ms": ms, "fine_sweeps": st["sweeps_per_level"][0],
+                     "params": "tuned for the shape" if prm_k != params else "4K parameters"})
     px = np.log([r["H"] * r["W"] for r in rows])
     ms = np.log([r["ms"] for r in rows])
     out["scaling"] = {"rows": rows, "loglog_slope": float(np.polyfit(px, ms, 1)[0])}

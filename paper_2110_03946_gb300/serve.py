@@ -252,9 +252,12 @@ class Server:
 class CudaBackend:
     """The real solver: one dd_inpaint handle and stream per slot, inputs from
     pinned host memory (copied inside the timed request), results left on the
-    device (or copied back when host_output is set)."""
+    device (or copied back when host_output is set).  per_shape: optional
+    {(H, W, C): params} overriding params for frames of that shape (e.g. the
+    autotuner's entries)."""
 
-    def __init__(self, params: dict, tol: float = 1e-6, device="cuda", host_output: bool = True):
+    def __init__(self, params: dict, tol: float = 1e-6, device="cuda", host_output: bool = True,
+                 per_shape: dict | None = None):
         import torch
 
         from . import binding as B
@@ -262,10 +265,15 @@ class CudaBackend:
         self.torch, self.B = torch, B
         self.dev = torch.device(device)
         self.tol = tol
-        self.prm = make_params(inputs_on_device=0, precision="fp32", **params)
+        self._make_params = make_params
+        self.params = dict(params)
+        self.per_shape = dict(per_shape or {})
         self.host_output = host_output
         self._state = {}
         self._bytes_cache = {}
+
+    def params_for(self, shape) -> dict:
+        return dict(self.per_shape.get(tuple(shape), self.params))
 
     def now(self) -> float:
         return time.perf_counter()
@@ -295,7 +303,8 @@ class CudaBackend:
         C, H, W = req.values.shape
         m = _host_u8(torch, req.mask)
         v = _host_f32(torch, req.values)
-        rc, h = B.dd_inpaint_create(H, W, C, m.data_ptr(), v.data_ptr(), self.prm)
+        prm = self._make_params(inputs_on_device=0, precision="fp32", **self.params_for((H, W, C)))
+        rc, h = B.dd_inpaint_create(H, W, C, m.data_ptr(), v.data_ptr(), prm)
         B.check(rc, "dd_inpaint_create")
         rc, st = B.dd_inpaint_stats(h)
         stream = torch.cuda.Stream(self.dev)
