@@ -164,6 +164,9 @@ def main():
     ap.add_argument("--shape", default=None, help="HxWxC instead of the workload's shape")
     ap.add_argument("--density", type=float, default=None, help="mask density instead of the workload's")
     ap.add_argument("--pattern", default=None, choices=["uniform", "edge"])
+    ap.add_argument("--mix", default=None,
+                    help="sample frames of mixed masks, e.g. 0.02:edge,0.04:uniform,0.08:edge (density:pattern per "
+                         "frame; the cache key takes --density)")
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
     ap.add_argument("--tol", type=float, default=1e-6)
@@ -184,9 +187,12 @@ def main():
     if a.pattern:
         w = dataclasses.replace(w, pattern=a.pattern)
     dev = torch.device("cuda", 0)
+    masks = [(w.density, w.pattern)] * a.frames
+    if a.mix:
+        masks = [(float(d), pat) for d, pat in (item.split(":") for item in a.mix.split(","))]
     frames = []
-    for j in range(a.frames):
-        f, m = synth.make_frame(w.H, w.W, w.C, w.density, w.pattern, w.seed_base + 50 + j)
+    for j, (dens, pat) in enumerate(masks):
+        f, m = synth.make_frame(w.H, w.W, w.C, dens, pat, w.seed_base + 50 + j)
         frames.append((torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev)))
     space = dict(SPACE, block=[int(b) for b in a.blocks.split(",")])
     start = json.loads(a.start) if a.start else lookup(w.H, w.W, w.C, w.density, a.precision, a.tol, a.out,
@@ -199,7 +205,8 @@ def main():
     cache[cache_key(w.H, w.W, w.C, w.density, a.precision, a.tol)] = {
         "params": best, "ms_per_frame": ms, "trials": len(seen), "workload": w.name,
         "pattern": w.pattern,
-        "sample_seeds": [w.seed_base + 50 + j for j in range(a.frames)]}
+        "sample_seeds": [w.seed_base + 50 + j for j in range(len(masks))],
+        "sample_masks": [f"{d:g}:{pat}" for d, pat in masks]}
     with open(a.out, "w") as fh:
         json.dump(cache, fh, indent=1, sort_keys=True)
     print(json.dumps({"best": best, "ms_per_frame": ms, "trials": len(seen)}))
