@@ -124,9 +124,7 @@ constexpr int R_ROWS = 4, R_BROWS = V_TY * R_ROWS;
 
 dim3 grid_res(int H, int W, int C) { return dim3((W + V_COLS - 1) / V_COLS, (H + R_BROWS - 1) / R_BROWS, C); }
 
-// REF: u = u0 = C f is 0 on unknown pixels, so r_p = sum of the in-image
-// neighbours' values (those outside the image and the unknown ones are 0).
-template <typename T, bool REF>
+template <typename T>
 __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
     if (a.skip != nullptr && *a.skip != 0) return;   // uniform: no partial, no ticket
     const int c = blockIdx.z;
@@ -159,14 +157,8 @@ __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
         bool known[4];
         ldm4(a.mask + (size_t)y * a.mp, x0, W, vec.m, known);
         float r[4];
-        if constexpr (REF) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float wv = j > 0 ? rw[j - 1] : left, ev = j < 3 ? rw[j + 1] : right;
-                r[j] = (x0 + j < W && !known[j]) ? (rows[k][j] + rows[k + 2][j]) + (wv + ev) : 0.f;
-            }
-        } else if (y > 0 && y < H - 1 && x0 > 0 && x0 + 4 < W) {
-            // all four pixels away from the image border: one branch per row group
+        // all four pixels away from the image border: one branch per row group
+        if (y > 0 && y < H - 1 && x0 > 0 && x0 + 4 < W) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 // (N + S) + (W + E) - 4 u_p by TwoSum steps (4 u_p is exact), the
@@ -272,6 +264,96 @@ __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
     if (tid == 0) *a.ticket = 0u;
 }
 
+// Reference norms ||b - A u0||, u0 = C f, of every level in one launch: the
+// residual of u0 on an unknown pixel is the sum of its known in-image
+// neighbours' values (u0 is 0 on unknown pixels), summed in FP32 (at most four
+// values), squared and added per thread in FP32, per block in FP64.  Blocks
+// cover (level, channel, 128 x 32 pixels); the last block (atomic ticket) sums
+// each level's block partials per channel in a fixed order into out[c] =
+// {sum, 0} and sqrt_out[c].
+__global__ void __launch_bounds__(V_TPB) ref_norms_kernel(RefNormArgs a) {
+    int l = 0;
+    while (l + 1 < a.nl && (int)blockIdx.x >= a.lv[l + 1].block0) ++l;
+    const RefLevel& L = a.lv[l];
+    int rem = (int)blockIdx.x - L.block0;
+    const int per_c = L.gx * L.gy;
+    const int c = rem / per_c;
+    rem -= c * per_c;
+    const int by = rem / L.gx, bx = rem - by * L.gx;
+    const int x0 = (bx * V_TX + threadIdx.x) * 4;
+    const int yb = (by * V_TY + threadIdx.y) * R_ROWS;
+    const int H = L.H, W = L.W;
+    const float* __restrict__ u = L.f + c * L.fplane;
+    const bool xin = x0 < W;
+    float rows[R_ROWS + 2][4];
+#pragma unroll
+    for (int k = 0; k < R_ROWS + 2; ++k) {
+        const int y = yb - 1 + k;
+        if (xin && y >= 0 && y < H) {
+            ld4(u + (size_t)y * L.fp, x0, W, true, rows[k]);
+        } else {
+            rows[k][0] = rows[k][1] = rows[k][2] = rows[k][3] = 0.f;
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < R_ROWS; ++k) {
+        const int y = yb + k;
+        const float* rw = rows[k + 1];
+        float left = __shfl_up_sync(0xffffffffu, rw[3], 1);
+        float right = __shfl_down_sync(0xffffffffu, rw[0], 1);
+        if (!xin || y >= H) continue;
+        if (threadIdx.x == 0) left = x0 > 0 ? u[(size_t)y * L.fp + x0 - 1] : 0.f;
+        if (threadIdx.x == V_TX - 1) right = x0 + 4 < W ? u[(size_t)y * L.fp + x0 + 4] : 0.f;
+        bool known[4];
+        ldm4(L.mask + (size_t)y * L.mp, x0, W, L.mvec != 0, known);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float wv = j > 0 ? rw[j - 1] : left, ev = j < 3 ? rw[j + 1] : right;
+            const float r = (x0 + j < W && !known[j]) ? (rows[k][j] + rows[k + 2][j]) + (wv + ev) : 0.f;
+            s = fmaf(r, r, s);
+        }
+    }
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+    __shared__ float ss[V_TPB / 32];
+    __shared__ int s_last;
+    const int tid = threadIdx.y * V_TX + threadIdx.x;
+    if ((tid & 31) == 0) ss[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+        double ts = 0.0;
+        for (int w = 0; w < V_TPB / 32; ++w) ts += (double)ss[w];
+        a.part[L.part0 + (size_t)c * per_c + by * L.gx + bx] = ts;
+        __threadfence();
+        s_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    __shared__ double rs[V_TPB];
+    for (int q = 0; q < a.nl; ++q) {
+        const RefLevel& Q = a.lv[q];
+        const int pc = Q.gx * Q.gy;
+        for (int cc = 0; cc < a.C; ++cc) {
+            double sv = 0.0;
+            for (int i = tid; i < pc; i += V_TPB) sv += __ldcg(a.part + Q.part0 + (size_t)cc * pc + i);
+            rs[tid] = sv;
+            __syncthreads();
+            for (int hh = V_TPB / 2; hh > 0; hh >>= 1) {
+                if (tid < hh) rs[tid] += rs[tid + hh];
+                __syncthreads();
+            }
+            if (tid == 0) {
+                Q.out[cc] = make_double2(rs[0], 0.0);
+                Q.sqrt_out[cc] = sqrt(rs[0]);
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0) *a.ticket = 0u;
+}
+
 // ---- streaming passes (vectorised layout above) -----------------------------------------
 struct CopyVec {
     bool src, dst, m;
@@ -331,53 +413,60 @@ __global__ void __launch_bounds__(V_TPB) masked_copy_kernel(int H, int W, const 
 // Bilinear cell-centred prolongation of the coarse iterate (Sec. 4) on
 // unknown pixels, f on known ones (mask may be null: everywhere bilinear).
 // The coarse source is sel[0] ? uc1 : uc0 (sel may be null: uc0).
+// Fine pixel x sits at coarse coordinate (x - 1/2)/2, clamped to [0, Wc - 1].
+// A thread's 4 columns start at an even coarse column x0/2 and need coarse
+// columns x0/2 - 1 .. x0/2 + 2 with the fixed weights 1/4, 3/4 (indices
+// clamped to the grid, which equals clamping the coordinate); likewise its 4
+// rows need coarse rows yb/2 - 1 .. yb/2 + 2.  So each thread reads 4 x 4
+// coarse values for its 16 fine pixels.
 __global__ void __launch_bounds__(V_TPB) prolong_kernel(int Hc, int Wc, int H, int W, const float* __restrict__ uc0,
                                                         const float* __restrict__ uc1, const int* __restrict__ sel,
                                                         int ucp, long long ucplane, const uint8_t* __restrict__ mask,
                                                         int mp, const float* __restrict__ f, int fp, long long fplane,
                                                         float* __restrict__ u, int up, long long uplane, CopyVec vec) {
+    static_assert(V_ROWS == 4, "the weight pattern covers 4 rows per thread");
     const int c = blockIdx.z;
     const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
     const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
-    if (x0 >= W) return;
+    if (x0 >= W || yb >= H) return;
     const float* __restrict__ p = ((sel != nullptr && sel[0]) ? uc1 : uc0) + c * ucplane;
-    int xa[4], xb[4];
-    float wx[4];
+    const int cx = x0 >> 1, cy = yb >> 1;
+    int col[4], row[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float tx = fminf(fmaxf((x0 + j - 0.5f) * 0.5f, 0.f), (float)(Wc - 1));
-        xa[j] = (int)floorf(tx);
-        xb[j] = min(xa[j] + 1, Wc - 1);
-        wx[j] = tx - (float)xa[j];
+        col[j] = min(max(cx - 1 + j, 0), Wc - 1);
+        row[j] = min(max(cy - 1 + j, 0), Hc - 1);
+    }
+    // horizontal interpolation of the 4 coarse rows onto the thread's 4 columns
+    float hrow[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float* __restrict__ pr = p + (size_t)row[r] * ucp;
+        const float c0 = pr[col[0]], c1 = pr[col[1]], c2 = pr[col[2]], c3 = pr[col[3]];
+        hrow[r][0] = 0.25f * c0 + 0.75f * c1;
+        hrow[r][1] = 0.75f * c1 + 0.25f * c2;
+        hrow[r][2] = 0.25f * c1 + 0.75f * c2;
+        hrow[r][3] = 0.75f * c2 + 0.25f * c3;
     }
 #pragma unroll
     for (int k = 0; k < V_ROWS; ++k) {
         const int y = yb + k;
         if (y >= H) break;
-        const float ty = fminf(fmaxf((y - 0.5f) * 0.5f, 0.f), (float)(Hc - 1));
-        const int ya = (int)floorf(ty), yb1 = min(ya + 1, Hc - 1);
-        const float wy = ty - (float)ya;
-        const float* __restrict__ ra = p + (size_t)ya * ucp;
-        const float* __restrict__ rb = p + (size_t)yb1 * ucp;
+        // rows yb, yb+1, yb+2, yb+3 sit between coarse rows (0,1), (1,2), (1,2), (2,3) of the four
+        const int ra = k == 0 ? 0 : (k == 3 ? 2 : 1);
+        const float wa = (k == 0 || k == 2) ? 0.25f : 0.75f;
         bool m[4] = {false, false, false, false};
         float fv[4] = {0.f, 0.f, 0.f, 0.f};
         if (mask != nullptr) {
             ldm4(mask + (size_t)y * mp, x0, W, vec.m, m);
-            ld4(f + c * fplane + (size_t)y * fp, x0, W, vec.src, fv);
+            // the known values only where the group has a known pixel (a few
+            // per cent of the groups at sparse masks)
+            if (m[0] || m[1] || m[2] || m[3]) ld4(f + c * fplane + (size_t)y * fp, x0, W, vec.src, fv);
         }
         float out[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (m[j]) {
-                out[j] = fv[j];
-            } else if (x0 + j < W) {
-                const float top = ra[xa[j]] * (1.f - wx[j]) + ra[xb[j]] * wx[j];
-                const float bot = rb[xa[j]] * (1.f - wx[j]) + rb[xb[j]] * wx[j];
-                out[j] = top * (1.f - wy) + bot * wy;
-            } else {
-                out[j] = 0.f;
-            }
-        }
+        for (int j = 0; j < 4; ++j)
+            out[j] = m[j] ? fv[j] : (x0 + j < W ? wa * hrow[ra][j] + (1.f - wa) * hrow[ra + 1][j] : 0.f);
         st4(u + c * uplane + (size_t)y * up, x0, W, vec.dst, out);
     }
 }
@@ -696,19 +785,68 @@ __global__ void __launch_bounds__(RED_TPB) reduce_part_kernel(const double2* __r
 }
 
 // ---- multilevel ----------------------------------------------------------------------
+// Four consecutive values of storage type T as floats (one 8- or 16-byte load
+// where the row allows it).
 template <typename T>
-__global__ void correct_kernel(int H, int W, float* __restrict__ u, int up, long long uplane,
-                               const T* __restrict__ e0, const T* __restrict__ e1, const int* __restrict__ sel,
-                               int ep, long long eplane, const uint8_t* __restrict__ mask, int mp,
-                               const double* __restrict__ scale, const int* __restrict__ skip) {
+__device__ __forceinline__ void ld4t(const T* __restrict__ row, int x0, int W, bool vec, float (&v)[4]) {
+    if (vec && x0 + 3 < W) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 t = *reinterpret_cast<const float4*>(row + x0);
+            v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
+            const uint2 t = *reinterpret_cast<const uint2*>(row + x0);
+            const T* h = reinterpret_cast<const T*>(&t);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = to_f(h[j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = x0 + j < W ? to_f(row[x0 + j]) : 0.f;
+    }
+}
+
+// u = fl32(u + s_c e) on unknown pixels, e in storage T.  The product and the
+// sum are formed by error-free FP32 transformations: s_c is split into two
+// floats, s_hi e is split exactly by an FMA, and the addition to u is a TwoSum,
+// so the one rounding to FP32 at the end is the only error beyond about 2^-48
+// relative.  The result is that of the FP64 formula fl32(u + s_c e) except in
+// rare near-tie cases, without the FP64 pipe, which is slow on this GPU.
+// Vectorised layout: 4 columns x V_ROWS rows per thread.
+template <typename T>
+__global__ void __launch_bounds__(V_TPB) correct_kernel(int H, int W, float* __restrict__ u, int up, long long uplane,
+                                                        const T* __restrict__ e0, const T* __restrict__ e1,
+                                                        const int* __restrict__ sel, int ep, long long eplane,
+                                                        const uint8_t* __restrict__ mask, int mp,
+                                                        const double* __restrict__ scale, const int* __restrict__ skip,
+                                                        CopyVec vec) {
     if (skip != nullptr && *skip != 0) return;
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, c = blockIdx.z;
-    if (x >= W || y >= H) return;
-    if (mask[(size_t)y * mp + x]) return;
-    const T* __restrict__ e = (sel != nullptr && sel[0]) ? e1 : e0;
-    float* pu = u + c * uplane + (size_t)y * up + x;
-    const double v = (double)*pu + scale[c] * (double)to_f(e[c * eplane + (size_t)y * ep + x]);
-    *pu = (float)v;
+    const int c = blockIdx.z;
+    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
+    const int yb = (blockIdx.y * V_TY + threadIdx.y) * V_ROWS;
+    if (x0 >= W) return;
+    const T* __restrict__ e = ((sel != nullptr && sel[0]) ? e1 : e0) + c * eplane;
+    float* __restrict__ uc = u + c * uplane;
+    const double sd = scale[c];
+    const float s_hi = (float)sd, s_lo = (float)(sd - (double)s_hi);
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        const int y = yb + k;
+        if (y >= H) break;
+        float uv[4], ev[4];
+        bool m[4];
+        ld4(uc + (size_t)y * up, x0, W, vec.dst, uv);
+        ldm4(mask + (size_t)y * mp, x0, W, vec.m, m);
+        ld4t<T>(e + (size_t)y * ep, x0, W, vec.src, ev);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float p = s_hi * ev[j];
+            const float pl = fmaf(s_lo, ev[j], fmaf(s_hi, ev[j], -p));   // the product's low part
+            float t, te;
+            two_sum(uv[j], p, t, te);
+            if (!m[j]) uv[j] = t + (te + pl);
+        }
+        st4(uc + (size_t)y * up, x0, W, vec.dst, uv);
+    }
 }
 
 // Outer control of the device-driven correction loop (one thread), after the
@@ -851,16 +989,42 @@ cudaError_t launch_res64(const Res64Args& a, cudaStream_t st) {
     v.m = vec_ok(a.mask, a.mp, 0, 1);
     v.g = a.g_out != nullptr && a.gst == Store::F32 && vec_ok(a.g_out, a.gp, a.gplane, 4);
     const dim3 block(V_TX, V_TY);
-    if (a.u0_ref) {
-        if (a.g_out != nullptr || a.copy_out != nullptr || a.sel != nullptr) return cudaErrorInvalidValue;
-        res64_kernel<float, true><<<grid, block, 0, st>>>(a, v);
-        return cudaGetLastError();
-    }
     switch (a.gst) {
-        case Store::F32: res64_kernel<float, false><<<grid, block, 0, st>>>(a, v); break;
-        case Store::F16: res64_kernel<__half, false><<<grid, block, 0, st>>>(a, v); break;
-        case Store::BF16: res64_kernel<__nv_bfloat16, false><<<grid, block, 0, st>>>(a, v); break;
+        case Store::F32: res64_kernel<float><<<grid, block, 0, st>>>(a, v); break;
+        case Store::F16: res64_kernel<__half><<<grid, block, 0, st>>>(a, v); break;
+        case Store::BF16: res64_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(a, v); break;
     }
+    return cudaGetLastError();
+}
+
+int ref_norm_part_words(int H, int W, int nl) {
+    int n = 0;
+    for (int l = 0; l < nl; ++l) {
+        n += res64_blocks(H, W);
+        H = (H + 1) / 2;
+        W = (W + 1) / 2;
+    }
+    return n;
+}
+
+cudaError_t launch_ref_norms(RefNormArgs a, cudaStream_t st) {
+    if (a.nl < 1 || a.nl > kRefMaxLevels || a.C < 1 || a.part == nullptr || a.ticket == nullptr)
+        return cudaErrorInvalidValue;
+    int blocks = 0, part = 0;
+    for (int l = 0; l < a.nl; ++l) {
+        RefLevel& L = a.lv[l];
+        const dim3 g = grid_res(L.H, L.W, 1);
+        L.gx = (int)g.x;
+        L.gy = (int)g.y;
+        L.block0 = blocks;
+        L.part0 = part;
+        L.mvec = vec_ok(L.mask, L.mp, 0, 1) ? 1 : 0;
+        if (!vec_ok(L.f, L.fp, L.fplane, 4) || L.out == nullptr || L.sqrt_out == nullptr) return cudaErrorInvalidValue;
+        blocks += L.gx * L.gy * a.C;
+        part += L.gx * L.gy * a.C;
+    }
+    if (part > a.part_capacity) return cudaErrorInvalidValue;
+    ref_norms_kernel<<<blocks, dim3(V_TX, V_TY), 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -893,21 +1057,29 @@ cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long upla
                            int ep, long long eplane, const uint8_t* mask, int mp, const double* scale,
                            cudaStream_t st, const void* e1, const int* sel, const int* skip) {
     if (e1 == nullptr) e1 = e;
+    const int es = (int)store_bytes(est);
+    // e rows as 4-element vectors: 16 bytes (FP32) or 8 bytes (FP16 / BF16)
+    auto evec = [&](const void* p) {
+        return (reinterpret_cast<uintptr_t>(p) & (uintptr_t)(4 * es - 1)) == 0 && ((long long)ep * es) % (4 * es) == 0 &&
+               (eplane * es) % (4 * es) == 0;
+    };
+    const CopyVec v{evec(e) && evec(e1), vec_ok(u, up, uplane, 4), vec_ok(mask, mp, 0, 1)};
+    const dim3 grid = gridv(H, W, C), block(V_TX, V_TY);
     switch (est) {
         case Store::F32:
-            correct_kernel<float><<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(
-                H, W, u, up, uplane, static_cast<const float*>(e), static_cast<const float*>(e1), sel, ep, eplane,
-                mask, mp, scale, skip);
+            correct_kernel<float><<<grid, block, 0, st>>>(H, W, u, up, uplane, static_cast<const float*>(e),
+                                                          static_cast<const float*>(e1), sel, ep, eplane, mask, mp,
+                                                          scale, skip, v);
             break;
         case Store::F16:
-            correct_kernel<__half><<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(
-                H, W, u, up, uplane, static_cast<const __half*>(e), static_cast<const __half*>(e1), sel, ep, eplane,
-                mask, mp, scale, skip);
+            correct_kernel<__half><<<grid, block, 0, st>>>(H, W, u, up, uplane, static_cast<const __half*>(e),
+                                                           static_cast<const __half*>(e1), sel, ep, eplane, mask, mp,
+                                                           scale, skip, v);
             break;
         case Store::BF16:
-            correct_kernel<__nv_bfloat16><<<grid2d(H, W, C), dim3(TX, TY), 0, st>>>(
+            correct_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(
                 H, W, u, up, uplane, static_cast<const __nv_bfloat16*>(e), static_cast<const __nv_bfloat16*>(e1), sel,
-                ep, eplane, mask, mp, scale, skip);
+                ep, eplane, mask, mp, scale, skip, v);
             break;
     }
     return cudaGetLastError();

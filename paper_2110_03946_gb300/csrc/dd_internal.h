@@ -287,14 +287,34 @@ struct Res64Args {
     const float* u1; const int* sel;
     float* copy_out; int cp; long long cplane;
     const int* skip;   // optional: the pass is a no-op if *skip != 0
-    // 1: u is the initial iterate u0 = C f (known values, 0 on unknown pixels),
-    // whose residual on an unknown pixel is the plain sum of its known in-image
-    // neighbours' values (FP32, the sum of at most four values): the reference
-    // norms ||b - A u0|| without the error-free transformations
-    int u0_ref;
 };
 int res64_blocks(int H, int W);
 cudaError_t launch_res64(const Res64Args& a, cudaStream_t st);
+
+// Reference norms ||b - A u0||, u0 = C f, of all levels of a handle in one
+// launch (the residual of u0 on an unknown pixel is the sum of its known
+// neighbours' values).  Per level: f (C planes of H x fp, 16-byte aligned
+// rows), mask (H x mp bytes), and the outputs out[c] = {sum r^2, 0} and
+// sqrt_out[c].  part: part_capacity doubles of block partials (at least
+// C * ref_norm_part_words(H, W, nl) for the level sizes halving from H x W);
+// ticket: a zero device counter, left zero.  The launcher fills the block and
+// partial offsets.
+constexpr int kRefMaxLevels = 8;
+struct RefLevel {
+    const float* f; int fp; long long fplane;
+    const uint8_t* mask; int mp;
+    int H, W;
+    double2* out; double* sqrt_out;
+    int gx, gy, block0, part0, mvec;   // set by launch_ref_norms
+};
+struct RefNormArgs {
+    RefLevel lv[kRefMaxLevels];
+    int nl, C;
+    double* part; int part_capacity;
+    unsigned int* ticket;
+};
+int ref_norm_part_words(int H, int W, int nl);
+cudaError_t launch_ref_norms(RefNormArgs a, cudaStream_t st);
 
 // Reduce per-block partials: out[c] = {sum over blocks, max over blocks}.
 cudaError_t launch_reduce_part(const double2* part, int nblk, int C, double2* out, cudaStream_t st);
@@ -307,7 +327,8 @@ cudaError_t launch_restrict(int H, int W, int C, const uint8_t* mask, int mp, co
 cudaError_t launch_prolong(int Hc, int Wc, int H, int W, int C, const float* uc, int ucp,
                            long long ucplane, const uint8_t* mask, int mp, const float* f, int fp,
                            long long fplane, float* u, int up, long long uplane, cudaStream_t st);
-// u = fl32(u + s_c * e) on unknown pixels (FP64 arithmetic), e in storage `est`.
+// u = fl32(u + s_c * e) on unknown pixels (error-free FP32 transformations: the
+// FP64 result up to rare near-ties), e in storage `est`.
 cudaError_t launch_correct(int H, int W, int C, float* u, int up, long long uplane, const void* e,
                            Store est, int ep, long long eplane, const uint8_t* mask, int mp,
                            const double* scale, cudaStream_t st, const void* e1 = nullptr,

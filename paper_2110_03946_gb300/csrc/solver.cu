@@ -139,6 +139,7 @@ struct dd_inpaint {
     double* scale_inv_d = nullptr;  // C
     // residual / stop-test scratch
     double2* res_part = nullptr;
+    int res_part_n = 0;             // res_part holds C x res_part_n double2
     int res_nblk = 0;
     double2* res_out = nullptr;     // C per level
     unsigned int* res_ticket = nullptr;   // completion ticket of the fused residual reduction (zero)
@@ -353,20 +354,25 @@ int load_data(dd_inpaint* h, const uint8_t* mask, const float* values, cudaStrea
     }
     for (auto& L : h->lv)
         DD_LAUNCH(h, dd::launch_build_tmask(L.geom, L.mask, L.W, L.tmask, st, &L == &L0 ? h->count_d : nullptr));
-    // reference norms ||b - A u0||, u0 = C f, per level and channel, kept on the device
+    // reference norms ||b - A u0||, u0 = C f, of every level and channel in one launch, kept on the device
     const int nl = (int)h->lv.size();
-    for (int l = 0; l < nl; ++l) {
-        Level& L = h->lv[l];
-        const int nblk = dd::res64_blocks(L.H, L.W);
-        dd::Res64Args a{};
-        a.H = L.H; a.W = L.W; a.C = h->C;
-        a.u = L.f; a.up = L.P; a.uplane = L.plane();
-        a.mask = L.mask; a.mp = L.W;
-        a.g_out = nullptr; a.gst = Store::F32;
-        a.part = h->res_part; a.nblk = nblk;
-        a.out = h->res_out + (size_t)l * h->C; a.sqrt_out = L.ref_d; a.ticket = h->res_ticket;
-        a.u0_ref = 1;
-        DD_LAUNCH(h, dd::launch_res64(a, st));
+    {
+        dd::RefNormArgs ra{};
+        ra.nl = nl;
+        ra.C = h->C;
+        for (int l = 0; l < nl; ++l) {
+            Level& L = h->lv[l];
+            dd::RefLevel& R = ra.lv[l];
+            R.f = L.f; R.fp = L.P; R.fplane = L.plane();
+            R.mask = L.mask; R.mp = L.W;
+            R.H = L.H; R.W = L.W;
+            R.out = h->res_out + (size_t)l * h->C;
+            R.sqrt_out = L.ref_d;
+        }
+        ra.part = reinterpret_cast<double*>(h->res_part);
+        ra.part_capacity = 2 * h->C * h->res_part_n;
+        ra.ticket = h->res_ticket;
+        DD_LAUNCH(h, dd::launch_ref_norms(ra, st));
     }
     DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     if (!sync) {   // counts and reference norms are read back with the next solve
@@ -1457,7 +1463,10 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         if ((rc = dalloc_t(h, &h->corr_prev, 1)) != DD_OK) return fail(rc);
     }
     h->res_nblk = dd::res64_blocks(H, W);
-    if ((rc = dalloc_t(h, &h->res_part, (size_t)C * h->res_nblk)) != DD_OK) return fail(rc);
+    // block partials: the residual passes (C x res_nblk double2) and the
+    // reference norms of all levels (C x their blocks, doubles)
+    h->res_part_n = std::max(h->res_nblk, dd::ref_norm_part_words(H, W, (int)h->lv.size()));
+    if ((rc = dalloc_t(h, &h->res_part, (size_t)C * h->res_part_n)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->res_out, (size_t)C * DD_MAX_LEVELS)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->norms2_d, (size_t)2 * C + 2)) != DD_OK) return fail(rc);
     if ((rc = dalloc_t(h, &h->sstate_d, 4)) != DD_OK) return fail(rc);

@@ -894,7 +894,7 @@ constexpr int kTmaskTPB = 256;
 template <class CF>
 __global__ void __launch_bounds__(kTmaskTPB)
 build_tmask_kernel(const uint8_t* __restrict__ mask, int mp, uint32_t* __restrict__ tmask, int H, int W, int s,
-                   int half_o, int ntx, int nty, int ntiles, unsigned long long* __restrict__ count) {
+                   int half_o, int ntx, int nty, int ntiles, unsigned long long* __restrict__ count, int vec4) {
     constexpr int PX = CF::PX, PY = CF::PY, LX = CF::LX, LY = CF::LY, NT = CF::NT;
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned unknown = 0;
@@ -908,14 +908,22 @@ build_tmask_kernel(const uint8_t* __restrict__ mask, int mp, uint32_t* __restric
         const int ox0 = tx == 0 ? 0 : x0 + half_o, ox1 = tx == ntx - 1 ? W : x0 + s + half_o;
         const int ry0 = (wt * LY + ly) * PY, rx0 = lx * PX;
         uint32_t kb = 0, ob = 0;
-        for (int i = 0; i < PY; ++i)
+        // a row's PX = 4 mask bytes as one 32-bit load where they are in the tile and aligned
+        const bool row4 = PX == 4 && vec4 && ((x0 + rx0) & 3) == 0 && rx0 + PX <= tw;
+        for (int i = 0; i < PY; ++i) {
+            const int y = y0 + ry0 + i;
+            const bool yin = ry0 + i < th;
+            uint32_t bytes = 0;
+            if (row4 && yin) bytes = *reinterpret_cast<const uint32_t*>(mask + (size_t)y * mp + x0 + rx0);
             for (int j = 0; j < PX; ++j) {
                 const int bit = i * PX + j;
-                const int y = y0 + ry0 + i, x = x0 + rx0 + j;
-                const bool in = (ry0 + i < th) && (rx0 + j < tw);
-                if (!in || mask[(size_t)y * mp + x] != 0) kb |= 1u << bit;
+                const int x = x0 + rx0 + j;
+                const bool in = yin && (rx0 + j < tw);
+                const bool known = in && (row4 ? ((bytes >> (8 * j)) & 0xffu) != 0 : mask[(size_t)y * mp + x] != 0);
+                if (!in || known) kb |= 1u << bit;
                 if (in && y >= oy0 && y < oy1 && x >= ox0 && x < ox1) ob |= 1u << bit;
             }
+        }
         tmask[(size_t)tile * 2 * NT + tt] = kb;
         tmask[(size_t)tile * 2 * NT + NT + tt] = ob;
         constexpr int LB = PX * PY;
@@ -1121,8 +1129,9 @@ template <class CF>
 cudaError_t tmask_cfg(const TileGeom& g, const uint8_t* mask, int mp, uint32_t* tmask, cudaStream_t st,
                       unsigned long long* count) {
     const long long n = (long long)g.ntiles * CF::NT;
+    const int vec4 = (reinterpret_cast<uintptr_t>(mask) & 3u) == 0 && (mp & 3) == 0;
     build_tmask_kernel<CF><<<(unsigned)((n + kTmaskTPB - 1) / kTmaskTPB), kTmaskTPB, 0, st>>>(
-        mask, mp, tmask, g.H, g.W, g.s, g.half_o, g.ntx, g.nty, g.ntiles, count);
+        mask, mp, tmask, g.H, g.W, g.s, g.half_o, g.ntx, g.nty, g.ntiles, count, vec4);
     return cudaGetLastError();
 }
 
