@@ -52,6 +52,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// TwoSum on two independent lanes at once (packed FP32 adds, each rounded to
+// nearest: the same operations as two_sum on each half)
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+    s = __fadd2_rn(a, b);
+    const float2 bb = __fadd2_rn(s, neg2(a));
+    e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
+}
+
 // (hi, lo) += (s, e), renormalised
 __device__ __forceinline__ void ds_add(float& hi, float& lo, float s, float e) {
     float t, err;
@@ -107,159 +116,228 @@ __device__ __forceinline__ void ldm4(const uint8_t* __restrict__ row, int x0, in
     }
 }
 
+// The 4 mask bytes of columns x0 .. x0+3 (byte j for column x0 + j; 0 past W).
+__device__ __forceinline__ uint32_t ldm4w(const uint8_t* __restrict__ row, int x0, int W, bool vec) {
+    if (vec && x0 + 3 < W) return *reinterpret_cast<const uint32_t*>(row + x0);
+    uint32_t w = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (x0 + j < W) w |= (uint32_t)row[x0 + j] << (8 * j);
+    return w;
+}
+
 struct ResVec {
     bool u, m, g, cp;   // float4 / uchar4 access to u (and u1), mask, g_out (F32 only), copy_out
 };
 
 // Per pixel p, r_p = sum over in-image neighbours q of (u_q - u_p), formed
 // with TwoSum so that only the final rounding to FP32 remains; r = 0 on known
-// pixels.  Each thread
-// accumulates r^2 (FP32) and max |r| over its pixels; warp butterflies, then
-// the block's warps in order, give one double2 partial per block.  With
-// a.out, the last block (atomic ticket) reduces the partials of every channel
-// in block order into out[c] = {sum r^2, max |r|} and sqrt_out[c] = sqrt(sum).
-// 4 rows per thread (a block covers 128 x 32 pixels): many short blocks keep
-// every SM busy to the end of the pass; only thread 0 fences and takes the ticket
+// pixels.  A tile is 128 x 32 pixels: each thread owns 4 columns in 4 rows.
+// Each thread accumulates r^2 (FP32) and max |r| over its pixels of a tile,
+// a warp butterfly sums them, and the warp's lane 0 adds the tile's sum into
+// an FP64 accumulator.
+// Grid (gx, 1, C): the gx blocks of channel c walk its tiles grid-stride, one
+// wave of resident blocks for the whole pass, so that the per-block work of
+// fencing, taking the ticket and writing a partial is paid once per block
+// rather than per tile.  Block b's partial (its warps in order) goes to
+// part[c * nblk + b].  With a.out, the last block (atomic ticket) reduces each
+// channel's gx partials, one warp per channel in a fixed lane order, into
+// out[c] = {sum r^2, max |r|} and sqrt_out[c] = sqrt(sum).  The order of every
+// sum depends only on the grid, so results repeat bit for bit on one device.
 constexpr int R_ROWS = 4, R_BROWS = V_TY * R_ROWS;
 
 dim3 grid_res(int H, int W, int C) { return dim3((W + V_COLS - 1) / V_COLS, (H + R_BROWS - 1) / R_BROWS, C); }
+
+// Sum (and max) of n per-block partials p[0..n) by one warp, in a fixed order
+// (lane-strided with four independent accumulators, then a butterfly); every
+// lane gets the result.
+__device__ __forceinline__ double2 warp_sum_parts(const double2* __restrict__ p, int n, int lane) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, m = 0.0;
+    int i = lane;
+    for (; i + 96 < n; i += 128) {
+        const double2 v0 = __ldcg(p + i), v1 = __ldcg(p + i + 32), v2 = __ldcg(p + i + 64), v3 = __ldcg(p + i + 96);
+        s0 += v0.x; s1 += v1.x; s2 += v2.x; s3 += v3.x;
+        m = fmax(fmax(m, fmax(v0.y, v1.y)), fmax(v2.y, v3.y));
+    }
+    for (; i < n; i += 32) {
+        const double2 v = __ldcg(p + i);
+        s0 += v.x;
+        m = fmax(m, v.y);
+    }
+    double sv = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) {
+        sv += __shfl_xor_sync(0xffffffffu, sv, k);
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, k));
+    }
+    return make_double2(sv, m);
+}
+__device__ __forceinline__ double warp_sum_parts(const double* __restrict__ p, int n, int lane) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = lane;
+    for (; i + 96 < n; i += 128) {
+        s0 += __ldcg(p + i);
+        s1 += __ldcg(p + i + 32);
+        s2 += __ldcg(p + i + 64);
+        s3 += __ldcg(p + i + 96);
+    }
+    for (; i < n; i += 32) s0 += __ldcg(p + i);
+    double sv = (s0 + s1) + (s2 + s3);
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, k);
+    return sv;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
     if (a.skip != nullptr && *a.skip != 0) return;   // uniform: no partial, no ticket
     const int c = blockIdx.z;
-    const int x0 = (blockIdx.x * V_TX + threadIdx.x) * 4;
-    const int yb = (blockIdx.y * V_TY + threadIdx.y) * R_ROWS;
     const int H = a.H, W = a.W;
+    const int gxt = (W + V_COLS - 1) / V_COLS, ntile = gxt * ((H + R_BROWS - 1) / R_BROWS);
     const float* __restrict__ u = ((a.sel != nullptr && a.sel[0]) ? a.u1 : a.u) + c * a.uplane;
     const float sinv = a.g_out ? (float)a.scale_inv[c] : 0.f;
-    const bool xin = x0 < W;
-    float rows[R_ROWS + 2][4];
+    const int lane = threadIdx.x, wid = threadIdx.y;   // one warp per thread row
+    double wsum = 0.0;   // lane 0: this warp's sum over the block's tiles
+    float wmax = 0.f;
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int by = t / gxt, bx = t - by * gxt;
+        const int x0 = (bx * V_TX + threadIdx.x) * 4;
+        const int yb = (by * V_TY + threadIdx.y) * R_ROWS;
+        const bool xin = x0 < W;
+        // every load of the tile before any arithmetic: the rows yb-1 .. yb+R_ROWS
+        // (0 outside the image), the halo columns x0-1 (lane 0) and x0+4 (lane 31)
+        // and the mask bytes of the thread's rows
+        float rows[R_ROWS + 2][4], hl[R_ROWS], hr[R_ROWS];
+        uint32_t mk[R_ROWS];
 #pragma unroll
-    for (int k = 0; k < R_ROWS + 2; ++k) {
-        const int y = yb - 1 + k;
-        if (xin && y >= 0 && y < H) {
-            ld4(u + (size_t)y * a.up, x0, W, vec.u, rows[k]);
-        } else {
-            rows[k][0] = rows[k][1] = rows[k][2] = rows[k][3] = 0.f;
+        for (int k = 0; k < R_ROWS + 2; ++k) {
+            const int y = yb - 1 + k;
+            if (xin && y >= 0 && y < H) {
+                ld4(u + (size_t)y * a.up, x0, W, vec.u, rows[k]);
+            } else {
+                rows[k][0] = rows[k][1] = rows[k][2] = rows[k][3] = 0.f;
+            }
         }
-    }
-    float s = 0.f, mx = 0.f;
 #pragma unroll
-    for (int k = 0; k < R_ROWS; ++k) {
-        const int y = yb + k;
-        const float* rw = rows[k + 1];
-        float left = __shfl_up_sync(0xffffffffu, rw[3], 1);
-        float right = __shfl_down_sync(0xffffffffu, rw[0], 1);
-        if (!xin || y >= H) continue;
-        if (threadIdx.x == 0) left = x0 > 0 ? u[(size_t)y * a.up + x0 - 1] : 0.f;
-        if (threadIdx.x == V_TX - 1) right = x0 + 4 < W ? u[(size_t)y * a.up + x0 + 4] : 0.f;
-        bool known[4];
-        ldm4(a.mask + (size_t)y * a.mp, x0, W, vec.m, known);
-        float r[4];
-        // all four pixels away from the image border: one branch per row group
-        if (y > 0 && y < H - 1 && x0 > 0 && x0 + 4 < W) {
+        for (int k = 0; k < R_ROWS; ++k) {
+            const int y = yb + k;
+            const bool yin = xin && y < H;
+            hl[k] = (lane == 0 && yin && x0 > 0) ? u[(size_t)y * a.up + x0 - 1] : 0.f;
+            hr[k] = (lane == V_TX - 1 && yin && x0 + 4 < W) ? u[(size_t)y * a.up + x0 + 4] : 0.f;
+            mk[k] = yin ? ldm4w(a.mask + (size_t)y * a.mp, x0, W, vec.m) : 0u;
+        }
+        float s = 0.f, mx = 0.f;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+        for (int k = 0; k < R_ROWS; ++k) {
+            const int y = yb + k;
+            const float* rw = rows[k + 1];
+            float left = __shfl_up_sync(0xffffffffu, rw[3], 1);
+            float right = __shfl_down_sync(0xffffffffu, rw[0], 1);
+            if (!xin || y >= H) continue;
+            if (lane == 0) left = hl[k];
+            if (lane == V_TX - 1) right = hr[k];
+            bool known[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) known[j] = ((mk[k] >> (8 * j)) & 0xffu) != 0u;
+            float r[4];
+            // all four pixels away from the image border: one branch per row group
+            if (y > 0 && y < H - 1 && x0 > 0 && x0 + 4 < W) {
                 // (N + S) + (W + E) - 4 u_p by TwoSum steps (4 u_p is exact), the
                 // rounding errors summed in FP32: ~48-bit accurate before the one
-                // final rounding, as the general path below
-                float s1, e1, s2, e2, t, e3, dd, e4;
-                two_sum(rows[k][j], rows[k + 2][j], s1, e1);
-                two_sum(j > 0 ? rw[j - 1] : left, j < 3 ? rw[j + 1] : right, s2, e2);
-                two_sum(s1, s2, t, e3);
-                two_sum(t, -4.f * rw[j], dd, e4);
-                const float rv = __fadd_rn(dd, __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, e4)));
-                r[j] = known[j] ? 0.f : rv;
-            }
-        } else {
+                // final rounding, as the general path below; pixels (0, 1) and
+                // (2, 3) side by side in packed adds
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                // the in-image neighbour differences u_q - u_p, each split exactly
-                // by TwoSum, accumulated double-single
-                const int x = x0 + j;
-                const float uc = rw[j];
-                float hi = 0.f, lo = 0.f, d, e;
-                if (y > 0) { two_sum(rows[k][j], -uc, d, e); ds_add(hi, lo, d, e); }
-                if (y < H - 1) { two_sum(rows[k + 2][j], -uc, d, e); ds_add(hi, lo, d, e); }
-                if (x > 0) { two_sum(j > 0 ? rw[j - 1] : left, -uc, d, e); ds_add(hi, lo, d, e); }
-                if (x < W - 1) { two_sum(j < 3 ? rw[j + 1] : right, -uc, d, e); ds_add(hi, lo, d, e); }
-                r[j] = (x < W && !known[j]) ? __fadd_rn(hi, lo) : 0.f;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            s = fmaf(r[j], r[j], s);
-            mx = fmaxf(mx, fabsf(r[j]));
-        }
-        if (a.copy_out) st4(a.copy_out + c * a.cplane + (size_t)y * a.cp, x0, W, vec.cp, rows[k + 1]);
-        if (a.g_out) {
-            T* g = static_cast<T*>(a.g_out) + c * a.gplane + (size_t)y * a.gp;
-            if constexpr (sizeof(T) == 4) {
-                const float gv[4] = {r[0] * sinv, r[1] * sinv, r[2] * sinv, r[3] * sinv};
-                st4(reinterpret_cast<float*>(g), x0, W, vec.g, gv);
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * h;
+                    const float2 nn = make_float2(rows[k][j], rows[k][j + 1]);
+                    const float2 ss2 = make_float2(rows[k + 2][j], rows[k + 2][j + 1]);
+                    const float2 ww = make_float2(j > 0 ? rw[j - 1] : left, rw[j]);
+                    const float2 ee = make_float2(rw[j + 1], j + 2 < 4 ? rw[j + 2] : right);
+                    const float2 c4 = make_float2(-4.f * rw[j], -4.f * rw[j + 1]);
+                    float2 s1, e1, s2, e2, t, e3, dd, e4;
+                    two_sum2(nn, ss2, s1, e1);
+                    two_sum2(ww, ee, s2, e2);
+                    two_sum2(s1, s2, t, e3);
+                    two_sum2(t, c4, dd, e4);
+                    const float2 rv = __fadd2_rn(dd, __fadd2_rn(__fadd2_rn(e1, e2), __fadd2_rn(e3, e4)));
+                    r[j] = known[j] ? 0.f : rv.x;
+                    r[j + 1] = known[j + 1] ? 0.f : rv.y;
+                }
             } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (x0 + j < W) g[x0 + j] = from_f<T>(r[j] * sinv);
+                for (int j = 0; j < 4; ++j) {
+                    // the in-image neighbour differences u_q - u_p, each split exactly
+                    // by TwoSum, accumulated double-single
+                    const int x = x0 + j;
+                    const float uc = rw[j];
+                    float hi = 0.f, lo = 0.f, d, e;
+                    if (y > 0) { two_sum(rows[k][j], -uc, d, e); ds_add(hi, lo, d, e); }
+                    if (y < H - 1) { two_sum(rows[k + 2][j], -uc, d, e); ds_add(hi, lo, d, e); }
+                    if (x > 0) { two_sum(j > 0 ? rw[j - 1] : left, -uc, d, e); ds_add(hi, lo, d, e); }
+                    if (x < W - 1) { two_sum(j < 3 ? rw[j + 1] : right, -uc, d, e); ds_add(hi, lo, d, e); }
+                    r[j] = (x < W && !known[j]) ? __fadd_rn(hi, lo) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                s = fmaf(r[j], r[j], s);
+                mx = fmaxf(mx, fabsf(r[j]));
+            }
+            if (a.copy_out) st4(a.copy_out + c * a.cplane + (size_t)y * a.cp, x0, W, vec.cp, rows[k + 1]);
+            if (a.g_out) {
+                T* g = static_cast<T*>(a.g_out) + c * a.gplane + (size_t)y * a.gp;
+                if constexpr (sizeof(T) == 4) {
+                    const float gv[4] = {r[0] * sinv, r[1] * sinv, r[2] * sinv, r[3] * sinv};
+                    st4(reinterpret_cast<float*>(g), x0, W, vec.g, gv);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (x0 + j < W) g[x0 + j] = from_f<T>(r[j] * sinv);
+                }
             }
         }
-    }
-    // fixed-order block reduction: warp butterflies, then the warps in order
 #pragma unroll
-    for (int k = 16; k >= 1; k >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, k);
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, k));
+        for (int k = 16; k >= 1; k >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, k);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, k));
+        }
+        if (lane == 0) {
+            wsum += (double)s;
+            wmax = fmaxf(wmax, mx);
+        }
     }
-    __shared__ float ss[V_TPB / 32], sm[V_TPB / 32];
+    __shared__ double ss[V_TY];
+    __shared__ float sm[V_TY];
     __shared__ int s_last;
     const int tid = threadIdx.y * V_TX + threadIdx.x;
-    if ((tid & 31) == 0) {
-        ss[tid >> 5] = s;
-        sm[tid >> 5] = mx;
+    if (lane == 0) {
+        ss[wid] = wsum;
+        sm[wid] = wmax;
     }
     __syncthreads();
     if (tid == 0) {
         double ts = 0.0;
         float tm = 0.f;
-        for (int w = 0; w < V_TPB / 32; ++w) {
-            ts += (double)ss[w];
+        for (int w = 0; w < V_TY; ++w) {
+            ts += ss[w];
             tm = fmaxf(tm, sm[w]);
         }
-        a.part[(size_t)c * a.nblk + blockIdx.y * gridDim.x + blockIdx.x] = make_double2(ts, (double)tm);
+        a.part[(size_t)c * a.nblk + blockIdx.x] = make_double2(ts, (double)tm);
         if (a.out != nullptr) {   // the partial is visible before the ticket is taken
             __threadfence();
-            s_last = atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.y * gridDim.z - 1;
+            s_last = atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.z - 1;
         }
     }
     if (a.out == nullptr) return;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    __shared__ double rs[V_TPB];
-    __shared__ double rm[V_TPB];
-    for (int cc = 0; cc < a.C; ++cc) {
-        double sv = 0.0, mv = 0.0;
-        for (int i = tid; i < a.nblk; i += V_TPB) {
-            const double2 v = __ldcg(a.part + (size_t)cc * a.nblk + i);
-            sv += v.x;
-            mv = fmax(mv, v.y);
+    for (int cc = wid; cc < a.C; cc += V_TY) {
+        const double2 r = warp_sum_parts(a.part + (size_t)cc * a.nblk, (int)gridDim.x, lane);
+        if (lane == 0) {
+            a.out[cc] = r;
+            if (a.sqrt_out) a.sqrt_out[cc] = sqrt(r.x);
         }
-        rs[tid] = sv;
-        rm[tid] = mv;
-        __syncthreads();
-        for (int hh = V_TPB / 2; hh > 0; hh >>= 1) {
-            if (tid < hh) {
-                rs[tid] += rs[tid + hh];
-                rm[tid] = fmax(rm[tid], rm[tid + hh]);
-            }
-            __syncthreads();
-        }
-        if (tid == 0) {
-            a.out[cc] = make_double2(rs[0], rm[0]);
-            if (a.sqrt_out) a.sqrt_out[cc] = sqrt(rs[0]);
-        }
-        __syncthreads();
     }
     if (tid == 0) *a.ticket = 0u;
 }
@@ -267,88 +345,95 @@ __global__ void __launch_bounds__(V_TPB) res64_kernel(Res64Args a, ResVec vec) {
 // Reference norms ||b - A u0||, u0 = C f, of every level in one launch: the
 // residual of u0 on an unknown pixel is the sum of its known in-image
 // neighbours' values (u0 is 0 on unknown pixels), summed in FP32 (at most four
-// values), squared and added per thread in FP32, per block in FP64.  Blocks
-// cover (level, channel, 128 x 32 pixels); the last block (atomic ticket) sums
-// each level's block partials per channel in a fixed order into out[c] =
-// {sum, 0} and sqrt_out[c].
+// values), squared and added per thread in FP32 and per warp and tile, then
+// across tiles in FP64.  Grid (gx, levels x C): the gx blocks of segment
+// (level, channel) walk its 128 x 32 tiles grid-stride (a coarse level's
+// segment has fewer tiles, and its surplus blocks only take the ticket).  Block
+// b writes its partial to part[seg * gx + b] if it had a tile; the last block
+// (atomic ticket) sums each segment's partials, one warp per segment in a
+// fixed lane order, into out[c] = {sum, 0} and sqrt_out[c].
 __global__ void __launch_bounds__(V_TPB) ref_norms_kernel(RefNormArgs a) {
-    int l = 0;
-    while (l + 1 < a.nl && (int)blockIdx.x >= a.lv[l + 1].block0) ++l;
+    const int seg = blockIdx.y;
+    const int l = seg / a.C, c = seg - l * a.C;
     const RefLevel& L = a.lv[l];
-    int rem = (int)blockIdx.x - L.block0;
-    const int per_c = L.gx * L.gy;
-    const int c = rem / per_c;
-    rem -= c * per_c;
-    const int by = rem / L.gx, bx = rem - by * L.gx;
-    const int x0 = (bx * V_TX + threadIdx.x) * 4;
-    const int yb = (by * V_TY + threadIdx.y) * R_ROWS;
     const int H = L.H, W = L.W;
+    const int ntile = L.gx * L.gy;
     const float* __restrict__ u = L.f + c * L.fplane;
-    const bool xin = x0 < W;
-    float rows[R_ROWS + 2][4];
+    const int lane = threadIdx.x, wid = threadIdx.y;
+    double wsum = 0.0;
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int by = t / L.gx, bx = t - by * L.gx;
+        const int x0 = (bx * V_TX + threadIdx.x) * 4;
+        const int yb = (by * V_TY + threadIdx.y) * R_ROWS;
+        const bool xin = x0 < W;
+        // every load of the tile before any arithmetic (as in the residual pass)
+        float rows[R_ROWS + 2][4], hl[R_ROWS], hr[R_ROWS];
+        uint32_t mk[R_ROWS];
 #pragma unroll
-    for (int k = 0; k < R_ROWS + 2; ++k) {
-        const int y = yb - 1 + k;
-        if (xin && y >= 0 && y < H) {
-            ld4(u + (size_t)y * L.fp, x0, W, true, rows[k]);
-        } else {
-            rows[k][0] = rows[k][1] = rows[k][2] = rows[k][3] = 0.f;
+        for (int k = 0; k < R_ROWS + 2; ++k) {
+            const int y = yb - 1 + k;
+            if (xin && y >= 0 && y < H) {
+                ld4(u + (size_t)y * L.fp, x0, W, true, rows[k]);
+            } else {
+                rows[k][0] = rows[k][1] = rows[k][2] = rows[k][3] = 0.f;
+            }
         }
-    }
-    float s = 0.f;
 #pragma unroll
-    for (int k = 0; k < R_ROWS; ++k) {
-        const int y = yb + k;
-        const float* rw = rows[k + 1];
-        float left = __shfl_up_sync(0xffffffffu, rw[3], 1);
-        float right = __shfl_down_sync(0xffffffffu, rw[0], 1);
-        if (!xin || y >= H) continue;
-        if (threadIdx.x == 0) left = x0 > 0 ? u[(size_t)y * L.fp + x0 - 1] : 0.f;
-        if (threadIdx.x == V_TX - 1) right = x0 + 4 < W ? u[(size_t)y * L.fp + x0 + 4] : 0.f;
-        bool known[4];
-        ldm4(L.mask + (size_t)y * L.mp, x0, W, L.mvec != 0, known);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float wv = j > 0 ? rw[j - 1] : left, ev = j < 3 ? rw[j + 1] : right;
-            const float r = (x0 + j < W && !known[j]) ? (rows[k][j] + rows[k + 2][j]) + (wv + ev) : 0.f;
-            s = fmaf(r, r, s);
+        for (int k = 0; k < R_ROWS; ++k) {
+            const int y = yb + k;
+            const bool yin = xin && y < H;
+            hl[k] = (lane == 0 && yin && x0 > 0) ? u[(size_t)y * L.fp + x0 - 1] : 0.f;
+            hr[k] = (lane == V_TX - 1 && yin && x0 + 4 < W) ? u[(size_t)y * L.fp + x0 + 4] : 0.f;
+            mk[k] = yin ? ldm4w(L.mask + (size_t)y * L.mp, x0, W, L.mvec != 0) : 0u;
         }
-    }
+        float s = 0.f;
 #pragma unroll
-    for (int k = 16; k >= 1; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
-    __shared__ float ss[V_TPB / 32];
+        for (int k = 0; k < R_ROWS; ++k) {
+            const int y = yb + k;
+            const float* rw = rows[k + 1];
+            float left = __shfl_up_sync(0xffffffffu, rw[3], 1);
+            float right = __shfl_down_sync(0xffffffffu, rw[0], 1);
+            if (!xin || y >= H) continue;
+            if (lane == 0) left = hl[k];
+            if (lane == V_TX - 1) right = hr[k];
+            bool known[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) known[j] = ((mk[k] >> (8 * j)) & 0xffu) != 0u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float wv = j > 0 ? rw[j - 1] : left, ev = j < 3 ? rw[j + 1] : right;
+                const float r = (x0 + j < W && !known[j]) ? (rows[k][j] + rows[k + 2][j]) + (wv + ev) : 0.f;
+                s = fmaf(r, r, s);
+            }
+        }
+#pragma unroll
+        for (int k = 16; k >= 1; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+        if (lane == 0) wsum += (double)s;
+    }
+    __shared__ double ss[V_TY];
     __shared__ int s_last;
     const int tid = threadIdx.y * V_TX + threadIdx.x;
-    if ((tid & 31) == 0) ss[tid >> 5] = s;
+    if (lane == 0) ss[wid] = wsum;
     __syncthreads();
     if (tid == 0) {
-        double ts = 0.0;
-        for (int w = 0; w < V_TPB / 32; ++w) ts += (double)ss[w];
-        a.part[L.part0 + (size_t)c * per_c + by * L.gx + bx] = ts;
+        if ((int)blockIdx.x < ntile) {
+            double ts = 0.0;
+            for (int w = 0; w < V_TY; ++w) ts += ss[w];
+            a.part[(size_t)seg * gridDim.x + blockIdx.x] = ts;
+        }
         __threadfence();
-        s_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.y - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    __shared__ double rs[V_TPB];
-    for (int q = 0; q < a.nl; ++q) {
-        const RefLevel& Q = a.lv[q];
-        const int pc = Q.gx * Q.gy;
-        for (int cc = 0; cc < a.C; ++cc) {
-            double sv = 0.0;
-            for (int i = tid; i < pc; i += V_TPB) sv += __ldcg(a.part + Q.part0 + (size_t)cc * pc + i);
-            rs[tid] = sv;
-            __syncthreads();
-            for (int hh = V_TPB / 2; hh > 0; hh >>= 1) {
-                if (tid < hh) rs[tid] += rs[tid + hh];
-                __syncthreads();
-            }
-            if (tid == 0) {
-                Q.out[cc] = make_double2(rs[0], 0.0);
-                Q.sqrt_out[cc] = sqrt(rs[0]);
-            }
-            __syncthreads();
+    for (int q = wid; q < (int)gridDim.y; q += V_TY) {
+        const int lq = q / a.C, cq = q - lq * a.C;
+        const RefLevel& Q = a.lv[lq];
+        const double sv = warp_sum_parts(a.part + (size_t)q * gridDim.x, min((int)gridDim.x, Q.gx * Q.gy), lane);
+        if (lane == 0) {
+            Q.out[cq] = make_double2(sv, 0.0);
+            Q.sqrt_out[cq] = sqrt(sv);
         }
     }
     if (tid == 0) *a.ticket = 0u;
@@ -437,6 +522,12 @@ __global__ void __launch_bounds__(V_TPB) prolong_kernel(int Hc, int Wc, int H, i
         col[j] = min(max(cx - 1 + j, 0), Wc - 1);
         row[j] = min(max(cy - 1 + j, 0), Hc - 1);
     }
+    // the mask bytes of the thread's rows first, so that the loads of the
+    // known values they select and of the coarse values go out together
+    uint32_t mk[V_ROWS];
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k)
+        mk[k] = (mask != nullptr && yb + k < H) ? ldm4w(mask + (size_t)(yb + k) * mp, x0, W, vec.m) : 0u;
     // horizontal interpolation of the 4 coarse rows onto the thread's 4 columns
     float hrow[4][4];
 #pragma unroll
@@ -448,6 +539,14 @@ __global__ void __launch_bounds__(V_TPB) prolong_kernel(int Hc, int Wc, int H, i
         hrow[r][2] = 0.25f * c1 + 0.75f * c2;
         hrow[r][3] = 0.75f * c2 + 0.25f * c3;
     }
+    // the known values only where the group has a known pixel (a few per cent
+    // of the groups at sparse masks)
+    float fv[V_ROWS][4];
+#pragma unroll
+    for (int k = 0; k < V_ROWS; ++k) {
+        fv[k][0] = fv[k][1] = fv[k][2] = fv[k][3] = 0.f;
+        if (mk[k] != 0u) ld4(f + c * fplane + (size_t)(yb + k) * fp, x0, W, vec.src, fv[k]);
+    }
 #pragma unroll
     for (int k = 0; k < V_ROWS; ++k) {
         const int y = yb + k;
@@ -455,18 +554,12 @@ __global__ void __launch_bounds__(V_TPB) prolong_kernel(int Hc, int Wc, int H, i
         // rows yb, yb+1, yb+2, yb+3 sit between coarse rows (0,1), (1,2), (1,2), (2,3) of the four
         const int ra = k == 0 ? 0 : (k == 3 ? 2 : 1);
         const float wa = (k == 0 || k == 2) ? 0.25f : 0.75f;
-        bool m[4] = {false, false, false, false};
-        float fv[4] = {0.f, 0.f, 0.f, 0.f};
-        if (mask != nullptr) {
-            ldm4(mask + (size_t)y * mp, x0, W, vec.m, m);
-            // the known values only where the group has a known pixel (a few
-            // per cent of the groups at sparse masks)
-            if (m[0] || m[1] || m[2] || m[3]) ld4(f + c * fplane + (size_t)y * fp, x0, W, vec.src, fv);
-        }
         float out[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            out[j] = m[j] ? fv[j] : (x0 + j < W ? wa * hrow[ra][j] + (1.f - wa) * hrow[ra + 1][j] : 0.f);
+        for (int j = 0; j < 4; ++j) {
+            const bool known = ((mk[k] >> (8 * j)) & 0xffu) != 0u;
+            out[j] = known ? fv[k][j] : (x0 + j < W ? wa * hrow[ra][j] + (1.f - wa) * hrow[ra + 1][j] : 0.f);
+        }
         st4(u + c * uplane + (size_t)y * up, x0, W, vec.dst, out);
     }
 }
@@ -524,7 +617,10 @@ __global__ void __launch_bounds__(V_TPB) restrict_kernel(int H, int W, int Hc, i
                         ++cnt;
                         acc += fv[dy][2 * j + dx];
                     }
-            out[j] = cnt > 0 ? acc / (float)cnt : 0.f;
+            // the mean by the reciprocal of the count (1, 1/2, 1/3, 1/4: within an
+            // ulp of the quotient, without the division's instruction sequence)
+            const float rc = cnt == 1 ? 1.f : (cnt == 2 ? 0.5f : (cnt == 3 ? (1.f / 3.f) : 0.25f));
+            out[j] = cnt > 0 ? acc * rc : 0.f;
             mo[j] = cnt > 0 ? 1 : 0;
         }
         st4(f_c + c * fcplane + (size_t)Y * fcp, X0, Wc, vec.dst, out);
@@ -759,31 +855,6 @@ __global__ void __launch_bounds__(V_TPB) corr_step_kernel(int H, int W, const fl
     }
 }
 
-constexpr int RED_TPB = 512;
-
-__global__ void __launch_bounds__(RED_TPB) reduce_part_kernel(const double2* __restrict__ part, int nblk,
-                                                              double2* __restrict__ out) {
-    const int c = blockIdx.x;
-    double s = 0.0, m = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += RED_TPB) {
-        const double2 v = part[(size_t)c * nblk + i];
-        s += v.x;
-        m = fmax(m, v.y);
-    }
-    __shared__ double ss[RED_TPB], sm[RED_TPB];
-    ss[threadIdx.x] = s;
-    sm[threadIdx.x] = m;
-    __syncthreads();
-    for (int h = RED_TPB / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            ss[threadIdx.x] += ss[threadIdx.x + h];
-            sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + h]);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[c] = make_double2(ss[0], sm[0]);
-}
-
 // ---- multilevel ----------------------------------------------------------------------
 // Four consecutive values of storage type T as floats (one 8- or 16-byte load
 // where the row allows it).
@@ -978,9 +1049,29 @@ int res64_blocks(int H, int W) {
     return (int)(g.x * g.y);
 }
 
+// One wave of resident blocks of a V_TPB-thread kernel on the current device
+// (0 if the device cannot be queried).
+template <typename K>
+int wave_blocks(K kernel) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, V_TPB, 0) != cudaSuccess)
+        return 0;
+    return sms * std::max(per, 1);
+}
+
+// Blocks per channel (or per segment) of a grid-stride pass over `tiles`
+// tiles with `groups` channels: about one wave in all, at least one block per
+// group, at most one per tile.
+int stride_blocks(int wave, int groups, int tiles) { return std::max(1, std::min(tiles, wave / std::max(groups, 1))); }
+
 cudaError_t launch_res64(const Res64Args& a, cudaStream_t st) {
-    const dim3 grid = grid_res(a.H, a.W, a.C);
-    if (a.nblk != (int)(grid.x * grid.y)) return cudaErrorInvalidValue;
+    const dim3 tiles = grid_res(a.H, a.W, 1);
+    if (a.nblk < (int)(tiles.x * tiles.y)) return cudaErrorInvalidValue;
+    const int wave = wave_blocks(res64_kernel<float>);
+    if (wave <= 0) return cudaErrorInvalidDevice;
+    const dim3 grid(stride_blocks(wave, a.C, (int)(tiles.x * tiles.y)), 1, a.C);
     if (a.out != nullptr && a.ticket == nullptr) return cudaErrorInvalidValue;
     if (a.sel != nullptr && a.u1 == nullptr) return cudaErrorInvalidValue;
     ResVec v;
@@ -997,39 +1088,25 @@ cudaError_t launch_res64(const Res64Args& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-int ref_norm_part_words(int H, int W, int nl) {
-    int n = 0;
-    for (int l = 0; l < nl; ++l) {
-        n += res64_blocks(H, W);
-        H = (H + 1) / 2;
-        W = (W + 1) / 2;
-    }
-    return n;
-}
+int ref_norm_part_words(int H, int W, int nl) { return nl * res64_blocks(H, W); }
 
 cudaError_t launch_ref_norms(RefNormArgs a, cudaStream_t st) {
     if (a.nl < 1 || a.nl > kRefMaxLevels || a.C < 1 || a.part == nullptr || a.ticket == nullptr)
         return cudaErrorInvalidValue;
-    int blocks = 0, part = 0;
     for (int l = 0; l < a.nl; ++l) {
         RefLevel& L = a.lv[l];
         const dim3 g = grid_res(L.H, L.W, 1);
         L.gx = (int)g.x;
         L.gy = (int)g.y;
-        L.block0 = blocks;
-        L.part0 = part;
         L.mvec = vec_ok(L.mask, L.mp, 0, 1) ? 1 : 0;
         if (!vec_ok(L.f, L.fp, L.fplane, 4) || L.out == nullptr || L.sqrt_out == nullptr) return cudaErrorInvalidValue;
-        blocks += L.gx * L.gy * a.C;
-        part += L.gx * L.gy * a.C;
     }
-    if (part > a.part_capacity) return cudaErrorInvalidValue;
-    ref_norms_kernel<<<blocks, dim3(V_TX, V_TY), 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reduce_part(const double2* part, int nblk, int C, double2* out, cudaStream_t st) {
-    reduce_part_kernel<<<C, RED_TPB, 0, st>>>(part, nblk, out);
+    const int wave = wave_blocks(ref_norms_kernel);
+    if (wave <= 0) return cudaErrorInvalidDevice;
+    // the blocks per segment suit the finest level, whose segments hold most tiles
+    const int gx = stride_blocks(wave, a.C, a.lv[0].gx * a.lv[0].gy);
+    if ((long long)gx * a.nl * a.C > a.part_capacity) return cudaErrorInvalidValue;
+    ref_norms_kernel<<<dim3(gx, a.nl * a.C), dim3(V_TX, V_TY), 0, st>>>(a);
     return cudaGetLastError();
 }
 

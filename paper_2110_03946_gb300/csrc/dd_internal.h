@@ -269,8 +269,10 @@ cudaError_t launch_reset_known(int H, int W, int C, float* u, int up, long long 
                                cudaStream_t st);
 
 // Residual r = b - A u of an FP32 iterate on unknown pixels (0 on known),
-// formed with error-free FP32 transformations (~48-bit significand); per
-// channel sum r^2 and max |r| per block into part[c*nblk + blk] (double2).
+// formed with error-free FP32 transformations (~48-bit significand).  The
+// pass's blocks (about one wave, at most nblk per channel) walk the tiles
+// grid-stride and write per channel their sums {r^2, max |r|} to
+// part[c*nblk + blk] (double2).
 // If g_out != nullptr, also writes g_out = r * scale_inv[c] in storage `gst`.
 struct Res64Args {
     int H, W, C;
@@ -278,7 +280,7 @@ struct Res64Args {
     const uint8_t* mask; int mp;
     void* g_out; Store gst; int gp; long long gplane;
     const double* scale_inv;   // device, per channel (only with g_out)
-    double2* part; int nblk;   // nblk = res64_blocks(H, W) per channel
+    double2* part; int nblk;   // partial stride per channel, at least res64_blocks(H, W)
     // optional, fused: the last block writes out[c] = {sum r^2, max |r|} (and
     // sqrt_out[c] = sqrt(sum) if given); ticket: a zero device counter, left zero
     double2* out; double* sqrt_out; unsigned int* ticket;
@@ -297,15 +299,15 @@ cudaError_t launch_res64(const Res64Args& a, cudaStream_t st);
 // rows), mask (H x mp bytes), and the outputs out[c] = {sum r^2, 0} and
 // sqrt_out[c].  part: part_capacity doubles of block partials (at least
 // C * ref_norm_part_words(H, W, nl) for the level sizes halving from H x W);
-// ticket: a zero device counter, left zero.  The launcher fills the block and
-// partial offsets.
+// ticket: a zero device counter, left zero.  The launcher fills each level's
+// tile grid (gx, gy) and mask access mode.
 constexpr int kRefMaxLevels = 8;
 struct RefLevel {
     const float* f; int fp; long long fplane;
     const uint8_t* mask; int mp;
     int H, W;
     double2* out; double* sqrt_out;
-    int gx, gy, block0, part0, mvec;   // set by launch_ref_norms
+    int gx, gy, mvec;   // set by launch_ref_norms
 };
 struct RefNormArgs {
     RefLevel lv[kRefMaxLevels];
@@ -316,8 +318,6 @@ struct RefNormArgs {
 int ref_norm_part_words(int H, int W, int nl);
 cudaError_t launch_ref_norms(RefNormArgs a, cudaStream_t st);
 
-// Reduce per-block partials: out[c] = {sum over blocks, max over blocks}.
-cudaError_t launch_reduce_part(const double2* part, int nblk, int C, double2* out, cudaStream_t st);
 
 // Dyadic restriction (Sec. 4): mask OR over 2x2, mean of known values.
 cudaError_t launch_restrict(int H, int W, int C, const uint8_t* mask, int mp, const float* f, int fp,

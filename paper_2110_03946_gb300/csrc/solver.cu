@@ -1776,19 +1776,27 @@ int dd_residual_norms(int H, int W, int C, const uint8_t* mask, const float* f, 
     const int nblk = dd::res64_blocks(H, W);
     double2* part = nullptr;
     double2* outd = nullptr;
+    unsigned int* ticket = nullptr;
     float* u0 = nullptr;
     std::vector<double2> hout(C);
     auto cleanup = [&]() {
         if (part) cudaFree(part);
         if (outd) cudaFree(outd);
+        if (ticket) cudaFree(ticket);
         if (u0) cudaFree(u0);
     };
     if (cudaMalloc(&part, sizeof(double2) * nblk * C) != cudaSuccess ||
         cudaMalloc(&outd, sizeof(double2) * C) != cudaSuccess ||
+        cudaMalloc(&ticket, sizeof(unsigned int)) != cudaSuccess ||
         cudaMalloc(&u0, sizeof(float) * (size_t)C * H * W) != cudaSuccess) {
         cleanup();
         set_error("cudaMalloc failed");
         return DD_ENOMEM;
+    }
+    if (cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st) != cudaSuccess) {   // the passes leave it zero
+        cleanup();
+        set_error("cudaMemsetAsync failed");
+        return DD_ECUDA;
     }
     for (int pass = 0; pass < 2; ++pass) {
         double* dst = pass == 0 ? norms : ref_norms;
@@ -1802,7 +1810,8 @@ int dd_residual_norms(int H, int W, int C, const uint8_t* mask, const float* f, 
         dd::Res64Args a{};
         a.H = H; a.W = W; a.C = C; a.u = src; a.up = W; a.uplane = (long long)H * W;
         a.mask = mask; a.mp = W; a.g_out = nullptr; a.gst = Store::F32; a.part = part; a.nblk = nblk;
-        if (dd::launch_res64(a, st) != cudaSuccess || dd::launch_reduce_part(part, nblk, C, outd, st) != cudaSuccess ||
+        a.out = outd; a.ticket = ticket;
+        if (dd::launch_res64(a, st) != cudaSuccess ||
             cudaMemcpyAsync(hout.data(), outd, sizeof(double2) * C, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             cleanup();

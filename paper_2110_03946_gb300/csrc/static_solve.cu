@@ -57,7 +57,8 @@ constexpr size_t kOffFlag = kOffRef + align256(kMaxChannels * 8);
 constexpr size_t kOffState = kOffFlag + align256(dd::kFlagWords * 4);
 constexpr size_t kOffTol = kOffState + align256(4 * 4);
 constexpr size_t kOffCount = kOffTol + align256(8);
-constexpr size_t kScratchBytes = kOffCount + align256(8);
+constexpr size_t kOffTicket = kOffCount + align256(8);
+constexpr size_t kScratchBytes = kOffTicket + align256(4);
 
 }  // namespace
 
@@ -100,16 +101,17 @@ int scratch_base(unsigned char** out) {
     } while (0)
 
 // FP64 residual norms of an FP32 iterate; norms and maxima back on the host.
+// ticket: a zero counter (the pass leaves it zero).
 int res_norms(int H, int W, int C, const float* u, int P, const uint8_t* mask, double2* part, int nblk,
-              double2* out_d, double2* out_h, cudaStream_t st) {
+              double2* out_d, unsigned int* ticket, double2* out_h, cudaStream_t st) {
     dd::Res64Args a{};
     a.H = H; a.W = W; a.C = C;
     a.u = u; a.up = P; a.uplane = (long long)H * P;
     a.mask = mask; a.mp = W;
     a.g_out = nullptr; a.gst = dd::Store::F32;
     a.part = part; a.nblk = nblk;
+    a.out = out_d; a.ticket = ticket;
     SS_CK(dd::launch_res64(a, st));
-    SS_CK(dd::launch_reduce_part(part, nblk, C, out_d, st));
     SS_CK(cudaMemcpyAsync(out_h, out_d, sizeof(double2) * C, cudaMemcpyDeviceToHost, st));
     SS_CK(cudaStreamSynchronize(st));
     return DD_OK;
@@ -152,6 +154,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     int* flag = reinterpret_cast<int*>(base + kOffFlag);
     int* sstate = reinterpret_cast<int*>(base + kOffState);
     double* tol_d = reinterpret_cast<double*>(base + kOffTol);
+    unsigned int* ticket = reinterpret_cast<unsigned int*>(base + kOffTicket);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long plane = (long long)H * P;
 
@@ -166,7 +169,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
     SS_CK(dd::launch_masked_copy(H, W, C, values, W, (long long)H * W, mask, W, u[0], P, plane, st));
     SS_CK(dd::launch_build_tmask(g, mask, W, tmask, st));
     double2 h_res[kMaxChannels];
-    if (int rc = res_norms(H, W, C, u[0], P, mask, res_part, nblk, res_out, h_res, st); rc != DD_OK) return rc;
+    if (int rc = res_norms(H, W, C, u[0], P, mask, res_part, nblk, res_out, ticket, h_res, st); rc != DD_OK) return rc;
     double ref[kMaxChannels];
     for (int c = 0; c < C; ++c) ref[c] = std::sqrt(h_res[c].x);
     {
@@ -216,7 +219,7 @@ extern "C" int dd_inpaint_solve_static(int H, int W, int C, const uint8_t* mask,
             if (hflag[0] == 1 || last_probe) break;
         }
         // verify in FP64 on the iterate that is returned
-        if (int rc = res_norms(H, W, C, u[cur], P, mask, res_part, nblk, res_out, h_res, st); rc != DD_OK) return rc;
+        if (int rc = res_norms(H, W, C, u[cur], P, mask, res_part, nblk, res_out, ticket, h_res, st); rc != DD_OK) return rc;
         double worst = 0.0;
         for (int c = 0; c < C; ++c) worst = std::max(worst, std::sqrt(h_res[c].x) / (ref[c] > 0.0 ? ref[c] : 1.0));
         if (!std::isfinite(worst)) return fail(DD_ENUMERIC, "non-finite residual");

@@ -6,7 +6,7 @@ the FP64-accurate outer correction.  For profilers, e.g.
 ``ncu --metrics gpu__time_duration.sum`` (a launch list) or a
 ``--section MemoryWorkloadAnalysis`` capture of the streaming passes.
 
-python -m paper_2110_03946_gb300.profile_passes [--workload rgb4k_edge3] [--legs oras,correction,cg,fp16]
+python -m paper_2110_03946_gb300.profile_passes [--workload rgb4k_edge3] [--legs oras,correction,cg,cg_fine,fp16]
 """
 from __future__ import annotations
 
@@ -19,6 +19,9 @@ LEGS = {
     "oras": dict(precision="fp32"),
     "correction": dict(precision="fp32", ml_mode="correction", correction_sweeps=2),
     "cg": dict(precision="fp32", solver="cg", max_sweeps=4000, coarse_sweeps=400),
+    # plain CG on the fine grid alone, a fixed 40 iterations (it does not converge):
+    # the fine-level operator and update passes at full size
+    "cg_fine": dict(precision="fp32", solver="cg", levels=1, max_sweeps=40),
     "fp16": dict(precision="fp16_ref"),
 }
 
@@ -44,7 +47,7 @@ def main():
     for leg in a.legs.split(","):
         prm = dict(base, device_loop=0, **LEGS[leg])
         with Inpainter(md, fd, device=dev, **prm) as ip:
-            ip.solve(a.tol)
+            ip.solve(a.tol, allow_unconverged=leg == "cg_fine")
             torch.cuda.synchronize()
             st = ip.stats()
         print(f"{leg}: sweeps {st['sweeps_per_level']} corrections {st['corrections']} "
