@@ -168,6 +168,11 @@ def main():
                     help="sample frames of mixed masks, e.g. 0.02:edge,0.04:uniform,0.08:edge (density:pattern per "
                          "frame; the cache key takes --density)")
     ap.add_argument("--frames", type=int, default=3)
+    ap.add_argument("--holdout", type=int, default=0,
+                    help="held-out frames per sample mask (new seeds): the tuned winner is kept only if it also "
+                         "beats the previous entry and the given fallbacks on them")
+    ap.add_argument("--fallback", action="append", default=[],
+                    help="JSON parameter set that the held-out check compares against (repeatable)")
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--budget", type=float, default=120.0, help="seconds")
@@ -201,12 +206,32 @@ def main():
         start = dict(START, **start)
     best, ms, seen = autotune(frames, a.precision, a.tol, a.budget, space=space, start=start,
                               log=lambda s: print(s, flush=True))
+    entry = {"params": best, "ms_per_frame": ms, "trials": len(seen), "workload": w.name,
+             "pattern": w.pattern,
+             "sample_seeds": [w.seed_base + 50 + j for j in range(len(masks))],
+             "sample_masks": [f"{d:g}:{pat}" for d, pat in masks]}
+    if a.holdout > 0:
+        # the winner against the start point and the fallbacks on frames it was not tuned on
+        held = []
+        for r in range(a.holdout):
+            for j, (dens, pat) in enumerate(masks):
+                f, m = synth.make_frame(w.H, w.W, w.C, dens, pat, w.seed_base + 150 + 16 * r + j)
+                held.append((torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev)))
+        trial = _Trial(held, a.precision, a.tol)
+        cands = [("tuned", best)] + ([("start", start)] if start else [])
+        cands += [(f"fallback{i}", dict(START, **json.loads(fb))) for i, fb in enumerate(a.fallback)]
+        scored = []
+        for name, prm in cands:
+            hms = trial(prm)
+            print(f"held-out {hms:9.3f} ms  {name} {prm}", flush=True)
+            scored.append((hms, name, prm))
+        hms, name, prm = min(scored, key=lambda t: t[0])
+        entry.update(params=prm, holdout_ms_per_frame=hms, holdout_winner=name,
+                     holdout_seeds=[w.seed_base + 150 + 16 * r + j for r in range(a.holdout)
+                                    for j in range(len(masks))])
+        best, ms = prm, hms
     cache = load_cache(a.out)
-    cache[cache_key(w.H, w.W, w.C, w.density, a.precision, a.tol)] = {
-        "params": best, "ms_per_frame": ms, "trials": len(seen), "workload": w.name,
-        "pattern": w.pattern,
-        "sample_seeds": [w.seed_base + 50 + j for j in range(len(masks))],
-        "sample_masks": [f"{d:g}:{pat}" for d, pat in masks]}
+    cache[cache_key(w.H, w.W, w.C, w.density, a.precision, a.tol)] = entry
     with open(a.out, "w") as fh:
         json.dump(cache, fh, indent=1, sort_keys=True)
     print(json.dumps({"best": best, "ms_per_frame": ms, "trials": len(seen)}))
