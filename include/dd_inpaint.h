@@ -61,7 +61,8 @@ extern "C" {
 /* multilevel modes */
 #define DD_ML_CASCADE     0  /* coarse-to-fine initialisation (Sec. 4) */
 #define DD_ML_CORRECTION  1  /* cascade initialisation, then a coarse-grid correction of the residual
-                                after each fine sweep (FP32, ORAS, levels >= 2) */
+                                after each fine sweep, or only after the sweeps that follow a slow
+                                pass (params.correction_trigger; FP32, ORAS, levels >= 2) */
 
 /* precision modes (storage of the Schwarz iterate; arithmetic is FP32) */
 #define DD_PREC_FP32      0  /* plain FP32 ORAS on u, FP64-verified stop test */
@@ -112,6 +113,13 @@ typedef struct dd_params {
                                 for a hung copy.  The solve then ends with DD_ETIMEOUT (the
                                 copies in flight are waited for, nothing faults) and the handle
                                 stays usable.  It exercises the timeout path without a fault */
+    double correction_trigger; /* DD_ML_CORRECTION: 0 (default) corrects after every fine sweep.  In
+                                (0, 1): a fine sweep is followed by the correction only when the
+                                pass before it reduced the fine relative residual by less than this
+                                factor (w_n > trigger w_{n-1}), i.e. once plain sweeps have slowed
+                                down to the contraction of a smooth error mode that the coarse grid
+                                removes; other sweeps run alone.  Decided on the device; inside
+                                device loops the correction is a conditional graph node */
 } dd_params;
 
 #define DD_MAX_STAT_CHANNELS 16
@@ -141,6 +149,8 @@ typedef struct dd_stats {
                                                   dd_inpaint_solve_finish continued under host control,
                                                   rewriting u_out (work enqueued on the stream after
                                                   dd_inpaint_solve_async saw the earlier result) */
+    int    coarse_corrections;                 /* DD_ML_CORRECTION: coarse-grid corrections applied to
+                                                  the fine iterate in the last solve */
 } dd_stats;
 
 /* Fill *p with the defaults listed above. */

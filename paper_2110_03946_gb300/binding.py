@@ -43,6 +43,7 @@ class dd_params(ctypes.Structure):
         ("max_corrections", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("timing", ctypes.c_int),
         ("tile_warps", ctypes.c_int), ("solver", ctypes.c_int), ("correction_sweeps", ctypes.c_int),
         ("local_rtol", ctypes.c_double), ("device_loop", ctypes.c_int), ("test_stall_polls", ctypes.c_int),
+        ("correction_trigger", ctypes.c_double),
     ]
 
 
@@ -55,7 +56,7 @@ class dd_stats(ctypes.Structure):
         ("local_unknowns", ctypes.c_longlong), ("fine_sweep_launches", ctypes.c_int),
         ("fine_sweep_ms", ctypes.c_double),
         ("fine_cg_pixel_steps", ctypes.c_longlong), ("fine_swept_unknowns", ctypes.c_longlong),
-        ("host_continued", ctypes.c_int),
+        ("host_continued", ctypes.c_int), ("coarse_corrections", ctypes.c_int),
     ]
 
 

@@ -1195,30 +1195,56 @@ cudaError_t launch_restrict_sum(int H, int W, int C, const float* src, int sp, l
     return cudaGetLastError();
 }
 
-// gate[0] = 1 if this pass's correction is skipped: the fine stop flag is set,
-// or corrections were switched off; gate[1] = off.  Corrections are switched
-// off once the fine residual (the worst relative residual of the latest full
-// sweep's input, norms2[2C]) fell by less than the factor kGateRatio since
-// the previous pass.  prev[0] holds that previous residual.
+// The decision, after a fine sweep, whether the coarse-grid correction follows
+// it.  gate: [0] skip this pass's correction, [1] corrections off for the rest
+// of the solve, [2] corrections applied, [3] full fine sweeps seen at the last
+// decision, [4] the last full pass was corrected.  prev[0]: the fine residual w
+// at the last full pass (w = norms2[2C], the worst relative residual of the
+// latest full sweep's input, i.e. of the previous pass's output).
+//  - A probe pass (state[1], the count of full sweeps, did not grow) changed
+//    no iterate: no correction, no history.
+//  - Corrections are switched off once a corrected pass reduced w by less than
+//    kGateRatio: with the non-symmetric ORAS smoother the corrected iteration
+//    can still grow slowly where plain ORAS converges.
+//  - trigger > 0: a sweep is corrected only if the pass before it reduced w by
+//    less than trigger (a slow pass: the residual is dominated by a smooth mode
+//    that the sweeps contract slowly); the first pass has no history and is not
+//    corrected.  trigger = 0: every pass is corrected.
+// has_cond: also set the condition of the graph IF node that holds the
+// correction (1 = run it).
 constexpr double kGateRatio = 0.7;
 
 __global__ void corr_gate_kernel(const int* __restrict__ flag, const double* __restrict__ norms2, int C,
-                                 int* __restrict__ gate, double* __restrict__ prev) {
+                                 const int* __restrict__ state, int* __restrict__ gate, double* __restrict__ prev,
+                                 double trigger, int has_cond, cudaGraphConditionalHandle cond) {
     if (threadIdx.x != 0) return;
     int skip = flag[0] != 0 || gate[1] != 0;
     if (!skip) {
-        const double w = norms2[2 * C];
-        if (prev[0] > 0.0 && !(w <= kGateRatio * prev[0])) {
-            gate[1] = 1;
-            skip = 1;
+        const int nfull = state[1];
+        if (nfull == gate[3]) {
+            skip = 1;   // a probe
+        } else {
+            gate[3] = nfull;
+            const double w = norms2[2 * C], wp = prev[0];
+            if (wp > 0.0 && gate[4] != 0 && !(w <= kGateRatio * wp)) {
+                gate[1] = 1;
+                skip = 1;
+            } else if (trigger > 0.0 && !(wp > 0.0 && w > trigger * wp)) {
+                skip = 1;
+            }
+            prev[0] = w;
+            gate[4] = skip ? 0 : 1;
         }
-        prev[0] = w;
     }
     gate[0] = skip;
+    if (!skip) gate[2] += 1;
+    if (has_cond) cudaGraphSetConditional(cond, skip ? 0u : 1u);
 }
 
-cudaError_t launch_corr_gate(const int* flag, const double* norms2, int C, int* gate, double* prev, cudaStream_t st) {
-    corr_gate_kernel<<<1, 32, 0, st>>>(flag, norms2, C, gate, prev);
+cudaError_t launch_corr_gate(const int* flag, const double* norms2, int C, const int* state, int* gate, double* prev,
+                             double trigger, const cudaGraphConditionalHandle* cond, cudaStream_t st) {
+    const cudaGraphConditionalHandle c = cond ? *cond : cudaGraphConditionalHandle{};
+    corr_gate_kernel<<<1, 32, 0, st>>>(flag, norms2, C, state, gate, prev, trigger, cond ? 1 : 0, c);
     return cudaGetLastError();
 }
 

@@ -220,7 +220,9 @@ cudaError_t launch_restrict_sum(int H, int W, int C, const float* src, int sp, l
 // off for the rest of the solve once the fine residual norms2[2C] fell by less
 // than a factor 0.7 since the previous pass (prev[0]).  gate and prev are reset
 // (to 0) before a solve's fine loop.
-cudaError_t launch_corr_gate(const int* flag, const double* norms2, int C, int* gate, double* prev, cudaStream_t st);
+// cond: NULL outside a graph; else the handle of the IF node holding the correction.
+cudaError_t launch_corr_gate(const int* flag, const double* norms2, int C, const int* state, int* gate, double* prev,
+                             double trigger, const cudaGraphConditionalHandle* cond, cudaStream_t st);
 
 // Energy-optimal step of the correction (omega = (r, d) / (d, A d) per channel):
 // corr_dir: d = bilinear prolongation of the coarse correction on mask == 0

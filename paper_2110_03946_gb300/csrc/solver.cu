@@ -159,8 +159,9 @@ struct dd_inpaint {
     double* norms2_c = nullptr;     // 2C + 2
     double* tol_c = nullptr;        // 1
     double* corr_dots = nullptr;    // 3C: (r, d), (d, A d), omega
-    int* corr_gate = nullptr;       // [0] skip this pass's correction, [1] corrections off
-    double* corr_prev = nullptr;    // the fine residual at the previous pass
+    int* corr_gate = nullptr;       // kGateWords: [0] skip this pass's correction, [1] corrections off,
+                                    // [2] corrections applied, [3]-[4] history (corr_gate_kernel)
+    double* corr_prev = nullptr;    // the fine residual at the previous full pass
     cudaStream_t cap_stream = nullptr;   // private stream on which loop bodies are captured
     cudaStream_t cap_stream2 = nullptr;  // ... and the bodies of loops nested in them
     // device-driven FP64 correction loop (precision != FP32, device_loop = 1)
@@ -247,6 +248,9 @@ int alloc_flag(dd_inpaint* h, int** f) {
 // Words of the work counters of timed sweeps: two sums and one kind per launch.
 constexpr int kWorkWords = 2 + dd::kTimedLaunches;
 
+// Words of the coarse-grid correction's gate (corr_gate_kernel).
+constexpr int kGateWords = 8;
+
 // The sticky error word shared by all sweep sequences of a handle.
 int* err_word(dd_inpaint* h) { return h->flag_d + 5; }
 
@@ -311,6 +315,10 @@ int validate(int H, int W, int C, const dd_params& p) {
     }
     if (!(p.local_rtol >= 0.0) || !(p.local_rtol < 1.0)) {
         set_error("local_rtol must be in [0, 1)");
+        return DD_EINVAL;
+    }
+    if (!(p.correction_trigger >= 0.0) || !(p.correction_trigger < 1.0)) {
+        set_error("correction_trigger must be in [0, 1)");
         return DD_EINVAL;
     }
     return DD_OK;
@@ -521,15 +529,18 @@ bool loop_mode(const dd_inpaint* h, bool timed) { return h->prm.device_loop != 0
 // Whether fine passes end with the coarse-grid correction.
 bool corrects(const dd_inpaint* h) { return h->prm.ml_mode == DD_ML_CORRECTION && h->lv.size() >= 2; }
 
-// Kernels of the coarse-grid correction after one fine sweep.
+// Kernels of the coarse-grid correction after one fine sweep, without its gate.
 int correction_kernels(const dd_inpaint* h) {
     const int nl = (int)h->lv.size();
-    return 1 + 1 + (nl - 1) + 1 + h->prm.correction_sweeps + (nl - 2) + 3;
+    return 1 + (nl - 1) + 1 + h->prm.correction_sweeps + (nl - 2) + 3;
 }
 
+// Kernels of one pass of a device loop: the sweep (or CG's two), the loop
+// control and, on a correcting fine level, the correction's gate; the
+// corrections the gate let run are counted apart (count_loop_launches).
 int pass_kernels_of(const dd_inpaint* h, const Level& L) {
     if (h->prm.solver == DD_SOLVER_CG) return 3;
-    return 2 + ((&L == &h->lv[0] && corrects(h)) ? correction_kernels(h) : 0);
+    return 2 + ((&L == &h->lv[0] && corrects(h)) ? 1 : 0);
 }
 
 dd::CGArgs cg_args(const dd_inpaint* h, const Level& L) {
@@ -563,11 +574,19 @@ dd::CGArgs cg_args(const dd_inpaint* h, const Level& L) {
 // corrections off for the rest of the solve once a pass reduced the fine
 // residual by less than a factor 0.7: with the non-symmetric ORAS smoother
 // the corrected iteration can still grow slowly, where plain ORAS converges.
-int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
+// The gate runs first (enqueue_correction_gate); cond: NULL for plain launches,
+// whose correction kernels then each return at once when the gate says skip,
+// else the handle of the graph IF node that holds the correction body.
+int enqueue_correction_gate(dd_inpaint* h, cudaStream_t st, const cudaGraphConditionalHandle* cond) {
+    DD_CK(dd::launch_corr_gate(h->flag_d, h->norms2_d, h->C, h->sstate_d, h->corr_gate, h->corr_prev,
+                               h->prm.correction_trigger, cond, st));
+    return DD_OK;
+}
+
+int enqueue_correction_body(dd_inpaint* h, cudaStream_t st) {
     const int nl = (int)h->lv.size();
     Level& F = h->lv[0];
     Level& Lc = h->lv[nl - 1];
-    DD_CK(dd::launch_corr_gate(h->flag_d, h->norms2_d, h->C, h->corr_gate, h->corr_prev, st));
     const int* skip = h->corr_gate;
     dd::Res64Args a{};
     a.H = F.H; a.W = F.W; a.C = h->C;
@@ -624,14 +643,61 @@ int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
     return DD_OK;
 }
 
+// The correction as plain launches: the gate and every kernel of the body.
+int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
+    DD_TRY(enqueue_correction_gate(h, st, nullptr));
+    return enqueue_correction_body(h, st);
+}
+
 // Corrections on, no residual history: before a solve's fine iterations.
 int reset_correction(dd_inpaint* h, cudaStream_t st) {
-    DD_CK(cudaMemsetAsync(h->corr_gate, 0, 2 * sizeof(int), st));
+    DD_CK(cudaMemsetAsync(h->corr_gate, 0, kGateWords * sizeof(int), st));
     DD_CK(cudaMemsetAsync(h->corr_prev, 0, sizeof(double), st));
     return DD_OK;
 }
 
-int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st, bool count_work = false) {
+int capture_append(cudaStream_t st, const std::function<int(cudaGraph_t, const cudaGraphNode_t*,
+                                                            const cudaGraphEdgeData*, size_t, cudaGraphNode_t*)>& add);
+
+// Inside the capture of a device loop's body (on st): the correction's gate,
+// which sets the condition of an IF node, and that IF node, whose body (the
+// correction kernels, captured on cap_stream2) runs only when the gate lets it.
+int add_gated_correction(dd_inpaint* h, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t body_graph = nullptr;
+    DD_CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &body_graph, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) {
+        set_error("gated correction: the stream is not capturing");
+        return DD_ECUDA;
+    }
+    cudaGraphConditionalHandle cond;
+    DD_CK(cudaGraphConditionalHandleCreate(&cond, body_graph, 0, 0));
+    DD_TRY(enqueue_correction_gate(h, st, &cond));
+    return capture_append(st, [&](cudaGraph_t g, const cudaGraphNode_t* deps, const cudaGraphEdgeData* edges,
+                                  size_t nd, cudaGraphNode_t* last) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        DD_CK(cudaGraphAddNode(&node, g, deps, edges, nd, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        DD_CK(cudaStreamBeginCaptureToGraph(h->cap_stream2, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue_correction_body(h, h->cap_stream2);
+        cudaGraph_t captured = body;
+        const cudaError_t ec = cudaStreamEndCapture(h->cap_stream2, &captured);
+        if (rc != DD_OK) return rc;
+        DD_CK(ec);
+        *last = node;
+        return DD_OK;
+    });
+}
+
+// in_graph: st is capturing a device loop's body (the correction becomes a
+// conditional node); otherwise plain launches.
+int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st, bool count_work = false, bool in_graph = false) {
     if (h->prm.solver == DD_SOLVER_CG) {
         DD_CK(dd::launch_cg_iteration(cg_args(h, L), st));
         return DD_OK;
@@ -640,7 +706,7 @@ int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st, bool count_work = fal
     const dd::SweepStop stop = make_stop(h, L.partial, L.ref_d, 0.0, count_work ? h->work_d : nullptr);
     DD_CK(dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), pair, nullptr, L.tmask, stop, h->prm.robin_p,
                            h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
-    if (&L == &h->lv[0] && corrects(h)) DD_TRY(enqueue_correction(h, st));
+    if (&L == &h->lv[0] && corrects(h)) DD_TRY(in_graph ? add_gated_correction(h, st) : enqueue_correction(h, st));
     return DD_OK;
 }
 
@@ -694,7 +760,7 @@ int add_loop(dd_inpaint* h, Level& L, int cap, cudaGraph_t g, const cudaGraphNod
     if (h->prm.solver == DD_SOLVER_ORAS) DD_CK(dd::prepare_sweep(Store::F32, L.geom, false));
     const int max_passes = h->prm.solver == DD_SOLVER_CG ? cap + 1 : 2 * cap + 2;
     return add_loop_fn(h, cap, max_passes, g, deps, edges, ndeps, h->cap_stream,
-                       [&](cudaStream_t bs) { return enqueue_pass(h, L, bs); }, last);
+                       [&](cudaStream_t bs) { return enqueue_pass(h, L, bs, false, true); }, last);
 }
 
 // Append nodes to the graph that st is capturing, after st's current
@@ -769,6 +835,7 @@ void count_loop_launches(dd_inpaint* h) {
         if (!h->lv[l].loop_pending) continue;
         h->lv[l].loop_pending = false;
         h->launches += (long long)h->h_state[4 * l + 3] * pass_kernels_of(h, h->lv[l]);
+        if (l == 0 && corrects(h)) h->launches += (long long)h->h_flag[6] * correction_kernels(h);
     }
 }
 
@@ -785,7 +852,7 @@ int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, 
     for (int i = 0; i < n; ++i) {
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
         DD_TRY(enqueue_pass(h, L, st, timed));
-        h->launches += pass_kernels_of(h, L) - 1;
+        h->launches += pass_kernels_of(h, L) - 1 + ((&L == &h->lv[0] && corrects(h)) ? correction_kernels(h) : 0);
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
     }
     DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, nullptr, L.state_d, st));
@@ -919,6 +986,7 @@ int enqueue_output_readback(dd_inpaint* h, float* u_out, double tol, cudaStream_
     DD_CK(cudaMemcpyAsync(h->h_flag + 3, err_word(h), sizeof(int), cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_ref, F.ref_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    if (corrects(h)) DD_CK(cudaMemcpyAsync(h->h_flag + 6, h->corr_gate + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
     if (timed)
         DD_CK(cudaMemcpyAsync(h->h_work, h->work_d, sizeof(unsigned long long) * kWorkWords, cudaMemcpyDeviceToHost,
                               st));
@@ -982,6 +1050,7 @@ int fp32_finish(dd_inpaint* h, cudaStream_t st) {
     if (h->h_flag[3] != 0) { set_error("a bounded device wait for a staged tile gave up"); return DD_ETIMEOUT; }
     if (h->pending_cascaded) take_level_stats(h);
     count_loop_launches(h);
+    h->stats.coarse_corrections = corrects(h) ? h->h_flag[6] : 0;
     const int status = h->h_state[2], applied = h->h_state[1];
     if (status == 2) { set_error("non-finite residual norm"); return DD_ENUMERIC; }
     const int n1 = first_chunk(h);
@@ -1459,7 +1528,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         if ((rc = dalloc_t(h, &h->norms2_c, (size_t)2 * C + 2)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &h->tol_c, 1)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &h->corr_dots, (size_t)3 * C)) != DD_OK) return fail(rc);
-        if ((rc = dalloc_t(h, &h->corr_gate, 2)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &h->corr_gate, kGateWords)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &h->corr_prev, 1)) != DD_OK) return fail(rc);
     }
     h->res_nblk = dd::res64_blocks(H, W);
@@ -1576,6 +1645,7 @@ void dd_params_default(dd_params* p) {
     p->device_loop = 1;
     p->correction_sweeps = 2;
     p->local_rtol = 0.0;
+    p->correction_trigger = 0.0;
 }
 
 const char* dd_strerror(int code) {
@@ -1730,7 +1800,7 @@ int dd_inpaint_sweep(dd_handle h, int n, double* rnorm_out, void* stream) {
                                       h->prm.robin_p, h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
         if (corrects(h)) {   // one pass of DD_ML_CORRECTION: the sweep, then the coarse-grid correction
             DD_TRY(enqueue_correction(h, st));
-            h->launches += correction_kernels(h);
+            h->launches += 1 + correction_kernels(h);
         }
         h->cur = 1 - h->cur;
     }

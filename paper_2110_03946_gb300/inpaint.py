@@ -19,7 +19,8 @@ def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_m
                 robin_p=None, precision=None, max_sweeps=None, coarse_tol=None, inner_tol=None,
                 max_corrections=None, coarse_sweeps=None, inputs_on_device=1, timing=None,
                 tile_warps=None, solver=None, device_loop=None, correction_sweeps=None,
-                local_rtol=None, coarse_factor=None, test_stall_polls=None) -> B.dd_params:
+                local_rtol=None, coarse_factor=None, test_stall_polls=None,
+                correction_trigger=None) -> B.dd_params:
     p = B.dd_params_default()
     if block is not None: p.block = int(block)
     if overlap is not None: p.overlap = int(overlap)
@@ -43,6 +44,7 @@ def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_m
     if local_rtol is not None: p.local_rtol = float(local_rtol)
     if coarse_factor is not None: p.coarse_factor = int(coarse_factor)
     if test_stall_polls is not None: p.test_stall_polls = int(test_stall_polls)
+    if correction_trigger is not None: p.correction_trigger = float(correction_trigger)
     p.inputs_on_device = int(inputs_on_device)
     return p
 
@@ -130,6 +132,7 @@ class Inpainter:
             "fine_cg_pixel_steps": int(s.fine_cg_pixel_steps),
             "fine_swept_unknowns": int(s.fine_swept_unknowns),
             "host_continued": bool(s.host_continued),
+            "coarse_corrections": int(s.coarse_corrections),
         }
 
     def close(self):
