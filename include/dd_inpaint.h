@@ -61,8 +61,8 @@ extern "C" {
 /* multilevel modes */
 #define DD_ML_CASCADE     0  /* coarse-to-fine initialisation (Sec. 4) */
 #define DD_ML_CORRECTION  1  /* cascade initialisation, then a coarse-grid correction of the residual
-                                after each fine sweep, or only after the sweeps that follow a slow
-                                pass (params.correction_trigger; FP32, ORAS, levels >= 2) */
+                                after each fine sweep, or after each one from the first slow pass on
+                                (params.correction_trigger; FP32, ORAS, levels >= 2) */
 
 /* precision modes (storage of the Schwarz iterate; arithmetic is FP32) */
 #define DD_PREC_FP32      0  /* plain FP32 ORAS on u, FP64-verified stop test */
@@ -114,12 +114,13 @@ typedef struct dd_params {
                                 copies in flight are waited for, nothing faults) and the handle
                                 stays usable.  It exercises the timeout path without a fault */
     double correction_trigger; /* DD_ML_CORRECTION: 0 (default) corrects after every fine sweep.  In
-                                (0, 1): a fine sweep is followed by the correction only when the
-                                pass before it reduced the fine relative residual by less than this
-                                factor (w_n > trigger w_{n-1}), i.e. once plain sweeps have slowed
-                                down to the contraction of a smooth error mode that the coarse grid
-                                removes; other sweeps run alone.  Decided on the device; inside
-                                device loops the correction is a conditional graph node */
+                                (0, 1): the fine sweeps run alone until the first pass that reduced
+                                the fine relative residual by less than this factor (w_n > trigger
+                                w_{n-1}): plain sweeps have slowed down to the contraction of a
+                                smooth error mode, which the coarse grid removes.  From the next
+                                sweep on every sweep is followed by the correction.  Decided on the
+                                device; in device loops the two phases are two graph loops, so the
+                                plain phase costs what the cascade alone does */
 } dd_params;
 
 #define DD_MAX_STAT_CHANNELS 16

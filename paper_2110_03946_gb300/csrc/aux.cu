@@ -1007,12 +1007,98 @@ __global__ void loop_begin_kernel(int* __restrict__ ctl, cudaGraphConditionalHan
     if (threadIdx.x == 0) cudaGraphSetConditional(cond, 1);
 }
 
+// The decision, after a fine sweep, whether the coarse-grid correction follows
+// it (returns 1 to skip it).  gate: [0] skip this pass's correction, [1]
+// corrections off for the rest of the solve, [2] corrections applied, [3] full
+// fine sweeps seen at the last decision, [4] the last full pass was corrected,
+// [5] the trigger has fired, [6] gate launches (counted by corr_gate_kernel).
+// prev[0]: the fine residual w at the last full pass (w = norms2[2C], the worst
+// relative residual of the latest full sweep's input, i.e. of the previous
+// pass's output).
+//  - A probe pass (state[1], the count of full sweeps, did not grow) changed
+//    no iterate: no correction, no history.
+//  - trigger > 0: until the first pass that reduced w by less than trigger (a
+//    slow pass: the residual is dominated by a smooth mode that the sweeps
+//    contract slowly) no pass is corrected; that pass sets [5], and every
+//    later pass is corrected.  trigger = 0: every pass is corrected.
+//  - Corrections are switched off once a corrected pass reduced w by less than
+//    kGateRatio: with the non-symmetric ORAS smoother the corrected iteration
+//    can still grow slowly where plain ORAS converges.  After a trigger the
+//    bound is the larger of kGateRatio and the contraction of the slow pass
+//    that fired it (prev[1]): corrected passes stay on while they beat the
+//    plain sweeps.
+constexpr double kGateRatio = 0.7;
+
+__device__ int corr_gate_decide(const int* __restrict__ flag, const double* __restrict__ norms2, int C,
+                                const int* __restrict__ state, int* __restrict__ gate, double* __restrict__ prev,
+                                double trigger) {
+    int skip = flag[0] != 0 || gate[1] != 0;
+    if (!skip) {
+        const int nfull = state[1];
+        if (nfull == gate[3]) {
+            skip = 1;   // a probe
+        } else {
+            gate[3] = nfull;
+            const double w = norms2[2 * C], wp = prev[0];
+            if (trigger > 0.0 && gate[5] == 0) {   // plain passes until a slow one
+                if (wp > 0.0 && w > trigger * wp) {
+                    gate[5] = 1;
+                    prev[1] = w / wp;
+                }
+                skip = 1;
+            } else if (wp > 0.0 && gate[4] != 0 && !(w <= fmax(kGateRatio, prev[1]) * wp)) {
+                gate[1] = 1;
+                skip = 1;
+            }
+            prev[0] = w;
+            gate[4] = skip ? 0 : 1;
+        }
+    }
+    gate[0] = skip;
+    if (!skip) gate[2] += 1;
+    return skip;
+}
+
+// The gate ahead of the correction kernels, which read gate[0].
+__global__ void corr_gate_kernel(const int* __restrict__ flag, const double* __restrict__ norms2, int C,
+                                 const int* __restrict__ state, int* __restrict__ gate, double* __restrict__ prev,
+                                 double trigger) {
+    if (threadIdx.x != 0) return;
+    gate[6] += 1;
+    (void)corr_gate_decide(flag, norms2, C, state, gate, prev, trigger);
+}
+
 __global__ void loop_ctl_kernel(const int* __restrict__ flag, const int* __restrict__ state, int* __restrict__ ctl,
                                 int cap, int max_passes, cudaGraphConditionalHandle cond) {
     if (threadIdx.x != 0) return;
     const int passes = ctl[0] + 1;
     ctl[0] = passes;
     if (flag[0] != 0 || state[1] >= cap || passes >= max_passes) cudaGraphSetConditional(cond, 0);
+}
+
+// Loop control of the plain phase of a fine level with a correction trigger
+// (body: sweep -> this kernel): the loop also ends once the trigger fires, and
+// the corrected phase's loop (loop_begin_corrected_kernel) takes over.
+__global__ void loop_ctl_trigger_kernel(const int* __restrict__ flag, const int* __restrict__ state,
+                                        int* __restrict__ ctl, int cap, int max_passes,
+                                        cudaGraphConditionalHandle cond, const double* __restrict__ norms2, int C,
+                                        int* __restrict__ gate, double* __restrict__ prev, double trigger) {
+    if (threadIdx.x != 0) return;
+    (void)corr_gate_decide(flag, norms2, C, state, gate, prev, trigger);
+    const int passes = ctl[0] + 1;
+    ctl[0] = passes;
+    if (flag[0] != 0 || state[1] >= cap || passes >= max_passes || gate[5] != 0) cudaGraphSetConditional(cond, 0);
+}
+
+// Entry of the corrected phase's loop: it runs only if the trigger fired and
+// the level is still iterating; the pass counter continues from the plain
+// phase, so both phases together stay within max_passes.
+__global__ void loop_begin_corrected_kernel(const int* __restrict__ ctl, const int* __restrict__ flag,
+                                            const int* __restrict__ state, const int* __restrict__ gate, int cap,
+                                            int max_passes, cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0) return;
+    const bool go = gate[5] != 0 && flag[0] == 0 && state[1] < cap && ctl[0] < max_passes;
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
 }
 
 }  // namespace
@@ -1195,56 +1281,9 @@ cudaError_t launch_restrict_sum(int H, int W, int C, const float* src, int sp, l
     return cudaGetLastError();
 }
 
-// The decision, after a fine sweep, whether the coarse-grid correction follows
-// it.  gate: [0] skip this pass's correction, [1] corrections off for the rest
-// of the solve, [2] corrections applied, [3] full fine sweeps seen at the last
-// decision, [4] the last full pass was corrected.  prev[0]: the fine residual w
-// at the last full pass (w = norms2[2C], the worst relative residual of the
-// latest full sweep's input, i.e. of the previous pass's output).
-//  - A probe pass (state[1], the count of full sweeps, did not grow) changed
-//    no iterate: no correction, no history.
-//  - Corrections are switched off once a corrected pass reduced w by less than
-//    kGateRatio: with the non-symmetric ORAS smoother the corrected iteration
-//    can still grow slowly where plain ORAS converges.
-//  - trigger > 0: a sweep is corrected only if the pass before it reduced w by
-//    less than trigger (a slow pass: the residual is dominated by a smooth mode
-//    that the sweeps contract slowly); the first pass has no history and is not
-//    corrected.  trigger = 0: every pass is corrected.
-// has_cond: also set the condition of the graph IF node that holds the
-// correction (1 = run it).
-constexpr double kGateRatio = 0.7;
-
-__global__ void corr_gate_kernel(const int* __restrict__ flag, const double* __restrict__ norms2, int C,
-                                 const int* __restrict__ state, int* __restrict__ gate, double* __restrict__ prev,
-                                 double trigger, int has_cond, cudaGraphConditionalHandle cond) {
-    if (threadIdx.x != 0) return;
-    int skip = flag[0] != 0 || gate[1] != 0;
-    if (!skip) {
-        const int nfull = state[1];
-        if (nfull == gate[3]) {
-            skip = 1;   // a probe
-        } else {
-            gate[3] = nfull;
-            const double w = norms2[2 * C], wp = prev[0];
-            if (wp > 0.0 && gate[4] != 0 && !(w <= kGateRatio * wp)) {
-                gate[1] = 1;
-                skip = 1;
-            } else if (trigger > 0.0 && !(wp > 0.0 && w > trigger * wp)) {
-                skip = 1;
-            }
-            prev[0] = w;
-            gate[4] = skip ? 0 : 1;
-        }
-    }
-    gate[0] = skip;
-    if (!skip) gate[2] += 1;
-    if (has_cond) cudaGraphSetConditional(cond, skip ? 0u : 1u);
-}
-
 cudaError_t launch_corr_gate(const int* flag, const double* norms2, int C, const int* state, int* gate, double* prev,
-                             double trigger, const cudaGraphConditionalHandle* cond, cudaStream_t st) {
-    const cudaGraphConditionalHandle c = cond ? *cond : cudaGraphConditionalHandle{};
-    corr_gate_kernel<<<1, 32, 0, st>>>(flag, norms2, C, state, gate, prev, trigger, cond ? 1 : 0, c);
+                             double trigger, cudaStream_t st) {
+    corr_gate_kernel<<<1, 32, 0, st>>>(flag, norms2, C, state, gate, prev, trigger);
     return cudaGetLastError();
 }
 
@@ -1288,6 +1327,16 @@ cudaError_t launch_loop_ctl(const int* flag, const int* state, int* ctl, int cap
     loop_ctl_kernel<<<1, 32, 0, st>>>(flag, state, ctl, cap, max_passes, cond);
     return cudaGetLastError();
 }
+
+cudaError_t launch_loop_ctl_trigger(const int* flag, const int* state, int* ctl, int cap, int max_passes,
+                                    cudaGraphConditionalHandle cond, const double* norms2, int C, int* gate,
+                                    double* prev, double trigger, cudaStream_t st) {
+    loop_ctl_trigger_kernel<<<1, 32, 0, st>>>(flag, state, ctl, cap, max_passes, cond, norms2, C, gate, prev,
+                                              trigger);
+    return cudaGetLastError();
+}
+
+const void* loop_begin_corrected_kernel_fn() { return reinterpret_cast<const void*>(&loop_begin_corrected_kernel); }
 
 cudaError_t launch_prolong_sel(int Hc, int Wc, int H, int W, int C, const float* uc0, const float* uc1,
                                const int* sel, int ucp, long long ucplane, const uint8_t* mask, int mp,

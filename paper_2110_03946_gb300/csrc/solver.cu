@@ -160,8 +160,10 @@ struct dd_inpaint {
     double* tol_c = nullptr;        // 1
     double* corr_dots = nullptr;    // 3C: (r, d), (d, A d), omega
     int* corr_gate = nullptr;       // kGateWords: [0] skip this pass's correction, [1] corrections off,
-                                    // [2] corrections applied, [3]-[4] history (corr_gate_kernel)
-    double* corr_prev = nullptr;    // the fine residual at the previous full pass
+                                    // [2] corrections applied, [3]-[5] history, [6] gate launches
+                                    // (corr_gate_kernel)
+    double* corr_prev = nullptr;    // [0] the fine residual at the previous full pass, [1] the contraction of
+                                    // the pass that fired the trigger
     cudaStream_t cap_stream = nullptr;   // private stream on which loop bodies are captured
     cudaStream_t cap_stream2 = nullptr;  // ... and the bodies of loops nested in them
     // device-driven FP64 correction loop (precision != FP32, device_loop = 1)
@@ -172,7 +174,8 @@ struct dd_inpaint {
     // pinned host mirrors
     double2* h_res = nullptr;
     double* h_small = nullptr;      // 3*C doubles scratch
-    int* h_flag = nullptr;          // [0..2] flag words, [3] error word, [4..5] sweep state
+    int* h_flag = nullptr;          // [0..2] flag words, [3] error word, [4..5] sweep state, [6] coarse
+                                    // corrections applied, [7] correction gate launches
     int* h_state = nullptr;         // 4 ints per level
     double* h_ref = nullptr;        // C: fine-level reference norms read back with a solve
     unsigned long long* h_cnt = nullptr;   // [0] unknown block pixels, [1] known pixels
@@ -535,12 +538,12 @@ int correction_kernels(const dd_inpaint* h) {
     return 1 + (nl - 1) + 1 + h->prm.correction_sweeps + (nl - 2) + 3;
 }
 
-// Kernels of one pass of a device loop: the sweep (or CG's two), the loop
-// control and, on a correcting fine level, the correction's gate; the
-// corrections the gate let run are counted apart (count_loop_launches).
+// Kernels of one pass of a device loop: the sweep (or CG's two) and the loop
+// control; on a correcting fine level the correction kernels (gate and body)
+// are counted apart, from the gate's launch count (count_loop_launches).
 int pass_kernels_of(const dd_inpaint* h, const Level& L) {
-    if (h->prm.solver == DD_SOLVER_CG) return 3;
-    return 2 + ((&L == &h->lv[0] && corrects(h)) ? 1 : 0);
+    (void)L;
+    return h->prm.solver == DD_SOLVER_CG ? 3 : 2;
 }
 
 dd::CGArgs cg_args(const dd_inpaint* h, const Level& L) {
@@ -574,15 +577,8 @@ dd::CGArgs cg_args(const dd_inpaint* h, const Level& L) {
 // corrections off for the rest of the solve once a pass reduced the fine
 // residual by less than a factor 0.7: with the non-symmetric ORAS smoother
 // the corrected iteration can still grow slowly, where plain ORAS converges.
-// The gate runs first (enqueue_correction_gate); cond: NULL for plain launches,
-// whose correction kernels then each return at once when the gate says skip,
-// else the handle of the graph IF node that holds the correction body.
-int enqueue_correction_gate(dd_inpaint* h, cudaStream_t st, const cudaGraphConditionalHandle* cond) {
-    DD_CK(dd::launch_corr_gate(h->flag_d, h->norms2_d, h->C, h->sstate_d, h->corr_gate, h->corr_prev,
-                               h->prm.correction_trigger, cond, st));
-    return DD_OK;
-}
-
+// The gate runs first (enqueue_correction) and the correction kernels each
+// return at once when it says skip.
 int enqueue_correction_body(dd_inpaint* h, cudaStream_t st) {
     const int nl = (int)h->lv.size();
     Level& F = h->lv[0];
@@ -645,59 +641,24 @@ int enqueue_correction_body(dd_inpaint* h, cudaStream_t st) {
 
 // The correction as plain launches: the gate and every kernel of the body.
 int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
-    DD_TRY(enqueue_correction_gate(h, st, nullptr));
+    DD_CK(dd::launch_corr_gate(h->flag_d, h->norms2_d, h->C, h->sstate_d, h->corr_gate, h->corr_prev,
+                               h->prm.correction_trigger, st));
     return enqueue_correction_body(h, st);
 }
 
 // Corrections on, no residual history: before a solve's fine iterations.
 int reset_correction(dd_inpaint* h, cudaStream_t st) {
     DD_CK(cudaMemsetAsync(h->corr_gate, 0, kGateWords * sizeof(int), st));
-    DD_CK(cudaMemsetAsync(h->corr_prev, 0, sizeof(double), st));
+    DD_CK(cudaMemsetAsync(h->corr_prev, 0, 2 * sizeof(double), st));
     return DD_OK;
 }
 
 int capture_append(cudaStream_t st, const std::function<int(cudaGraph_t, const cudaGraphNode_t*,
                                                             const cudaGraphEdgeData*, size_t, cudaGraphNode_t*)>& add);
 
-// Inside the capture of a device loop's body (on st): the correction's gate,
-// which sets the condition of an IF node, and that IF node, whose body (the
-// correction kernels, captured on cap_stream2) runs only when the gate lets it.
-int add_gated_correction(dd_inpaint* h, cudaStream_t st) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaGraph_t body_graph = nullptr;
-    DD_CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &body_graph, nullptr, nullptr, nullptr));
-    if (cs != cudaStreamCaptureStatusActive) {
-        set_error("gated correction: the stream is not capturing");
-        return DD_ECUDA;
-    }
-    cudaGraphConditionalHandle cond;
-    DD_CK(cudaGraphConditionalHandleCreate(&cond, body_graph, 0, 0));
-    DD_TRY(enqueue_correction_gate(h, st, &cond));
-    return capture_append(st, [&](cudaGraph_t g, const cudaGraphNode_t* deps, const cudaGraphEdgeData* edges,
-                                  size_t nd, cudaGraphNode_t* last) {
-        cudaGraphNodeParams cp{};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = cond;
-        cp.conditional.type = cudaGraphCondTypeIf;
-        cp.conditional.size = 1;
-        cudaGraphNode_t node = nullptr;
-        DD_CK(cudaGraphAddNode(&node, g, deps, edges, nd, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        DD_CK(cudaStreamBeginCaptureToGraph(h->cap_stream2, body, nullptr, nullptr, 0,
-                                            cudaStreamCaptureModeThreadLocal));
-        const int rc = enqueue_correction_body(h, h->cap_stream2);
-        cudaGraph_t captured = body;
-        const cudaError_t ec = cudaStreamEndCapture(h->cap_stream2, &captured);
-        if (rc != DD_OK) return rc;
-        DD_CK(ec);
-        *last = node;
-        return DD_OK;
-    });
-}
-
-// in_graph: st is capturing a device loop's body (the correction becomes a
-// conditional node); otherwise plain launches.
-int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st, bool count_work = false, bool in_graph = false) {
+// with_correction: a correcting fine level's sweep is followed by the
+// correction (its gate decides whether it does anything).
+int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st, bool count_work = false, bool with_correction = true) {
     if (h->prm.solver == DD_SOLVER_CG) {
         DD_CK(dd::launch_cg_iteration(cg_args(h, L), st));
         return DD_OK;
@@ -706,7 +667,7 @@ int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st, bool count_work = fal
     const dd::SweepStop stop = make_stop(h, L.partial, L.ref_d, 0.0, count_work ? h->work_d : nullptr);
     DD_CK(dd::launch_sweep(Store::F32, L.geom, h->C, L.plane(), pair, nullptr, L.tmask, stop, h->prm.robin_p,
                            h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
-    if (&L == &h->lv[0] && corrects(h)) DD_TRY(in_graph ? add_gated_correction(h, st) : enqueue_correction(h, st));
+    if (with_correction && &L == &h->lv[0] && corrects(h)) DD_TRY(enqueue_correction(h, st));
     return DD_OK;
 }
 
@@ -714,21 +675,33 @@ int enqueue_pass(dd_inpaint* h, Level& L, cudaStream_t st, bool count_work = fal
 // counter 0, condition 1), then a WHILE node whose body (pass(body_stream),
 // then the loop control) is captured on body_stream.  *last = the WHILE node.  The loop ends
 // when flag_d[0] is set, when sstate_d[1] reaches cap or after max_passes.
+// control (may be empty): launches the loop control in place of loop_ctl_kernel.
+// corrected_phase: the loop is the corrected phase of a fine level with a
+// correction trigger; its entry kernel lets it run only if the trigger fired,
+// and the pass counter continues from the plain phase.
 int add_loop_fn(dd_inpaint* h, int cap, int max_passes, cudaGraph_t g, const cudaGraphNode_t* deps,
                 const cudaGraphEdgeData* edges, size_t ndeps, cudaStream_t body_stream,
-                const std::function<int(cudaStream_t)>& pass, cudaGraphNode_t* last) {
+                const std::function<int(cudaStream_t)>& pass, cudaGraphNode_t* last,
+                const std::function<cudaError_t(cudaStream_t, cudaGraphConditionalHandle)>& control = {},
+                bool corrected_phase = false) {
     cudaGraphConditionalHandle cond;
     DD_CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
     // entry node: pass counter 0, condition 1 (re-armed on every entry when nested)
     int* ctl = h->ctl_d;
     void* kargs[2] = {&ctl, &cond};
+    const int* flag = h->flag_d;
+    const int* state = h->sstate_d;
+    const int* gate = h->corr_gate;
+    int cap_v = cap, maxp_v = max_passes;
+    void* kargs_c[7] = {&ctl, &flag, &state, &gate, &cap_v, &maxp_v, &cond};
     cudaGraphNodeParams kp{};
     kp.type = cudaGraphNodeTypeKernel;
-    kp.kernel.func = const_cast<void*>(dd::loop_begin_kernel_fn());
+    kp.kernel.func = const_cast<void*>(corrected_phase ? dd::loop_begin_corrected_kernel_fn()
+                                                       : dd::loop_begin_kernel_fn());
     kp.kernel.gridDim = dim3(1, 1, 1);
     kp.kernel.blockDim = dim3(32, 1, 1);
     kp.kernel.sharedMemBytes = 0;
-    kp.kernel.kernelParams = kargs;
+    kp.kernel.kernelParams = corrected_phase ? kargs_c : kargs;
     cudaGraphNode_t reset = nullptr, loop = nullptr;
     DD_CK(cudaGraphAddNode(&reset, g, deps, edges, ndeps, &kp));
     cudaGraphNodeParams cp{};
@@ -740,9 +713,10 @@ int add_loop_fn(dd_inpaint* h, int cap, int max_passes, cudaGraph_t g, const cud
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     DD_CK(cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const int rc = pass(body_stream);
-    const cudaError_t el = rc == DD_OK ? dd::launch_loop_ctl(h->flag_d, h->sstate_d, h->ctl_d, cap, max_passes, cond,
-                                                             body_stream)
-                                       : cudaSuccess;
+    const cudaError_t el = rc != DD_OK ? cudaSuccess
+                           : control ? control(body_stream, cond)
+                                 : dd::launch_loop_ctl(h->flag_d, h->sstate_d, h->ctl_d, cap, max_passes, cond,
+                                                       body_stream);
     cudaGraph_t captured = body;
     const cudaError_t ec = cudaStreamEndCapture(body_stream, &captured);
     if (rc != DD_OK) return rc;
@@ -759,8 +733,24 @@ int add_loop(dd_inpaint* h, Level& L, int cap, cudaGraph_t g, const cudaGraphNod
              const cudaGraphEdgeData* edges, size_t ndeps, cudaGraphNode_t* last) {
     if (h->prm.solver == DD_SOLVER_ORAS) DD_CK(dd::prepare_sweep(Store::F32, L.geom, false));
     const int max_passes = h->prm.solver == DD_SOLVER_CG ? cap + 1 : 2 * cap + 2;
+    if (&L == &h->lv[0] && corrects(h) && h->prm.correction_trigger > 0.0) {
+        // plain phase: sweep -> loop control, which also ends the loop when the
+        // trigger fires; then the corrected phase (sweep -> correction -> loop
+        // control), which runs only if it fired
+        cudaGraphNode_t plain = nullptr;
+        DD_TRY(add_loop_fn(
+            h, cap, max_passes, g, deps, edges, ndeps, h->cap_stream,
+            [&](cudaStream_t bs) { return enqueue_pass(h, L, bs, false, false); }, &plain,
+            [&](cudaStream_t bs, cudaGraphConditionalHandle cw) {
+                return dd::launch_loop_ctl_trigger(h->flag_d, h->sstate_d, h->ctl_d, cap, max_passes, cw,
+                                                   h->norms2_d, h->C, h->corr_gate, h->corr_prev,
+                                                   h->prm.correction_trigger, bs);
+            }));
+        return add_loop_fn(h, cap, max_passes, g, &plain, nullptr, 1, h->cap_stream,
+                           [&](cudaStream_t bs) { return enqueue_pass(h, L, bs); }, last, {}, true);
+    }
     return add_loop_fn(h, cap, max_passes, g, deps, edges, ndeps, h->cap_stream,
-                       [&](cudaStream_t bs) { return enqueue_pass(h, L, bs, false, true); }, last);
+                       [&](cudaStream_t bs) { return enqueue_pass(h, L, bs); }, last);
 }
 
 // Append nodes to the graph that st is capturing, after st's current
@@ -835,7 +825,7 @@ void count_loop_launches(dd_inpaint* h) {
         if (!h->lv[l].loop_pending) continue;
         h->lv[l].loop_pending = false;
         h->launches += (long long)h->h_state[4 * l + 3] * pass_kernels_of(h, h->lv[l]);
-        if (l == 0 && corrects(h)) h->launches += (long long)h->h_flag[6] * correction_kernels(h);
+        if (l == 0 && corrects(h)) h->launches += (long long)h->h_flag[7] * (1 + correction_kernels(h));
     }
 }
 
@@ -852,7 +842,7 @@ int enqueue_sweeps(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, 
     for (int i = 0; i < n; ++i) {
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i], st));
         DD_TRY(enqueue_pass(h, L, st, timed));
-        h->launches += pass_kernels_of(h, L) - 1 + ((&L == &h->lv[0] && corrects(h)) ? correction_kernels(h) : 0);
+        h->launches += pass_kernels_of(h, L) - 1 + ((&L == &h->lv[0] && corrects(h)) ? 1 + correction_kernels(h) : 0);
         if (timed && i < dd_inpaint::kFirst) DD_CK(cudaEventRecord(h->sw_ev[2 * i + 1], st));
     }
     DD_LAUNCH(h, dd::launch_resolve(h->flag_d, h->sstate_d, nullptr, L.state_d, st));
@@ -986,7 +976,10 @@ int enqueue_output_readback(dd_inpaint* h, float* u_out, double tol, cudaStream_
     DD_CK(cudaMemcpyAsync(h->h_flag + 3, err_word(h), sizeof(int), cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_ref, F.ref_d, sizeof(double) * h->C, cudaMemcpyDeviceToHost, st));
     DD_CK(cudaMemcpyAsync(h->h_cnt, h->count_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    if (corrects(h)) DD_CK(cudaMemcpyAsync(h->h_flag + 6, h->corr_gate + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (corrects(h)) {   // corrections applied, gate launches
+        DD_CK(cudaMemcpyAsync(h->h_flag + 6, h->corr_gate + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DD_CK(cudaMemcpyAsync(h->h_flag + 7, h->corr_gate + 6, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
     if (timed)
         DD_CK(cudaMemcpyAsync(h->h_work, h->work_d, sizeof(unsigned long long) * kWorkWords, cudaMemcpyDeviceToHost,
                               st));
@@ -1529,7 +1522,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         if ((rc = dalloc_t(h, &h->tol_c, 1)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &h->corr_dots, (size_t)3 * C)) != DD_OK) return fail(rc);
         if ((rc = dalloc_t(h, &h->corr_gate, kGateWords)) != DD_OK) return fail(rc);
-        if ((rc = dalloc_t(h, &h->corr_prev, 1)) != DD_OK) return fail(rc);
+        if ((rc = dalloc_t(h, &h->corr_prev, 2)) != DD_OK) return fail(rc);
     }
     h->res_nblk = dd::res64_blocks(H, W);
     // block partials: the residual passes (C x res_nblk double2) and the

@@ -3,10 +3,11 @@
 
 The cascade's fine sweeps contract fast until the residual is dominated by a
 smooth error mode, e.g. in a large unsampled region, which the local solves
-spread slowly (the multilevel argument of Sec. 4).  With a trigger, a sweep
-is followed by the coarse-grid correction only when the previous pass reduced
-the residual by less than the trigger factor.  Every result must still be the
-solution of Eq. eq:ls (the FP64 direct solve), within the FP32 tolerance."""
+spread slowly (the multilevel argument of Sec. 4).  With a trigger, the fine
+sweeps run alone until a pass reduces the residual by less than the trigger
+factor; from the next sweep on each sweep is followed by the coarse-grid
+correction.  Every result must still be the solution of Eq. eq:ls (the FP64
+direct solve), within the FP32 tolerance."""
 import numpy as np
 import pytest
 
@@ -77,7 +78,8 @@ def test_trigger_that_never_fires_gives_the_cascade_bit_for_bit():
 @pytest.mark.parametrize("trigger", [0.0, 0.5])
 def test_launches_and_device_loop_agree(trigger):
     """The gate decides the same on plain launches (kernels that return when
-    the gate says skip) and inside the device loop (a conditional node)."""
+    the gate says skip) and in the device loops (a plain-phase loop, then a
+    corrected-phase loop that runs only if the trigger fired)."""
     f, m = _hole_frame(160, 224, 3, 8)
     prm = dict(PRM, ml_mode="correction", correction_trigger=trigger)
     u_l, st_l = _solve(f, m, **prm, device_loop=1)
