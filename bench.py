@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--k", type=int, default=None, help="local CG steps per sweep")
     ap.add_argument("--robin", type=float, default=None)
     ap.add_argument("--coarse-tol", type=float, default=None)
+    ap.add_argument("--final-rtol", type=float, default=None,
+                    help="local CG tolerance of a sweep predicted to be a level's last (0 = off)")
     ap.add_argument("--no-tuned", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -81,7 +83,8 @@ def solver_params(args, precision):
             prm.update(t)
             src = "autotuned (paper_2110_03946_gb300/tuned.json)"
     for key, val in [("block", args.block), ("overlap", args.overlap), ("local_cg_iters", args.k),
-                     ("robin_p", args.robin), ("levels", args.levels), ("coarse_tol", args.coarse_tol)]:
+                     ("robin_p", args.robin), ("levels", args.levels), ("coarse_tol", args.coarse_tol),
+                     ("final_local_rtol", args.final_rtol)]:
         if val is not None:
             prm[key] = val
             src += f"; {key} overridden"
@@ -849,7 +852,7 @@ def run_ours(args):
         "config": {"workload": "rgb4k_edge3: 3840x2160x3, 3% edge-clustered mask, rel-res 1e-6",
                    "frames_in_flight": nmain,
                    "block": prm["block"], "overlap": prm["overlap"], "local_cg_iters": prm["local_cg_iters"],
-                   "local_rtol": prm.get("local_rtol", 0.0),
+                   "local_rtol": prm.get("local_rtol", 0.0), "final_local_rtol": prm.get("final_local_rtol", 0.0),
                    "levels": prm["levels"], "robin_p": prm["robin_p"], "coarse_tol": prm["coarse_tol"],
                    "params_source": tuned_src, "precision": args.precision, "frames_resident": args.frames,
                    "device_loop": args.device_loop,

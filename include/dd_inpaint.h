@@ -121,6 +121,13 @@ typedef struct dd_params {
                                 sweep on every sweep is followed by the correction.  Decided on the
                                 device; in device loops the two phases are two graph loops, so the
                                 plain phase costs what the cascade alone does */
+    double final_local_rtol; /* 0 (default): every sweep uses local_rtol.  In (0, 1): a sweep that the
+                                device stop test predicts to be a level's last one (its input
+                                residual, extrapolated from the last two sweeps, within a factor
+                                1/0.6 of the tolerance) ends its local CG once the local residual
+                                fell by this factor instead.  The last sweep only has to close a
+                                small gap, so looser local solves do; if it falls short, the
+                                following sweeps run as usual (the global test decides, Sec. 4) */
 } dd_params;
 
 #define DD_MAX_STAT_CHANNELS 16

@@ -108,6 +108,10 @@ struct SweepStop {
     // mbarrier that no copy completes, stall_polls times, and then gives up as
     // a hung copy would (the DD_ETIMEOUT path, exercised without a fault)
     int stall_polls;
+    // > 0: the local relative tolerance of a sweep that the stop test predicts
+    // to be the last one (its input residual within 1/kFinalContraction of tol);
+    // 0: every sweep uses the launch's local_rtol
+    float final_local_rtol;
 };
 constexpr int kTimedLaunches = 64;   // launches per sequence whose kind work[2 + i] records
 
@@ -142,7 +146,7 @@ struct SweepFrame {   // aligned as CUtensorMap (at least 64 bytes)
     long long plane;
     FastDiv dv_tiles, dv_ntx;
     int H, W, pitch, C, s, ntx, ntiles, has_g;
-    float p_robin, local_rtol2;
+    float p_robin, local_rtol2, local_rtol2_final;
     int k, stall_polls, force_probe;
     int cap;                   // batched levels: full sweeps after which the frame drops out
     double level_tol;          // batched levels: the stop tolerance launch_batch_reset sets

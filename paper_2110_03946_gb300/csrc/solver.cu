@@ -262,7 +262,7 @@ int* err_word(dd_inpaint* h) { return h->flag_d + 5; }
 dd::SweepStop make_stop(dd_inpaint* h, unsigned long long* partial, const double* ref_d, double stall,
                         unsigned long long* work = nullptr) {
     return dd::SweepStop{partial, h->norms2_d, ref_d, h->tol_d, stall, h->flag_d, h->sstate_d, 0,
-                         work, err_word(h), h->prm.test_stall_polls};
+                         work, err_word(h), h->prm.test_stall_polls, (float)h->prm.final_local_rtol};
 }
 
 // Clear the error word at the start of a solve (enqueued, so it also works in a capture).
@@ -322,6 +322,10 @@ int validate(int H, int W, int C, const dd_params& p) {
     }
     if (!(p.correction_trigger >= 0.0) || !(p.correction_trigger < 1.0)) {
         set_error("correction_trigger must be in [0, 1)");
+        return DD_EINVAL;
+    }
+    if (!(p.final_local_rtol >= 0.0) || !(p.final_local_rtol < 1.0)) {
+        set_error("final_local_rtol must be in [0, 1)");
         return DD_EINVAL;
     }
     return DD_OK;
@@ -1639,6 +1643,7 @@ void dd_params_default(dd_params* p) {
     p->correction_sweeps = 2;
     p->local_rtol = 0.0;
     p->correction_trigger = 0.0;
+    p->final_local_rtol = 0.0;
 }
 
 const char* dd_strerror(int code) {

@@ -45,6 +45,10 @@ namespace {
 // sweeps of history (probe prediction only: it decides whether the next launch
 // probes or sweeps, never whether the level has converged).
 constexpr double kFirstContraction = 0.3;
+// The residual contraction a final sweep with the looser local tolerance
+// (SweepStop::final_local_rtol) is counted on: the next sweep is such a final
+// sweep when its predicted input residual times this factor meets tol.
+constexpr double kFinalContraction = 0.6;
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kWaitLimit = 1 << 22;   // bounded mbarrier polls (a TMA copy takes ~1 us)
@@ -327,7 +331,10 @@ __device__ __forceinline__ void frame_stop_test(const SweepFrame& F, bool probe,
         const double pred = history ? worst * (worst / prev_worst) : worst * kFirstContraction;
         state[0] = cur ^ 1;
         state[1] += 1;
-        state[2] = (tol > 0.0 && pred <= tol) ? 1 : 0;
+        // 1: probe the next iterate; 2: the next sweep is predicted to be the last
+        // and takes the final local tolerance
+        state[2] = (tol > 0.0 && pred <= tol) ? 1
+                   : (tol > 0.0 && F.local_rtol2_final > 0.f && pred * kFinalContraction <= tol) ? 2 : 0;
     } else {
         state[2] = 0;   // the probe failed: sweep the same iterate in full
     }
@@ -445,6 +452,7 @@ oras_sweep_kernel(const __grid_constant__ SweepFrame one, const SweepFrame* __re
     const SweepFrame* Fp = nullptr;
     int f_cur = 0, f_kcg = 0, f_tiles = 0;
     int f_probe = 0;   // (ints rather than bools for the state kept across tiles: fewer live predicates)
+    float f_rtol2 = 0.f;   // the squared local tolerance of this frame's sweep
     // Residual sums of the input iterate per channel, exact (Fix128): lane
     // (it mod 32) holds the owned ||r||^2 of this CTA's tile it until every 32
     // tiles (or a change of channel) all lanes add their value into their own
@@ -508,7 +516,9 @@ oras_sweep_kernel(const __grid_constant__ SweepFrame one, const SweepFrame* __re
             q_pr = q;
             Fp = frame_at(q);
             f_cur = __ldcg(Fp->state);
-            f_probe = (Fp->force_probe != 0 || __ldcg(Fp->state + 2) != 0) ? 1 : 0;
+            const int req = __ldcg(Fp->state + 2);
+            f_probe = (Fp->force_probe != 0 || req == 1) ? 1 : 0;
+            f_rtol2 = req == 2 ? Fp->local_rtol2_final : Fp->local_rtol2;
             f_kcg = f_probe ? 0 : Fp->k;
         }
         const int local = t - begin_at(q);
@@ -652,7 +662,7 @@ oras_sweep_kernel(const __grid_constant__ SweepFrame one, const SweepFrame* __re
             const float2 both = tile_sum2<CF>(make_float2(s2, rr0), red[0], red[1], wt, lane);
             s2 = both.x;
             rr = both.y;
-            rr_stop = Fp->local_rtol2 * rr;
+            rr_stop = f_rtol2 * rr;
         }
         // the owned residual sum of this tile into the lane-batched accumulators
         if (c != cur_c) {
@@ -1285,6 +1295,7 @@ cudaError_t make_frame(SweepFrame* f, const TileGeom& g, int C, long long plane,
     f->has_g = map_g != nullptr ? 1 : 0;
     f->p_robin = p_robin;
     f->local_rtol2 = local_rtol * local_rtol;
+    f->local_rtol2_final = stop.final_local_rtol > 0.f ? stop.final_local_rtol * stop.final_local_rtol : 0.f;
     f->k = k;
     f->stall_polls = stop.stall_polls;
     f->force_probe = stop.force_probe;

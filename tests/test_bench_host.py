@@ -38,7 +38,7 @@ def test_sweep_flops_counts_steps_and_unknowns():
 
 def _args(**kw):
     base = dict(no_tuned=False, block=None, overlap=None, k=None, robin=None, levels=None, coarse_tol=None,
-                device_loop=1)
+                final_rtol=None, device_loop=1)
     base.update(kw)
     return argparse.Namespace(**base)
 
@@ -49,5 +49,7 @@ def test_solver_params_tuned_then_overrides():
     prm2, src2 = bench.solver_params(_args(overlap=5, k=12, device_loop=0), "fp32")
     assert prm2["overlap"] == 5 and prm2["local_cg_iters"] == 12 and prm2["device_loop"] == 0
     assert "overlap overridden" in src2 and "device loops off" in src2
+    prm4, src4 = bench.solver_params(_args(final_rtol=0.0), "fp32")
+    assert prm4["final_local_rtol"] == 0.0 and "final_local_rtol overridden" in src4
     prm3, src3 = bench.solver_params(_args(no_tuned=True), "fp32")
     assert prm3 == bench.PAPER_DEFAULTS and src3.startswith("defaults")

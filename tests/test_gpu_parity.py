@@ -132,6 +132,10 @@ SOLVE_CASES = [
     ("rgb_mlcg_3level", 200, 330, 3, dict(levels=3, precision="fp32", solver="cg", max_sweeps=2000,
                                           coarse_sweeps=200, coarse_tol=1e-3)),
     ("rgb_correction_3level", 200, 330, 3, dict(levels=3, precision="fp32", ml_mode="correction")),
+    # the sweep predicted to be a level's last with a looser local tolerance (device loops, and launches)
+    ("rgb_final_rtol", 200, 330, 3, dict(levels=3, precision="fp32", local_rtol=0.05, final_local_rtol=0.5)),
+    ("gray256_final_rtol_launches", 256, 256, 1, dict(levels=2, precision="fp32", local_rtol=0.05,
+                                                      final_local_rtol=0.35, device_loop=0)),
     ("gray256_correction_2level_launches", 256, 256, 1, dict(levels=2, precision="fp32", ml_mode="correction",
                                                              correction_sweeps=3, device_loop=0)),
     # two solved levels with a 1/8 coarse grid (two pass-through dyadic levels between them)
