@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--coarse-tol", type=float, default=None)
     ap.add_argument("--final-rtol", type=float, default=None,
                     help="local CG tolerance of a sweep predicted to be a level's last (0 = off)")
+    ap.add_argument("--ml-mode", default=None, choices=["cascade", "correction"])
+    ap.add_argument("--trigger", type=float, default=None, help="correction trigger (DD_ML_CORRECTION)")
+    ap.add_argument("--correction-cg", type=int, default=None,
+                    help="small-grid CG iteration cap of the coarse correction (0 = ORAS sweeps)")
     ap.add_argument("--no-tuned", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -84,7 +88,9 @@ def solver_params(args, precision):
             src = "autotuned (paper_2110_03946_gb300/tuned.json)"
     for key, val in [("block", args.block), ("overlap", args.overlap), ("local_cg_iters", args.k),
                      ("robin_p", args.robin), ("levels", args.levels), ("coarse_tol", args.coarse_tol),
-                     ("final_local_rtol", args.final_rtol)]:
+                     ("final_local_rtol", args.final_rtol), ("ml_mode", getattr(args, "ml_mode", None)),
+                     ("correction_trigger", getattr(args, "trigger", None)),
+                     ("correction_cg", getattr(args, "correction_cg", None))]:
         if val is not None:
             prm[key] = val
             src += f"; {key} overridden"
@@ -853,6 +859,8 @@ def run_ours(args):
                    "frames_in_flight": nmain,
                    "block": prm["block"], "overlap": prm["overlap"], "local_cg_iters": prm["local_cg_iters"],
                    "local_rtol": prm.get("local_rtol", 0.0), "final_local_rtol": prm.get("final_local_rtol", 0.0),
+                   "ml_mode": prm.get("ml_mode", "cascade"), "correction_trigger": prm.get("correction_trigger", 0.0),
+                   "correction_cg": prm.get("correction_cg", 0),
                    "levels": prm["levels"], "robin_p": prm["robin_p"], "coarse_tol": prm["coarse_tol"],
                    "params_source": tuned_src, "precision": args.precision, "frames_resident": args.frames,
                    "device_loop": args.device_loop,

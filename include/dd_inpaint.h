@@ -128,6 +128,12 @@ typedef struct dd_params {
                                 fell by this factor instead.  The last sweep only has to close a
                                 small gap, so looser local solves do; if it falls short, the
                                 following sweeps run as usual (the global test decides, Sec. 4) */
+    int    correction_cg;    /* DD_ML_CORRECTION: 0 (default) solves the coarse correction equation
+                                by correction_sweeps ORAS sweeps from zero.  > 0: by conjugate
+                                gradients on the coarsest level held in one SM's shared memory (one
+                                CTA per channel, FP64 dot products), at most this many iterations, to
+                                relative residual 1e-3; the coarsest level may then have at most
+                                12288 pixels (else DD_EINVAL at create; add levels) */
 } dd_params;
 
 #define DD_MAX_STAT_CHANNELS 16
@@ -355,6 +361,20 @@ int dd_restrict(int H, int W, int C, const uint8_t *mask, const float *f,
  */
 int dd_prolong(int Hc, int Wc, int H, int W, int C, const float *u_c, const uint8_t *mask,
                const float *f, float *u, void *stream);
+
+/*
+ * Small-grid coarse solve (the coarse problem of Sec. 4, the operator of
+ * Sec. 2 on a coarse grid): conjugate gradients on A e = g with e = 0 where
+ * mask != 0 (reflecting image borders, h = 1), from e = 0, until
+ * ||g - A e|| <= tol ||g|| or max_iter iterations.  One CTA per channel holds
+ * the grid in shared memory: H*W <= 12288.
+ *   mask (H*W bytes), g, e (C*H*W floats): DEVICE, dense;
+ *   iters: HOST array of C ints (iterations taken) or NULL.
+ * Enqueued on stream; with iters != NULL the call synchronises stream.
+ * Errors: DD_EINVAL (sizes, NULL pointers), DD_ECUDA.
+ */
+int dd_coarse_cg(int H, int W, int C, const uint8_t *mask, const float *g, float *e, int max_iter, double tol,
+                 int *iters, void *stream);
 
 /*
  * FP64 residual norms ||b - A u||_2 per channel of a float32 iterate u, and

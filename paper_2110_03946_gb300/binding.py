@@ -27,7 +27,7 @@ EXPORTS = (
     "dd_params_default", "dd_strerror", "dd_last_error",
     "dd_inpaint_create", "dd_inpaint_solve", "dd_inpaint_destroy", "dd_inpaint_set_data",
     "dd_inpaint_stats", "dd_inpaint_set_iterate", "dd_inpaint_get_iterate", "dd_inpaint_sweep",
-    "dd_restrict", "dd_prolong", "dd_residual_norms", "dd_inpaint_solve_static",
+    "dd_restrict", "dd_prolong", "dd_coarse_cg", "dd_residual_norms", "dd_inpaint_solve_static",
     "dd_inpaint_set_data_async", "dd_inpaint_solve_async", "dd_inpaint_query", "dd_inpaint_solve_finish",
     "dd_batch_create", "dd_batch_create_mode", "dd_batch_launch", "dd_batch_finish", "dd_batch_destroy",
     "dd_set_device_budget", "dd_device_bytes_in_use", "dd_fp32_fma_peak",
@@ -44,6 +44,7 @@ class dd_params(ctypes.Structure):
         ("tile_warps", ctypes.c_int), ("solver", ctypes.c_int), ("correction_sweeps", ctypes.c_int),
         ("local_rtol", ctypes.c_double), ("device_loop", ctypes.c_int), ("test_stall_polls", ctypes.c_int),
         ("correction_trigger", ctypes.c_double), ("final_local_rtol", ctypes.c_double),
+        ("correction_cg", ctypes.c_int),
     ]
 
 
@@ -89,6 +90,7 @@ def load(path: str | None = None):
         "dd_inpaint_sweep": (_I, [_P, _I, _P, _P]),
         "dd_restrict": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),
         "dd_prolong": (_I, [_I, _I, _I, _I, _I, _P, _P, _P, _P, _P]),
+        "dd_coarse_cg": (_I, [_I, _I, _I, _P, _P, _P, _I, _D, _P, _P]),
         "dd_residual_norms": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
         "dd_inpaint_solve_static": (_I, [_I, _I, _I, _P, _P, _P, ctypes.POINTER(dd_params), _D, _P]),
         "dd_inpaint_set_data_async": (_I, [_P, _P, _P, _I, _P]),
@@ -201,6 +203,13 @@ def dd_restrict(H, W, C, mask_ptr, f_ptr, mask_c_ptr, f_c_ptr, stream=None) -> i
 
 def dd_prolong(Hc, Wc, H, W, C, uc_ptr, mask_ptr, f_ptr, u_ptr, stream=None) -> int:
     return load().dd_prolong(Hc, Wc, H, W, C, uc_ptr, mask_ptr, f_ptr, u_ptr, _stream(stream))
+
+
+def dd_coarse_cg(H, W, C, mask_ptr, g_ptr, e_ptr, max_iter: int, tol: float, stream=None):
+    """Returns (code, list of C iteration counts)."""
+    it = (ctypes.c_int * C)()
+    rc = load().dd_coarse_cg(H, W, C, mask_ptr, g_ptr, e_ptr, int(max_iter), float(tol), it, _stream(stream))
+    return rc, list(it)
 
 
 def dd_inpaint_solve_static(H, W, C, mask_ptr, values_ptr, u_out_ptr, params, tol, stream=None) -> int:

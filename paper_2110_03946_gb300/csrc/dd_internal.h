@@ -214,6 +214,19 @@ cudaError_t launch_batch_resolve(const SweepFrame* frames, int n, const int* ctl
 cudaError_t launch_reset_sweep_state(int* state, int* flag, int cur, double* tol_d, double tol, cudaStream_t st,
                                      const int* skip_if = nullptr);
 
+// Small-grid coarse solve (coarse_cg.cu): CG on A_c e = g with e = 0 where
+// mask != 0, one CTA per channel, the grid in shared memory (H*W at most
+// kCoarseCgMaxPixels), FP32 vectors and FP64 dots, from e = 0 until
+// ||r|| <= tol ||g|| or max_iter iterations; iters (may be null): C ints, the
+// iterations taken; a no-op if skip != null and *skip != 0.  prepare_coarse_cg
+// sets the kernel's shared-memory limit (once per device, before any capture).
+constexpr int kCoarseCgMaxPixels = 12288;
+size_t coarse_cg_smem_bytes(int H, int W);
+cudaError_t prepare_coarse_cg();
+cudaError_t launch_coarse_cg(int H, int W, int C, const uint8_t* mask, int mp, const float* g, int gp,
+                             long long gplane, float* e, int ep, long long eplane, int max_iter, double tol,
+                             int* iters, const int* skip, cudaStream_t st);
+
 // Two-level coarse correction (DD_ML_CORRECTION), each a no-op if *skip != 0
 // (skip may be null):
 // dst (ceil(H/2) x ceil(W/2)) = sum of src over each 2x2 block inside the image.

@@ -328,6 +328,10 @@ int validate(int H, int W, int C, const dd_params& p) {
         set_error("final_local_rtol must be in [0, 1)");
         return DD_EINVAL;
     }
+    if (p.correction_cg < 0 || p.correction_cg > 100000) {
+        set_error("correction_cg must be in [0, 100000]");
+        return DD_EINVAL;
+    }
     return DD_OK;
 }
 
@@ -536,10 +540,16 @@ bool loop_mode(const dd_inpaint* h, bool timed) { return h->prm.device_loop != 0
 // Whether fine passes end with the coarse-grid correction.
 bool corrects(const dd_inpaint* h) { return h->prm.ml_mode == DD_ML_CORRECTION && h->lv.size() >= 2; }
 
-// Kernels of the coarse-grid correction after one fine sweep, without its gate.
+// Relative residual to which the small-grid CG solves the coarse correction equation.
+constexpr double kCorrectionCgTol = 1e-3;
+
+// Kernels of the coarse-grid correction after one fine sweep, without its gate:
+// fine residual, restrictions, the coarse solve (reset + ORAS sweeps, or the
+// small-grid CG), prolongations, and the three step kernels.
 int correction_kernels(const dd_inpaint* h) {
     const int nl = (int)h->lv.size();
-    return 1 + (nl - 1) + 1 + h->prm.correction_sweeps + (nl - 2) + 3;
+    const int coarse = h->prm.correction_cg > 0 ? 1 : 1 + h->prm.correction_sweeps;
+    return 1 + (nl - 1) + coarse + (nl - 2) + 3;
 }
 
 // Kernels of one pass of a device loop: the sweep (or CG's two) and the loop
@@ -608,19 +618,26 @@ int enqueue_correction_body(dd_inpaint* h, cudaStream_t st) {
         sp = L.P;
         splane = L.plane();
     }
-    const size_t cbytes = sizeof(float) * (size_t)h->C * Lc.plane();
-    DD_CK(cudaMemsetAsync(Lc.u[0], 0, cbytes, st));
-    DD_CK(cudaMemsetAsync(Lc.u[1], 0, cbytes, st));
-    DD_CK(dd::launch_reset_sweep_state(h->state_c, h->flag_c, 0, h->tol_c, -1.0, st, skip));
-    const dd::SweepPair pair{{&Lc.map_u[0], &Lc.map_u[1]}, {Lc.u[0], Lc.u[1]}};
-    const dd::SweepStop stop{Lc.partial, h->norms2_c, Lc.ref_d, h->tol_c, 0.0, h->flag_c, h->state_c,
-                             0, nullptr, err_word(h), h->prm.test_stall_polls};
-    for (int i = 0; i < h->prm.correction_sweeps; ++i)
-        DD_CK(dd::launch_sweep(Store::F32, Lc.geom, h->C, Lc.plane(), pair, &Lc.map_cg, Lc.tmask, stop,
-                               h->prm.robin_p, h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
     const float* e0 = Lc.u[0];
     const float* e1 = Lc.u[1];
     const int* sel = h->state_c;
+    if (h->prm.correction_cg > 0) {   // the small-grid CG: e_c into u[0]
+        DD_CK(dd::launch_coarse_cg(Lc.H, Lc.W, h->C, Lc.mask, Lc.W, Lc.corr_g, Lc.P, Lc.plane(), Lc.u[0], Lc.P,
+                                   Lc.plane(), h->prm.correction_cg, kCorrectionCgTol, nullptr, skip, st));
+        e1 = Lc.u[0];
+        sel = nullptr;
+    } else {   // correction_sweeps ORAS sweeps from e_c = 0
+        const size_t cbytes = sizeof(float) * (size_t)h->C * Lc.plane();
+        DD_CK(cudaMemsetAsync(Lc.u[0], 0, cbytes, st));
+        DD_CK(cudaMemsetAsync(Lc.u[1], 0, cbytes, st));
+        DD_CK(dd::launch_reset_sweep_state(h->state_c, h->flag_c, 0, h->tol_c, -1.0, st, skip));
+        const dd::SweepPair pair{{&Lc.map_u[0], &Lc.map_u[1]}, {Lc.u[0], Lc.u[1]}};
+        const dd::SweepStop stop{Lc.partial, h->norms2_c, Lc.ref_d, h->tol_c, 0.0, h->flag_c, h->state_c,
+                                 0, nullptr, err_word(h), h->prm.test_stall_polls};
+        for (int i = 0; i < h->prm.correction_sweeps; ++i)
+            DD_CK(dd::launch_sweep(Store::F32, Lc.geom, h->C, Lc.plane(), pair, &Lc.map_cg, Lc.tmask, stop,
+                                   h->prm.robin_p, h->prm.local_cg_iters, st, (float)h->prm.local_rtol));
+    }
     int eH = Lc.H, eW = Lc.W, ep = Lc.P;
     long long eplane = Lc.plane();
     for (int l = nl - 2; l >= 1; --l) {
@@ -1509,6 +1526,17 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         }
     }
     if (corrects(h)) {   // coarse-grid correction buffers
+        if (p.correction_cg > 0) {   // the small-grid CG holds the coarsest level in shared memory
+            const Level& Lc = h->lv.back();
+            if ((long long)Lc.H * Lc.W > dd::kCoarseCgMaxPixels) {
+                set_error("correction_cg: the coarsest level has more than 12288 pixels (add levels)");
+                return fail(DD_EINVAL);
+            }
+            if (dd::prepare_coarse_cg() != cudaSuccess) {
+                set_error("coarse CG: cudaFuncSetAttribute failed");
+                return fail(DD_ECUDA);
+            }
+        }
         const size_t fb = sizeof(float) * (size_t)C * F.plane();
         if ((rc = dalloc(h, (void**)&h->corr_r, fb)) != DD_OK) return fail(rc);
         for (size_t l = 1; l < h->lv.size(); ++l) {
@@ -1644,6 +1672,7 @@ void dd_params_default(dd_params* p) {
     p->local_rtol = 0.0;
     p->correction_trigger = 0.0;
     p->final_local_rtol = 0.0;
+    p->correction_cg = 0;
 }
 
 const char* dd_strerror(int code) {
@@ -1834,6 +1863,34 @@ int dd_prolong(int Hc, int Wc, int H, int W, int C, const float* u_c, const uint
     }
     DD_CK(dd::launch_prolong(Hc, Wc, H, W, C, u_c, Wc, (long long)Hc * Wc, mask, W, f, W, (long long)H * W, u, W,
                              (long long)H * W, static_cast<cudaStream_t>(stream)));
+    return DD_OK;
+}
+
+int dd_coarse_cg(int H, int W, int C, const uint8_t* mask, const float* g, float* e, int max_iter, double tol,
+                 int* iters, void* stream) {
+    if (H <= 0 || W <= 0 || C <= 0 || !mask || !g || !e || max_iter < 0 || !(tol >= 0.0)) {
+        set_error("bad arguments");
+        return DD_EINVAL;
+    }
+    if ((long long)H * W > dd::kCoarseCgMaxPixels) {
+        set_error("dd_coarse_cg: more than 12288 pixels");
+        return DD_EINVAL;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DD_CK(dd::prepare_coarse_cg());
+    int* it_d = nullptr;
+    if (iters != nullptr) DD_CK(cudaMallocAsync(reinterpret_cast<void**>(&it_d), sizeof(int) * C, st));
+    const long long plane = (long long)H * W;
+    const cudaError_t e1 = dd::launch_coarse_cg(H, W, C, mask, W, g, W, plane, e, W, plane, max_iter, tol, it_d,
+                                                nullptr, st);
+    cudaError_t e2 = cudaSuccess;
+    if (it_d != nullptr) {
+        if (e1 == cudaSuccess) e2 = cudaMemcpyAsync(iters, it_d, sizeof(int) * C, cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(it_d, st);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    }
+    DD_CK(e1);
+    DD_CK(e2);
     return DD_OK;
 }
 
