@@ -6,7 +6,8 @@ the FP64-accurate outer correction.  For profilers, e.g.
 ``ncu --metrics gpu__time_duration.sum`` (a launch list) or a
 ``--section MemoryWorkloadAnalysis`` capture of the streaming passes.
 
-python -m paper_2110_03946_gb300.profile_passes [--workload rgb4k_edge3] [--legs oras,correction,cg,cg_fine,fp16]
+python -m paper_2110_03946_gb300.profile_passes [--workload rgb4k_edge3]
+       [--legs oras,correction,cg,cg_fine,fp16,correction_cg]
 """
 from __future__ import annotations
 
@@ -23,6 +24,9 @@ LEGS = {
     # the fine-level operator and update passes at full size
     "cg_fine": dict(precision="fp32", solver="cg", levels=1, max_sweeps=40),
     "fp16": dict(precision="fp16_ref"),
+    # the coarse-grid correction after every fine sweep with the small-grid coarse CG on a
+    # hierarchy deep enough for it (4K: 6 levels, coarsest 120 x 68)
+    "correction_cg": dict(precision="fp32", ml_mode="correction", levels=6, correction_cg=300),
 }
 
 
