@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--coarse-tol", type=float, default=None)
     ap.add_argument("--final-rtol", type=float, default=None,
                     help="local CG tolerance of a sweep predicted to be a level's last (0 = off)")
+    ap.add_argument("--local-atol", type=float, default=None,
+                    help="absolute local CG stop as a share of the level's tolerance (0 = off)")
     ap.add_argument("--ml-mode", default=None, choices=["cascade", "correction"])
     ap.add_argument("--trigger", type=float, default=None, help="correction trigger (DD_ML_CORRECTION)")
     ap.add_argument("--correction-cg", type=int, default=None,
@@ -90,7 +92,8 @@ def solver_params(args, precision):
                      ("robin_p", args.robin), ("levels", args.levels), ("coarse_tol", args.coarse_tol),
                      ("final_local_rtol", args.final_rtol), ("ml_mode", getattr(args, "ml_mode", None)),
                      ("correction_trigger", getattr(args, "trigger", None)),
-                     ("correction_cg", getattr(args, "correction_cg", None))]:
+                     ("correction_cg", getattr(args, "correction_cg", None)),
+                     ("local_atol", getattr(args, "local_atol", None))]:
         if val is not None:
             prm[key] = val
             src += f"; {key} overridden"
@@ -860,7 +863,7 @@ def run_ours(args):
                    "block": prm["block"], "overlap": prm["overlap"], "local_cg_iters": prm["local_cg_iters"],
                    "local_rtol": prm.get("local_rtol", 0.0), "final_local_rtol": prm.get("final_local_rtol", 0.0),
                    "ml_mode": prm.get("ml_mode", "cascade"), "correction_trigger": prm.get("correction_trigger", 0.0),
-                   "correction_cg": prm.get("correction_cg", 0),
+                   "correction_cg": prm.get("correction_cg", 0), "local_atol": prm.get("local_atol", 0.0),
                    "levels": prm["levels"], "robin_p": prm["robin_p"], "coarse_tol": prm["coarse_tol"],
                    "params_source": tuned_src, "precision": args.precision, "frames_resident": args.frames,
                    "device_loop": args.device_loop,

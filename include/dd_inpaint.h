@@ -134,6 +134,13 @@ typedef struct dd_params {
                                 CTA per channel, FP64 dot products), at most this many iterations, to
                                 relative residual 1e-3; the coarsest level may then have at most
                                 12288 pixels (else DD_EINVAL at create; add levels) */
+    double local_atol;       /* 0 (default): no absolute local stop.  In (0, 1): a block's local CG
+                                also stops once its residual norm is at most local_atol * tol *
+                                ||b - A u0|| / sqrt(blocks per channel), the block's share of the
+                                level's stop test scaled by local_atol; blocks whose residual is
+                                already below it take no CG step.  Below 1 the level cannot stall:
+                                while its residual is above tol, some block is above its share and
+                                iterates.  Applies when the level's tolerance is positive */
 } dd_params;
 
 #define DD_MAX_STAT_CHANNELS 16

@@ -33,9 +33,10 @@ SPACE = {
     "levels": [1, 2, 3, 4, 5, 6],
     "coarse_tol": [1e-1, 1e-2, 3e-3, 1e-3, 3e-4],
     "final_local_rtol": [0.0, 0.2, 0.35, 0.5],   # 0.0 = the predicted-last sweep uses local_rtol too
+    "local_atol": [0.0, 0.3, 0.5, 0.7],          # 0.0 = no absolute local stop (values >= 1 can stall)
 }
 START = {"block": 32, "overlap": 6, "local_cg_iters": 16, "local_rtol": 0.0, "robin_p": 0.0, "levels": 3,
-         "coarse_tol": 1e-2, "final_local_rtol": 0.0}
+         "coarse_tol": 1e-2, "final_local_rtol": 0.0, "local_atol": 0.0}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 
 

@@ -44,7 +44,7 @@ class dd_params(ctypes.Structure):
         ("tile_warps", ctypes.c_int), ("solver", ctypes.c_int), ("correction_sweeps", ctypes.c_int),
         ("local_rtol", ctypes.c_double), ("device_loop", ctypes.c_int), ("test_stall_polls", ctypes.c_int),
         ("correction_trigger", ctypes.c_double), ("final_local_rtol", ctypes.c_double),
-        ("correction_cg", ctypes.c_int),
+        ("correction_cg", ctypes.c_int), ("local_atol", ctypes.c_double),
     ]
 
 

@@ -112,6 +112,9 @@ struct SweepStop {
     // to be the last one (its input residual within 1/kFinalContraction of tol);
     // 0: every sweep uses the launch's local_rtol
     float final_local_rtol;
+    // > 0: a block's local CG also stops once its residual norm is at most
+    // local_atol * tol * ||b - A u0||_c / sqrt(blocks per channel) (tol > 0 only)
+    float local_atol;
 };
 constexpr int kTimedLaunches = 64;   // launches per sequence whose kind work[2 + i] records
 
@@ -146,7 +149,7 @@ struct SweepFrame {   // aligned as CUtensorMap (at least 64 bytes)
     long long plane;
     FastDiv dv_tiles, dv_ntx;
     int H, W, pitch, C, s, ntx, ntiles, has_g;
-    float p_robin, local_rtol2, local_rtol2_final;
+    float p_robin, local_rtol2, local_rtol2_final, local_atol2;
     int k, stall_polls, force_probe;
     int cap;                   // batched levels: full sweeps after which the frame drops out
     double level_tol;          // batched levels: the stop tolerance launch_batch_reset sets

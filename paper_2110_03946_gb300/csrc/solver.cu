@@ -262,7 +262,8 @@ int* err_word(dd_inpaint* h) { return h->flag_d + 5; }
 dd::SweepStop make_stop(dd_inpaint* h, unsigned long long* partial, const double* ref_d, double stall,
                         unsigned long long* work = nullptr) {
     return dd::SweepStop{partial, h->norms2_d, ref_d, h->tol_d, stall, h->flag_d, h->sstate_d, 0,
-                         work, err_word(h), h->prm.test_stall_polls, (float)h->prm.final_local_rtol};
+                         work, err_word(h), h->prm.test_stall_polls, (float)h->prm.final_local_rtol,
+                         (float)h->prm.local_atol};
 }
 
 // Clear the error word at the start of a solve (enqueued, so it also works in a capture).
@@ -326,6 +327,10 @@ int validate(int H, int W, int C, const dd_params& p) {
     }
     if (!(p.final_local_rtol >= 0.0) || !(p.final_local_rtol < 1.0)) {
         set_error("final_local_rtol must be in [0, 1)");
+        return DD_EINVAL;
+    }
+    if (!(p.local_atol >= 0.0) || !(p.local_atol < 1.0)) {   // >= 1 could stall above tol
+        set_error("local_atol must be in [0, 1)");
         return DD_EINVAL;
     }
     if (p.correction_cg < 0 || p.correction_cg > 100000) {
@@ -1673,6 +1678,7 @@ void dd_params_default(dd_params* p) {
     p->correction_trigger = 0.0;
     p->final_local_rtol = 0.0;
     p->correction_cg = 0;
+    p->local_atol = 0.0;
 }
 
 const char* dd_strerror(int code) {

@@ -453,6 +453,8 @@ oras_sweep_kernel(const __grid_constant__ SweepFrame one, const SweepFrame* __re
     int f_cur = 0, f_kcg = 0, f_tiles = 0;
     int f_probe = 0;   // (ints rather than bools for the state kept across tiles: fewer live predicates)
     float f_rtol2 = 0.f;   // the squared local tolerance of this frame's sweep
+    float f_aunit = 0.f;   // local_atol^2 tol^2 / blocks: times ref_c^2, the squared absolute local stop
+    float f_atol2 = 0.f;   // ... of the current channel
     // Residual sums of the input iterate per channel, exact (Fix128): lane
     // (it mod 32) holds the owned ||r||^2 of this CTA's tile it until every 32
     // tiles (or a change of channel) all lanes add their value into their own
@@ -519,6 +521,12 @@ oras_sweep_kernel(const __grid_constant__ SweepFrame one, const SweepFrame* __re
             const int req = __ldcg(Fp->state + 2);
             f_probe = (Fp->force_probe != 0 || req == 1) ? 1 : 0;
             f_rtol2 = req == 2 ? Fp->local_rtol2_final : Fp->local_rtol2;
+            if (Fp->local_atol2 > 0.f) {
+                const double tv = __ldcg(Fp->tol);
+                f_aunit = tv > 0.0 ? (float)((double)Fp->local_atol2 * tv * tv / (double)Fp->ntiles) : 0.f;
+            } else {
+                f_aunit = 0.f;
+            }
             f_kcg = f_probe ? 0 : Fp->k;
         }
         const int local = t - begin_at(q);
@@ -662,14 +670,17 @@ oras_sweep_kernel(const __grid_constant__ SweepFrame one, const SweepFrame* __re
             const float2 both = tile_sum2<CF>(make_float2(s2, rr0), red[0], red[1], wt, lane);
             s2 = both.x;
             rr = both.y;
-            rr_stop = f_rtol2 * rr;
         }
         // the owned residual sum of this tile into the lane-batched accumulators
         if (c != cur_c) {
             flush_channel();
             cur_c = c;
-            eu = fix_unit(Fp->ref[c]);
+            const double refc = Fp->ref[c];
+            eu = fix_unit(refc);
+            f_atol2 = (float)((double)f_aunit * refc * refc);
         }
+        // local stop: the relative decrease, or the absolute share of the global tolerance
+        rr_stop = fmaxf(f_rtol2 * rr, f_atol2);
         ++f_tiles;
         acc_bad |= isfinite(s2) ? 0 : 1;
         if (lane == (it & 31)) pend = s2;
@@ -1296,6 +1307,7 @@ cudaError_t make_frame(SweepFrame* f, const TileGeom& g, int C, long long plane,
     f->p_robin = p_robin;
     f->local_rtol2 = local_rtol * local_rtol;
     f->local_rtol2_final = stop.final_local_rtol > 0.f ? stop.final_local_rtol * stop.final_local_rtol : 0.f;
+    f->local_atol2 = stop.local_atol > 0.f ? stop.local_atol * stop.local_atol : 0.f;
     f->k = k;
     f->stall_polls = stop.stall_polls;
     f->force_probe = stop.force_probe;

@@ -20,7 +20,8 @@ def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_m
                 max_corrections=None, coarse_sweeps=None, inputs_on_device=1, timing=None,
                 tile_warps=None, solver=None, device_loop=None, correction_sweeps=None,
                 local_rtol=None, coarse_factor=None, test_stall_polls=None,
-                correction_trigger=None, final_local_rtol=None, correction_cg=None) -> B.dd_params:
+                correction_trigger=None, final_local_rtol=None, correction_cg=None,
+                local_atol=None) -> B.dd_params:
     p = B.dd_params_default()
     if block is not None: p.block = int(block)
     if overlap is not None: p.overlap = int(overlap)
@@ -47,6 +48,7 @@ def make_params(block=None, overlap=None, local_cg_iters=None, levels=None, ml_m
     if correction_trigger is not None: p.correction_trigger = float(correction_trigger)
     if final_local_rtol is not None: p.final_local_rtol = float(final_local_rtol)
     if correction_cg is not None: p.correction_cg = int(correction_cg)
+    if local_atol is not None: p.local_atol = float(local_atol)
     p.inputs_on_device = int(inputs_on_device)
     return p
 

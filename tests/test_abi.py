@@ -72,7 +72,8 @@ def test_defaults_and_strings(lib):
                                          ("ml_mode", 5), ("inner_tol", 1.5), ("coarse_factor", 3),
                                          ("coarse_factor", 16), ("test_stall_polls", -1),
                                          ("correction_trigger", 1.0), ("correction_trigger", -0.1),
-                                         ("final_local_rtol", 1.0), ("final_local_rtol", -0.5)])
+                                         ("final_local_rtol", 1.0), ("final_local_rtol", -0.5),
+                                         ("local_atol", -1.0), ("local_atol", 1.0), ("correction_cg", -1)])
 def test_invalid_params_rejected_on_host(lib, field, value):
     from paper_2110_03946_gb300 import binding as B
     p = B.dd_params_default()

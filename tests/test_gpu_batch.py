@@ -233,7 +233,7 @@ def _run_batch(ips, outs, mode):
 
 @pytest.mark.parametrize("prm", [PRM, dict(PRM, overlap=4), dict(PRM, overlap=4, coarse_factor=4, levels=2),
                                  dict(PRM, block=64, overlap=4, levels=2),
-                                 dict(PRM, overlap=4, local_rtol=0.05, final_local_rtol=0.35)])
+                                 dict(PRM, overlap=4, local_rtol=0.05, final_local_rtol=0.35, local_atol=0.5)])
 def test_persistent_batch_equals_independent_solves(prm):
     """Frames of different sizes, channel counts and level counts (the 5 x 6 and
     2 x 40 frames have fewer levels) swept level by level in single persistent

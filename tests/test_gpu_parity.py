@@ -136,6 +136,11 @@ SOLVE_CASES = [
     ("rgb_final_rtol", 200, 330, 3, dict(levels=3, precision="fp32", local_rtol=0.05, final_local_rtol=0.5)),
     ("gray256_final_rtol_launches", 256, 256, 1, dict(levels=2, precision="fp32", local_rtol=0.05,
                                                       final_local_rtol=0.35, device_loop=0)),
+    # the absolute local stop (blocks below their share of the tolerance take no CG step)
+    ("rgb_local_atol", 200, 330, 3, dict(levels=3, precision="fp32", local_rtol=0.05, local_atol=0.5,
+                                         final_local_rtol=0.35)),
+    ("gray256_local_atol_launches", 256, 256, 1, dict(levels=2, precision="fp32", local_atol=0.9, device_loop=0)),
+    ("rgb_local_atol_fp16ref", 200, 330, 3, dict(levels=3, precision="fp16_ref", local_rtol=0.05, local_atol=0.5)),
     ("gray256_correction_2level_launches", 256, 256, 1, dict(levels=2, precision="fp32", ml_mode="correction",
                                                              correction_sweeps=3, device_loop=0)),
     # two solved levels with a 1/8 coarse grid (two pass-through dyadic levels between them)
