@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--coarse-tol", type=float, default=None)
     ap.add_argument("--final-rtol", type=float, default=None,
                     help="local CG tolerance of a sweep predicted to be a level's last (0 = off)")
+    ap.add_argument("--local-rtol", type=float, default=None, help="relative local CG stop (0 = k steps)")
     ap.add_argument("--local-atol", type=float, default=None,
                     help="absolute local CG stop as a share of the level's tolerance (0 = off)")
     ap.add_argument("--ml-mode", default=None, choices=["cascade", "correction"])
@@ -93,7 +94,8 @@ def solver_params(args, precision):
                      ("final_local_rtol", args.final_rtol), ("ml_mode", getattr(args, "ml_mode", None)),
                      ("correction_trigger", getattr(args, "trigger", None)),
                      ("correction_cg", getattr(args, "correction_cg", None)),
-                     ("local_atol", getattr(args, "local_atol", None))]:
+                     ("local_atol", getattr(args, "local_atol", None)),
+                     ("local_rtol", getattr(args, "local_rtol", None))]:
         if val is not None:
             prm[key] = val
             src += f"; {key} overridden"
