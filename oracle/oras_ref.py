@@ -115,11 +115,11 @@ def local_matrix(A, mask, blk, p_robin: float):
     return idx, M.tocsr()
 
 
-def cg_fixed(M, rhs, k, rtol=0.0):
+def cg_fixed(M, rhs, k, rtol=0.0, atol=0.0):
     """Conjugate gradients (Saad 2003, the CG algorithm of Ch. 6) from x = 0
     for k iterations; stops early if (r, r) or (p, Ap) is not positive, or,
-    with rtol > 0, once ||r|| <= rtol ||r_0|| (checked before each step).
-    k = None solves exactly."""
+    with rtol > 0, once ||r|| <= rtol ||r_0||, or, with atol > 0, once
+    ||r|| <= atol (checked before each step).  k = None solves exactly."""
     if k is None:
         if rhs.size == 0:
             return rhs.copy()
@@ -128,7 +128,7 @@ def cg_fixed(M, rhs, k, rtol=0.0):
     r = rhs.copy()
     p = r.copy()
     rr = float(r @ r)
-    rr_stop = rtol * rtol * rr
+    rr_stop = max(rtol * rtol * rr, atol * atol)
     for _ in range(k):
         if not rr > 0.0 or rr <= rr_stop:
             break
@@ -146,14 +146,16 @@ def cg_fixed(M, rhs, k, rtol=0.0):
     return x
 
 
-def oras_sweep(u, f, mask, b, o, p_robin, k, g=None, A=None, local_rtol=0.0):
+def oras_sweep(u, f, mask, b, o, p_robin, k, g=None, A=None, local_rtol=0.0, local_atol=None):
     """One ORAS iteration: returns (u_next, ||r^n|| per channel).
 
     u, f: (C, H, W).  g (optional, (C,H,W)): extra source term on unknown
     pixels, i.e. the sweep solves A u = C f + (I - C) g (used for correction
     equations).  r^n is the residual of the INPUT iterate u^n.  local_rtol > 0
     lets each local CG stop once its residual fell by that factor (the paper
-    runs a fixed number of steps; 0 keeps that)."""
+    runs a fixed number of steps; 0 keeps that).  local_atol (optional, C
+    values): each local CG of channel c also stops once its residual norm is at
+    most local_atol[c] (an absolute local stop; see oras_solve)."""
     u = np.asarray(u, dtype=np.float64)
     two_d = u.ndim == 2
     u3 = u[None] if two_d else u
@@ -186,25 +188,43 @@ def oras_sweep(u, f, mask, b, o, p_robin, k, g=None, A=None, local_rtol=0.0):
             v = np.zeros(idx.size)
             v[known] = rl[known]               # identity rows of A
             rhs = rl[unk] - Muk @ v[known]
-            v[unk] = cg_fixed(Muu, rhs, k, local_rtol)
+            at = 0.0 if local_atol is None else float(local_atol[c])
+            v[unk] = cg_fixed(Muu, rhs, k, local_rtol, at)
             out[c, idx[own]] += v[own]
     out = out.reshape(C, H, W)
     return (out[0] if two_d else out), rn
 
 
-def oras_solve(f, mask, b, o, p_robin, k, tol, max_sweeps, u0=None):
+def absolute_local_tol(f, mask, b, o, tol, kappa):
+    """Per channel, the absolute local stop kappa * tol * ||b - A u0|| /
+    sqrt(blocks): a block's share of the stop test ||b - A u|| <= tol ||b - A u0||,
+    scaled by kappa.  Since the blocks' owned cores partition the image, the
+    sum over blocks of their local residuals squared is at least ||b - A u||^2:
+    with kappa < 1, while the stop test fails some block is above its share."""
+    f3 = np.asarray(f, dtype=np.float64)
+    f3 = f3[None] if f3.ndim == 2 else f3
+    mask = np.asarray(mask)
+    r0 = ref.residual(ref.initial_guess(f3, mask), f3, mask)
+    ref_n = np.sqrt((r0 * r0).reshape(f3.shape[0], -1).sum(axis=1))
+    nblk = len(subdomains(mask.shape[0], mask.shape[1], b, o))
+    return kappa * tol * ref_n / np.sqrt(nblk)
+
+
+def oras_solve(f, mask, b, o, p_robin, k, tol, max_sweeps, u0=None, local_rtol=0.0, local_atol=0.0):
     """Iterate ORAS sweeps from u0 (default C f) until the relative residual
     (reference u0 = C f) of the current iterate is <= tol for every channel.
+    local_atol = kappa > 0: the absolute local stop of absolute_local_tol.
     Returns (u, sweeps_applied)."""
     mask = np.asarray(mask)
     A = ref.assemble_A(mask)
     u = ref.initial_guess(f, mask) if u0 is None else np.array(u0, dtype=np.float64)
+    at = absolute_local_tol(f, mask, b, o, tol, local_atol) if local_atol > 0 else None
     for n in range(max_sweeps + 1):
         if np.all(ref.rel_residual(u, f, mask) <= tol):
             return u, n
         if n == max_sweeps:
             break
-        u, _ = oras_sweep(u, f, mask, b, o, p_robin, k, A=A)
+        u, _ = oras_sweep(u, f, mask, b, o, p_robin, k, A=A, local_rtol=local_rtol, local_atol=at)
     return u, max_sweeps
 
 

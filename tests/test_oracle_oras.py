@@ -318,3 +318,52 @@ def test_one_reduction_cg_step_equals_textbook_cg(rng):
         for k in (1, 2, 5, 10, 20):
             a, b = oras.cg_fixed(Muu, rhs, k), _cg_one_reduction(Muu, rhs, k)
             assert np.max(np.abs(a - b)) <= 1e-9 * max(1.0, np.max(np.abs(a)))
+
+
+# ------------------------------------------------ absolute local stop (reading C7)
+def _block_local_residuals(u, f, m, b, o):
+    """||R_i r|| over the unknown pixels of each block, r = b - A u."""
+    r = ref.residual(u[None], f[None], m)[0].ravel()
+    H, W = m.shape
+    out = []
+    for y0, y1, x0, x1, *_ in oras.subdomains(H, W, b, o):
+        yy, xx = np.meshgrid(np.arange(y0, y1), np.arange(x0, x1), indexing="ij")
+        idx = (yy * W + xx).ravel()
+        out.append(np.linalg.norm(r[idx][m.ravel()[idx] == 0]))
+    return np.array(out), np.linalg.norm(r)
+
+
+def test_block_residuals_bound_the_global_residual(rng):
+    """The argument behind local_atol < 1: the owned cores partition the image,
+    so the blocks' local residuals squared sum to at least ||r||^2."""
+    f, m = _case(rng, 37, 53, 0.05)
+    u = rng.uniform(0, 255, size=f.shape)
+    u[m != 0] = f[m != 0]
+    for b, o in [(16, 2), (12, 5), (8, 1)]:
+        loc, glob = _block_local_residuals(u, f, m, b, o)
+        assert np.sum(loc ** 2) >= glob ** 2 * (1 - 1e-12)
+
+
+def test_absolute_local_stop_below_one_converges(rng):
+    f, m = _case(rng, 40, 56, 0.05)
+    us = ref.solve_direct(f, m)
+    for kappa in (0.5, 0.9):
+        u, n = oras.oras_solve(f, m, 16, 3, 0.3, 12, 1e-8, 300, local_rtol=0.05, local_atol=kappa)
+        assert n < 300
+        assert np.all(ref.rel_residual(u, f, m) <= 1e-8)
+        assert np.max(np.abs(u - us)) <= 1e-4
+
+
+def test_absolute_local_stop_at_or_above_one_can_stall(rng):
+    """With kappa >= 1 every block can sit below its share while the stop test
+    fails: then no block iterates and a sweep returns its input unchanged."""
+    f, m = _case(rng, 40, 56, 0.05)
+    b, o, kappa = 16, 3, 3.0
+    u0 = ref.initial_guess(f, m)
+    loc, glob = _block_local_residuals(u0, f, m, b, o)
+    nblk = loc.size
+    tol = loc.max() * np.sqrt(nblk) / (kappa * glob)   # every block exactly at its kappa-share
+    assert tol < 1.0                                     # the stop test ||r|| <= tol ||r0|| fails at u0
+    at = oras.absolute_local_tol(f, m, b, o, tol, kappa)
+    u1, _ = oras.oras_sweep(u0, f, m, b, o, 0.3, 12, local_atol=at * (1 + 1e-9))
+    assert np.array_equal(u1, u0)
