@@ -323,7 +323,7 @@ def restrict_sum(r):
     return out[0] if two_d else out
 
 
-def correction_pass(u, f, mask, hier, b, o, p_robin, k, m):
+def correction_pass(u, f, mask, hier, b, o, p_robin, k, m, coarse_exact=False):
     """One fine ORAS sweep followed by a coarse-grid correction on the coarsest
     level of hier (from build_hierarchy): the fine residual r = b - A u (zero
     on known pixels) is summed down to that level, the correction equation
@@ -332,7 +332,9 @@ def correction_pass(u, f, mask, hier, b, o, p_robin, k, m):
     pixels), is added with the step omega = (r, d) / (d, A d) per channel: the
     minimiser of the A-norm of the error along d (A is SPD on the unknowns;
     the rediscretised coarse problem is not the Galerkin one, so the plain
-    step can overshoot).  Returns (u_next, ||r^n|| of the input per channel)."""
+    step can overshoot).  coarse_exact: the correction equation is solved
+    exactly (sparse LU) instead of by m ORAS sweeps.  Returns (u_next, ||r^n||
+    of the input per channel)."""
     mask = np.asarray(mask)
     u1, rn = oras_sweep(u, f, mask, b, o, p_robin, k)
     two_d = np.asarray(u1).ndim == 2
@@ -344,8 +346,14 @@ def correction_pass(u, f, mask, hier, b, o, p_robin, k, m):
         r = restrict_sum(r)
     _, mask_c = hier[-1]
     e = np.zeros_like(r)
-    for _ in range(m):
-        e, _ = oras_sweep(e, np.zeros_like(r), mask_c, b, o, p_robin, k, g=r)
+    if coarse_exact:   # A_c e = r on coarse-unknown pixels, e = 0 on coarse-known ones
+        lu = spla.splu(ref.assemble_A(mask_c).tocsc())
+        for c in range(r.shape[0]):
+            rhs = np.where(np.asarray(mask_c) != 0, 0.0, r[c]).ravel()
+            e[c] = lu.solve(rhs).reshape(r.shape[1:])
+    else:
+        for _ in range(m):
+            e, _ = oras_sweep(e, np.zeros_like(r), mask_c, b, o, p_robin, k, g=r)
     for lvl in range(len(hier) - 2, -1, -1):
         H, W = np.asarray(hier[lvl][1]).shape
         e = prolong_bilinear(e, H, W)

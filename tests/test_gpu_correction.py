@@ -92,9 +92,10 @@ def test_launches_and_device_loop_agree(trigger):
         assert np.array_equal(u_l, u_p)
 
 
-def test_adaptive_correction_in_a_batch_graph_equals_solves_alone():
+@pytest.mark.parametrize("coarse_cg", [0, 300])
+def test_adaptive_correction_in_a_batch_graph_equals_solves_alone(coarse_cg):
     frames = [_hole_frame(192, 256, 3, 7), synth.make_frame(144, 200, 3, 0.05, "edge", 9)]
-    prm = dict(PRM, ml_mode="correction", correction_trigger=0.5)
+    prm = dict(PRM, ml_mode="correction", correction_trigger=0.5, correction_cg=coarse_cg)
     alone = [_solve(f, m, **prm) for f, m in frames]
     ips = [Inpainter(m, f, **prm) for f, m in frames]
     outs = [torch.zeros(f.shape, dtype=torch.float32, device=DEV) for f, _ in frames]

@@ -366,6 +366,29 @@ def test_correction_pass_matches_oracle(levels, m):
 
 
 
+@pytest.mark.parametrize("levels", [2, 3])
+def test_correction_pass_with_coarse_cg_matches_oracle(levels):
+    """One pass of DD_ML_CORRECTION whose coarse equation is solved by the
+    small-grid CG (to relative residual 1e-3) against the oracle's pass with
+    an exact coarse solve, from the same iterate.  The tolerance allows the
+    CG's 1e-3 on the correction's size."""
+    b, o, k, p = 16, 4, 8, 0.3
+    f, msk = synth.make_frame(70, 90, 2, 0.04, "edge", 41 + levels)
+    with Inpainter(msk, f, block=b, overlap=o, local_cg_iters=k, robin_p=p, levels=levels, precision="fp32",
+                   ml_mode="correction", correction_cg=500) as ip:
+        u0 = ref.initial_guess(f, msk).astype(np.float32)
+        ip.set_iterate(torch.as_tensor(u0))
+        ip.sweep(1)
+        u1 = ip.get_iterate().cpu().numpy()
+    hier = oras.build_hierarchy(f, msk, levels)
+    e1, _ = oras.correction_pass(u0.astype(np.float64), f, msk, hier, b, o, p, k, 0, coarse_exact=True)
+    us, _ = oras.oras_sweep(u0.astype(np.float64), f, msk, b, o, p, k)
+    corr = float(np.max(np.abs(e1 - us)))
+    assert corr > 0.0
+    assert np.max(np.abs(u1 - e1)) <= 2e-3 + 1e-2 * corr
+    assert np.array_equal(u1[:, msk != 0], f[:, msk != 0].astype(np.float32))
+
+
 @pytest.mark.parametrize("rtol", [0.1, 0.02])
 def test_sweep_with_local_rtol_matches_oracle(rtol):
     """Local CG with the relative stop: the block's CG ends once its residual

@@ -367,3 +367,14 @@ def test_absolute_local_stop_at_or_above_one_can_stall(rng):
     at = oras.absolute_local_tol(f, m, b, o, tol, kappa)
     u1, _ = oras.oras_sweep(u0, f, m, b, o, 0.3, 12, local_atol=at * (1 + 1e-9))
     assert np.array_equal(u1, u0)
+
+
+def test_exact_coarse_correction_on_the_fine_grid_gives_the_solution(rng):
+    """With a one-level hierarchy the coarse grid is the fine grid: the exact
+    correction e = A^-1 r is the whole error, omega = (r, e) / (e, A e) = 1,
+    and the corrected iterate is the solution of Eq. eq:ls."""
+    f, m = _case(rng, 30, 41, 0.06)
+    hier = oras.build_hierarchy(f, m, 1)
+    u0 = ref.initial_guess(f, m)
+    u1, _ = oras.correction_pass(u0, f, m, hier, 12, 3, 0.3, 4, 0, coarse_exact=True)
+    assert np.max(np.abs(u1 - ref.solve_direct(f, m))) <= 1e-8
