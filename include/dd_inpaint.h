@@ -130,10 +130,12 @@ typedef struct dd_params {
                                 following sweeps run as usual (the global test decides, Sec. 4) */
     int    correction_cg;    /* DD_ML_CORRECTION: 0 (default) solves the coarse correction equation
                                 by correction_sweeps ORAS sweeps from zero.  > 0: by conjugate
-                                gradients on the coarsest level held in one SM's shared memory (one
-                                CTA per channel, FP64 dot products), at most this many iterations, to
-                                relative residual 1e-3; the coarsest level may then have at most
-                                12288 pixels (else DD_EINVAL at create; add levels) */
+                                gradients on a coarse level held in one SM's shared memory (one CTA
+                                per channel, FP64 dot products), at most this many iterations, to
+                                relative residual 1e-3.  That level has at most 12288 pixels: below
+                                the cascade's coarsest level the 2x2 restriction continues with
+                                correction-only levels (no sweeps) until one fits, within 8 dyadic
+                                levels in all (else DD_EINVAL at create) */
     double local_atol;       /* 0 (default): no absolute local stop.  In (0, 1): a block's local CG
                                 also stops once its residual norm is at most local_atol * tol *
                                 ||b - A u0|| / sqrt(blocks per channel), the block's share of the

@@ -1009,30 +1009,31 @@ __global__ void loop_begin_kernel(int* __restrict__ ctl, cudaGraphConditionalHan
 
 // The decision, after a fine sweep, whether the coarse-grid correction follows
 // it (returns 1 to skip it).  gate: [0] skip this pass's correction, [1]
-// corrections off for the rest of the solve, [2] corrections applied, [3] full
-// fine sweeps seen at the last decision, [4] the last full pass was corrected,
-// [5] the trigger has fired, [6] gate launches (counted by corr_gate_kernel).
-// prev[0]: the fine residual w at the last full pass (w = norms2[2C], the worst
-// relative residual of the latest full sweep's input, i.e. of the previous
-// pass's output).
+// corrections off (trigger 0) or paused (trigger > 0), [2] corrections
+// applied, [3] full fine sweeps seen at the last decision, [4] the last full
+// pass was corrected, [5] the trigger has fired, [6] gate launches (counted by
+// corr_gate_kernel).  prev[0]: the fine residual w at the last full pass
+// (w = norms2[2C], the worst relative residual of the latest full sweep's
+// input, i.e. of the previous pass's output); prev[1]: the contraction of the
+// slow pass that fired the trigger (or resumed the corrections).
 //  - A probe pass (state[1], the count of full sweeps, did not grow) changed
 //    no iterate: no correction, no history.
 //  - trigger > 0: until the first pass that reduced w by less than trigger (a
 //    slow pass: the residual is dominated by a smooth mode that the sweeps
-//    contract slowly) no pass is corrected; that pass sets [5], and every
-//    later pass is corrected.  trigger = 0: every pass is corrected.
-//  - Corrections are switched off once a corrected pass reduced w by less than
-//    kGateRatio: with the non-symmetric ORAS smoother the corrected iteration
-//    can still grow slowly where plain ORAS converges.  After a trigger the
-//    bound is the larger of kGateRatio and the contraction of the slow pass
-//    that fired it (prev[1]): corrected passes stay on while they beat the
-//    plain sweeps.
+//    contract slowly) no pass is corrected; that pass sets [5], and the later
+//    passes are corrected.  trigger = 0: every pass is corrected.
+//  - A corrected pass that reduced w by less than kGateRatio (after a trigger:
+//    by less than the slow pass's own contraction, if that is larger) switches
+//    corrections off: for good with trigger 0 (with the non-symmetric ORAS
+//    smoother the corrected iteration can grow slowly where plain ORAS
+//    converges), and with a trigger only until a plain pass is slow again (a
+//    smooth correction can remove error without moving the residual much).
 constexpr double kGateRatio = 0.7;
 
 __device__ int corr_gate_decide(const int* __restrict__ flag, const double* __restrict__ norms2, int C,
                                 const int* __restrict__ state, int* __restrict__ gate, double* __restrict__ prev,
                                 double trigger) {
-    int skip = flag[0] != 0 || gate[1] != 0;
+    int skip = flag[0] != 0 || (trigger <= 0.0 && gate[1] != 0);
     if (!skip) {
         const int nfull = state[1];
         if (nfull == gate[3]) {
@@ -1040,12 +1041,20 @@ __device__ int corr_gate_decide(const int* __restrict__ flag, const double* __re
         } else {
             gate[3] = nfull;
             const double w = norms2[2 * C], wp = prev[0];
+            const bool slow = trigger > 0.0 && wp > 0.0 && w > trigger * wp;
             if (trigger > 0.0 && gate[5] == 0) {   // plain passes until a slow one
-                if (wp > 0.0 && w > trigger * wp) {
+                if (slow) {
                     gate[5] = 1;
                     prev[1] = w / wp;
                 }
                 skip = 1;
+            } else if (gate[1] != 0) {             // paused: resume after a slow plain pass
+                if (slow) {
+                    gate[1] = 0;
+                    prev[1] = w / wp;
+                } else {
+                    skip = 1;
+                }
             } else if (wp > 0.0 && gate[4] != 0 && !(w <= fmax(kGateRatio, prev[1]) * wp)) {
                 gate[1] = 1;
                 skip = 1;

@@ -126,6 +126,8 @@ struct dd_inpaint {
     dd_params prm{};
     Store lowst = Store::F32;
     std::vector<Level> lv;
+    int nc = 0;               // levels of the cascade (lv[0 .. nc)); lv[nc ..) are correction-only levels
+                              // below the cascade's coarsest, for the small-grid coarse solve
     int cur = 0;              // buffer of lv[0] holding the fine iterate
     bool warm = false;        // next solve starts from the kept iterate
     bool valid = false;       // mask/values loaded and not empty
@@ -914,7 +916,7 @@ int enqueue_level(dd_inpaint* h, Level& L, int n, double tol, cudaStream_t st, b
 // enqueued without host synchronisation: each level's result buffer is chosen
 // on the device.
 int cascade(dd_inpaint* h, cudaStream_t st, bool capture) {
-    const int nl = (int)h->lv.size();
+    const int nl = h->nc;
     for (int l = nl - 1; l >= 1; --l) {
         Level& L = h->lv[l];
         if (l == nl - 1) {
@@ -978,8 +980,8 @@ int rel_from_h_res(dd_inpaint* h, std::vector<double>& rel, std::vector<double>&
 
 // Read the per-level sweep counts resolved on the device (after a sync).
 void take_level_stats(dd_inpaint* h) {
-    for (size_t l = 1; l < h->lv.size() && l < DD_MAX_LEVELS; ++l) h->stats.sweeps_per_level[l] = h->h_state[4 * l + 1];
-    for (size_t l = 1; l < h->lv.size(); ++l) h->stats.sweeps_total += h->h_state[4 * l + 1];
+    for (int l = 1; l < h->nc && l < DD_MAX_LEVELS; ++l) h->stats.sweeps_per_level[l] = h->h_state[4 * l + 1];
+    for (int l = 1; l < h->nc; ++l) h->stats.sweeps_total += h->h_state[4 * l + 1];
 }
 
 // Fine-level launches enqueued before the first read-back.
@@ -992,7 +994,7 @@ int first_chunk(const dd_inpaint* h) {
 // iterate with its FP64-accurate residual, and the read-back of everything the
 // finish step needs (level states, flags, reference norms, pixel counts).
 int enqueue_output_readback(dd_inpaint* h, float* u_out, double tol, cudaStream_t st, bool capture, bool timed) {
-    const int nl = (int)h->lv.size();
+    const int nl = h->nc;
     Level& F = h->lv[0];
     DD_TRY(output_and_residual(h, u_out, st));
     DD_CK(cudaMemcpyAsync(h->h_state, F.state_d, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1478,9 +1480,17 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         int hh = H, ww = W, l = 1;
         while (l < nl && hh > 2 && ww > 2) { hh = (hh + 1) / 2; ww = (ww + 1) / 2; ++l; }
         nl = l;
+        h->nc = nl;
+        // the small-grid coarse CG of the correction holds its level in shared memory:
+        // correction-only levels continue the 2x2 restriction below the cascade's
+        // coarsest level until one fits (no sweeps on them)
+        if (p.ml_mode == DD_ML_CORRECTION && p.correction_cg > 0 && nl >= 2)
+            while ((long long)hh * ww > dd::kCoarseCgMaxPixels && nl < DD_MAX_LEVELS && hh > 2 && ww > 2) {
+                hh = (hh + 1) / 2; ww = (ww + 1) / 2; ++nl;
+            }
     }
     h->lv.resize(nl);
-    for (int l = 0; l < nl; ++l) h->lv[l].solved = (l % fstep == 0) || l == nl - 1;
+    for (int l = 0; l < nl; ++l) h->lv[l].solved = l < h->nc && ((l % fstep == 0) || l == h->nc - 1);
     int hh = H, ww = W;
     for (int l = 0; l < nl; ++l) {
         Level& L = h->lv[l];
@@ -1534,7 +1544,7 @@ int create_impl(int H, int W, int C, const uint8_t* mask, const float* values, c
         if (p.correction_cg > 0) {   // the small-grid CG holds the coarsest level in shared memory
             const Level& Lc = h->lv.back();
             if ((long long)Lc.H * Lc.W > dd::kCoarseCgMaxPixels) {
-                set_error("correction_cg: the coarsest level has more than 12288 pixels (add levels)");
+                set_error("correction_cg: no level of at most 12288 pixels within 8 dyadic levels");
                 return fail(DD_EINVAL);
             }
             if (dd::prepare_coarse_cg() != cudaSuccess) {

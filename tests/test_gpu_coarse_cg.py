@@ -115,8 +115,29 @@ def test_correction_with_coarse_cg_on_a_large_hole():
     assert st["sweeps_per_level"][0] < out["cascade"][1]["sweeps_per_level"][0]
 
 
-def test_correction_cg_rejects_a_coarsest_level_too_large():
-    f, m = synth.make_frame(256, 256, 1, 0.05, "uniform", 3)
+def test_correction_cg_below_a_shallow_cascade():
+    """A 2-level cascade on 480 x 640: its coarsest level (240 x 320) is too
+    large for the small-grid CG, so the correction restricts on through
+    correction-only levels down to 60 x 80; the cascade itself keeps 2 levels."""
+    H, W = 480, 640
+    f, m = synth.make_frame(H, W, 3, 0.03, "uniform", 17)
+    yy, xx = np.mgrid[:H, :W]
+    m = m.copy()
+    m[(yy - H / 2) ** 2 + (xx - W / 2) ** 2 < (0.3 * min(H, W)) ** 2] = 0
+    with Inpainter(m, f, block=32, overlap=4, local_cg_iters=20, local_rtol=0.05, robin_p=0.15, levels=2,
+                   coarse_tol=3e-3, precision="fp32", max_sweeps=400, ml_mode="correction", correction_trigger=0.5,
+                   correction_cg=500) as ip:
+        u = ip.solve(1e-6).cpu().numpy()
+        st = ip.stats()
+    assert st["converged"] and st["coarse_corrections"] >= 1
+    assert st["sweeps_per_level"][1] > 0 and all(n == 0 for n in st["sweeps_per_level"][2:])
+    assert np.max(np.abs(u - ref.solve_direct(f, m))) <= 0.05
+    assert np.all(ref.rel_residual(u.astype(np.float64), f, m) <= 1e-6)
+
+
+def test_correction_cg_rejects_a_frame_with_no_small_level():
+    # 3 x 60000: the restriction stops at 2 rows, every level keeps more than 12288 pixels
+    f, m = synth.make_frame(3, 60000, 1, 0.05, "uniform", 3)
     with pytest.raises(B.DDError) as ei:
-        Inpainter(m, f, levels=2, precision="fp32", ml_mode="correction", correction_cg=100)   # 128 x 128 > 12288
+        Inpainter(m, f, levels=2, precision="fp32", ml_mode="correction", correction_cg=100)
     assert ei.value.code == B.DD_EINVAL
