@@ -114,11 +114,13 @@ typedef struct dd_params {
                                 copies in flight are waited for, nothing faults) and the handle
                                 stays usable.  It exercises the timeout path without a fault */
     double correction_trigger; /* DD_ML_CORRECTION: 0 (default) corrects after every fine sweep.  In
-                                (0, 1): the fine sweeps run alone until the first pass that reduced
-                                the fine relative residual by less than this factor (w_n > trigger
-                                w_{n-1}): plain sweeps have slowed down to the contraction of a
-                                smooth error mode, which the coarse grid removes.  From the next
-                                sweep on every sweep is followed by the correction.  Decided on the
+                                (0, 1): the fine sweeps run alone until the second pass in a row
+                                that reduced the fine relative residual by less than this factor
+                                (w_n > trigger w_{n-1}) while it is still above 4 tol: plain sweeps
+                                have slowed down to the contraction of a smooth error mode, which
+                                the coarse grid removes.  From the next sweep on every sweep is
+                                followed by the correction; a correction that does not reduce the
+                                residual pauses them until a plain pass is slow again.  Decided on the
                                 device; in device loops the two phases are two graph loops, so the
                                 plain phase costs what the cascade alone does */
     double final_local_rtol; /* 0 (default): every sweep uses local_rtol.  In (0, 1): a sweep that the

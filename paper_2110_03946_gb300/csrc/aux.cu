@@ -1012,16 +1012,18 @@ __global__ void loop_begin_kernel(int* __restrict__ ctl, cudaGraphConditionalHan
 // corrections off (trigger 0) or paused (trigger > 0), [2] corrections
 // applied, [3] full fine sweeps seen at the last decision, [4] the last full
 // pass was corrected, [5] the trigger has fired, [6] gate launches (counted by
-// corr_gate_kernel).  prev[0]: the fine residual w at the last full pass
+// corr_gate_kernel), [7] consecutive slow passes.  prev[0]: the fine residual w at the last full pass
 // (w = norms2[2C], the worst relative residual of the latest full sweep's
 // input, i.e. of the previous pass's output); prev[1]: the contraction of the
 // slow pass that fired the trigger (or resumed the corrections).
 //  - A probe pass (state[1], the count of full sweeps, did not grow) changed
 //    no iterate: no correction, no history.
-//  - trigger > 0: until the first pass that reduced w by less than trigger (a
-//    slow pass: the residual is dominated by a smooth mode that the sweeps
-//    contract slowly) no pass is corrected; that pass sets [5], and the later
-//    passes are corrected.  trigger = 0: every pass is corrected.
+//  - trigger > 0: a pass that reduced w by less than trigger while w is still
+//    above kTriggerMargin tol is slow (the residual is dominated by a smooth
+//    mode that the sweeps contract slowly; close to tol a correction cannot
+//    pay).  No pass is corrected until the second slow pass in a row, which
+//    sets [5]; the later passes are corrected.  trigger = 0: every pass is
+//    corrected.
 //  - A corrected pass that reduced w by less than kGateRatio (after a trigger:
 //    by less than the slow pass's own contraction, if that is larger) switches
 //    corrections off: for good with trigger 0 (with the non-symmetric ORAS
@@ -1029,10 +1031,11 @@ __global__ void loop_begin_kernel(int* __restrict__ ctl, cudaGraphConditionalHan
 //    converges), and with a trigger only until a plain pass is slow again (a
 //    smooth correction can remove error without moving the residual much).
 constexpr double kGateRatio = 0.7;
+constexpr double kTriggerMargin = 4.0;
 
 __device__ int corr_gate_decide(const int* __restrict__ flag, const double* __restrict__ norms2, int C,
                                 const int* __restrict__ state, int* __restrict__ gate, double* __restrict__ prev,
-                                double trigger) {
+                                double trigger, const double* __restrict__ tol) {
     int skip = flag[0] != 0 || (trigger <= 0.0 && gate[1] != 0);
     if (!skip) {
         const int nfull = state[1];
@@ -1041,9 +1044,10 @@ __device__ int corr_gate_decide(const int* __restrict__ flag, const double* __re
         } else {
             gate[3] = nfull;
             const double w = norms2[2 * C], wp = prev[0];
-            const bool slow = trigger > 0.0 && wp > 0.0 && w > trigger * wp;
-            if (trigger > 0.0 && gate[5] == 0) {   // plain passes until a slow one
-                if (slow) {
+            const bool slow = trigger > 0.0 && wp > 0.0 && w > trigger * wp && w > kTriggerMargin * tol[0];
+            gate[7] = slow ? gate[7] + 1 : 0;
+            if (trigger > 0.0 && gate[5] == 0) {   // plain passes until the second slow one in a row
+                if (gate[7] >= 2) {
                     gate[5] = 1;
                     prev[1] = w / wp;
                 }
@@ -1071,10 +1075,10 @@ __device__ int corr_gate_decide(const int* __restrict__ flag, const double* __re
 // The gate ahead of the correction kernels, which read gate[0].
 __global__ void corr_gate_kernel(const int* __restrict__ flag, const double* __restrict__ norms2, int C,
                                  const int* __restrict__ state, int* __restrict__ gate, double* __restrict__ prev,
-                                 double trigger) {
+                                 double trigger, const double* __restrict__ tol) {
     if (threadIdx.x != 0) return;
     gate[6] += 1;
-    (void)corr_gate_decide(flag, norms2, C, state, gate, prev, trigger);
+    (void)corr_gate_decide(flag, norms2, C, state, gate, prev, trigger, tol);
 }
 
 __global__ void loop_ctl_kernel(const int* __restrict__ flag, const int* __restrict__ state, int* __restrict__ ctl,
@@ -1091,9 +1095,10 @@ __global__ void loop_ctl_kernel(const int* __restrict__ flag, const int* __restr
 __global__ void loop_ctl_trigger_kernel(const int* __restrict__ flag, const int* __restrict__ state,
                                         int* __restrict__ ctl, int cap, int max_passes,
                                         cudaGraphConditionalHandle cond, const double* __restrict__ norms2, int C,
-                                        int* __restrict__ gate, double* __restrict__ prev, double trigger) {
+                                        int* __restrict__ gate, double* __restrict__ prev, double trigger,
+                                        const double* __restrict__ tol) {
     if (threadIdx.x != 0) return;
-    (void)corr_gate_decide(flag, norms2, C, state, gate, prev, trigger);
+    (void)corr_gate_decide(flag, norms2, C, state, gate, prev, trigger, tol);
     const int passes = ctl[0] + 1;
     ctl[0] = passes;
     if (flag[0] != 0 || state[1] >= cap || passes >= max_passes || gate[5] != 0) cudaGraphSetConditional(cond, 0);
@@ -1291,8 +1296,8 @@ cudaError_t launch_restrict_sum(int H, int W, int C, const float* src, int sp, l
 }
 
 cudaError_t launch_corr_gate(const int* flag, const double* norms2, int C, const int* state, int* gate, double* prev,
-                             double trigger, cudaStream_t st) {
-    corr_gate_kernel<<<1, 32, 0, st>>>(flag, norms2, C, state, gate, prev, trigger);
+                             double trigger, const double* tol, cudaStream_t st) {
+    corr_gate_kernel<<<1, 32, 0, st>>>(flag, norms2, C, state, gate, prev, trigger, tol);
     return cudaGetLastError();
 }
 
@@ -1339,9 +1344,9 @@ cudaError_t launch_loop_ctl(const int* flag, const int* state, int* ctl, int cap
 
 cudaError_t launch_loop_ctl_trigger(const int* flag, const int* state, int* ctl, int cap, int max_passes,
                                     cudaGraphConditionalHandle cond, const double* norms2, int C, int* gate,
-                                    double* prev, double trigger, cudaStream_t st) {
+                                    double* prev, double trigger, const double* tol, cudaStream_t st) {
     loop_ctl_trigger_kernel<<<1, 32, 0, st>>>(flag, state, ctl, cap, max_passes, cond, norms2, C, gate, prev,
-                                              trigger);
+                                              trigger, tol);
     return cudaGetLastError();
 }
 

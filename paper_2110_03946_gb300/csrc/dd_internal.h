@@ -242,12 +242,12 @@ cudaError_t launch_restrict_sum(int H, int W, int C, const float* src, int sp, l
 // (to 0) before a solve's fine loop.
 // The coarse-grid correction's gate (gate[0] = skip, read by the correction kernels).
 cudaError_t launch_corr_gate(const int* flag, const double* norms2, int C, const int* state, int* gate, double* prev,
-                             double trigger, cudaStream_t st);
+                             double trigger, const double* tol, cudaStream_t st);
 // Loop control of the plain phase of a fine level with a correction trigger: it
 // also ends the loop when the trigger fires.
 cudaError_t launch_loop_ctl_trigger(const int* flag, const int* state, int* ctl, int cap, int max_passes,
                                     cudaGraphConditionalHandle cond, const double* norms2, int C, int* gate,
-                                    double* prev, double trigger, cudaStream_t st);
+                                    double* prev, double trigger, const double* tol, cudaStream_t st);
 // Entry kernel of the corrected phase's loop: (ctl, flag, state, gate, cap, max_passes, cond).
 const void* loop_begin_corrected_kernel_fn();
 

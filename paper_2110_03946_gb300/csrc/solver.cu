@@ -670,7 +670,7 @@ int enqueue_correction_body(dd_inpaint* h, cudaStream_t st) {
 // The correction as plain launches: the gate and every kernel of the body.
 int enqueue_correction(dd_inpaint* h, cudaStream_t st) {
     DD_CK(dd::launch_corr_gate(h->flag_d, h->norms2_d, h->C, h->sstate_d, h->corr_gate, h->corr_prev,
-                               h->prm.correction_trigger, st));
+                               h->prm.correction_trigger, h->tol_d, st));
     return enqueue_correction_body(h, st);
 }
 
@@ -772,7 +772,7 @@ int add_loop(dd_inpaint* h, Level& L, int cap, cudaGraph_t g, const cudaGraphNod
             [&](cudaStream_t bs, cudaGraphConditionalHandle cw) {
                 return dd::launch_loop_ctl_trigger(h->flag_d, h->sstate_d, h->ctl_d, cap, max_passes, cw,
                                                    h->norms2_d, h->C, h->corr_gate, h->corr_prev,
-                                                   h->prm.correction_trigger, bs);
+                                                   h->prm.correction_trigger, h->tol_d, bs);
             }));
         return add_loop_fn(h, cap, max_passes, g, &plain, nullptr, 1, h->cap_stream,
                            [&](cudaStream_t bs) { return enqueue_pass(h, L, bs); }, last, {}, true);
