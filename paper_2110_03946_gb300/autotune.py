@@ -202,6 +202,8 @@ def main():
         f, m = synth.make_frame(w.H, w.W, w.C, dens, pat, w.seed_base + 50 + j)
         frames.append((torch.as_tensor(m).to(dev), torch.as_tensor(f).to(dev)))
     space = dict(SPACE, block=[int(b) for b in a.blocks.split(",")])
+    if a.precision != "fp32":   # the outer correction's inner tolerance (ignored by FP32 solves)
+        space["inner_tol"] = [1e-2, 3e-3, 1e-3]
     start = json.loads(a.start) if a.start else lookup(w.H, w.W, w.C, w.density, a.precision, a.tol, a.out,
                                                        nearest=False)
     if start:
