@@ -77,9 +77,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
@@ -399,19 +396,26 @@ oras_sweep_kernel(const __grid_constant__ SweepFrame one, const SweepFrame* __re
     // the TMA box of a block starts at the 16-byte aligned column at or left of x0 - 1
     auto box_x = [](int x0) { return ((x0 - 1) >= 0 ? (x0 - 1) / BOX::ALIGN : -1) * BOX::ALIGN; };
     int q_st = 0;   // thread 0: frame slot of the last staged tile (a CTA's tiles increase)
+    int q_map = -1;   // thread 0: the frame slot whose iterate map is cached in map_st
+    const CUtensorMap* map_st = nullptr;
     auto issue = [&](int tn, int buf) {   // thread 0 only
         while (q_st + 1 < n_act && tn >= end_at(q_st)) ++q_st;
         const SweepFrame* const F = frame_at(q_st);
+        if (q_map != q_st) {   // the buffer holding the frame's iterate is fixed for the launch
+            map_st = __ldcg(F->state) ? &F->map_u[1] : &F->map_u[0];
+            q_map = q_st;
+        }
         const int local = tn - begin_at(q_st);
         const int c = fdiv(local, F->dv_tiles);
         const int tile = local - c * F->ntiles;
         const int ty = fdiv(tile, F->dv_ntx), tx = tile - ty * F->ntx;
         const int x0 = tx * F->s, y0 = ty * F->s;
         const int xs = box_x(x0);
-        const CUtensorMap* const map = __ldcg(F->state) ? &F->map_u[1] : &F->map_u[0];
-        fence_proxy_async();
+        // (no proxy fence: the staging buffers are written only by these copies, and
+        // the generic reads of a buffer's previous tile ended at the barrier
+        // that closed its iteration)
         mbar_expect_tx(&mbar[buf], tx_bytes);
-        tma_load_3d(stage(buf, 0), map, xs, y0 - 1, c, &mbar[buf]);
+        tma_load_3d(stage(buf, 0), map_st, xs, y0 - 1, c, &mbar[buf]);
         if constexpr (HASG) tma_load_3d(stage(buf, 1), &F->map_g, xs, y0 - 1, c, &mbar[buf]);
         bulk_load(stage_mask(buf), F->tmask + (size_t)tile * 2 * NT, (uint32_t)MB, &mbar[buf]);
     };
