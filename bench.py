@@ -401,7 +401,7 @@ def run_serving(dev, params):
     """Poisson arrivals at 60 requests/s for 4 s: 70 % 4K, 20 % 1080p, 10 %
     720p RGB video sequences of 30 frames (shift 1..3 px + noise, warm start
     from the previous frame), uniform masks of density U[2 %, 8 %], pinned host
-    inputs and outputs, 40 GB HBM budget; three slots per shape are created
+    inputs and outputs, 40 GB HBM budget; four slots per shape are created
     before the first arrival (Server.prewarm: the concurrency this stream
     reaches, so no request waits for a slot's allocations and graphs) and a
     1 s stream of other sequences runs before the measured one."""
@@ -412,7 +412,7 @@ def run_serving(dev, params):
     per_shape = {s_: shape_params(s_[0], s_[1], s_[2], 0.05, "fp32", params) for s_ in shapes}
     srv = Server(CudaBackend(params, tol=TOL, device=dev, per_shape=per_shape), hbm_budget=40 << 30)
     try:
-        prewarmed = srv.prewarm(reqs, per_shape=3)   # slots created before the stream starts
+        prewarmed = srv.prewarm(reqs, per_shape=4)   # slots created before the stream starts
         # a 1 s stream of other sequences first: the measured stream then sees a
         # server in steady state (kernels loaded, slots in use)
         srv.run(poisson_stream(60.0, 1.0, shapes, [0.7, 0.2, 0.1], 30, 5002, pool), realtime=True)
