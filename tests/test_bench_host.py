@@ -51,5 +51,9 @@ def test_solver_params_tuned_then_overrides():
     assert "overlap overridden" in src2 and "device loops off" in src2
     prm4, src4 = bench.solver_params(_args(final_rtol=0.0), "fp32")
     assert prm4["final_local_rtol"] == 0.0 and "final_local_rtol overridden" in src4
+    prm5, src5 = bench.solver_params(_args(ml_mode="correction", trigger=0.9, correction_cg=300, local_atol=0.5,
+                                           local_rtol=0.02), "fp32")
+    assert (prm5["ml_mode"], prm5["correction_trigger"], prm5["correction_cg"]) == ("correction", 0.9, 300)
+    assert prm5["local_atol"] == 0.5 and prm5["local_rtol"] == 0.02 and "correction_cg overridden" in src5
     prm3, src3 = bench.solver_params(_args(no_tuned=True), "fp32")
     assert prm3 == bench.PAPER_DEFAULTS and src3.startswith("defaults")
